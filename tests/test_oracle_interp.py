@@ -1,0 +1,102 @@
+"""Pins for the oracle's ramp filter and FBP (Sec. 2.2, Eqs. 12-14), Lanczos-3 upsampler
+(Sec. 2.3, Eqs. 16-17) and projection subsampling (Sec. 2.3)."""
+import math
+import os
+
+import numpy as np
+
+import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def read_golden(name):
+    vals = {}
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.split("#", 1)[0].strip()
+            if line:
+                k, v = line.split()
+                vals[k] = float(v)
+    return vals
+
+
+def test_ramp_kernel_has_ramp_spectrum(orc):
+    nd = 2048
+    g = np.zeros((1, nd))
+    g[0, nd // 2] = 1.0
+    h = orc.ramp_filter(g)[0]  # impulse response, centred
+    n = np.arange(nd) - nd // 2
+    for w in (0.0, 0.05, 0.2, 0.37, 0.5):
+        H = np.sum(h * np.cos(2 * np.pi * w * n))
+        assert abs(H - w) < 2e-4
+    gold = read_golden("ramlak.txt")
+    assert abs(h[nd // 2] - gold["h0"]) < 1e-15
+    assert abs(h[nd // 2 + 1] - gold["h1"]) < 1e-15 and abs(h[nd // 2 - 3] - gold["h3"]) < 1e-15
+    assert h[nd // 2 + 2] == 0.0
+
+
+def test_fbp_reconstructs_blob(orc):
+    N, na = 48, 180
+    th = synth.angles(na)
+    g = synth.gaussian_blob_projections(th, N, 3.0, -2.0, 3.0)
+    f0 = orc.fbp(g, N, th, np.pi)
+    ref = synth.gaussian_blob(N, 3.0, -2.0, 3.0)
+    # pixels outside the inscribed disc wrap around the periodic detector; compare inside it
+    cc = np.arange(N) - N // 2
+    m = np.hypot(cc[None, :], cc[:, None]) < N // 2 - 2
+    assert np.linalg.norm((f0 - ref)[m]) / np.linalg.norm(ref[m]) < 1e-3
+
+
+def test_fbp_disk_interior(orc):
+    N, na = 48, 360
+    th = synth.angles(na)
+    e = synth.Ellipses(*(np.array([v]) for v in (0.0, 0.0, 15.0, 15.0, 0.0, 1.0)))
+    f0 = orc.fbp(synth.ellipse_projections(e, th, N), N, th, np.pi)
+    cc = np.arange(N) - N // 2
+    r = np.hypot(cc[None, :], cc[:, None])
+    interior = f0[r < 11]
+    # sharp edges ring (Gibbs) under band-limited interpolation; the level must be right
+    assert abs(interior.mean() - 1.0) < 0.01 and interior.std() < 0.06
+    assert np.abs(f0[(r > 19) & (r < N // 2 - 1)]).mean() < 0.04
+
+
+def test_lanczos_values(orc):
+    gold = read_golden("lanczos3.txt")
+    assert orc.lanczos(0.0) == 1.0
+    for k in (1, 2, -1, -2):
+        assert abs(orc.lanczos(float(k))) < 1e-15
+    assert orc.lanczos(3.0) == 0.0 and orc.lanczos(-3.5) == 0.0
+    assert abs(orc.lanczos(0.5) - gold["L0.5"]) < 1e-5 and abs(orc.lanczos(0.5) - 6 / math.pi ** 2) < 1e-15
+    assert abs(orc.lanczos(1.5) - gold["L1.5"]) < 1e-5
+    assert abs(orc.lanczos(2.5) - gold["L2.5"]) < 1e-5
+    assert abs(orc.lanczos(-1.5) - orc.lanczos(1.5)) < 1e-16
+
+
+def test_lanczos_upsampling(orc):
+    rng = np.random.default_rng(31)
+    x = rng.standard_normal((2, 12, 12))
+    up = orc.lanczos_up(x)
+    assert up.shape == (2, 24, 24)
+    assert np.array_equal(up[:, ::2, ::2], x)  # node exactness
+    # constants and linear ramps are reproduced away from the zero-extended border
+    c = orc.lanczos_up(np.full((16, 16), 2.5))
+    assert np.allclose(c[6:-6, 6:-6], 2.5, atol=1e-14)
+    i = np.arange(16, dtype=float)
+    ramp = np.add.outer(0.3 * i, -0.7 * i)
+    u = orc.lanczos_up(ramp)
+    j = np.arange(32) / 2.0
+    assert np.allclose(u[6:-6, 6:-6], np.add.outer(0.3 * j, -0.7 * j)[6:-6, 6:-6], atol=1e-12)
+    # a smooth band-limited signal is interpolated accurately
+    s = np.cos(2 * np.pi * 0.06 * i)
+    us = orc.lanczos_up(np.outer(np.ones(16), s))
+    assert np.max(np.abs(us[8, 8:-8] - np.cos(2 * np.pi * 0.06 * j[8:-8]))) < 5e-3
+
+
+def test_downsample_sino(orc):
+    g = np.arange(2 * 3 * 16, dtype=float).reshape(2, 3, 16)
+    d = orc.downsample_sino(g, 4)
+    assert d.shape == (2, 3, 4)
+    assert np.array_equal(d, g[:, :, ::4] / 4)
+    # the centre bin nd/2 maps to the coarse centre bin
+    assert d[0, 0, 2] == g[0, 0, 8] / 4

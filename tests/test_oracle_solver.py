@@ -1,0 +1,124 @@
+"""Pins for the oracle's objective, gradient and optimisers (Sec. 2, Eqs. 5-6, 10-11).
+
+The quadratic special case (p = q = 2) makes the whole problem linear; its minimiser
+is then the solution of a dense linear system built here from the explicit
+non-uniform DFT matrix and the graph Laplacian of the neighbour weights, solved by
+numpy.linalg.solve.
+"""
+import itertools
+
+import numpy as np
+
+import synth
+from test_oracle_radon import nudft_forward
+
+
+def small_problem(orc, N=10, nd=12, na=7, S=1, seed=21):
+    rng = np.random.default_rng(seed)
+    th = synth.angles(na)
+    x_true = rng.uniform(0, 1, (S, N, N))
+    g = np.stack([orc.forward(s, th, nd) for s in x_true]) + rng.normal(0, 0.05, (S, na, nd))
+    K = orc.kernel(N, th, nd)
+    atg = orc.adjoint(g, N, th)
+    return th, g, K, atg, float(np.sum(g * g))
+
+
+def test_toeplitz_objective_equals_eq5(orc):
+    pr = orc.Prior()
+    th, g, K, atg, gtg = small_problem(orc, S=2)
+    rng = np.random.default_rng(22)
+    for _ in range(3):
+        x = rng.normal(0.5, 0.2, atg.shape)
+        assert abs(orc.objective(x, atg, gtg, K, pr) - orc.objective_direct(x, g, th, pr)) < 1e-10 * orc.objective_direct(x, g, th, pr)
+
+
+def test_gradient_is_derivative_of_eq5(orc):
+    pr = orc.Prior()
+    th, g, K, atg, gtg = small_problem(orc, S=2)
+    x = np.random.default_rng(23).normal(0.5, 0.2, atg.shape)
+    G = orc.gradient(x, atg, K, pr)
+    h = 1e-6
+    for idx in [(0, 0, 0), (1, 4, 7), (0, 9, 3), (1, 5, 5)]:
+        xp = x.copy()
+        xp[idx] += h
+        xm = x.copy()
+        xm[idx] -= h
+        fd = (orc.objective_direct(xp, g, th, pr) - orc.objective_direct(xm, g, th, pr)) / (2 * h)
+        assert abs(G[idx] - fd) < 1e-5 * max(1.0, abs(fd))
+
+
+def test_power_iteration_bounds_largest_eigenvalue(orc):
+    N, nd = 8, 10
+    th = synth.angles(9)
+    K = orc.kernel(N, th, nd)
+    A = np.stack([nudft_forward(e.reshape(N, N), th, nd).ravel() for e in np.eye(N * N)], axis=1)
+    lmax = np.linalg.eigvalsh(A.T @ A).max()
+    est = orc.power_lambda_max(K, N)
+    assert est <= lmax * (1 + 1e-12) and est >= 0.995 * lmax
+
+
+def gaussian_mrf_laplacian(orc, S, N):
+    """Hessian of Phi for p = q = 2 (rho = D^2 / (2 sigma^2)) times sigma^2: weighted graph Laplacian."""
+    n = S * N * N
+    H = np.zeros((n, n))
+    idx = lambda z, r, c: (z * N + r) * N + c
+    for z, r, c in itertools.product(range(S), range(N), range(N)):
+        for dz, dy, dx in itertools.product((-1, 0, 1), repeat=3):
+            if (dz, dy, dx) == (0, 0, 0):
+                continue
+            z2, r2, c2 = z + dz, r + dy, c + dx
+            if 0 <= z2 < S and 0 <= r2 < N and 0 <= c2 < N:
+                b = orc.neighbour_weight(dz, dy, dx)
+                H[idx(z, r, c), idx(z, r, c)] += b
+                H[idx(z, r, c), idx(z2, r2, c2)] -= b
+    return H
+
+
+def test_quadratic_case_reaches_linear_solve(orc):
+    S, N, nd, na = 2, 6, 8, 5
+    pr = orc.Prior(p=2.0, q=2.0, sigma=0.5, lam=0.3)
+    rng = np.random.default_rng(24)
+    th = synth.angles(na)
+    g = rng.uniform(0, 1, (S, na, nd))
+    A = np.stack([nudft_forward(e.reshape(N, N), th, nd).ravel() for e in np.eye(N * N)], axis=1)
+    H = np.kron(np.eye(S), A.T @ A) + pr.lam / pr.sigma ** 2 * gaussian_mrf_laplacian(orc, S, N)
+    rhs = np.concatenate([A.T @ g[s].ravel() for s in range(S)])
+    x_star = np.linalg.solve(H, rhs).reshape(S, N, N)
+    K = orc.kernel(N, th, nd)
+    atg = orc.adjoint(g, N, th)
+    L = orc.lipschitz(K, N, pr)
+    x = orc.nesterov(np.zeros((S, N, N)), atg, float(np.sum(g * g)), K, pr, L, 3000)
+    assert np.linalg.norm(x - x_star) < 1e-6 * np.linalg.norm(x_star)
+    xg = orc.gradient_descent(np.zeros((S, N, N)), atg, K, pr, L, 200)
+    # plain descent is slower than the accelerated method from the same start
+    assert np.linalg.norm(xg - x_star) > np.linalg.norm(orc.nesterov(np.zeros((S, N, N)), atg, float(np.sum(g * g)), K, pr, L, 200) - x_star)
+
+
+def test_descent_is_monotone_and_nesterov_reaches_same_minimum(orc):
+    pr = orc.Prior()
+    th, g, K, atg, gtg = small_problem(orc, N=10, S=2)
+    N = 10
+    L = orc.lipschitz(K, N, pr)
+    x = np.zeros_like(atg)
+    F = [orc.objective(x, atg, gtg, K, pr)]
+    for _ in range(30):
+        x = orc.gradient_descent(x, atg, K, pr, L, 1)
+        F.append(orc.objective(x, atg, gtg, K, pr))
+    assert all(b <= a + 1e-12 * abs(a) for a, b in zip(F, F[1:]))
+    xa = orc.nesterov(np.zeros_like(atg), atg, gtg, K, pr, L, 4000)
+    xb = orc.gradient_descent(xa, atg, K, pr, L, 2000)
+    Fa, Fb = orc.objective(xa, atg, gtg, K, pr), orc.objective(xb, atg, gtg, K, pr)
+    assert Fa - Fb < 1e-8 * abs(Fb)
+
+
+def test_restart_log(orc):
+    pr = orc.Prior()
+    th, g, K, atg, gtg = small_problem(orc, N=10, S=1)
+    L = orc.lipschitz(K, 10, pr)
+    log = []
+    orc.nesterov(np.zeros_like(atg), atg, gtg, K, pr, L, 60, log=log)
+    assert len(log) == 60
+    # F(y_0) at y_0 = x_0 = 0 is 1/2 g.g
+    assert abs(log[0][0] - 0.5 * gtg) < 1e-12 * gtg
+    assert all((d > 0) == r for _, d, r in log)
+    assert log[-1][0] < 0.5 * log[0][0]
