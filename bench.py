@@ -1,0 +1,327 @@
+"""Benchmark: gradient voxel-updates/s of the Toeplitz MBIR path on GB300.
+
+One step = one full reconstruction of a synthetic batch through the C ABI, with the
+sinogram already resident on the device:
+  build_operator (kernel K, its 2N x 2N spectrum, R*g, 1/2 g.g, lambda_max)  -- setup, FP64
+  fbp (ramp-filtered back-projection start)
+  reconstruct (100 fast-gradient iterations replayed from one CUDA graph).
+value = slices * N^2 * iterations / step time, summed over ranks (each rank reconstructs its
+own independent batch: weak scaling, no collective on the data path).
+
+The default workload is 64 slices of 1024^2, 256 angles over [0, pi), 100 iterations.
+`--impl reference` times the FP64 CPU oracle on the host cores instead, on a bounded
+sample of the same workload (iteration phase only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: (slices, N, angles, span, iterations, ellipsoids)
+    "batched-64x1024sq-256ang-100it": (64, 1024, 256, math.pi, 100, 20),
+    "single-1x128sq-90ang-50it": (1, 128, 90, math.pi, 50, 10),
+    "small-8x256sq-128ang-50it": (8, 256, 128, math.pi, 50, 10),
+}
+DEFAULT = "batched-64x1024sq-256ang-100it"
+PRIOR = dict(p=1.2, q=2.0, c=0.01, sigma=0.1, lam=1.0)
+METRIC = "gradient voxel-updates/s"
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def make_problem(name, rank):
+    import synth
+
+    S, N, na, span, iters, ne = WORKLOADS[name]
+    p = synth.volume(S=S, N=N, n_angles=na, n_ellipsoids=ne, span=span, seed=1002 + 17 * rank)
+    return p, iters
+
+
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [v.strip() for v in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = max(float(r[2]) for r in rows if r[2].replace(".", "").isdigit())
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if "Active" in r[5 + k] and "Not" not in r[5 + k]})
+        load = [v for v in sm if v > 0.5 * smax] or sm
+        return {"sm_mhz": statistics.median(load), "sm_max_mhz": smax, "reasons": reasons, "samples": len(rows)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_traffic(kernel, workload):
+    """DRAM bytes per launch from the committed ncu summary, if it matches the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        src = os.path.join(ROOT, "paper_2603_28756_gb300", "csrc", "toeplitz_kernels.cuh")
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        e = d.get(workload, {}).get(kernel)
+        if e and e.get("source_sha") == h:
+            return e["dram_bytes_per_launch"]
+    except Exception:
+        pass
+    return None
+
+
+def cpu_baseline(name, samples_slices=2, samples_iters=2):
+    """FP64 oracle on the host cores: iteration phase of the same workload on a bounded sample."""
+    import numpy as np
+
+    import oracle
+    import synth
+
+    S, N, na, span, iters, _ = WORKLOADS[name]
+    th = synth.angles(na, span)
+    rng = np.random.default_rng(5)
+    s = min(samples_slices, S)
+    x0 = rng.uniform(0, 0.5, (s, N, N))
+    atg = rng.uniform(0, 1.0, (s, N, N))
+    pr = oracle.Prior(**PRIOR)
+    t0 = time.perf_counter()
+    K = oracle.kernel(N, th, N)
+    t_setup = time.perf_counter() - t0
+    Chat = oracle.circulant_spectrum(K)
+    L = 1.01 * 50.0 + pr.lam * 4.0 / pr.sigma ** 2
+    t0 = time.perf_counter()
+    oracle.nesterov(x0, atg, 1.0, K, pr, L, samples_iters, Chat=Chat)
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {
+        "value": s * N * N * samples_iters / dt,
+        "unit": "voxel-updates/s",
+        "cores": cores,
+        "kind": "oracle",
+        "sample": f"{s} of {S} slices x {samples_iters} of {iters} iterations at {N}^2, {na} angles; "
+                  f"iteration phase only (kernel K setup {t_setup:.1f} s excluded); numpy FFT single-threaded, "
+                  f"prior in C with OpenMP",
+    }
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    cb = cpu_baseline(args.workload)
+    S, N, na, span, iters, _ = WORKLOADS[args.workload]
+    # each step: the bounded oracle sample; the line reports its rate
+    vals = []
+    for _ in range(args.warmup):
+        cpu_baseline(args.workload)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        vals.append(cpu_baseline(args.workload)["value"])
+    el = time.perf_counter() - t0
+    v = statistics.mean(vals)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "voxel-updates/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / max(args.steps, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "slices": S, "N": N, "angles": na, "iterations": iters},
+        "cpu_baseline": dict(cb, value=v),
+        "e2e": {"value": v, "unit": "voxel-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import numpy as np
+    import torch
+
+    import paper_2603_28756_gb300 as tm
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    S, N, na, span, iters, _ = WORKLOADS[args.workload]
+    prob, iters = make_problem(args.workload, rank)
+    ctx = tm.Context([tm.Group(N=N, angles=list(prob.theta), n_slices=S, span=span)])
+    stream = ctx.stream
+    sino = torch.from_numpy(prob.sino.ravel()).cuda()
+    with torch.cuda.stream(stream):
+        atg = torch.empty(S * N * N, dtype=torch.float32, device="cuda")
+        x = torch.empty_like(atg)
+    prm = tm.Params(**PRIOR, max_iter=iters, use_graph=True)
+    torch.cuda.synchronize()
+
+    def step():
+        ctx.build_operator(sino, atg)
+        ctx.fbp(sino, x)
+        ctx.reconstruct(x, atg, prm, want_stats=False)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    clocks = Clocks(local)
+    n0 = ctx.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    launches = ctx.launch_count() - n0
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    vox = S * N * N * iters
+    value = world * vox * args.steps / (ms * 1e-3)
+
+    # one reconstruction's stats (outside the timed region): convergence sanity
+    st = ctx.reconstruct(x, atg, prm)
+
+    # per-pass device times, eager, on the context stream (iteration phase only)
+    ctx.fbp(sino, x)
+    pt = ctx.pass_times(x, atg, tm.Params(**PRIOR), iters)
+    it_ms = sum(pt)
+    names = ["pass1_rows_fwd", "pass2_columns", "pass3_rows_grad_update", "finalize"]
+    top = max(range(3), key=lambda k: pt[k])
+    bpv = [8.0 + 8.0 * (N + 1) / N, 16.0 * (N + 1) / N, 8.0 * (N + 1) / N + 4 + 8 + 4][top]
+    alg_bytes = bpv * S * N * N
+    achieved = alg_bytes / (pt[top] / iters * 1e-3) / 1e9
+    peak, peak_kind = measured_peaks()
+
+    # end to end through the C ABI with host buffers: H2D sinogram, step, D2H image
+    h_sino = torch.from_numpy(prob.sino.ravel()).pin_memory()
+    h_x = torch.empty(S * N * N, dtype=torch.float32).pin_memory()
+    d_sino = torch.empty_like(sino)
+    barrier()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    with torch.cuda.stream(stream):
+        for _ in range(args.steps):
+            d_sino.copy_(h_sino, non_blocking=True)
+            ctx.build_operator(d_sino, atg)
+            ctx.fbp(d_sino, x)
+            ctx.reconstruct(x, atg, prm, want_stats=False)
+            h_x.copy_(x, non_blocking=True)
+    f1.record(stream)
+    barrier()
+    e2e_ms = f0.elapsed_time(f1)
+    if world > 1:
+        t = torch.tensor([e2e_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+
+    if rank == 0:
+        line = {
+            "metric": METRIC,
+            "value": value,
+            "unit": "voxel-updates/s",
+            "n_gpus": world,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": ms / args.steps,
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f32",
+            "data": "synthetic",
+            "config": {
+                "workload": args.workload, "slices": S, "N": N, "angles": na, "span": span, "iterations": iters,
+                "step": "build_operator + fbp + reconstruct(graph)", "l2": "working set > L2 (no explicit flush)",
+                "parallelism": f"replicas{world}",
+            },
+            "iteration_phase": {
+                "voxel_updates_per_s": vox / (it_ms * 1e-3), "ms_per_iteration": it_ms / iters,
+                "ms_per_pass": dict(zip(names, [v / iters for v in pt])),
+            },
+            "roofline": {
+                "kernel": names[top], "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": peak_kind, "algorithmic_bytes_per_voxel": bpv,
+                "traffic": kernel_traffic(names[top], args.workload),
+            },
+            "e2e": {"value": world * vox * args.steps / (e2e_ms * 1e-3), "unit": "voxel-updates/s",
+                    "h2d_bytes_per_step": sino.numel() * 4, "d2h_bytes_per_step": x.numel() * 4},
+            "gpu_launches": launches,
+            "clocks": clk,
+            "last_run": {"objective": st.objective, "restarts": st.restarts, "L": st.L, "status": st.status},
+        }
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(args.workload)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,214 @@
+/*
+ * tmbir.h -- C ABI of the Toeplitz-accelerated MBIR gradient path (Kumar & Donatelli,
+ * "Fast Large-Scale Model-Based Iterative Tomography ...").
+ *
+ * The library reconstructs stacks of parallel-beam slices by minimising Eq. 5,
+ *     F(f) = 1/2 ||R f - g||^2 + lambda Phi(f),
+ * with the fast gradient method of Sec. 2.  Every gradient uses the Toeplitz form of
+ * Sec. 2.1 (Eqs. 9-11): R*R f is a zero-padded 2N x 2N FFT convolution with the
+ * point-spread kernel K, and R*g is precomputed once.  Phi is the qGGMRF prior over the
+ * 26-voxel neighbourhood (Sec. 2, Sec. 2.4).
+ *
+ * Conventions
+ *   - Every call returns an int status: TMBIR_OK (0) or a negative TMBIR_ERR_* code;
+ *     tmbir_last_error() gives a message for the calling thread.  No exception crosses
+ *     the ABI.
+ *   - Work is enqueued asynchronously on the CUDA stream bound at tmbir_create.  Calls
+ *     that return host values (stats, objective, lambda_max) synchronise that stream.
+ *   - Pointers named d_* are device pointers, h_* host pointers.  The caller owns every
+ *     device buffer, including the workspace sized by tmbir_workspace_size; the library
+ *     allocates no device memory.  Device buffers must be 16-byte aligned.
+ *   - Images are float32 [slice][row][col] (row-major N x N per slice); pixel (r, c) sits at
+ *     x = c - N/2, y = r - N/2.  Sinograms are float32 [slice][angle][bin]; bin m sits at
+ *     s = m - n_det/2.  An angle theta projects onto s = x cos(theta) + y sin(theta).
+ *   - Radial frequencies are k / n_det with |k| <= n_det/2 - 1: the Nyquist bin is dropped,
+ *     so R is real and R*R is exactly Toeplitz.
+ */
+#ifndef TMBIR_H
+#define TMBIR_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  TMBIR_OK = 0,
+  TMBIR_ERR_ARG = -1,       /* null pointer, bad value, misaligned buffer */
+  TMBIR_ERR_SHAPE = -2,     /* unsupported size (N, n_det, factorisation of 2N) */
+  TMBIR_ERR_WORKSPACE = -3, /* no workspace bound, or too small */
+  TMBIR_ERR_CUDA = -4,      /* a CUDA runtime call failed */
+  TMBIR_ERR_TIMEOUT = -5,   /* a bounded device wait gave up */
+  TMBIR_ERR_NONFINITE = -6, /* NaN or Inf in a reduction */
+  TMBIR_ERR_STATE = -7      /* call order (no geometry, operator not built) */
+};
+
+enum { TMBIR_RESTART_GRADIENT = 0, TMBIR_RESTART_NONE = 1 };
+enum { TMBIR_SPECTRA_FP32 = 0, TMBIR_SPECTRA_BF16 = 1 };
+
+typedef struct tmbir_ctx tmbir_ctx;
+
+/*
+ * One geometry group: n_slices slices of N x N pixels seen under the same n_angles
+ * parallel-beam angles by n_det detector bins (Sec. 2, Eq. 1).  Slices of a group are
+ * coupled by the 3D prior; different groups are independent.
+ *   N        image side; 64 <= N <= 1024 and a power of two.
+ *   n_det    detector bins; must equal N (pixel pitch = bin pitch).
+ *   angles   host array of n_angles radians; copied by tmbir_set_geometry.
+ *   span     angular range covered by the angles (pi for a full half turn); the FBP
+ *            quadrature weight is span / n_angles (Eq. 14).
+ */
+typedef struct {
+  int N;
+  int n_det;
+  int n_angles;
+  const double* angles;
+  double span;
+  int n_slices;
+} tmbir_group;
+
+/*
+ * Prior and optimiser parameters (Eq. 5-6, Sec. 2).
+ *   p, q, c, sigma  qGGMRF potential rho(D) = |D/sigma|^q / (1 + |D/(c sigma)|^(q-p)),
+ *                   1 <= p <= q; q = 2 is the fast path.
+ *   lambda          prior weight.
+ *   L               step constant; <= 0 selects 1.01 lambda_max(R*R) + lambda*2*(2/sigma^2)
+ *                   (needs q = 2 and a built operator).
+ *   max_iter        iterations of the fast gradient method.
+ *   gap_tol, F_ref  stop early once (F(y_k) - F_ref) / (F(0) - F_ref) <= gap_tol
+ *                   (gap_tol <= 0 disables it).
+ *   restart         TMBIR_RESTART_GRADIENT: momentum restarts when <grad F(y_k), x_{k+1}-x_k> > 0.
+ *   use_graph       capture the iterations in a CUDA graph and replay it.
+ */
+typedef struct {
+  double p, q, c, sigma, lambda;
+  double L;
+  int max_iter;
+  double gap_tol;
+  double F_ref;
+  int restart;
+  int use_graph;
+} tmbir_params;
+
+/* Result of tmbir_reconstruct (host struct filled on return). */
+typedef struct {
+  int iterations;   /* iterations run */
+  int restarts;     /* momentum restarts */
+  int status;       /* TMBIR_OK, TMBIR_ERR_NONFINITE */
+  double objective; /* F(y_k) of the last iteration (Eq. 10 + lambda Phi) */
+  double gap;       /* relative gap of that value when F_ref was given, else 0 */
+  double L;         /* step constant used */
+  double grad_norm; /* ||grad F(y_k)||_2 of the last iteration */
+} tmbir_stats;
+
+/* Create a context bound to a CUDA stream (cudaStream_t passed as void*; NULL = legacy default stream). */
+int tmbir_create(tmbir_ctx** out, void* stream);
+int tmbir_destroy(tmbir_ctx* ctx);
+/* Message of the last failing call on this thread ("" if none).  Owned by the library. */
+const char* tmbir_last_error(void);
+
+/*
+ * Define the slices to reconstruct (Sec. 2: slices are independent in the data term and
+ * coupled by the prior).  Copies the groups and angles; invalidates the workspace binding.
+ */
+int tmbir_set_geometry(tmbir_ctx* ctx, int n_groups, const tmbir_group* groups);
+
+/* Bytes of device workspace the current geometry needs. */
+int tmbir_workspace_size(const tmbir_ctx* ctx, size_t* bytes);
+
+/*
+ * Bind caller-owned device workspace (16-byte aligned, >= tmbir_workspace_size bytes).  The
+ * library keeps the kernel spectrum, twiddle tables, iterate buffers and scratch in it; it
+ * must stay valid until the next set_geometry / set_workspace / destroy.  Enqueues the
+ * upload of the twiddle tables on the context stream.
+ */
+int tmbir_set_workspace(tmbir_ctx* ctx, void* d_workspace, size_t bytes);
+
+/*
+ * Setup of Sec. 2.1 ("computed once prior to the iterative reconstruction"): per group the
+ * point-spread kernel K = NUFFT1(ones) on [-(N-1), N-1]^2 and the real spectrum of its 2N x 2N
+ * circulant embedding (kept in the workspace); R*g for every slice into d_atg
+ * [slice][row][col]; 1/2 g.g per group; lambda_max(R*R) by 100 power steps (kept in the
+ * workspace).  d_sino is [slice][angle][bin] for all groups back to back.  FP64 arithmetic.
+ */
+int tmbir_build_operator(tmbir_ctx* ctx, const float* d_sino, float* d_atg);
+
+/*
+ * Filtered back-projection start of Sec. 2.2 (Eqs. 12-14): every projection row is
+ * convolved with the unit-pitch Ram-Lak kernel (zero padded, no wrap-around), back-projected
+ * with R* and weighted by span / n_angles.  d_x0 receives [slice][row][col].
+ */
+int tmbir_fbp(tmbir_ctx* ctx, const float* d_sino, float* d_x0);
+
+/*
+ * Fast gradient method with restart (Sec. 2, Eq. 6 with the '+' sign on the prior term)
+ * from the image in d_x, which receives the last iterate.  Each iteration:
+ *   y = x_k + beta_k (x_k - x_{k-1});  G = K (*) y - R*g + lambda grad Phi(y)   (Eqs. 9, 11)
+ *   x_{k+1} = y - G / L;  restart test; t_{k+1}, beta_{k+1}.
+ * d_atg is the R*g from tmbir_build_operator.  h_stats (may be NULL) receives the summary.
+ */
+int tmbir_reconstruct(tmbir_ctx* ctx, float* d_x, const float* d_atg, const tmbir_params* prm, tmbir_stats* h_stats);
+
+/* Per-iteration log of the last tmbir_reconstruct: h_log[4*k + {0,1,2,3}] = F(y_k),
+ * <G, x_{k+1} - x_k>, restarted (0/1), ||G||^2.  Copies min(max_entries, iterations) rows;
+ * *n_out receives that count. */
+int tmbir_get_log(tmbir_ctx* ctx, double* h_log, int max_entries, int* n_out);
+
+/* d_z = R*R d_x = Res(F^-1(F K . F Pad x)) for every slice (Eq. 9), FP32. */
+int tmbir_normal_apply(tmbir_ctx* ctx, const float* d_x, float* d_z);
+
+/* d_grad = K (*) d_x - d_atg + lambda grad Phi(d_x) (Eq. 11 plus the prior), FP32. */
+int tmbir_gradient(tmbir_ctx* ctx, const float* d_x, const float* d_atg, const tmbir_params* prm, float* d_grad);
+
+/*
+ * One fused iteration at a given momentum: y = x + beta (x - x_prev), G as in
+ * tmbir_gradient at y, x_next = y - G / L.  h_partials (may be NULL) receives, in FP64,
+ * { y.(K*y), y.R*g, Phi(y) (without lambda), <G, x_next - x>, ||G||^2 }.
+ */
+int tmbir_step(tmbir_ctx* ctx, const float* d_x, const float* d_x_prev, double beta, const float* d_atg,
+               const tmbir_params* prm, double L, float* d_x_next, double* h_partials);
+
+/* F(x) = 1/2 x.(K*x) - x.R*g + 1/2 g.g + lambda Phi(x) (Eq. 10 plus the prior), FP64 reduction. */
+int tmbir_objective(tmbir_ctx* ctx, const float* d_x, const float* d_atg, const tmbir_params* prm, double* h_F);
+
+/* Largest eigenvalue of R*R per group (power iteration of tmbir_build_operator); h_out[n_groups]. */
+int tmbir_lambda_max(tmbir_ctx* ctx, double* h_out);
+
+/* FP64 point-spread kernel of one group, K[(dy + N-1) * (2N-1) + (dx + N-1)], into d_K (device). */
+int tmbir_kernel(tmbir_ctx* ctx, int group, double* d_K);
+
+/*
+ * x2 Lanczos-3 level transfer of Sec. 2.3 (Eqs. 16-17, with the standard windowed sinc
+ * L(x) = sinc(x) sinc(x/3)): coarse sample i lands on fine sample 2i; odd fine samples take
+ * the six normalised taps at offsets +-0.5, +-1.5, +-2.5; zero outside the grid; separable.
+ * d_coarse [n_slices][Nc][Nc] -> d_fine [n_slices][2Nc][2Nc].  No context geometry needed.
+ */
+int tmbir_upsample_lanczos3(tmbir_ctx* ctx, const float* d_coarse, int n_slices, int Nc, float* d_fine);
+
+/*
+ * Coarse projections of Sec. 2.3 ("subsampling the full-resolution projection data"): every
+ * factor-th bin aligned on the centre bin, divided by factor (line integrals in coarse-pixel
+ * units).  d_sino [n_slices][n_angles][n_det] -> d_out [n_slices][n_angles][n_det/factor].
+ */
+int tmbir_downsample_sino(tmbir_ctx* ctx, const float* d_sino, int n_slices, int n_angles, int n_det, int factor,
+                          float* d_out);
+
+/*
+ * Measurement: run `iters` iterations of tmbir_reconstruct's loop eagerly (no graph) from d_x
+ * with CUDA events recorded on the context stream around every launch, and return the summed
+ * device time per kernel kind in h_ms[4] = { pass 1 (rows), pass 2 (columns), pass 3 (rows +
+ * gradient + update), finalize }.  d_x receives the iterate like tmbir_reconstruct.
+ */
+int tmbir_pass_times(tmbir_ctx* ctx, float* d_x, const float* d_atg, const tmbir_params* prm, int iters, double* h_ms);
+
+/* Number of kernels this context has launched so far (graph replays count their kernel nodes). */
+int tmbir_launch_count(const tmbir_ctx* ctx, long long* h_count);
+
+/* Wait for the context stream; reports a pending CUDA error. */
+int tmbir_sync(tmbir_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TMBIR_H */

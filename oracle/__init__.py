@@ -76,6 +76,10 @@ def lib():
         L.orc_adjoint.argtypes = [dp, i, dp, i, i, dp]
         L.orc_kernel.argtypes = [i, dp, i, i, dp]
         L.orc_normal_direct.argtypes = [dp, i, dp, dp]
+        L.orc_normal_point.restype = d
+        L.orc_normal_point.argtypes = [dp, i, dp, i, i]
+        L.orc_adjoint_point.restype = d
+        L.orc_adjoint_point.argtypes = [dp, i, dp, i, i, i, i]
         L.orc_rho.restype = d
         L.orc_rho.argtypes = [d, d, d, d, d]
         L.orc_drho.restype = d
@@ -167,6 +171,37 @@ def normal_direct(x, K) -> np.ndarray:
     z = np.zeros_like(x)
     lib().orc_normal_direct(_p(x), N, _p(K), _p(z))
     return z
+
+
+def normal_point(x, K, r: int, c: int) -> float:
+    """(K (*) x)[r, c] of one slice by the direct sum."""
+    x = _f64(x)
+    K = _f64(K)
+    return lib().orc_normal_point(_p(x), x.shape[0], _p(K), r, c)
+
+
+def adjoint_point(g, N: int, theta, r: int, c: int) -> float:
+    """(A^T g)[r, c] of one sinogram by the direct sum."""
+    g = _f64(g)
+    th = _f64(theta)
+    return lib().orc_adjoint_point(_p(g), N, _p(th), th.size, g.shape[1], r, c)
+
+
+def prior_point(x, pr: Prior, z: int, r: int, c: int) -> float:
+    """lambda * dPhi/dx at voxel (z, r, c) of a volume, from its 3x3x3 neighbourhood only."""
+    x = _f64(x)
+    v = x.reshape((1,) + x.shape) if x.ndim == 2 else x
+    S, N = v.shape[0], v.shape[1]
+    g = 0.0
+    for dz in (-1, 0, 1):
+        for dy in (-1, 0, 1):
+            for dx in (-1, 0, 1):
+                if (dz, dy, dx) == (0, 0, 0):
+                    continue
+                z2, r2, c2 = z + dz, r + dy, c + dx
+                if 0 <= z2 < S and 0 <= r2 < N and 0 <= c2 < N:
+                    g += neighbour_weight(dz, dy, dx) * drho(v[z, r, c] - v[z2, r2, c2], pr)
+    return pr.lam * g
 
 
 def circulant_spectrum(K, M: int | None = None) -> np.ndarray:

@@ -117,3 +117,28 @@ void orc_normal_direct(const double *x, int N, const double *K, double *z)
         }
     }
 }
+
+/* Single outputs of the same definitions, for sampled checks on large grids. */
+double orc_normal_point(const double *x, int N, const double *K, int r, int c)
+{
+    int W = 2 * N - 1;
+    double acc = 0.0;
+    for (int r2 = 0; r2 < N; ++r2) {
+        const double *Krow = K + (size_t)(r - r2 + N - 1) * W + (N - 1) + c;
+        const double *xrow = x + (size_t)r2 * N;
+        for (int c2 = 0; c2 < N; ++c2) acc += Krow[-c2] * xrow[c2];
+    }
+    return acc;
+}
+
+double orc_adjoint_point(const double *g, int N, const double *theta, int na, int nd, int r, int c)
+{
+    int h = N / 2;
+    double acc = 0.0;
+    for (int a = 0; a < na; ++a) {
+        double u = (double)(c - h) * cos(theta[a]) + (double)(r - h) * sin(theta[a]);
+        const double *ga = g + (size_t)a * nd;
+        for (int m = 0; m < nd; ++m) acc += ga[m] * orc_dirichlet((double)m - 0.5 * nd - u, nd);
+    }
+    return acc / (double)nd;
+}

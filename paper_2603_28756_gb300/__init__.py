@@ -1,0 +1,338 @@
+"""Toeplitz-accelerated MBIR on one GB300: thin Python binding over the libtmbir C ABI.
+
+Every computation runs in the CUDA library (``include/tmbir.h``); this module only
+marshals arguments.  PyTorch provides device memory and the stream.  There is no CPU
+fallback: if the library is missing or no GPU is present the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+from dataclasses import dataclass, field
+
+from .build import LIB, build  # noqa: F401
+
+__all__ = ["Context", "Group", "Params", "Stats", "TmbirError", "load", "SYMBOLS", "build"]
+
+TMBIR_OK = 0
+ERRORS = {
+    -1: "TMBIR_ERR_ARG",
+    -2: "TMBIR_ERR_SHAPE",
+    -3: "TMBIR_ERR_WORKSPACE",
+    -4: "TMBIR_ERR_CUDA",
+    -5: "TMBIR_ERR_TIMEOUT",
+    -6: "TMBIR_ERR_NONFINITE",
+    -7: "TMBIR_ERR_STATE",
+}
+
+
+class TmbirError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class _Group(ctypes.Structure):
+    _fields_ = [
+        ("N", ctypes.c_int),
+        ("n_det", ctypes.c_int),
+        ("n_angles", ctypes.c_int),
+        ("angles", ctypes.POINTER(ctypes.c_double)),
+        ("span", ctypes.c_double),
+        ("n_slices", ctypes.c_int),
+    ]
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [
+        ("p", ctypes.c_double),
+        ("q", ctypes.c_double),
+        ("c", ctypes.c_double),
+        ("sigma", ctypes.c_double),
+        ("lambda_", ctypes.c_double),
+        ("L", ctypes.c_double),
+        ("max_iter", ctypes.c_int),
+        ("gap_tol", ctypes.c_double),
+        ("F_ref", ctypes.c_double),
+        ("restart", ctypes.c_int),
+        ("use_graph", ctypes.c_int),
+    ]
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [
+        ("iterations", ctypes.c_int),
+        ("restarts", ctypes.c_int),
+        ("status", ctypes.c_int),
+        ("objective", ctypes.c_double),
+        ("gap", ctypes.c_double),
+        ("L", ctypes.c_double),
+        ("grad_norm", ctypes.c_double),
+    ]
+
+
+SYMBOLS = [
+    "tmbir_create", "tmbir_destroy", "tmbir_last_error", "tmbir_set_geometry", "tmbir_workspace_size",
+    "tmbir_set_workspace", "tmbir_build_operator", "tmbir_fbp", "tmbir_reconstruct", "tmbir_get_log",
+    "tmbir_normal_apply", "tmbir_gradient", "tmbir_step", "tmbir_objective", "tmbir_lambda_max", "tmbir_kernel",
+    "tmbir_upsample_lanczos3", "tmbir_downsample_sino", "tmbir_sync", "tmbir_pass_times", "tmbir_launch_count",
+]
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load libtmbir.so (building it first if the sources are newer).  Raises if it cannot."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    so = path or build()
+    if not os.path.exists(so):
+        raise RuntimeError(f"libtmbir.so not found at {so}; run paper_2603_28756_gb300.build.build()")
+    L = ctypes.CDLL(so)
+    vp, i, d, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+    dp = ctypes.POINTER(ctypes.c_double)
+    sig = {
+        "tmbir_create": [ctypes.POINTER(vp), vp],
+        "tmbir_destroy": [vp],
+        "tmbir_set_geometry": [vp, i, ctypes.POINTER(_Group)],
+        "tmbir_workspace_size": [vp, ctypes.POINTER(sz)],
+        "tmbir_set_workspace": [vp, vp, sz],
+        "tmbir_build_operator": [vp, vp, vp],
+        "tmbir_fbp": [vp, vp, vp],
+        "tmbir_reconstruct": [vp, vp, vp, ctypes.POINTER(_Params), ctypes.POINTER(_Stats)],
+        "tmbir_get_log": [vp, dp, i, ctypes.POINTER(i)],
+        "tmbir_normal_apply": [vp, vp, vp],
+        "tmbir_gradient": [vp, vp, vp, ctypes.POINTER(_Params), vp],
+        "tmbir_step": [vp, vp, vp, d, vp, ctypes.POINTER(_Params), d, vp, dp],
+        "tmbir_objective": [vp, vp, vp, ctypes.POINTER(_Params), dp],
+        "tmbir_lambda_max": [vp, dp],
+        "tmbir_kernel": [vp, i, vp],
+        "tmbir_upsample_lanczos3": [vp, vp, i, i, vp],
+        "tmbir_downsample_sino": [vp, vp, i, i, i, i, vp],
+        "tmbir_sync": [vp],
+        "tmbir_pass_times": [vp, vp, vp, ctypes.POINTER(_Params), i, dp],
+        "tmbir_launch_count": [vp, ctypes.POINTER(ctypes.c_longlong)],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    L.tmbir_last_error.restype = ctypes.c_char_p
+    L.tmbir_last_error.argtypes = []
+    _lib = L
+    return L
+
+
+def _check(code: int):
+    if code != TMBIR_OK:
+        raise TmbirError(code, _lib.tmbir_last_error().decode(errors="replace"))
+
+
+@dataclass
+class Group:
+    """n_slices slices of N x N seen under `angles` (radians) covering `span` radians."""
+
+    N: int
+    angles: list
+    n_slices: int = 1
+    span: float = math.pi
+    n_det: int | None = None
+
+
+@dataclass
+class Params:
+    """qGGMRF prior and optimiser settings (see tmbir_params in include/tmbir.h)."""
+
+    p: float = 1.2
+    q: float = 2.0
+    c: float = 0.01
+    sigma: float = 0.1
+    lam: float = 1.0
+    L: float = 0.0
+    max_iter: int = 50
+    gap_tol: float = 0.0
+    F_ref: float = 0.0
+    restart: int = 0
+    use_graph: bool = True
+
+    def c_struct(self) -> _Params:
+        return _Params(self.p, self.q, self.c, self.sigma, self.lam, self.L, self.max_iter, self.gap_tol, self.F_ref,
+                       self.restart, 1 if self.use_graph else 0)
+
+
+@dataclass
+class Stats:
+    iterations: int
+    restarts: int
+    status: int
+    objective: float
+    gap: float
+    L: float
+    grad_norm: float
+
+
+def _ptr(t) -> int:
+    import torch
+
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return t.data_ptr()
+
+
+class Context:
+    """One libtmbir context bound to a CUDA stream, with a torch-allocated workspace."""
+
+    def __init__(self, groups, stream=None, device="cuda"):
+        import torch
+
+        load()
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=self.device)
+        h = ctypes.c_void_p()
+        _check(_lib.tmbir_create(ctypes.byref(h), ctypes.c_void_p(self.stream.cuda_stream)))
+        self._h = h
+        self.groups = [g if isinstance(g, Group) else Group(**g) for g in groups]
+        self._angle_bufs = []
+        arr = (_Group * len(self.groups))()
+        for k, g in enumerate(self.groups):
+            a = (ctypes.c_double * len(g.angles))(*[float(v) for v in g.angles])
+            self._angle_bufs.append(a)
+            arr[k] = _Group(g.N, g.n_det or g.N, len(g.angles), ctypes.cast(a, ctypes.POINTER(ctypes.c_double)),
+                            float(g.span), g.n_slices)
+        _check(_lib.tmbir_set_geometry(self._h, len(self.groups), arr))
+        nbytes = ctypes.c_size_t()
+        _check(_lib.tmbir_workspace_size(self._h, ctypes.byref(nbytes)))
+        self.workspace_bytes = nbytes.value
+        with torch.cuda.stream(self.stream):
+            self.workspace = torch.empty(nbytes.value + 256, dtype=torch.uint8, device=self.device)
+        base = self.workspace.data_ptr()
+        aligned = (base + 255) // 256 * 256
+        _check(_lib.tmbir_set_workspace(self._h, ctypes.c_void_p(aligned), nbytes.value))
+
+    # shapes -----------------------------------------------------------------
+    @property
+    def n_slices(self) -> int:
+        return sum(g.n_slices for g in self.groups)
+
+    def image_numel(self) -> int:
+        return sum(g.n_slices * g.N * g.N for g in self.groups)
+
+    def sino_numel(self) -> int:
+        return sum(g.n_slices * len(g.angles) * (g.n_det or g.N) for g in self.groups)
+
+    def _empty(self, n):
+        import torch
+
+        with torch.cuda.stream(self.stream):
+            return torch.empty(n, dtype=torch.float32, device=self.device)
+
+    # calls --------------------------------------------------------------------
+    def build_operator(self, sino, atg=None):
+        atg = self._empty(self.image_numel()) if atg is None else atg
+        _check(_lib.tmbir_build_operator(self._h, ctypes.c_void_p(_ptr(sino)), ctypes.c_void_p(_ptr(atg))))
+        return atg
+
+    def fbp(self, sino, out=None):
+        out = self._empty(self.image_numel()) if out is None else out
+        _check(_lib.tmbir_fbp(self._h, ctypes.c_void_p(_ptr(sino)), ctypes.c_void_p(_ptr(out))))
+        return out
+
+    def reconstruct(self, x, atg, params: Params, want_stats: bool = True):
+        st = _Stats()
+        pr = params.c_struct()
+        _check(_lib.tmbir_reconstruct(self._h, ctypes.c_void_p(_ptr(x)), ctypes.c_void_p(_ptr(atg)), ctypes.byref(pr),
+                                      ctypes.byref(st) if want_stats else None))
+        if not want_stats:
+            return None
+        return Stats(st.iterations, st.restarts, st.status, st.objective, st.gap, st.L, st.grad_norm)
+
+    def get_log(self, max_entries: int = 1 << 16):
+        buf = (ctypes.c_double * (4 * max_entries))()
+        n = ctypes.c_int()
+        _check(_lib.tmbir_get_log(self._h, buf, max_entries, ctypes.byref(n)))
+        return [tuple(buf[4 * k: 4 * k + 4]) for k in range(n.value)]
+
+    def normal_apply(self, x, out=None):
+        out = self._empty(x.numel()) if out is None else out
+        _check(_lib.tmbir_normal_apply(self._h, ctypes.c_void_p(_ptr(x)), ctypes.c_void_p(_ptr(out))))
+        return out
+
+    def gradient(self, x, atg, params: Params, out=None):
+        out = self._empty(x.numel()) if out is None else out
+        pr = params.c_struct()
+        _check(_lib.tmbir_gradient(self._h, ctypes.c_void_p(_ptr(x)), ctypes.c_void_p(_ptr(atg)), ctypes.byref(pr),
+                                   ctypes.c_void_p(_ptr(out))))
+        return out
+
+    def step(self, x, x_prev, beta, atg, params: Params, L, out=None):
+        out = self._empty(x.numel()) if out is None else out
+        pr = params.c_struct()
+        parts = (ctypes.c_double * 5)()
+        _check(_lib.tmbir_step(self._h, ctypes.c_void_p(_ptr(x)), ctypes.c_void_p(_ptr(x_prev)), float(beta),
+                               ctypes.c_void_p(_ptr(atg)), ctypes.byref(pr), float(L), ctypes.c_void_p(_ptr(out)),
+                               parts))
+        return out, list(parts)
+
+    def objective(self, x, atg, params: Params) -> float:
+        pr = params.c_struct()
+        F = ctypes.c_double()
+        _check(_lib.tmbir_objective(self._h, ctypes.c_void_p(_ptr(x)), ctypes.c_void_p(_ptr(atg)), ctypes.byref(pr),
+                                    ctypes.byref(F)))
+        return F.value
+
+    def lambda_max(self):
+        out = (ctypes.c_double * len(self.groups))()
+        _check(_lib.tmbir_lambda_max(self._h, out))
+        return list(out)
+
+    def kernel(self, group: int = 0):
+        import torch
+
+        N = self.groups[group].N
+        with torch.cuda.stream(self.stream):
+            K = torch.empty((2 * N - 1) * (2 * N - 1), dtype=torch.float64, device=self.device)
+        _check(_lib.tmbir_kernel(self._h, group, ctypes.c_void_p(_ptr(K))))
+        return K
+
+    def upsample_lanczos3(self, coarse, n_slices: int, Nc: int, out=None):
+        out = self._empty(n_slices * 4 * Nc * Nc) if out is None else out
+        _check(_lib.tmbir_upsample_lanczos3(self._h, ctypes.c_void_p(_ptr(coarse)), n_slices, Nc,
+                                            ctypes.c_void_p(_ptr(out))))
+        return out
+
+    def downsample_sino(self, sino, n_slices: int, n_angles: int, n_det: int, factor: int, out=None):
+        out = self._empty(n_slices * n_angles * (n_det // factor)) if out is None else out
+        _check(_lib.tmbir_downsample_sino(self._h, ctypes.c_void_p(_ptr(sino)), n_slices, n_angles, n_det, factor,
+                                          ctypes.c_void_p(_ptr(out))))
+        return out
+
+    def pass_times(self, x, atg, params: Params, iters: int):
+        """Summed device ms of (pass 1, pass 2, pass 3, finalize) over `iters` eager iterations."""
+        pr = params.c_struct()
+        out = (ctypes.c_double * 4)()
+        _check(_lib.tmbir_pass_times(self._h, ctypes.c_void_p(_ptr(x)), ctypes.c_void_p(_ptr(atg)), ctypes.byref(pr),
+                                     iters, out))
+        return list(out)
+
+    def launch_count(self) -> int:
+        n = ctypes.c_longlong()
+        _check(_lib.tmbir_launch_count(self._h, ctypes.byref(n)))
+        return n.value
+
+    def sync(self):
+        _check(_lib.tmbir_sync(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.tmbir_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

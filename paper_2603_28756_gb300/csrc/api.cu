@@ -1,0 +1,661 @@
+// C ABI entry points: context, geometry, workspace layout, and the call sequences of the
+// setup, warm-start and iteration phases.  All device work is enqueued on the context stream.
+#include <cmath>
+#include <cstring>
+#include <limits>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace tmbir {
+
+static thread_local std::string g_last_error;
+long long g_launches = 0;
+
+int set_error(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+PriorC make_prior(const tmbir_params& p) {
+  PriorC c{};
+  c.p = (float)p.p;
+  c.q = (float)p.q;
+  c.qp = (float)(p.q - p.p);
+  c.inv_csig = (float)(1.0 / (p.c * p.sigma));
+  c.inv_sig = (float)(1.0 / p.sigma);
+  c.inv_sig2 = (float)(1.0 / (p.sigma * p.sigma));
+  c.lam = (float)p.lambda;
+  const double total = 6.0 + 12.0 / std::sqrt(2.0) + 8.0 / std::sqrt(3.0);
+  c.wf = (float)(1.0 / total);
+  c.we = (float)(1.0 / std::sqrt(2.0) / total);
+  c.wc = (float)(1.0 / std::sqrt(3.0) / total);
+  c.q_is_2 = p.q == 2.0 ? 1 : 0;
+  return c;
+}
+
+static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// ---------------------------------------------------------------- small device kernels
+// lam_max[i], gtg[i]: per-group lambda_max(R*R) and 1/2 g.g gathered into consecutive doubles
+__global__ void k_init_state(IterState* st, const double* lam_max, const double* gtg, int n_groups, double L_given,
+                             double lambda, double sigma, double Fref, double gap_tol, int max_iter, int restart_mode) {
+  double lm = 0.0, gh = 0.0;
+  for (int i = 0; i < n_groups; ++i) {
+    lm = fmax(lm, lam_max[i]);
+    gh += gtg[i];
+  }
+  double L = L_given > 0.0 ? L_given : 1.01 * lm + lambda * 2.0 * (2.0 / (sigma * sigma));
+  st->t = 1.0;
+  st->beta = 0.0;
+  st->L = L;
+  st->invL = 1.0 / L;
+  st->lambda = lambda;
+  st->gtg_half = gh;
+  st->F0 = gh;
+  st->Fref = Fref;
+  st->gap_tol = gap_tol;
+  st->last_F = st->last_gap = st->last_gg = st->last_dot = 0.0;
+  st->k = 0;
+  st->max_iter = max_iter;
+  st->restarts = 0;
+  st->cur = 0;
+  st->done = max_iter <= 0 ? 1 : 0;
+  st->status = 0;
+  st->restart_mode = restart_mode;
+  st->log_cap = kLogCap;
+}
+
+// copy the current iterate back into slot 0 (the caller's buffer) when the rotation ended elsewhere
+__global__ void k_gather_final(const IterState* st, float* x0, const float* x1, const float* x2, size_t n) {
+  const int cur = st->cur;
+  if (cur == 0) return;
+  const float* src = cur == 1 ? x1 : x2;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n / 4; i += (size_t)gridDim.x * blockDim.x)
+    reinterpret_cast<float4*>(x0)[i] = reinterpret_cast<const float4*>(src)[i];
+}
+
+__global__ void k_scale_copy(const float* __restrict__ in, float* __restrict__ out, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) out[i] = in[i];
+}
+
+}  // namespace tmbir
+
+using namespace tmbir;
+
+struct tmbir_ctx {
+  Ctx c;
+};
+
+static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+#define REQUIRE(cond, code, msg) \
+  do {                           \
+    if (!(cond)) return set_error(code, msg); \
+  } while (0)
+
+extern "C" {
+
+const char* tmbir_last_error(void) { return g_last_error.c_str(); }
+
+int tmbir_create(tmbir_ctx** out, void* stream) {
+  REQUIRE(out != nullptr, TMBIR_ERR_ARG, "tmbir_create: out is NULL");
+  int dev_count = 0;
+  cudaError_t e = cudaGetDeviceCount(&dev_count);
+  if (e != cudaSuccess || dev_count == 0) return set_error(TMBIR_ERR_CUDA, "tmbir_create: no CUDA device");
+  tmbir_ctx* ctx = new tmbir_ctx();
+  ctx->c.stream = (cudaStream_t)stream;
+  *out = ctx;
+  g_last_error.clear();
+  return TMBIR_OK;
+}
+
+int tmbir_destroy(tmbir_ctx* ctx) {
+  if (!ctx) return TMBIR_OK;
+  if (ctx->c.graph_exec) cudaGraphExecDestroy(ctx->c.graph_exec);
+  delete ctx;
+  return TMBIR_OK;
+}
+
+int tmbir_set_geometry(tmbir_ctx* ctx, int n_groups, const tmbir_group* groups) {
+  REQUIRE(ctx != nullptr, TMBIR_ERR_ARG, "set_geometry: ctx is NULL");
+  REQUIRE(n_groups >= 1 && groups != nullptr, TMBIR_ERR_ARG, "set_geometry: need at least one group");
+  Ctx& c = ctx->c;
+  std::vector<tmbir_group> gs(groups, groups + n_groups);
+  std::vector<std::vector<double>> angs(n_groups);
+  for (int i = 0; i < n_groups; ++i) {
+    const tmbir_group& g = gs[i];
+    REQUIRE(supported_N(g.N), TMBIR_ERR_SHAPE, "set_geometry: N must be a power of two in [64, 1024]");
+    REQUIRE(g.n_det == g.N, TMBIR_ERR_SHAPE, "set_geometry: n_det must equal N");
+    REQUIRE(g.n_angles >= 1 && g.n_angles <= 1 << 16, TMBIR_ERR_ARG, "set_geometry: n_angles out of range");
+    REQUIRE(g.angles != nullptr, TMBIR_ERR_ARG, "set_geometry: angles is NULL");
+    REQUIRE(g.n_slices >= 1, TMBIR_ERR_ARG, "set_geometry: n_slices must be >= 1");
+    REQUIRE(g.span > 0.0 && std::isfinite(g.span), TMBIR_ERR_ARG, "set_geometry: span must be positive");
+    angs[i].assign(g.angles, g.angles + g.n_angles);
+    for (double a : angs[i]) REQUIRE(std::isfinite(a), TMBIR_ERR_ARG, "set_geometry: non-finite angle");
+    gs[i].angles = nullptr;
+  }
+  if (c.graph_exec) {
+    cudaGraphExecDestroy(c.graph_exec);
+    c.graph_exec = nullptr;
+  }
+  c.groups = gs;
+  c.angles = angs;
+  c.gdev.assign(n_groups, GroupDev{});
+  c.ws = nullptr;
+  c.ws_bytes = 0;
+  c.operator_built = false;
+  c.nufft_beta64 = 2.30 * 12;
+  c.nufft_beta32 = 2.30 * 7;
+  c.psiK_h.assign(n_groups, {});
+  c.psiA_h.assign(n_groups, {});
+  c.psiA32_h.assign(n_groups, {});
+
+  // workspace layout
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    off = align_up(off, 256);
+    size_t o = off;
+    off += bytes;
+    return o;
+  };
+  c.off_state = take(sizeof(IterState));
+  c.off_dscal = take((16 + 2 * (size_t)n_groups) * sizeof(double));
+  int max_blocks = 0, slices = 0;
+  size_t voxels = 0, sino = 0, scratch = 0;
+  for (int i = 0; i < n_groups; ++i) {
+    GroupDev tmp{};
+    tmp.N = gs[i].N;
+    tmp.S = gs[i].n_slices;
+    max_blocks += blocks_pass3(tmp);
+    voxels += (size_t)gs[i].n_slices * gs[i].N * gs[i].N;
+    sino += (size_t)gs[i].n_slices * gs[i].n_angles * gs[i].n_det;
+    scratch = std::max(scratch, setup_scratch_bytes(gs[i]));
+  }
+  c.max_blocks = std::max(max_blocks, 1);
+  c.off_partials = take((size_t)c.max_blocks * kParts * sizeof(double));
+  c.off_log = take((size_t)kLogCap * 4 * sizeof(double));
+  c.off_chat.resize(n_groups);
+  c.off_twN.resize(n_groups);
+  c.off_twM.resize(n_groups);
+  c.off_spec.resize(n_groups);
+  c.off_ang.resize(n_groups);
+  c.off_K.resize(n_groups);
+  c.off_psiK.resize(n_groups);
+  c.off_psiA.resize(n_groups);
+  c.off_psiA32.resize(n_groups);
+  c.off_lam.resize(n_groups);
+  c.off_gtg.resize(n_groups);
+  for (int i = 0; i < n_groups; ++i) {
+    const size_t N = gs[i].N;
+    c.off_chat[i] = take((N + 1) * 2 * N * sizeof(float));
+    c.off_twN[i] = take(N * sizeof(float2));
+    c.off_twM[i] = take(N * sizeof(float2));
+    c.off_spec[i] = take((size_t)gs[i].n_slices * (N + 1) * N * sizeof(float2));
+    c.off_ang[i] = take(gs[i].n_angles * sizeof(double));
+    c.off_K[i] = take((2 * N - 1) * (2 * N - 1) * sizeof(double));
+    c.off_psiK[i] = take((2 * N - 1) * sizeof(double));
+    c.off_psiA[i] = take(N * sizeof(double));
+    c.off_psiA32[i] = take(N * sizeof(double));
+    c.off_lam[i] = take(sizeof(double));
+    c.off_gtg[i] = take(sizeof(double));
+    nufft_psi_table(2 * N - 1, 4 * N, 12, c.nufft_beta64, c.psiK_h[i]);
+    nufft_psi_table(N, 2 * N, 12, c.nufft_beta64, c.psiA_h[i]);
+    nufft_psi_table(N, 2 * N, 7, c.nufft_beta32, c.psiA32_h[i]);
+  }
+  c.off_xbuf0 = take(voxels * sizeof(float));
+  c.off_xbuf1 = take(voxels * sizeof(float));
+  c.off_scratch = take(scratch);
+  c.scratch_bytes = scratch;
+  c.ws_need = align_up(off, 256);
+  c.total_voxels = voxels;
+  c.total_sino = sino;
+  c.total_slices = slices;
+  int s0 = 0;
+  for (int i = 0; i < n_groups; ++i) {
+    c.gdev[i].slice0 = s0;
+    s0 += gs[i].n_slices;
+  }
+  c.total_slices = s0;
+  g_last_error.clear();
+  return TMBIR_OK;
+}
+
+int tmbir_workspace_size(const tmbir_ctx* ctx, size_t* bytes) {
+  REQUIRE(ctx != nullptr && bytes != nullptr, TMBIR_ERR_ARG, "workspace_size: NULL argument");
+  REQUIRE(!ctx->c.groups.empty(), TMBIR_ERR_STATE, "workspace_size: no geometry");
+  *bytes = ctx->c.ws_need;
+  return TMBIR_OK;
+}
+
+int tmbir_set_workspace(tmbir_ctx* ctx, void* d_ws, size_t bytes) {
+  REQUIRE(ctx != nullptr, TMBIR_ERR_ARG, "set_workspace: ctx is NULL");
+  Ctx& c = ctx->c;
+  REQUIRE(!c.groups.empty(), TMBIR_ERR_STATE, "set_workspace: no geometry");
+  REQUIRE(d_ws != nullptr, TMBIR_ERR_ARG, "set_workspace: workspace is NULL");
+  REQUIRE(((uintptr_t)d_ws & 255u) == 0, TMBIR_ERR_ARG, "set_workspace: workspace must be 256-byte aligned");
+  REQUIRE(bytes >= c.ws_need, TMBIR_ERR_WORKSPACE, "set_workspace: workspace too small");
+  if (c.graph_exec) {
+    cudaGraphExecDestroy(c.graph_exec);
+    c.graph_exec = nullptr;
+  }
+  char* ws = static_cast<char*>(d_ws);
+  c.ws = ws;
+  c.ws_bytes = bytes;
+  c.state = reinterpret_cast<IterState*>(ws + c.off_state);
+  c.dscal = reinterpret_cast<double*>(ws + c.off_dscal);
+  c.partials = reinterpret_cast<double*>(ws + c.off_partials);
+  c.log = reinterpret_cast<double*>(ws + c.off_log);
+  c.xbuf[0] = reinterpret_cast<float*>(ws + c.off_xbuf0);
+  c.xbuf[1] = reinterpret_cast<float*>(ws + c.off_xbuf1);
+  c.scratch = ws + c.off_scratch;
+  for (size_t i = 0; i < c.groups.size(); ++i) {
+    const tmbir_group& g = c.groups[i];
+    GroupDev& d = c.gdev[i];
+    d.N = g.N;
+    d.nd = g.n_det;
+    d.na = g.n_angles;
+    d.S = g.n_slices;
+    d.span = (float)g.span;
+    d.chat = reinterpret_cast<float*>(ws + c.off_chat[i]);
+    d.twN = reinterpret_cast<float2*>(ws + c.off_twN[i]);
+    d.twM = reinterpret_cast<float2*>(ws + c.off_twM[i]);
+    d.spec = reinterpret_cast<float2*>(ws + c.off_spec[i]);
+    d.angles = reinterpret_cast<double*>(ws + c.off_ang[i]);
+    d.K = reinterpret_cast<double*>(ws + c.off_K[i]);
+    d.psiK = reinterpret_cast<double*>(ws + c.off_psiK[i]);
+    d.psiA = reinterpret_cast<double*>(ws + c.off_psiA[i]);
+    d.psiA32 = reinterpret_cast<double*>(ws + c.off_psiA32[i]);
+    d.lam_max = reinterpret_cast<double*>(ws + c.off_lam[i]);
+    d.gtg = reinterpret_cast<double*>(ws + c.off_gtg[i]);
+    // twiddle tables: twN[k][t] = exp(-2 pi i t k / N) in the group-FFT layout, twM[n] = exp(-2 pi i n / 2N)
+    int T, P;
+    fft_shape(g.N, &T, &P);
+    std::vector<float2> twN((size_t)T * P), twM(g.N);
+    for (int k = 0; k < P; ++k)
+      for (int t = 0; t < T; ++t) {
+        const long long q = (long long)t * k % g.N;
+        const double a = -2.0 * M_PI * (double)q / g.N;
+        twN[(size_t)k * T + t] = make_float2((float)std::cos(a), (float)std::sin(a));
+      }
+    for (int n = 0; n < g.N; ++n) {
+      const double a = -M_PI * (double)n / g.N;
+      twM[n] = make_float2((float)std::cos(a), (float)std::sin(a));
+    }
+    TMBIR_CUDA(cudaMemcpyAsync(d.twN, twN.data(), twN.size() * sizeof(float2), cudaMemcpyHostToDevice, c.stream));
+    TMBIR_CUDA(cudaMemcpyAsync(d.twM, twM.data(), twM.size() * sizeof(float2), cudaMemcpyHostToDevice, c.stream));
+    TMBIR_CUDA(cudaMemcpyAsync(d.angles, c.angles[i].data(), c.angles[i].size() * sizeof(double), cudaMemcpyHostToDevice,
+                               c.stream));
+    TMBIR_CUDA(cudaMemcpyAsync(d.psiK, c.psiK_h[i].data(), c.psiK_h[i].size() * sizeof(double), cudaMemcpyHostToDevice,
+                               c.stream));
+    TMBIR_CUDA(cudaMemcpyAsync(d.psiA, c.psiA_h[i].data(), c.psiA_h[i].size() * sizeof(double), cudaMemcpyHostToDevice,
+                               c.stream));
+    TMBIR_CUDA(cudaMemcpyAsync(d.psiA32, c.psiA32_h[i].data(), c.psiA32_h[i].size() * sizeof(double),
+                               cudaMemcpyHostToDevice, c.stream));
+  }
+  // pageable host sources: make sure the copies have consumed them before the vectors go away
+  TMBIR_CUDA(cudaStreamSynchronize(c.stream));
+  c.operator_built = false;
+  return TMBIR_OK;
+}
+
+static int require_ready(const tmbir_ctx* ctx, bool need_operator) {
+  if (!ctx) return set_error(TMBIR_ERR_ARG, "ctx is NULL");
+  if (ctx->c.groups.empty()) return set_error(TMBIR_ERR_STATE, "no geometry set");
+  if (!ctx->c.ws) return set_error(TMBIR_ERR_WORKSPACE, "no workspace bound");
+  if (need_operator && !ctx->c.operator_built) return set_error(TMBIR_ERR_STATE, "operator not built");
+  return TMBIR_OK;
+}
+
+static int check_params(const tmbir_params* p) {
+  if (!p) return set_error(TMBIR_ERR_ARG, "params is NULL");
+  if (!(p->p >= 1.0 && p->q >= p->p && p->q <= 4.0)) return set_error(TMBIR_ERR_ARG, "need 1 <= p <= q <= 4");
+  if (!(p->c > 0.0 && p->sigma > 0.0 && p->lambda >= 0.0)) return set_error(TMBIR_ERR_ARG, "need c > 0, sigma > 0, lambda >= 0");
+  if (p->L <= 0.0 && p->q != 2.0) return set_error(TMBIR_ERR_ARG, "automatic L needs q = 2; pass L > 0");
+  return TMBIR_OK;
+}
+
+int tmbir_build_operator(tmbir_ctx* ctx, const float* d_sino, float* d_atg) {
+  if (int e = require_ready(ctx, false)) return e;
+  REQUIRE(d_sino && d_atg && aligned16(d_sino) && aligned16(d_atg), TMBIR_ERR_ARG,
+          "build_operator: sinogram and output must be non-NULL and 16-byte aligned");
+  Ctx& c = ctx->c;
+  for (size_t i = 0; i < c.groups.size(); ++i) {
+    if (int e = build_kernel_spectrum(c, (int)i)) return e;
+    if (int e = backproject(c, (int)i, d_sino, d_atg, false, true)) return e;
+    if (int e = group_gtg(c, (int)i, d_sino)) return e;
+    if (int e = power_iteration(c, (int)i, 100)) return e;
+  }
+  c.operator_built = true;
+  return TMBIR_OK;
+}
+
+int tmbir_fbp(tmbir_ctx* ctx, const float* d_sino, float* d_x0) {
+  if (int e = require_ready(ctx, false)) return e;
+  REQUIRE(d_sino && d_x0 && aligned16(d_sino) && aligned16(d_x0), TMBIR_ERR_ARG,
+          "fbp: sinogram and output must be non-NULL and 16-byte aligned");
+  Ctx& c = ctx->c;
+  for (size_t i = 0; i < c.groups.size(); ++i)
+    if (int e = backproject(c, (int)i, d_sino, d_x0, true, false)) return e;
+  return TMBIR_OK;
+}
+
+static int enqueue_iterations(Ctx& c, float* d_x, const float* d_atg, const PriorC& pc, int iters) {
+  StepArgs a{};
+  a.atg = d_atg;
+  a.xb[0] = d_x;
+  a.xb[1] = c.xbuf[0];
+  a.xb[2] = c.xbuf[1];
+  a.st = c.state;
+  for (int k = 0; k < iters; ++k) {
+    int off = 0;
+    for (size_t i = 0; i < c.gdev.size(); ++i) {
+      const GroupDev& g = c.gdev[i];
+      if (int e = launch_pass1(g, a, c.stream)) return e;
+      if (int e = launch_pass2(g, c.state, c.stream)) return e;
+      if (int e = launch_pass3(g, a, Pass3Mode::Iterate, pc, c.partials, off, c.stream)) return e;
+      off += blocks_pass3(g);
+    }
+    if (int e = launch_finalize(c.state, c.partials, off, c.log, c.stream)) return e;
+  }
+  return TMBIR_OK;
+}
+
+int tmbir_reconstruct(tmbir_ctx* ctx, float* d_x, const float* d_atg, const tmbir_params* prm, tmbir_stats* h_stats) {
+  if (int e = require_ready(ctx, true)) return e;
+  if (int e = check_params(prm)) return e;
+  REQUIRE(d_x && d_atg && aligned16(d_x) && aligned16(d_atg), TMBIR_ERR_ARG,
+          "reconstruct: image and R*g must be non-NULL and 16-byte aligned");
+  REQUIRE(prm->max_iter >= 0 && prm->max_iter <= kLogCap, TMBIR_ERR_ARG, "reconstruct: max_iter out of range");
+  Ctx& c = ctx->c;
+  cudaStream_t s = c.stream;
+  const PriorC pc = make_prior(*prm);
+  // gather the per-group lambda_max and 1/2 g.g into dscal[16 .. 16 + 2 ng)
+  const int ng = (int)c.gdev.size();
+  for (int i = 0; i < ng; ++i) {
+    TMBIR_CUDA(cudaMemcpyAsync(c.dscal + 16 + i, c.gdev[i].lam_max, sizeof(double), cudaMemcpyDeviceToDevice, s));
+    TMBIR_CUDA(cudaMemcpyAsync(c.dscal + 16 + ng + i, c.gdev[i].gtg, sizeof(double), cudaMemcpyDeviceToDevice, s));
+  }
+  k_init_state<<<1, 1, 0, s>>>(c.state, c.dscal + 16, c.dscal + 16 + ng, ng, prm->L, prm->lambda, prm->sigma,
+                               prm->F_ref, prm->gap_tol, prm->max_iter, prm->restart);
+  TMBIR_CHECK_LAUNCH();
+  // x_{-1} = x_0 so that the first (beta = 0) extrapolation reads finite values
+  TMBIR_CUDA(cudaMemcpyAsync(c.xbuf[1], d_x, c.total_voxels * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  const int iters = prm->max_iter;
+  bool graph = prm->use_graph != 0 && s != nullptr;
+  if (graph) {
+    const bool reuse = c.graph_exec && c.graph_iters == iters && c.graph_x == d_x && c.graph_atg == d_atg &&
+                       std::memcmp(&c.graph_prior, &pc, sizeof(PriorC)) == 0;
+    if (!reuse) {
+      if (c.graph_exec) {
+        cudaGraphExecDestroy(c.graph_exec);
+        c.graph_exec = nullptr;
+      }
+      cudaGraph_t gr;
+      const long long n0 = __atomic_load_n(&g_launches, __ATOMIC_RELAXED);
+      TMBIR_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+      int e = enqueue_iterations(c, d_x, d_atg, pc, iters);
+      cudaError_t ce = cudaStreamEndCapture(s, &gr);
+      // captured launches run only on replay: count them there
+      c.graph_nodes = __atomic_load_n(&g_launches, __ATOMIC_RELAXED) - n0;
+      __atomic_sub_fetch(&g_launches, c.graph_nodes, __ATOMIC_RELAXED);
+      if (e) return e;
+      if (ce != cudaSuccess) return set_error(TMBIR_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+      TMBIR_CUDA(cudaGraphInstantiate(&c.graph_exec, gr, 0));
+      cudaGraphDestroy(gr);
+      c.graph_iters = iters;
+      c.graph_x = d_x;
+      c.graph_atg = d_atg;
+      c.graph_prior = pc;
+    }
+    TMBIR_CUDA(cudaGraphLaunch(c.graph_exec, s));
+    __atomic_add_fetch(&g_launches, c.graph_nodes, __ATOMIC_RELAXED);
+  } else {
+    if (int e = enqueue_iterations(c, d_x, d_atg, pc, iters)) return e;
+  }
+  k_gather_final<<<1024, 256, 0, s>>>(c.state, d_x, c.xbuf[0], c.xbuf[1], c.total_voxels);
+  TMBIR_CHECK_LAUNCH();
+  c.last_iters = iters;
+  if (h_stats) {
+    IterState st;
+    TMBIR_CUDA(cudaMemcpyAsync(&st, c.state, sizeof(IterState), cudaMemcpyDeviceToHost, s));
+    TMBIR_CUDA(cudaStreamSynchronize(s));
+    h_stats->iterations = st.k;
+    h_stats->restarts = st.restarts;
+    h_stats->status = st.status;
+    h_stats->objective = st.last_F;
+    h_stats->gap = st.last_gap;
+    h_stats->L = st.L;
+    h_stats->grad_norm = std::sqrt(st.last_gg);
+    c.last_iters = st.k;
+    if (st.status != 0) return set_error(st.status, "reconstruct: non-finite value in a reduction");
+  }
+  return TMBIR_OK;
+}
+
+int tmbir_get_log(tmbir_ctx* ctx, double* h_log, int max_entries, int* n_out) {
+  if (int e = require_ready(ctx, false)) return e;
+  REQUIRE(h_log && n_out && max_entries >= 0, TMBIR_ERR_ARG, "get_log: NULL argument");
+  Ctx& c = ctx->c;
+  IterState st;
+  TMBIR_CUDA(cudaMemcpyAsync(&st, c.state, sizeof(IterState), cudaMemcpyDeviceToHost, c.stream));
+  TMBIR_CUDA(cudaStreamSynchronize(c.stream));
+  const int n = std::min(std::min(st.k, max_entries), kLogCap);
+  if (n > 0) {
+    TMBIR_CUDA(cudaMemcpyAsync(h_log, c.log, (size_t)n * 4 * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+    TMBIR_CUDA(cudaStreamSynchronize(c.stream));
+  }
+  *n_out = n;
+  return TMBIR_OK;
+}
+
+// one pass-1/2/3 sequence per group with explicit arguments, then the partial sums to the host
+static int run_explicit(Ctx& c, const StepArgs& a, Pass3Mode m, const PriorC& pc, double* h_parts) {
+  int off = 0;
+  for (size_t i = 0; i < c.gdev.size(); ++i) {
+    const GroupDev& g = c.gdev[i];
+    if (int e = launch_pass1(g, a, c.stream)) return e;
+    if (int e = launch_pass2(g, nullptr, c.stream)) return e;
+    if (int e = launch_pass3(g, a, m, pc, c.partials, off, c.stream)) return e;
+    off += blocks_pass3(g);
+  }
+  if (h_parts) {
+    if (int e = launch_sum_partials(c.partials, off, c.dscal, c.stream)) return e;
+    TMBIR_CUDA(cudaMemcpyAsync(h_parts, c.dscal, kParts * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+    TMBIR_CUDA(cudaStreamSynchronize(c.stream));
+  }
+  return TMBIR_OK;
+}
+
+int tmbir_normal_apply(tmbir_ctx* ctx, const float* d_x, float* d_z) {
+  if (int e = require_ready(ctx, true)) return e;
+  REQUIRE(d_x && d_z && aligned16(d_x) && aligned16(d_z), TMBIR_ERR_ARG, "normal_apply: bad buffers");
+  REQUIRE(d_x != d_z, TMBIR_ERR_ARG, "normal_apply: in-place not supported");
+  StepArgs a{};
+  a.x = d_x;
+  a.xprev = d_x;
+  a.beta = 0.f;
+  a.out = d_z;
+  PriorC pc{};
+  return run_explicit(ctx->c, a, Pass3Mode::Apply, pc, nullptr);
+}
+
+int tmbir_gradient(tmbir_ctx* ctx, const float* d_x, const float* d_atg, const tmbir_params* prm, float* d_grad) {
+  if (int e = require_ready(ctx, true)) return e;
+  if (int e = check_params(prm)) return e;
+  REQUIRE(d_x && d_atg && d_grad && aligned16(d_x) && aligned16(d_atg) && aligned16(d_grad), TMBIR_ERR_ARG,
+          "gradient: bad buffers");
+  REQUIRE(d_x != d_grad, TMBIR_ERR_ARG, "gradient: in-place not supported");
+  StepArgs a{};
+  a.x = d_x;
+  a.xprev = d_x;
+  a.beta = 0.f;
+  a.atg = d_atg;
+  a.out = d_grad;
+  return run_explicit(ctx->c, a, Pass3Mode::Gradient, make_prior(*prm), nullptr);
+}
+
+int tmbir_step(tmbir_ctx* ctx, const float* d_x, const float* d_x_prev, double beta, const float* d_atg,
+               const tmbir_params* prm, double L, float* d_x_next, double* h_partials) {
+  if (int e = require_ready(ctx, true)) return e;
+  if (int e = check_params(prm)) return e;
+  REQUIRE(d_x && d_x_prev && d_atg && d_x_next && aligned16(d_x) && aligned16(d_x_prev) && aligned16(d_atg) &&
+              aligned16(d_x_next),
+          TMBIR_ERR_ARG, "step: bad buffers");
+  REQUIRE(d_x_next != d_x && d_x_next != d_x_prev, TMBIR_ERR_ARG, "step: output must not alias the inputs");
+  REQUIRE(L > 0.0 && std::isfinite(beta), TMBIR_ERR_ARG, "step: need L > 0 and finite beta");
+  StepArgs a{};
+  a.x = d_x;
+  a.xprev = d_x_prev;
+  a.beta = (float)beta;
+  a.atg = d_atg;
+  a.out = d_x_next;
+  a.invL = (float)(1.0 / L);
+  double parts[kParts];
+  if (int e = run_explicit(ctx->c, a, Pass3Mode::Step, make_prior(*prm), parts)) return e;
+  if (h_partials) std::memcpy(h_partials, parts, 5 * sizeof(double));
+  return TMBIR_OK;
+}
+
+int tmbir_objective(tmbir_ctx* ctx, const float* d_x, const float* d_atg, const tmbir_params* prm, double* h_F) {
+  if (int e = require_ready(ctx, true)) return e;
+  if (int e = check_params(prm)) return e;
+  REQUIRE(d_x && d_atg && h_F && aligned16(d_x) && aligned16(d_atg), TMBIR_ERR_ARG, "objective: bad arguments");
+  Ctx& c = ctx->c;
+  StepArgs a{};
+  a.x = d_x;
+  a.xprev = d_x;
+  a.beta = 0.f;
+  a.atg = d_atg;
+  a.out = nullptr;
+  double parts[kParts];
+  if (int e = run_explicit(c, a, Pass3Mode::Objective, make_prior(*prm), parts)) return e;
+  double gh = 0.0;
+  for (size_t i = 0; i < c.gdev.size(); ++i) {
+    double v;
+    TMBIR_CUDA(cudaMemcpy(&v, c.gdev[i].gtg, sizeof(double), cudaMemcpyDeviceToHost));
+    gh += v;
+  }
+  *h_F = 0.5 * parts[0] - parts[1] + gh + prm->lambda * parts[2];
+  return TMBIR_OK;
+}
+
+int tmbir_lambda_max(tmbir_ctx* ctx, double* h_out) {
+  if (int e = require_ready(ctx, true)) return e;
+  REQUIRE(h_out != nullptr, TMBIR_ERR_ARG, "lambda_max: NULL output");
+  Ctx& c = ctx->c;
+  TMBIR_CUDA(cudaStreamSynchronize(c.stream));
+  for (size_t i = 0; i < c.gdev.size(); ++i)
+    TMBIR_CUDA(cudaMemcpy(&h_out[i], c.gdev[i].lam_max, sizeof(double), cudaMemcpyDeviceToHost));
+  return TMBIR_OK;
+}
+
+int tmbir_kernel(tmbir_ctx* ctx, int group, double* d_K) {
+  if (int e = require_ready(ctx, true)) return e;
+  Ctx& c = ctx->c;
+  REQUIRE(group >= 0 && group < (int)c.gdev.size() && d_K != nullptr, TMBIR_ERR_ARG, "kernel: bad group or output");
+  const size_t n = (size_t)(2 * c.gdev[group].N - 1) * (2 * c.gdev[group].N - 1);
+  TMBIR_CUDA(cudaMemcpyAsync(d_K, c.gdev[group].K, n * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+  return TMBIR_OK;
+}
+
+int tmbir_upsample_lanczos3(tmbir_ctx* ctx, const float* d_coarse, int n_slices, int Nc, float* d_fine) {
+  REQUIRE(ctx != nullptr, TMBIR_ERR_ARG, "upsample: ctx is NULL");
+  REQUIRE(d_coarse && d_fine && aligned16(d_coarse) && aligned16(d_fine), TMBIR_ERR_ARG, "upsample: bad buffers");
+  REQUIRE(n_slices >= 0 && Nc >= 1 && Nc <= 1 << 15, TMBIR_ERR_ARG, "upsample: bad sizes");
+  if (n_slices == 0) return TMBIR_OK;
+  return launch_upsample_lanczos3(d_coarse, n_slices, Nc, d_fine, ctx->c.stream);
+}
+
+int tmbir_downsample_sino(tmbir_ctx* ctx, const float* d_sino, int n_slices, int n_angles, int n_det, int factor,
+                          float* d_out) {
+  REQUIRE(ctx != nullptr, TMBIR_ERR_ARG, "downsample: ctx is NULL");
+  REQUIRE(d_sino && d_out && aligned16(d_sino) && aligned16(d_out), TMBIR_ERR_ARG, "downsample: bad buffers");
+  REQUIRE(n_slices >= 0 && n_angles >= 1 && n_det >= 2 && factor >= 1 && n_det % factor == 0 &&
+              (n_det / factor) % 2 == 0,
+          TMBIR_ERR_ARG, "downsample: need factor | n_det and an even coarse bin count");
+  if (n_slices == 0) return TMBIR_OK;
+  return launch_downsample_sino(d_sino, n_slices, n_angles, n_det, factor, d_out, ctx->c.stream);
+}
+
+int tmbir_pass_times(tmbir_ctx* ctx, float* d_x, const float* d_atg, const tmbir_params* prm, int iters, double* h_ms) {
+  if (int e = require_ready(ctx, true)) return e;
+  if (int e = check_params(prm)) return e;
+  REQUIRE(d_x && d_atg && h_ms && aligned16(d_x) && aligned16(d_atg) && iters >= 1 && iters <= kLogCap, TMBIR_ERR_ARG,
+          "pass_times: bad arguments");
+  Ctx& c = ctx->c;
+  cudaStream_t s = c.stream;
+  const PriorC pc = make_prior(*prm);
+  const int ng = (int)c.gdev.size();
+  for (int i = 0; i < ng; ++i) {
+    TMBIR_CUDA(cudaMemcpyAsync(c.dscal + 16 + i, c.gdev[i].lam_max, sizeof(double), cudaMemcpyDeviceToDevice, s));
+    TMBIR_CUDA(cudaMemcpyAsync(c.dscal + 16 + ng + i, c.gdev[i].gtg, sizeof(double), cudaMemcpyDeviceToDevice, s));
+  }
+  k_init_state<<<1, 1, 0, s>>>(c.state, c.dscal + 16, c.dscal + 16 + ng, ng, prm->L, prm->lambda, prm->sigma,
+                               prm->F_ref, 0.0, iters, prm->restart);
+  TMBIR_CHECK_LAUNCH();
+  TMBIR_CUDA(cudaMemcpyAsync(c.xbuf[1], d_x, c.total_voxels * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  StepArgs a{};
+  a.atg = d_atg;
+  a.xb[0] = d_x;
+  a.xb[1] = c.xbuf[0];
+  a.xb[2] = c.xbuf[1];
+  a.st = c.state;
+  cudaEvent_t ev[5];
+  for (auto& e : ev) TMBIR_CUDA(cudaEventCreate(&e));
+  double acc[4] = {0, 0, 0, 0};
+  int rc = TMBIR_OK;
+  for (int k = 0; k < iters && rc == TMBIR_OK; ++k) {
+    int off = 0;
+    for (int i = 0; i < ng && rc == TMBIR_OK; ++i) {
+      const GroupDev& g = c.gdev[i];
+      cudaEventRecord(ev[0], s);
+      if ((rc = launch_pass1(g, a, s))) break;
+      cudaEventRecord(ev[1], s);
+      if ((rc = launch_pass2(g, c.state, s))) break;
+      cudaEventRecord(ev[2], s);
+      if ((rc = launch_pass3(g, a, Pass3Mode::Iterate, pc, c.partials, off, s))) break;
+      cudaEventRecord(ev[3], s);
+      cudaEventSynchronize(ev[3]);
+      float ms;
+      cudaEventElapsedTime(&ms, ev[0], ev[1]);
+      acc[0] += ms;
+      cudaEventElapsedTime(&ms, ev[1], ev[2]);
+      acc[1] += ms;
+      cudaEventElapsedTime(&ms, ev[2], ev[3]);
+      acc[2] += ms;
+      off += blocks_pass3(g);
+    }
+    if (rc) break;
+    cudaEventRecord(ev[3], s);
+    rc = launch_finalize(c.state, c.partials, off, c.log, s);
+    cudaEventRecord(ev[4], s);
+    cudaEventSynchronize(ev[4]);
+    float ms;
+    cudaEventElapsedTime(&ms, ev[3], ev[4]);
+    acc[3] += ms;
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  if (rc) return rc;
+  k_gather_final<<<1024, 256, 0, s>>>(c.state, d_x, c.xbuf[0], c.xbuf[1], c.total_voxels);
+  TMBIR_CHECK_LAUNCH();
+  TMBIR_CUDA(cudaStreamSynchronize(s));
+  for (int j = 0; j < 4; ++j) h_ms[j] = acc[j];
+  return TMBIR_OK;
+}
+
+int tmbir_launch_count(const tmbir_ctx* ctx, long long* h_count) {
+  REQUIRE(ctx != nullptr && h_count != nullptr, TMBIR_ERR_ARG, "launch_count: NULL argument");
+  *h_count = __atomic_load_n(&g_launches, __ATOMIC_RELAXED);
+  return TMBIR_OK;
+}
+
+int tmbir_sync(tmbir_ctx* ctx) {
+  REQUIRE(ctx != nullptr, TMBIR_ERR_ARG, "sync: ctx is NULL");
+  TMBIR_CUDA(cudaStreamSynchronize(ctx->c.stream));
+  TMBIR_CUDA(cudaGetLastError());
+  return TMBIR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,160 @@
+// Internal declarations shared by the translation units of libtmbir.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/tmbir.h"
+
+namespace tmbir {
+
+// Device-resident optimiser state, advanced by the finalize kernel once per iteration.
+struct IterState {
+  double t;         // momentum sequence t_k
+  double beta;      // beta_k used by the current iteration
+  double L, invL;   // step constant
+  double lambda;    // prior weight
+  double gtg_half;  // 1/2 g.g summed over all groups
+  double F0, Fref, gap_tol;
+  double last_F, last_gap, last_gg, last_dot;
+  int k;            // iterations completed
+  int max_iter;
+  int restarts;
+  int cur;          // xbuf[cur] = x_k, xbuf[(cur+2)%3] = x_{k-1}, xbuf[(cur+1)%3] = x_{k+1}
+  int done;
+  int status;
+  int restart_mode;
+  int log_cap;
+};
+
+// Number of FP64 partial sums each reducing block writes.
+constexpr int kParts = 6;  // y.z, y.atg, Phi(y), <G, x_new - x>, G.G, z.z
+constexpr int kLogCap = 1 << 16;
+
+// qGGMRF constants in the form the kernels use.
+struct PriorC {
+  float p, q, qp;        // exponents and q - p
+  float inv_csig;        // 1 / (c sigma)
+  float inv_sig;         // 1 / sigma
+  float inv_sig2;        // 1 / sigma^2
+  float lam;             // lambda
+  float wf, we, wc;      // face / edge / corner neighbour weights (sum of the 26 is 1)
+  int q_is_2;
+};
+
+// One geometry group as the kernels see it (device pointers into the workspace).
+struct GroupDev {
+  int N, nd, na, S;
+  int slice0;          // first slice of the group in the stacked arrays
+  float span;
+  // Toeplitz operator
+  float* chat;         // [N+1][2][N] real spectrum, even/odd rows of the 2N grid, scaled by 1/(2N)^2
+  float2* twN;         // [P][T] exp(-2 pi i t k / N) for the row/column group FFT
+  float2* twM;         // [N] exp(-2 pi i n / 2N)
+  float2* spec;        // [S][N+1][N] intermediate spectra
+  // setup
+  double* angles;      // [na]
+  double* K;           // [(2N-1)^2] point-spread kernel
+  double* psiK;        // [2N-1] deconvolution factors for K (fine grid 4N)
+  double* psiA;        // [N] deconvolution factors for R*g (fine grid 2N)
+  double* psiA32;      // [N] deconvolution factors for the FP32 back-projection
+  double* lam_max;     // device scalar
+  double* gtg;         // device scalar (1/2 g.g of the group)
+};
+
+struct Ctx {
+  cudaStream_t stream = nullptr;
+  std::vector<tmbir_group> groups;
+  std::vector<std::vector<double>> angles;
+  std::vector<GroupDev> gdev;
+  // host copies of the NUFFT deconvolution tables (uploaded at set_workspace)
+  std::vector<std::vector<double>> psiK_h, psiA_h, psiA32_h;
+  int nufft_w64 = 12, nufft_w32 = 7;
+  double nufft_beta64 = 0, nufft_beta32 = 0;
+  size_t total_voxels = 0, total_sino = 0;
+  int total_slices = 0;
+  // workspace
+  char* ws = nullptr;
+  size_t ws_bytes = 0, ws_need = 0;
+  IterState* state = nullptr;
+  double* partials = nullptr;  // [max_blocks][kParts]
+  int max_blocks = 0;
+  double* log = nullptr;       // [kLogCap][4]
+  float* xbuf[2] = {nullptr, nullptr};
+  char* scratch = nullptr;     // setup scratch (aliases nothing used across calls)
+  size_t scratch_bytes = 0;
+  double* dscal = nullptr;     // small FP64 device scalars [64]
+  bool operator_built = false;
+  int last_iters = 0;
+  // layout offsets computed at set_geometry
+  std::vector<size_t> off_chat, off_twN, off_twM, off_spec, off_ang, off_K, off_psiK, off_psiA, off_psiA32, off_lam, off_gtg;
+  size_t off_state = 0, off_partials = 0, off_log = 0, off_xbuf0 = 0, off_xbuf1 = 0, off_scratch = 0, off_dscal = 0;
+  // CUDA graph cache for reconstruct
+  cudaGraphExec_t graph_exec = nullptr;
+  int graph_iters = -1;
+  const float* graph_atg = nullptr;
+  float* graph_x = nullptr;
+  PriorC graph_prior{};
+  long long graph_nodes = 0;
+};
+
+// error handling ------------------------------------------------------------
+int set_error(int code, const std::string& msg);
+#define TMBIR_CUDA(call)                                                                    \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess)                                                                  \
+      return ::tmbir::set_error(TMBIR_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+// kernels launched by the library in this process (graph replays add their kernel nodes)
+extern long long g_launches;
+#define TMBIR_CHECK_LAUNCH()             \
+  do {                                   \
+    TMBIR_CUDA(cudaGetLastError());      \
+    __atomic_add_fetch(&::tmbir::g_launches, 1, __ATOMIC_RELAXED); \
+  } while (0)
+
+// toeplitz.cu ---------------------------------------------------------------
+enum class Pass3Mode { Apply = 0, Gradient = 1, Step = 2, Iterate = 3, Objective = 4 };
+
+struct StepArgs {
+  const float* x;       // x_k (or the image for apply/gradient/objective)
+  const float* xprev;   // x_{k-1} (== x when beta = 0)
+  float beta;           // explicit momentum (ignored in Iterate mode)
+  const float* atg;     // R*g (Gradient, Step, Iterate, Objective)
+  float* out;           // z (Apply), G (Gradient), x_next (Step)
+  float invL;           // explicit step (Step mode)
+  // Iterate mode: rotation buffers and device state
+  float* xb[3];
+  const IterState* st;
+};
+
+int launch_pass1(const GroupDev& g, const StepArgs& a, cudaStream_t s);
+int launch_pass2(const GroupDev& g, const IterState* st, cudaStream_t s);
+int launch_pass3(const GroupDev& g, const StepArgs& a, Pass3Mode mode, const PriorC& pc, double* partials,
+                 int block_offset, cudaStream_t s);
+int blocks_pass3(const GroupDev& g);
+int launch_finalize(IterState* st, const double* partials, int nblocks, double* log, cudaStream_t s);
+int launch_sum_partials(const double* partials, int nblocks, double* out, cudaStream_t s);
+bool supported_N(int N);
+void fft_shape(int N, int* T, int* P);
+
+// setup.cu ------------------------------------------------------------------
+int setup_tables(Ctx& c);  // enqueue uploads of twiddles / psi tables into the workspace
+int build_kernel_spectrum(Ctx& c, int gi);
+int backproject(Ctx& c, int gi, const float* d_sino, float* d_out, bool ramp, bool fp64);
+int power_iteration(Ctx& c, int gi, int steps);
+int group_gtg(Ctx& c, int gi, const float* d_sino);
+void nufft_psi_table(int nmodes, int nfine, int w, double beta, std::vector<double>& out);
+size_t setup_scratch_bytes(const tmbir_group& g);
+
+// levels.cu -----------------------------------------------------------------
+int launch_upsample_lanczos3(const float* in, int S, int Nc, float* out, cudaStream_t s);
+int launch_downsample_sino(const float* in, int S, int na, int nd, int f, float* out, cudaStream_t s);
+
+PriorC make_prior(const tmbir_params& p);
+
+}  // namespace tmbir

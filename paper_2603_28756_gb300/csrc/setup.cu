@@ -1,0 +1,503 @@
+// Setup of the Toeplitz operator (Sec. 2.1) and the back-projection used for R*g and the
+// FBP start (Sec. 2.2), both through a type-1 non-uniform FFT (Eq. 4).
+//
+// Polar samples xi_{a,k} = (k / n_det) (cos theta_a, sin theta_a), |k| <= n_det/2 - 1.
+//   K(d)    = (1/n_det) sum_{a,k} exp(+2 pi i xi . d),               d in [-(N-1), N-1]^2
+//   R*g(x)  = (1/n_det) sum_{a,k} G(a,k) exp(-2 pi i xi . x),       G(a,k) = sum_m g(a,m) exp(2 pi i k s_m / n_det)
+// The type-1 transform spreads the samples onto a 2x oversampled periodic grid with the
+// "exponential of semicircle" kernel psi(u) = exp(beta (sqrt(1 - (2u/w)^2) - 1)) (Barnett,
+// Magland & af Klinteberg 2019), takes a 2D FFT and divides each output mode by the
+// kernel's Fourier transform.  Everything runs in FP64 for the operator (K, its spectrum and
+// R*g) and in FP32 for the FBP start.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "fft.cuh"
+#include "internal.h"
+
+namespace tmbir {
+
+// ---------------------------------------------------------------- batched 1D FFT along rows
+// Stockham autosort in shared memory: one block per row, radix 8/4/2 stages, natural order
+// in and out.  tw[j] = exp(-2 pi i j / n).
+template <int R, int DIR, class C>
+__device__ __forceinline__ void stockham_stage(const C* X, C* Y, int n, int Ls, const C* __restrict__ tw) {
+  const int nb = n / R;
+  const int tstep = n / (Ls * R);
+  for (int j = threadIdx.x; j < nb; j += blockDim.x) {
+    const int k = j & (Ls - 1);
+    C a[R];
+#pragma unroll
+    for (int m = 0; m < R; ++m) {
+      C v = X[j + m * nb];
+      if (m > 0 && k > 0) {
+        const C w = tw[(size_t)k * m * tstep & (n - 1)];
+        v = DIR < 0 ? cmul(v, w) : cmulc(v, w);
+      }
+      a[m] = v;
+    }
+    reg_dft<R, DIR, C>(a);
+    const int o = (j - k) * R + k;
+#pragma unroll
+    for (int m = 0; m < R; ++m) Y[o + m * Ls] = a[m];
+  }
+}
+
+template <int DIR, class C>
+__global__ void __launch_bounds__(256) k_fft_rows(C* data, int n, int log2n, size_t stride, const C* __restrict__ tw) {
+  extern __shared__ unsigned char smraw[];
+  C* X = reinterpret_cast<C*>(smraw);
+  C* Y = X + n;
+  C* row = data + (size_t)blockIdx.x * stride;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) X[j] = row[j];
+  __syncthreads();
+  int Ls = 1, rem = log2n;
+  while (rem > 0) {
+    if (rem >= 3) {
+      stockham_stage<8, DIR>(X, Y, n, Ls, tw);
+      Ls *= 8;
+      rem -= 3;
+    } else if (rem == 2) {
+      stockham_stage<4, DIR>(X, Y, n, Ls, tw);
+      Ls *= 4;
+      rem -= 2;
+    } else {
+      stockham_stage<2, DIR>(X, Y, n, Ls, tw);
+      Ls *= 2;
+      rem -= 1;
+    }
+    __syncthreads();
+    C* tmp = X;
+    X = Y;
+    Y = tmp;
+  }
+  for (int j = threadIdx.x; j < n; j += blockDim.x) row[j] = X[j];
+}
+
+// out[b][c][r] = in[b][r][c] for a batch of rows x cols matrices
+template <class C>
+__global__ void k_transpose(const C* __restrict__ in, C* __restrict__ out, int rows, int cols) {
+  __shared__ C tile[32][33];
+  const size_t boff = (size_t)blockIdx.z * rows * cols;
+  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int r = r0 + i, c = c0 + threadIdx.x;
+    if (r < rows && c < cols) tile[i][threadIdx.x] = in[boff + (size_t)r * cols + c];
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int c = c0 + i, r = r0 + threadIdx.x;
+    if (r < rows && c < cols) out[boff + (size_t)c * rows + r] = tile[threadIdx.x][i];
+  }
+}
+
+static int ilog2(int n) {
+  int l = 0;
+  while ((1 << l) < n) ++l;
+  return l;
+}
+
+template <class C>
+static int fft_rows(C* data, int n, int rows, int dir, const C* tw, cudaStream_t s) {
+  const size_t smem = 2 * (size_t)n * sizeof(C);
+  static bool attr_set = false;
+  if (!attr_set) {
+    TMBIR_CUDA(cudaFuncSetAttribute(k_fft_rows<-1, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    TMBIR_CUDA(cudaFuncSetAttribute(k_fft_rows<1, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    attr_set = true;
+  }
+  if (smem > 200 * 1024) return set_error(TMBIR_ERR_SHAPE, "setup FFT length too large");
+  if (dir < 0)
+    k_fft_rows<-1, C><<<rows, 256, smem, s>>>(data, n, ilog2(n), (size_t)n, tw);
+  else
+    k_fft_rows<1, C><<<rows, 256, smem, s>>>(data, n, ilog2(n), (size_t)n, tw);
+  TMBIR_CHECK_LAUNCH();
+  return TMBIR_OK;
+}
+
+template <class C>
+static int transpose(const C* in, C* out, int rows, int cols, int batch, cudaStream_t s) {
+  dim3 grid((cols + 31) / 32, (rows + 31) / 32, batch), block(32, 8);
+  k_transpose<C><<<grid, block, 0, s>>>(in, out, rows, cols);
+  TMBIR_CHECK_LAUNCH();
+  return TMBIR_OK;
+}
+
+// 2D FFT of `batch` n x n grids; result left transposed in `tmp` (tmp[b][kx][ky]).
+template <class C>
+static int fft2_transposed(C* grid, C* tmp, int n, int batch, int dir, const C* tw, cudaStream_t s) {
+  if (int e = fft_rows(grid, n, n * batch, dir, tw, s)) return e;
+  if (int e = transpose(grid, tmp, n, n, batch, s)) return e;
+  return fft_rows(tmp, n, n * batch, dir, tw, s);
+}
+
+// ---------------------------------------------------------------- spreading
+__device__ __forceinline__ double es_kernel(double z, double beta) {  // z in [-1, 1]
+  const double t = 1.0 - z * z;
+  return t > 0.0 ? exp(beta * (sqrt(t) - 1.0)) : 0.0;
+}
+__device__ __forceinline__ float es_kernel(float z, float beta) {
+  const float t = 1.0f - z * z;
+  return t > 0.0f ? __expf(beta * (sqrtf(t) - 1.0f)) : 0.0f;
+}
+__device__ __forceinline__ void atomic_add_c(double2* p, double2 v) {
+  atomicAdd(&p->x, v.x);
+  atomicAdd(&p->y, v.y);
+}
+__device__ __forceinline__ void atomic_add_c(float2* p, float2 v) {
+  atomicAdd(&p->x, v.x);
+  atomicAdd(&p->y, v.y);
+}
+
+// One thread per polar sample (slice b, angle a, radial k).  strengths == nullptr spreads
+// the constant 1/n_det (the kernel K).  grid: [b][n_f][n_f] indexed [ly][lx].
+template <int W, class C>
+__global__ void k_spread(const double* __restrict__ angles, int na, int nd, int nf, int batch,
+                         const C* __restrict__ strengths, C* __restrict__ grid, real_t<C> beta) {
+  using S = real_t<C>;
+  const int npa = nd - 1;  // radial samples per angle
+  const size_t total = (size_t)batch * na * npa;
+  for (size_t id = blockIdx.x * (size_t)blockDim.x + threadIdx.x; id < total; id += (size_t)gridDim.x * blockDim.x) {
+    const int kk = (int)(id % npa);
+    const int a = (int)((id / npa) % na);
+    const int b = (int)(id / ((size_t)npa * na));
+    const int k = kk - (nd / 2 - 1);
+    C c;
+    if (strengths) {
+      c = strengths[((size_t)b * na + a) * nd + (k < 0 ? k + nd : k)];
+    } else {
+      c = mkc((S)(1.0 / nd), (S)0);
+    }
+    double sa, ca;
+    sincos(angles[a], &sa, &ca);
+    const double ux = (double)k * ca * nf / nd, uy = (double)k * sa * nf / nd;
+    const int lx0 = (int)ceil(ux - 0.5 * W), ly0 = (int)ceil(uy - 0.5 * W);
+    S kx[W], ky[W];
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+      kx[j] = es_kernel((S)((2.0 * (lx0 + j - ux)) / W), beta);
+      ky[j] = es_kernel((S)((2.0 * (ly0 + j - uy)) / W), beta);
+    }
+    C* gb = grid + (size_t)b * nf * nf;
+#pragma unroll 1
+    for (int jy = 0; jy < W; ++jy) {
+      const int ly = (ly0 + jy + nf) % nf;
+      const C cy = mkc(c.x * ky[jy], c.y * ky[jy]);
+#pragma unroll
+      for (int jx = 0; jx < W; ++jx) {
+        const int lx = (lx0 + jx + nf) % nf;
+        atomic_add_c(&gb[(size_t)ly * nf + lx], mkc(cy.x * kx[jx], cy.y * kx[jx]));
+      }
+    }
+  }
+}
+
+// K[(dy+N-1)(2N-1) + dx+N-1] = Re B[dx][dy] / (psi(dx) psi(dy)); B transposed ([kx][ky]).
+__global__ void k_deconv_K(const double2* __restrict__ B, int nf, int N, const double* __restrict__ psi, double* K) {
+  const int W = 2 * N - 1;
+  for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < W * W; id += gridDim.x * blockDim.x) {
+    const int ix = id % W, iy = id / W;
+    const int dx = ix - (N - 1), dy = iy - (N - 1);
+    const double2 v = B[(size_t)((dx + nf) % nf) * nf + (dy + nf) % nf];
+    K[id] = v.x / (psi[ix] * psi[iy]);
+  }
+}
+
+// out[b][r][c] = scale * Re B[b][kx = c - N/2][ky = r - N/2] / (psi psi)
+template <class C>
+__global__ void k_deconv_img(const C* __restrict__ B, int nf, int N, int batch, const double* __restrict__ psi,
+                             float scale, float* __restrict__ out) {
+  const size_t total = (size_t)batch * N * N;
+  for (size_t id = blockIdx.x * (size_t)blockDim.x + threadIdx.x; id < total; id += (size_t)gridDim.x * blockDim.x) {
+    const int c = (int)(id % N), r = (int)((id / N) % N), b = (int)(id / ((size_t)N * N));
+    const int dx = c - N / 2, dy = r - N / 2;
+    const C v = B[(size_t)b * nf * nf + (size_t)((dx + nf) % nf) * nf + (dy + nf) % nf];
+    out[id] = (float)(scale * ((double)v.x / (psi[c] * psi[r])));
+  }
+}
+
+// circulant embedding of K in an M x M grid (M = 2N), complex FP64, [row = y][col = x]
+__global__ void k_circulant(const double* __restrict__ K, int N, double2* Cg) {
+  const int M = 2 * N, W = 2 * N - 1;
+  for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < M * M; id += gridDim.x * blockDim.x) {
+    const int x = id % M, y = id / M;
+    const int dx = x < N ? x : x - M, dy = y < N ? y : y - M;  // x == N (d = +-N) is never read by the crop
+    double v = 0.0;
+    if (dx > -N && dx < N && dy > -N && dy < N) v = K[(dy + N - 1) * W + dx + N - 1];
+    Cg[id] = make_double2(v, 0.0);
+  }
+}
+
+// chat[v][h][k] = Re C_hat[u = 2k + h][v] / M^2, spectrum transposed ([kx = v][ky = u])
+__global__ void k_chat_layout(const double2* __restrict__ B, int N, float* chat) {
+  const int M = 2 * N;
+  const size_t total = (size_t)(N + 1) * 2 * N;
+  for (size_t id = blockIdx.x * (size_t)blockDim.x + threadIdx.x; id < total; id += (size_t)gridDim.x * blockDim.x) {
+    const int k = (int)(id % N), h = (int)((id / N) % 2), v = (int)(id / (2 * (size_t)N));
+    const int u = 2 * k + h;
+    chat[id] = (float)(B[(size_t)v * M + u].x / ((double)M * (double)M));
+  }
+}
+
+// real sinogram rows -> complex rows for the radial FFT, optional ramp filter (Eq. 12 with the
+// unit-pitch Ram-Lak kernel h[0] = 1/4, h[odd n] = -1/(pi^2 n^2), h[even n != 0] = 0; linear
+// convolution over the detector, FP32 -- only the FBP start uses it)
+template <class C>
+__global__ void k_prepare_rows(const float* __restrict__ sino, int nd, size_t rows, int ramp, C* out) {
+  extern __shared__ float srow[];
+  float* htab = srow + nd;
+  using S = real_t<C>;
+  if (ramp) {
+    for (int n = threadIdx.x; n < nd; n += blockDim.x)
+      htab[n] = (n & 1) ? (float)(-1.0 / (M_PI * M_PI * (double)n * (double)n)) : 0.f;
+  }
+  for (size_t row = blockIdx.x; row < rows; row += gridDim.x) {
+    const float* g = sino + row * nd;
+    __syncthreads();
+    for (int m = threadIdx.x; m < nd; m += blockDim.x) srow[m] = g[m];
+    __syncthreads();
+    for (int m = threadIdx.x; m < nd; m += blockDim.x) {
+      float v = srow[m];
+      if (ramp) {
+        float acc = 0.25f * srow[m];
+        for (int m2 = (m & 1) ? 0 : 1; m2 < nd; m2 += 2) acc = fmaf(srow[m2], htab[m > m2 ? m - m2 : m2 - m], acc);
+        v = acc;
+      }
+      out[row * nd + m] = mkc((S)v, (S)0);
+    }
+  }
+}
+
+// G(a,k) = (-1)^k * sum_m g(a,m) exp(+2 pi i k m / nd) / nd: sign flip from s_m = m - nd/2, and the 1/nd of R*
+template <class C>
+__global__ void k_strength_fix(C* rows, int nd, size_t total) {
+  using S = real_t<C>;
+  for (size_t id = blockIdx.x * (size_t)blockDim.x + threadIdx.x; id < total; id += (size_t)gridDim.x * blockDim.x) {
+    const int k = (int)(id % nd);
+    const S sg = (k & 1) ? (S)(-1.0 / nd) : (S)(1.0 / nd);
+    const C v = rows[id];
+    rows[id] = mkc(v.x * sg, v.y * sg);
+  }
+}
+
+__global__ void k_sumsq(const float* __restrict__ x, size_t n, double* out) {
+  __shared__ double sh[256];
+  double s = 0.0;
+  for (size_t i = threadIdx.x; i < n; i += blockDim.x) s += (double)x[i] * (double)x[i];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = 0.5 * sh[0];
+}
+
+// ---------------------------------------------------------------- power iteration helpers
+__global__ void k_fill(float* x, size_t n, float v) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) x[i] = v;
+}
+// v = w / ||w||, ||w||^2 = sums[5];  lam = sums[0] (v.w)
+__global__ void k_normalize(const float* __restrict__ w, float* __restrict__ v, size_t n, const double* sums, double* lam) {
+  const double nrm = sqrt(sums[5]);
+  const float inv = (float)(1.0 / nrm);
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) v[i] = w[i] * inv;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *lam = sums[0];
+}
+
+// ---------------------------------------------------------------- host side
+// Gauss-Legendre nodes/weights on [-1, 1] by Newton iteration on the Legendre recurrence.
+static void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.resize(n);
+  w.resize(n);
+  for (int i = 0; i < n; ++i) {
+    double z = cos(M_PI * (i + 0.75) / (n + 0.5));
+    double dp = 0.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int j = 2; j <= n; ++j) {
+        double p2 = ((2.0 * j - 1.0) * z * p1 - (j - 1.0) * p0) / j;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+      double dz = p1 / dp;
+      z -= dz;
+      if (fabs(dz) < 1e-16) break;
+    }
+    double p0 = 1.0, p1 = z;
+    for (int j = 2; j <= n; ++j) {
+      double p2 = ((2.0 * j - 1.0) * z * p1 - (j - 1.0) * p0) / j;
+      p0 = p1;
+      p1 = p2;
+    }
+    dp = n * (z * p1 - p0) / (z * z - 1.0);
+    x[i] = z;
+    w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+// psi_hat(d) = int psi(u) cos(2 pi d u / nfine) du over |u| <= w/2, for modes d = -(nmodes/2) ..
+// (output index i <-> d = i - nmodes/2 for the image tables, d = i - (nmodes-1)/2 for K).
+void nufft_psi_table(int nmodes, int nfine, int w, double beta, std::vector<double>& out) {
+  std::vector<double> x, wt;
+  gauss_legendre(4 * w + 40, x, wt);
+  const int off = (nmodes % 2 == 1) ? (nmodes - 1) / 2 : nmodes / 2;
+  out.resize(nmodes);
+  for (int i = 0; i < nmodes; ++i) {
+    const int d = i - off;
+    double s = 0.0;
+    for (size_t q = 0; q < x.size(); ++q) {
+      const double u = 0.5 * w * x[q];
+      const double z = x[q];
+      const double t = 1.0 - z * z;
+      const double psi = t > 0 ? exp(beta * (sqrt(t) - 1.0)) : 0.0;
+      s += wt[q] * psi * cos(2.0 * M_PI * d * u / nfine);
+    }
+    out[i] = 0.5 * w * s;
+  }
+}
+
+// Scratch carve-up (complex elements, FP64 worst case):
+//   kernel spectrum:  tw[4N] | grid[(4N)^2] | tmp[(4N)^2]   (the 2N circulant FFT reuses grid)
+//   back-projection:  tw[2N] | strengths[n_angles * n_det] | grid[(2N)^2] | tmp[(2N)^2]
+size_t setup_scratch_bytes(const tmbir_group& g) {
+  const size_t N = g.N, nf_k = 4 * N, nf_a = 2 * N;
+  const size_t k_elems = nf_k + 2 * nf_k * nf_k;
+  const size_t rows = (size_t)g.n_angles * g.n_det;
+  const size_t a_elems = nf_a + rows + 2 * nf_a * nf_a;
+  return std::max(k_elems, a_elems) * sizeof(double2) + 256;
+}
+
+template <int Wd, class C>
+static int spread(const double* angles, int na, int nd, int nf, int batch, const C* strengths, C* grid, double beta,
+                  cudaStream_t s) {
+  const size_t total = (size_t)batch * na * (nd - 1);
+  const int blocks = (int)std::min<size_t>((total + 255) / 256, 152 * 16);
+  k_spread<Wd, C><<<blocks, 256, 0, s>>>(angles, na, nd, nf, batch, strengths, grid, (real_t<C>)beta);
+  TMBIR_CHECK_LAUNCH();
+  return TMBIR_OK;
+}
+
+// device twiddle tables for the setup FFTs (n up to 4N), carved from the front of the scratch
+template <class C>
+__global__ void k_twiddle(C* tw, int n) {
+  using S = real_t<C>;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    double sv, cv;
+    sincospi(-2.0 * j / n, &sv, &cv);
+    tw[j] = mkc((S)cv, (S)sv);
+  }
+}
+
+int build_kernel_spectrum(Ctx& c, int gi) {
+  GroupDev& g = c.gdev[gi];
+  cudaStream_t s = c.stream;
+  const int N = g.N, nf = 4 * N, M = 2 * N;
+  double2* tw = reinterpret_cast<double2*>(c.scratch);
+  double2* grid = tw + nf;
+  double2* tmp = grid + (size_t)nf * nf;
+  k_twiddle<double2><<<(nf + 255) / 256, 256, 0, s>>>(tw, nf);
+  TMBIR_CHECK_LAUNCH();
+  TMBIR_CUDA(cudaMemsetAsync(grid, 0, sizeof(double2) * nf * nf, s));
+  if (int e = spread<12, double2>(g.angles, g.na, g.nd, nf, 1, nullptr, grid, c.nufft_beta64, s)) return e;
+  if (int e = fft2_transposed(grid, tmp, nf, 1, +1, tw, s)) return e;
+  k_deconv_K<<<1024, 256, 0, s>>>(tmp, nf, N, g.psiK, g.K);
+  TMBIR_CHECK_LAUNCH();
+  // real spectrum of the 2N x 2N circulant embedding
+  k_twiddle<double2><<<(M + 255) / 256, 256, 0, s>>>(tw, M);
+  TMBIR_CHECK_LAUNCH();
+  double2* cg = grid;
+  double2* ct = grid + (size_t)M * M;
+  k_circulant<<<1024, 256, 0, s>>>(g.K, N, cg);
+  TMBIR_CHECK_LAUNCH();
+  if (int e = fft2_transposed(cg, ct, M, 1, -1, tw, s)) return e;
+  k_chat_layout<<<1024, 256, 0, s>>>(ct, N, g.chat);
+  TMBIR_CHECK_LAUNCH();
+  return TMBIR_OK;
+}
+
+template <class C>
+static int backproject_t(Ctx& c, int gi, const float* d_sino, float* d_out, bool ramp, float scale, int wsel) {
+  GroupDev& g = c.gdev[gi];
+  cudaStream_t s = c.stream;
+  const int N = g.N, nf = 2 * N, nd = g.nd, na = g.na;
+  const size_t rows = (size_t)na * nd;
+  C* tw = reinterpret_cast<C*>(c.scratch);
+  C* strengths = tw + nf;
+  C* grid = strengths + rows;
+  C* tmp = grid + (size_t)nf * nf;
+  const double* psi = std::is_same<C, double2>::value ? g.psiA : g.psiA32;
+  for (int b = 0; b < g.S; ++b) {
+    const float* sino_b = d_sino + (size_t)(g.slice0 + b) * na * nd;
+    // radial 1D transform of every projection: G(a, k)
+    k_prepare_rows<C><<<std::min<size_t>(na, 4096), 256, 2 * nd * sizeof(float), s>>>(sino_b, nd, na, ramp ? 1 : 0, strengths);
+    TMBIR_CHECK_LAUNCH();
+    k_twiddle<C><<<(nd + 255) / 256, 256, 0, s>>>(tw, nd);
+    TMBIR_CHECK_LAUNCH();
+    if (int e = fft_rows(strengths, nd, na, +1, tw, s)) return e;
+    k_strength_fix<C><<<1024, 256, 0, s>>>(strengths, nd, rows);
+    TMBIR_CHECK_LAUNCH();
+    TMBIR_CUDA(cudaMemsetAsync(grid, 0, sizeof(C) * nf * nf, s));
+    int e = 0;
+    if (wsel == 12)
+      e = spread<12, C>(g.angles, na, nd, nf, 1, strengths, grid, c.nufft_beta64, s);
+    else
+      e = spread<7, C>(g.angles, na, nd, nf, 1, strengths, grid, c.nufft_beta32, s);
+    if (e) return e;
+    k_twiddle<C><<<(nf + 255) / 256, 256, 0, s>>>(tw, nf);
+    TMBIR_CHECK_LAUNCH();
+    if (int e2 = fft2_transposed(grid, tmp, nf, 1, -1, tw, s)) return e2;
+    k_deconv_img<C><<<1024, 256, 0, s>>>(tmp, nf, N, 1, psi, scale, d_out + (size_t)(g.slice0 + b) * N * N);
+    TMBIR_CHECK_LAUNCH();
+  }
+  return TMBIR_OK;
+}
+
+int backproject(Ctx& c, int gi, const float* d_sino, float* d_out, bool ramp, bool fp64) {
+  const GroupDev& g = c.gdev[gi];
+  const float scale = ramp ? (float)(g.span / g.na) : 1.0f;
+  if (fp64) return backproject_t<double2>(c, gi, d_sino, d_out, ramp, scale, 12);
+  return backproject_t<float2>(c, gi, d_sino, d_out, ramp, scale, 7);
+}
+
+int group_gtg(Ctx& c, int gi, const float* d_sino) {
+  const GroupDev& g = c.gdev[gi];
+  const float* p = d_sino + (size_t)g.slice0 * g.na * g.nd;
+  k_sumsq<<<1, 256, 0, c.stream>>>(p, (size_t)g.S * g.na * g.nd, g.gtg);
+  TMBIR_CHECK_LAUNCH();
+  return TMBIR_OK;
+}
+
+// lambda_max(R*R) of a group: 100 power steps on one slice from the all-ones image
+int power_iteration(Ctx& c, int gi, int steps) {
+  GroupDev g = c.gdev[gi];
+  cudaStream_t s = c.stream;
+  const size_t n = (size_t)g.N * g.N;
+  // one-slice view of the group; images live in the two iterate buffers
+  g.S = 1;
+  g.slice0 = 0;
+  float* v = c.xbuf[0];
+  float* w = c.xbuf[1];
+  k_fill<<<256, 256, 0, s>>>(v, n, (float)(1.0 / g.N));
+  TMBIR_CHECK_LAUNCH();
+  PriorC pc{};
+  for (int it = 0; it < steps; ++it) {
+    StepArgs a{};
+    a.x = v;
+    a.xprev = v;
+    a.beta = 0.f;
+    a.out = w;
+    a.st = nullptr;
+    if (int e = launch_pass1(g, a, s)) return e;
+    if (int e = launch_pass2(g, nullptr, s)) return e;
+    if (int e = launch_pass3(g, a, Pass3Mode::Apply, pc, c.partials, 0, s)) return e;
+    if (int e = launch_sum_partials(c.partials, blocks_pass3(g), c.dscal, s)) return e;
+    k_normalize<<<256, 256, 0, s>>>(w, v, n, c.dscal, g.lam_max);
+    TMBIR_CHECK_LAUNCH();
+  }
+  return TMBIR_OK;
+}
+
+}  // namespace tmbir

@@ -1,0 +1,124 @@
+// Reductions, the optimiser state update and the size dispatch of the Toeplitz passes.
+// The passes themselves live in toeplitz_kernels.cuh (instantiated per image side by
+// toeplitz_inst.cu).
+#include "fft.cuh"
+#include "internal.h"
+
+namespace tmbir {
+
+bool supported_N(int N) { return N == 64 || N == 128 || N == 256 || N == 512 || N == 1024; }
+
+void fft_shape(int N, int* T, int* P) {
+  switch (N) {
+    case 64: *T = 8; *P = 8; break;
+    case 128: *T = 8; *P = 16; break;
+    case 256: *T = 16; *P = 16; break;
+    case 512: *T = 16; *P = 32; break;
+    default: *T = 32; *P = 32; break;
+  }
+}
+
+#define TMBIR_DECL_N(N)                                                                                     \
+  int pass1_##N(const GroupDev& g, const StepArgs& a, cudaStream_t s);                                      \
+  int pass2_##N(const GroupDev& g, const IterState* st, cudaStream_t s);                                    \
+  int pass3_##N(const GroupDev& g, const StepArgs& a, Pass3Mode m, const PriorC& pc, double* partials, int off, \
+                cudaStream_t s);
+TMBIR_DECL_N(64)
+TMBIR_DECL_N(128)
+TMBIR_DECL_N(256)
+TMBIR_DECL_N(512)
+TMBIR_DECL_N(1024)
+#undef TMBIR_DECL_N
+
+// ---------------------------------------------------------------- reductions and state update
+__device__ void reduce_blocks(const double* partials, int nblocks, double* outv) {
+  __shared__ double sh[512];
+  for (int j = 0; j < kParts; ++j) {
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) s += partials[(size_t)b * kParts + j];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+      if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) outv[j] = sh[0];
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(512) k_sum_partials(const double* partials, int nblocks, double* out) {
+  reduce_blocks(partials, nblocks, out);
+}
+
+__global__ void __launch_bounds__(512) k_finalize(IterState* st, const double* partials, int nblocks, double* log) {
+  __shared__ double S[kParts];
+  if (st->done) return;
+  reduce_blocks(partials, nblocks, S);
+  if (threadIdx.x != 0) return;
+  const double yz = S[0], yatg = S[1], phi = S[2], gdx = S[3], gg = S[4];
+  const double F = 0.5 * yz - yatg + st->gtg_half + st->lambda * phi;
+  const bool restart = st->restart_mode == TMBIR_RESTART_GRADIENT && gdx > 0.0;
+  const int k = st->k;
+  if (k < st->log_cap) {
+    log[4 * k + 0] = F;
+    log[4 * k + 1] = gdx;
+    log[4 * k + 2] = restart ? 1.0 : 0.0;
+    log[4 * k + 3] = gg;
+  }
+  const double tn = restart ? 1.0 : 0.5 * (1.0 + sqrt(1.0 + 4.0 * st->t * st->t));
+  const double tnn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * tn * tn));
+  st->beta = (tn - 1.0) / tnn;
+  st->t = tn;
+  st->restarts += restart ? 1 : 0;
+  st->k = k + 1;
+  st->cur = (st->cur + 1) % 3;
+  st->last_F = F;
+  st->last_dot = gdx;
+  st->last_gg = gg;
+  double gap = 0.0;
+  if (st->Fref == st->Fref && st->F0 != st->Fref) gap = (F - st->Fref) / (st->F0 - st->Fref);
+  st->last_gap = gap;
+  if (!isfinite(F) || !isfinite(gdx) || !isfinite(gg)) {
+    st->status = TMBIR_ERR_NONFINITE;
+    st->done = 1;
+  }
+  if (k + 1 >= st->max_iter) st->done = 1;
+  if (st->gap_tol > 0.0 && gap <= st->gap_tol) st->done = 1;
+}
+
+#define TMBIR_DISPATCH_N(N_, FN, ...)                               \
+  switch (N_) {                                                     \
+    case 64: return FN##64(__VA_ARGS__);                            \
+    case 128: return FN##128(__VA_ARGS__);                          \
+    case 256: return FN##256(__VA_ARGS__);                          \
+    case 512: return FN##512(__VA_ARGS__);                          \
+    case 1024: return FN##1024(__VA_ARGS__);                        \
+    default: return set_error(TMBIR_ERR_SHAPE, "unsupported N");    \
+  }
+
+int launch_pass1(const GroupDev& g, const StepArgs& a, cudaStream_t s) { TMBIR_DISPATCH_N(g.N, pass1_, g, a, s); }
+int launch_pass2(const GroupDev& g, const IterState* st, cudaStream_t s) { TMBIR_DISPATCH_N(g.N, pass2_, g, st, s); }
+int launch_pass3(const GroupDev& g, const StepArgs& a, Pass3Mode m, const PriorC& pc, double* partials, int off,
+                 cudaStream_t s) {
+  TMBIR_DISPATCH_N(g.N, pass3_, g, a, m, pc, partials, off, s);
+}
+int blocks_pass3(const GroupDev& g) {
+  int T, P;
+  fft_shape(g.N, &T, &P);
+  const int rb = 4 * (32 / T);
+  return g.S * (g.N / rb);
+}
+
+int launch_finalize(IterState* st, const double* partials, int nblocks, double* log, cudaStream_t s) {
+  k_finalize<<<1, 512, 0, s>>>(st, partials, nblocks, log);
+  TMBIR_CHECK_LAUNCH();
+  return TMBIR_OK;
+}
+int launch_sum_partials(const double* partials, int nblocks, double* out, cudaStream_t s) {
+  k_sum_partials<<<1, 512, 0, s>>>(partials, nblocks, out);
+  TMBIR_CHECK_LAUNCH();
+  return TMBIR_OK;
+}
+
+}  // namespace tmbir

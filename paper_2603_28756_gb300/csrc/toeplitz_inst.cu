@@ -1,0 +1,19 @@
+// Instantiates the three Toeplitz passes for one image side N (compiled once per supported N
+// with -DTMBIR_N=<N>, so the sizes build in parallel).
+#include "toeplitz_kernels.cuh"
+
+#ifndef TMBIR_N
+#error "compile with -DTMBIR_N=<image side>"
+#endif
+
+#define TMBIR_CAT2(a, b) a##b
+#define TMBIR_CAT(a, b) TMBIR_CAT2(a, b)
+
+namespace tmbir {
+int TMBIR_CAT(pass1_, TMBIR_N)(const GroupDev& g, const StepArgs& a, cudaStream_t s) { return pass1_n<TMBIR_N>(g, a, s); }
+int TMBIR_CAT(pass2_, TMBIR_N)(const GroupDev& g, const IterState* st, cudaStream_t s) { return pass2_n<TMBIR_N>(g, st, s); }
+int TMBIR_CAT(pass3_, TMBIR_N)(const GroupDev& g, const StepArgs& a, Pass3Mode m, const PriorC& pc, double* partials,
+                                int off, cudaStream_t s) {
+  return pass3_n<TMBIR_N>(g, a, m, pc, partials, off, s);
+}
+}  // namespace tmbir

@@ -1,0 +1,227 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances: the FP32 operator and gradient within 1e-5 relative L2 of the oracle; the FP64
+setup (kernel K, R*g) within 1e-10 / 1e-6 (the latter is the FP32 storage of R*g); the FP32
+FBP start within 1e-4 (its NUFFT uses a width-7 kernel, error ~1e-6 per sample).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2603_28756_gb300 as tm  # noqa: E402
+
+PRIOR = dict(p=1.2, q=2.0, c=0.01, sigma=0.1, lam=1.0)
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32).ravel()).cuda()
+
+
+def host(t, shape):
+    torch.cuda.synchronize()
+    return t.double().cpu().numpy().reshape(shape)
+
+
+class Problem:
+    def __init__(self, orc, N, S, na, span=math.pi, seed=5):
+        self.N, self.S, self.na = N, S, na
+        p = synth.volume(S=S, N=N, n_angles=na, n_ellipsoids=6, span=span, seed=seed)
+        self.theta, self.span = p.theta, span
+        self.sino = p.sino  # FP32 (S, na, N)
+        self.g = self.sino.astype(np.float64)
+        self.ctx = tm.Context([tm.Group(N=N, angles=list(self.theta), n_slices=S, span=span)])
+        self.d_sino = dev(self.sino)
+        self.d_atg = self.ctx.build_operator(self.d_sino)
+        self.K = orc.kernel(N, self.theta, N)
+        self.atg = orc.adjoint(self.g, N, self.theta)
+        rng = np.random.default_rng(seed + 1)
+        self.x = synth.random_image(rng, (S, N, N), 0.5).astype(np.float64)
+        self.xp = synth.random_image(rng, (S, N, N), 0.5).astype(np.float64)
+
+
+@pytest.fixture(scope="module", params=[(64, 3, 37, math.pi), (128, 2, 45, 2 * math.pi / 3)], ids=["N64", "N128limited"])
+def prob(request, orc):
+    N, S, na, span = request.param
+    return Problem(orc, N, S, na, span)
+
+
+def test_kernel_matches_dirichlet_sum(prob):
+    K = host(prob.ctx.kernel(0), prob.K.shape)
+    assert np.max(np.abs(K - prob.K)) <= 1e-10 * np.max(np.abs(prob.K))
+
+
+def test_atg_matches_adjoint(prob):
+    got = host(prob.d_atg, prob.atg.shape)
+    assert rel(got, prob.atg) < 1e-6
+
+
+def test_lambda_max_matches_power_iteration(prob, orc):
+    lam = prob.ctx.lambda_max()[0]
+    ref = orc.power_lambda_max(prob.K, prob.N)
+    assert abs(lam - ref) <= 1e-5 * ref
+
+
+def test_normal_apply(prob, orc):
+    z = host(prob.ctx.normal_apply(dev(prob.x)), prob.x.shape)
+    ref = orc.toeplitz(prob.x, prob.K)
+    assert rel(z, ref) < 1e-5
+
+
+def test_gradient(prob, orc):
+    pr = orc.Prior(**PRIOR)
+    G = host(prob.ctx.gradient(dev(prob.x), prob.d_atg, tm.Params(**PRIOR)), prob.x.shape)
+    ref = orc.gradient(prob.x, prob.atg, prob.K, pr)
+    assert rel(G, ref) < 1e-5
+
+
+def test_fused_step_and_partials(prob, orc):
+    pr = orc.Prior(**PRIOR)
+    beta, L = 0.37, 55.0
+    out, parts = prob.ctx.step(dev(prob.x), dev(prob.xp), beta, prob.d_atg, tm.Params(**PRIOR), L)
+    xn = host(out, prob.x.shape)
+    x32, xp32 = prob.x.astype(np.float32).astype(np.float64), prob.xp.astype(np.float32).astype(np.float64)
+    y = x32 + beta * (x32 - xp32)
+    z = orc.toeplitz(y, prob.K)
+    gp, phi = orc.prior(y, pr)
+    G = z - prob.atg + gp
+    ref = y - G / L
+    assert rel(xn, ref) < 1e-5
+    want = [np.sum(y * z), np.sum(y * prob.atg), phi / pr.lam, np.sum(G * (ref - x32)), np.sum(G * G)]
+    for k, (a, b) in enumerate(zip(parts, want)):
+        assert abs(a - b) <= 1e-5 * max(abs(b), 1e-3 * abs(want[0])), (k, a, b)
+
+
+def test_objective(prob, orc):
+    pr = orc.Prior(**PRIOR)
+    F = prob.ctx.objective(dev(prob.x), prob.d_atg, tm.Params(**PRIOR))
+    ref = orc.objective(prob.x, prob.atg, float(np.sum(prob.g ** 2)), prob.K, pr)
+    assert abs(F - ref) <= 1e-5 * abs(ref)
+
+
+def test_fbp(prob, orc):
+    f0 = host(prob.ctx.fbp(prob.d_sino), prob.atg.shape)
+    ref = orc.fbp(prob.g, prob.N, prob.theta, prob.span)
+    assert rel(f0, ref) < 1e-4
+
+
+def test_reconstruct_follows_oracle_trajectory(prob, orc):
+    pr = orc.Prior(**PRIOR)
+    iters = 30
+    x = torch.zeros(prob.x.size, dtype=torch.float32, device="cuda")
+    st = prob.ctx.reconstruct(x, prob.d_atg, tm.Params(**PRIOR, max_iter=iters))
+    assert st.iterations == iters and st.status == 0
+    log = prob.ctx.get_log()
+    L = orc.lipschitz(prob.K, prob.N, pr)
+    assert abs(st.L - L) <= 1e-5 * L
+    olog = []
+    ref = orc.nesterov(np.zeros(prob.x.shape), prob.atg, float(np.sum(prob.g ** 2)), prob.K, pr, L, iters, log=olog)
+    got = host(x, prob.x.shape)
+    assert rel(got, ref) < 1e-4
+    for (F, dot, rs, gg), (Fo, doto, rso) in zip(log, olog):
+        assert abs(F - Fo) <= 1e-5 * abs(Fo)
+        if abs(doto) > 1e-3 * abs(F):
+            assert bool(rs) == rso
+
+
+def test_graph_replay_is_bitwise_eager(prob):
+    prm = dict(PRIOR, max_iter=7)
+    a = torch.zeros(prob.x.size, dtype=torch.float32, device="cuda")
+    b = torch.zeros_like(a)
+    prob.ctx.reconstruct(a, prob.d_atg, tm.Params(**prm, use_graph=True))
+    prob.ctx.reconstruct(b, prob.d_atg, tm.Params(**prm, use_graph=False))
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    # a second replay of the cached graph gives the same result again
+    c = torch.zeros_like(a)
+    prob.ctx.reconstruct(c, prob.d_atg, tm.Params(**prm, use_graph=True))
+    torch.cuda.synchronize()
+    assert torch.equal(a, c)
+
+
+def test_uneven_groups_equal_separate_contexts(orc):
+    specs = [(64, 2, 30), (128, 1, 50), (64, 1, 20)]
+    groups, sinos, ctxs = [], [], []
+    for k, (N, S, na) in enumerate(specs):
+        p = synth.volume(S=S, N=N, n_angles=na, n_ellipsoids=4, seed=40 + k)
+        groups.append(tm.Group(N=N, angles=list(p.theta), n_slices=S))
+        sinos.append(p.sino.ravel())
+        ctxs.append(tm.Context([groups[-1]]))
+    big = tm.Context(groups)
+    atg = big.build_operator(dev(np.concatenate(sinos)))
+    rng = np.random.default_rng(3)
+    xs = [synth.random_image(rng, (S, N, N)).ravel() for N, S, _ in specs]
+    G = big.gradient(dev(np.concatenate(xs)), atg, tm.Params(**PRIOR))
+    torch.cuda.synchronize()
+    off = 0
+    for k, (N, S, _) in enumerate(specs):
+        a1 = ctxs[k].build_operator(dev(sinos[k]))
+        G1 = ctxs[k].gradient(dev(xs[k]), a1, tm.Params(**PRIOR))
+        torch.cuda.synchronize()
+        n = S * N * N
+        assert torch.equal(G[off:off + n], G1), k
+        off += n
+
+
+def test_lanczos_upsampling(orc):
+    rng = np.random.default_rng(9)
+    for S, Nc in [(2, 32), (1, 100)]:
+        c = rng.standard_normal((S, Nc, Nc)).astype(np.float32)
+        ctx = tm.Context([tm.Group(N=64, angles=[0.0], n_slices=1)])
+        f = host(ctx.upsample_lanczos3(dev(c), S, Nc), (S, 2 * Nc, 2 * Nc))
+        ref = orc.lanczos_up(c.astype(np.float64))
+        assert np.array_equal(f[:, ::2, ::2], c.astype(np.float64))
+        assert np.max(np.abs(f - ref)) < 1e-5 * np.max(np.abs(ref))
+
+
+def test_downsample_sino_bitwise(orc):
+    rng = np.random.default_rng(10)
+    g = rng.standard_normal((3, 7, 64)).astype(np.float32)
+    ctx = tm.Context([tm.Group(N=64, angles=[0.0], n_slices=1)])
+    for f in (2, 4):
+        d = host(ctx.downsample_sino(dev(g), 3, 7, 64, f), (3, 7, 64 // f))
+        assert np.array_equal(d, orc.downsample_sino(g.astype(np.float64), f))
+
+
+def test_argument_errors():
+    with pytest.raises(tm.TmbirError) as e:
+        tm.Context([tm.Group(N=96, angles=[0.0, 1.0])])
+    assert e.value.code == -2
+    with pytest.raises(tm.TmbirError) as e:
+        tm.Context([tm.Group(N=64, angles=[0.0], n_det=128)])
+    assert e.value.code == -2
+    ctx = tm.Context([tm.Group(N=64, angles=[0.0, 1.0])])
+    x = torch.zeros(64 * 64 + 1, device="cuda")
+    with pytest.raises(tm.TmbirError) as e:
+        ctx.normal_apply(x)  # operator not built yet
+    assert e.value.code == -7
+    sino = torch.zeros(2 * 64 + 4, device="cuda")
+    with pytest.raises(tm.TmbirError) as e:
+        ctx.build_operator(sino[1:], torch.zeros(64 * 64, device="cuda"))  # misaligned
+    assert e.value.code == -1
+    with pytest.raises(tm.TmbirError) as e:
+        ctx.downsample_sino(sino, 1, 2, 64, 3)
+    assert e.value.code == -1
+
+
+def test_nonfinite_input_is_reported():
+    p = synth.volume(S=1, N=64, n_angles=20, n_ellipsoids=3, seed=77)
+    ctx = tm.Context([tm.Group(N=64, angles=list(p.theta))])
+    atg = ctx.build_operator(dev(p.sino))
+    x = torch.zeros(64 * 64, device="cuda")
+    x[100] = float("nan")
+    with pytest.raises(tm.TmbirError) as e:
+        ctx.reconstruct(x, atg, tm.Params(max_iter=5))
+    assert e.value.code == -6
