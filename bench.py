@@ -33,6 +33,8 @@ WORKLOADS = {
     "batched-64x1024sq-256ang-100it": (64, 1024, 256, math.pi, 100, 20),
     "single-1x128sq-90ang-50it": (1, 128, 90, math.pi, 50, 10),
     "small-8x256sq-128ang-50it": (8, 256, 128, math.pi, 50, 10),
+    # profiling case: same image side and angles as the default, 16 slices (> L2, a few GB on device)
+    "profile-16x1024sq-256ang-20it": (16, 1024, 256, math.pi, 20, 20),
 }
 DEFAULT = "batched-64x1024sq-256ang-100it"
 PRIOR = dict(p=1.2, q=2.0, c=0.01, sigma=0.1, lam=1.0)

@@ -32,6 +32,8 @@ PriorC make_prior(const tmbir_params& p) {
   c.we = (float)(1.0 / std::sqrt(2.0) / total);
   c.wc = (float)(1.0 / std::sqrt(3.0) / total);
   c.q_is_2 = p.q == 2.0 ? 1 : 0;
+  c.l2_inv_csig = (float)std::log2(1.0 / (p.c * p.sigma));
+  c.l2_inv_sig = (float)std::log2(1.0 / p.sigma);
   return c;
 }
 
@@ -213,9 +215,14 @@ int tmbir_set_geometry(tmbir_ctx* ctx, int n_groups, const tmbir_group* groups) 
   c.total_sino = sino;
   c.total_slices = slices;
   int s0 = 0;
+  size_t io = 0, so = 0;
   for (int i = 0; i < n_groups; ++i) {
     c.gdev[i].slice0 = s0;
+    c.gdev[i].img_off = io;
+    c.gdev[i].sino_off = so;
     s0 += gs[i].n_slices;
+    io += (size_t)gs[i].n_slices * gs[i].N * gs[i].N;
+    so += (size_t)gs[i].n_slices * gs[i].n_angles * gs[i].n_det;
   }
   c.total_slices = s0;
   g_last_error.clear();

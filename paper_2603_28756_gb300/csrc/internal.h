@@ -42,6 +42,8 @@ struct PriorC {
   float inv_sig2;        // 1 / sigma^2
   float lam;             // lambda
   float wf, we, wc;      // face / edge / corner neighbour weights (sum of the 26 is 1)
+  float l2_inv_csig;     // log2(1 / (c sigma))
+  float l2_inv_sig;      // log2(1 / sigma)
   int q_is_2;
 };
 
@@ -49,6 +51,8 @@ struct PriorC {
 struct GroupDev {
   int N, nd, na, S;
   int slice0;          // first slice of the group in the stacked arrays
+  size_t img_off;      // first element of the group in the stacked image arrays
+  size_t sino_off;     // first element of the group in the stacked sinogram
   float span;
   // Toeplitz operator
   float* chat;         // [N+1][2][N] real spectrum, even/odd rows of the 2N grid, scaled by 1/(2N)^2
@@ -137,6 +141,14 @@ int launch_pass2(const GroupDev& g, const IterState* st, cudaStream_t s);
 int launch_pass3(const GroupDev& g, const StepArgs& a, Pass3Mode mode, const PriorC& pc, double* partials,
                  int block_offset, cudaStream_t s);
 int blocks_pass3(const GroupDev& g);
+// Slices each pass-3 block marches through: enough blocks for about four waves of two
+// blocks per SM on 152 SMs, longer marches when the volume has slices to spare.
+inline int pass3_slices_per_block(int S, int row_blocks) {
+  int chunks = (1216 + row_blocks / 2) / row_blocks;
+  if (chunks < 1) chunks = 1;
+  if (chunks > S) chunks = S;
+  return (S + chunks - 1) / chunks;
+}
 int launch_finalize(IterState* st, const double* partials, int nblocks, double* log, cudaStream_t s);
 int launch_sum_partials(const double* partials, int nblocks, double* out, cudaStream_t s);
 bool supported_N(int N);

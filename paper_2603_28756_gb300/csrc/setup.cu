@@ -281,10 +281,27 @@ __global__ void k_strength_fix(C* rows, int nd, size_t total) {
   }
 }
 
-__global__ void k_sumsq(const float* __restrict__ x, size_t n, double* out) {
+// 1/2 sum x^2: each block reduces a strided share in FP64 (fixed order), then one block sums
+// the block partials in order.
+__global__ void k_sumsq_blocks(const float* __restrict__ x, size_t n, double* part) {
   __shared__ double sh[256];
   double s = 0.0;
-  for (size_t i = threadIdx.x; i < n; i += blockDim.x) s += (double)x[i] * (double)x[i];
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const double v = x[i];
+    s += v * v;
+  }
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+__global__ void k_sum_half(const double* __restrict__ part, int n, double* out) {
+  __shared__ double sh[256];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += part[i];
   sh[threadIdx.x] = s;
   __syncthreads();
   for (int o = 128; o > 0; o >>= 1) {
@@ -430,7 +447,7 @@ static int backproject_t(Ctx& c, int gi, const float* d_sino, float* d_out, bool
   C* tmp = grid + (size_t)nf * nf;
   const double* psi = std::is_same<C, double2>::value ? g.psiA : g.psiA32;
   for (int b = 0; b < g.S; ++b) {
-    const float* sino_b = d_sino + (size_t)(g.slice0 + b) * na * nd;
+    const float* sino_b = d_sino + g.sino_off + (size_t)b * na * nd;
     // radial 1D transform of every projection: G(a, k)
     k_prepare_rows<C><<<std::min<size_t>(na, 4096), 256, 2 * nd * sizeof(float), s>>>(sino_b, nd, na, ramp ? 1 : 0, strengths);
     TMBIR_CHECK_LAUNCH();
@@ -449,7 +466,7 @@ static int backproject_t(Ctx& c, int gi, const float* d_sino, float* d_out, bool
     k_twiddle<C><<<(nf + 255) / 256, 256, 0, s>>>(tw, nf);
     TMBIR_CHECK_LAUNCH();
     if (int e2 = fft2_transposed(grid, tmp, nf, 1, -1, tw, s)) return e2;
-    k_deconv_img<C><<<1024, 256, 0, s>>>(tmp, nf, N, 1, psi, scale, d_out + (size_t)(g.slice0 + b) * N * N);
+    k_deconv_img<C><<<1024, 256, 0, s>>>(tmp, nf, N, 1, psi, scale, d_out + g.img_off + (size_t)b * N * N);
     TMBIR_CHECK_LAUNCH();
   }
   return TMBIR_OK;
@@ -464,8 +481,11 @@ int backproject(Ctx& c, int gi, const float* d_sino, float* d_out, bool ramp, bo
 
 int group_gtg(Ctx& c, int gi, const float* d_sino) {
   const GroupDev& g = c.gdev[gi];
-  const float* p = d_sino + (size_t)g.slice0 * g.na * g.nd;
-  k_sumsq<<<1, 256, 0, c.stream>>>(p, (size_t)g.S * g.na * g.nd, g.gtg);
+  const float* p = d_sino + g.sino_off;
+  double* part = reinterpret_cast<double*>(c.scratch);
+  k_sumsq_blocks<<<1024, 256, 0, c.stream>>>(p, (size_t)g.S * g.na * g.nd, part);
+  TMBIR_CHECK_LAUNCH();
+  k_sum_half<<<1, 256, 0, c.stream>>>(part, 1024, g.gtg);
   TMBIR_CHECK_LAUNCH();
   return TMBIR_OK;
 }
@@ -478,6 +498,7 @@ int power_iteration(Ctx& c, int gi, int steps) {
   // one-slice view of the group; images live in the two iterate buffers
   g.S = 1;
   g.slice0 = 0;
+  g.img_off = 0;
   float* v = c.xbuf[0];
   float* w = c.xbuf[1];
   k_fill<<<256, 256, 0, s>>>(v, n, (float)(1.0 / g.N));

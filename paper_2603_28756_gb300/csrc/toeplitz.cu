@@ -106,8 +106,9 @@ int launch_pass3(const GroupDev& g, const StepArgs& a, Pass3Mode m, const PriorC
 int blocks_pass3(const GroupDev& g) {
   int T, P;
   fft_shape(g.N, &T, &P);
-  const int rb = 4 * (32 / T);
-  return g.S * (g.N / rb);
+  const int nb = g.N / (4 * (32 / T));
+  const int zc = pass3_slices_per_block(g.S, nb);
+  return nb * ((g.S + zc - 1) / zc);
 }
 
 int launch_finalize(IterState* st, const double* partials, int nblocks, double* log, cudaStream_t s) {

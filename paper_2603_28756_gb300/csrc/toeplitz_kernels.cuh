@@ -60,20 +60,31 @@ __device__ __forceinline__ float rcpa(float x) {
   return y;
 }
 
+// 1/x for x >= 1 on the FMA pipe: integer seed then three Newton steps r <- r (2 - x r).
+// Seed: the bit pattern of 1/x is about (253 + c) 2^23 - bits(x); c = 0.9 balances the seed
+// error to within 5.2 % over every binade, and three quadratic steps bring it below 1e-7.
+__device__ __forceinline__ float rcp_newton(float x) {
+  float r = __int_as_float(0x7EF33333 - __float_as_int(x));
+#pragma unroll
+  for (int it = 0; it < 3; ++it) r = fmaf(r, fmaf(-x, r, 1.0f), r);
+  return r;
+}
+
 // rho'(d) (and rho(d) when PHI) of the qGGMRF potential
 //   rho(d)  = |d/sigma|^q / (1 + u),            u = |d/(c sigma)|^(q-p)
 //   rho'(d) = d/sigma^2 |d/sigma|^(q-2) (q + p u) / (1 + u)^2
+// Two special-function operations (log2 and exp2) per call; the reciprocal runs on the FMA pipe.
 template <bool Q2, bool PHI>
 __device__ __forceinline__ float drho(float d, const PriorC& c, float& rho) {
-  float a = fmaxf(fabsf(d), 1e-30f);
-  float la = lg2a(a);
-  float u = ex2a(c.qp * (la + lg2a(c.inv_csig)));
-  float r = rcpa(1.0f + u);
+  const float a = fmaxf(fabsf(d), 1e-30f);
+  const float la = lg2a(a);
+  const float u = ex2a(fmaf(c.qp, la, c.qp * c.l2_inv_csig));
+  const float r = rcp_newton(1.0f + u);
   if constexpr (Q2) {
     if constexpr (PHI) rho = d * d * c.inv_sig2 * r;
     return d * c.inv_sig2 * fmaf(c.p, u, 2.0f) * r * r;
   } else {
-    float aq2 = ex2a((c.q - 2.0f) * (la + lg2a(c.inv_sig)));
+    const float aq2 = ex2a((c.q - 2.0f) * (la + c.l2_inv_sig));
     if constexpr (PHI) rho = aq2 * d * d * c.inv_sig2 * r;
     return d * c.inv_sig2 * aq2 * fmaf(c.p, u, c.q) * r * r;
   }
@@ -87,11 +98,11 @@ __device__ __forceinline__ double warp_sum(double v) {
 
 // Block reduction of kParts values to partials[block]: fixed order, FP64.
 template <int W>
-__device__ __forceinline__ void block_partials(float (&acc)[kParts], double* red, double* out) {
+__device__ __forceinline__ void block_partials(double (&acc)[kParts], double* red, double* out) {
   int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
   for (int j = 0; j < kParts; ++j) {
-    double v = warp_sum((double)acc[j]);
+    double v = warp_sum(acc[j]);
     if (lane == 0) red[warp * kParts + j] = v;
   }
   __syncthreads();
@@ -126,7 +137,7 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) k_pass1(GroupDev g, StepArgs 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, grp = lane / T, t = lane % T;
   const int rl = warp * G + grp;
   const int r = rb * RB + rl;
-  const size_t base = ((size_t)(g.slice0 + s) * N + r) * N;
+  const size_t base = g.img_off + ((size_t)s * N + r) * N;
 
   // packed real row: z[n] = y[2n] + i y[2n+1], nonzero for n < N/2 (the rest is padding)
   float2 v[P];
@@ -233,15 +244,63 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) k_pass2(GroupDev g, const Ite
 }
 
 // ---------------------------------------------------------------- pass 3: rows, inverse + gradient
+// A block owns RB consecutive rows of one group and marches through a chunk of its slices.
+// Per slice: the inverse row transforms give K (*) y for the block's rows; then the qGGMRF
+// gradient is accumulated pair by pair.  For the neighbourhood, thread t owns a band of RS
+// rows and KCH chunks of CHW columns.  A neighbour pair whose two voxels the same thread owns
+// (in the same slice, or in consecutive slices of the block's chunk) is evaluated once and
+// applied to both voxels -- the next-slice half is carried in registers to the next step;
+// every other pair is evaluated from each side for that side only.  Each unordered pair
+// enters Phi once, from the voxel it is a forward offset of (lexicographic in dz, dy, dx).
+template <int N>
+struct Geo3 {
+  using Gm = Geo<N>;
+  static constexpr int RB = Gm::RB, THREADS = Gm::THREADS;
+  static constexpr int RS = 4;                      // rows per band
+  static constexpr int NBAND = RB / RS;
+  static constexpr int NSTRIP = THREADS / NBAND;    // column strips per band
+  static constexpr int CW = N / NSTRIP;             // columns per thread
+  static constexpr int CHW = CW < 4 ? CW : 4;       // columns per chunk
+  static constexpr int KCH = CW / CHW;              // chunks per thread
+  static constexpr int ROWS = RB + 2;               // ring rows (one halo row each side)
+  static constexpr size_t SM_RING = (size_t)2 * ROWS * N * sizeof(float);
+  static constexpr size_t SM_A = Gm::cmax(Gm::SM1, (size_t)RB * N * sizeof(float));
+  static constexpr size_t SM = SM_A + SM_RING;
+  static_assert(NBAND * RS == RB && NSTRIP * NBAND == THREADS && KCH * CHW * NSTRIP == N, "stencil layout");
+};
+
+// y = x + beta (x - x_prev) for block rows -1 .. RB of one slice into a ring slot (zero outside)
+template <int N>
+__device__ __forceinline__ void load_ring(float* slot, const float* x, const float* xp, float beta, size_t off_slice,
+                                          int r0, bool valid_slice) {
+  using G3 = Geo3<N>;
+  for (int e = threadIdx.x; e < G3::ROWS * (N / 4); e += G3::THREADS) {
+    const int c4 = e % (N / 4), rowi = e / (N / 4);
+    const int rr = r0 - 1 + rowi;
+    float4 yv = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (valid_slice && rr >= 0 && rr < N) {
+      const size_t off = off_slice + (size_t)rr * N;
+      const float4 xv = __ldg(reinterpret_cast<const float4*>(x + off) + c4);
+      const float4 pv = __ldg(reinterpret_cast<const float4*>(xp + off) + c4);
+      yv = make_float4(fmaf(beta, xv.x - pv.x, xv.x), fmaf(beta, xv.y - pv.y, xv.y), fmaf(beta, xv.z - pv.z, xv.z),
+                       fmaf(beta, xv.w - pv.w, xv.w));
+    }
+    reinterpret_cast<float4*>(slot + rowi * N)[c4] = yv;
+  }
+}
+
 template <int N, int MODE, bool Q2>
 __global__ void __launch_bounds__(Geo<N>::THREADS)
-    k_pass3(GroupDev g, StepArgs a, PriorC pc, double* partials, int block_offset) {
+    k_pass3(GroupDev g, StepArgs a, PriorC pc, double* partials, int block_offset, int zc) {
   using Gm = Geo<N>;
+  using G3 = Geo3<N>;
   using F = typename Gm::F;
   constexpr int T = Gm::T, P = Gm::P, G = Gm::G, RB = Gm::RB, LD = Gm::LD;
+  constexpr int RS = G3::RS, CHW = G3::CHW, KCH = G3::KCH, NSTRIP = G3::NSTRIP, ROWS = G3::ROWS;
   constexpr bool PRIOR = MODE != (int)Pass3Mode::Apply;
   constexpr bool PHI = MODE == (int)Pass3Mode::Step || MODE == (int)Pass3Mode::Iterate ||
                        MODE == (int)Pass3Mode::Objective;
+  constexpr bool UPDATE = MODE == (int)Pass3Mode::Step || MODE == (int)Pass3Mode::Iterate;
   extern __shared__ float2 sm[];
   __shared__ double red[Gm::W * kParts];
   const float *x, *xp;
@@ -250,9 +309,9 @@ __global__ void __launch_bounds__(Geo<N>::THREADS)
   if constexpr (MODE == (int)Pass3Mode::Iterate) {
     if (a.st->done) return;
     const int cur = a.st->cur;
-    x = a.xb[cur];
-    xp = a.xb[(cur + 2) % 3];
-    out = a.xb[(cur + 1) % 3];
+    x = cur == 0 ? a.xb[0] : (cur == 1 ? a.xb[1] : a.xb[2]);
+    xp = cur == 0 ? a.xb[2] : (cur == 1 ? a.xb[0] : a.xb[1]);
+    out = cur == 0 ? a.xb[1] : (cur == 1 ? a.xb[2] : a.xb[0]);
     beta = (float)a.st->beta;
     invL = (float)a.st->invL;
   } else {
@@ -262,144 +321,253 @@ __global__ void __launch_bounds__(Geo<N>::THREADS)
     beta = a.beta;
     invL = a.invL;
   }
-  const int s = blockIdx.x / Gm::NB, rb = blockIdx.x % Gm::NB;
+  const int rb = blockIdx.x % Gm::NB, chunk = blockIdx.x / Gm::NB;
+  const int z0 = chunk * zc, z1 = min(g.S, z0 + zc);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, grp = lane / T, t = lane % T;
   const int rl = warp * G + grp;
-  const int r0 = rb * RB, r = r0 + rl;
-  const size_t slice_base = (size_t)(g.slice0 + s) * N * N;
-  const size_t base = slice_base + (size_t)r * N;
-
-  // stage the half-spectrum rows of this block: tb[row][v]
+  const int r0 = rb * RB;
+  // stencil ownership
+  const int band = threadIdx.x / NSTRIP, strip = threadIdx.x % NSTRIP;
+  const int brow0 = band * RS;  // first block row of the band
   float2* tb = sm;
-  {
-    const float2* sp = g.spec + (size_t)s * (N + 1) * N + r0;
-    for (int e = threadIdx.x; e < (N + 1) * RB; e += Gm::THREADS) {
-      const int vv = e / RB, rr = e - vv * RB;
-      tb[rr * LD + vv] = sp[(size_t)vv * N + rr];
-    }
+  float* kzs = reinterpret_cast<float*>(sm);  // K(*)y of the block rows, [RB][N], after the transforms
+  float* ring = reinterpret_cast<float*>(reinterpret_cast<char*>(sm) + G3::SM_A);
+  const size_t N2 = (size_t)N * N;
+
+  double dacc[kParts];
+#pragma unroll
+  for (int j = 0; j < kParts; ++j) dacc[j] = 0.0;
+  float own[RS][KCH * CHW], nxt[RS][KCH * CHW];
+#pragma unroll
+  for (int i = 0; i < RS; ++i)
+#pragma unroll
+    for (int j = 0; j < KCH * CHW; ++j) own[i][j] = nxt[i][j] = 0.f;
+
+  if constexpr (PRIOR) {
+    load_ring<N>(ring + (z0 & 1) * ROWS * N, x, xp, beta, g.img_off + (size_t)z0 * N2, r0, true);
+    if (z0 > 0) load_ring<N>(ring + ((z0 - 1) & 1) * ROWS * N, x, xp, beta, g.img_off + (size_t)(z0 - 1) * N2, r0, true);
   }
-  __syncthreads();
-  // fold the Hermitian half spectrum into a packed length-N inverse transform:
-  //   E[v] = Z[v] + conj(Z[N-v]),  O[v] = (Z[v] - conj(Z[N-v])) exp(+2 pi i v / 2N),  q = IFFT(E + iO)
-  float2 q[P];
-  SFor<0, P>::run([&](auto i_) {
-    constexpr int i = decltype(i_)::value;
-    const int vp = t + T * i;
-    const float2 z = tb[rl * LD + vp];
-    const float2 zr = tb[rl * LD + N - vp];
-    const float2 e = make_float2(z.x + zr.x, z.y - zr.y);
-    const float2 d = make_float2(z.x - zr.x, z.y + zr.y);
-    const float2 o = cmulc(d, __ldg(&g.twM[vp]));
-    q[i] = make_float2(e.x - o.y, e.y + o.x);
-  });
-  __syncthreads();
-  F::template run<1>(q, sm + (warp * G + grp) * F::SMEM, g.twN, t);
-  // q[i], i < P/2, holds (K(*)y)[r][2n], [r][2n+1] with n = t + T i
+  const float wts[4] = {0.f, pc.wf, pc.we, pc.wc};
+  const float mL = (strip == 0) ? 0.f : 1.f;           // chunk 0's left halo column exists
+  const float mR = (strip == NSTRIP - 1) ? 0.f : 1.f;  // last chunk's right halo column exists
 
-  float acc[kParts];
-#pragma unroll
-  for (int j = 0; j < kParts; ++j) acc[j] = 0.f;
-
-  if constexpr (!PRIOR) {
-    // operator only: z = K (*) x
-    SFor<0, P / 2>::run([&](auto i_) {
-      constexpr int i = decltype(i_)::value;
-      const int n = t + T * i;
-      const float2 xv = __ldg(reinterpret_cast<const float2*>(x + base) + n);
-      reinterpret_cast<float2*>(out + base)[n] = q[i];
-      acc[0] += xv.x * q[i].x + xv.y * q[i].y;
-      acc[5] += q[i].x * q[i].x + q[i].y * q[i].y;
-    });
-  } else {
-    // y tile with one halo row and one halo slice on each side: yt[dz][row][col]
+  for (int z = z0; z < z1; ++z) {
+    const size_t slice_base = g.img_off + (size_t)z * N2;
+    // ---- K (*) y for rows r0 .. r0+RB-1 of slice z
     __syncthreads();
-    float* yt = reinterpret_cast<float*>(sm);
-    constexpr int ROWS = RB + 2;
-    for (int e = threadIdx.x; e < 3 * ROWS * (N / 4); e += Gm::THREADS) {
-      const int c4 = e % (N / 4);
-      const int rowi = (e / (N / 4)) % ROWS;
-      const int dz = e / (ROWS * (N / 4));
-      const int zz = s - 1 + dz, rr = r0 - 1 + rowi;
-      float4 yv = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (zz >= 0 && zz < g.S && rr >= 0 && rr < N) {
-        const size_t off = ((size_t)(g.slice0 + zz) * N + rr) * N;
-        const float4 xv = __ldg(reinterpret_cast<const float4*>(x + off) + c4);
-        const float4 pv = __ldg(reinterpret_cast<const float4*>(xp + off) + c4);
-        yv = make_float4(fmaf(beta, xv.x - pv.x, xv.x), fmaf(beta, xv.y - pv.y, xv.y),
-                         fmaf(beta, xv.z - pv.z, xv.z), fmaf(beta, xv.w - pv.w, xv.w));
+    {
+      const float2* sp = g.spec + (size_t)z * (N + 1) * N + r0;
+      for (int e = threadIdx.x; e < (N + 1) * RB; e += Gm::THREADS) {
+        const int vv = e / RB, rr = e - vv * RB;
+        tb[rr * LD + vv] = sp[(size_t)vv * N + rr];
       }
-      reinterpret_cast<float4*>(yt + (dz * ROWS + rowi) * N)[c4] = yv;
     }
     __syncthreads();
-    const bool zval[3] = {s > 0, true, s + 1 < g.S};
-    const bool rval[3] = {r > 0, true, r + 1 < N};
-    const float wts[4] = {0.f, pc.wf, pc.we, pc.wc};
+    float2 q[P];
+    SFor<0, P>::run([&](auto i_) {
+      constexpr int i = decltype(i_)::value;
+      const int vp = t + T * i;
+      const float2 zv = tb[rl * LD + vp];
+      const float2 zr = tb[rl * LD + N - vp];
+      const float2 e = make_float2(zv.x + zr.x, zv.y - zr.y);
+      const float2 d = make_float2(zv.x - zr.x, zv.y + zr.y);
+      const float2 o = cmulc(d, __ldg(&g.twM[vp]));
+      q[i] = make_float2(e.x - o.y, e.y + o.x);
+    });
+    __syncthreads();
+    F::template run<1>(q, sm + (warp * G + grp) * F::SMEM, g.twN, t);
+    __syncthreads();
     SFor<0, P / 2>::run([&](auto i_) {
       constexpr int i = decltype(i_)::value;
-      const int n = t + T * i;
-      const int c0 = 2 * n;
-      const float* yc = yt + (1 * ROWS + rl + 1) * N;
-      const float y0 = yc[c0], y1 = yc[c0 + 1];
-      const float mL = c0 > 0 ? 1.f : 0.f, mR = c0 + 2 < N ? 1.f : 0.f;
-      float g0 = 0.f, g1 = 0.f, ph = 0.f, rh = 0.f;
+      reinterpret_cast<float2*>(kzs + rl * N)[t + T * i] = q[i];
+    });
+
+    float yo[RS][KCH * CHW];  // own y values of slice z
+    float acc[kParts];
 #pragma unroll
-      for (int dz = 0; dz < 3; ++dz) {
-        if (!zval[dz]) continue;
-#pragma unroll
-        for (int dy = 0; dy < 3; ++dy) {
-          if (!rval[dy]) continue;
-          const float* rp = yt + (dz * ROWS + rl + dy) * N;
-          const float A = rp[c0], B = rp[c0 + 1];
-          const float Lf = c0 > 0 ? rp[c0 - 1] : 0.f;
-          const float Rt = c0 + 2 < N ? rp[c0 + 2] : 0.f;
-          const int ring = (dz != 1) + (dy != 1);
-          const float w0 = wts[ring], w1 = wts[ring + 1];
-          // forward offsets (lexicographic in dz, dy, dx) count each unordered pair once in Phi
-          const bool fwd_plane = dz > 1 || (dz == 1 && dy > 1);
-          if (ring != 0) {
-            g0 += w0 * drho<Q2, PHI>(y0 - A, pc, rh);
-            if (PHI && fwd_plane) ph += w0 * rh;
-            g1 += w0 * drho<Q2, PHI>(y1 - B, pc, rh);
-            if (PHI && fwd_plane) ph += w0 * rh;
-            float f = w1 * drho<Q2, PHI>(y0 - B, pc, rh);  // (0, +1) from voxel 0
-            g0 += f;
-            if (PHI && fwd_plane) ph += w1 * rh;
-            f = w1 * drho<Q2, PHI>(y1 - A, pc, rh);  // (0, -1) from voxel 1
-            g1 += f;
-            if (PHI && fwd_plane) ph += w1 * rh;
-          } else {
-            // the pair (voxel 0, voxel 1) itself: one evaluation, antisymmetric
-            const float f = w1 * drho<Q2, PHI>(y0 - y1, pc, rh);
-            g0 += f;
-            g1 -= f;
-            if (PHI) ph += w1 * rh;
+    for (int j = 0; j < kParts; ++j) acc[j] = 0.f;
+
+    if constexpr (PRIOR) {
+      const float* slot_z = ring + (z & 1) * ROWS * N;
+      SFor<0, RS>::run([&](auto i_) {
+        constexpr int i = decltype(i_)::value;
+        SFor<0, KCH>::run([&](auto k_) {
+          constexpr int k = decltype(k_)::value;
+          const int col0 = CHW * (strip + NSTRIP * k);
+          SFor<0, CHW>::run([&](auto c_) {
+            constexpr int ci = decltype(c_)::value;
+            yo[i][k * CHW + ci] = slot_z[(brow0 + i + 1) * N + col0 + ci];
+          });
+        });
+      });
+      // pair evaluation against one partner row (slice z + DZ, band row PR), for every own row
+      // within one row of it.  SHARED: the partner slice is processed by this block (both ends
+      // owned by one thread are then updated here, or were already, see below).
+      auto pairs = [&](auto dz_, auto pr_, const float* slot, bool shared_z) {
+        constexpr int DZ = decltype(dz_)::value, PR = decltype(pr_)::value;
+        float pv[KCH][CHW + 2];
+        const int prow = brow0 + PR;  // partner block row
+        SFor<0, KCH>::run([&](auto k_) {
+          constexpr int k = decltype(k_)::value;
+          const int col0 = CHW * (strip + NSTRIP * k);
+          const float* rp = slot + (prow + 1) * N;
+          SFor<0, CHW>::run([&](auto c_) {
+            constexpr int ci = decltype(c_)::value;
+            pv[k][ci + 1] = rp[col0 + ci];
+          });
+          pv[k][0] = rp[col0 > 0 ? col0 - 1 : 0];
+          pv[k][CHW + 1] = rp[col0 + CHW < N ? col0 + CHW : N - 1];
+        });
+        SFor<0, RS>::run([&](auto i_) {
+          constexpr int RR = decltype(i_)::value;
+          constexpr int DY = PR - RR;
+          if constexpr (DY >= -1 && DY <= 1) {
+            SFor<0, KCH>::run([&](auto k_) {
+              constexpr int k = decltype(k_)::value;
+              SFor<0, CHW>::run([&](auto c_) {
+                constexpr int ci = decltype(c_)::value;
+                SFor<0, 3>::run([&](auto d_) {
+                  constexpr int DX = decltype(d_)::value - 1;
+                  if constexpr (!(DZ == 0 && DY == 0 && DX == 0)) {
+                    constexpr bool owned = PR >= 0 && PR < RS && ci + DX >= 0 && ci + DX < CHW;
+                    constexpr bool fwd = DZ > 0 || (DZ == 0 && (DY > 0 || (DY == 0 && DX > 0)));
+                    constexpr int ring_n = (DZ != 0) + (DY != 0) + (DX != 0);
+                    // 0: skip, 1: both ends (same slice), 2: own end (+ next-slice end if shared)
+                    constexpr int kind = DZ == 0 ? (owned ? (fwd ? 1 : 0) : 2) : (DZ > 0 ? 2 : (owned ? 3 : 2));
+                    if constexpr (kind != 0) {
+                      // kind 3: owned partner in slice z-1, evaluated at step z-1 unless z is the chunk start
+                      if (kind != 3 || !shared_z) {
+                        float m = 1.f;
+                        if constexpr (ci + DX < 0) m = (k == 0) ? mL : 1.f;
+                        if constexpr (ci + DX >= CHW) m = (k == KCH - 1) ? mR : 1.f;
+                        const float w = wts[ring_n];
+                        float rh = 0.f;
+                        const float f = w * drho<Q2, PHI>(yo[RR][k * CHW + ci] - pv[k][ci + DX + 1], pc, rh);
+                        if constexpr (kind == 1) {
+                          own[RR][k * CHW + ci] += f;
+                          own[PR][k * CHW + ci + DX] -= f;
+                          if constexpr (PHI) acc[2] += w * rh;
+                        } else {
+                          own[RR][k * CHW + ci] += m * f;
+                          if constexpr (PHI && fwd) acc[2] += m * w * rh;
+                          if constexpr (DZ > 0 && owned) {
+                            if (shared_z) nxt[PR][k * CHW + ci + DX] -= f;
+                          }
+                        }
+                      }
+                    }
+                  }
+                });
+              });
+            });
           }
-          g0 += mL * w1 * drho<Q2, PHI>(y0 - Lf, pc, rh);
-          if (PHI && fwd_plane) ph += mL * w1 * rh;
-          const float fr = mR * w1 * drho<Q2, PHI>(y1 - Rt, pc, rh);
-          g1 += fr;
-          if (PHI && (fwd_plane || ring == 0)) ph += mR * w1 * rh;
+        });
+      };
+      const bool row_lo = r0 + brow0 - 1 >= 0, row_hi = r0 + brow0 + RS < N;
+      // slice z - 1 (own end only, except owned pairs at the chunk start)
+      if (z > 0) {
+        const float* slot_m = ring + ((z - 1) & 1) * ROWS * N;
+        const bool shared_m = z - 1 >= z0;
+        if (row_lo) pairs(std::integral_constant<int, -1>{}, std::integral_constant<int, -1>{}, slot_m, shared_m);
+        SFor<0, RS>::run([&](auto p_) { pairs(std::integral_constant<int, -1>{}, p_, slot_m, shared_m); });
+        if (row_hi) pairs(std::integral_constant<int, -1>{}, std::integral_constant<int, RS>{}, slot_m, shared_m);
+      }
+      __syncthreads();  // kzs complete; slot of z - 1 free
+      if (z + 1 < g.S)
+        load_ring<N>(ring + ((z + 1) & 1) * ROWS * N, x, xp, beta, slice_base + N2, r0, true);
+      __syncthreads();
+      // slice z
+      if (row_lo) pairs(std::integral_constant<int, 0>{}, std::integral_constant<int, -1>{}, slot_z, true);
+      SFor<0, RS>::run([&](auto p_) { pairs(std::integral_constant<int, 0>{}, p_, slot_z, true); });
+      if (row_hi) pairs(std::integral_constant<int, 0>{}, std::integral_constant<int, RS>{}, slot_z, true);
+      // slice z + 1
+      if (z + 1 < g.S) {
+        const float* slot_p = ring + ((z + 1) & 1) * ROWS * N;
+        const bool shared_p = z + 1 < z1;
+        if (row_lo) pairs(std::integral_constant<int, 1>{}, std::integral_constant<int, -1>{}, slot_p, shared_p);
+        SFor<0, RS>::run([&](auto p_) { pairs(std::integral_constant<int, 1>{}, p_, slot_p, shared_p); });
+        if (row_hi) pairs(std::integral_constant<int, 1>{}, std::integral_constant<int, RS>{}, slot_p, shared_p);
+      }
+    } else {
+      __syncthreads();
+    }
+
+    // ---- per voxel: gradient, update, partial sums (CHW consecutive columns at a time)
+    SFor<0, RS>::run([&](auto i_) {
+      constexpr int i = decltype(i_)::value;
+      const int row = r0 + brow0 + i;
+      const size_t rbase = slice_base + (size_t)row * N;
+      SFor<0, KCH>::run([&](auto k_) {
+        constexpr int k = decltype(k_)::value;
+        const int col0 = CHW * (strip + NSTRIP * k);
+        float zd[CHW], at[CHW], xv[CHW], res[CHW];
+        (void)res;
+        SFor<0, CHW>::run([&](auto c_) {
+          constexpr int ci = decltype(c_)::value;
+          zd[ci] = kzs[(brow0 + i) * N + col0 + ci];
+        });
+        const bool need_x = !PRIOR || UPDATE;
+        const bool need_at = PRIOR;
+        if constexpr (CHW == 4) {
+          if (need_x) {
+            const float4 v = __ldg(reinterpret_cast<const float4*>(x + rbase + col0));
+            xv[0] = v.x; xv[1] = v.y; xv[2] = v.z; xv[3] = v.w;
+          }
+          if (need_at) {
+            const float4 v = __ldg(reinterpret_cast<const float4*>(a.atg + rbase + col0));
+            at[0] = v.x; at[1] = v.y; at[2] = v.z; at[3] = v.w;
+          }
+        } else {
+          SFor<0, CHW>::run([&](auto c_) {
+            constexpr int ci = decltype(c_)::value;
+            if (need_x) xv[ci] = __ldg(x + rbase + col0 + ci);
+            if (need_at) at[ci] = __ldg(a.atg + rbase + col0 + ci);
+          });
         }
-      }
-      const float2 zd = q[i];
-      const float2 at = __ldg(reinterpret_cast<const float2*>(a.atg + base) + n);
-      const float G0 = zd.x - at.x + pc.lam * g0;
-      const float G1 = zd.y - at.y + pc.lam * g1;
-      acc[0] += y0 * zd.x + y1 * zd.y;
-      acc[1] += y0 * at.x + y1 * at.y;
-      acc[2] += ph;
-      acc[4] += G0 * G0 + G1 * G1;
-      if constexpr (MODE == (int)Pass3Mode::Gradient) {
-        reinterpret_cast<float2*>(out + base)[n] = make_float2(G0, G1);
-      } else if constexpr (MODE == (int)Pass3Mode::Step || MODE == (int)Pass3Mode::Iterate) {
-        const float2 xv = __ldg(reinterpret_cast<const float2*>(x + base) + n);
-        const float n0 = fmaf(-invL, G0, y0), n1 = fmaf(-invL, G1, y1);
-        reinterpret_cast<float2*>(out + base)[n] = make_float2(n0, n1);
-        acc[3] += G0 * (n0 - xv.x) + G1 * (n1 - xv.y);
-      }
+        SFor<0, CHW>::run([&](auto c_) {
+          constexpr int ci = decltype(c_)::value;
+          if constexpr (!PRIOR) {
+            res[ci] = zd[ci];
+            acc[0] += xv[ci] * zd[ci];
+            acc[5] += zd[ci] * zd[ci];
+          } else {
+            const float yv = yo[i][k * CHW + ci];
+            const float Gv = zd[ci] - at[ci] + pc.lam * own[i][k * CHW + ci];
+            acc[0] += yv * zd[ci];
+            acc[1] += yv * at[ci];
+            acc[4] += Gv * Gv;
+            if constexpr (MODE == (int)Pass3Mode::Gradient) {
+              res[ci] = Gv;
+            } else if constexpr (UPDATE) {
+              const float xn = fmaf(-invL, Gv, yv);
+              res[ci] = xn;
+              acc[3] += Gv * (xn - xv[ci]);
+            }
+          }
+        });
+        if constexpr (MODE != (int)Pass3Mode::Objective) {
+          if constexpr (CHW == 4) {
+            *reinterpret_cast<float4*>(out + rbase + col0) = make_float4(res[0], res[1], res[2], res[3]);
+          } else {
+            SFor<0, CHW>::run([&](auto c_) {
+              constexpr int ci = decltype(c_)::value;
+              out[rbase + col0 + ci] = res[ci];
+            });
+          }
+        }
+      });
     });
+#pragma unroll
+    for (int j = 0; j < kParts; ++j) dacc[j] += (double)acc[j];
+#pragma unroll
+    for (int i = 0; i < RS; ++i)
+#pragma unroll
+      for (int j = 0; j < KCH * CHW; ++j) {
+        own[i][j] = nxt[i][j];
+        nxt[i][j] = 0.f;
+      }
   }
-  block_partials<Gm::W>(acc, red, partials + (size_t)(block_offset + blockIdx.x) * kParts);
+  block_partials<Gm::W>(dacc, red, partials + (size_t)(block_offset + blockIdx.x) * kParts);
 }
 
 // ---------------------------------------------------------------- host launchers
@@ -412,7 +580,7 @@ static int set_smem_limits() {
   TMBIR_CUDA(cudaFuncSetAttribute(k_pass2<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Gm::SM2));
 #define TMBIR_P3ATTR(M, Q)                                                                           \
   TMBIR_CUDA(cudaFuncSetAttribute(k_pass3<N, M, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                  (int)Gm::SM3));
+                                  (int)Geo3<N>::SM));
   TMBIR_P3ATTR(0, true) TMBIR_P3ATTR(1, true) TMBIR_P3ATTR(2, true) TMBIR_P3ATTR(3, true) TMBIR_P3ATTR(4, true)
   TMBIR_P3ATTR(1, false) TMBIR_P3ATTR(2, false) TMBIR_P3ATTR(3, false) TMBIR_P3ATTR(4, false)
 #undef TMBIR_P3ATTR
@@ -442,10 +610,12 @@ static int pass3_nm(const GroupDev& g, const StepArgs& a, const PriorC& pc, doub
                     cudaStream_t s) {
   using Gm = Geo<N>;
   if (int e = set_smem_limits<N>()) return e;
+  const int zc = pass3_slices_per_block(g.S, Gm::NB);
+  const int blocks = Gm::NB * ((g.S + zc - 1) / zc);
   if (pc.q_is_2 || MODE == 0)
-    k_pass3<N, MODE, true><<<g.S * Gm::NB, Gm::THREADS, Gm::SM3, s>>>(g, a, pc, partials, off);
+    k_pass3<N, MODE, true><<<blocks, Gm::THREADS, Geo3<N>::SM, s>>>(g, a, pc, partials, off, zc);
   else
-    k_pass3<N, MODE, false><<<g.S * Gm::NB, Gm::THREADS, Gm::SM3, s>>>(g, a, pc, partials, off);
+    k_pass3<N, MODE, false><<<blocks, Gm::THREADS, Geo3<N>::SM, s>>>(g, a, pc, partials, off, zc);
   TMBIR_CHECK_LAUNCH();
   return TMBIR_OK;
 }

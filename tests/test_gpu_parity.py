@@ -130,9 +130,13 @@ def test_reconstruct_follows_oracle_trajectory(prob, orc):
     ref = orc.nesterov(np.zeros(prob.x.shape), prob.atg, float(np.sum(prob.g ** 2)), prob.K, pr, L, iters, log=olog)
     got = host(x, prob.x.shape)
     assert rel(got, ref) < 1e-4
+    # F(y_k) is assembled from terms as large as F(0) = 1/2 g.g, accumulated from FP32
+    # products: compare on that scale
+    F0 = 0.5 * float(np.sum(prob.g ** 2))
+    assert abs(log[0][0] - F0) <= 1e-7 * F0
     for (F, dot, rs, gg), (Fo, doto, rso) in zip(log, olog):
-        assert abs(F - Fo) <= 1e-5 * abs(Fo)
-        if abs(doto) > 1e-3 * abs(F):
+        assert abs(F - Fo) <= 1e-7 * F0
+        if abs(doto) > 1e-4 * abs(gg) / L:
             assert bool(rs) == rso
 
 
