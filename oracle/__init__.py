@@ -27,6 +27,8 @@ What each function computes, with the passage of the paper it follows:
 * ``ramp_filter`` / ``fbp``: Eqs. 12-14, f0 = dtheta * A^T (h (*) g).
 * ``lanczos_up`` / ``downsample_sino``: Eqs. 16-17 and the projection subsampling
   of Sec. 2.3.
+* ``cnn_forward`` / ``cnn_backward``: the learned warm-start refiner (not in the paper;
+  four 3x3 convolutions 1 -> 32 -> 32 -> 32 -> 1 with ReLU), see ``cnn.c``.
 
 Parity unpinned: none of these; the pins live in ``tests/test_oracle_*.py``.
 """
@@ -92,9 +94,10 @@ def lib():
         L.orc_lanczos.argtypes = [d, i]
         L.orc_lanczos_up.argtypes = [dp, i, i, dp, dp]
         L.orc_downsample_sino.argtypes = [dp, i, i, i, i, dp]
-        if hasattr(L, "orc_cnn_forward"):
-            L.orc_cnn_forward.argtypes = [dp, i, i, i, dp, dp]
-            L.orc_cnn_backward.argtypes = [dp, i, i, i, dp, dp, dp, dp]
+        L.orc_cnn_param_count.restype = i
+        L.orc_cnn_param_count.argtypes = []
+        L.orc_cnn_forward.argtypes = [dp, i, i, i, dp, dp]
+        L.orc_cnn_backward.argtypes = [dp, i, i, i, dp, dp, dp, dp]
     return _lib
 
 
@@ -398,3 +401,43 @@ def downsample_sino(g, factor: int) -> np.ndarray:
     out = np.zeros((S, na, nd // factor))
     lib().orc_downsample_sino(_p(v), S, na, nd, factor, _p(out))
     return out[0] if g.ndim == 2 else out
+
+
+# ----------------------------------------------------------------------------- learned warm start
+
+
+def cnn_param_count() -> int:
+    return lib().orc_cnn_param_count()
+
+
+def cnn_forward(x, params) -> np.ndarray:
+    """net(x) for a batch (B, H, W) or one image (H, W)."""
+    x = _f64(x)
+    v = x.reshape((1,) + x.shape) if x.ndim == 2 else x
+    p = _f64(params)
+    assert p.size == cnn_param_count()
+    out = np.zeros_like(v)
+    lib().orc_cnn_forward(_p(v), v.shape[0], v.shape[1], v.shape[2], _p(p), _p(out))
+    return out.reshape(x.shape)
+
+
+def cnn_backward(x, params, gout):
+    """(d/dparams, d/dx) of sum(gout * net(x))."""
+    x = _f64(x)
+    v = x.reshape((1,) + x.shape) if x.ndim == 2 else x
+    p = _f64(params)
+    g = _f64(gout).reshape(v.shape)
+    gp = np.zeros_like(p)
+    gx = np.zeros_like(v)
+    lib().orc_cnn_backward(_p(v), v.shape[0], v.shape[1], v.shape[2], _p(p), _p(g), _p(gp), _p(gx))
+    return gp, gx.reshape(x.shape)
+
+
+def cnn_layer_slices():
+    """(weight slice, bias slice, cin, cout) of each layer in the flat parameter vector."""
+    out, off = [], 0
+    for cin, cout in ((1, 32), (32, 32), (32, 32), (32, 1)):
+        nw = cout * cin * 9
+        out.append((slice(off, off + nw), slice(off + nw, off + nw + cout), cin, cout))
+        off += nw + cout
+    return out

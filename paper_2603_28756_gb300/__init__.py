@@ -230,22 +230,49 @@ class Context:
         with torch.cuda.stream(self.stream):
             return torch.empty(n, dtype=torch.float32, device=self.device)
 
+    # stream ordering: the context stream is a PyTorch side stream (non-blocking), so every
+    # call first makes it wait for the caller's current stream (inputs written there) and
+    # afterwards makes the caller's stream wait for it (outputs read there); input tensors are
+    # marked as used on the context stream so the caching allocator does not recycle them early.
+    def _pre(self):
+        import torch
+
+        cur = torch.cuda.current_stream(self.device)
+        if cur != self.stream:
+            self.stream.wait_stream(cur)
+
+    def _post(self, *tensors):
+        import torch
+
+        cur = torch.cuda.current_stream(self.device)
+        if cur != self.stream:
+            cur.wait_stream(self.stream)
+            for t in tensors:
+                if t is not None:
+                    t.record_stream(self.stream)
+
     # calls --------------------------------------------------------------------
     def build_operator(self, sino, atg=None):
         atg = self._empty(self.image_numel()) if atg is None else atg
+        self._pre()
         _check(_lib.tmbir_build_operator(self._h, ctypes.c_void_p(_ptr(sino)), ctypes.c_void_p(_ptr(atg))))
+        self._post(sino, atg)
         return atg
 
     def fbp(self, sino, out=None):
         out = self._empty(self.image_numel()) if out is None else out
+        self._pre()
         _check(_lib.tmbir_fbp(self._h, ctypes.c_void_p(_ptr(sino)), ctypes.c_void_p(_ptr(out))))
+        self._post(sino, out)
         return out
 
     def reconstruct(self, x, atg, params: Params, want_stats: bool = True):
         st = _Stats()
         pr = params.c_struct()
+        self._pre()
         _check(_lib.tmbir_reconstruct(self._h, ctypes.c_void_p(_ptr(x)), ctypes.c_void_p(_ptr(atg)), ctypes.byref(pr),
                                       ctypes.byref(st) if want_stats else None))
+        self._post(x, atg)
         if not want_stats:
             return None
         return Stats(st.iterations, st.restarts, st.status, st.objective, st.gap, st.L, st.grad_norm)
@@ -258,30 +285,38 @@ class Context:
 
     def normal_apply(self, x, out=None):
         out = self._empty(x.numel()) if out is None else out
+        self._pre()
         _check(_lib.tmbir_normal_apply(self._h, ctypes.c_void_p(_ptr(x)), ctypes.c_void_p(_ptr(out))))
+        self._post(x, out)
         return out
 
     def gradient(self, x, atg, params: Params, out=None):
         out = self._empty(x.numel()) if out is None else out
         pr = params.c_struct()
+        self._pre()
         _check(_lib.tmbir_gradient(self._h, ctypes.c_void_p(_ptr(x)), ctypes.c_void_p(_ptr(atg)), ctypes.byref(pr),
                                    ctypes.c_void_p(_ptr(out))))
+        self._post(x, atg, out)
         return out
 
     def step(self, x, x_prev, beta, atg, params: Params, L, out=None):
         out = self._empty(x.numel()) if out is None else out
         pr = params.c_struct()
         parts = (ctypes.c_double * 5)()
+        self._pre()
         _check(_lib.tmbir_step(self._h, ctypes.c_void_p(_ptr(x)), ctypes.c_void_p(_ptr(x_prev)), float(beta),
                                ctypes.c_void_p(_ptr(atg)), ctypes.byref(pr), float(L), ctypes.c_void_p(_ptr(out)),
                                parts))
+        self._post(x, x_prev, atg, out)
         return out, list(parts)
 
     def objective(self, x, atg, params: Params) -> float:
         pr = params.c_struct()
         F = ctypes.c_double()
+        self._pre()
         _check(_lib.tmbir_objective(self._h, ctypes.c_void_p(_ptr(x)), ctypes.c_void_p(_ptr(atg)), ctypes.byref(pr),
                                     ctypes.byref(F)))
+        self._post(x, atg)
         return F.value
 
     def lambda_max(self):
@@ -295,27 +330,35 @@ class Context:
         N = self.groups[group].N
         with torch.cuda.stream(self.stream):
             K = torch.empty((2 * N - 1) * (2 * N - 1), dtype=torch.float64, device=self.device)
+        self._pre()
         _check(_lib.tmbir_kernel(self._h, group, ctypes.c_void_p(_ptr(K))))
+        self._post(K)
         return K
 
     def upsample_lanczos3(self, coarse, n_slices: int, Nc: int, out=None):
         out = self._empty(n_slices * 4 * Nc * Nc) if out is None else out
+        self._pre()
         _check(_lib.tmbir_upsample_lanczos3(self._h, ctypes.c_void_p(_ptr(coarse)), n_slices, Nc,
                                             ctypes.c_void_p(_ptr(out))))
+        self._post(coarse, out)
         return out
 
     def downsample_sino(self, sino, n_slices: int, n_angles: int, n_det: int, factor: int, out=None):
         out = self._empty(n_slices * n_angles * (n_det // factor)) if out is None else out
+        self._pre()
         _check(_lib.tmbir_downsample_sino(self._h, ctypes.c_void_p(_ptr(sino)), n_slices, n_angles, n_det, factor,
                                           ctypes.c_void_p(_ptr(out))))
+        self._post(sino, out)
         return out
 
     def pass_times(self, x, atg, params: Params, iters: int):
         """Summed device ms of (pass 1, pass 2, pass 3, finalize) over `iters` eager iterations."""
         pr = params.c_struct()
         out = (ctypes.c_double * 4)()
+        self._pre()
         _check(_lib.tmbir_pass_times(self._h, ctypes.c_void_p(_ptr(x)), ctypes.c_void_p(_ptr(atg)), ctypes.byref(pr),
                                      iters, out))
+        self._post(x, atg)
         return list(out)
 
     def launch_count(self) -> int:

@@ -33,6 +33,7 @@ PriorC make_prior(const tmbir_params& p) {
   c.wc = (float)(1.0 / std::sqrt(3.0) / total);
   c.q_is_2 = p.q == 2.0 ? 1 : 0;
   c.l2_inv_csig = (float)std::log2(1.0 / (p.c * p.sigma));
+  c.qp_l2_inv_csig = (float)((p.q - p.p) * std::log2(1.0 / (p.c * p.sigma)));
   c.l2_inv_sig = (float)std::log2(1.0 / p.sigma);
   return c;
 }
@@ -85,10 +86,6 @@ __global__ void k_scale_copy(const float* __restrict__ in, float* __restrict__ o
 }  // namespace tmbir
 
 using namespace tmbir;
-
-struct tmbir_ctx {
-  Ctx c;
-};
 
 static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
@@ -149,10 +146,11 @@ int tmbir_set_geometry(tmbir_ctx* ctx, int n_groups, const tmbir_group* groups) 
   c.ws_bytes = 0;
   c.operator_built = false;
   c.nufft_beta64 = 2.30 * 12;
-  c.nufft_beta32 = 2.30 * 7;
+  c.spread_beta = 2.30 * kSpreadW;
   c.psiK_h.assign(n_groups, {});
   c.psiA_h.assign(n_groups, {});
-  c.psiA32_h.assign(n_groups, {});
+  c.geom_ready.assign(n_groups, false);
+  c.spread_ready.assign(n_groups, false);
 
   // workspace layout
   size_t off = 0;
@@ -186,7 +184,9 @@ int tmbir_set_geometry(tmbir_ctx* ctx, int n_groups, const tmbir_group* groups) 
   c.off_K.resize(n_groups);
   c.off_psiK.resize(n_groups);
   c.off_psiA.resize(n_groups);
-  c.off_psiA32.resize(n_groups);
+  c.off_csr_ptr.resize(n_groups);
+  c.off_csr_idx.resize(n_groups);
+  c.off_csr_w.resize(n_groups);
   c.off_lam.resize(n_groups);
   c.off_gtg.resize(n_groups);
   for (int i = 0; i < n_groups; ++i) {
@@ -199,12 +199,13 @@ int tmbir_set_geometry(tmbir_ctx* ctx, int n_groups, const tmbir_group* groups) 
     c.off_K[i] = take((2 * N - 1) * (2 * N - 1) * sizeof(double));
     c.off_psiK[i] = take((2 * N - 1) * sizeof(double));
     c.off_psiA[i] = take(N * sizeof(double));
-    c.off_psiA32[i] = take(N * sizeof(double));
+    c.off_csr_ptr[i] = take((4 * N * N + 1) * sizeof(int));
+    c.off_csr_idx[i] = take(spread_nnz(gs[i]) * sizeof(int));
+    c.off_csr_w[i] = take(spread_nnz(gs[i]) * sizeof(double));
     c.off_lam[i] = take(sizeof(double));
     c.off_gtg[i] = take(sizeof(double));
     nufft_psi_table(2 * N - 1, 4 * N, 12, c.nufft_beta64, c.psiK_h[i]);
-    nufft_psi_table(N, 2 * N, 12, c.nufft_beta64, c.psiA_h[i]);
-    nufft_psi_table(N, 2 * N, 7, c.nufft_beta32, c.psiA32_h[i]);
+    nufft_psi_table(N, 2 * N, kSpreadW, c.spread_beta, c.psiA_h[i]);
   }
   c.off_xbuf0 = take(voxels * sizeof(float));
   c.off_xbuf1 = take(voxels * sizeof(float));
@@ -273,7 +274,9 @@ int tmbir_set_workspace(tmbir_ctx* ctx, void* d_ws, size_t bytes) {
     d.K = reinterpret_cast<double*>(ws + c.off_K[i]);
     d.psiK = reinterpret_cast<double*>(ws + c.off_psiK[i]);
     d.psiA = reinterpret_cast<double*>(ws + c.off_psiA[i]);
-    d.psiA32 = reinterpret_cast<double*>(ws + c.off_psiA32[i]);
+    d.csr_ptr = reinterpret_cast<int*>(ws + c.off_csr_ptr[i]);
+    d.csr_idx = reinterpret_cast<int*>(ws + c.off_csr_idx[i]);
+    d.csr_w = reinterpret_cast<double*>(ws + c.off_csr_w[i]);
     d.lam_max = reinterpret_cast<double*>(ws + c.off_lam[i]);
     d.gtg = reinterpret_cast<double*>(ws + c.off_gtg[i]);
     // twiddle tables: twN[k][t] = exp(-2 pi i t k / N) in the group-FFT layout, twM[n] = exp(-2 pi i n / 2N)
@@ -298,12 +301,13 @@ int tmbir_set_workspace(tmbir_ctx* ctx, void* d_ws, size_t bytes) {
                                c.stream));
     TMBIR_CUDA(cudaMemcpyAsync(d.psiA, c.psiA_h[i].data(), c.psiA_h[i].size() * sizeof(double), cudaMemcpyHostToDevice,
                                c.stream));
-    TMBIR_CUDA(cudaMemcpyAsync(d.psiA32, c.psiA32_h[i].data(), c.psiA32_h[i].size() * sizeof(double),
-                               cudaMemcpyHostToDevice, c.stream));
+
   }
   // pageable host sources: make sure the copies have consumed them before the vectors go away
   TMBIR_CUDA(cudaStreamSynchronize(c.stream));
   c.operator_built = false;
+  c.geom_ready.assign(c.groups.size(), false);
+  c.spread_ready.assign(c.groups.size(), false);
   return TMBIR_OK;
 }
 
@@ -329,10 +333,19 @@ int tmbir_build_operator(tmbir_ctx* ctx, const float* d_sino, float* d_atg) {
           "build_operator: sinogram and output must be non-NULL and 16-byte aligned");
   Ctx& c = ctx->c;
   for (size_t i = 0; i < c.groups.size(); ++i) {
-    if (int e = build_kernel_spectrum(c, (int)i)) return e;
+    // geometry-only parts: once per geometry and workspace binding
+    if (!c.spread_ready[i]) {
+      if (int e = build_spread_matrix(c, (int)i)) return e;
+      c.spread_ready[i] = true;
+    }
+    if (!c.geom_ready[i]) {
+      if (int e = build_kernel_spectrum(c, (int)i)) return e;
+      if (int e = power_iteration(c, (int)i, 100)) return e;
+      c.geom_ready[i] = true;
+    }
+    // data parts: every call
     if (int e = backproject(c, (int)i, d_sino, d_atg, false, true)) return e;
     if (int e = group_gtg(c, (int)i, d_sino)) return e;
-    if (int e = power_iteration(c, (int)i, 100)) return e;
   }
   c.operator_built = true;
   return TMBIR_OK;
@@ -343,8 +356,13 @@ int tmbir_fbp(tmbir_ctx* ctx, const float* d_sino, float* d_x0) {
   REQUIRE(d_sino && d_x0 && aligned16(d_sino) && aligned16(d_x0), TMBIR_ERR_ARG,
           "fbp: sinogram and output must be non-NULL and 16-byte aligned");
   Ctx& c = ctx->c;
-  for (size_t i = 0; i < c.groups.size(); ++i)
+  for (size_t i = 0; i < c.groups.size(); ++i) {
+    if (!c.spread_ready[i]) {
+      if (int e = build_spread_matrix(c, (int)i)) return e;
+      c.spread_ready[i] = true;
+    }
     if (int e = backproject(c, (int)i, d_sino, d_x0, true, false)) return e;
+  }
   return TMBIR_OK;
 }
 

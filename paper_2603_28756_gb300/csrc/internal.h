@@ -43,6 +43,7 @@ struct PriorC {
   float lam;             // lambda
   float wf, we, wc;      // face / edge / corner neighbour weights (sum of the 26 is 1)
   float l2_inv_csig;     // log2(1 / (c sigma))
+  float qp_l2_inv_csig;  // (q - p) log2(1 / (c sigma))
   float l2_inv_sig;      // log2(1 / sigma)
   int q_is_2;
 };
@@ -63,11 +64,17 @@ struct GroupDev {
   double* angles;      // [na]
   double* K;           // [(2N-1)^2] point-spread kernel
   double* psiK;        // [2N-1] deconvolution factors for K (fine grid 4N)
-  double* psiA;        // [N] deconvolution factors for R*g (fine grid 2N)
-  double* psiA32;      // [N] deconvolution factors for the FP32 back-projection
+  double* psiA;        // [N] deconvolution factors of the back-projection spreading (fine grid 2N)
   double* lam_max;     // device scalar
   double* gtg;         // device scalar (1/2 g.g of the group)
+  // sparse spreading onto the 2N x 2N grid (geometry only)
+  int* csr_ptr;        // [(2N)^2 + 1]
+  int* csr_idx;        // [nnz] strength index a * n_det + (k mod n_det)
+  double* csr_w;       // [nnz] kernel weight
 };
+
+constexpr int kSpreadW = 10;       // kernel width of the R*g / FBP spreading (error ~1e-9)
+constexpr int kBackprojBatch = 8;  // slices per back-projection batch
 
 struct Ctx {
   cudaStream_t stream = nullptr;
@@ -75,9 +82,10 @@ struct Ctx {
   std::vector<std::vector<double>> angles;
   std::vector<GroupDev> gdev;
   // host copies of the NUFFT deconvolution tables (uploaded at set_workspace)
-  std::vector<std::vector<double>> psiK_h, psiA_h, psiA32_h;
-  int nufft_w64 = 12, nufft_w32 = 7;
-  double nufft_beta64 = 0, nufft_beta32 = 0;
+  std::vector<std::vector<double>> psiK_h, psiA_h;
+  double nufft_beta64 = 0, spread_beta = 0;
+  std::vector<bool> geom_ready;    // K, its spectrum and lambda_max built
+  std::vector<bool> spread_ready;  // sparse spreading matrix built
   size_t total_voxels = 0, total_sino = 0;
   int total_slices = 0;
   // workspace
@@ -94,7 +102,8 @@ struct Ctx {
   bool operator_built = false;
   int last_iters = 0;
   // layout offsets computed at set_geometry
-  std::vector<size_t> off_chat, off_twN, off_twM, off_spec, off_ang, off_K, off_psiK, off_psiA, off_psiA32, off_lam, off_gtg;
+  std::vector<size_t> off_chat, off_twN, off_twM, off_spec, off_ang, off_K, off_psiK, off_psiA, off_lam, off_gtg,
+      off_csr_ptr, off_csr_idx, off_csr_w;
   size_t off_state = 0, off_partials = 0, off_log = 0, off_xbuf0 = 0, off_xbuf1 = 0, off_scratch = 0, off_dscal = 0;
   // CUDA graph cache for reconstruct
   cudaGraphExec_t graph_exec = nullptr;
@@ -158,6 +167,8 @@ void fft_shape(int N, int* T, int* P);
 int setup_tables(Ctx& c);  // enqueue uploads of twiddles / psi tables into the workspace
 int build_kernel_spectrum(Ctx& c, int gi);
 int backproject(Ctx& c, int gi, const float* d_sino, float* d_out, bool ramp, bool fp64);
+int build_spread_matrix(Ctx& c, int gi);
+size_t spread_nnz(const tmbir_group& g);
 int power_iteration(Ctx& c, int gi, int steps);
 int group_gtg(Ctx& c, int gi, const float* d_sino);
 void nufft_psi_table(int nmodes, int nfine, int w, double beta, std::vector<double>& out);
@@ -170,3 +181,8 @@ int launch_downsample_sino(const float* in, int S, int na, int nd, int f, float*
 PriorC make_prior(const tmbir_params& p);
 
 }  // namespace tmbir
+
+// the opaque handle of the C ABI
+struct tmbir_ctx {
+  tmbir::Ctx c;
+};

@@ -7,8 +7,9 @@
 // The type-1 transform spreads the samples onto a 2x oversampled periodic grid with the
 // "exponential of semicircle" kernel psi(u) = exp(beta (sqrt(1 - (2u/w)^2) - 1)) (Barnett,
 // Magland & af Klinteberg 2019), takes a 2D FFT and divides each output mode by the
-// kernel's Fourier transform.  Everything runs in FP64 for the operator (K, its spectrum and
-// R*g) and in FP32 for the FBP start.
+// kernel's Fourier transform.  K (width 12) and R*g (width 10) run in FP64, the FBP start in
+// FP32.  K is spread with fixed-point integer atomics and R*g / FBP through a sorted sparse
+// matrix, so every result is bit-reproducible.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -137,59 +138,191 @@ __device__ __forceinline__ double es_kernel(double z, double beta) {  // z in [-
   const double t = 1.0 - z * z;
   return t > 0.0 ? exp(beta * (sqrt(t) - 1.0)) : 0.0;
 }
-__device__ __forceinline__ float es_kernel(float z, float beta) {
-  const float t = 1.0f - z * z;
-  return t > 0.0f ? __expf(beta * (sqrtf(t) - 1.0f)) : 0.0f;
-}
-__device__ __forceinline__ void atomic_add_c(double2* p, double2 v) {
-  atomicAdd(&p->x, v.x);
-  atomicAdd(&p->y, v.y);
-}
-__device__ __forceinline__ void atomic_add_c(float2* p, float2 v) {
-  atomicAdd(&p->x, v.x);
-  atomicAdd(&p->y, v.y);
-}
-
-// One thread per polar sample (slice b, angle a, radial k).  strengths == nullptr spreads
-// the constant 1/n_det (the kernel K).  grid: [b][n_f][n_f] indexed [ly][lx].
-template <int W, class C>
-__global__ void k_spread(const double* __restrict__ angles, int na, int nd, int nf, int batch,
-                         const C* __restrict__ strengths, C* __restrict__ grid, real_t<C> beta) {
-  using S = real_t<C>;
-  const int npa = nd - 1;  // radial samples per angle
-  const size_t total = (size_t)batch * na * npa;
+// Spreading of the constant strength 1/n_det (the kernel K) with 64-bit fixed-point integer
+// atomics: integer addition is associative, so the grid is bit-identical run to run.  Every
+// cell sum is below 2 (at most ~2 n_det points of weight <= 1/n_det each reach one cell), so a
+// scale of 2^52 keeps ~1e-16 absolute resolution without overflow.
+constexpr double kFixScale = 4503599627370496.0;  // 2^52
+template <int W>
+__global__ void k_spread_fixed(const double* __restrict__ angles, int na, int nd, int nf,
+                               unsigned long long* __restrict__ grid, double beta) {
+  const int npa = nd - 1;
+  const size_t total = (size_t)na * npa;
   for (size_t id = blockIdx.x * (size_t)blockDim.x + threadIdx.x; id < total; id += (size_t)gridDim.x * blockDim.x) {
-    const int kk = (int)(id % npa);
-    const int a = (int)((id / npa) % na);
-    const int b = (int)(id / ((size_t)npa * na));
+    const int kk = (int)(id % npa), a = (int)(id / npa);
     const int k = kk - (nd / 2 - 1);
-    C c;
-    if (strengths) {
-      c = strengths[((size_t)b * na + a) * nd + (k < 0 ? k + nd : k)];
-    } else {
-      c = mkc((S)(1.0 / nd), (S)0);
-    }
     double sa, ca;
     sincos(angles[a], &sa, &ca);
     const double ux = (double)k * ca * nf / nd, uy = (double)k * sa * nf / nd;
     const int lx0 = (int)ceil(ux - 0.5 * W), ly0 = (int)ceil(uy - 0.5 * W);
-    S kx[W], ky[W];
+    double kx[W], ky[W];
 #pragma unroll
     for (int j = 0; j < W; ++j) {
-      kx[j] = es_kernel((S)((2.0 * (lx0 + j - ux)) / W), beta);
-      ky[j] = es_kernel((S)((2.0 * (ly0 + j - uy)) / W), beta);
+      kx[j] = es_kernel((2.0 * (lx0 + j - ux)) / W, beta);
+      ky[j] = es_kernel((2.0 * (ly0 + j - uy)) / W, beta);
     }
-    C* gb = grid + (size_t)b * nf * nf;
+    const double c = kFixScale / nd;
 #pragma unroll 1
     for (int jy = 0; jy < W; ++jy) {
       const int ly = (ly0 + jy + nf) % nf;
-      const C cy = mkc(c.x * ky[jy], c.y * ky[jy]);
 #pragma unroll
       for (int jx = 0; jx < W; ++jx) {
         const int lx = (lx0 + jx + nf) % nf;
-        atomic_add_c(&gb[(size_t)ly * nf + lx], mkc(cy.x * kx[jx], cy.y * kx[jx]));
+        atomicAdd(&grid[(size_t)ly * nf + lx], (unsigned long long)(long long)llrint(c * ky[jy] * kx[jx]));
       }
     }
+  }
+}
+__global__ void k_fixed_to_complex(const unsigned long long* __restrict__ in, double2* __restrict__ out, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    out[i] = make_double2((double)(long long)in[i] / kFixScale, 0.0);
+}
+
+// ---------------------------------------------------------------- sparse spreading operator
+// The polar sample positions depend on the geometry only, so the spreading onto the 2N x 2N
+// grid of R*g and of the FBP start is stored once as a sparse matrix in compressed rows, one
+// row per grid cell: the strength index a * n_det + (k mod n_det) of every contributing
+// sample and its kernel weight psi(x) psi(y).  Entries of a row are sorted by strength index,
+// so every later gather sums in a fixed order (deterministic) and needs no atomics.
+__global__ void k_csr_count(const double* __restrict__ angles, int na, int nd, int nf, int W, int* __restrict__ cnt) {
+  const int npa = nd - 1;
+  const size_t total = (size_t)na * npa;
+  for (size_t id = blockIdx.x * (size_t)blockDim.x + threadIdx.x; id < total; id += (size_t)gridDim.x * blockDim.x) {
+    const int kk = (int)(id % npa), a = (int)(id / npa);
+    const int k = kk - (nd / 2 - 1);
+    double sa, ca;
+    sincos(angles[a], &sa, &ca);
+    const double ux = (double)k * ca * nf / nd, uy = (double)k * sa * nf / nd;
+    const int lx0 = (int)ceil(ux - 0.5 * W), ly0 = (int)ceil(uy - 0.5 * W);
+    for (int jy = 0; jy < W; ++jy)
+      for (int jx = 0; jx < W; ++jx) {
+        const int ly = (ly0 + jy + nf) % nf, lx = (lx0 + jx + nf) % nf;
+        atomicAdd(&cnt[(size_t)ly * nf + lx + 1], 1);
+      }
+  }
+}
+__global__ void k_csr_fill(const double* __restrict__ angles, int na, int nd, int nf, int W, double beta,
+                           int* __restrict__ cursor, int* __restrict__ idx, double* __restrict__ wt) {
+  const int npa = nd - 1;
+  const size_t total = (size_t)na * npa;
+  for (size_t id = blockIdx.x * (size_t)blockDim.x + threadIdx.x; id < total; id += (size_t)gridDim.x * blockDim.x) {
+    const int kk = (int)(id % npa), a = (int)(id / npa);
+    const int k = kk - (nd / 2 - 1);
+    double sa, ca;
+    sincos(angles[a], &sa, &ca);
+    const double ux = (double)k * ca * nf / nd, uy = (double)k * sa * nf / nd;
+    const int lx0 = (int)ceil(ux - 0.5 * W), ly0 = (int)ceil(uy - 0.5 * W);
+    const int sidx = a * nd + (k < 0 ? k + nd : k);
+    for (int jy = 0; jy < W; ++jy) {
+      const double wy = es_kernel((2.0 * (ly0 + jy - uy)) / W, beta);
+      for (int jx = 0; jx < W; ++jx) {
+        const int ly = (ly0 + jy + nf) % nf, lx = (lx0 + jx + nf) % nf;
+        const int pos = atomicAdd(&cursor[(size_t)ly * nf + lx], 1);
+        idx[pos] = sidx;
+        wt[pos] = wy * es_kernel((2.0 * (lx0 + jx - ux)) / W, beta);
+      }
+    }
+  }
+}
+// insertion sort of each row by strength index (rows are short except near the centre)
+__global__ void k_csr_sort(const int* __restrict__ ptr, int ncells, int* __restrict__ idx, double* __restrict__ wt) {
+  for (int cell = blockIdx.x * blockDim.x + threadIdx.x; cell < ncells; cell += gridDim.x * blockDim.x) {
+    const int b = ptr[cell], e = ptr[cell + 1];
+    for (int i = b + 1; i < e; ++i) {
+      const int ki = idx[i];
+      const double wi = wt[i];
+      int j = i - 1;
+      while (j >= b && idx[j] > ki) {
+        idx[j + 1] = idx[j];
+        wt[j + 1] = wt[j];
+        --j;
+      }
+      idx[j + 1] = ki;
+      wt[j + 1] = wi;
+    }
+  }
+}
+// inclusive scan, three phases over tiles of 2048 ints
+__global__ void k_scan_tiles(int* __restrict__ a, int n, int* __restrict__ sums) {
+  __shared__ int sh[2048];
+  const int base = blockIdx.x * 2048;
+  for (int i = threadIdx.x; i < 2048; i += blockDim.x) sh[i] = base + i < n ? a[base + i] : 0;
+  __syncthreads();
+  for (int off = 1; off < 2048; off <<= 1) {
+    int v[8];
+    for (int r = 0; r < 8; ++r) {
+      const int i = threadIdx.x + r * 256;
+      v[r] = i >= off ? sh[i - off] : 0;
+    }
+    __syncthreads();
+    for (int r = 0; r < 8; ++r) sh[threadIdx.x + r * 256] += v[r];
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < 2048; i += blockDim.x)
+    if (base + i < n) a[base + i] = sh[i];
+  if (threadIdx.x == 0) sums[blockIdx.x] = sh[2047];
+}
+__global__ void k_scan_sums(int* sums, int nt) {
+  if (threadIdx.x == 0 && blockIdx.x == 0)
+    for (int i = 1; i < nt; ++i) sums[i] += sums[i - 1];
+}
+__global__ void k_scan_add(int* __restrict__ a, int n, const int* __restrict__ sums) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int t = i / 2048;
+    if (t > 0) a[i] += sums[t - 1];
+  }
+}
+// grid[b][cell] = sum_j wt[j] strengths[b][idx[j]], B slices per launch
+template <int B, class C>
+__global__ void k_csr_gather(const int* __restrict__ ptr, const int* __restrict__ idx, const double* __restrict__ wt,
+                             int ncells, const C* __restrict__ strengths, size_t sstride, C* __restrict__ grid, int nb) {
+  using S = real_t<C>;
+  for (int cell = blockIdx.x * blockDim.x + threadIdx.x; cell < ncells; cell += gridDim.x * blockDim.x) {
+    C acc[B];
+#pragma unroll
+    for (int b = 0; b < B; ++b) acc[b] = mkc((S)0, (S)0);
+    const int e = ptr[cell + 1];
+    for (int j = ptr[cell]; j < e; ++j) {
+      const int k = idx[j];
+      const S w = (S)wt[j];
+#pragma unroll
+      for (int b = 0; b < B; ++b)
+        if (b < nb) {
+          const C v = strengths[b * sstride + k];
+          acc[b].x = fmar(w, v.x, acc[b].x);
+          acc[b].y = fmar(w, v.y, acc[b].y);
+        }
+    }
+#pragma unroll
+    for (int b = 0; b < B; ++b)
+      if (b < nb) grid[(size_t)b * ncells + cell] = acc[b];
+  }
+}
+// tmp[b][j][r] = grid[b][r][(j - N/2) mod nf] for the N kept x-modes j (column pruning)
+template <class C>
+__global__ void k_transpose_prune(const C* __restrict__ in, C* __restrict__ out, int nf, int N) {
+  __shared__ C tile[32][33];
+  const size_t ib = (size_t)blockIdx.z * nf * nf, ob = (size_t)blockIdx.z * N * nf;
+  const int j0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int r = r0 + i, j = j0 + threadIdx.x;
+    if (r < nf && j < N) tile[i][threadIdx.x] = in[ib + (size_t)r * nf + ((j - N / 2 + nf) % nf)];
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int j = j0 + i, r = r0 + threadIdx.x;
+    if (r < nf && j < N) out[ob + (size_t)j * nf + r] = tile[threadIdx.x][i];
+  }
+}
+// out[b][r][c] = scale * Re tmp[b][c][(r - N/2) mod nf] / (psi[c] psi[r])
+template <class C>
+__global__ void k_deconv_pruned(const C* __restrict__ B, int nf, int N, int nb, const double* __restrict__ psi,
+                                float scale, float* __restrict__ out) {
+  const size_t total = (size_t)nb * N * N;
+  for (size_t id = blockIdx.x * (size_t)blockDim.x + threadIdx.x; id < total; id += (size_t)gridDim.x * blockDim.x) {
+    const int c = (int)(id % N), r = (int)((id / N) % N), b = (int)(id / ((size_t)N * N));
+    const C v = B[(size_t)b * N * nf + (size_t)c * nf + (r - N / 2 + nf) % nf];
+    out[id] = (float)(scale * ((double)v.x / (psi[c] * psi[r])));
   }
 }
 
@@ -201,19 +334,6 @@ __global__ void k_deconv_K(const double2* __restrict__ B, int nf, int N, const d
     const int dx = ix - (N - 1), dy = iy - (N - 1);
     const double2 v = B[(size_t)((dx + nf) % nf) * nf + (dy + nf) % nf];
     K[id] = v.x / (psi[ix] * psi[iy]);
-  }
-}
-
-// out[b][r][c] = scale * Re B[b][kx = c - N/2][ky = r - N/2] / (psi psi)
-template <class C>
-__global__ void k_deconv_img(const C* __restrict__ B, int nf, int N, int batch, const double* __restrict__ psi,
-                             float scale, float* __restrict__ out) {
-  const size_t total = (size_t)batch * N * N;
-  for (size_t id = blockIdx.x * (size_t)blockDim.x + threadIdx.x; id < total; id += (size_t)gridDim.x * blockDim.x) {
-    const int c = (int)(id % N), r = (int)((id / N) % N), b = (int)(id / ((size_t)N * N));
-    const int dx = c - N / 2, dy = r - N / 2;
-    const C v = B[(size_t)b * nf * nf + (size_t)((dx + nf) % nf) * nf + (dy + nf) % nf];
-    out[id] = (float)(scale * ((double)v.x / (psi[c] * psi[r])));
   }
 }
 
@@ -383,19 +503,12 @@ size_t setup_scratch_bytes(const tmbir_group& g) {
   const size_t N = g.N, nf_k = 4 * N, nf_a = 2 * N;
   const size_t k_elems = nf_k + 2 * nf_k * nf_k;
   const size_t rows = (size_t)g.n_angles * g.n_det;
-  const size_t a_elems = nf_a + rows + 2 * nf_a * nf_a;
-  return std::max(k_elems, a_elems) * sizeof(double2) + 256;
+  const size_t B = std::min(g.n_slices, kBackprojBatch);
+  const size_t a_elems = nf_a + B * rows + B * nf_a * nf_a + B * N * nf_a;
+  const size_t csr_build = (nf_a * nf_a + 2 * ((nf_a * nf_a + 2048) / 2048 + 1)) * sizeof(int);
+  return std::max(std::max(k_elems, a_elems) * sizeof(double2), csr_build) + 256;
 }
-
-template <int Wd, class C>
-static int spread(const double* angles, int na, int nd, int nf, int batch, const C* strengths, C* grid, double beta,
-                  cudaStream_t s) {
-  const size_t total = (size_t)batch * na * (nd - 1);
-  const int blocks = (int)std::min<size_t>((total + 255) / 256, 152 * 16);
-  k_spread<Wd, C><<<blocks, 256, 0, s>>>(angles, na, nd, nf, batch, strengths, grid, (real_t<C>)beta);
-  TMBIR_CHECK_LAUNCH();
-  return TMBIR_OK;
-}
+size_t spread_nnz(const tmbir_group& g) { return (size_t)g.n_angles * (g.n_det - 1) * kSpreadW * kSpreadW; }
 
 // device twiddle tables for the setup FFTs (n up to 4N), carved from the front of the scratch
 template <class C>
@@ -417,8 +530,16 @@ int build_kernel_spectrum(Ctx& c, int gi) {
   double2* tmp = grid + (size_t)nf * nf;
   k_twiddle<double2><<<(nf + 255) / 256, 256, 0, s>>>(tw, nf);
   TMBIR_CHECK_LAUNCH();
-  TMBIR_CUDA(cudaMemsetAsync(grid, 0, sizeof(double2) * nf * nf, s));
-  if (int e = spread<12, double2>(g.angles, g.na, g.nd, nf, 1, nullptr, grid, c.nufft_beta64, s)) return e;
+  unsigned long long* fixed_grid = reinterpret_cast<unsigned long long*>(tmp);
+  TMBIR_CUDA(cudaMemsetAsync(fixed_grid, 0, sizeof(unsigned long long) * nf * nf, s));
+  {
+    const size_t total = (size_t)g.na * (g.nd - 1);
+    const int blocks = (int)std::min<size_t>((total + 255) / 256, 152 * 16);
+    k_spread_fixed<12><<<blocks, 256, 0, s>>>(g.angles, g.na, g.nd, nf, fixed_grid, c.nufft_beta64);
+    TMBIR_CHECK_LAUNCH();
+  }
+  k_fixed_to_complex<<<1024, 256, 0, s>>>(fixed_grid, grid, (size_t)nf * nf);
+  TMBIR_CHECK_LAUNCH();
   if (int e = fft2_transposed(grid, tmp, nf, 1, +1, tw, s)) return e;
   k_deconv_K<<<1024, 256, 0, s>>>(tmp, nf, N, g.psiK, g.K);
   TMBIR_CHECK_LAUNCH();
@@ -435,38 +556,69 @@ int build_kernel_spectrum(Ctx& c, int gi) {
   return TMBIR_OK;
 }
 
-template <class C>
-static int backproject_t(Ctx& c, int gi, const float* d_sino, float* d_out, bool ramp, float scale, int wsel) {
+int build_spread_matrix(Ctx& c, int gi) {
   GroupDev& g = c.gdev[gi];
   cudaStream_t s = c.stream;
-  const int N = g.N, nf = 2 * N, nd = g.nd, na = g.na;
+  const int nf = 2 * g.N, ncells = nf * nf;
+  const size_t total = (size_t)g.na * (g.nd - 1);
+  const int blocks = (int)std::min<size_t>((total + 255) / 256, 152 * 16);
+  int* cursor = reinterpret_cast<int*>(c.scratch);
+  int* sums = cursor + ncells;
+  TMBIR_CUDA(cudaMemsetAsync(g.csr_ptr, 0, sizeof(int) * (ncells + 1), s));
+  k_csr_count<<<blocks, 256, 0, s>>>(g.angles, g.na, g.nd, nf, kSpreadW, g.csr_ptr);
+  TMBIR_CHECK_LAUNCH();
+  const int ntiles = (ncells + 1 + 2047) / 2048;
+  k_scan_tiles<<<ntiles, 256, 0, s>>>(g.csr_ptr, ncells + 1, sums);
+  TMBIR_CHECK_LAUNCH();
+  k_scan_sums<<<1, 32, 0, s>>>(sums, ntiles);
+  TMBIR_CHECK_LAUNCH();
+  k_scan_add<<<1024, 256, 0, s>>>(g.csr_ptr, ncells + 1, sums);
+  TMBIR_CHECK_LAUNCH();
+  TMBIR_CUDA(cudaMemcpyAsync(cursor, g.csr_ptr, sizeof(int) * ncells, cudaMemcpyDeviceToDevice, s));
+  k_csr_fill<<<blocks, 256, 0, s>>>(g.angles, g.na, g.nd, nf, kSpreadW, c.spread_beta, cursor, g.csr_idx, g.csr_w);
+  TMBIR_CHECK_LAUNCH();
+  k_csr_sort<<<(ncells + 255) / 256, 256, 0, s>>>(g.csr_ptr, ncells, g.csr_idx, g.csr_w);
+  TMBIR_CHECK_LAUNCH();
+  return TMBIR_OK;
+}
+
+template <class C>
+static int backproject_t(Ctx& c, int gi, const float* d_sino, float* d_out, bool ramp, float scale) {
+  GroupDev& g = c.gdev[gi];
+  cudaStream_t s = c.stream;
+  const int N = g.N, nf = 2 * N, nd = g.nd, na = g.na, ncells = nf * nf;
   const size_t rows = (size_t)na * nd;
+  const int B = std::min(g.S, kBackprojBatch);
   C* tw = reinterpret_cast<C*>(c.scratch);
   C* strengths = tw + nf;
-  C* grid = strengths + rows;
-  C* tmp = grid + (size_t)nf * nf;
-  const double* psi = std::is_same<C, double2>::value ? g.psiA : g.psiA32;
-  for (int b = 0; b < g.S; ++b) {
-    const float* sino_b = d_sino + g.sino_off + (size_t)b * na * nd;
+  C* grid = strengths + (size_t)B * rows;
+  C* tmp = grid + (size_t)B * ncells;
+  for (int b0 = 0; b0 < g.S; b0 += B) {
+    const int nb = std::min(B, g.S - b0);
+    const float* sino_b = d_sino + g.sino_off + (size_t)b0 * rows;
     // radial 1D transform of every projection: G(a, k)
-    k_prepare_rows<C><<<std::min<size_t>(na, 4096), 256, 2 * nd * sizeof(float), s>>>(sino_b, nd, na, ramp ? 1 : 0, strengths);
+    k_prepare_rows<C><<<(int)std::min<size_t>((size_t)nb * na, 4096), 256, 2 * nd * sizeof(float), s>>>(
+        sino_b, nd, (size_t)nb * na, ramp ? 1 : 0, strengths);
     TMBIR_CHECK_LAUNCH();
     k_twiddle<C><<<(nd + 255) / 256, 256, 0, s>>>(tw, nd);
     TMBIR_CHECK_LAUNCH();
-    if (int e = fft_rows(strengths, nd, na, +1, tw, s)) return e;
-    k_strength_fix<C><<<1024, 256, 0, s>>>(strengths, nd, rows);
+    if (int e = fft_rows(strengths, nd, nb * na, +1, tw, s)) return e;
+    k_strength_fix<C><<<1024, 256, 0, s>>>(strengths, nd, (size_t)nb * rows);
     TMBIR_CHECK_LAUNCH();
-    TMBIR_CUDA(cudaMemsetAsync(grid, 0, sizeof(C) * nf * nf, s));
-    int e = 0;
-    if (wsel == 12)
-      e = spread<12, C>(g.angles, na, nd, nf, 1, strengths, grid, c.nufft_beta64, s);
-    else
-      e = spread<7, C>(g.angles, na, nd, nf, 1, strengths, grid, c.nufft_beta32, s);
-    if (e) return e;
+    k_csr_gather<kBackprojBatch, C><<<(ncells + 255) / 256, 256, 0, s>>>(g.csr_ptr, g.csr_idx, g.csr_w, ncells,
+                                                                          strengths, rows, grid, nb);
+    TMBIR_CHECK_LAUNCH();
     k_twiddle<C><<<(nf + 255) / 256, 256, 0, s>>>(tw, nf);
     TMBIR_CHECK_LAUNCH();
-    if (int e2 = fft2_transposed(grid, tmp, nf, 1, -1, tw, s)) return e2;
-    k_deconv_img<C><<<1024, 256, 0, s>>>(tmp, nf, N, 1, psi, scale, d_out + g.img_off + (size_t)b * N * N);
+    // 2D transform with the output pruned to the N x N image modes
+    if (int e = fft_rows(grid, nf, nb * nf, -1, tw, s)) return e;
+    {
+      dim3 gr((N + 31) / 32, (nf + 31) / 32, nb), bl(32, 8);
+      k_transpose_prune<C><<<gr, bl, 0, s>>>(grid, tmp, nf, N);
+      TMBIR_CHECK_LAUNCH();
+    }
+    if (int e = fft_rows(tmp, nf, nb * N, -1, tw, s)) return e;
+    k_deconv_pruned<C><<<1024, 256, 0, s>>>(tmp, nf, N, nb, g.psiA, scale, d_out + g.img_off + (size_t)b0 * N * N);
     TMBIR_CHECK_LAUNCH();
   }
   return TMBIR_OK;
@@ -475,8 +627,8 @@ static int backproject_t(Ctx& c, int gi, const float* d_sino, float* d_out, bool
 int backproject(Ctx& c, int gi, const float* d_sino, float* d_out, bool ramp, bool fp64) {
   const GroupDev& g = c.gdev[gi];
   const float scale = ramp ? (float)(g.span / g.na) : 1.0f;
-  if (fp64) return backproject_t<double2>(c, gi, d_sino, d_out, ramp, scale, 12);
-  return backproject_t<float2>(c, gi, d_sino, d_out, ramp, scale, 7);
+  if (fp64) return backproject_t<double2>(c, gi, d_sino, d_out, ramp, scale);
+  return backproject_t<float2>(c, gi, d_sino, d_out, ramp, scale);
 }
 
 int group_gtg(Ctx& c, int gi, const float* d_sino) {

@@ -73,20 +73,23 @@ __device__ __forceinline__ float rcp_newton(float x) {
 // rho'(d) (and rho(d) when PHI) of the qGGMRF potential
 //   rho(d)  = |d/sigma|^q / (1 + u),            u = |d/(c sigma)|^(q-p)
 //   rho'(d) = d/sigma^2 |d/sigma|^(q-2) (q + p u) / (1 + u)^2
-// Two special-function operations (log2 and exp2) per call; the reciprocal runs on the FMA pipe.
+// Returns rho'(d) * sigma^2 (the caller folds 1/sigma^2 into the neighbour weight) and, when
+// PHI, rho(d) * sigma^2.  Three special-function operations per call (log2, exp2, reciprocal).
 template <bool Q2, bool PHI>
 __device__ __forceinline__ float drho(float d, const PriorC& c, float& rho) {
   const float a = fmaxf(fabsf(d), 1e-30f);
   const float la = lg2a(a);
-  const float u = ex2a(fmaf(c.qp, la, c.qp * c.l2_inv_csig));
-  const float r = rcp_newton(1.0f + u);
+  const float u = ex2a(fmaf(c.qp, la, c.qp_l2_inv_csig));
+  const float r = rcpa(1.0f + u);
   if constexpr (Q2) {
-    if constexpr (PHI) rho = d * d * c.inv_sig2 * r;
-    return d * c.inv_sig2 * fmaf(c.p, u, 2.0f) * r * r;
+    const float dr = d * r;
+    if constexpr (PHI) rho = d * dr;
+    return dr * r * fmaf(c.p, u, 2.0f);
   } else {
     const float aq2 = ex2a((c.q - 2.0f) * (la + c.l2_inv_sig));
-    if constexpr (PHI) rho = aq2 * d * d * c.inv_sig2 * r;
-    return d * c.inv_sig2 * aq2 * fmaf(c.p, u, c.q) * r * r;
+    const float dr = d * r * aq2;
+    if constexpr (PHI) rho = d * dr;
+    return dr * r * fmaf(c.p, u, c.q);
   }
 }
 
@@ -244,41 +247,33 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) k_pass2(GroupDev g, const Ite
 }
 
 // ---------------------------------------------------------------- pass 3: rows, inverse + gradient
-// A block owns RB consecutive rows of one group and marches through a chunk of its slices.
-// Per slice: the inverse row transforms give K (*) y for the block's rows; then the qGGMRF
-// gradient is accumulated pair by pair.  For the neighbourhood, thread t owns a band of RS
-// rows and KCH chunks of CHW columns.  A neighbour pair whose two voxels the same thread owns
-// (in the same slice, or in consecutive slices of the block's chunk) is evaluated once and
-// applied to both voxels -- the next-slice half is carried in registers to the next step;
-// every other pair is evaluated from each side for that side only.  Each unordered pair
-// enters Phi once, from the voxel it is a forward offset of (lexicographic in dz, dy, dx).
+// A block owns RB consecutive rows of one group and marches through a chunk of its slices,
+// keeping y for slices z-1, z, z+1 (rows -1 .. RB) in a three-slot ring so every slice of y is
+// read from memory once per chunk.  Per slice: the inverse row transforms give K (*) y for
+// the block's rows; then each thread walks its voxels (consecutive threads on consecutive
+// columns) and sums rho' over the 26 neighbours.  The voxel loop is a plain runtime loop so
+// the unrolled neighbourhood stays small enough for the instruction cache.  Each unordered
+// neighbour pair enters Phi once, from the voxel it is a forward offset of.
 template <int N>
 struct Geo3 {
   using Gm = Geo<N>;
   static constexpr int RB = Gm::RB, THREADS = Gm::THREADS;
-  static constexpr int RS = 4;                      // rows per band
-  static constexpr int NBAND = RB / RS;
-  static constexpr int NSTRIP = THREADS / NBAND;    // column strips per band
-  static constexpr int CW = N / NSTRIP;             // columns per thread
-  static constexpr int CHW = CW < 4 ? CW : 4;       // columns per chunk
-  static constexpr int KCH = CW / CHW;              // chunks per thread
-  static constexpr int ROWS = RB + 2;               // ring rows (one halo row each side)
-  static constexpr size_t SM_RING = (size_t)2 * ROWS * N * sizeof(float);
+  static constexpr int ROWS = RB + 2;  // ring rows (one halo row each side)
+  static constexpr size_t SM_RING = (size_t)3 * ROWS * N * sizeof(float);
   static constexpr size_t SM_A = Gm::cmax(Gm::SM1, (size_t)RB * N * sizeof(float));
   static constexpr size_t SM = SM_A + SM_RING;
-  static_assert(NBAND * RS == RB && NSTRIP * NBAND == THREADS && KCH * CHW * NSTRIP == N, "stencil layout");
 };
 
 // y = x + beta (x - x_prev) for block rows -1 .. RB of one slice into a ring slot (zero outside)
 template <int N>
 __device__ __forceinline__ void load_ring(float* slot, const float* x, const float* xp, float beta, size_t off_slice,
-                                          int r0, bool valid_slice) {
+                                          int r0) {
   using G3 = Geo3<N>;
   for (int e = threadIdx.x; e < G3::ROWS * (N / 4); e += G3::THREADS) {
     const int c4 = e % (N / 4), rowi = e / (N / 4);
     const int rr = r0 - 1 + rowi;
     float4 yv = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (valid_slice && rr >= 0 && rr < N) {
+    if (rr >= 0 && rr < N) {
       const size_t off = off_slice + (size_t)rr * N;
       const float4 xv = __ldg(reinterpret_cast<const float4*>(x + off) + c4);
       const float4 pv = __ldg(reinterpret_cast<const float4*>(xp + off) + c4);
@@ -295,8 +290,7 @@ __global__ void __launch_bounds__(Geo<N>::THREADS)
   using Gm = Geo<N>;
   using G3 = Geo3<N>;
   using F = typename Gm::F;
-  constexpr int T = Gm::T, P = Gm::P, G = Gm::G, RB = Gm::RB, LD = Gm::LD;
-  constexpr int RS = G3::RS, CHW = G3::CHW, KCH = G3::KCH, NSTRIP = G3::NSTRIP, ROWS = G3::ROWS;
+  constexpr int T = Gm::T, P = Gm::P, G = Gm::G, RB = Gm::RB, LD = Gm::LD, ROWS = G3::ROWS;
   constexpr bool PRIOR = MODE != (int)Pass3Mode::Apply;
   constexpr bool PHI = MODE == (int)Pass3Mode::Step || MODE == (int)Pass3Mode::Iterate ||
                        MODE == (int)Pass3Mode::Objective;
@@ -326,30 +320,21 @@ __global__ void __launch_bounds__(Geo<N>::THREADS)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, grp = lane / T, t = lane % T;
   const int rl = warp * G + grp;
   const int r0 = rb * RB;
-  // stencil ownership
-  const int band = threadIdx.x / NSTRIP, strip = threadIdx.x % NSTRIP;
-  const int brow0 = band * RS;  // first block row of the band
   float2* tb = sm;
   float* kzs = reinterpret_cast<float*>(sm);  // K(*)y of the block rows, [RB][N], after the transforms
   float* ring = reinterpret_cast<float*>(reinterpret_cast<char*>(sm) + G3::SM_A);
   const size_t N2 = (size_t)N * N;
+  // neighbour weights with 1/sigma^2 folded in: drho returns sigma^2 rho' and sigma^2 rho
+  const float wts[4] = {0.f, pc.wf * pc.inv_sig2, pc.we * pc.inv_sig2, pc.wc * pc.inv_sig2};
 
   double dacc[kParts];
 #pragma unroll
   for (int j = 0; j < kParts; ++j) dacc[j] = 0.0;
-  float own[RS][KCH * CHW], nxt[RS][KCH * CHW];
-#pragma unroll
-  for (int i = 0; i < RS; ++i)
-#pragma unroll
-    for (int j = 0; j < KCH * CHW; ++j) own[i][j] = nxt[i][j] = 0.f;
 
   if constexpr (PRIOR) {
-    load_ring<N>(ring + (z0 & 1) * ROWS * N, x, xp, beta, g.img_off + (size_t)z0 * N2, r0, true);
-    if (z0 > 0) load_ring<N>(ring + ((z0 - 1) & 1) * ROWS * N, x, xp, beta, g.img_off + (size_t)(z0 - 1) * N2, r0, true);
+    load_ring<N>(ring + (z0 % 3) * ROWS * N, x, xp, beta, g.img_off + (size_t)z0 * N2, r0);
+    if (z0 > 0) load_ring<N>(ring + ((z0 + 2) % 3) * ROWS * N, x, xp, beta, g.img_off + (size_t)(z0 - 1) * N2, r0);
   }
-  const float wts[4] = {0.f, pc.wf, pc.we, pc.wc};
-  const float mL = (strip == 0) ? 0.f : 1.f;           // chunk 0's left halo column exists
-  const float mR = (strip == NSTRIP - 1) ? 0.f : 1.f;  // last chunk's right halo column exists
 
   for (int z = z0; z < z1; ++z) {
     const size_t slice_base = g.img_off + (size_t)z * N2;
@@ -361,6 +346,9 @@ __global__ void __launch_bounds__(Geo<N>::THREADS)
         const int vv = e / RB, rr = e - vv * RB;
         tb[rr * LD + vv] = sp[(size_t)vv * N + rr];
       }
+    }
+    if constexpr (PRIOR) {
+      if (z + 1 < g.S) load_ring<N>(ring + ((z + 1) % 3) * ROWS * N, x, xp, beta, slice_base + N2, r0);
     }
     __syncthreads();
     float2 q[P];
@@ -381,191 +369,75 @@ __global__ void __launch_bounds__(Geo<N>::THREADS)
       constexpr int i = decltype(i_)::value;
       reinterpret_cast<float2*>(kzs + rl * N)[t + T * i] = q[i];
     });
+    __syncthreads();
 
-    float yo[RS][KCH * CHW];  // own y values of slice z
+    // ---- per voxel: prior, gradient, update, partial sums
+    const float* sz[3] = {ring + ((z + 2) % 3) * ROWS * N, ring + (z % 3) * ROWS * N, ring + ((z + 1) % 3) * ROWS * N};
+    const bool zval0 = z > 0, zval2 = z + 1 < g.S;
     float acc[kParts];
 #pragma unroll
     for (int j = 0; j < kParts; ++j) acc[j] = 0.f;
-
-    if constexpr (PRIOR) {
-      const float* slot_z = ring + (z & 1) * ROWS * N;
-      SFor<0, RS>::run([&](auto i_) {
-        constexpr int i = decltype(i_)::value;
-        SFor<0, KCH>::run([&](auto k_) {
-          constexpr int k = decltype(k_)::value;
-          const int col0 = CHW * (strip + NSTRIP * k);
-          SFor<0, CHW>::run([&](auto c_) {
-            constexpr int ci = decltype(c_)::value;
-            yo[i][k * CHW + ci] = slot_z[(brow0 + i + 1) * N + col0 + ci];
-          });
-        });
-      });
-      // pair evaluation against one partner row (slice z + DZ, band row PR), for every own row
-      // within one row of it.  SHARED: the partner slice is processed by this block (both ends
-      // owned by one thread are then updated here, or were already, see below).
-      auto pairs = [&](auto dz_, auto pr_, const float* slot, bool shared_z) {
-        constexpr int DZ = decltype(dz_)::value, PR = decltype(pr_)::value;
-        float pv[KCH][CHW + 2];
-        const int prow = brow0 + PR;  // partner block row
-        SFor<0, KCH>::run([&](auto k_) {
-          constexpr int k = decltype(k_)::value;
-          const int col0 = CHW * (strip + NSTRIP * k);
-          const float* rp = slot + (prow + 1) * N;
-          SFor<0, CHW>::run([&](auto c_) {
-            constexpr int ci = decltype(c_)::value;
-            pv[k][ci + 1] = rp[col0 + ci];
-          });
-          pv[k][0] = rp[col0 > 0 ? col0 - 1 : 0];
-          pv[k][CHW + 1] = rp[col0 + CHW < N ? col0 + CHW : N - 1];
-        });
-        SFor<0, RS>::run([&](auto i_) {
-          constexpr int RR = decltype(i_)::value;
-          constexpr int DY = PR - RR;
-          if constexpr (DY >= -1 && DY <= 1) {
-            SFor<0, KCH>::run([&](auto k_) {
-              constexpr int k = decltype(k_)::value;
-              SFor<0, CHW>::run([&](auto c_) {
-                constexpr int ci = decltype(c_)::value;
-                SFor<0, 3>::run([&](auto d_) {
-                  constexpr int DX = decltype(d_)::value - 1;
-                  if constexpr (!(DZ == 0 && DY == 0 && DX == 0)) {
-                    constexpr bool owned = PR >= 0 && PR < RS && ci + DX >= 0 && ci + DX < CHW;
-                    constexpr bool fwd = DZ > 0 || (DZ == 0 && (DY > 0 || (DY == 0 && DX > 0)));
-                    constexpr int ring_n = (DZ != 0) + (DY != 0) + (DX != 0);
-                    // 0: skip, 1: both ends (same slice), 2: own end (+ next-slice end if shared)
-                    constexpr int kind = DZ == 0 ? (owned ? (fwd ? 1 : 0) : 2) : (DZ > 0 ? 2 : (owned ? 3 : 2));
-                    if constexpr (kind != 0) {
-                      // kind 3: owned partner in slice z-1, evaluated at step z-1 unless z is the chunk start
-                      if (kind != 3 || !shared_z) {
-                        float m = 1.f;
-                        if constexpr (ci + DX < 0) m = (k == 0) ? mL : 1.f;
-                        if constexpr (ci + DX >= CHW) m = (k == KCH - 1) ? mR : 1.f;
-                        const float w = wts[ring_n];
-                        float rh = 0.f;
-                        const float f = w * drho<Q2, PHI>(yo[RR][k * CHW + ci] - pv[k][ci + DX + 1], pc, rh);
-                        if constexpr (kind == 1) {
-                          own[RR][k * CHW + ci] += f;
-                          own[PR][k * CHW + ci + DX] -= f;
-                          if constexpr (PHI) acc[2] += w * rh;
-                        } else {
-                          own[RR][k * CHW + ci] += m * f;
-                          if constexpr (PHI && fwd) acc[2] += m * w * rh;
-                          if constexpr (DZ > 0 && owned) {
-                            if (shared_z) nxt[PR][k * CHW + ci + DX] -= f;
-                          }
-                        }
-                      }
-                    }
-                  }
-                });
-              });
-            });
-          }
-        });
-      };
-      const bool row_lo = r0 + brow0 - 1 >= 0, row_hi = r0 + brow0 + RS < N;
-      // slice z - 1 (own end only, except owned pairs at the chunk start)
-      if (z > 0) {
-        const float* slot_m = ring + ((z - 1) & 1) * ROWS * N;
-        const bool shared_m = z - 1 >= z0;
-        if (row_lo) pairs(std::integral_constant<int, -1>{}, std::integral_constant<int, -1>{}, slot_m, shared_m);
-        SFor<0, RS>::run([&](auto p_) { pairs(std::integral_constant<int, -1>{}, p_, slot_m, shared_m); });
-        if (row_hi) pairs(std::integral_constant<int, -1>{}, std::integral_constant<int, RS>{}, slot_m, shared_m);
-      }
-      __syncthreads();  // kzs complete; slot of z - 1 free
-      if (z + 1 < g.S)
-        load_ring<N>(ring + ((z + 1) & 1) * ROWS * N, x, xp, beta, slice_base + N2, r0, true);
-      __syncthreads();
-      // slice z
-      if (row_lo) pairs(std::integral_constant<int, 0>{}, std::integral_constant<int, -1>{}, slot_z, true);
-      SFor<0, RS>::run([&](auto p_) { pairs(std::integral_constant<int, 0>{}, p_, slot_z, true); });
-      if (row_hi) pairs(std::integral_constant<int, 0>{}, std::integral_constant<int, RS>{}, slot_z, true);
-      // slice z + 1
-      if (z + 1 < g.S) {
-        const float* slot_p = ring + ((z + 1) & 1) * ROWS * N;
-        const bool shared_p = z + 1 < z1;
-        if (row_lo) pairs(std::integral_constant<int, 1>{}, std::integral_constant<int, -1>{}, slot_p, shared_p);
-        SFor<0, RS>::run([&](auto p_) { pairs(std::integral_constant<int, 1>{}, p_, slot_p, shared_p); });
-        if (row_hi) pairs(std::integral_constant<int, 1>{}, std::integral_constant<int, RS>{}, slot_p, shared_p);
-      }
-    } else {
-      __syncthreads();
-    }
-
-    // ---- per voxel: gradient, update, partial sums (CHW consecutive columns at a time)
-    SFor<0, RS>::run([&](auto i_) {
-      constexpr int i = decltype(i_)::value;
-      const int row = r0 + brow0 + i;
-      const size_t rbase = slice_base + (size_t)row * N;
-      SFor<0, KCH>::run([&](auto k_) {
-        constexpr int k = decltype(k_)::value;
-        const int col0 = CHW * (strip + NSTRIP * k);
-        float zd[CHW], at[CHW], xv[CHW], res[CHW];
-        (void)res;
-        SFor<0, CHW>::run([&](auto c_) {
-          constexpr int ci = decltype(c_)::value;
-          zd[ci] = kzs[(brow0 + i) * N + col0 + ci];
-        });
-        const bool need_x = !PRIOR || UPDATE;
-        const bool need_at = PRIOR;
-        if constexpr (CHW == 4) {
-          if (need_x) {
-            const float4 v = __ldg(reinterpret_cast<const float4*>(x + rbase + col0));
-            xv[0] = v.x; xv[1] = v.y; xv[2] = v.z; xv[3] = v.w;
-          }
-          if (need_at) {
-            const float4 v = __ldg(reinterpret_cast<const float4*>(a.atg + rbase + col0));
-            at[0] = v.x; at[1] = v.y; at[2] = v.z; at[3] = v.w;
-          }
-        } else {
-          SFor<0, CHW>::run([&](auto c_) {
-            constexpr int ci = decltype(c_)::value;
-            if (need_x) xv[ci] = __ldg(x + rbase + col0 + ci);
-            if (need_at) at[ci] = __ldg(a.atg + rbase + col0 + ci);
-          });
-        }
-        SFor<0, CHW>::run([&](auto c_) {
-          constexpr int ci = decltype(c_)::value;
-          if constexpr (!PRIOR) {
-            res[ci] = zd[ci];
-            acc[0] += xv[ci] * zd[ci];
-            acc[5] += zd[ci] * zd[ci];
-          } else {
-            const float yv = yo[i][k * CHW + ci];
-            const float Gv = zd[ci] - at[ci] + pc.lam * own[i][k * CHW + ci];
-            acc[0] += yv * zd[ci];
-            acc[1] += yv * at[ci];
-            acc[4] += Gv * Gv;
-            if constexpr (MODE == (int)Pass3Mode::Gradient) {
-              res[ci] = Gv;
-            } else if constexpr (UPDATE) {
-              const float xn = fmaf(-invL, Gv, yv);
-              res[ci] = xn;
-              acc[3] += Gv * (xn - xv[ci]);
+    auto voxel = [&](int v) {
+      const int row = v / N, col = v - row * N;  // block row, column (a warp covers one row)
+      const int grow = r0 + row;
+      const size_t idx = slice_base + (size_t)grow * N + col;
+      const float zd = kzs[row * N + col];
+      if constexpr (!PRIOR) {
+        const float xv = __ldg(x + idx);
+        out[idx] = zd;
+        acc[0] += xv * zd;
+        acc[5] += zd * zd;
+      } else {
+        float at = 0.f, xv = 0.f;
+        at = __ldg(a.atg + idx);
+        if constexpr (UPDATE) xv = __ldg(x + idx);
+        const float yv = sz[1][(row + 1) * N + col];
+        const float mL = col > 0 ? 1.f : 0.f, mR = col + 1 < N ? 1.f : 0.f;
+        const int cl = col > 0 ? col - 1 : col, cr = col + 1 < N ? col + 1 : col;
+        float gp = 0.f, ph = 0.f;
+#pragma unroll
+        for (int dz = 0; dz < 3; ++dz) {
+          if ((dz == 0 && !zval0) || (dz == 2 && !zval2)) continue;
+#pragma unroll
+          for (int dy = 0; dy < 3; ++dy) {
+            if ((dy == 0 && grow == 0) || (dy == 2 && grow + 1 == N)) continue;
+            const float* rp = sz[dz] + (row + dy) * N;
+            const int ring_n = (dz != 1) + (dy != 1);
+            const bool fwd_plane = dz > 1 || (dz == 1 && dy > 1);
+#pragma unroll
+            for (int dx = 0; dx < 3; ++dx) {
+              if (dz == 1 && dy == 1 && dx == 1) continue;
+              const float nb = rp[dx == 0 ? cl : (dx == 1 ? col : cr)];
+              const float m = dx == 0 ? mL : (dx == 2 ? mR : 1.f);
+              const float w = wts[ring_n + (dx != 1)] * m;
+              float rh = 0.f;
+              gp = fmaf(w, drho<Q2, PHI>(yv - nb, pc, rh), gp);
+              if (PHI && (fwd_plane || (dz == 1 && dy == 1 && dx == 2))) ph = fmaf(w, rh, ph);
             }
           }
-        });
-        if constexpr (MODE != (int)Pass3Mode::Objective) {
-          if constexpr (CHW == 4) {
-            *reinterpret_cast<float4*>(out + rbase + col0) = make_float4(res[0], res[1], res[2], res[3]);
-          } else {
-            SFor<0, CHW>::run([&](auto c_) {
-              constexpr int ci = decltype(c_)::value;
-              out[rbase + col0 + ci] = res[ci];
-            });
-          }
         }
-      });
-    });
+        const float Gv = zd - at + pc.lam * gp;
+        acc[0] += yv * zd;
+        acc[1] += yv * at;
+        acc[2] += ph;
+        acc[4] += Gv * Gv;
+        if constexpr (MODE == (int)Pass3Mode::Gradient) {
+          out[idx] = Gv;
+        } else if constexpr (UPDATE) {
+          const float xn = fmaf(-invL, Gv, yv);
+          out[idx] = xn;
+          acc[3] += Gv * (xn - xv);
+        }
+      }
+    };
+    // two voxels per trip (half a block apart) for instruction-level parallelism
+#pragma unroll 1
+    for (int v = threadIdx.x; v < RB * N; v += 2 * Gm::THREADS) {
+      voxel(v);
+      if (v + Gm::THREADS < RB * N) voxel(v + Gm::THREADS);
+    }
 #pragma unroll
     for (int j = 0; j < kParts; ++j) dacc[j] += (double)acc[j];
-#pragma unroll
-    for (int i = 0; i < RS; ++i)
-#pragma unroll
-      for (int j = 0; j < KCH * CHW; ++j) {
-        own[i][j] = nxt[i][j];
-        nxt[i][j] = 0.f;
-      }
   }
   block_partials<Gm::W>(dacc, red, partials + (size_t)(block_offset + blockIdx.x) * kParts);
 }

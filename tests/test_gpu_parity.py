@@ -2,7 +2,7 @@
 
 Tolerances: the FP32 operator and gradient within 1e-5 relative L2 of the oracle; the FP64
 setup (kernel K, R*g) within 1e-10 / 1e-6 (the latter is the FP32 storage of R*g); the FP32
-FBP start within 1e-4 (its NUFFT uses a width-7 kernel, error ~1e-6 per sample).
+FBP start within 1e-4 (FP32 arithmetic end to end).
 """
 import math
 
@@ -157,26 +157,57 @@ def test_graph_replay_is_bitwise_eager(prob):
 
 def test_uneven_groups_equal_separate_contexts(orc):
     specs = [(64, 2, 30), (128, 1, 50), (64, 1, 20)]
-    groups, sinos, ctxs = [], [], []
+    groups, sinos, thetas, ctxs = [], [], [], []
     for k, (N, S, na) in enumerate(specs):
         p = synth.volume(S=S, N=N, n_angles=na, n_ellipsoids=4, seed=40 + k)
         groups.append(tm.Group(N=N, angles=list(p.theta), n_slices=S))
         sinos.append(p.sino.ravel())
+        thetas.append(p.theta)
         ctxs.append(tm.Context([groups[-1]]))
     big = tm.Context(groups)
-    atg = big.build_operator(dev(np.concatenate(sinos)))
+    d_sino = dev(np.concatenate(sinos))
+    atg = big.build_operator(d_sino)
     rng = np.random.default_rng(3)
     xs = [synth.random_image(rng, (S, N, N)).ravel() for N, S, _ in specs]
-    G = big.gradient(dev(np.concatenate(xs)), atg, tm.Params(**PRIOR))
+    d_x = dev(np.concatenate(xs))
+    G = big.gradient(d_x, atg, tm.Params(**PRIOR))
     torch.cuda.synchronize()
     off = 0
-    for k, (N, S, _) in enumerate(specs):
-        a1 = ctxs[k].build_operator(dev(sinos[k]))
-        G1 = ctxs[k].gradient(dev(xs[k]), a1, tm.Params(**PRIOR))
+    for k, (N, S, na) in enumerate(specs):
+        d_sk, d_xk = dev(sinos[k]), dev(xs[k])
+        a1 = ctxs[k].build_operator(d_sk)
+        G1 = ctxs[k].gradient(d_xk, a1, tm.Params(**PRIOR))
         torch.cuda.synchronize()
         n = S * N * N
-        assert torch.equal(G[off:off + n], G1), k
+        atg_ref = orc.adjoint(sinos[k].reshape(S, na, N).astype(np.float64), N, thetas[k])
+        e_big = rel(host(atg[off:off + n], (S, N, N)), atg_ref)
+        e_sep = rel(host(a1, (S, N, N)), atg_ref)
+        assert e_big < 1e-6 and e_sep < 1e-6, (k, "R*g vs oracle", e_big, e_sep)
+        ref = orc.gradient(xs[k].reshape(S, N, N), atg_ref, orc.kernel(N, thetas[k], N), orc.Prior(**PRIOR))
+        e_big = rel(host(G[off:off + n], (S, N, N)), ref)
+        e_sep = rel(host(G1, (S, N, N)), ref)
+        assert e_big < 1e-5 and e_sep < 1e-5, (k, "gradient vs oracle", e_big, e_sep)
+        # and the batched run is bit-identical to the separate one
+        assert torch.equal(big.kernel(k), ctxs[k].kernel(0)), (k, "kernel")
+        assert big.lambda_max()[k] == ctxs[k].lambda_max()[0], (k, "lambda_max")
+        assert torch.equal(atg[off:off + n], a1), (k, "R*g")
+        assert torch.equal(G[off:off + n], G1), (k, "gradient")
         off += n
+
+
+def test_identical_groups_give_identical_results():
+    p = synth.volume(S=2, N=64, n_angles=24, n_ellipsoids=4, seed=50)
+    grp = tm.Group(N=64, angles=list(p.theta), n_slices=2)
+    ctx = tm.Context([grp, grp, grp])
+    sino = np.concatenate([p.sino.ravel()] * 3)
+    atg = ctx.build_operator(dev(sino))
+    x = dev(np.concatenate([synth.random_image(np.random.default_rng(4), (2, 64, 64)).ravel()] * 3))
+    G = ctx.gradient(x, atg, tm.Params(**PRIOR))
+    torch.cuda.synchronize()
+    n = 2 * 64 * 64
+    for k in (1, 2):
+        assert torch.equal(atg[:n], atg[k * n:(k + 1) * n]), (k, "R*g")
+        assert torch.equal(G[:n], G[k * n:(k + 1) * n]), (k, "gradient")
 
 
 def test_lanczos_upsampling(orc):
