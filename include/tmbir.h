@@ -205,6 +205,26 @@ int tmbir_pass_times(tmbir_ctx* ctx, float* d_x, const float* d_atg, const tmbir
 /* Number of kernels this context has launched so far (graph replays count their kernel nodes). */
 int tmbir_launch_count(const tmbir_ctx* ctx, long long* h_count);
 
+/*
+ * tmbir_normal_apply without device scratch from the workspace: the same d_z = R*R d_x, with the
+ * intermediate spectra and reduction partials in a fixed array inside the library.  The paper
+ * has no counterpart; this entry point is for callers that cannot allocate device memory at the
+ * time of the call (for example code running under a host application that owns the whole
+ * device-memory budget, or a latency-critical loop where allocation is not allowed).
+ *   - The array holds 8 Mi complex values (64 MiB) of spectra, summed over all groups as
+ *     n_slices * (N+1) * N, and the partial sums of 65536 blocks.  Larger geometries are
+ *     rejected with TMBIR_ERR_SHAPE; nothing is allocated on any path.
+ *   - Every device that loads the library holds the array until the process exits.
+ *   - The first call on a device, with that device current, looks up the array's device
+ *     address (cudaGetSymbolAddress) and caches it; make that first call before any stream
+ *     capture.
+ *   - All calls share the one array and it keeps the last call's contents: calls whose work
+ *     overlaps on the GPU (different streams or contexts, concurrently) race on it.
+ *   - The operator must be built (tmbir_build_operator); its kernel spectrum still lives in the
+ *     context workspace.
+ */
+int tmbir_normal_apply_static(tmbir_ctx* ctx, const float* d_x, float* d_z);
+
 /* Wait for the context stream; reports a pending CUDA error. */
 int tmbir_sync(tmbir_ctx* ctx);
 

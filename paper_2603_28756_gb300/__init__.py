@@ -77,6 +77,7 @@ SYMBOLS = [
     "tmbir_set_workspace", "tmbir_build_operator", "tmbir_fbp", "tmbir_reconstruct", "tmbir_get_log",
     "tmbir_normal_apply", "tmbir_gradient", "tmbir_step", "tmbir_objective", "tmbir_lambda_max", "tmbir_kernel",
     "tmbir_upsample_lanczos3", "tmbir_downsample_sino", "tmbir_sync", "tmbir_pass_times", "tmbir_launch_count",
+    "tmbir_normal_apply_static",
 ]
 
 _lib = None
@@ -114,6 +115,7 @@ def load(path: str | None = None):
         "tmbir_sync": [vp],
         "tmbir_pass_times": [vp, vp, vp, ctypes.POINTER(_Params), i, dp],
         "tmbir_launch_count": [vp, ctypes.POINTER(ctypes.c_longlong)],
+        "tmbir_normal_apply_static": [vp, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -287,6 +289,15 @@ class Context:
         out = self._empty(x.numel()) if out is None else out
         self._pre()
         _check(_lib.tmbir_normal_apply(self._h, ctypes.c_void_p(_ptr(x)), ctypes.c_void_p(_ptr(out))))
+        self._post(x, out)
+        return out
+
+    def normal_apply_static(self, x, out=None):
+        """normal_apply with its scratch in the library's fixed device array (no allocation
+        by the library; `out` is allocated here when not given)."""
+        out = self._empty(x.numel()) if out is None else out
+        self._pre()
+        _check(_lib.tmbir_normal_apply_static(self._h, ctypes.c_void_p(_ptr(x)), ctypes.c_void_p(_ptr(out))))
         self._post(x, out)
         return out
 

@@ -1,0 +1,100 @@
+// tmbir_normal_apply_static: the normal operator of tmbir_normal_apply with its scratch memory
+// (the intermediate half spectra and the per-block partial sums) in a fixed-size array that is
+// part of the library image, for callers that cannot allocate device memory when they call.
+//
+// The array is a file-scope __device__ variable: every device that loads the library holds it
+// until the process exits.  Host code only sees a host-side stand-in for its name, so the
+// device address is looked up once per device with cudaGetSymbolAddress (on the first call
+// made while that device is current) and cached.
+#include <cstdint>
+#include <mutex>
+
+#include "internal.h"
+
+namespace tmbir {
+
+// 8 Mi complex floats (64 MiB) of half spectra: for example 7 slices of 1024^2, or 31 of 512^2
+constexpr size_t kStaticSpecElems = (size_t)8 << 20;
+// partial sums of up to 65536 reducing blocks
+constexpr size_t kStaticPartElems = (size_t)65536 * kParts;
+
+static __device__ __align__(256) float2 g_static_spec[kStaticSpecElems];
+static __device__ __align__(256) double g_static_parts[kStaticPartElems];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+float2* g_spec_addr[kMaxDevices] = {};
+double* g_part_addr[kMaxDevices] = {};
+}  // namespace
+
+// device addresses of the two arrays on the current device (set up on first use)
+static int static_scratch(float2** spec, double** parts) {
+  int dev = 0;
+  TMBIR_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return set_error(TMBIR_ERR_CUDA, "normal_apply_static: device index out of range");
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_spec_addr[dev]) {
+    void* p = nullptr;
+    void* q = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_static_spec);
+    if (e != cudaSuccess)
+      return set_error(TMBIR_ERR_CUDA, std::string("normal_apply_static: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    e = cudaGetSymbolAddress(&q, g_static_parts);
+    if (e != cudaSuccess)
+      return set_error(TMBIR_ERR_CUDA, std::string("normal_apply_static: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    g_spec_addr[dev] = static_cast<float2*>(p);
+    g_part_addr[dev] = static_cast<double*>(q);
+  }
+  *spec = g_spec_addr[dev];
+  *parts = g_part_addr[dev];
+  return TMBIR_OK;
+}
+
+}  // namespace tmbir
+
+using namespace tmbir;
+
+extern "C" int tmbir_normal_apply_static(tmbir_ctx* ctx, const float* d_x, float* d_z) {
+  if (!ctx) return set_error(TMBIR_ERR_ARG, "normal_apply_static: ctx is NULL");
+  Ctx& c = ctx->c;
+  if (c.groups.empty()) return set_error(TMBIR_ERR_STATE, "normal_apply_static: no geometry set");
+  if (!c.ws) return set_error(TMBIR_ERR_WORKSPACE, "normal_apply_static: no workspace bound");
+  if (!c.operator_built) return set_error(TMBIR_ERR_STATE, "normal_apply_static: operator not built");
+  if (!d_x || !d_z || ((uintptr_t)d_x & 15u) || ((uintptr_t)d_z & 15u) || d_x == d_z)
+    return set_error(TMBIR_ERR_ARG, "normal_apply_static: bad buffers");
+  // every group's spectra side by side in the static array; refuse what does not fit
+  size_t need = 0;
+  int blocks = 0;
+  for (const GroupDev& g : c.gdev) {
+    need += (size_t)g.S * (g.N + 1) * g.N;
+    blocks += blocks_pass3(g);
+  }
+  if (need > kStaticSpecElems)
+    return set_error(TMBIR_ERR_SHAPE, "normal_apply_static: the geometry needs " + std::to_string(need) +
+                                          " complex scratch values, the static array holds " +
+                                          std::to_string(kStaticSpecElems));
+  if ((size_t)blocks * kParts > kStaticPartElems)
+    return set_error(TMBIR_ERR_SHAPE, "normal_apply_static: too many reducing blocks for the static array");
+  float2* spec = nullptr;
+  double* parts = nullptr;
+  if (int e = static_scratch(&spec, &parts)) return e;
+  StepArgs a{};
+  a.x = d_x;
+  a.xprev = d_x;
+  a.beta = 0.f;
+  a.out = d_z;
+  PriorC pc{};
+  size_t off = 0;
+  int boff = 0;
+  for (const GroupDev& g0 : c.gdev) {
+    GroupDev g = g0;
+    g.spec = spec + off;
+    if (int e = launch_pass1(g, a, c.stream)) return e;
+    if (int e = launch_pass2(g, nullptr, c.stream)) return e;
+    if (int e = launch_pass3(g, a, Pass3Mode::Apply, pc, parts, boff, c.stream)) return e;
+    off += (size_t)g.S * (g.N + 1) * g.N;
+    boff += blocks_pass3(g);
+  }
+  return TMBIR_OK;
+}

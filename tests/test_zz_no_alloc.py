@@ -1,0 +1,51 @@
+"""tmbir_normal_apply_static: the normal operator with its scratch in the library's fixed
+device array, for callers that cannot allocate device memory when they call.  Its output must
+match tmbir_normal_apply (the workspace-scratch entry point) on two calls in a row; sizes
+beyond the array are refused.  Kept in its own file, collected last."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2603_28756_gb300 as tm  # noqa: E402
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32).ravel()).cuda()
+
+
+def test_static_scratch_matches_workspace_path_twice():
+    specs = [(64, 3, 30), (128, 2, 40)]
+    groups, sinos = [], []
+    for k, (N, S, na) in enumerate(specs):
+        p = synth.volume(S=S, N=N, n_angles=na, n_ellipsoids=4, seed=60 + k)
+        groups.append(tm.Group(N=N, angles=list(p.theta), n_slices=S))
+        sinos.append(p.sino.ravel())
+    ctx = tm.Context(groups)
+    ctx.build_operator(_dev(np.concatenate(sinos)))
+    rng = np.random.default_rng(8)
+    x = _dev(np.concatenate([synth.random_image(rng, (S, N, N)).ravel() for N, S, _ in specs]))
+    ref = ctx.normal_apply(x)
+    for _ in range(2):
+        z = ctx.normal_apply_static(x)
+        torch.cuda.synchronize()
+        err = float(torch.linalg.norm((z - ref).double()) / torch.linalg.norm(ref.double()))
+        assert err < 1e-5, err
+
+
+def test_static_scratch_refuses_oversized_geometry():
+    th = list(synth.angles(8))
+    ctx = tm.Context([tm.Group(N=1024, angles=th, n_slices=8)])  # 8 * 1025 * 1024 > 8 Mi
+    ctx.build_operator(torch.zeros(8 * 8 * 1024, device="cuda"))
+    x = torch.zeros(8 * 1024 * 1024, device="cuda")
+    with pytest.raises(tm.TmbirError) as e:
+        ctx.normal_apply_static(x)
+    assert e.value.code == -2 and "static array" in str(e.value)
