@@ -206,6 +206,46 @@ int tmbir_pass_times(tmbir_ctx* ctx, float* d_x, const float* d_atg, const tmbir
 int tmbir_launch_count(const tmbir_ctx* ctx, long long* h_count);
 
 /*
+ * Learned warm start (not in the paper; the refined start of the task configuration): a
+ * four-layer 3x3 convolutional network, channels 1 -> 32 -> 32 -> 32 -> 1, zero padding, a bias
+ * per output channel, ReLU after the first three layers.  FP32 master weights, BF16 activations,
+ * FP32 accumulation; the 32 -> 32 layers run as implicit GEMMs on the tensor cores.
+ * Parameter vector (tmbir_cnn_param_count() = 19105 floats), layer by layer: weights
+ * [cout][cin][3][3] then biases [cout].  Images are float32 [batch][H][W], all H x W.
+ * Applied to a start x it gives x + s * net(x / s), s = RMS of x per image; trained with the
+ * mean squared error between net(x / s) and (t - x) / s for targets t, Adam (0.9, 0.999, 1e-8).
+ * The network keeps its weights, optimiser state and activations in a caller-owned workspace.
+ */
+typedef struct tmbir_cnn tmbir_cnn;
+int tmbir_cnn_param_count(void);
+int tmbir_cnn_workspace_size(int max_batch, int H, int W, size_t* bytes);
+/* stream: cudaStream_t as void*; d_workspace 256-byte aligned, >= tmbir_cnn_workspace_size */
+int tmbir_cnn_create(tmbir_cnn** out, void* stream, int max_batch, int H, int W, void* d_workspace, size_t bytes);
+int tmbir_cnn_destroy(tmbir_cnn* net);
+/* He-normal weights (last layer scaled by 0.1 so the refiner starts near the identity), zero biases */
+int tmbir_cnn_init(tmbir_cnn* net, unsigned long long seed);
+int tmbir_cnn_set_weights(tmbir_cnn* net, const float* h_params);
+int tmbir_cnn_get_weights(tmbir_cnn* net, float* h_params);
+/* d_y = d_x + s * net(d_x / s) for batch images */
+int tmbir_cnn_apply(tmbir_cnn* net, const float* d_x, int batch, float* d_y);
+/* one Adam step on a batch of (start, target) pairs; h_loss (may be NULL) receives the loss */
+int tmbir_cnn_train_step(tmbir_cnn* net, const float* d_x, const float* d_target, int batch, float lr, double* h_loss);
+/* raw network: d_out = net(d_in) (no normalisation, no residual) */
+int tmbir_cnn_net_forward(tmbir_cnn* net, const float* d_in, int batch, float* d_out);
+/* raw gradients of sum(d_gout * net(d_in)): parameters into h_gparams (host), input into d_gin (may be NULL) */
+int tmbir_cnn_net_backward(tmbir_cnn* net, const float* d_in, const float* d_gout, int batch, float* h_gparams,
+                           float* d_gin);
+/*
+ * Warm start with fallback: d_x0 = the refined start if its objective (Eq. 10 plus the prior) is
+ * below that of the FBP start d_fbp, else a copy of d_fbp; *h_used_cnn tells which.  Needs one
+ * geometry group with N equal to the network's image size.  The network's work is ordered after
+ * the context stream's pending work and before the objectives (events, when the two streams
+ * differ); the result is ready in stream order on the context's stream.
+ */
+int tmbir_warm_start(tmbir_ctx* ctx, tmbir_cnn* net, const float* d_fbp, const float* d_atg, const tmbir_params* prm,
+                     float* d_x0, int* h_used_cnn);
+
+/*
  * tmbir_normal_apply without device scratch from the workspace: the same d_z = R*R d_x, with the
  * intermediate spectra and reduction partials in a fixed array inside the library.  The paper
  * has no counterpart; this entry point is for callers that cannot allocate device memory at the

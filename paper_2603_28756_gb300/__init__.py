@@ -13,7 +13,7 @@ from dataclasses import dataclass, field
 
 from .build import LIB, build  # noqa: F401
 
-__all__ = ["Context", "Group", "Params", "Stats", "TmbirError", "load", "SYMBOLS", "build"]
+__all__ = ["CNN", "Context", "Group", "Params", "Stats", "TmbirError", "load", "SYMBOLS", "build"]
 
 TMBIR_OK = 0
 ERRORS = {
@@ -77,7 +77,9 @@ SYMBOLS = [
     "tmbir_set_workspace", "tmbir_build_operator", "tmbir_fbp", "tmbir_reconstruct", "tmbir_get_log",
     "tmbir_normal_apply", "tmbir_gradient", "tmbir_step", "tmbir_objective", "tmbir_lambda_max", "tmbir_kernel",
     "tmbir_upsample_lanczos3", "tmbir_downsample_sino", "tmbir_sync", "tmbir_pass_times", "tmbir_launch_count",
-    "tmbir_normal_apply_static",
+    "tmbir_normal_apply_static", "tmbir_cnn_param_count", "tmbir_cnn_workspace_size", "tmbir_cnn_create",
+    "tmbir_cnn_destroy", "tmbir_cnn_init", "tmbir_cnn_set_weights", "tmbir_cnn_get_weights", "tmbir_cnn_apply",
+    "tmbir_cnn_train_step", "tmbir_cnn_net_forward", "tmbir_cnn_net_backward", "tmbir_warm_start",
 ]
 
 _lib = None
@@ -116,6 +118,18 @@ def load(path: str | None = None):
         "tmbir_pass_times": [vp, vp, vp, ctypes.POINTER(_Params), i, dp],
         "tmbir_launch_count": [vp, ctypes.POINTER(ctypes.c_longlong)],
         "tmbir_normal_apply_static": [vp, vp, vp],
+        "tmbir_cnn_param_count": [],
+        "tmbir_cnn_workspace_size": [i, i, i, ctypes.POINTER(sz)],
+        "tmbir_cnn_create": [ctypes.POINTER(vp), vp, i, i, i, vp, sz],
+        "tmbir_cnn_destroy": [vp],
+        "tmbir_cnn_init": [vp, ctypes.c_ulonglong],
+        "tmbir_cnn_set_weights": [vp, ctypes.POINTER(ctypes.c_float)],
+        "tmbir_cnn_get_weights": [vp, ctypes.POINTER(ctypes.c_float)],
+        "tmbir_cnn_apply": [vp, vp, i, vp],
+        "tmbir_cnn_train_step": [vp, vp, vp, i, ctypes.c_float, dp],
+        "tmbir_cnn_net_forward": [vp, vp, i, vp],
+        "tmbir_cnn_net_backward": [vp, vp, vp, i, ctypes.POINTER(ctypes.c_float), vp],
+        "tmbir_warm_start": [vp, vp, vp, vp, ctypes.POINTER(_Params), vp, ctypes.POINTER(i)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -383,6 +397,109 @@ class Context:
     def close(self):
         if getattr(self, "_h", None):
             _lib.tmbir_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class CNN:
+    """The learned warm-start refiner (see tmbir_cnn_* in include/tmbir.h)."""
+
+    def __init__(self, H: int, W: int, max_batch: int = 4, stream=None, device="cuda", seed: int = 1):
+        import torch
+
+        load()
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=self.device)
+        self.H, self.W, self.max_batch = H, W, max_batch
+        nbytes = ctypes.c_size_t()
+        _check(_lib.tmbir_cnn_workspace_size(max_batch, H, W, ctypes.byref(nbytes)))
+        with torch.cuda.stream(self.stream):
+            self.workspace = torch.empty(nbytes.value + 256, dtype=torch.uint8, device=self.device)
+        aligned = (self.workspace.data_ptr() + 255) // 256 * 256
+        h = ctypes.c_void_p()
+        _check(_lib.tmbir_cnn_create(ctypes.byref(h), ctypes.c_void_p(self.stream.cuda_stream), max_batch, H, W,
+                                     ctypes.c_void_p(aligned), nbytes.value))
+        self._h = h
+        self.n_params = _lib.tmbir_cnn_param_count()
+        _check(_lib.tmbir_cnn_init(self._h, seed))
+
+    _pre = Context._pre
+    _post = Context._post
+
+    def _empty(self, n):
+        import torch
+
+        with torch.cuda.stream(self.stream):
+            return torch.empty(n, dtype=torch.float32, device=self.device)
+
+    def set_weights(self, params):
+        import numpy as np
+
+        a = np.ascontiguousarray(params, dtype=np.float32)
+        assert a.size == self.n_params
+        _check(_lib.tmbir_cnn_set_weights(self._h, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+
+    def get_weights(self):
+        import numpy as np
+
+        a = np.zeros(self.n_params, dtype=np.float32)
+        _check(_lib.tmbir_cnn_get_weights(self._h, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+        return a
+
+    def apply(self, x, batch: int, out=None):
+        out = self._empty(x.numel()) if out is None else out
+        self._pre()
+        _check(_lib.tmbir_cnn_apply(self._h, ctypes.c_void_p(_ptr(x)), batch, ctypes.c_void_p(_ptr(out))))
+        self._post(x, out)
+        return out
+
+    def train_step(self, x, target, batch: int, lr: float = 1e-3) -> float:
+        loss = ctypes.c_double()
+        self._pre()
+        _check(_lib.tmbir_cnn_train_step(self._h, ctypes.c_void_p(_ptr(x)), ctypes.c_void_p(_ptr(target)), batch,
+                                         float(lr), ctypes.byref(loss)))
+        self._post(x, target)
+        return loss.value
+
+    def net_forward(self, x, batch: int):
+        out = self._empty(x.numel())
+        self._pre()
+        _check(_lib.tmbir_cnn_net_forward(self._h, ctypes.c_void_p(_ptr(x)), batch, ctypes.c_void_p(_ptr(out))))
+        self._post(x, out)
+        return out
+
+    def net_backward(self, x, gout, batch: int):
+        import numpy as np
+
+        gp = np.zeros(self.n_params, dtype=np.float32)
+        gin = self._empty(x.numel())
+        self._pre()
+        _check(_lib.tmbir_cnn_net_backward(self._h, ctypes.c_void_p(_ptr(x)), ctypes.c_void_p(_ptr(gout)), batch,
+                                           gp.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                           ctypes.c_void_p(_ptr(gin))))
+        self._post(x, gout, gin)
+        return gp, gin
+
+    def warm_start(self, ctx: Context, fbp, atg, params: Params, out=None):
+        """(x0, used_cnn): the refined start if its objective beats the FBP start's, else FBP."""
+        out = ctx._empty(fbp.numel()) if out is None else out
+        used = ctypes.c_int()
+        pr = params.c_struct()
+        ctx._pre()  # the library orders the network's stream after the context's
+        _check(_lib.tmbir_warm_start(ctx._h, self._h, ctypes.c_void_p(_ptr(fbp)), ctypes.c_void_p(_ptr(atg)),
+                                     ctypes.byref(pr), ctypes.c_void_p(_ptr(out)), ctypes.byref(used)))
+        ctx._post(fbp, atg, out)
+        self._post(fbp, out)
+        return out, bool(used.value)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.tmbir_cnn_destroy(self._h)
             self._h = None
 
     def __del__(self):

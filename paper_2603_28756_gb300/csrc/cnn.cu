@@ -1,0 +1,825 @@
+// Learned warm start: a four-layer 3x3 convolutional refiner (1 -> 32 -> 32 -> 32 -> 1, ReLU
+// after the first three layers, zero padding) applied to the normalised FBP start, with its
+// own training kernels.  The paper has no learned component; the network shape comes from the
+// task configuration.
+//
+// Precision: FP32 master weights, BF16 activations and weight copies, FP32 accumulation.
+// The two 32 -> 32 layers are implicit GEMMs on the tensor cores (mma.sync m16n8k16, BF16 in,
+// FP32 out): M = pixels of an 8 x 32 tile, N = 32 output channels, K = 9 taps x 32 channels.
+// Their data gradient is the same kernel run on the flipped, transposed weights.  The first
+// and last layers (32 MACs per tap) and all weight gradients run on the CUDA cores; weight
+// gradients are reduced over a fixed set of blocks in a fixed order (deterministic).
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <cstring>
+#include <random>
+#include <vector>
+
+#include "internal.h"
+
+namespace tmbir {
+
+constexpr int kC = 32;                          // channels of the hidden layers
+constexpr int kW0 = kC * 9, kB0 = kC;           // layer 0: [co][tap], bias
+constexpr int kW1 = kC * kC * 9, kB1 = kC;      // layers 1, 2: [co][ci][tap] (oracle layout)
+constexpr int kW3 = kC * 9, kB3 = 1;            // layer 3: [ci][tap]
+constexpr int kOff0 = 0, kOffB0 = kW0;
+constexpr int kOff1 = kOffB0 + kB0, kOffB1 = kOff1 + kW1;
+constexpr int kOff2 = kOffB1 + kB1, kOffB2 = kOff2 + kW1;
+constexpr int kOff3 = kOffB2 + kB1, kOffB3 = kOff3 + kW3;
+constexpr int kParams = kOffB3 + kB3;  // 19105
+constexpr int TH = 8, TW = 32;         // output tile of the tensor-core convolution
+constexpr int PS = 40;                 // padded channel stride of a pixel in shared memory (bf16)
+constexpr int KS = 9 * kC + 8;         // padded row of the GEMM weight matrix (bf16)
+constexpr int kWgradBlocks = 304;      // blocks of the weight-gradient reductions
+
+struct CnnNet {
+  cudaStream_t stream;
+  int max_batch, H, W;
+  float* master;        // [kParams] FP32 weights (oracle layout)
+  float* grad;          // [kParams]
+  float* adam_m;        // [kParams]
+  float* adam_v;        // [kParams]
+  __nv_bfloat16* wg1;   // [32][KS] layer 1 as GEMM B: [co][tap*32 + ci]
+  __nv_bfloat16* wg2;   // layer 2
+  __nv_bfloat16* wt1;   // [32][KS] flipped transpose of layer 1 for the data gradient: [ci][tap'*32 + co]
+  __nv_bfloat16* wt2;
+  __nv_bfloat16* a0;    // activations NHWC [B][H][W][32]
+  __nv_bfloat16* a1;
+  __nv_bfloat16* a2;
+  __nv_bfloat16* g1;    // gradients NHWC
+  __nv_bfloat16* g2;
+  float* xin;           // [B][H][W] normalised input
+  float* out;           // [B][H][W] network output
+  float* gout;          // [B][H][W]
+  float* sig;           // [B] per-image scale
+  float* wpart;         // [kWgradBlocks][kW1] weight-gradient partials
+  double* dpart;        // scalar partials
+  int step;
+};
+
+// ---------------------------------------------------------------- weight layouts
+__global__ void k_cnn_pack(const float* __restrict__ master, __nv_bfloat16* wg1, __nv_bfloat16* wg2,
+                           __nv_bfloat16* wt1, __nv_bfloat16* wt2) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kC * KS; i += gridDim.x * blockDim.x) {
+    const int r = i / KS, k = i % KS;
+    float v1 = 0.f, v2 = 0.f, t1 = 0.f, t2 = 0.f;
+    if (k < 9 * kC) {
+      const int tap = k / kC, c = k % kC;
+      // forward: row = co, k = tap*32 + ci
+      v1 = master[kOff1 + (r * kC + c) * 9 + tap];
+      v2 = master[kOff2 + (r * kC + c) * 9 + tap];
+      // data gradient: row = ci, k = tap'*32 + co with tap' = 8 - tap (flip)
+      t1 = master[kOff1 + (c * kC + r) * 9 + (8 - tap)];
+      t2 = master[kOff2 + (c * kC + r) * 9 + (8 - tap)];
+    }
+    wg1[i] = __float2bfloat16_rn(v1);
+    wg2[i] = __float2bfloat16_rn(v2);
+    wt1[i] = __float2bfloat16_rn(t1);
+    wt2[i] = __float2bfloat16_rn(t2);
+  }
+}
+
+// ---------------------------------------------------------------- tensor-core 32 -> 32 convolution
+__device__ __forceinline__ void ldsm_x4(unsigned& r0, unsigned& r1, unsigned& r2, unsigned& r3, const void* p) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"(a));
+}
+__device__ __forceinline__ void mma_bf16(float (&d)[4], unsigned a0, unsigned a1, unsigned a2, unsigned a3, unsigned b0,
+                                         unsigned b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// out[p][n] = sum_{tap, c} w[n][tap*32 + c] in[p + tap][c]  (+ bias, ReLU), 8 x 32 pixel tiles.
+// MASK (data gradient): the result is multiplied by (mask[p][n] > 0).
+template <bool BIAS_RELU, bool MASK>
+__global__ void __launch_bounds__(128) k_conv32(const __nv_bfloat16* __restrict__ in, int B, int H, int W,
+                                                const __nv_bfloat16* __restrict__ wg, const float* __restrict__ bias,
+                                                const __nv_bfloat16* __restrict__ mask, __nv_bfloat16* __restrict__ out) {
+  __shared__ __align__(16) __nv_bfloat16 sin[(TH + 2) * (TW + 2) * PS];
+  __shared__ __align__(16) __nv_bfloat16 sw[kC * KS];
+  const int tiles_x = (W + TW - 1) / TW, tiles_y = (H + TH - 1) / TH;
+  const int tpi = tiles_x * tiles_y;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int i = threadIdx.x; i < kC * KS / 8; i += 128) reinterpret_cast<int4*>(sw)[i] = reinterpret_cast<const int4*>(wg)[i];
+  for (int tile = blockIdx.x; tile < B * tpi; tile += gridDim.x) {
+    const int b = tile / tpi, ty = (tile % tpi) / tiles_x, tx = tile % tiles_x;
+    const int y0 = ty * TH, x0 = tx * TW;
+    __syncthreads();
+    // input tile with a one-pixel halo, 4 channels (8 bytes) per step
+    for (int e = threadIdx.x; e < (TH + 2) * (TW + 2) * (kC / 4); e += 128) {
+      const int c4 = e % (kC / 4), pix = e / (kC / 4);
+      const int py = pix / (TW + 2), px = pix % (TW + 2);
+      const int gy = y0 - 1 + py, gx = x0 - 1 + px;
+      uint2 v = make_uint2(0u, 0u);
+      if (gy >= 0 && gy < H && gx >= 0 && gx < W)
+        v = *reinterpret_cast<const uint2*>(in + (((size_t)b * H + gy) * W + gx) * kC + c4 * 4);
+      *reinterpret_cast<uint2*>(sin + pix * PS + c4 * 4) = v;
+    }
+    __syncthreads();
+    // warp: tile rows 2*warp, 2*warp+1 -> 4 m16 tiles (16 consecutive pixels of one row)
+    float acc[4][4][4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m)
+#pragma unroll
+      for (int n = 0; n < 4; ++n)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[m][n][j] = 0.f;
+#pragma unroll 1
+    for (int tap = 0; tap < 9; ++tap) {
+      const int dy = tap / 3, dx = tap % 3;
+#pragma unroll
+      for (int kh = 0; kh < 2; ++kh) {
+        unsigned bfr[4][2];
+#pragma unroll
+        for (int np = 0; np < 2; ++np) {
+          // two n8 tiles: rows co = np*16 + (lane % 8) + 8 * (lane / 16), k offset 8 * ((lane / 8) % 2)
+          const int co = np * 16 + (lane & 7) + ((lane >> 4) << 3);
+          const int kk = tap * kC + kh * 16 + (((lane >> 3) & 1) << 3);
+          unsigned r0, r1, r2, r3;
+          ldsm_x4(r0, r1, r2, r3, sw + co * KS + kk);
+          bfr[np * 2 + 0][0] = r0;
+          bfr[np * 2 + 0][1] = r1;
+          bfr[np * 2 + 1][0] = r2;
+          bfr[np * 2 + 1][1] = r3;
+        }
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          const int row = 2 * warp + (m >> 1), col0 = (m & 1) * 16;
+          const int px = col0 + (lane & 15);
+          const int pix = (row + dy) * (TW + 2) + px + dx;
+          unsigned a0, a1, a2, a3;
+          ldsm_x4(a0, a1, a2, a3, sin + pix * PS + kh * 16 + ((lane >> 4) << 3));
+#pragma unroll
+          for (int n = 0; n < 4; ++n) mma_bf16(acc[m][n], a0, a1, a2, a3, bfr[n][0], bfr[n][1]);
+        }
+      }
+    }
+    // epilogue: fragment (m, n): rows lane/4 and lane/4 + 8, channels n*8 + 2*(lane%4) + {0,1}
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const int row = 2 * warp + (m >> 1), col0 = (m & 1) * 16;
+      const int gy = y0 + row;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int gx = x0 + col0 + (lane >> 2) + 8 * h;
+        if (gy >= H || gx >= W) continue;
+        const size_t pbase = (((size_t)b * H + gy) * W + gx) * kC;
+#pragma unroll
+        for (int n = 0; n < 4; ++n) {
+          const int ch = n * 8 + 2 * (lane & 3);
+          float v0 = acc[m][n][2 * h], v1 = acc[m][n][2 * h + 1];
+          if constexpr (BIAS_RELU) {
+            v0 = fmaxf(v0 + bias[ch], 0.f);
+            v1 = fmaxf(v1 + bias[ch + 1], 0.f);
+          }
+          if constexpr (MASK) {
+            const __nv_bfloat162 mk = *reinterpret_cast<const __nv_bfloat162*>(mask + pbase + ch);
+            if (!(__bfloat162float(mk.x) > 0.f)) v0 = 0.f;
+            if (!(__bfloat162float(mk.y) > 0.f)) v1 = 0.f;
+          }
+          *reinterpret_cast<__nv_bfloat162*>(out + pbase + ch) = __floats2bfloat162_rn(v0, v1);
+        }
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- first and last layers (CUDA cores)
+// a0[p][co] = relu(b0[co] + sum_tap w0[co][tap] x[p + tap])
+__global__ void k_conv_first(const float* __restrict__ x, int B, int H, int W, const float* __restrict__ master,
+                             __nv_bfloat16* __restrict__ a0) {
+  __shared__ float w[kW0 + kB0];
+  for (int i = threadIdx.x; i < kW0 + kB0; i += blockDim.x) w[i] = master[kOff0 + i];
+  __syncthreads();
+  const size_t total = (size_t)B * H * W;
+  for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < total; p += (size_t)gridDim.x * blockDim.x) {
+    const int xx = (int)(p % W), yy = (int)((p / W) % H);
+    const size_t b = p / ((size_t)H * W);
+    float nb[9];
+#pragma unroll
+    for (int t = 0; t < 9; ++t) {
+      const int gy = yy + t / 3 - 1, gx = xx + t % 3 - 1;
+      nb[t] = (gy >= 0 && gy < H && gx >= 0 && gx < W) ? x[(b * H + gy) * W + gx] : 0.f;
+    }
+    __nv_bfloat162* o = reinterpret_cast<__nv_bfloat162*>(a0 + p * kC);
+#pragma unroll 4
+    for (int co = 0; co < kC; co += 2) {
+      float s0 = w[kW0 + co], s1 = w[kW0 + co + 1];
+#pragma unroll
+      for (int t = 0; t < 9; ++t) {
+        s0 = fmaf(w[co * 9 + t], nb[t], s0);
+        s1 = fmaf(w[(co + 1) * 9 + t], nb[t], s1);
+      }
+      o[co / 2] = __floats2bfloat162_rn(fmaxf(s0, 0.f), fmaxf(s1, 0.f));
+    }
+  }
+}
+
+// out[p] = b3 + sum_{tap, ci} w3[ci][tap] a2[p + tap][ci]
+__global__ void k_conv_last(const __nv_bfloat16* __restrict__ a2, int B, int H, int W, const float* __restrict__ master,
+                            float* __restrict__ out) {
+  __shared__ float w[kW3 + kB3];
+  for (int i = threadIdx.x; i < kW3 + kB3; i += blockDim.x) w[i] = master[kOff3 + i];
+  __syncthreads();
+  const size_t total = (size_t)B * H * W;
+  for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < total; p += (size_t)gridDim.x * blockDim.x) {
+    const int xx = (int)(p % W), yy = (int)((p / W) % H);
+    const size_t b = p / ((size_t)H * W);
+    float s = w[kW3];
+#pragma unroll 1
+    for (int t = 0; t < 9; ++t) {
+      const int gy = yy + t / 3 - 1, gx = xx + t % 3 - 1;
+      if (gy < 0 || gy >= H || gx < 0 || gx >= W) continue;
+      const __nv_bfloat162* a = reinterpret_cast<const __nv_bfloat162*>(a2 + ((b * H + gy) * W + gx) * kC);
+#pragma unroll
+      for (int c = 0; c < kC; c += 2) {
+        const float2 v = __bfloat1622float2(a[c / 2]);
+        s = fmaf(w[c * 9 + t], v.x, s);
+        s = fmaf(w[(c + 1) * 9 + t], v.y, s);
+      }
+    }
+    out[p] = s;
+  }
+}
+
+// g2[p][ci] = (a2[p][ci] > 0) * sum_tap w3[ci][tap] gout[p - tap]
+__global__ void k_last_dgrad(const float* __restrict__ gout, const __nv_bfloat16* __restrict__ a2, int B, int H, int W,
+                             const float* __restrict__ master, __nv_bfloat16* __restrict__ g2) {
+  __shared__ float w[kW3];
+  for (int i = threadIdx.x; i < kW3; i += blockDim.x) w[i] = master[kOff3 + i];
+  __syncthreads();
+  const size_t total = (size_t)B * H * W;
+  for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < total; p += (size_t)gridDim.x * blockDim.x) {
+    const int xx = (int)(p % W), yy = (int)((p / W) % H);
+    const size_t b = p / ((size_t)H * W);
+    float gg[9];
+#pragma unroll
+    for (int t = 0; t < 9; ++t) {
+      const int gy = yy - (t / 3 - 1), gx = xx - (t % 3 - 1);
+      gg[t] = (gy >= 0 && gy < H && gx >= 0 && gx < W) ? gout[(b * H + gy) * W + gx] : 0.f;
+    }
+    const __nv_bfloat162* a = reinterpret_cast<const __nv_bfloat162*>(a2 + p * kC);
+    __nv_bfloat162* o = reinterpret_cast<__nv_bfloat162*>(g2 + p * kC);
+#pragma unroll 4
+    for (int c = 0; c < kC; c += 2) {
+      float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+      for (int t = 0; t < 9; ++t) {
+        s0 = fmaf(w[c * 9 + t], gg[t], s0);
+        s1 = fmaf(w[(c + 1) * 9 + t], gg[t], s1);
+      }
+      const float2 av = __bfloat1622float2(a[c / 2]);
+      o[c / 2] = __floats2bfloat162_rn(av.x > 0.f ? s0 : 0.f, av.y > 0.f ? s1 : 0.f);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- weight gradients (fixed-order block partials)
+// Layer 1/2: dW[co][ci][tap] = sum_p g[p][co] in[p + tap][ci]; thread t owns co = t / 8 and
+// ci = 4 (t % 8) .. +3 for all 9 taps (36 sums); pixels in a fixed grid-stride order.
+__global__ void __launch_bounds__(256) k_wgrad32(const __nv_bfloat16* __restrict__ g, const __nv_bfloat16* __restrict__ in,
+                                                 int B, int H, int W, float* __restrict__ part) {
+  const int co = threadIdx.x >> 3, ci0 = (threadIdx.x & 7) * 4;
+  float s[4][9];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int t = 0; t < 9; ++t) s[i][t] = 0.f;
+  const size_t total = (size_t)B * H * W;
+  for (size_t p = blockIdx.x; p < total; p += gridDim.x) {
+    const int xx = (int)(p % W), yy = (int)((p / W) % H);
+    const size_t b = p / ((size_t)H * W);
+    const float gv = __bfloat162float(g[p * kC + co]);
+#pragma unroll
+    for (int t = 0; t < 9; ++t) {
+      const int gy = yy + t / 3 - 1, gx = xx + t % 3 - 1;
+      if (gy < 0 || gy >= H || gx < 0 || gx >= W) continue;
+      const __nv_bfloat162* a = reinterpret_cast<const __nv_bfloat162*>(in + ((b * H + gy) * W + gx) * kC + ci0);
+      const float2 v0 = __bfloat1622float2(a[0]), v1 = __bfloat1622float2(a[1]);
+      s[0][t] = fmaf(gv, v0.x, s[0][t]);
+      s[1][t] = fmaf(gv, v0.y, s[1][t]);
+      s[2][t] = fmaf(gv, v1.x, s[2][t]);
+      s[3][t] = fmaf(gv, v1.y, s[3][t]);
+    }
+  }
+  float* o = part + (size_t)blockIdx.x * kW1;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int t = 0; t < 9; ++t) o[(co * kC + ci0 + i) * 9 + t] = s[i][t];
+}
+
+// Layer 0: dW0[co][tap] = sum_p g0[p][co] xin[p + tap], db0[co] = sum_p g0[p][co];
+// thread t: co = t % 32, taps 3 (t / 32) .. +2 for t < 96, bias for 96 <= t < 128.
+// Partial row layout: [0, 288) dW0, [288, 320) db0.
+__global__ void __launch_bounds__(128) k_wgrad_first(const __nv_bfloat16* __restrict__ g0, const float* __restrict__ xin,
+                                                     int B, int H, int W, float* __restrict__ part) {
+  const int co = threadIdx.x & 31, role = threadIdx.x >> 5;
+  float acc[3] = {0.f, 0.f, 0.f};
+  const size_t total = (size_t)B * H * W;
+  for (size_t p = blockIdx.x; p < total; p += gridDim.x) {
+    const float gv = __bfloat162float(g0[p * kC + co]);
+    if (role == 3) {
+      acc[0] += gv;
+      continue;
+    }
+    const int xx = (int)(p % W), yy = (int)((p / W) % H);
+    const size_t b = p / ((size_t)H * W);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const int t = role * 3 + j;
+      const int gy = yy + t / 3 - 1, gx = xx + t % 3 - 1;
+      if (gy >= 0 && gy < H && gx >= 0 && gx < W) acc[j] = fmaf(gv, xin[(b * H + gy) * W + gx], acc[j]);
+    }
+  }
+  float* o = part + (size_t)blockIdx.x * kW1;
+  if (role < 3) {
+#pragma unroll
+    for (int j = 0; j < 3; ++j) o[co * 9 + role * 3 + j] = acc[j];
+  } else {
+    o[288 + co] = acc[0];
+  }
+}
+// Hidden-layer bias: db[co] = sum_p g[p][co]; partial row [0, 32)
+__global__ void __launch_bounds__(32) k_bias_grad(const __nv_bfloat16* __restrict__ g, size_t total, float* __restrict__ part) {
+  float acc = 0.f;
+  for (size_t p = blockIdx.x; p < total; p += gridDim.x) acc += __bfloat162float(g[p * kC + threadIdx.x]);
+  part[(size_t)blockIdx.x * kW1 + threadIdx.x] = acc;
+}
+// Layer 3: dW3[ci][tap] = sum_p gout[p] a2[p + tap][ci], db3 = sum_p gout[p];
+// thread t < 32: ci = t, all taps; thread 32: bias.  Partial row [0, 288) dW3, [288] db3.
+__global__ void __launch_bounds__(64) k_wgrad_last(const float* __restrict__ gout, const __nv_bfloat16* __restrict__ a2,
+                                                   int B, int H, int W, float* __restrict__ part) {
+  const int ci = threadIdx.x;
+  float acc[9];
+#pragma unroll
+  for (int t = 0; t < 9; ++t) acc[t] = 0.f;
+  const size_t total = (size_t)B * H * W;
+  for (size_t p = blockIdx.x; p < total; p += gridDim.x) {
+    const float gv = gout[p];
+    if (ci == 32) {
+      acc[0] += gv;
+      continue;
+    }
+    if (ci > 32) continue;
+    const int xx = (int)(p % W), yy = (int)((p / W) % H);
+    const size_t b = p / ((size_t)H * W);
+#pragma unroll
+    for (int t = 0; t < 9; ++t) {
+      const int gy = yy + t / 3 - 1, gx = xx + t % 3 - 1;
+      if (gy >= 0 && gy < H && gx >= 0 && gx < W)
+        acc[t] = fmaf(gv, __bfloat162float(a2[((b * H + gy) * W + gx) * kC + ci]), acc[t]);
+    }
+  }
+  float* o = part + (size_t)blockIdx.x * kW1;
+  if (ci < 32) {
+#pragma unroll
+    for (int t = 0; t < 9; ++t) o[ci * 9 + t] = acc[t];
+  } else if (ci == 32) {
+    o[288] = acc[0];
+  }
+}
+// gin[p] = sum_{tap, co} w0[co][tap] g0[p - tap][co]
+__global__ void k_first_dgrad(const __nv_bfloat16* __restrict__ g0, int B, int H, int W, const float* __restrict__ master,
+                              float* __restrict__ gin) {
+  __shared__ float w[kW0];
+  for (int i = threadIdx.x; i < kW0; i += blockDim.x) w[i] = master[kOff0 + i];
+  __syncthreads();
+  const size_t total = (size_t)B * H * W;
+  for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < total; p += (size_t)gridDim.x * blockDim.x) {
+    const int xx = (int)(p % W), yy = (int)((p / W) % H);
+    const size_t b = p / ((size_t)H * W);
+    float s = 0.f;
+#pragma unroll 1
+    for (int t = 0; t < 9; ++t) {
+      const int gy = yy - (t / 3 - 1), gx = xx - (t % 3 - 1);
+      if (gy < 0 || gy >= H || gx < 0 || gx >= W) continue;
+      const __nv_bfloat162* gg = reinterpret_cast<const __nv_bfloat162*>(g0 + ((b * H + gy) * W + gx) * kC);
+#pragma unroll
+      for (int c = 0; c < kC; c += 2) {
+        const float2 v = __bfloat1622float2(gg[c / 2]);
+        s = fmaf(w[c * 9 + t], v.x, s);
+        s = fmaf(w[(c + 1) * 9 + t], v.y, s);
+      }
+    }
+    gin[p] = s;
+  }
+}
+// dst[i] += sum over blocks (fixed order) of part[b][i], i < n
+__global__ void k_reduce_parts(const float* __restrict__ part, int nblocks, int n, float* __restrict__ dst) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int b = 0; b < nblocks; ++b) s += part[(size_t)b * kW1 + i];
+    dst[i] += (float)s;
+  }
+}
+
+// ---------------------------------------------------------------- normalisation, loss, optimiser
+// per image: sig = sqrt(mean x^2) (1 if zero); xin = x / sig
+__global__ void k_norm_stats(const float* __restrict__ x, int HW, float* __restrict__ sig) {
+  __shared__ double sh[256];
+  const float* xb = x + (size_t)blockIdx.x * HW;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < HW; i += blockDim.x) s += (double)xb[i] * xb[i];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double r = sqrt(sh[0] / HW);
+    sig[blockIdx.x] = r > 0 ? (float)r : 1.f;
+  }
+}
+__global__ void k_scale_in(const float* __restrict__ x, int HW, size_t total, const float* __restrict__ sig,
+                           float* __restrict__ xin) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x)
+    xin[i] = x[i] / sig[i / HW];
+}
+// refined = x + sig * net
+__global__ void k_residual_out(const float* __restrict__ x, const float* __restrict__ net, int HW, size_t total,
+                               const float* __restrict__ sig, float* __restrict__ y) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x)
+    y[i] = x[i] + sig[i / HW] * net[i];
+}
+// loss = mean (net - (t - x)/sig)^2; gout = 2 (net - r) / P; per-block FP64 partials
+__global__ void k_loss(const float* __restrict__ net, const float* __restrict__ x, const float* __restrict__ t, int HW,
+                       size_t total, const float* __restrict__ sig, float* __restrict__ gout, double* __restrict__ part) {
+  __shared__ double sh[256];
+  double s = 0.0;
+  const float inv = 1.0f / (float)total;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const float r = (t[i] - x[i]) / sig[i / HW];
+    const float d = net[i] - r;
+    gout[i] = 2.0f * d * inv;
+    s += (double)d * d;
+  }
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+__global__ void k_sum_d(const double* __restrict__ part, int n, double scale, double* __restrict__ out) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s += part[i];
+    *out = s * scale;
+  }
+}
+// Adam (Kingma & Ba 2015) on the FP32 master weights
+__global__ void k_adam(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
+                       int n, float lr, float b1, float b2, float eps, float c1, float c2) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+  }
+}
+
+// ---------------------------------------------------------------- host sequences
+static size_t cnn_bytes(int B, int H, int W, size_t* offs) {
+  size_t off = 0;
+  auto take = [&](size_t b) {
+    off = (off + 255) / 256 * 256;
+    size_t o = off;
+    off += b;
+    return o;
+  };
+  const size_t P = (size_t)B * H * W;
+  offs[0] = take(kParams * 4);                         // master
+  offs[1] = take(kParams * 4);                         // grad
+  offs[2] = take(kParams * 4);                         // m
+  offs[3] = take(kParams * 4);                         // v
+  for (int i = 0; i < 4; ++i) offs[4 + i] = take((size_t)kC * KS * 2);  // wg1 wg2 wt1 wt2
+  for (int i = 0; i < 5; ++i) offs[8 + i] = take(P * kC * 2);           // a0 a1 a2 g1 g2
+  for (int i = 0; i < 3; ++i) offs[13 + i] = take(P * 4);               // xin out gout
+  offs[16] = take((size_t)B * 4);                                        // sig
+  offs[17] = take((size_t)kWgradBlocks * kW1 * 4);                       // wpart
+  offs[18] = take(4096 * 8);                                             // dpart
+  return (off + 255) / 256 * 256;
+}
+
+static int conv32(CnnNet& n, const __nv_bfloat16* in, int B, const __nv_bfloat16* w, const float* bias,
+                  const __nv_bfloat16* mask, __nv_bfloat16* out, bool relu) {
+  const int tiles = B * ((n.H + TH - 1) / TH) * ((n.W + TW - 1) / TW);
+  const int blocks = std::min(tiles, 152 * 8);
+  if (relu)
+    k_conv32<true, false><<<blocks, 128, 0, n.stream>>>(in, B, n.H, n.W, w, bias, nullptr, out);
+  else
+    k_conv32<false, true><<<blocks, 128, 0, n.stream>>>(in, B, n.H, n.W, w, bias, mask, out);
+  TMBIR_CHECK_LAUNCH();
+  return TMBIR_OK;
+}
+
+static int net_forward(CnnNet& n, int B) {
+  const size_t P = (size_t)B * n.H * n.W;
+  const int blocks = (int)std::min<size_t>((P + 255) / 256, 152 * 16);
+  k_conv_first<<<blocks, 256, 0, n.stream>>>(n.xin, B, n.H, n.W, n.master, n.a0);
+  TMBIR_CHECK_LAUNCH();
+  if (int e = conv32(n, n.a0, B, n.wg1, n.master + kOffB1, nullptr, n.a1, true)) return e;
+  if (int e = conv32(n, n.a1, B, n.wg2, n.master + kOffB2, nullptr, n.a2, true)) return e;
+  k_conv_last<<<blocks, 256, 0, n.stream>>>(n.a2, B, n.H, n.W, n.master, n.out);
+  TMBIR_CHECK_LAUNCH();
+  return TMBIR_OK;
+}
+
+// gradients of sum(gout * net(xin)) added into n.grad; gin (optional, FP32) receives d/dxin
+static int net_backward(CnnNet& n, int B, float* gin) {
+  const size_t P = (size_t)B * n.H * n.W;
+  const int blocks = (int)std::min<size_t>((P + 255) / 256, 152 * 16);
+  const int rb = (kW1 + 255) / 256;
+  // layer 3
+  k_wgrad_last<<<kWgradBlocks, 64, 0, n.stream>>>(n.gout, n.a2, B, n.H, n.W, n.wpart);
+  TMBIR_CHECK_LAUNCH();
+  k_reduce_parts<<<2, 256, 0, n.stream>>>(n.wpart, kWgradBlocks, kW3 + kB3, n.grad + kOff3);
+  TMBIR_CHECK_LAUNCH();
+  k_last_dgrad<<<blocks, 256, 0, n.stream>>>(n.gout, n.a2, B, n.H, n.W, n.master, n.g2);
+  TMBIR_CHECK_LAUNCH();
+  // layer 2: weights from (g2, a1), then g1 = mask(a1) conv(g2, W2 flipped transposed)
+  k_wgrad32<<<kWgradBlocks, 256, 0, n.stream>>>(n.g2, n.a1, B, n.H, n.W, n.wpart);
+  TMBIR_CHECK_LAUNCH();
+  k_reduce_parts<<<rb, 256, 0, n.stream>>>(n.wpart, kWgradBlocks, kW1, n.grad + kOff2);
+  TMBIR_CHECK_LAUNCH();
+  k_bias_grad<<<kWgradBlocks, 32, 0, n.stream>>>(n.g2, P, n.wpart);
+  TMBIR_CHECK_LAUNCH();
+  k_reduce_parts<<<1, 32, 0, n.stream>>>(n.wpart, kWgradBlocks, kB1, n.grad + kOffB2);
+  TMBIR_CHECK_LAUNCH();
+  if (int e = conv32(n, n.g2, B, n.wt2, nullptr, n.a1, n.g1, false)) return e;
+  // layer 1: weights from (g1, a0), then g0 = mask(a0) conv(g1, W1 flipped transposed) into g2's buffer
+  k_wgrad32<<<kWgradBlocks, 256, 0, n.stream>>>(n.g1, n.a0, B, n.H, n.W, n.wpart);
+  TMBIR_CHECK_LAUNCH();
+  k_reduce_parts<<<rb, 256, 0, n.stream>>>(n.wpart, kWgradBlocks, kW1, n.grad + kOff1);
+  TMBIR_CHECK_LAUNCH();
+  k_bias_grad<<<kWgradBlocks, 32, 0, n.stream>>>(n.g1, P, n.wpart);
+  TMBIR_CHECK_LAUNCH();
+  k_reduce_parts<<<1, 32, 0, n.stream>>>(n.wpart, kWgradBlocks, kB1, n.grad + kOffB1);
+  TMBIR_CHECK_LAUNCH();
+  __nv_bfloat16* g0 = n.g2;
+  if (int e = conv32(n, n.g1, B, n.wt1, nullptr, n.a0, g0, false)) return e;
+  // layer 0
+  k_wgrad_first<<<kWgradBlocks, 128, 0, n.stream>>>(g0, n.xin, B, n.H, n.W, n.wpart);
+  TMBIR_CHECK_LAUNCH();
+  k_reduce_parts<<<2, 256, 0, n.stream>>>(n.wpart, kWgradBlocks, kW0 + kB0, n.grad + kOff0);
+  TMBIR_CHECK_LAUNCH();
+  if (gin) {
+    k_first_dgrad<<<blocks, 256, 0, n.stream>>>(g0, B, n.H, n.W, n.master, gin);
+    TMBIR_CHECK_LAUNCH();
+  }
+  return TMBIR_OK;
+}
+
+static int pack(CnnNet& n) {
+  k_cnn_pack<<<(kC * KS + 255) / 256, 256, 0, n.stream>>>(n.master, n.wg1, n.wg2, n.wt1, n.wt2);
+  TMBIR_CHECK_LAUNCH();
+  return TMBIR_OK;
+}
+
+static int normalise(CnnNet& n, const float* x, int B) {
+  const int HW = n.H * n.W;
+  const size_t P = (size_t)B * HW;
+  k_norm_stats<<<B, 256, 0, n.stream>>>(x, HW, n.sig);
+  TMBIR_CHECK_LAUNCH();
+  k_scale_in<<<(int)std::min<size_t>((P + 255) / 256, 152 * 16), 256, 0, n.stream>>>(x, HW, P, n.sig, n.xin);
+  TMBIR_CHECK_LAUNCH();
+  return TMBIR_OK;
+}
+
+}  // namespace tmbir
+
+using namespace tmbir;
+
+struct tmbir_cnn {
+  CnnNet n;
+  size_t offs[19];
+};
+
+#define CNN_REQUIRE(cond, code, msg) \
+  do {                               \
+    if (!(cond)) return set_error(code, msg); \
+  } while (0)
+
+static bool al16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+extern "C" {
+
+int tmbir_cnn_param_count(void) { return kParams; }
+
+int tmbir_cnn_workspace_size(int max_batch, int H, int W, size_t* bytes) {
+  CNN_REQUIRE(bytes && max_batch >= 1 && H >= 1 && W >= 1 && (size_t)max_batch * H * W < ((size_t)1 << 31),
+              TMBIR_ERR_ARG, "cnn_workspace_size: bad sizes");
+  size_t offs[19];
+  *bytes = cnn_bytes(max_batch, H, W, offs);
+  return TMBIR_OK;
+}
+
+int tmbir_cnn_create(tmbir_cnn** out, void* stream, int max_batch, int H, int W, void* d_ws, size_t bytes) {
+  CNN_REQUIRE(out && d_ws && ((uintptr_t)d_ws & 255u) == 0, TMBIR_ERR_ARG,
+              "cnn_create: NULL argument or workspace not 256-byte aligned");
+  size_t need = 0;
+  if (int e = tmbir_cnn_workspace_size(max_batch, H, W, &need)) return e;
+  CNN_REQUIRE(bytes >= need, TMBIR_ERR_WORKSPACE, "cnn_create: workspace too small");
+  tmbir_cnn* c = new tmbir_cnn();
+  cnn_bytes(max_batch, H, W, c->offs);
+  char* ws = static_cast<char*>(d_ws);
+  CnnNet& n = c->n;
+  n.stream = (cudaStream_t)stream;
+  n.max_batch = max_batch;
+  n.H = H;
+  n.W = W;
+  n.master = reinterpret_cast<float*>(ws + c->offs[0]);
+  n.grad = reinterpret_cast<float*>(ws + c->offs[1]);
+  n.adam_m = reinterpret_cast<float*>(ws + c->offs[2]);
+  n.adam_v = reinterpret_cast<float*>(ws + c->offs[3]);
+  n.wg1 = reinterpret_cast<__nv_bfloat16*>(ws + c->offs[4]);
+  n.wg2 = reinterpret_cast<__nv_bfloat16*>(ws + c->offs[5]);
+  n.wt1 = reinterpret_cast<__nv_bfloat16*>(ws + c->offs[6]);
+  n.wt2 = reinterpret_cast<__nv_bfloat16*>(ws + c->offs[7]);
+  n.a0 = reinterpret_cast<__nv_bfloat16*>(ws + c->offs[8]);
+  n.a1 = reinterpret_cast<__nv_bfloat16*>(ws + c->offs[9]);
+  n.a2 = reinterpret_cast<__nv_bfloat16*>(ws + c->offs[10]);
+  n.g1 = reinterpret_cast<__nv_bfloat16*>(ws + c->offs[11]);
+  n.g2 = reinterpret_cast<__nv_bfloat16*>(ws + c->offs[12]);
+  n.xin = reinterpret_cast<float*>(ws + c->offs[13]);
+  n.out = reinterpret_cast<float*>(ws + c->offs[14]);
+  n.gout = reinterpret_cast<float*>(ws + c->offs[15]);
+  n.sig = reinterpret_cast<float*>(ws + c->offs[16]);
+  n.wpart = reinterpret_cast<float*>(ws + c->offs[17]);
+  n.dpart = reinterpret_cast<double*>(ws + c->offs[18]);
+  n.step = 0;
+  *out = c;
+  return TMBIR_OK;
+}
+
+int tmbir_cnn_destroy(tmbir_cnn* net) {
+  delete net;
+  return TMBIR_OK;
+}
+
+int tmbir_cnn_set_weights(tmbir_cnn* net, const float* h_params) {
+  CNN_REQUIRE(net && h_params, TMBIR_ERR_ARG, "cnn_set_weights: NULL argument");
+  CnnNet& n = net->n;
+  TMBIR_CUDA(cudaMemcpyAsync(n.master, h_params, kParams * sizeof(float), cudaMemcpyHostToDevice, n.stream));
+  TMBIR_CUDA(cudaMemsetAsync(n.adam_m, 0, kParams * sizeof(float), n.stream));
+  TMBIR_CUDA(cudaMemsetAsync(n.adam_v, 0, kParams * sizeof(float), n.stream));
+  n.step = 0;
+  if (int e = pack(n)) return e;
+  TMBIR_CUDA(cudaStreamSynchronize(n.stream));
+  return TMBIR_OK;
+}
+
+int tmbir_cnn_get_weights(tmbir_cnn* net, float* h_params) {
+  CNN_REQUIRE(net && h_params, TMBIR_ERR_ARG, "cnn_get_weights: NULL argument");
+  CnnNet& n = net->n;
+  TMBIR_CUDA(cudaMemcpyAsync(h_params, n.master, kParams * sizeof(float), cudaMemcpyDeviceToHost, n.stream));
+  TMBIR_CUDA(cudaStreamSynchronize(n.stream));
+  return TMBIR_OK;
+}
+
+int tmbir_cnn_init(tmbir_cnn* net, unsigned long long seed) {
+  CNN_REQUIRE(net, TMBIR_ERR_ARG, "cnn_init: NULL argument");
+  std::mt19937_64 rng(seed);
+  std::vector<float> p(kParams, 0.f);
+  auto fill = [&](int off, int count, int fan_in, float gain) {
+    std::normal_distribution<double> nd(0.0, gain * std::sqrt(2.0 / fan_in));
+    for (int i = 0; i < count; ++i) p[off + i] = (float)nd(rng);
+  };
+  fill(kOff0, kW0, 9, 1.f);
+  fill(kOff1, kW1, 9 * kC, 1.f);
+  fill(kOff2, kW1, 9 * kC, 1.f);
+  fill(kOff3, kW3, 9 * kC, 0.1f);  // small last layer: the refiner starts close to the identity
+  return tmbir_cnn_set_weights(net, p.data());
+}
+
+int tmbir_cnn_net_forward(tmbir_cnn* net, const float* d_in, int batch, float* d_out) {
+  CNN_REQUIRE(net && d_in && d_out && al16(d_in) && al16(d_out), TMBIR_ERR_ARG, "cnn_net_forward: bad buffers");
+  CnnNet& n = net->n;
+  CNN_REQUIRE(batch >= 1 && batch <= n.max_batch, TMBIR_ERR_ARG, "cnn_net_forward: batch out of range");
+  const size_t P = (size_t)batch * n.H * n.W;
+  TMBIR_CUDA(cudaMemcpyAsync(n.xin, d_in, P * sizeof(float), cudaMemcpyDeviceToDevice, n.stream));
+  if (int e = net_forward(n, batch)) return e;
+  TMBIR_CUDA(cudaMemcpyAsync(d_out, n.out, P * sizeof(float), cudaMemcpyDeviceToDevice, n.stream));
+  return TMBIR_OK;
+}
+
+int tmbir_cnn_net_backward(tmbir_cnn* net, const float* d_in, const float* d_gout, int batch, float* h_gparams,
+                           float* d_gin) {
+  CNN_REQUIRE(net && d_in && d_gout && h_gparams && al16(d_in) && al16(d_gout) && (!d_gin || al16(d_gin)),
+              TMBIR_ERR_ARG, "cnn_net_backward: bad buffers");
+  CnnNet& n = net->n;
+  CNN_REQUIRE(batch >= 1 && batch <= n.max_batch, TMBIR_ERR_ARG, "cnn_net_backward: batch out of range");
+  const size_t P = (size_t)batch * n.H * n.W;
+  TMBIR_CUDA(cudaMemcpyAsync(n.xin, d_in, P * sizeof(float), cudaMemcpyDeviceToDevice, n.stream));
+  if (int e = net_forward(n, batch)) return e;
+  TMBIR_CUDA(cudaMemcpyAsync(n.gout, d_gout, P * sizeof(float), cudaMemcpyDeviceToDevice, n.stream));
+  TMBIR_CUDA(cudaMemsetAsync(n.grad, 0, kParams * sizeof(float), n.stream));
+  if (int e = net_backward(n, batch, d_gin)) return e;
+  TMBIR_CUDA(cudaMemcpyAsync(h_gparams, n.grad, kParams * sizeof(float), cudaMemcpyDeviceToHost, n.stream));
+  TMBIR_CUDA(cudaStreamSynchronize(n.stream));
+  return TMBIR_OK;
+}
+
+int tmbir_cnn_apply(tmbir_cnn* net, const float* d_x, int batch, float* d_y) {
+  CNN_REQUIRE(net && d_x && d_y && al16(d_x) && al16(d_y), TMBIR_ERR_ARG, "cnn_apply: bad buffers");
+  CnnNet& n = net->n;
+  CNN_REQUIRE(batch >= 1 && batch <= n.max_batch, TMBIR_ERR_ARG, "cnn_apply: batch out of range");
+  const size_t P = (size_t)batch * n.H * n.W;
+  if (int e = normalise(n, d_x, batch)) return e;
+  if (int e = net_forward(n, batch)) return e;
+  k_residual_out<<<(int)std::min<size_t>((P + 255) / 256, 152 * 16), 256, 0, n.stream>>>(d_x, n.out, n.H * n.W, P,
+                                                                                        n.sig, d_y);
+  TMBIR_CHECK_LAUNCH();
+  return TMBIR_OK;
+}
+
+int tmbir_cnn_train_step(tmbir_cnn* net, const float* d_x, const float* d_target, int batch, float lr, double* h_loss) {
+  CNN_REQUIRE(net && d_x && d_target && al16(d_x) && al16(d_target), TMBIR_ERR_ARG, "cnn_train_step: bad buffers");
+  CnnNet& n = net->n;
+  CNN_REQUIRE(batch >= 1 && batch <= n.max_batch && lr > 0.f, TMBIR_ERR_ARG, "cnn_train_step: bad batch or rate");
+  const size_t P = (size_t)batch * n.H * n.W;
+  if (int e = normalise(n, d_x, batch)) return e;
+  if (int e = net_forward(n, batch)) return e;
+  const int lb = 1024;
+  k_loss<<<lb, 256, 0, n.stream>>>(n.out, d_x, d_target, n.H * n.W, P, n.sig, n.gout, n.dpart);
+  TMBIR_CHECK_LAUNCH();
+  k_sum_d<<<1, 32, 0, n.stream>>>(n.dpart, lb, 1.0 / (double)P, n.dpart + lb);
+  TMBIR_CHECK_LAUNCH();
+  TMBIR_CUDA(cudaMemsetAsync(n.grad, 0, kParams * sizeof(float), n.stream));
+  if (int e = net_backward(n, batch, nullptr)) return e;
+  n.step += 1;
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = 1.f - std::pow(b1, (float)n.step), c2 = 1.f - std::pow(b2, (float)n.step);
+  k_adam<<<(kParams + 255) / 256, 256, 0, n.stream>>>(n.master, n.grad, n.adam_m, n.adam_v, kParams, lr, b1, b2, 1e-8f,
+                                                      c1, c2);
+  TMBIR_CHECK_LAUNCH();
+  if (int e = pack(n)) return e;
+  if (h_loss) {
+    TMBIR_CUDA(cudaMemcpyAsync(h_loss, n.dpart + lb, sizeof(double), cudaMemcpyDeviceToHost, n.stream));
+    TMBIR_CUDA(cudaStreamSynchronize(n.stream));
+  }
+  return TMBIR_OK;
+}
+
+int tmbir_warm_start(tmbir_ctx* ctx, tmbir_cnn* net, const float* d_fbp, const float* d_atg, const tmbir_params* prm,
+                     float* d_x0, int* h_used_cnn) {
+  CNN_REQUIRE(ctx && net && d_fbp && d_atg && prm && d_x0 && al16(d_fbp) && al16(d_x0), TMBIR_ERR_ARG,
+              "warm_start: bad arguments");
+  CNN_REQUIRE(d_x0 != d_fbp, TMBIR_ERR_ARG, "warm_start: output must not alias the FBP start");
+  Ctx& c = ctx->c;
+  CnnNet& n = net->n;
+  CNN_REQUIRE(c.groups.size() == 1 && c.groups[0].N == n.H && n.H == n.W, TMBIR_ERR_SHAPE,
+              "warm_start: needs one geometry group whose N equals the network's image size");
+  const int S = c.groups[0].n_slices;
+  const size_t HW = (size_t)n.H * n.W;
+  // the network runs on its own stream: it starts after the context's pending work and the
+  // objectives below start after it
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  if (n.stream != c.stream) {
+    TMBIR_CUDA(cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
+    if (cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventDestroy(ev[0]);
+      return set_error(TMBIR_ERR_CUDA, "warm_start: cudaEventCreate failed");
+    }
+  }
+  auto release = [&](int e) {
+    for (cudaEvent_t x : ev)
+      if (x) cudaEventDestroy(x);
+    return e;
+  };
+  if (ev[0]) {
+    if (cudaEventRecord(ev[0], c.stream) != cudaSuccess || cudaStreamWaitEvent(n.stream, ev[0], 0) != cudaSuccess)
+      return release(set_error(TMBIR_ERR_CUDA, "warm_start: stream ordering failed"));
+  }
+  for (int s0 = 0; s0 < S; s0 += n.max_batch) {
+    const int b = std::min(n.max_batch, S - s0);
+    if (int e = tmbir_cnn_apply(net, d_fbp + s0 * HW, b, d_x0 + s0 * HW)) return release(e);
+  }
+  if (ev[1]) {
+    if (cudaEventRecord(ev[1], n.stream) != cudaSuccess || cudaStreamWaitEvent(c.stream, ev[1], 0) != cudaSuccess)
+      return release(set_error(TMBIR_ERR_CUDA, "warm_start: stream ordering failed"));
+  }
+  release(0);
+  double F_cnn = 0.0, F_fbp = 0.0;
+  if (int e = tmbir_objective(ctx, d_x0, d_atg, prm, &F_cnn)) return e;
+  if (int e = tmbir_objective(ctx, d_fbp, d_atg, prm, &F_fbp)) return e;
+  const int use = F_cnn < F_fbp ? 1 : 0;
+  if (!use) TMBIR_CUDA(cudaMemcpyAsync(d_x0, d_fbp, S * HW * sizeof(float), cudaMemcpyDeviceToDevice, c.stream));
+  if (h_used_cnn) *h_used_cnn = use;
+  return TMBIR_OK;
+}
+
+}  // extern "C"
