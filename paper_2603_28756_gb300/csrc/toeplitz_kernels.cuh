@@ -254,10 +254,13 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) k_pass2(GroupDev g, const Ite
 // columns) and sums rho' over the 26 neighbours.  The voxel loop is a plain runtime loop so
 // the unrolled neighbourhood stays small enough for the instruction cache.  Each unordered
 // neighbour pair enters Phi once, from the voxel it is a forward offset of.
+// The transforms run on the first Gm::W warps (one row group each); the voxel phase runs on
+// twice as many warps, so two resident blocks keep 16 warps per SM to hide the latency of the
+// special-function chains.
 template <int N>
 struct Geo3 {
   using Gm = Geo<N>;
-  static constexpr int RB = Gm::RB, THREADS = Gm::THREADS;
+  static constexpr int RB = Gm::RB, W = 2 * Gm::W, THREADS = 32 * W;
   static constexpr int ROWS = RB + 2;  // ring rows (one halo row each side)
   static constexpr size_t SM_RING = (size_t)3 * ROWS * N * sizeof(float);
   static constexpr size_t SM_A = Gm::cmax(Gm::SM1, (size_t)RB * N * sizeof(float));
@@ -285,7 +288,7 @@ __device__ __forceinline__ void load_ring(float* slot, const float* x, const flo
 }
 
 template <int N, int MODE, bool Q2>
-__global__ void __launch_bounds__(Geo<N>::THREADS)
+__global__ void __launch_bounds__(Geo3<N>::THREADS, 2)
     k_pass3(GroupDev g, StepArgs a, PriorC pc, double* partials, int block_offset, int zc) {
   using Gm = Geo<N>;
   using G3 = Geo3<N>;
@@ -296,7 +299,7 @@ __global__ void __launch_bounds__(Geo<N>::THREADS)
                        MODE == (int)Pass3Mode::Objective;
   constexpr bool UPDATE = MODE == (int)Pass3Mode::Step || MODE == (int)Pass3Mode::Iterate;
   extern __shared__ float2 sm[];
-  __shared__ double red[Gm::W * kParts];
+  __shared__ double red[G3::W * kParts];
   const float *x, *xp;
   float* out;
   float beta, invL;
@@ -342,7 +345,7 @@ __global__ void __launch_bounds__(Geo<N>::THREADS)
     __syncthreads();
     {
       const float2* sp = g.spec + (size_t)z * (N + 1) * N + r0;
-      for (int e = threadIdx.x; e < (N + 1) * RB; e += Gm::THREADS) {
+      for (int e = threadIdx.x; e < (N + 1) * RB; e += G3::THREADS) {
         const int vv = e / RB, rr = e - vv * RB;
         tb[rr * LD + vv] = sp[(size_t)vv * N + rr];
       }
@@ -351,24 +354,29 @@ __global__ void __launch_bounds__(Geo<N>::THREADS)
       if (z + 1 < g.S) load_ring<N>(ring + ((z + 1) % 3) * ROWS * N, x, xp, beta, slice_base + N2, r0);
     }
     __syncthreads();
+    const bool fft_warp = warp < Gm::W;
     float2 q[P];
-    SFor<0, P>::run([&](auto i_) {
-      constexpr int i = decltype(i_)::value;
-      const int vp = t + T * i;
-      const float2 zv = tb[rl * LD + vp];
-      const float2 zr = tb[rl * LD + N - vp];
-      const float2 e = make_float2(zv.x + zr.x, zv.y - zr.y);
-      const float2 d = make_float2(zv.x - zr.x, zv.y + zr.y);
-      const float2 o = cmulc(d, __ldg(&g.twM[vp]));
-      q[i] = make_float2(e.x - o.y, e.y + o.x);
-    });
+    if (fft_warp) {
+      SFor<0, P>::run([&](auto i_) {
+        constexpr int i = decltype(i_)::value;
+        const int vp = t + T * i;
+        const float2 zv = tb[rl * LD + vp];
+        const float2 zr = tb[rl * LD + N - vp];
+        const float2 e = make_float2(zv.x + zr.x, zv.y - zr.y);
+        const float2 d = make_float2(zv.x - zr.x, zv.y + zr.y);
+        const float2 o = cmulc(d, __ldg(&g.twM[vp]));
+        q[i] = make_float2(e.x - o.y, e.y + o.x);
+      });
+    }
     __syncthreads();
-    F::template run<1>(q, sm + (warp * G + grp) * F::SMEM, g.twN, t);
+    if (fft_warp) F::template run<1>(q, sm + (warp * G + grp) * F::SMEM, g.twN, t);
     __syncthreads();
-    SFor<0, P / 2>::run([&](auto i_) {
-      constexpr int i = decltype(i_)::value;
-      reinterpret_cast<float2*>(kzs + rl * N)[t + T * i] = q[i];
-    });
+    if (fft_warp) {
+      SFor<0, P / 2>::run([&](auto i_) {
+        constexpr int i = decltype(i_)::value;
+        reinterpret_cast<float2*>(kzs + rl * N)[t + T * i] = q[i];
+      });
+    }
     __syncthreads();
 
     // ---- per voxel: prior, gradient, update, partial sums
@@ -432,14 +440,14 @@ __global__ void __launch_bounds__(Geo<N>::THREADS)
     };
     // two voxels per trip (half a block apart) for instruction-level parallelism
 #pragma unroll 1
-    for (int v = threadIdx.x; v < RB * N; v += 2 * Gm::THREADS) {
+    for (int v = threadIdx.x; v < RB * N; v += 2 * G3::THREADS) {
       voxel(v);
-      if (v + Gm::THREADS < RB * N) voxel(v + Gm::THREADS);
+      if (v + G3::THREADS < RB * N) voxel(v + G3::THREADS);
     }
 #pragma unroll
     for (int j = 0; j < kParts; ++j) dacc[j] += (double)acc[j];
   }
-  block_partials<Gm::W>(dacc, red, partials + (size_t)(block_offset + blockIdx.x) * kParts);
+  block_partials<G3::W>(dacc, red, partials + (size_t)(block_offset + blockIdx.x) * kParts);
 }
 
 // ---------------------------------------------------------------- host launchers
@@ -485,9 +493,9 @@ static int pass3_nm(const GroupDev& g, const StepArgs& a, const PriorC& pc, doub
   const int zc = pass3_slices_per_block(g.S, Gm::NB);
   const int blocks = Gm::NB * ((g.S + zc - 1) / zc);
   if (pc.q_is_2 || MODE == 0)
-    k_pass3<N, MODE, true><<<blocks, Gm::THREADS, Geo3<N>::SM, s>>>(g, a, pc, partials, off, zc);
+    k_pass3<N, MODE, true><<<blocks, Geo3<N>::THREADS, Geo3<N>::SM, s>>>(g, a, pc, partials, off, zc);
   else
-    k_pass3<N, MODE, false><<<blocks, Gm::THREADS, Geo3<N>::SM, s>>>(g, a, pc, partials, off, zc);
+    k_pass3<N, MODE, false><<<blocks, Geo3<N>::THREADS, Geo3<N>::SM, s>>>(g, a, pc, partials, off, zc);
   TMBIR_CHECK_LAUNCH();
   return TMBIR_OK;
 }
