@@ -312,22 +312,29 @@ def lipschitz(K, N: int, pr: Prior, steps: int = 100, Chat=None) -> float:
 # ----------------------------------------------------------------------------- optimisers
 
 
-def nesterov(x0, atg, gtg: float, K, pr: Prior, L: float, iters: int, Chat=None, log=None):
-    """Fast gradient method with gradient-based restart (Sec. 2).
+def nesterov(x0, atg, gtg: float, K, pr: Prior, L: float, iters: int, Chat=None, log=None, restart="gradient"):
+    """Fast gradient method with adaptive restart (Sec. 2, which cites the restarted scheme
+    without stating the test).
 
     t_0 = 1, x_{-1} = x_0.  Each step:
       t' = (1 + sqrt(1 + 4 t^2)) / 2,  beta = (t - 1) / t'
       y = x + beta (x - x_prev)
       G = K*y - A^T g + lambda grad Phi(y)
       x_new = y - G / L
-      if <G, x_new - x> > 0: t' = 1           (restart)
+      restart (t' = 1) when
+        "gradient": <G, x_new - x> > 0
+        "function": F(y_k) > F(y_{k-1})
+        "none":     never
     ``log`` (a list) receives (F(y_k), <G,x_new-x>, restarted) per step.
     """
+    if restart not in ("gradient", "function", "none"):
+        raise ValueError(restart)
     if Chat is None:
         Chat = circulant_spectrum(K)
     x = _f64(x0).copy()
     x_prev = x.copy()
     t = 1.0
+    F_prev = None
     for _ in range(iters):
         t_next = 0.5 * (1.0 + math.sqrt(1.0 + 4.0 * t * t))
         beta = (t - 1.0) / t_next
@@ -337,12 +344,18 @@ def nesterov(x0, atg, gtg: float, K, pr: Prior, L: float, iters: int, Chat=None,
         G = z - atg + gp
         x_new = y - G / L
         dot = float(np.sum(G * (x_new - x)))
-        restart = dot > 0.0
-        if restart:
+        F = 0.5 * float(np.sum(y * z)) - float(np.sum(y * atg)) + 0.5 * gtg + phi
+        if restart == "gradient":
+            restarted = dot > 0.0
+        elif restart == "function":
+            restarted = F_prev is not None and F > F_prev
+        else:
+            restarted = False
+        if restarted:
             t_next = 1.0
         if log is not None:
-            F = 0.5 * float(np.sum(y * z)) - float(np.sum(y * atg)) + 0.5 * gtg + phi
-            log.append((F, dot, restart))
+            log.append((F, dot, restarted))
+        F_prev = F
         x_prev, x, t = x, x_new, t_next
     return x
 

@@ -122,3 +122,32 @@ def test_restart_log(orc):
     assert abs(log[0][0] - 0.5 * gtg) < 1e-12 * gtg
     assert all((d > 0) == r for _, d, r in log)
     assert log[-1][0] < 0.5 * log[0][0]
+
+
+def test_restart_modes(orc):
+    # every restart mode reaches the minimiser of the quadratic case (a dense linear solve)
+    S, N, nd, na = 1, 6, 8, 5
+    pr = orc.Prior(p=2.0, q=2.0, sigma=0.5, lam=0.3)
+    rng = np.random.default_rng(25)
+    th = synth.angles(na)
+    g = rng.uniform(0, 1, (S, na, nd))
+    A = np.stack([nudft_forward(e.reshape(N, N), th, nd).ravel() for e in np.eye(N * N)], axis=1)
+    H = A.T @ A + pr.lam / pr.sigma ** 2 * gaussian_mrf_laplacian(orc, S, N)
+    x_star = np.linalg.solve(H, A.T @ g[0].ravel()).reshape(S, N, N)
+    K = orc.kernel(N, th, nd)
+    atg = orc.adjoint(g, N, th)
+    L = orc.lipschitz(K, N, pr)
+    gtg = float(np.sum(g * g))
+    logs = {}
+    for mode in ("gradient", "function", "none"):
+        logs[mode] = []
+        x = orc.nesterov(np.zeros((S, N, N)), atg, gtg, K, pr, L, 3000, log=logs[mode], restart=mode)
+        assert np.linalg.norm(x - x_star) < 1e-6 * np.linalg.norm(x_star), mode
+    # the function test restarts exactly when the objective at y went up
+    lf = logs["function"]
+    assert all(r == (k > 0 and lf[k][0] > lf[k - 1][0]) for k, (_, _, r) in enumerate(lf))
+    assert not any(r for _, _, r in logs["none"])
+    # without restart the first steps are the plain accelerated sequence, so all modes agree
+    # until the first restart of a mode
+    first = min(k for k, (_, _, r) in enumerate(logs["gradient"]) if r)
+    assert all(abs(a[0] - b[0]) <= 1e-12 * abs(b[0]) for a, b in zip(logs["gradient"][:first + 1], logs["none"][:first + 1]))
