@@ -157,6 +157,54 @@ def cpu_baseline(name, samples_slices=2, samples_iters=2):
     }
 
 
+GAP = 1e-3
+REF_ITERS = 1000
+
+
+def time_to_gap(tm, ctx, stream, sino, atg, x, barrier, world):
+    """Device time from a resident sinogram to relative objective gap <= 1e-3.
+
+    gap(y_k) = (F(y_k) - F_ref) / (F(0) - F_ref) with F(0) = 1/2 g.g and F_ref the objective
+    after REF_ITERS fast-gradient iterations from the FBP start (FP32).  Each form is timed
+    from build_operator through the stop; the device ends the iterations at the gap.
+    """
+    import torch
+
+    ctx.build_operator(sino, atg)
+    ctx.fbp(sino, x)
+    st = ctx.reconstruct(x, atg, tm.Params(**PRIOR, max_iter=REF_ITERS))
+    log = ctx.get_log(REF_ITERS)
+    F_ref = st.objective
+    F0 = ctx.objective(torch.zeros_like(x), atg, tm.Params(**PRIOR))
+    half = log[REF_ITERS // 2 - 1][0]
+    out = {"gap": GAP, "F_ref": F_ref, "F_ref_iterations": REF_ITERS, "F0": F0,
+           "ref_change_last_half_in_gap_units": (half - F_ref) / (F0 - F_ref), "forms": {}}
+    forms = {
+        "plain": dict(use_graph=False, desc="FP32 spectra, FBP start, one level, no warm start, eager launches"),
+        "batched_graph": dict(use_graph=True, desc="FP32 spectra, FBP start, one level, device-driven graph loop"),
+    }
+    for name, f in forms.items():
+        prm = tm.Params(**PRIOR, max_iter=REF_ITERS, gap_tol=GAP, F_ref=F_ref, use_graph=f["use_graph"])
+        for timed in (False, True):
+            barrier()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.build_operator(sino, atg)
+            ctx.fbp(sino, x)
+            ctx.reconstruct(x, atg, prm, want_stats=False)
+            e1.record(stream)
+            barrier()
+        ms = e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([ms], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = float(t.item())
+        ctx.fbp(sino, x)
+        st = ctx.reconstruct(x, atg, prm)  # the same run again, for its stats
+        out["forms"][name] = {"ms": ms, "iterations": st.iterations, "gap_reached": st.gap, "form": f["desc"]}
+    return out
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -190,6 +238,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-graph", action="store_true", help="launch the iterations eagerly (profiling)")
+    ap.add_argument("--no-gap", action="store_true", help="skip the time-to-gap measurement")
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.impl == "reference":
@@ -213,7 +263,7 @@ def main():
     with torch.cuda.stream(stream):
         atg = torch.empty(S * N * N, dtype=torch.float32, device="cuda")
         x = torch.empty_like(atg)
-    prm = tm.Params(**PRIOR, max_iter=iters, use_graph=True)
+    prm = tm.Params(**PRIOR, max_iter=iters, use_graph=not args.no_graph)
     torch.cuda.synchronize()
 
     def step():
@@ -284,6 +334,8 @@ def main():
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         e2e_ms = float(t.item())
 
+    gap_info = None if args.no_gap else time_to_gap(tm, ctx, stream, sino, atg, x, barrier, world)
+
     if rank == 0:
         line = {
             "metric": METRIC,
@@ -315,6 +367,7 @@ def main():
             "e2e": {"value": world * vox * args.steps / (e2e_ms * 1e-3), "unit": "voxel-updates/s",
                     "h2d_bytes_per_step": sino.numel() * 4, "d2h_bytes_per_step": x.numel() * 4},
             "gpu_launches": launches,
+            "time_to_gap": gap_info,
             "clocks": clk,
             "last_run": {"objective": st.objective, "restarts": st.restarts, "L": st.L, "status": st.status},
         }

@@ -44,7 +44,7 @@ enum {
   TMBIR_ERR_STATE = -7      /* call order (no geometry, operator not built) */
 };
 
-enum { TMBIR_RESTART_GRADIENT = 0, TMBIR_RESTART_NONE = 1 };
+enum { TMBIR_RESTART_GRADIENT = 0, TMBIR_RESTART_NONE = 1, TMBIR_RESTART_FUNCTION = 2 };
 enum { TMBIR_SPECTRA_FP32 = 0, TMBIR_SPECTRA_BF16 = 1 };
 
 typedef struct tmbir_ctx tmbir_ctx;
@@ -78,8 +78,14 @@ typedef struct {
  *   max_iter        iterations of the fast gradient method.
  *   gap_tol, F_ref  stop early once (F(y_k) - F_ref) / (F(0) - F_ref) <= gap_tol
  *                   (gap_tol <= 0 disables it).
- *   restart         TMBIR_RESTART_GRADIENT: momentum restarts when <grad F(y_k), x_{k+1}-x_k> > 0.
- *   use_graph       capture the iterations in a CUDA graph and replay it.
+ *   restart         TMBIR_RESTART_GRADIENT: momentum restarts when <grad F(y_k), x_{k+1}-x_k> > 0;
+ *                   TMBIR_RESTART_FUNCTION: when F(y_k) > F(y_{k-1}); TMBIR_RESTART_NONE: never
+ *                   (the restart rule is not stated in the paper; Sec. 2 cites the restarted
+ *                   fast gradient method).
+ *   use_graph       run the iterations as one CUDA graph: a device-driven WHILE loop whose body
+ *                   is one iteration; the device stops it at max_iter or the gap tolerance, so
+ *                   no launch is spent after the stop.  The executable graph is cached and
+ *                   reused while the image and R*g buffers and the prior stay the same.
  */
 typedef struct {
   double p, q, c, sigma, lambda;
@@ -202,7 +208,11 @@ int tmbir_downsample_sino(tmbir_ctx* ctx, const float* d_sino, int n_slices, int
  */
 int tmbir_pass_times(tmbir_ctx* ctx, float* d_x, const float* d_atg, const tmbir_params* prm, int iters, double* h_ms);
 
-/* Number of kernels this context has launched so far (graph replays count their kernel nodes). */
+/*
+ * Number of library kernels launched so far: the host-side count of every launch by this
+ * process plus the kernels this context ran inside device-driven graph loops (counted by the
+ * loop's finalize kernel; reading it synchronises the context stream).
+ */
 int tmbir_launch_count(const tmbir_ctx* ctx, long long* h_count);
 
 /*

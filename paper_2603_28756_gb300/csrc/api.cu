@@ -258,6 +258,7 @@ int tmbir_set_workspace(tmbir_ctx* ctx, void* d_ws, size_t bytes) {
   c.xbuf[0] = reinterpret_cast<float*>(ws + c.off_xbuf0);
   c.xbuf[1] = reinterpret_cast<float*>(ws + c.off_xbuf1);
   c.scratch = ws + c.off_scratch;
+  TMBIR_CUDA(cudaMemsetAsync(c.state, 0, sizeof(IterState), c.stream));
   for (size_t i = 0; i < c.groups.size(); ++i) {
     const tmbir_group& g = c.groups[i];
     GroupDev& d = c.gdev[i];
@@ -324,6 +325,8 @@ static int check_params(const tmbir_params* p) {
   if (!(p->p >= 1.0 && p->q >= p->p && p->q <= 4.0)) return set_error(TMBIR_ERR_ARG, "need 1 <= p <= q <= 4");
   if (!(p->c > 0.0 && p->sigma > 0.0 && p->lambda >= 0.0)) return set_error(TMBIR_ERR_ARG, "need c > 0, sigma > 0, lambda >= 0");
   if (p->L <= 0.0 && p->q != 2.0) return set_error(TMBIR_ERR_ARG, "automatic L needs q = 2; pass L > 0");
+  if (p->restart != TMBIR_RESTART_GRADIENT && p->restart != TMBIR_RESTART_NONE && p->restart != TMBIR_RESTART_FUNCTION)
+    return set_error(TMBIR_ERR_ARG, "unknown restart mode");
   return TMBIR_OK;
 }
 
@@ -366,7 +369,9 @@ int tmbir_fbp(tmbir_ctx* ctx, const float* d_sino, float* d_x0) {
   return TMBIR_OK;
 }
 
-static int enqueue_iterations(Ctx& c, float* d_x, const float* d_atg, const PriorC& pc, int iters) {
+// iters iterations on the context stream; with use_cond, one trip of a device-driven graph loop
+static int enqueue_iterations(Ctx& c, float* d_x, const float* d_atg, const PriorC& pc, int iters,
+                              cudaGraphConditionalHandle cond = 0, int use_cond = 0) {
   StepArgs a{};
   a.atg = d_atg;
   a.xb[0] = d_x;
@@ -382,8 +387,49 @@ static int enqueue_iterations(Ctx& c, float* d_x, const float* d_atg, const Prio
       if (int e = launch_pass3(g, a, Pass3Mode::Iterate, pc, c.partials, off, c.stream)) return e;
       off += blocks_pass3(g);
     }
-    if (int e = launch_finalize(c.state, c.partials, off, c.log, c.stream)) return e;
+    const int trip_launches = 3 * (int)c.gdev.size() + 1;
+    if (int e = launch_finalize(c.state, c.partials, off, c.log, c.stream, cond, use_cond, trip_launches)) return e;
   }
+  return TMBIR_OK;
+}
+
+// One executable graph: a WHILE node whose body is one iteration (passes 1-3 of every group and
+// the finalize kernel, which clears the condition when the run is done).
+static int build_loop_graph(Ctx& c, float* d_x, const float* d_atg, const PriorC& pc) {
+  cudaGraph_t gr = nullptr;
+  TMBIR_CUDA(cudaGraphCreate(&gr, 0));
+  auto fail = [&](int e) {
+    cudaGraphDestroy(gr);
+    return e;
+  };
+  cudaGraphConditionalHandle h;
+  if (cudaGraphConditionalHandleCreate(&h, gr, 1, cudaGraphCondAssignDefault) != cudaSuccess)
+    return fail(set_error(TMBIR_ERR_CUDA, "graph: conditional handle"));
+  cudaGraphNodeParams np{};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  if (cudaGraphAddNode(&node, gr, nullptr, nullptr, 0, &np) != cudaSuccess)
+    return fail(set_error(TMBIR_ERR_CUDA, "graph: conditional node"));
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+  if (cudaStreamBeginCaptureToGraph(c.stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) !=
+      cudaSuccess)
+    return fail(set_error(TMBIR_ERR_CUDA, "graph: begin capture"));
+  const long long n0 = __atomic_load_n(&g_launches, __ATOMIC_RELAXED);
+  int e = enqueue_iterations(c, d_x, d_atg, pc, 1, h, 1);
+  cudaGraph_t captured = nullptr;
+  cudaError_t ce = cudaStreamEndCapture(c.stream, &captured);
+  // captured launches run on replay, where the finalize kernel counts them on the device
+  __atomic_sub_fetch(&g_launches, __atomic_load_n(&g_launches, __ATOMIC_RELAXED) - n0, __ATOMIC_RELAXED);
+  if (e) return fail(e);
+  if (ce != cudaSuccess) return fail(set_error(TMBIR_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce)));
+  if (cudaGraphInstantiate(&c.graph_exec, gr, 0) != cudaSuccess) {
+    c.graph_exec = nullptr;
+    return fail(set_error(TMBIR_ERR_CUDA, "graph: instantiate"));
+  }
+  cudaGraphDestroy(gr);
   return TMBIR_OK;
 }
 
@@ -409,33 +455,22 @@ int tmbir_reconstruct(tmbir_ctx* ctx, float* d_x, const float* d_atg, const tmbi
   TMBIR_CUDA(cudaMemcpyAsync(c.xbuf[1], d_x, c.total_voxels * sizeof(float), cudaMemcpyDeviceToDevice, s));
   const int iters = prm->max_iter;
   bool graph = prm->use_graph != 0 && s != nullptr;
-  if (graph) {
-    const bool reuse = c.graph_exec && c.graph_iters == iters && c.graph_x == d_x && c.graph_atg == d_atg &&
+  if (iters == 0) {
+    // nothing to iterate
+  } else if (graph) {
+    const bool reuse = c.graph_exec && c.graph_x == d_x && c.graph_atg == d_atg &&
                        std::memcmp(&c.graph_prior, &pc, sizeof(PriorC)) == 0;
     if (!reuse) {
       if (c.graph_exec) {
         cudaGraphExecDestroy(c.graph_exec);
         c.graph_exec = nullptr;
       }
-      cudaGraph_t gr;
-      const long long n0 = __atomic_load_n(&g_launches, __ATOMIC_RELAXED);
-      TMBIR_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-      int e = enqueue_iterations(c, d_x, d_atg, pc, iters);
-      cudaError_t ce = cudaStreamEndCapture(s, &gr);
-      // captured launches run only on replay: count them there
-      c.graph_nodes = __atomic_load_n(&g_launches, __ATOMIC_RELAXED) - n0;
-      __atomic_sub_fetch(&g_launches, c.graph_nodes, __ATOMIC_RELAXED);
-      if (e) return e;
-      if (ce != cudaSuccess) return set_error(TMBIR_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
-      TMBIR_CUDA(cudaGraphInstantiate(&c.graph_exec, gr, 0));
-      cudaGraphDestroy(gr);
-      c.graph_iters = iters;
+      if (int e = build_loop_graph(c, d_x, d_atg, pc)) return e;
       c.graph_x = d_x;
       c.graph_atg = d_atg;
       c.graph_prior = pc;
     }
     TMBIR_CUDA(cudaGraphLaunch(c.graph_exec, s));
-    __atomic_add_fetch(&g_launches, c.graph_nodes, __ATOMIC_RELAXED);
   } else {
     if (int e = enqueue_iterations(c, d_x, d_atg, pc, iters)) return e;
   }
@@ -672,7 +707,14 @@ int tmbir_pass_times(tmbir_ctx* ctx, float* d_x, const float* d_atg, const tmbir
 
 int tmbir_launch_count(const tmbir_ctx* ctx, long long* h_count) {
   REQUIRE(ctx != nullptr && h_count != nullptr, TMBIR_ERR_ARG, "launch_count: NULL argument");
-  *h_count = __atomic_load_n(&g_launches, __ATOMIC_RELAXED);
+  long long dev = 0;
+  const Ctx& c = ctx->c;
+  if (c.state) {
+    // kernels run inside device-driven graph loops are counted on the device
+    TMBIR_CUDA(cudaMemcpyAsync(&dev, &c.state->graph_launches, sizeof(long long), cudaMemcpyDeviceToHost, c.stream));
+    TMBIR_CUDA(cudaStreamSynchronize(c.stream));
+  }
+  *h_count = __atomic_load_n(&g_launches, __ATOMIC_RELAXED) + dev;
   return TMBIR_OK;
 }
 

@@ -28,6 +28,8 @@ struct IterState {
   int status;
   int restart_mode;
   int log_cap;
+  double prev_F;             // F(y_{k-1}), for the function-value restart
+  long long graph_launches;  // kernels run by device-driven graph trips, cumulative (zeroed at workspace binding)
 };
 
 // Number of FP64 partial sums each reducing block writes.
@@ -107,11 +109,9 @@ struct Ctx {
   size_t off_state = 0, off_partials = 0, off_log = 0, off_xbuf0 = 0, off_xbuf1 = 0, off_scratch = 0, off_dscal = 0;
   // CUDA graph cache for reconstruct
   cudaGraphExec_t graph_exec = nullptr;
-  int graph_iters = -1;
   const float* graph_atg = nullptr;
   float* graph_x = nullptr;
   PriorC graph_prior{};
-  long long graph_nodes = 0;
 };
 
 // error handling ------------------------------------------------------------
@@ -158,7 +158,10 @@ inline int pass3_slices_per_block(int S, int row_blocks) {
   if (chunks > S) chunks = S;
   return (S + chunks - 1) / chunks;
 }
-int launch_finalize(IterState* st, const double* partials, int nblocks, double* log, cudaStream_t s);
+// cond: the WHILE handle of a device-driven graph loop (use_cond != 0), set to 0 once the run
+// is done; trip_launches: kernels of one loop trip, added to IterState::graph_launches.
+int launch_finalize(IterState* st, const double* partials, int nblocks, double* log, cudaStream_t s,
+                    cudaGraphConditionalHandle cond = 0, int use_cond = 0, int trip_launches = 0);
 int launch_sum_partials(const double* partials, int nblocks, double* out, cudaStream_t s);
 bool supported_N(int N);
 void fft_shape(int N, int* T, int* P);

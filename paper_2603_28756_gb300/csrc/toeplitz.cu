@@ -51,14 +51,24 @@ __global__ void __launch_bounds__(512) k_sum_partials(const double* partials, in
   reduce_blocks(partials, nblocks, out);
 }
 
-__global__ void __launch_bounds__(512) k_finalize(IterState* st, const double* partials, int nblocks, double* log) {
+// Reduces the partial sums of one iteration and advances the momentum state (Eq. 6 with the
+// restart test).  Inside a device-driven graph loop it also sets the loop's condition: 0 once
+// the run is done (every path sets it, so the loop always ends by max_iter).
+__global__ void __launch_bounds__(512) k_finalize(IterState* st, const double* partials, int nblocks, double* log,
+                                                  cudaGraphConditionalHandle cond, int use_cond, int trip_launches) {
   __shared__ double S[kParts];
-  if (st->done) return;
+  if (st->done) {
+    if (use_cond && threadIdx.x == 0) cudaGraphSetConditional(cond, 0);
+    return;
+  }
   reduce_blocks(partials, nblocks, S);
   if (threadIdx.x != 0) return;
   const double yz = S[0], yatg = S[1], phi = S[2], gdx = S[3], gg = S[4];
   const double F = 0.5 * yz - yatg + st->gtg_half + st->lambda * phi;
-  const bool restart = st->restart_mode == TMBIR_RESTART_GRADIENT && gdx > 0.0;
+  // gradient restart: <grad F(y_k), x_{k+1} - x_k> > 0; function restart: F(y_k) > F(y_{k-1})
+  const bool restart = (st->restart_mode == TMBIR_RESTART_GRADIENT && gdx > 0.0) ||
+                       (st->restart_mode == TMBIR_RESTART_FUNCTION && st->k > 0 && F > st->prev_F);
+  st->prev_F = F;
   const int k = st->k;
   if (k < st->log_cap) {
     log[4 * k + 0] = F;
@@ -85,6 +95,10 @@ __global__ void __launch_bounds__(512) k_finalize(IterState* st, const double* p
   }
   if (k + 1 >= st->max_iter) st->done = 1;
   if (st->gap_tol > 0.0 && gap <= st->gap_tol) st->done = 1;
+  if (use_cond) {
+    st->graph_launches += trip_launches;
+    cudaGraphSetConditional(cond, st->done ? 0 : 1);
+  }
 }
 
 #define TMBIR_DISPATCH_N(N_, FN, ...)                               \
@@ -111,8 +125,9 @@ int blocks_pass3(const GroupDev& g) {
   return nb * ((g.S + zc - 1) / zc);
 }
 
-int launch_finalize(IterState* st, const double* partials, int nblocks, double* log, cudaStream_t s) {
-  k_finalize<<<1, 512, 0, s>>>(st, partials, nblocks, log);
+int launch_finalize(IterState* st, const double* partials, int nblocks, double* log, cudaStream_t s,
+                    cudaGraphConditionalHandle cond, int use_cond, int trip_launches) {
+  k_finalize<<<1, 512, 0, s>>>(st, partials, nblocks, log, cond, use_cond, trip_launches);
   TMBIR_CHECK_LAUNCH();
   return TMBIR_OK;
 }

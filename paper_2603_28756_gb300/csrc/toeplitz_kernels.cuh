@@ -70,27 +70,55 @@ __device__ __forceinline__ float rcp_newton(float x) {
   return r;
 }
 
-// rho'(d) (and rho(d) when PHI) of the qGGMRF potential
-//   rho(d)  = |d/sigma|^q / (1 + u),            u = |d/(c sigma)|^(q-p)
+// Packed FP32 pairs: one instruction computes both lanes of a float2 (sm_100 and later).
+__device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 f2mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 f2add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+
+// Constants of the qGGMRF potential in the form the packed neighbour term uses.
+struct PriorK {
+  float2 half_qp;  // (q - p) / 2
+  float2 qp_l2;    // (q - p) log2(1 / (c sigma))
+  float2 p, qmp;   // p, q - p
+  float2 half_q2;  // (q - 2) / 2
+  float2 q2_l2;    // (q - 2) log2(1 / sigma)
+};
+__device__ __forceinline__ PriorK prior_k(const PriorC& c) {
+  PriorK k;
+  k.half_qp = f2(0.5f * c.qp);
+  k.qp_l2 = f2(c.qp_l2_inv_csig);
+  k.p = f2(c.p);
+  k.qmp = f2(c.qp);
+  k.half_q2 = f2(0.5f * (c.q - 2.0f));
+  k.q2_l2 = f2((c.q - 2.0f) * c.l2_inv_sig);
+  return k;
+}
+
+// One neighbour term of the qGGMRF potential for two voxels at once (the two lanes):
+//   rho(d)  = |d/sigma|^q / (1 + u),  u = |d/(c sigma)|^(q-p),  r = 1 / (1 + u)
 //   rho'(d) = d/sigma^2 |d/sigma|^(q-2) (q + p u) / (1 + u)^2
-// Returns rho'(d) * sigma^2 (the caller folds 1/sigma^2 into the neighbour weight) and, when
-// PHI, rho(d) * sigma^2.  Three special-function operations per call (log2, exp2, reciprocal).
-template <bool Q2, bool PHI>
-__device__ __forceinline__ float drho(float d, const PriorC& c, float& rho) {
-  const float a = fmaxf(fabsf(d), 1e-30f);
-  const float la = lg2a(a);
-  const float u = ex2a(fmaf(c.qp, la, c.qp_l2_inv_csig));
-  const float r = rcpa(1.0f + u);
-  if constexpr (Q2) {
-    const float dr = d * r;
-    if constexpr (PHI) rho = d * dr;
-    return dr * r * fmaf(c.p, u, 2.0f);
-  } else {
-    const float aq2 = ex2a((c.q - 2.0f) * (la + c.l2_inv_sig));
-    const float dr = d * r * aq2;
-    if constexpr (PHI) rho = d * dr;
-    return dr * r * fmaf(c.p, u, c.q);
+//           = d/sigma^2 |d/sigma|^(q-2) r (p + (q - p) r)
+// g += sigma^2 rho'(d) and, when phi, ph += sigma^2 rho(d) (the caller folds 1/sigma^2 into
+// the neighbour weight).  u comes from log2(d^2 + 1e-30), which stays finite at d = 0 (there
+// r = 1 and both terms vanish).  Three special-function operations per lane (log2, exp2,
+// reciprocal), four for q != 2.
+template <bool Q2>
+__device__ __forceinline__ void nbr2(float2 y, float2 nb, const PriorK& k, float2& g, float2& ph, bool phi) {
+  const float2 d = f2fma(nb, f2(-1.f), y);
+  const float2 sq = f2fma(d, d, f2(1e-30f));
+  const float2 la = make_float2(lg2a(sq.x), lg2a(sq.y));
+  const float2 s = f2fma(k.half_qp, la, k.qp_l2);
+  const float2 e = f2add(make_float2(ex2a(s.x), ex2a(s.y)), f2(1.f));
+  const float2 r = make_float2(rcpa(e.x), rcpa(e.y));
+  const float2 t = f2fma(k.qmp, r, k.p);
+  float2 dr = f2mul(d, r);
+  if constexpr (!Q2) {
+    const float2 s2 = f2fma(k.half_q2, la, k.q2_l2);
+    dr = f2mul(dr, make_float2(ex2a(s2.x), ex2a(s2.y)));
   }
+  g = f2fma(dr, t, g);
+  if (phi) ph = f2fma(d, dr, ph);
 }
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -327,8 +355,12 @@ __global__ void __launch_bounds__(Geo3<N>::THREADS, 2)
   float* kzs = reinterpret_cast<float*>(sm);  // K(*)y of the block rows, [RB][N], after the transforms
   float* ring = reinterpret_cast<float*>(reinterpret_cast<char*>(sm) + G3::SM_A);
   const size_t N2 = (size_t)N * N;
-  // neighbour weights with 1/sigma^2 folded in: drho returns sigma^2 rho' and sigma^2 rho
-  const float wts[4] = {0.f, pc.wf * pc.inv_sig2, pc.we * pc.inv_sig2, pc.wc * pc.inv_sig2};
+  // neighbour weights with 1/sigma^2 folded in: nbr2 sums sigma^2 rho' and sigma^2 rho
+  const float2 wf = f2(pc.wf * pc.inv_sig2), we = f2(pc.we * pc.inv_sig2), wc = f2(pc.wc * pc.inv_sig2);
+  const float2 lam = f2(pc.lam);
+  const PriorK pk = prior_k(pc);
+  constexpr int H = N / 2;
+  static_assert(H % 32 == 0, "a warp must cover one row segment");
 
   double dacc[kParts];
 #pragma unroll
@@ -379,30 +411,38 @@ __global__ void __launch_bounds__(Geo3<N>::THREADS, 2)
     }
     __syncthreads();
 
-    // ---- per voxel: prior, gradient, update, partial sums
+    // ---- per voxel: prior, gradient, update, partial sums.  A thread takes the voxels in
+    // columns c and c + N/2 of one block row as the two lanes of packed FP32 pairs (a warp
+    // covers 32 consecutive c of one row, so the row and slice tests are warp-uniform).
     const float* sz[3] = {ring + ((z + 2) % 3) * ROWS * N, ring + (z % 3) * ROWS * N, ring + ((z + 1) % 3) * ROWS * N};
     const bool zval0 = z > 0, zval2 = z + 1 < g.S;
-    float acc[kParts];
+    float2 acc[kParts];
 #pragma unroll
-    for (int j = 0; j < kParts; ++j) acc[j] = 0.f;
-    auto voxel = [&](int v) {
-      const int row = v / N, col = v - row * N;  // block row, column (a warp covers one row)
+    for (int j = 0; j < kParts; ++j) acc[j] = f2(0.f);
+#pragma unroll 1
+    for (int i = threadIdx.x; i < RB * H; i += G3::THREADS) {
+      const int row = i / H, c = i - row * H;
       const int grow = r0 + row;
-      const size_t idx = slice_base + (size_t)grow * N + col;
-      const float zd = kzs[row * N + col];
+      const size_t ia = slice_base + (size_t)grow * N + c, ib = ia + H;
+      const float2 zd = make_float2(kzs[row * N + c], kzs[row * N + c + H]);
       if constexpr (!PRIOR) {
-        const float xv = __ldg(x + idx);
-        out[idx] = zd;
-        acc[0] += xv * zd;
-        acc[5] += zd * zd;
+        const float2 xv = make_float2(__ldg(x + ia), __ldg(x + ib));
+        out[ia] = zd.x;
+        out[ib] = zd.y;
+        acc[0] = f2fma(xv, zd, acc[0]);
+        acc[5] = f2fma(zd, zd, acc[5]);
       } else {
-        float at = 0.f, xv = 0.f;
-        at = __ldg(a.atg + idx);
-        if constexpr (UPDATE) xv = __ldg(x + idx);
-        const float yv = sz[1][(row + 1) * N + col];
-        const float mL = col > 0 ? 1.f : 0.f, mR = col + 1 < N ? 1.f : 0.f;
-        const int cl = col > 0 ? col - 1 : col, cr = col + 1 < N ? col + 1 : col;
-        float gp = 0.f, ph = 0.f;
+        const float2 at = make_float2(__ldg(a.atg + ia), __ldg(a.atg + ib));
+        float2 xv = f2(0.f);
+        if constexpr (UPDATE) xv = make_float2(__ldg(x + ia), __ldg(x + ib));
+        const float* ry = sz[1] + (row + 1) * N;
+        const float2 yv = make_float2(ry[c], ry[c + H]);
+        // missing neighbours (free boundary) read the voxel itself: d = 0 adds nothing
+        const bool hasL = c > 0, hasR = c + 1 < H;  // column 0 (lane x), column N - 1 (lane y)
+        const int cl = hasL ? c - 1 : c, cr = hasR ? c + H + 1 : c + H;
+        float2 gp[3], ph[3];  // by neighbour class: face, edge, corner
+#pragma unroll
+        for (int j = 0; j < 3; ++j) gp[j] = ph[j] = f2(0.f);
 #pragma unroll
         for (int dz = 0; dz < 3; ++dz) {
           if ((dz == 0 && !zval0) || (dz == 2 && !zval2)) continue;
@@ -410,42 +450,34 @@ __global__ void __launch_bounds__(Geo3<N>::THREADS, 2)
           for (int dy = 0; dy < 3; ++dy) {
             if ((dy == 0 && grow == 0) || (dy == 2 && grow + 1 == N)) continue;
             const float* rp = sz[dz] + (row + dy) * N;
-            const int ring_n = (dz != 1) + (dy != 1);
-            const bool fwd_plane = dz > 1 || (dz == 1 && dy > 1);
-#pragma unroll
-            for (int dx = 0; dx < 3; ++dx) {
-              if (dz == 1 && dy == 1 && dx == 1) continue;
-              const float nb = rp[dx == 0 ? cl : (dx == 1 ? col : cr)];
-              const float m = dx == 0 ? mL : (dx == 2 ? mR : 1.f);
-              const float w = wts[ring_n + (dx != 1)] * m;
-              float rh = 0.f;
-              gp = fmaf(w, drho<Q2, PHI>(yv - nb, pc, rh), gp);
-              if (PHI && (fwd_plane || (dz == 1 && dy == 1 && dx == 2))) ph = fmaf(w, rh, ph);
-            }
+            const int cls = (dz != 1) + (dy != 1);  // class of the dx = -1, +1 neighbours
+            const bool fwd = dz > 1 || (dz == 1 && dy > 1);
+            const float2 nbL = make_float2(hasL ? rp[cl] : yv.x, rp[c + H - 1]);
+            const float2 nbR = make_float2(rp[c + 1], hasR ? rp[cr] : yv.y);
+            if (cls > 0) nbr2<Q2>(yv, make_float2(rp[c], rp[c + H]), pk, gp[cls - 1], ph[cls - 1], PHI && fwd);
+            nbr2<Q2>(yv, nbL, pk, gp[cls], ph[cls], PHI && fwd);
+            nbr2<Q2>(yv, nbR, pk, gp[cls], ph[cls], PHI && (fwd || cls == 0));
           }
         }
-        const float Gv = zd - at + pc.lam * gp;
-        acc[0] += yv * zd;
-        acc[1] += yv * at;
-        acc[2] += ph;
-        acc[4] += Gv * Gv;
+        const float2 gpv = f2fma(wc, gp[2], f2fma(we, gp[1], f2mul(wf, gp[0])));
+        const float2 Gv = f2fma(lam, gpv, f2fma(at, f2(-1.f), zd));
+        acc[0] = f2fma(yv, zd, acc[0]);
+        acc[1] = f2fma(yv, at, acc[1]);
+        if constexpr (PHI) acc[2] = f2add(acc[2], f2fma(wc, ph[2], f2fma(we, ph[1], f2mul(wf, ph[0]))));
+        acc[4] = f2fma(Gv, Gv, acc[4]);
         if constexpr (MODE == (int)Pass3Mode::Gradient) {
-          out[idx] = Gv;
+          out[ia] = Gv.x;
+          out[ib] = Gv.y;
         } else if constexpr (UPDATE) {
-          const float xn = fmaf(-invL, Gv, yv);
-          out[idx] = xn;
-          acc[3] += Gv * (xn - xv);
+          const float2 xn = f2fma(f2(-invL), Gv, yv);
+          out[ia] = xn.x;
+          out[ib] = xn.y;
+          acc[3] = f2fma(Gv, f2fma(xv, f2(-1.f), xn), acc[3]);
         }
       }
-    };
-    // two voxels per trip (half a block apart) for instruction-level parallelism
-#pragma unroll 1
-    for (int v = threadIdx.x; v < RB * N; v += 2 * G3::THREADS) {
-      voxel(v);
-      if (v + G3::THREADS < RB * N) voxel(v + G3::THREADS);
     }
 #pragma unroll
-    for (int j = 0; j < kParts; ++j) dacc[j] += (double)acc[j];
+    for (int j = 0; j < kParts; ++j) dacc[j] += (double)acc[j].x + (double)acc[j].y;
   }
   block_partials<G3::W>(dacc, red, partials + (size_t)(block_offset + blockIdx.x) * kParts);
 }

@@ -155,6 +155,59 @@ def test_graph_replay_is_bitwise_eager(prob):
     assert torch.equal(a, c)
 
 
+RESTART = {"gradient": 0, "none": 1, "function": 2}
+
+
+@pytest.mark.parametrize("mode", ["function", "none"])
+def test_restart_modes_follow_oracle(prob, orc, mode):
+    pr = orc.Prior(**PRIOR)
+    iters = 30
+    x = torch.zeros(prob.x.size, dtype=torch.float32, device="cuda")
+    st = prob.ctx.reconstruct(x, prob.d_atg, tm.Params(**PRIOR, max_iter=iters, restart=RESTART[mode]))
+    assert st.iterations == iters and st.status == 0
+    log = prob.ctx.get_log()
+    L = orc.lipschitz(prob.K, prob.N, pr)
+    olog = []
+    ref = orc.nesterov(np.zeros(prob.x.shape), prob.atg, float(np.sum(prob.g ** 2)), prob.K, pr, L, iters, log=olog,
+                       restart=mode)
+    assert rel(host(x, prob.x.shape), ref) < 1e-4
+    F0 = 0.5 * float(np.sum(prob.g ** 2))
+    for k, ((F, dot, rs, gg), (Fo, doto, rso)) in enumerate(zip(log, olog)):
+        assert abs(F - Fo) <= 1e-7 * F0
+        if mode == "none":
+            assert not rs
+        elif k > 0 and abs(Fo - olog[k - 1][0]) > 1e-6 * F0:
+            assert bool(rs) == rso
+
+
+def test_device_loop_stops_at_gap(prob):
+    # F_ref from a longer run; the device-driven graph loop and the eager launches must stop
+    # at the same iteration with bitwise equal iterates, and no kernel runs after the stop
+    x = torch.zeros(prob.x.size, dtype=torch.float32, device="cuda")
+    F_ref = prob.ctx.reconstruct(x, prob.d_atg, tm.Params(**PRIOR, max_iter=200)).objective
+    prm = dict(PRIOR, max_iter=200, gap_tol=1e-2, F_ref=F_ref)
+    a = torch.zeros_like(x)
+    b = torch.zeros_like(x)
+    n0 = prob.ctx.launch_count()
+    sa = prob.ctx.reconstruct(a, prob.d_atg, tm.Params(**prm, use_graph=True))
+    n1 = prob.ctx.launch_count()
+    sb = prob.ctx.reconstruct(b, prob.d_atg, tm.Params(**prm, use_graph=False))
+    torch.cuda.synchronize()
+    assert 1 < sa.iterations == sb.iterations < 200
+    assert torch.equal(a, b)
+    # state init + 4 kernels per iteration (passes 1-3, finalize) + final gather
+    assert n1 - n0 == 4 * sa.iterations + 2
+    log = prob.ctx.get_log()
+    F0 = 0.5 * float(np.sum(prob.g ** 2))
+    gaps = [(F - F_ref) / (F0 - F_ref) for F, _, _, _ in log]
+    assert len(gaps) == sb.iterations and gaps[-1] <= 1e-2 < gaps[-2]
+    # a replay of the cached graph with another stop rule reuses it
+    a.zero_()
+    n2 = prob.ctx.launch_count()
+    sc = prob.ctx.reconstruct(a, prob.d_atg, tm.Params(**dict(prm, gap_tol=0.0, max_iter=5), use_graph=True))
+    assert sc.iterations == 5 and prob.ctx.launch_count() - n2 == 4 * 5 + 2
+
+
 def test_uneven_groups_equal_separate_contexts(orc):
     specs = [(64, 2, 30), (128, 1, 50), (64, 1, 20)]
     groups, sinos, thetas, ctxs = [], [], [], []
