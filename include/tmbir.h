@@ -53,7 +53,7 @@ typedef struct tmbir_ctx tmbir_ctx;
  * One geometry group: n_slices slices of N x N pixels seen under the same n_angles
  * parallel-beam angles by n_det detector bins (Sec. 2, Eq. 1).  Slices of a group are
  * coupled by the 3D prior; different groups are independent.
- *   N        image side; 64 <= N <= 1024 and a power of two.
+ *   N        image side; 64 <= N <= 2048 and a power of two.
  *   n_det    detector bins; must equal N (pixel pitch = bin pitch).
  *   angles   host array of n_angles radians; copied by tmbir_set_geometry.
  *   span     angular range covered by the angles (pi for a full half turn); the FBP
@@ -86,6 +86,13 @@ typedef struct {
  *                   is one iteration; the device stops it at max_iter or the gap tolerance, so
  *                   no launch is spent after the stop.  The executable graph is cached and
  *                   reused while the image and R*g buffers and the prior stay the same.
+ *   spectra         storage of the padded intermediate spectrum during the iterations:
+ *                   TMBIR_SPECTRA_FP32, or TMBIR_SPECTRA_BF16 (half the bytes; transforms,
+ *                   kernel multiply and prior still in FP32).  Not a paper setting: the paper
+ *                   computes in FP32 throughout (Sec. 3.1).
+ *   refine_gap      with BF16 spectra: switch to FP32 spectra for the remaining iterations
+ *                   once the relative gap (as for gap_tol) is <= refine_gap; 0 keeps BF16 to
+ *                   the end.
  */
 typedef struct {
   double p, q, c, sigma, lambda;
@@ -95,6 +102,8 @@ typedef struct {
   double F_ref;
   int restart;
   int use_graph;
+  int spectra;
+  double refine_gap;
 } tmbir_params;
 
 /* Result of tmbir_reconstruct (host struct filled on return). */

@@ -13,7 +13,7 @@ from dataclasses import dataclass, field
 
 from .build import LIB, build  # noqa: F401
 
-__all__ = ["CNN", "Context", "Group", "Params", "Stats", "TmbirError", "load", "SYMBOLS", "build"]
+__all__ = ["CNN", "Context", "Group", "Params", "Stats", "TmbirError", "load", "SYMBOLS", "build", "reconstruct_levels"]
 
 TMBIR_OK = 0
 ERRORS = {
@@ -57,6 +57,8 @@ class _Params(ctypes.Structure):
         ("F_ref", ctypes.c_double),
         ("restart", ctypes.c_int),
         ("use_graph", ctypes.c_int),
+        ("spectra", ctypes.c_int),
+        ("refine_gap", ctypes.c_double),
     ]
 
 
@@ -172,10 +174,12 @@ class Params:
     F_ref: float = 0.0
     restart: int = 0
     use_graph: bool = True
+    bf16: bool = False  # BF16 storage of the intermediate spectrum
+    refine_gap: float = 0.0  # with bf16: switch to FP32 spectra once the gap is <= refine_gap
 
     def c_struct(self) -> _Params:
         return _Params(self.p, self.q, self.c, self.sigma, self.lam, self.L, self.max_iter, self.gap_tol, self.F_ref,
-                       self.restart, 1 if self.use_graph else 0)
+                       self.restart, 1 if self.use_graph else 0, 1 if self.bf16 else 0, self.refine_gap)
 
 
 @dataclass
@@ -404,6 +408,43 @@ class Context:
             self.close()
         except Exception:
             pass
+
+
+def reconstruct_levels(N: int, angles, n_slices: int, sino, levels: int, params, span: float = math.pi,
+                       stream=None, device="cuda", start=None):
+    """Hierarchical reconstruction (Sec. 2.3) through the C ABI.
+
+    Level l = 0 .. levels-1 reconstructs n_slices slices of N / 2^(levels-1-l) pixels.  A
+    level's sinogram keeps every angle and every f-th detector bin about the centre bin,
+    divided by f (tmbir_downsample_sino, f = 2^(levels-1-l)); the coarsest level starts from
+    its FBP image (or from `start`, a callable (ctx, sino_l, atg_l) -> image), every finer
+    level from the Lanczos-3 x2 upsampling of the level below (tmbir_upsample_lanczos3).
+    `params` is one Params per level.  All levels share one stream.  Returns the finest
+    image, the level contexts and the per-level Stats.
+    """
+    import torch
+
+    if len(params) != levels:
+        raise ValueError("one Params per level")
+    if N % (1 << (levels - 1)):
+        raise ValueError("N must be divisible by 2^(levels-1)")
+    stream = stream if stream is not None else torch.cuda.Stream(device=torch.device(device))
+    na = len(angles)
+    ctxs, stats = [], []
+    x = None
+    for lev in range(levels):
+        f = 1 << (levels - 1 - lev)
+        Nl = N // f
+        ctx = Context([Group(N=Nl, angles=list(angles), n_slices=n_slices, span=span)], stream=stream, device=device)
+        sino_l = sino if f == 1 else ctx.downsample_sino(sino, n_slices, na, N, f)
+        atg = ctx.build_operator(sino_l)
+        if x is None:
+            x = start(ctx, sino_l, atg) if start is not None else ctx.fbp(sino_l)
+        else:
+            x = ctx.upsample_lanczos3(x, n_slices, Nl // 2)
+        stats.append(ctx.reconstruct(x, atg, params[lev]))
+        ctxs.append(ctx)
+    return x, ctxs, stats
 
 
 class CNN:

@@ -43,7 +43,8 @@ static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 // ---------------------------------------------------------------- small device kernels
 // lam_max[i], gtg[i]: per-group lambda_max(R*R) and 1/2 g.g gathered into consecutive doubles
 __global__ void k_init_state(IterState* st, const double* lam_max, const double* gtg, int n_groups, double L_given,
-                             double lambda, double sigma, double Fref, double gap_tol, int max_iter, int restart_mode) {
+                             double lambda, double sigma, double Fref, double gap_tol, int max_iter, int restart_mode,
+                             int bf16, double refine_gap) {
   double lm = 0.0, gh = 0.0;
   for (int i = 0; i < n_groups; ++i) {
     lm = fmax(lm, lam_max[i]);
@@ -68,6 +69,9 @@ __global__ void k_init_state(IterState* st, const double* lam_max, const double*
   st->status = 0;
   st->restart_mode = restart_mode;
   st->log_cap = kLogCap;
+  st->prev_F = 0.0;
+  st->bf16 = bf16;
+  st->refine_gap = refine_gap;
 }
 
 // copy the current iterate back into slot 0 (the caller's buffer) when the rotation ended elsewhere
@@ -125,7 +129,7 @@ int tmbir_set_geometry(tmbir_ctx* ctx, int n_groups, const tmbir_group* groups) 
   std::vector<std::vector<double>> angs(n_groups);
   for (int i = 0; i < n_groups; ++i) {
     const tmbir_group& g = gs[i];
-    REQUIRE(supported_N(g.N), TMBIR_ERR_SHAPE, "set_geometry: N must be a power of two in [64, 1024]");
+    REQUIRE(supported_N(g.N), TMBIR_ERR_SHAPE, "set_geometry: N must be a power of two in [64, 2048]");
     REQUIRE(g.n_det == g.N, TMBIR_ERR_SHAPE, "set_geometry: n_det must equal N");
     REQUIRE(g.n_angles >= 1 && g.n_angles <= 1 << 16, TMBIR_ERR_ARG, "set_geometry: n_angles out of range");
     REQUIRE(g.angles != nullptr, TMBIR_ERR_ARG, "set_geometry: angles is NULL");
@@ -327,6 +331,8 @@ static int check_params(const tmbir_params* p) {
   if (p->L <= 0.0 && p->q != 2.0) return set_error(TMBIR_ERR_ARG, "automatic L needs q = 2; pass L > 0");
   if (p->restart != TMBIR_RESTART_GRADIENT && p->restart != TMBIR_RESTART_NONE && p->restart != TMBIR_RESTART_FUNCTION)
     return set_error(TMBIR_ERR_ARG, "unknown restart mode");
+  if ((p->spectra != TMBIR_SPECTRA_FP32 && p->spectra != TMBIR_SPECTRA_BF16) || !(p->refine_gap >= 0.0))
+    return set_error(TMBIR_ERR_ARG, "spectra must be FP32 or BF16 and refine_gap >= 0");
   return TMBIR_OK;
 }
 
@@ -369,68 +375,95 @@ int tmbir_fbp(tmbir_ctx* ctx, const float* d_sino, float* d_x0) {
   return TMBIR_OK;
 }
 
-// iters iterations on the context stream; with use_cond, one trip of a device-driven graph loop
-static int enqueue_iterations(Ctx& c, float* d_x, const float* d_atg, const PriorC& pc, int iters,
-                              cudaGraphConditionalHandle cond = 0, int use_cond = 0) {
+// Passes 1-3 of every group in Iterate mode, FP32 or BF16 storage variant; *nblocks receives
+// the number of partial-sum rows they write.
+static int enqueue_passes(Ctx& c, float* d_x, const float* d_atg, const PriorC& pc, bool bf16, int* nblocks) {
   StepArgs a{};
   a.atg = d_atg;
   a.xb[0] = d_x;
   a.xb[1] = c.xbuf[0];
   a.xb[2] = c.xbuf[1];
   a.st = c.state;
+  int off = 0;
+  for (size_t i = 0; i < c.gdev.size(); ++i) {
+    const GroupDev& g = c.gdev[i];
+    if (int e = launch_pass1(g, a, c.stream, bf16)) return e;
+    if (int e = launch_pass2(g, c.state, c.stream, bf16)) return e;
+    if (int e = launch_pass3(g, a, Pass3Mode::Iterate, pc, c.partials, off, c.stream, bf16)) return e;
+    off += blocks_pass3(g);
+  }
+  *nblocks = off;
+  return TMBIR_OK;
+}
+
+// iters eager iterations.  kind (see Ctx::graph_kind) selects the storage variants: every
+// variant checks the run's phase on the device, so a BF16 run with refinement enqueues both
+// and the one that does not match leaves at once.
+static int enqueue_iterations(Ctx& c, float* d_x, const float* d_atg, const PriorC& pc, int iters, int kind) {
   for (int k = 0; k < iters; ++k) {
-    int off = 0;
-    for (size_t i = 0; i < c.gdev.size(); ++i) {
-      const GroupDev& g = c.gdev[i];
-      if (int e = launch_pass1(g, a, c.stream)) return e;
-      if (int e = launch_pass2(g, c.state, c.stream)) return e;
-      if (int e = launch_pass3(g, a, Pass3Mode::Iterate, pc, c.partials, off, c.stream)) return e;
-      off += blocks_pass3(g);
-    }
-    const int trip_launches = 3 * (int)c.gdev.size() + 1;
-    if (int e = launch_finalize(c.state, c.partials, off, c.log, c.stream, cond, use_cond, trip_launches)) return e;
+    int nb = 0;
+    if (kind >= 2)
+      if (int e = enqueue_passes(c, d_x, d_atg, pc, true, &nb)) return e;
+    if (kind != 2)
+      if (int e = enqueue_passes(c, d_x, d_atg, pc, false, &nb)) return e;
+    if (int e = launch_finalize(c.state, c.partials, nb, c.log, c.stream)) return e;
   }
   return TMBIR_OK;
 }
 
-// One executable graph: a WHILE node whose body is one iteration (passes 1-3 of every group and
-// the finalize kernel, which clears the condition when the run is done).
-static int build_loop_graph(Ctx& c, float* d_x, const float* d_atg, const PriorC& pc) {
-  cudaGraph_t gr = nullptr;
-  TMBIR_CUDA(cudaGraphCreate(&gr, 0));
-  auto fail = [&](int e) {
-    cudaGraphDestroy(gr);
-    return e;
-  };
+// one trip of a device-driven loop: the passes of one storage variant and the finalize kernel
+static int enqueue_trip(Ctx& c, float* d_x, const float* d_atg, const PriorC& pc, bool bf16,
+                        cudaGraphConditionalHandle cond, int use_cond) {
+  int nb = 0;
+  if (int e = enqueue_passes(c, d_x, d_atg, pc, bf16, &nb)) return e;
+  const int trip_launches = 3 * (int)c.gdev.size() + 1;
+  return launch_finalize(c.state, c.partials, nb, c.log, c.stream, cond, use_cond, trip_launches);
+}
+
+// Appends a WHILE node after `dep` (may be null) whose body is one trip; *node receives it.
+static int add_loop(Ctx& c, cudaGraph_t gr, cudaGraphNode_t* dep, float* d_x, const float* d_atg, const PriorC& pc,
+                    bool bf16, int use_cond, cudaGraphNode_t* node) {
   cudaGraphConditionalHandle h;
   if (cudaGraphConditionalHandleCreate(&h, gr, 1, cudaGraphCondAssignDefault) != cudaSuccess)
-    return fail(set_error(TMBIR_ERR_CUDA, "graph: conditional handle"));
+    return set_error(TMBIR_ERR_CUDA, "graph: conditional handle");
   cudaGraphNodeParams np{};
   np.type = cudaGraphNodeTypeConditional;
   np.conditional.handle = h;
   np.conditional.type = cudaGraphCondTypeWhile;
   np.conditional.size = 1;
-  cudaGraphNode_t node;
-  if (cudaGraphAddNode(&node, gr, nullptr, nullptr, 0, &np) != cudaSuccess)
-    return fail(set_error(TMBIR_ERR_CUDA, "graph: conditional node"));
+  if (cudaGraphAddNode(node, gr, dep, nullptr, dep ? 1 : 0, &np) != cudaSuccess)
+    return set_error(TMBIR_ERR_CUDA, "graph: conditional node");
   cudaGraph_t body = np.conditional.phGraph_out[0];
   if (cudaStreamBeginCaptureToGraph(c.stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) !=
       cudaSuccess)
-    return fail(set_error(TMBIR_ERR_CUDA, "graph: begin capture"));
+    return set_error(TMBIR_ERR_CUDA, "graph: begin capture");
   const long long n0 = __atomic_load_n(&g_launches, __ATOMIC_RELAXED);
-  int e = enqueue_iterations(c, d_x, d_atg, pc, 1, h, 1);
+  int e = enqueue_trip(c, d_x, d_atg, pc, bf16, h, use_cond);
   cudaGraph_t captured = nullptr;
   cudaError_t ce = cudaStreamEndCapture(c.stream, &captured);
   // captured launches run on replay, where the finalize kernel counts them on the device
   __atomic_sub_fetch(&g_launches, __atomic_load_n(&g_launches, __ATOMIC_RELAXED) - n0, __ATOMIC_RELAXED);
-  if (e) return fail(e);
-  if (ce != cudaSuccess) return fail(set_error(TMBIR_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce)));
-  if (cudaGraphInstantiate(&c.graph_exec, gr, 0) != cudaSuccess) {
+  if (e) return e;
+  if (ce != cudaSuccess) return set_error(TMBIR_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+  return TMBIR_OK;
+}
+
+// One executable graph of WHILE nodes, each repeating one iteration until its finalize kernel
+// clears the condition: kind 1 a FP32 loop; kind 2 a BF16 loop; kind 3 a BF16 loop that ends
+// at the refinement switch followed by a FP32 loop.
+static int build_loop_graph(Ctx& c, float* d_x, const float* d_atg, const PriorC& pc, int kind) {
+  cudaGraph_t gr = nullptr;
+  TMBIR_CUDA(cudaGraphCreate(&gr, 0));
+  cudaGraphNode_t first = nullptr, second = nullptr;
+  int e = TMBIR_OK;
+  if (kind >= 2) e = add_loop(c, gr, nullptr, d_x, d_atg, pc, true, kind == 3 ? 2 : 1, &first);
+  if (!e && kind != 2) e = add_loop(c, gr, first ? &first : nullptr, d_x, d_atg, pc, false, 1, &second);
+  if (!e && cudaGraphInstantiate(&c.graph_exec, gr, 0) != cudaSuccess) {
     c.graph_exec = nullptr;
-    return fail(set_error(TMBIR_ERR_CUDA, "graph: instantiate"));
+    e = set_error(TMBIR_ERR_CUDA, "graph: instantiate");
   }
   cudaGraphDestroy(gr);
-  return TMBIR_OK;
+  return e;
 }
 
 int tmbir_reconstruct(tmbir_ctx* ctx, float* d_x, const float* d_atg, const tmbir_params* prm, tmbir_stats* h_stats) {
@@ -448,31 +481,35 @@ int tmbir_reconstruct(tmbir_ctx* ctx, float* d_x, const float* d_atg, const tmbi
     TMBIR_CUDA(cudaMemcpyAsync(c.dscal + 16 + i, c.gdev[i].lam_max, sizeof(double), cudaMemcpyDeviceToDevice, s));
     TMBIR_CUDA(cudaMemcpyAsync(c.dscal + 16 + ng + i, c.gdev[i].gtg, sizeof(double), cudaMemcpyDeviceToDevice, s));
   }
+  const bool bf16 = prm->spectra == TMBIR_SPECTRA_BF16;
   k_init_state<<<1, 1, 0, s>>>(c.state, c.dscal + 16, c.dscal + 16 + ng, ng, prm->L, prm->lambda, prm->sigma,
-                               prm->F_ref, prm->gap_tol, prm->max_iter, prm->restart);
+                               prm->F_ref, prm->gap_tol, prm->max_iter, prm->restart, bf16 ? 1 : 0,
+                               prm->refine_gap);
   TMBIR_CHECK_LAUNCH();
   // x_{-1} = x_0 so that the first (beta = 0) extrapolation reads finite values
   TMBIR_CUDA(cudaMemcpyAsync(c.xbuf[1], d_x, c.total_voxels * sizeof(float), cudaMemcpyDeviceToDevice, s));
   const int iters = prm->max_iter;
+  const int kind = !bf16 ? 1 : (prm->refine_gap > 0.0 ? 3 : 2);
   bool graph = prm->use_graph != 0 && s != nullptr;
   if (iters == 0) {
     // nothing to iterate
   } else if (graph) {
-    const bool reuse = c.graph_exec && c.graph_x == d_x && c.graph_atg == d_atg &&
+    const bool reuse = c.graph_exec && c.graph_x == d_x && c.graph_atg == d_atg && c.graph_kind == kind &&
                        std::memcmp(&c.graph_prior, &pc, sizeof(PriorC)) == 0;
     if (!reuse) {
       if (c.graph_exec) {
         cudaGraphExecDestroy(c.graph_exec);
         c.graph_exec = nullptr;
       }
-      if (int e = build_loop_graph(c, d_x, d_atg, pc)) return e;
+      if (int e = build_loop_graph(c, d_x, d_atg, pc, kind)) return e;
       c.graph_x = d_x;
       c.graph_atg = d_atg;
       c.graph_prior = pc;
+      c.graph_kind = kind;
     }
     TMBIR_CUDA(cudaGraphLaunch(c.graph_exec, s));
   } else {
-    if (int e = enqueue_iterations(c, d_x, d_atg, pc, iters)) return e;
+    if (int e = enqueue_iterations(c, d_x, d_atg, pc, iters, kind)) return e;
   }
   k_gather_final<<<1024, 256, 0, s>>>(c.state, d_x, c.xbuf[0], c.xbuf[1], c.total_voxels);
   TMBIR_CHECK_LAUNCH();
@@ -652,8 +689,10 @@ int tmbir_pass_times(tmbir_ctx* ctx, float* d_x, const float* d_atg, const tmbir
     TMBIR_CUDA(cudaMemcpyAsync(c.dscal + 16 + i, c.gdev[i].lam_max, sizeof(double), cudaMemcpyDeviceToDevice, s));
     TMBIR_CUDA(cudaMemcpyAsync(c.dscal + 16 + ng + i, c.gdev[i].gtg, sizeof(double), cudaMemcpyDeviceToDevice, s));
   }
+  // the storage chosen by prm->spectra for every iteration (no refinement switch)
+  const bool bf16 = prm->spectra == TMBIR_SPECTRA_BF16;
   k_init_state<<<1, 1, 0, s>>>(c.state, c.dscal + 16, c.dscal + 16 + ng, ng, prm->L, prm->lambda, prm->sigma,
-                               prm->F_ref, 0.0, iters, prm->restart);
+                               prm->F_ref, 0.0, iters, prm->restart, bf16 ? 1 : 0, 0.0);
   TMBIR_CHECK_LAUNCH();
   TMBIR_CUDA(cudaMemcpyAsync(c.xbuf[1], d_x, c.total_voxels * sizeof(float), cudaMemcpyDeviceToDevice, s));
   StepArgs a{};
@@ -671,11 +710,11 @@ int tmbir_pass_times(tmbir_ctx* ctx, float* d_x, const float* d_atg, const tmbir
     for (int i = 0; i < ng && rc == TMBIR_OK; ++i) {
       const GroupDev& g = c.gdev[i];
       cudaEventRecord(ev[0], s);
-      if ((rc = launch_pass1(g, a, s))) break;
+      if ((rc = launch_pass1(g, a, s, bf16))) break;
       cudaEventRecord(ev[1], s);
-      if ((rc = launch_pass2(g, c.state, s))) break;
+      if ((rc = launch_pass2(g, c.state, s, bf16))) break;
       cudaEventRecord(ev[2], s);
-      if ((rc = launch_pass3(g, a, Pass3Mode::Iterate, pc, c.partials, off, s))) break;
+      if ((rc = launch_pass3(g, a, Pass3Mode::Iterate, pc, c.partials, off, s, bf16))) break;
       cudaEventRecord(ev[3], s);
       cudaEventSynchronize(ev[3]);
       float ms;

@@ -261,7 +261,7 @@ struct GroupFFT {
   }
 };
 
-// group shape for a transform of length n (power of two times 1, 3 or 5 up to 1024 per row)
+// group shape for a transform of length n (a power of two from 64 to 2048)
 template <int n>
 struct FFTShape;
 template <> struct FFTShape<64> { using type = GroupFFT<8, 8>; };
@@ -269,5 +269,6 @@ template <> struct FFTShape<128> { using type = GroupFFT<8, 16>; };
 template <> struct FFTShape<256> { using type = GroupFFT<16, 16>; };
 template <> struct FFTShape<512> { using type = GroupFFT<16, 32>; };
 template <> struct FFTShape<1024> { using type = GroupFFT<32, 32>; };
+template <> struct FFTShape<2048> { using type = GroupFFT<32, 64>; };
 
 }  // namespace tmbir

@@ -29,6 +29,8 @@ struct IterState {
   int restart_mode;
   int log_cap;
   double prev_F;             // F(y_{k-1}), for the function-value restart
+  int bf16;                  // 1 while the iterations store the spectrum in BF16
+  double refine_gap;         // BF16 -> FP32 switch: gap <= refine_gap (with F_ref), or F(y_k) > F(y_{k-1})
   long long graph_launches;  // kernels run by device-driven graph trips, cumulative (zeroed at workspace binding)
 };
 
@@ -112,6 +114,7 @@ struct Ctx {
   const float* graph_atg = nullptr;
   float* graph_x = nullptr;
   PriorC graph_prior{};
+  int graph_kind = 0;  // 1: one FP32 loop; 2: BF16 loop only; 3: BF16 loop then FP32 loop
 };
 
 // error handling ------------------------------------------------------------
@@ -145,10 +148,12 @@ struct StepArgs {
   const IterState* st;
 };
 
-int launch_pass1(const GroupDev& g, const StepArgs& a, cudaStream_t s);
-int launch_pass2(const GroupDev& g, const IterState* st, cudaStream_t s);
+// bf16: the BF16-storage variant of the pass (Iterate mode only for pass 3); in Iterate mode a
+// variant runs only while the run's storage phase (IterState::bf16) matches it.
+int launch_pass1(const GroupDev& g, const StepArgs& a, cudaStream_t s, bool bf16 = false);
+int launch_pass2(const GroupDev& g, const IterState* st, cudaStream_t s, bool bf16 = false);
 int launch_pass3(const GroupDev& g, const StepArgs& a, Pass3Mode mode, const PriorC& pc, double* partials,
-                 int block_offset, cudaStream_t s);
+                 int block_offset, cudaStream_t s, bool bf16 = false);
 int blocks_pass3(const GroupDev& g);
 // Slices each pass-3 block marches through: enough blocks for about four waves of two
 // blocks per SM on 152 SMs, longer marches when the volume has slices to spare.
@@ -158,8 +163,9 @@ inline int pass3_slices_per_block(int S, int row_blocks) {
   if (chunks > S) chunks = S;
   return (S + chunks - 1) / chunks;
 }
-// cond: the WHILE handle of a device-driven graph loop (use_cond != 0), set to 0 once the run
-// is done; trip_launches: kernels of one loop trip, added to IterState::graph_launches.
+// cond: the WHILE handle of a device-driven graph loop, set to 0 once the run is done
+// (use_cond 1) or also once the run leaves its BF16 phase (use_cond 2); trip_launches:
+// kernels of one loop trip, added to IterState::graph_launches.
 int launch_finalize(IterState* st, const double* partials, int nblocks, double* log, cudaStream_t s,
                     cudaGraphConditionalHandle cond = 0, int use_cond = 0, int trip_launches = 0);
 int launch_sum_partials(const double* partials, int nblocks, double* out, cudaStream_t s);

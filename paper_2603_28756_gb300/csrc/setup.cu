@@ -76,6 +76,31 @@ __global__ void __launch_bounds__(256) k_fft_rows(C* data, int n, int log2n, siz
   for (int j = threadIdx.x; j < n; j += blockDim.x) row[j] = X[j];
 }
 
+// In-place variant for rows whose two Stockham buffers do not fit in shared memory: the row
+// is loaded in bit-reversed order, then log2(n) radix-2 decimation-in-time stages.
+template <int DIR, class C>
+__global__ void __launch_bounds__(1024) k_fft_rows_inplace(C* data, int n, int log2n, size_t stride,
+                                                           const C* __restrict__ tw) {
+  extern __shared__ unsigned char smraw[];
+  C* X = reinterpret_cast<C*>(smraw);
+  C* row = data + (size_t)blockIdx.x * stride;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) X[__brev((unsigned)j) >> (32 - log2n)] = row[j];
+  __syncthreads();
+  for (int half = 1, tstep = n / 2; half < n; half <<= 1, tstep >>= 1) {
+    for (int b = threadIdx.x; b < n / 2; b += blockDim.x) {
+      const int k = b & (half - 1);
+      const int i0 = 2 * (b - k) + k, i1 = i0 + half;
+      const C w = tw[(size_t)k * tstep];
+      const C v = DIR < 0 ? cmul(X[i1], w) : cmulc(X[i1], w);
+      const C u = X[i0];
+      X[i0] = cadd(u, v);
+      X[i1] = csub(u, v);
+    }
+    __syncthreads();
+  }
+  for (int j = threadIdx.x; j < n; j += blockDim.x) row[j] = X[j];
+}
+
 // out[b][c][r] = in[b][r][c] for a batch of rows x cols matrices
 template <class C>
 __global__ void k_transpose(const C* __restrict__ in, C* __restrict__ out, int rows, int cols) {
@@ -106,9 +131,21 @@ static int fft_rows(C* data, int n, int rows, int dir, const C* tw, cudaStream_t
   if (!attr_set) {
     TMBIR_CUDA(cudaFuncSetAttribute(k_fft_rows<-1, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     TMBIR_CUDA(cudaFuncSetAttribute(k_fft_rows<1, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    TMBIR_CUDA(cudaFuncSetAttribute(k_fft_rows_inplace<-1, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    200 * 1024));
+    TMBIR_CUDA(cudaFuncSetAttribute(k_fft_rows_inplace<1, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    200 * 1024));
     attr_set = true;
   }
-  if (smem > 200 * 1024) return set_error(TMBIR_ERR_SHAPE, "setup FFT length too large");
+  if (smem > 200 * 1024) {
+    if (smem / 2 > 200 * 1024) return set_error(TMBIR_ERR_SHAPE, "setup FFT length too large");
+    if (dir < 0)
+      k_fft_rows_inplace<-1, C><<<rows, 1024, smem / 2, s>>>(data, n, ilog2(n), (size_t)n, tw);
+    else
+      k_fft_rows_inplace<1, C><<<rows, 1024, smem / 2, s>>>(data, n, ilog2(n), (size_t)n, tw);
+    TMBIR_CHECK_LAUNCH();
+    return TMBIR_OK;
+  }
   if (dir < 0)
     k_fft_rows<-1, C><<<rows, 256, smem, s>>>(data, n, ilog2(n), (size_t)n, tw);
   else

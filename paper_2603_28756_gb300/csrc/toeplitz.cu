@@ -6,7 +6,7 @@
 
 namespace tmbir {
 
-bool supported_N(int N) { return N == 64 || N == 128 || N == 256 || N == 512 || N == 1024; }
+bool supported_N(int N) { return N == 64 || N == 128 || N == 256 || N == 512 || N == 1024 || N == 2048; }
 
 void fft_shape(int N, int* T, int* P) {
   switch (N) {
@@ -14,20 +14,22 @@ void fft_shape(int N, int* T, int* P) {
     case 128: *T = 8; *P = 16; break;
     case 256: *T = 16; *P = 16; break;
     case 512: *T = 16; *P = 32; break;
-    default: *T = 32; *P = 32; break;
+    case 1024: *T = 32; *P = 32; break;
+    default: *T = 32; *P = 64; break;
   }
 }
 
 #define TMBIR_DECL_N(N)                                                                                     \
-  int pass1_##N(const GroupDev& g, const StepArgs& a, cudaStream_t s);                                      \
-  int pass2_##N(const GroupDev& g, const IterState* st, cudaStream_t s);                                    \
+  int pass1_##N(const GroupDev& g, const StepArgs& a, bool bf16, cudaStream_t s);                           \
+  int pass2_##N(const GroupDev& g, const IterState* st, bool bf16, cudaStream_t s);                         \
   int pass3_##N(const GroupDev& g, const StepArgs& a, Pass3Mode m, const PriorC& pc, double* partials, int off, \
-                cudaStream_t s);
+                bool bf16, cudaStream_t s);
 TMBIR_DECL_N(64)
 TMBIR_DECL_N(128)
 TMBIR_DECL_N(256)
 TMBIR_DECL_N(512)
 TMBIR_DECL_N(1024)
+TMBIR_DECL_N(2048)
 #undef TMBIR_DECL_N
 
 // ---------------------------------------------------------------- reductions and state update
@@ -89,6 +91,8 @@ __global__ void __launch_bounds__(512) k_finalize(IterState* st, const double* p
   double gap = 0.0;
   if (st->Fref == st->Fref && st->F0 != st->Fref) gap = (F - st->Fref) / (st->F0 - st->Fref);
   st->last_gap = gap;
+  // BF16 -> FP32 refinement: later iterations store the spectrum in FP32
+  if (st->bf16 && st->refine_gap > 0.0 && gap <= st->refine_gap) st->bf16 = 0;
   if (!isfinite(F) || !isfinite(gdx) || !isfinite(gg)) {
     st->status = TMBIR_ERR_NONFINITE;
     st->done = 1;
@@ -96,8 +100,9 @@ __global__ void __launch_bounds__(512) k_finalize(IterState* st, const double* p
   if (k + 1 >= st->max_iter) st->done = 1;
   if (st->gap_tol > 0.0 && gap <= st->gap_tol) st->done = 1;
   if (use_cond) {
+    // loop kind 1 runs to the end of the run; kind 2 (the BF16 loop) also ends at the switch
     st->graph_launches += trip_launches;
-    cudaGraphSetConditional(cond, st->done ? 0 : 1);
+    cudaGraphSetConditional(cond, (st->done || (use_cond == 2 && !st->bf16)) ? 0 : 1);
   }
 }
 
@@ -108,14 +113,19 @@ __global__ void __launch_bounds__(512) k_finalize(IterState* st, const double* p
     case 256: return FN##256(__VA_ARGS__);                          \
     case 512: return FN##512(__VA_ARGS__);                          \
     case 1024: return FN##1024(__VA_ARGS__);                        \
+    case 2048: return FN##2048(__VA_ARGS__);                        \
     default: return set_error(TMBIR_ERR_SHAPE, "unsupported N");    \
   }
 
-int launch_pass1(const GroupDev& g, const StepArgs& a, cudaStream_t s) { TMBIR_DISPATCH_N(g.N, pass1_, g, a, s); }
-int launch_pass2(const GroupDev& g, const IterState* st, cudaStream_t s) { TMBIR_DISPATCH_N(g.N, pass2_, g, st, s); }
+int launch_pass1(const GroupDev& g, const StepArgs& a, cudaStream_t s, bool bf16) {
+  TMBIR_DISPATCH_N(g.N, pass1_, g, a, bf16, s);
+}
+int launch_pass2(const GroupDev& g, const IterState* st, cudaStream_t s, bool bf16) {
+  TMBIR_DISPATCH_N(g.N, pass2_, g, st, bf16, s);
+}
 int launch_pass3(const GroupDev& g, const StepArgs& a, Pass3Mode m, const PriorC& pc, double* partials, int off,
-                 cudaStream_t s) {
-  TMBIR_DISPATCH_N(g.N, pass3_, g, a, m, pc, partials, off, s);
+                 cudaStream_t s, bool bf16) {
+  TMBIR_DISPATCH_N(g.N, pass3_, g, a, m, pc, partials, off, bf16, s);
 }
 int blocks_pass3(const GroupDev& g) {
   int T, P;

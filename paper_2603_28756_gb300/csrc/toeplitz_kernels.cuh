@@ -16,11 +16,38 @@
 //                    FP64 partial sums the optimiser needs.
 // A finalize kernel (one block) reduces the partials in a fixed order and advances the
 // device-resident momentum state, so a whole run needs no host round trip.
+//
+// The intermediate spectrum is stored as FP32 complex, or (BF = true) as BF16 pairs with all
+// arithmetic still in FP32: the storage halves and every transform accumulates in FP32.
 #pragma once
+#include <cuda_bf16.h>
+
 #include "fft.cuh"
 #include "internal.h"
 
 namespace tmbir {
+
+// ---------------------------------------------------------------- spectrum storage
+template <bool BF>
+struct SpecIO;
+template <>
+struct SpecIO<false> {
+  using T = float2;
+  __device__ __forceinline__ static float2 ld(const T* p, size_t i) { return p[i]; }
+  __device__ __forceinline__ static void st(T* p, size_t i, float2 v) { p[i] = v; }
+};
+template <>
+struct SpecIO<true> {
+  using T = __nv_bfloat162;
+  __device__ __forceinline__ static float2 ld(const T* p, size_t i) { return __bfloat1622float2(p[i]); }
+  __device__ __forceinline__ static void st(T* p, size_t i, float2 v) { p[i] = __float22bfloat162_rn(v); }
+};
+// In Iterate mode every pass checks the run's current storage phase and leaves when it is
+// not its own, so the BF16 and FP32 variants can be enqueued back to back.
+template <bool BF>
+__device__ __forceinline__ bool skip_iter(const IterState* st) {
+  return st->done || (st->bf16 != 0) != BF;
+}
 
 // ---------------------------------------------------------------- launch geometry
 template <int N>
@@ -145,7 +172,7 @@ __device__ __forceinline__ void block_partials(double (&acc)[kParts], double* re
 }
 
 // ---------------------------------------------------------------- pass 1: rows, forward
-template <int N>
+template <int N, bool BF>
 __global__ void __launch_bounds__(Geo<N>::THREADS) k_pass1(GroupDev g, StepArgs a) {
   using Gm = Geo<N>;
   using F = typename Gm::F;
@@ -154,7 +181,7 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) k_pass1(GroupDev g, StepArgs 
   const float *x, *xp;
   float beta;
   if (a.st) {
-    if (a.st->done) return;
+    if (skip_iter<BF>(a.st)) return;
     int cur = a.st->cur;
     x = a.xb[cur];
     xp = a.xb[(cur + 2) % 3];
@@ -210,33 +237,35 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) k_pass1(GroupDev g, StepArgs 
   });
   if (t == 0) tb[rl * LD + N] = make_float2(nyq, 0.f);
   __syncthreads();
-  float2* out = g.spec + (size_t)s * (N + 1) * N + rb * RB;
+  using IO = SpecIO<BF>;
+  typename IO::T* out = reinterpret_cast<typename IO::T*>(g.spec) + (size_t)s * (N + 1) * N + rb * RB;
   for (int e = threadIdx.x; e < (N + 1) * RB; e += Gm::THREADS) {
     const int vv = e / RB, rr = e - vv * RB;
-    out[(size_t)vv * N + rr] = tb[rr * LD + vv];
+    IO::st(out, (size_t)vv * N + rr, tb[rr * LD + vv]);
   }
 }
 
 // ---------------------------------------------------------------- pass 2: columns
-template <int N>
+template <int N, bool BF>
 __global__ void __launch_bounds__(Geo<N>::THREADS) k_pass2(GroupDev g, const IterState* st) {
   using Gm = Geo<N>;
   using F = typename Gm::F;
   constexpr int T = Gm::T, P = Gm::P, G = Gm::G;
   extern __shared__ float2 sm[];
-  if (st && st->done) return;
+  if (st && skip_iter<BF>(st)) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, grp = lane / T, t = lane % T;
   const int unit = warp * G + grp, h = unit & 1;
   const int col = blockIdx.x * Gm::CPB + (unit >> 1);
   const int ncols = g.S * (N + 1);
   const bool active = col < ncols;
   const int vcol = active ? col / g.S : 0, s = active ? col % g.S : 0;  // slices fastest: kernel column reuse
-  float2* p = g.spec + ((size_t)s * (N + 1) + vcol) * N;
+  using IO = SpecIO<BF>;
+  typename IO::T* p = reinterpret_cast<typename IO::T*>(g.spec) + ((size_t)s * (N + 1) + vcol) * N;
   float2 v[P];
   SFor<0, P>::run([&](auto i_) {
     constexpr int i = decltype(i_)::value;
     const int rr = t + T * i;
-    float2 w = active ? p[rr] : make_float2(0.f, 0.f);
+    float2 w = active ? IO::ld(p, rr) : make_float2(0.f, 0.f);
     if (h) w = cmul(w, __ldg(&g.twM[rr]));  // odd half: w[r] * exp(-2 pi i r / 2N)
     v[i] = w;
   });
@@ -269,7 +298,7 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) k_pass2(GroupDev g, const Ite
     SFor<0, P>::run([&](auto i_) {
       constexpr int i = decltype(i_)::value;
       const int rr = t + T * i;
-      p[rr] = cadd(v[i], os[rr]);
+      IO::st(p, rr, cadd(v[i], os[rr]));
     });
   }
 }
@@ -289,6 +318,9 @@ template <int N>
 struct Geo3 {
   using Gm = Geo<N>;
   static constexpr int RB = Gm::RB, W = 2 * Gm::W, THREADS = 32 * W;
+  // resident blocks per SM the launch bounds ask for: two (16 warps), one for N = 2048 whose
+  // 64-point register transforms and 147 KB ring fill an SM
+  static constexpr int MINB = N >= 2048 ? 1 : 2;
   static constexpr int ROWS = RB + 2;  // ring rows (one halo row each side)
   static constexpr size_t SM_RING = (size_t)3 * ROWS * N * sizeof(float);
   static constexpr size_t SM_A = Gm::cmax(Gm::SM1, (size_t)RB * N * sizeof(float));
@@ -315,8 +347,8 @@ __device__ __forceinline__ void load_ring(float* slot, const float* x, const flo
   }
 }
 
-template <int N, int MODE, bool Q2>
-__global__ void __launch_bounds__(Geo3<N>::THREADS, 2)
+template <int N, int MODE, bool Q2, bool BF>
+__global__ void __launch_bounds__(Geo3<N>::THREADS, Geo3<N>::MINB)
     k_pass3(GroupDev g, StepArgs a, PriorC pc, double* partials, int block_offset, int zc) {
   using Gm = Geo<N>;
   using G3 = Geo3<N>;
@@ -332,7 +364,7 @@ __global__ void __launch_bounds__(Geo3<N>::THREADS, 2)
   float* out;
   float beta, invL;
   if constexpr (MODE == (int)Pass3Mode::Iterate) {
-    if (a.st->done) return;
+    if (skip_iter<BF>(a.st)) return;
     const int cur = a.st->cur;
     x = cur == 0 ? a.xb[0] : (cur == 1 ? a.xb[1] : a.xb[2]);
     xp = cur == 0 ? a.xb[2] : (cur == 1 ? a.xb[0] : a.xb[1]);
@@ -376,10 +408,11 @@ __global__ void __launch_bounds__(Geo3<N>::THREADS, 2)
     // ---- K (*) y for rows r0 .. r0+RB-1 of slice z
     __syncthreads();
     {
-      const float2* sp = g.spec + (size_t)z * (N + 1) * N + r0;
+      using IO = SpecIO<BF>;
+      const typename IO::T* sp = reinterpret_cast<const typename IO::T*>(g.spec) + (size_t)z * (N + 1) * N + r0;
       for (int e = threadIdx.x; e < (N + 1) * RB; e += G3::THREADS) {
         const int vv = e / RB, rr = e - vv * RB;
-        tb[rr * LD + vv] = sp[(size_t)vv * N + rr];
+        tb[rr * LD + vv] = IO::ld(sp, (size_t)vv * N + rr);
       }
     }
     if constexpr (PRIOR) {
@@ -488,36 +521,46 @@ static int set_smem_limits() {
   using Gm = Geo<N>;
   static bool done = false;
   if (done) return TMBIR_OK;
-  TMBIR_CUDA(cudaFuncSetAttribute(k_pass1<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Gm::SM1));
-  TMBIR_CUDA(cudaFuncSetAttribute(k_pass2<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Gm::SM2));
-#define TMBIR_P3ATTR(M, Q)                                                                           \
-  TMBIR_CUDA(cudaFuncSetAttribute(k_pass3<N, M, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+  TMBIR_CUDA(cudaFuncSetAttribute(k_pass1<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Gm::SM1));
+  TMBIR_CUDA(cudaFuncSetAttribute(k_pass1<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Gm::SM1));
+  TMBIR_CUDA(cudaFuncSetAttribute(k_pass2<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Gm::SM2));
+  TMBIR_CUDA(cudaFuncSetAttribute(k_pass2<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Gm::SM2));
+#define TMBIR_P3ATTR(M, Q, B)                                                                           \
+  TMBIR_CUDA(cudaFuncSetAttribute(k_pass3<N, M, Q, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                   (int)Geo3<N>::SM));
-  TMBIR_P3ATTR(0, true) TMBIR_P3ATTR(1, true) TMBIR_P3ATTR(2, true) TMBIR_P3ATTR(3, true) TMBIR_P3ATTR(4, true)
-  TMBIR_P3ATTR(1, false) TMBIR_P3ATTR(2, false) TMBIR_P3ATTR(3, false) TMBIR_P3ATTR(4, false)
+  TMBIR_P3ATTR(0, true, false) TMBIR_P3ATTR(1, true, false) TMBIR_P3ATTR(2, true, false)
+  TMBIR_P3ATTR(3, true, false) TMBIR_P3ATTR(4, true, false) TMBIR_P3ATTR(1, false, false)
+  TMBIR_P3ATTR(2, false, false) TMBIR_P3ATTR(3, false, false) TMBIR_P3ATTR(4, false, false)
+  TMBIR_P3ATTR(3, true, true) TMBIR_P3ATTR(3, false, true)
 #undef TMBIR_P3ATTR
   done = true;
   return TMBIR_OK;
 }
 
 template <int N>
-static int pass1_n(const GroupDev& g, const StepArgs& a, cudaStream_t s) {
+static int pass1_n(const GroupDev& g, const StepArgs& a, bool bf16, cudaStream_t s) {
   using Gm = Geo<N>;
   if (int e = set_smem_limits<N>()) return e;
-  k_pass1<N><<<g.S * Gm::NB, Gm::THREADS, Gm::SM1, s>>>(g, a);
+  if (bf16)
+    k_pass1<N, true><<<g.S * Gm::NB, Gm::THREADS, Gm::SM1, s>>>(g, a);
+  else
+    k_pass1<N, false><<<g.S * Gm::NB, Gm::THREADS, Gm::SM1, s>>>(g, a);
   TMBIR_CHECK_LAUNCH();
   return TMBIR_OK;
 }
 template <int N>
-static int pass2_n(const GroupDev& g, const IterState* st, cudaStream_t s) {
+static int pass2_n(const GroupDev& g, const IterState* st, bool bf16, cudaStream_t s) {
   using Gm = Geo<N>;
   if (int e = set_smem_limits<N>()) return e;
   const int blocks = (g.S * (N + 1) + Gm::CPB - 1) / Gm::CPB;
-  k_pass2<N><<<blocks, Gm::THREADS, Gm::SM2, s>>>(g, st);
+  if (bf16)
+    k_pass2<N, true><<<blocks, Gm::THREADS, Gm::SM2, s>>>(g, st);
+  else
+    k_pass2<N, false><<<blocks, Gm::THREADS, Gm::SM2, s>>>(g, st);
   TMBIR_CHECK_LAUNCH();
   return TMBIR_OK;
 }
-template <int N, int MODE>
+template <int N, int MODE, bool BF>
 static int pass3_nm(const GroupDev& g, const StepArgs& a, const PriorC& pc, double* partials, int off,
                     cudaStream_t s) {
   using Gm = Geo<N>;
@@ -525,21 +568,25 @@ static int pass3_nm(const GroupDev& g, const StepArgs& a, const PriorC& pc, doub
   const int zc = pass3_slices_per_block(g.S, Gm::NB);
   const int blocks = Gm::NB * ((g.S + zc - 1) / zc);
   if (pc.q_is_2 || MODE == 0)
-    k_pass3<N, MODE, true><<<blocks, Geo3<N>::THREADS, Geo3<N>::SM, s>>>(g, a, pc, partials, off, zc);
+    k_pass3<N, MODE, true, BF><<<blocks, Geo3<N>::THREADS, Geo3<N>::SM, s>>>(g, a, pc, partials, off, zc);
   else
-    k_pass3<N, MODE, false><<<blocks, Geo3<N>::THREADS, Geo3<N>::SM, s>>>(g, a, pc, partials, off, zc);
+    k_pass3<N, MODE, false, BF><<<blocks, Geo3<N>::THREADS, Geo3<N>::SM, s>>>(g, a, pc, partials, off, zc);
   TMBIR_CHECK_LAUNCH();
   return TMBIR_OK;
 }
 template <int N>
 static int pass3_n(const GroupDev& g, const StepArgs& a, Pass3Mode m, const PriorC& pc, double* partials, int off,
-                   cudaStream_t s) {
+                   bool bf16, cudaStream_t s) {
+  if (bf16) {
+    if (m != Pass3Mode::Iterate) return set_error(TMBIR_ERR_ARG, "BF16 spectra are an iteration option only");
+    return pass3_nm<N, 3, true>(g, a, pc, partials, off, s);
+  }
   switch (m) {
-    case Pass3Mode::Apply: return pass3_nm<N, 0>(g, a, pc, partials, off, s);
-    case Pass3Mode::Gradient: return pass3_nm<N, 1>(g, a, pc, partials, off, s);
-    case Pass3Mode::Step: return pass3_nm<N, 2>(g, a, pc, partials, off, s);
-    case Pass3Mode::Iterate: return pass3_nm<N, 3>(g, a, pc, partials, off, s);
-    default: return pass3_nm<N, 4>(g, a, pc, partials, off, s);
+    case Pass3Mode::Apply: return pass3_nm<N, 0, false>(g, a, pc, partials, off, s);
+    case Pass3Mode::Gradient: return pass3_nm<N, 1, false>(g, a, pc, partials, off, s);
+    case Pass3Mode::Step: return pass3_nm<N, 2, false>(g, a, pc, partials, off, s);
+    case Pass3Mode::Iterate: return pass3_nm<N, 3, false>(g, a, pc, partials, off, s);
+    default: return pass3_nm<N, 4, false>(g, a, pc, partials, off, s);
   }
 }
 

@@ -1,0 +1,134 @@
+"""Parity at large sizes.
+
+* The workload bench.py times: 64 slices of 1024^2, 256 angles over [0, pi), 20 ellipsoids.
+* The finest level of the hierarchical geometry: 2048^2 slices seen under 128 angles over
+  [0, 2 pi/3) (missing wedge).
+
+The oracle evaluates sampled outputs one by one (R*g, K (*) x, the prior gradient and the FBP
+start at a pixel); the kernel K and, at 2048^2 with two slices, whole results are compared in
+full.  Tolerances as in test_gpu_parity.py.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2603_28756_gb300 as tm  # noqa: E402
+
+PRIOR = dict(p=1.2, q=2.0, c=0.01, sigma=0.1, lam=1.0)
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32).ravel()).cuda()
+
+
+def host(t, shape):
+    torch.cuda.synchronize()
+    return t.double().cpu().numpy().reshape(shape)
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+
+def samples(rng, S, N, n):
+    """n voxels: the corners and edges of the volume and random interior ones."""
+    pts = [(0, 0, 0), (S - 1, N - 1, N - 1), (0, N - 1, 0), (S - 1, 0, N - 1), (S // 2, N // 2, N // 2)]
+    while len(pts) < n:
+        pts.append((int(rng.integers(S)), int(rng.integers(N)), int(rng.integers(N))))
+    return pts
+
+
+@pytest.fixture(scope="module")
+def bench_case(orc):
+    S, N, na = 64, 1024, 256
+    p = synth.volume(S=S, N=N, n_angles=na, n_ellipsoids=20, seed=1002)
+    ctx = tm.Context([tm.Group(N=N, angles=list(p.theta), n_slices=S)])
+    sino = dev(p.sino)
+    atg = ctx.build_operator(sino)
+    K = orc.kernel(N, p.theta, N)
+    return dict(S=S, N=N, p=p, ctx=ctx, sino=sino, atg=atg, K=K)
+
+
+def test_bench_workload_setup(bench_case, orc):
+    c = bench_case
+    S, N, p = c["S"], c["N"], c["p"]
+    K = host(c["ctx"].kernel(0), c["K"].shape)
+    assert np.max(np.abs(K - c["K"])) <= 1e-10 * np.max(np.abs(c["K"]))
+    atg = host(c["atg"], (S, N, N))
+    fbp = host(c["ctx"].fbp(c["sino"]), (S, N, N))
+    g = p.sino.astype(np.float64)
+    scale = np.max(np.abs(atg))
+    rng = np.random.default_rng(7)
+    filtered = {}
+    for z, r, col in samples(rng, S, N, 24):
+        ref = orc.adjoint_point(g[z], N, p.theta, r, col)
+        assert abs(atg[z, r, col] - ref) <= 1e-6 * scale
+        if z not in filtered:
+            filtered[z] = orc.ramp_filter(g[z])
+        fref = (math.pi / len(p.theta)) * orc.adjoint_point(filtered[z], N, p.theta, r, col)
+        assert abs(fbp[z, r, col] - fref) <= 1e-4 * np.max(np.abs(fbp))
+
+
+def test_bench_workload_gradient_and_step(bench_case, orc):
+    # gradient and one step for a seeded image and a seeded stand-in for R*g (any image is a
+    # valid input of the operator), compared at sampled voxels
+    c = bench_case
+    S, N = c["S"], c["N"]
+    pr = orc.Prior(**PRIOR)
+    rng = np.random.default_rng(8)
+    x = synth.random_image(rng, (S, N, N), 0.5).astype(np.float64)
+    b = synth.random_image(rng, (S, N, N), 4.0e4).astype(np.float64)
+    d_b = dev(b)
+    G = host(c["ctx"].gradient(dev(x), d_b, tm.Params(**PRIOR)), (S, N, N))
+    z = host(c["ctx"].normal_apply(dev(x)), (S, N, N))
+    zscale = np.sqrt(np.mean(z ** 2))
+    gscale = np.sqrt(np.mean(G ** 2))
+    # one fast-gradient step from x (beta = 0) with an explicit step constant
+    L = 3.0e5
+    xs = dev(x)
+    c["ctx"].reconstruct(xs, d_b, tm.Params(**PRIOR, L=L, max_iter=1))
+    x1 = host(xs, (S, N, N))
+    for zz, r, col in samples(rng, S, N, 24):
+        zr = orc.normal_point(x[zz], c["K"], r, col)
+        assert abs(z[zz, r, col] - zr) <= 1e-5 * zscale
+        gr = zr - b[zz, r, col] + orc.prior_point(x, pr, zz, r, col)
+        assert abs(G[zz, r, col] - gr) <= 1e-5 * gscale
+        assert abs(x1[zz, r, col] - (x[zz, r, col] - gr / L)) <= 1e-5 * gscale / L + 1e-7
+
+
+def test_n2048_limited_angle(orc):
+    # two slices at the finest level of the hierarchical geometry, compared in full
+    S, N, na, span = 2, 2048, 128, 2 * math.pi / 3
+    p = synth.volume(S=S, N=N, n_angles=na, n_ellipsoids=6, span=span, seed=1003)
+    ctx = tm.Context([tm.Group(N=N, angles=list(p.theta), n_slices=S, span=span)])
+    d_atg = ctx.build_operator(dev(p.sino))
+    Kref = orc.kernel(N, p.theta, N)
+    K = host(ctx.kernel(0), Kref.shape)
+    assert np.max(np.abs(K - Kref)) <= 1e-10 * np.max(np.abs(Kref))
+    atg = host(d_atg, (S, N, N))
+    g = p.sino.astype(np.float64)
+    rng = np.random.default_rng(9)
+    for z, r, col in samples(rng, S, N, 12):
+        assert abs(atg[z, r, col] - orc.adjoint_point(g[z], N, p.theta, r, col)) <= 1e-6 * np.max(np.abs(atg))
+    pr = orc.Prior(**PRIOR)
+    x = synth.random_image(rng, (S, N, N), 0.5).astype(np.float64)
+    b = synth.random_image(rng, (S, N, N), 4.0e4).astype(np.float64)  # seeded stand-in for R*g
+    d_b = dev(b)
+    Chat = orc.circulant_spectrum(Kref)
+    assert rel(host(ctx.normal_apply(dev(x)), x.shape), orc.toeplitz(x, Kref, Chat)) < 1e-5
+    assert rel(host(ctx.gradient(dev(x), d_b, tm.Params(**PRIOR)), x.shape), orc.gradient(x, b, Kref, pr, Chat)) < 1e-5
+    # three fast-gradient iterations from zero with an explicit step constant
+    L = 1.0e5
+    xs = torch.zeros(x.size, dtype=torch.float32, device="cuda")
+    ctx.reconstruct(xs, d_b, tm.Params(**PRIOR, L=L, max_iter=3))
+    ref = orc.nesterov(np.zeros(x.shape), b, 0.0, Kref, pr, L, 3, Chat=Chat)
+    assert rel(host(xs, x.shape), ref) < 1e-4

@@ -208,6 +208,50 @@ def test_device_loop_stops_at_gap(prob):
     assert sc.iterations == 5 and prob.ctx.launch_count() - n2 == 4 * 5 + 2
 
 
+def test_bf16_spectra_follow_oracle(prob, orc):
+    # BF16 storage of the padded spectrum (8-bit mantissa, relative rounding 2^-9 per entry,
+    # two roundings per iteration): one gradient within 3e-3 relative L2 of the FP64 oracle
+    pr = orc.Prior(**PRIOR)
+    x = dev(prob.x)
+    st = prob.ctx.reconstruct(x, prob.d_atg, tm.Params(**PRIOR, max_iter=1, bf16=True))
+    G = (prob.x - host(x, prob.x.shape)) * st.L
+    assert rel(G, orc.gradient(prob.x, prob.atg, prob.K, pr)) < 3e-3
+    # over 30 iterations the rounding noise of every gradient accumulates in the iterate
+    iters = 30
+    x = torch.zeros(prob.x.size, dtype=torch.float32, device="cuda")
+    st = prob.ctx.reconstruct(x, prob.d_atg, tm.Params(**PRIOR, max_iter=iters, bf16=True))
+    assert st.iterations == iters and st.status == 0
+    L = orc.lipschitz(prob.K, prob.N, pr)
+    olog = []
+    ref = orc.nesterov(np.zeros(prob.x.shape), prob.atg, float(np.sum(prob.g ** 2)), prob.K, pr, L, iters, log=olog)
+    assert rel(host(x, prob.x.shape), ref) < 2e-2
+    # F(y_k) = 1/2 y.z - y.R*g + 1/2 g.g is assembled from terms of the size of F(0) = 1/2 g.g
+    # that cancel as the iterates converge: bound the BF16 error on that scale (measured about
+    # 1.5e-4 F(0))
+    F0 = 0.5 * float(np.sum(prob.g ** 2))
+    for (F, _, _, _), (Fo, _, _) in zip(prob.ctx.get_log(), olog):
+        assert abs(F - Fo) <= 1e-3 * F0
+
+
+def test_bf16_refinement_matches_fp32(prob):
+    # BF16 iterations until the gap reaches 1e-1, FP32 after: the run reaches the 1e-3 gap of
+    # the FP32 run; graph and eager launches give bitwise equal iterates
+    x = torch.zeros(prob.x.size, dtype=torch.float32, device="cuda")
+    F_ref = prob.ctx.reconstruct(x, prob.d_atg, tm.Params(**PRIOR, max_iter=300)).objective
+    stop = dict(PRIOR, max_iter=300, gap_tol=1e-3, F_ref=F_ref)
+    a = torch.zeros_like(x)
+    b = torch.zeros_like(x)
+    c = torch.zeros_like(x)
+    s32 = prob.ctx.reconstruct(c, prob.d_atg, tm.Params(**stop))
+    sa = prob.ctx.reconstruct(a, prob.d_atg, tm.Params(**stop, bf16=True, refine_gap=1e-1, use_graph=True))
+    sb = prob.ctx.reconstruct(b, prob.d_atg, tm.Params(**stop, bf16=True, refine_gap=1e-1, use_graph=False))
+    torch.cuda.synchronize()
+    assert sa.iterations == sb.iterations and torch.equal(a, b)
+    assert sa.gap <= 1e-3 and sa.iterations < 300
+    assert sa.iterations <= s32.iterations + 5
+    assert rel(host(a, prob.x.shape), host(c, prob.x.shape).astype(np.float64)) < 1e-2
+
+
 def test_uneven_groups_equal_separate_contexts(orc):
     specs = [(64, 2, 30), (128, 1, 50), (64, 1, 20)]
     groups, sinos, thetas, ctxs = [], [], [], []
@@ -281,6 +325,30 @@ def test_downsample_sino_bitwise(orc):
     for f in (2, 4):
         d = host(ctx.downsample_sino(dev(g), 3, 7, 64, f), (3, 7, 64 // f))
         assert np.array_equal(d, orc.downsample_sino(g.astype(np.float64), f))
+
+
+def test_hierarchical_levels_follow_oracle(orc):
+    # three levels 64 -> 128 -> 256 (Sec. 2.3): coarse sinograms by bin subsampling, FBP at the
+    # coarsest level, Lanczos-3 x2 upsampling between levels; the oracle runs the same chain
+    N, S, na, levels = 256, 3, 60, 3
+    iters = [25, 15, 8]
+    p = synth.volume(S=S, N=N, n_angles=na, n_ellipsoids=6, seed=61)
+    pr = orc.Prior(**PRIOR)
+    x, ctxs, stats = tm.reconstruct_levels(N, p.theta, S, dev(p.sino), levels,
+                                           [tm.Params(**PRIOR, max_iter=k) for k in iters])
+    assert [s.iterations for s in stats] == iters
+    g = p.sino.astype(np.float64)
+    xo = None
+    for lev in range(levels):
+        f = 1 << (levels - 1 - lev)
+        Nl = N // f
+        gl = g if f == 1 else orc.downsample_sino(g, f)
+        K = orc.kernel(Nl, p.theta, Nl)
+        atg = orc.adjoint(gl, Nl, p.theta)
+        x0 = orc.fbp(gl, Nl, p.theta, math.pi) if xo is None else orc.lanczos_up(xo)
+        L = orc.lipschitz(K, Nl, pr)
+        xo = orc.nesterov(x0, atg, float(np.sum(gl ** 2)), K, pr, L, iters[lev])
+    assert rel(host(x, xo.shape), xo) < 1e-3
 
 
 def test_argument_errors():
