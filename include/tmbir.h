@@ -93,6 +93,10 @@ typedef struct {
  *   refine_gap      with BF16 spectra: switch to FP32 spectra for the remaining iterations
  *                   once the relative gap (as for gap_tol) is <= refine_gap; 0 keeps BF16 to
  *                   the end.
+ *   resume          0: start a new run from d_x (x_{-1} = x_0, t = 1).  1: continue the run
+ *                   the context holds (the previous tmbir_reconstruct, or a checkpoint loaded
+ *                   by tmbir_state_import) for max_iter more iterations; d_x must hold that
+ *                   run's x_k.  The result is bitwise the one an uninterrupted run gives.
  */
 typedef struct {
   double p, q, c, sigma, lambda;
@@ -104,6 +108,7 @@ typedef struct {
   int use_graph;
   int spectra;
   double refine_gap;
+  int resume;
 } tmbir_params;
 
 /* Result of tmbir_reconstruct (host struct filled on return). */
@@ -216,6 +221,29 @@ int tmbir_downsample_sino(tmbir_ctx* ctx, const float* d_sino, int n_slices, int
  * gradient + update), finalize }.  d_x receives the iterate like tmbir_reconstruct.
  */
 int tmbir_pass_times(tmbir_ctx* ctx, float* d_x, const float* d_atg, const tmbir_params* prm, int iters, double* h_ms);
+
+/*
+ * Autotuner (no counterpart in the paper): times pass 3 of one iteration on d_x / d_atg with
+ * every candidate number of slices a block marches through (1, 2, 3, 4, 6, 8, 12, 16, 24, 32
+ * up to the group's slice count, and the default rule) and keeps the fastest per group;
+ * h_zc (may be NULL) receives the choice per group.  Later contexts of this process with the
+ * same image side and slice count start from the choice.  The transform tile shapes (rows per
+ * block, threads per row) are fixed per image side at compile time.  d_x is not modified.
+ */
+int tmbir_autotune(tmbir_ctx* ctx, const float* d_x, const float* d_atg, const tmbir_params* prm, int* h_zc);
+
+/*
+ * Checkpoint of a run (no counterpart in the paper): the fast-gradient state after
+ * tmbir_reconstruct (momentum t and beta, step constant, iteration count, restart count,
+ * F(y_{k-1}) for the function restart) and x_{k-1}; x_k is the caller's image.  d_state is a
+ * caller-owned device buffer of tmbir_state_size bytes, 16-byte aligned.  Export needs a
+ * finished run; import replaces the context's state (same geometry), after which
+ * tmbir_reconstruct with resume = 1 continues it.  Both are asynchronous on the context
+ * stream except import, which returns after the copy.
+ */
+int tmbir_state_size(const tmbir_ctx* ctx, size_t* bytes);
+int tmbir_state_export(tmbir_ctx* ctx, void* d_state);
+int tmbir_state_import(tmbir_ctx* ctx, const void* d_state);
 
 /*
  * Number of library kernels launched so far: the host-side count of every launch by this

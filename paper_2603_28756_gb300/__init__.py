@@ -59,6 +59,7 @@ class _Params(ctypes.Structure):
         ("use_graph", ctypes.c_int),
         ("spectra", ctypes.c_int),
         ("refine_gap", ctypes.c_double),
+        ("resume", ctypes.c_int),
     ]
 
 
@@ -82,6 +83,7 @@ SYMBOLS = [
     "tmbir_normal_apply_static", "tmbir_cnn_param_count", "tmbir_cnn_workspace_size", "tmbir_cnn_create",
     "tmbir_cnn_destroy", "tmbir_cnn_init", "tmbir_cnn_set_weights", "tmbir_cnn_get_weights", "tmbir_cnn_apply",
     "tmbir_cnn_train_step", "tmbir_cnn_net_forward", "tmbir_cnn_net_backward", "tmbir_warm_start",
+    "tmbir_state_size", "tmbir_state_export", "tmbir_state_import", "tmbir_autotune",
 ]
 
 _lib = None
@@ -132,6 +134,10 @@ def load(path: str | None = None):
         "tmbir_cnn_net_forward": [vp, vp, i, vp],
         "tmbir_cnn_net_backward": [vp, vp, vp, i, ctypes.POINTER(ctypes.c_float), vp],
         "tmbir_warm_start": [vp, vp, vp, vp, ctypes.POINTER(_Params), vp, ctypes.POINTER(i)],
+        "tmbir_state_size": [vp, ctypes.POINTER(sz)],
+        "tmbir_state_export": [vp, vp],
+        "tmbir_state_import": [vp, vp],
+        "tmbir_autotune": [vp, vp, vp, ctypes.POINTER(_Params), ctypes.POINTER(i)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -176,10 +182,12 @@ class Params:
     use_graph: bool = True
     bf16: bool = False  # BF16 storage of the intermediate spectrum
     refine_gap: float = 0.0  # with bf16: switch to FP32 spectra once the gap is <= refine_gap
+    resume: bool = False  # continue the context's run (or an imported checkpoint)
 
     def c_struct(self) -> _Params:
         return _Params(self.p, self.q, self.c, self.sigma, self.lam, self.L, self.max_iter, self.gap_tol, self.F_ref,
-                       self.restart, 1 if self.use_graph else 0, 1 if self.bf16 else 0, self.refine_gap)
+                       self.restart, 1 if self.use_graph else 0, 1 if self.bf16 else 0, self.refine_gap,
+                       1 if self.resume else 0)
 
 
 @dataclass
@@ -380,6 +388,34 @@ class Context:
         self._post(sino, out)
         return out
 
+    def autotune(self, x, atg, params: Params):
+        """Pick the pass-3 slices per block for every group by timing them; returns the choices."""
+        zc = (ctypes.c_int * len(self.groups))()
+        pr = params.c_struct()
+        self._pre()
+        _check(_lib.tmbir_autotune(self._h, ctypes.c_void_p(_ptr(x)), ctypes.c_void_p(_ptr(atg)), ctypes.byref(pr), zc))
+        self._post(x, atg)
+        return list(zc)
+
+    def state_export(self, out=None):
+        """Checkpoint of the last run (device uint8 tensor); x_k is the run's image."""
+        import torch
+
+        n = ctypes.c_size_t()
+        _check(_lib.tmbir_state_size(self._h, ctypes.byref(n)))
+        if out is None:
+            with torch.cuda.stream(self.stream):
+                out = torch.empty(n.value, dtype=torch.uint8, device=self.device)
+        self._pre()
+        _check(_lib.tmbir_state_export(self._h, ctypes.c_void_p(out.data_ptr())))
+        self._post(out)
+        return out
+
+    def state_import(self, state):
+        self._pre()
+        _check(_lib.tmbir_state_import(self._h, ctypes.c_void_p(state.data_ptr())))
+        self._post(state)
+
     def pass_times(self, x, atg, params: Params, iters: int):
         """Summed device ms of (pass 1, pass 2, pass 3, finalize) over `iters` eager iterations."""
         pr = params.c_struct()
@@ -411,7 +447,7 @@ class Context:
 
 
 def reconstruct_levels(N: int, angles, n_slices: int, sino, levels: int, params, span: float = math.pi,
-                       stream=None, device="cuda", start=None):
+                       stream=None, device="cuda", start=None, ctxs=None):
     """Hierarchical reconstruction (Sec. 2.3) through the C ABI.
 
     Level l = 0 .. levels-1 reconstructs n_slices slices of N / 2^(levels-1-l) pixels.  A
@@ -419,8 +455,9 @@ def reconstruct_levels(N: int, angles, n_slices: int, sino, levels: int, params,
     divided by f (tmbir_downsample_sino, f = 2^(levels-1-l)); the coarsest level starts from
     its FBP image (or from `start`, a callable (ctx, sino_l, atg_l) -> image), every finer
     level from the Lanczos-3 x2 upsampling of the level below (tmbir_upsample_lanczos3).
-    `params` is one Params per level.  All levels share one stream.  Returns the finest
-    image, the level contexts and the per-level Stats.
+    `params` is one Params per level.  All levels share one stream; `ctxs` (the list a
+    previous call returned) reuses the level contexts and their workspaces.  Returns the
+    finest image, the level contexts and the per-level Stats.
     """
     import torch
 
@@ -428,22 +465,34 @@ def reconstruct_levels(N: int, angles, n_slices: int, sino, levels: int, params,
         raise ValueError("one Params per level")
     if N % (1 << (levels - 1)):
         raise ValueError("N must be divisible by 2^(levels-1)")
-    stream = stream if stream is not None else torch.cuda.Stream(device=torch.device(device))
+    if ctxs is None:
+        stream = stream if stream is not None else torch.cuda.Stream(device=torch.device(device))
+        ctxs = [Context([Group(N=N >> (levels - 1 - lev), angles=list(angles), n_slices=n_slices, span=span)],
+                        stream=stream, device=device) for lev in range(levels)]
     na = len(angles)
-    ctxs, stats = [], []
+    stats = []
     x = None
     for lev in range(levels):
         f = 1 << (levels - 1 - lev)
         Nl = N // f
-        ctx = Context([Group(N=Nl, angles=list(angles), n_slices=n_slices, span=span)], stream=stream, device=device)
-        sino_l = sino if f == 1 else ctx.downsample_sino(sino, n_slices, na, N, f)
-        atg = ctx.build_operator(sino_l)
+        ctx = ctxs[lev]
+        # per-level buffers live on the context, so repeated calls reuse them (and the
+        # context's cached iteration graph, which is keyed on the buffers)
+        if getattr(ctx, "_lv", None) is None:
+            ctx._lv = {"x": ctx._empty(n_slices * Nl * Nl), "atg": ctx._empty(n_slices * Nl * Nl),
+                       "sino": ctx._empty(n_slices * na * Nl) if f > 1 else None}
+        lv = ctx._lv
+        sino_l = sino if f == 1 else ctx.downsample_sino(sino, n_slices, na, N, f, out=lv["sino"])
+        atg = ctx.build_operator(sino_l, lv["atg"])
         if x is None:
-            x = start(ctx, sino_l, atg) if start is not None else ctx.fbp(sino_l)
+            if start is not None:
+                lv["x"].copy_(start(ctx, sino_l, atg))
+            else:
+                ctx.fbp(sino_l, lv["x"])
         else:
-            x = ctx.upsample_lanczos3(x, n_slices, Nl // 2)
+            ctx.upsample_lanczos3(x, n_slices, Nl // 2, out=lv["x"])
+        x = lv["x"]
         stats.append(ctx.reconstruct(x, atg, params[lev]))
-        ctxs.append(ctx)
     return x, ctxs, stats
 
 

@@ -1,8 +1,11 @@
 // C ABI entry points: context, geometry, workspace layout, and the call sequences of the
 // setup, warm-start and iteration phases.  All device work is enqueued on the context stream.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <limits>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -40,6 +43,17 @@ PriorC make_prior(const tmbir_params& p) {
 
 static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
+// Slices per pass-3 block chosen by tmbir_autotune, by image side and slice count, shared by
+// the contexts of this process (0: not tuned).
+static std::mutex g_tune_mu;
+static std::map<std::pair<int, int>, int> g_tuned_zc;
+
+static int tuned_zc(int N, int S) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tuned_zc.find({N, S});
+  return it == g_tuned_zc.end() ? 0 : it->second;
+}
+
 // ---------------------------------------------------------------- small device kernels
 // lam_max[i], gtg[i]: per-group lambda_max(R*R) and 1/2 g.g gathered into consecutive doubles
 __global__ void k_init_state(IterState* st, const double* lam_max, const double* gtg, int n_groups, double L_given,
@@ -74,13 +88,40 @@ __global__ void k_init_state(IterState* st, const double* lam_max, const double*
   st->refine_gap = refine_gap;
 }
 
-// copy the current iterate back into slot 0 (the caller's buffer) when the rotation ended elsewhere
-__global__ void k_gather_final(const IterState* st, float* x0, const float* x1, const float* x2, size_t n) {
+// End of a run: bring the rotation to its start position, x_k in slot 0 (the caller's buffer)
+// and x_{k-1} in slot 2, so the state can be exported or resumed (k_rotation_reset then sets
+// the rotation index to 0).
+__global__ void k_gather_final(const IterState* st, float* x0, float* x1, float* x2, size_t n) {
   const int cur = st->cur;
   if (cur == 0) return;
-  const float* src = cur == 1 ? x1 : x2;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n / 4; i += (size_t)gridDim.x * blockDim.x)
-    reinterpret_cast<float4*>(x0)[i] = reinterpret_cast<const float4*>(src)[i];
+  float4* a = reinterpret_cast<float4*>(x0);
+  float4* b = reinterpret_cast<float4*>(x1);
+  float4* c = reinterpret_cast<float4*>(x2);
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n / 4; i += (size_t)gridDim.x * blockDim.x) {
+    if (cur == 1) {  // x_k in slot 1, x_{k-1} in slot 0
+      const float4 xk = b[i], xp = a[i];
+      a[i] = xk;
+      c[i] = xp;
+    } else {  // x_k in slot 2, x_{k-1} in slot 1
+      const float4 xk = c[i], xp = b[i];
+      a[i] = xk;
+      c[i] = xp;
+    }
+  }
+}
+__global__ void k_rotation_reset(IterState* st) { st->cur = 0; }
+
+// continue a run from the current state: max_iter more iterations with new stop settings
+__global__ void k_resume_state(IterState* st, double Fref, double gap_tol, int max_iter, int restart_mode, int bf16,
+                               double refine_gap) {
+  st->max_iter = st->k + max_iter;
+  st->Fref = Fref;
+  st->gap_tol = gap_tol;
+  st->restart_mode = restart_mode;
+  st->bf16 = bf16;
+  st->refine_gap = refine_gap;
+  st->done = max_iter <= 0 ? 1 : 0;
+  st->status = 0;
 }
 
 __global__ void k_scale_copy(const float* __restrict__ in, float* __restrict__ out, size_t n) {
@@ -122,6 +163,7 @@ int tmbir_destroy(tmbir_ctx* ctx) {
 }
 
 int tmbir_set_geometry(tmbir_ctx* ctx, int n_groups, const tmbir_group* groups) {
+  TMBIR_TRACE("tmbir_set_geometry");
   REQUIRE(ctx != nullptr, TMBIR_ERR_ARG, "set_geometry: ctx is NULL");
   REQUIRE(n_groups >= 1 && groups != nullptr, TMBIR_ERR_ARG, "set_geometry: need at least one group");
   Ctx& c = ctx->c;
@@ -172,7 +214,7 @@ int tmbir_set_geometry(tmbir_ctx* ctx, int n_groups, const tmbir_group* groups) 
     GroupDev tmp{};
     tmp.N = gs[i].N;
     tmp.S = gs[i].n_slices;
-    max_blocks += blocks_pass3(tmp);
+    max_blocks += max_blocks_pass3(tmp);  // any slices-per-block choice fits
     voxels += (size_t)gs[i].n_slices * gs[i].N * gs[i].N;
     sino += (size_t)gs[i].n_slices * gs[i].n_angles * gs[i].n_det;
     scratch = std::max(scratch, setup_scratch_bytes(gs[i]));
@@ -242,6 +284,7 @@ int tmbir_workspace_size(const tmbir_ctx* ctx, size_t* bytes) {
 }
 
 int tmbir_set_workspace(tmbir_ctx* ctx, void* d_ws, size_t bytes) {
+  TMBIR_TRACE("tmbir_set_workspace");
   REQUIRE(ctx != nullptr, TMBIR_ERR_ARG, "set_workspace: ctx is NULL");
   Ctx& c = ctx->c;
   REQUIRE(!c.groups.empty(), TMBIR_ERR_STATE, "set_workspace: no geometry");
@@ -263,6 +306,7 @@ int tmbir_set_workspace(tmbir_ctx* ctx, void* d_ws, size_t bytes) {
   c.xbuf[1] = reinterpret_cast<float*>(ws + c.off_xbuf1);
   c.scratch = ws + c.off_scratch;
   TMBIR_CUDA(cudaMemsetAsync(c.state, 0, sizeof(IterState), c.stream));
+  c.state_ready = false;
   for (size_t i = 0; i < c.groups.size(); ++i) {
     const tmbir_group& g = c.groups[i];
     GroupDev& d = c.gdev[i];
@@ -271,6 +315,7 @@ int tmbir_set_workspace(tmbir_ctx* ctx, void* d_ws, size_t bytes) {
     d.na = g.n_angles;
     d.S = g.n_slices;
     d.span = (float)g.span;
+    d.zc = tuned_zc(d.N, d.S);
     d.chat = reinterpret_cast<float*>(ws + c.off_chat[i]);
     d.twN = reinterpret_cast<float2*>(ws + c.off_twN[i]);
     d.twM = reinterpret_cast<float2*>(ws + c.off_twM[i]);
@@ -337,6 +382,7 @@ static int check_params(const tmbir_params* p) {
 }
 
 int tmbir_build_operator(tmbir_ctx* ctx, const float* d_sino, float* d_atg) {
+  TMBIR_TRACE("tmbir_build_operator");
   if (int e = require_ready(ctx, false)) return e;
   REQUIRE(d_sino && d_atg && aligned16(d_sino) && aligned16(d_atg), TMBIR_ERR_ARG,
           "build_operator: sinogram and output must be non-NULL and 16-byte aligned");
@@ -361,6 +407,7 @@ int tmbir_build_operator(tmbir_ctx* ctx, const float* d_sino, float* d_atg) {
 }
 
 int tmbir_fbp(tmbir_ctx* ctx, const float* d_sino, float* d_x0) {
+  TMBIR_TRACE("tmbir_fbp");
   if (int e = require_ready(ctx, false)) return e;
   REQUIRE(d_sino && d_x0 && aligned16(d_sino) && aligned16(d_x0), TMBIR_ERR_ARG,
           "fbp: sinogram and output must be non-NULL and 16-byte aligned");
@@ -467,6 +514,7 @@ static int build_loop_graph(Ctx& c, float* d_x, const float* d_atg, const PriorC
 }
 
 int tmbir_reconstruct(tmbir_ctx* ctx, float* d_x, const float* d_atg, const tmbir_params* prm, tmbir_stats* h_stats) {
+  TMBIR_TRACE("tmbir_reconstruct");
   if (int e = require_ready(ctx, true)) return e;
   if (int e = check_params(prm)) return e;
   REQUIRE(d_x && d_atg && aligned16(d_x) && aligned16(d_atg), TMBIR_ERR_ARG,
@@ -482,12 +530,20 @@ int tmbir_reconstruct(tmbir_ctx* ctx, float* d_x, const float* d_atg, const tmbi
     TMBIR_CUDA(cudaMemcpyAsync(c.dscal + 16 + ng + i, c.gdev[i].gtg, sizeof(double), cudaMemcpyDeviceToDevice, s));
   }
   const bool bf16 = prm->spectra == TMBIR_SPECTRA_BF16;
-  k_init_state<<<1, 1, 0, s>>>(c.state, c.dscal + 16, c.dscal + 16 + ng, ng, prm->L, prm->lambda, prm->sigma,
-                               prm->F_ref, prm->gap_tol, prm->max_iter, prm->restart, bf16 ? 1 : 0,
-                               prm->refine_gap);
-  TMBIR_CHECK_LAUNCH();
-  // x_{-1} = x_0 so that the first (beta = 0) extrapolation reads finite values
-  TMBIR_CUDA(cudaMemcpyAsync(c.xbuf[1], d_x, c.total_voxels * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  if (prm->resume) {
+    // continue the previous (or imported) run: x_k is d_x, x_{k-1} is in slot 2
+    REQUIRE(c.state_ready, TMBIR_ERR_STATE, "reconstruct: nothing to resume (no run or imported state)");
+    k_resume_state<<<1, 1, 0, s>>>(c.state, prm->F_ref, prm->gap_tol, prm->max_iter, prm->restart, bf16 ? 1 : 0,
+                                   prm->refine_gap);
+    TMBIR_CHECK_LAUNCH();
+  } else {
+    k_init_state<<<1, 1, 0, s>>>(c.state, c.dscal + 16, c.dscal + 16 + ng, ng, prm->L, prm->lambda, prm->sigma,
+                                 prm->F_ref, prm->gap_tol, prm->max_iter, prm->restart, bf16 ? 1 : 0,
+                                 prm->refine_gap);
+    TMBIR_CHECK_LAUNCH();
+    // x_{-1} = x_0 so that the first (beta = 0) extrapolation reads finite values
+    TMBIR_CUDA(cudaMemcpyAsync(c.xbuf[1], d_x, c.total_voxels * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  }
   const int iters = prm->max_iter;
   const int kind = !bf16 ? 1 : (prm->refine_gap > 0.0 ? 3 : 2);
   bool graph = prm->use_graph != 0 && s != nullptr;
@@ -513,6 +569,9 @@ int tmbir_reconstruct(tmbir_ctx* ctx, float* d_x, const float* d_atg, const tmbi
   }
   k_gather_final<<<1024, 256, 0, s>>>(c.state, d_x, c.xbuf[0], c.xbuf[1], c.total_voxels);
   TMBIR_CHECK_LAUNCH();
+  k_rotation_reset<<<1, 1, 0, s>>>(c.state);
+  TMBIR_CHECK_LAUNCH();
+  c.state_ready = true;
   c.last_iters = iters;
   if (h_stats) {
     IterState st;
@@ -566,6 +625,7 @@ static int run_explicit(Ctx& c, const StepArgs& a, Pass3Mode m, const PriorC& pc
 }
 
 int tmbir_normal_apply(tmbir_ctx* ctx, const float* d_x, float* d_z) {
+  TMBIR_TRACE("tmbir_normal_apply");
   if (int e = require_ready(ctx, true)) return e;
   REQUIRE(d_x && d_z && aligned16(d_x) && aligned16(d_z), TMBIR_ERR_ARG, "normal_apply: bad buffers");
   REQUIRE(d_x != d_z, TMBIR_ERR_ARG, "normal_apply: in-place not supported");
@@ -579,6 +639,7 @@ int tmbir_normal_apply(tmbir_ctx* ctx, const float* d_x, float* d_z) {
 }
 
 int tmbir_gradient(tmbir_ctx* ctx, const float* d_x, const float* d_atg, const tmbir_params* prm, float* d_grad) {
+  TMBIR_TRACE("tmbir_gradient");
   if (int e = require_ready(ctx, true)) return e;
   if (int e = check_params(prm)) return e;
   REQUIRE(d_x && d_atg && d_grad && aligned16(d_x) && aligned16(d_atg) && aligned16(d_grad), TMBIR_ERR_ARG,
@@ -595,6 +656,7 @@ int tmbir_gradient(tmbir_ctx* ctx, const float* d_x, const float* d_atg, const t
 
 int tmbir_step(tmbir_ctx* ctx, const float* d_x, const float* d_x_prev, double beta, const float* d_atg,
                const tmbir_params* prm, double L, float* d_x_next, double* h_partials) {
+  TMBIR_TRACE("tmbir_step");
   if (int e = require_ready(ctx, true)) return e;
   if (int e = check_params(prm)) return e;
   REQUIRE(d_x && d_x_prev && d_atg && d_x_next && aligned16(d_x) && aligned16(d_x_prev) && aligned16(d_atg) &&
@@ -616,6 +678,7 @@ int tmbir_step(tmbir_ctx* ctx, const float* d_x, const float* d_x_prev, double b
 }
 
 int tmbir_objective(tmbir_ctx* ctx, const float* d_x, const float* d_atg, const tmbir_params* prm, double* h_F) {
+  TMBIR_TRACE("tmbir_objective");
   if (int e = require_ready(ctx, true)) return e;
   if (int e = check_params(prm)) return e;
   REQUIRE(d_x && d_atg && h_F && aligned16(d_x) && aligned16(d_atg), TMBIR_ERR_ARG, "objective: bad arguments");
@@ -639,6 +702,7 @@ int tmbir_objective(tmbir_ctx* ctx, const float* d_x, const float* d_atg, const 
 }
 
 int tmbir_lambda_max(tmbir_ctx* ctx, double* h_out) {
+  TMBIR_TRACE("tmbir_lambda_max");
   if (int e = require_ready(ctx, true)) return e;
   REQUIRE(h_out != nullptr, TMBIR_ERR_ARG, "lambda_max: NULL output");
   Ctx& c = ctx->c;
@@ -658,6 +722,7 @@ int tmbir_kernel(tmbir_ctx* ctx, int group, double* d_K) {
 }
 
 int tmbir_upsample_lanczos3(tmbir_ctx* ctx, const float* d_coarse, int n_slices, int Nc, float* d_fine) {
+  TMBIR_TRACE("tmbir_upsample_lanczos3");
   REQUIRE(ctx != nullptr, TMBIR_ERR_ARG, "upsample: ctx is NULL");
   REQUIRE(d_coarse && d_fine && aligned16(d_coarse) && aligned16(d_fine), TMBIR_ERR_ARG, "upsample: bad buffers");
   REQUIRE(n_slices >= 0 && Nc >= 1 && Nc <= 1 << 15, TMBIR_ERR_ARG, "upsample: bad sizes");
@@ -667,6 +732,7 @@ int tmbir_upsample_lanczos3(tmbir_ctx* ctx, const float* d_coarse, int n_slices,
 
 int tmbir_downsample_sino(tmbir_ctx* ctx, const float* d_sino, int n_slices, int n_angles, int n_det, int factor,
                           float* d_out) {
+  TMBIR_TRACE("tmbir_downsample_sino");
   REQUIRE(ctx != nullptr, TMBIR_ERR_ARG, "downsample: ctx is NULL");
   REQUIRE(d_sino && d_out && aligned16(d_sino) && aligned16(d_out), TMBIR_ERR_ARG, "downsample: bad buffers");
   REQUIRE(n_slices >= 0 && n_angles >= 1 && n_det >= 2 && factor >= 1 && n_det % factor == 0 &&
@@ -677,6 +743,7 @@ int tmbir_downsample_sino(tmbir_ctx* ctx, const float* d_sino, int n_slices, int
 }
 
 int tmbir_pass_times(tmbir_ctx* ctx, float* d_x, const float* d_atg, const tmbir_params* prm, int iters, double* h_ms) {
+  TMBIR_TRACE("tmbir_pass_times");
   if (int e = require_ready(ctx, true)) return e;
   if (int e = check_params(prm)) return e;
   REQUIRE(d_x && d_atg && h_ms && aligned16(d_x) && aligned16(d_atg) && iters >= 1 && iters <= kLogCap, TMBIR_ERR_ARG,
@@ -739,6 +806,9 @@ int tmbir_pass_times(tmbir_ctx* ctx, float* d_x, const float* d_atg, const tmbir
   if (rc) return rc;
   k_gather_final<<<1024, 256, 0, s>>>(c.state, d_x, c.xbuf[0], c.xbuf[1], c.total_voxels);
   TMBIR_CHECK_LAUNCH();
+  k_rotation_reset<<<1, 1, 0, s>>>(c.state);
+  TMBIR_CHECK_LAUNCH();
+  c.state_ready = true;
   TMBIR_CUDA(cudaStreamSynchronize(s));
   for (int j = 0; j < 4; ++j) h_ms[j] = acc[j];
   return TMBIR_OK;
@@ -754,6 +824,123 @@ int tmbir_launch_count(const tmbir_ctx* ctx, long long* h_count) {
     TMBIR_CUDA(cudaStreamSynchronize(c.stream));
   }
   *h_count = __atomic_load_n(&g_launches, __ATOMIC_RELAXED) + dev;
+  return TMBIR_OK;
+}
+
+// ---------------------------------------------------------------- autotuning
+
+int tmbir_autotune(tmbir_ctx* ctx, const float* d_x, const float* d_atg, const tmbir_params* prm, int* h_zc) {
+  TMBIR_TRACE("tmbir_autotune");
+  if (int e = require_ready(ctx, true)) return e;
+  if (int e = check_params(prm)) return e;
+  REQUIRE(d_x && d_atg && aligned16(d_x) && aligned16(d_atg), TMBIR_ERR_ARG, "autotune: bad buffers");
+  Ctx& c = ctx->c;
+  cudaStream_t s = c.stream;
+  const PriorC pc = make_prior(*prm);
+  const int ng = (int)c.gdev.size();
+  for (int i = 0; i < ng; ++i) {
+    TMBIR_CUDA(cudaMemcpyAsync(c.dscal + 16 + i, c.gdev[i].lam_max, sizeof(double), cudaMemcpyDeviceToDevice, s));
+    TMBIR_CUDA(cudaMemcpyAsync(c.dscal + 16 + ng + i, c.gdev[i].gtg, sizeof(double), cudaMemcpyDeviceToDevice, s));
+  }
+  // a state whose iterations never stop, and x_{-1} = x_0: pass 3 (Iterate) writes only the
+  // rotation slot of x_{k+1} and the partial sums, never d_x
+  k_init_state<<<1, 1, 0, s>>>(c.state, c.dscal + 16, c.dscal + 16 + ng, ng, prm->L, prm->lambda, prm->sigma, 0.0, 0.0,
+                               kLogCap, TMBIR_RESTART_GRADIENT, 0, 0.0);
+  TMBIR_CHECK_LAUNCH();
+  TMBIR_CUDA(cudaMemcpyAsync(c.xbuf[1], d_x, c.total_voxels * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  StepArgs a{};
+  a.atg = d_atg;
+  a.xb[0] = const_cast<float*>(d_x);
+  a.xb[1] = c.xbuf[0];
+  a.xb[2] = c.xbuf[1];
+  a.st = c.state;
+  cudaEvent_t e0, e1;
+  TMBIR_CUDA(cudaEventCreate(&e0));
+  TMBIR_CUDA(cudaEventCreate(&e1));
+  int rc = TMBIR_OK;
+  for (int i = 0; i < ng && rc == TMBIR_OK; ++i) {
+    GroupDev& g = c.gdev[i];
+    if ((rc = launch_pass1(g, a, s)) || (rc = launch_pass2(g, c.state, s))) break;
+    std::vector<int> cands;
+    for (int z : {1, 2, 3, 4, 6, 8, 12, 16, 24, 32})
+      if (z <= g.S) cands.push_back(z);
+    g.zc = 0;
+    int T, P;
+    fft_shape(g.N, &T, &P);
+    const int dflt = pass3_slices_per_block(g.S, g.N / (4 * (32 / T)));
+    if (std::find(cands.begin(), cands.end(), dflt) == cands.end()) cands.push_back(dflt);
+    float best = 1e30f;
+    int best_z = dflt;
+    for (int z : cands) {
+      g.zc = z;
+      float ms = 0.f;
+      for (int rep = 0; rep < 4 && rc == TMBIR_OK; ++rep) {
+        if (rep == 1) cudaEventRecord(e0, s);
+        rc = launch_pass3(g, a, Pass3Mode::Iterate, pc, c.partials, 0, s);
+      }
+      if (rc) break;
+      cudaEventRecord(e1, s);
+      if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+        rc = set_error(TMBIR_ERR_CUDA, "autotune: event timing failed");
+        break;
+      }
+      if (ms < best) {
+        best = ms;
+        best_z = z;
+      }
+    }
+    g.zc = best_z;
+    if (h_zc) h_zc[i] = best_z;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned_zc[{g.N, g.S}] = best_z;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  // the block counts changed: the cached iteration graph and the run state are stale
+  if (c.graph_exec) {
+    cudaGraphExecDestroy(c.graph_exec);
+    c.graph_exec = nullptr;
+  }
+  c.state_ready = false;
+  return rc;
+}
+
+int tmbir_state_size(const tmbir_ctx* ctx, size_t* bytes) {
+  if (int e = require_ready(ctx, false)) return e;
+  REQUIRE(bytes != nullptr, TMBIR_ERR_ARG, "state_size: NULL argument");
+  *bytes = kStateHeader + ctx->c.total_voxels * sizeof(float);
+  return TMBIR_OK;
+}
+
+int tmbir_state_export(tmbir_ctx* ctx, void* d_state) {
+  TMBIR_TRACE("tmbir_state_export");
+  if (int e = require_ready(ctx, false)) return e;
+  REQUIRE(d_state && aligned16(d_state), TMBIR_ERR_ARG, "state_export: buffer must be non-NULL and 16-byte aligned");
+  Ctx& c = ctx->c;
+  REQUIRE(c.state_ready, TMBIR_ERR_STATE, "state_export: no run to export");
+  char* p = static_cast<char*>(d_state);
+  TMBIR_CUDA(cudaMemcpyAsync(p, c.state, sizeof(IterState), cudaMemcpyDeviceToDevice, c.stream));
+  TMBIR_CUDA(cudaMemcpyAsync(p + kStateHeader, c.xbuf[1], c.total_voxels * sizeof(float), cudaMemcpyDeviceToDevice,
+                             c.stream));
+  return TMBIR_OK;
+}
+
+int tmbir_state_import(tmbir_ctx* ctx, const void* d_state) {
+  TMBIR_TRACE("tmbir_state_import");
+  if (int e = require_ready(ctx, false)) return e;
+  REQUIRE(d_state && aligned16(d_state), TMBIR_ERR_ARG, "state_import: buffer must be non-NULL and 16-byte aligned");
+  Ctx& c = ctx->c;
+  const char* p = static_cast<const char*>(d_state);
+  // the device-side launch counter is the context's own, not part of the checkpoint
+  long long launches = 0;
+  TMBIR_CUDA(cudaMemcpyAsync(&launches, &c.state->graph_launches, sizeof(long long), cudaMemcpyDeviceToHost, c.stream));
+  TMBIR_CUDA(cudaStreamSynchronize(c.stream));
+  TMBIR_CUDA(cudaMemcpyAsync(c.state, p, sizeof(IterState), cudaMemcpyDeviceToDevice, c.stream));
+  TMBIR_CUDA(cudaMemcpyAsync(&c.state->graph_launches, &launches, sizeof(long long), cudaMemcpyHostToDevice, c.stream));
+  TMBIR_CUDA(cudaMemcpyAsync(c.xbuf[1], p + kStateHeader, c.total_voxels * sizeof(float), cudaMemcpyDeviceToDevice,
+                             c.stream));
+  TMBIR_CUDA(cudaStreamSynchronize(c.stream));
+  c.state_ready = true;
   return TMBIR_OK;
 }
 

@@ -706,6 +706,7 @@ int tmbir_cnn_init(tmbir_cnn* net, unsigned long long seed) {
 }
 
 int tmbir_cnn_net_forward(tmbir_cnn* net, const float* d_in, int batch, float* d_out) {
+  TMBIR_TRACE("tmbir_cnn_net_forward");
   CNN_REQUIRE(net && d_in && d_out && al16(d_in) && al16(d_out), TMBIR_ERR_ARG, "cnn_net_forward: bad buffers");
   CnnNet& n = net->n;
   CNN_REQUIRE(batch >= 1 && batch <= n.max_batch, TMBIR_ERR_ARG, "cnn_net_forward: batch out of range");
@@ -718,6 +719,7 @@ int tmbir_cnn_net_forward(tmbir_cnn* net, const float* d_in, int batch, float* d
 
 int tmbir_cnn_net_backward(tmbir_cnn* net, const float* d_in, const float* d_gout, int batch, float* h_gparams,
                            float* d_gin) {
+  TMBIR_TRACE("tmbir_cnn_net_backward");
   CNN_REQUIRE(net && d_in && d_gout && h_gparams && al16(d_in) && al16(d_gout) && (!d_gin || al16(d_gin)),
               TMBIR_ERR_ARG, "cnn_net_backward: bad buffers");
   CnnNet& n = net->n;
@@ -734,6 +736,7 @@ int tmbir_cnn_net_backward(tmbir_cnn* net, const float* d_in, const float* d_gou
 }
 
 int tmbir_cnn_apply(tmbir_cnn* net, const float* d_x, int batch, float* d_y) {
+  TMBIR_TRACE("tmbir_cnn_apply");
   CNN_REQUIRE(net && d_x && d_y && al16(d_x) && al16(d_y), TMBIR_ERR_ARG, "cnn_apply: bad buffers");
   CnnNet& n = net->n;
   CNN_REQUIRE(batch >= 1 && batch <= n.max_batch, TMBIR_ERR_ARG, "cnn_apply: batch out of range");
@@ -747,6 +750,7 @@ int tmbir_cnn_apply(tmbir_cnn* net, const float* d_x, int batch, float* d_y) {
 }
 
 int tmbir_cnn_train_step(tmbir_cnn* net, const float* d_x, const float* d_target, int batch, float lr, double* h_loss) {
+  TMBIR_TRACE("tmbir_cnn_train_step");
   CNN_REQUIRE(net && d_x && d_target && al16(d_x) && al16(d_target), TMBIR_ERR_ARG, "cnn_train_step: bad buffers");
   CnnNet& n = net->n;
   CNN_REQUIRE(batch >= 1 && batch <= n.max_batch && lr > 0.f, TMBIR_ERR_ARG, "cnn_train_step: bad batch or rate");
@@ -776,6 +780,7 @@ int tmbir_cnn_train_step(tmbir_cnn* net, const float* d_x, const float* d_target
 
 int tmbir_warm_start(tmbir_ctx* ctx, tmbir_cnn* net, const float* d_fbp, const float* d_atg, const tmbir_params* prm,
                      float* d_x0, int* h_used_cnn) {
+  TMBIR_TRACE("tmbir_warm_start");
   CNN_REQUIRE(ctx && net && d_fbp && d_atg && prm && d_x0 && al16(d_fbp) && al16(d_x0), TMBIR_ERR_ARG,
               "warm_start: bad arguments");
   CNN_REQUIRE(d_x0 != d_fbp, TMBIR_ERR_ARG, "warm_start: output must not alias the FBP start");

@@ -1,6 +1,7 @@
 // Internal declarations shared by the translation units of libtmbir.
 #pragma once
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cstddef>
 #include <cstdint>
@@ -37,6 +38,9 @@ struct IterState {
 // Number of FP64 partial sums each reducing block writes.
 constexpr int kParts = 6;  // y.z, y.atg, Phi(y), <G, x_new - x>, G.G, z.z
 constexpr int kLogCap = 1 << 16;
+// checkpoint layout: the iteration state in the first kStateHeader bytes, then x_{k-1}
+constexpr size_t kStateHeader = 256;
+static_assert(sizeof(IterState) <= kStateHeader, "checkpoint header too small");
 
 // qGGMRF constants in the form the kernels use.
 struct PriorC {
@@ -75,6 +79,7 @@ struct GroupDev {
   int* csr_ptr;        // [(2N)^2 + 1]
   int* csr_idx;        // [nnz] strength index a * n_det + (k mod n_det)
   double* csr_w;       // [nnz] kernel weight
+  int zc;              // slices each pass-3 block marches through (0: the default rule)
 };
 
 constexpr int kSpreadW = 10;       // kernel width of the R*g / FBP spreading (error ~1e-9)
@@ -114,8 +119,20 @@ struct Ctx {
   const float* graph_atg = nullptr;
   float* graph_x = nullptr;
   PriorC graph_prior{};
-  int graph_kind = 0;  // 1: one FP32 loop; 2: BF16 loop only; 3: BF16 loop then FP32 loop
+  int graph_kind = 0;
+  bool state_ready = false;  // the iteration state holds a finished run (or an imported one)  // 1: one FP32 loop; 2: BF16 loop only; 3: BF16 loop then FP32 loop
 };
+
+// tracing -------------------------------------------------------------------
+// An NVTX range around each C-ABI call, visible to Nsight tools when one is attached (the
+// header-only NVTX API costs a branch otherwise).
+struct TraceRange {
+  explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+  ~TraceRange() { nvtxRangePop(); }
+  TraceRange(const TraceRange&) = delete;
+  TraceRange& operator=(const TraceRange&) = delete;
+};
+#define TMBIR_TRACE(name) ::tmbir::TraceRange tmbir_trace_range_(name)
 
 // error handling ------------------------------------------------------------
 int set_error(int code, const std::string& msg);
@@ -163,6 +180,12 @@ inline int pass3_slices_per_block(int S, int row_blocks) {
   if (chunks > S) chunks = S;
   return (S + chunks - 1) / chunks;
 }
+// the group's tuned value (tmbir_autotune) or the default rule
+inline int pass3_zc(const GroupDev& g, int row_blocks) {
+  return g.zc > 0 ? (g.zc < g.S ? g.zc : g.S) : pass3_slices_per_block(g.S, row_blocks);
+}
+// partial-sum rows pass 3 can write for a group at most (one slice per block)
+int max_blocks_pass3(const GroupDev& g);
 // cond: the WHILE handle of a device-driven graph loop, set to 0 once the run is done
 // (use_cond 1) or also once the run leaves its BF16 phase (use_cond 2); trip_launches:
 // kernels of one loop trip, added to IterState::graph_launches.

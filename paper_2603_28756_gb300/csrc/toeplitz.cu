@@ -131,8 +131,13 @@ int blocks_pass3(const GroupDev& g) {
   int T, P;
   fft_shape(g.N, &T, &P);
   const int nb = g.N / (4 * (32 / T));
-  const int zc = pass3_slices_per_block(g.S, nb);
+  const int zc = pass3_zc(g, nb);
   return nb * ((g.S + zc - 1) / zc);
+}
+int max_blocks_pass3(const GroupDev& g) {
+  int T, P;
+  fft_shape(g.N, &T, &P);
+  return g.N / (4 * (32 / T)) * g.S;
 }
 
 int launch_finalize(IterState* st, const double* partials, int nblocks, double* log, cudaStream_t s,

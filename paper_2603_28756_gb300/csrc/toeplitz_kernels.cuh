@@ -565,7 +565,7 @@ static int pass3_nm(const GroupDev& g, const StepArgs& a, const PriorC& pc, doub
                     cudaStream_t s) {
   using Gm = Geo<N>;
   if (int e = set_smem_limits<N>()) return e;
-  const int zc = pass3_slices_per_block(g.S, Gm::NB);
+  const int zc = pass3_zc(g, Gm::NB);
   const int blocks = Gm::NB * ((g.S + zc - 1) / zc);
   if (pc.q_is_2 || MODE == 0)
     k_pass3<N, MODE, true, BF><<<blocks, Geo3<N>::THREADS, Geo3<N>::SM, s>>>(g, a, pc, partials, off, zc);

@@ -195,8 +195,8 @@ def test_device_loop_stops_at_gap(prob):
     torch.cuda.synchronize()
     assert 1 < sa.iterations == sb.iterations < 200
     assert torch.equal(a, b)
-    # state init + 4 kernels per iteration (passes 1-3, finalize) + final gather
-    assert n1 - n0 == 4 * sa.iterations + 2
+    # state init + 4 kernels per iteration (passes 1-3, finalize) + final gather and rotation reset
+    assert n1 - n0 == 4 * sa.iterations + 3
     log = prob.ctx.get_log()
     F0 = 0.5 * float(np.sum(prob.g ** 2))
     gaps = [(F - F_ref) / (F0 - F_ref) for F, _, _, _ in log]
@@ -205,7 +205,7 @@ def test_device_loop_stops_at_gap(prob):
     a.zero_()
     n2 = prob.ctx.launch_count()
     sc = prob.ctx.reconstruct(a, prob.d_atg, tm.Params(**dict(prm, gap_tol=0.0, max_iter=5), use_graph=True))
-    assert sc.iterations == 5 and prob.ctx.launch_count() - n2 == 4 * 5 + 2
+    assert sc.iterations == 5 and prob.ctx.launch_count() - n2 == 4 * 5 + 3
 
 
 def test_bf16_spectra_follow_oracle(prob, orc):
@@ -250,6 +250,46 @@ def test_bf16_refinement_matches_fp32(prob):
     assert sa.gap <= 1e-3 and sa.iterations < 300
     assert sa.iterations <= s32.iterations + 5
     assert rel(host(a, prob.x.shape), host(c, prob.x.shape).astype(np.float64)) < 1e-2
+
+
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_checkpoint_resume_is_bitwise(prob, use_graph):
+    # 30 iterations in one run == 18 iterations, export, unrelated work, import, 12 more
+    prm = dict(PRIOR, use_graph=use_graph)
+    a = torch.zeros(prob.x.size, dtype=torch.float32, device="cuda")
+    sa = prob.ctx.reconstruct(a, prob.d_atg, tm.Params(**prm, max_iter=30))
+    b = torch.zeros_like(a)
+    prob.ctx.reconstruct(b, prob.d_atg, tm.Params(**prm, max_iter=18))
+    ck = prob.ctx.state_export()
+    other = dev(prob.x)
+    prob.ctx.reconstruct(other, prob.d_atg, tm.Params(**prm, max_iter=5))
+    prob.ctx.state_import(ck)
+    sb = prob.ctx.reconstruct(b, prob.d_atg, tm.Params(**prm, max_iter=12, resume=True))
+    torch.cuda.synchronize()
+    assert sb.iterations == 30 and sb.restarts == sa.restarts
+    assert torch.equal(a, b)
+    assert sb.objective == sa.objective
+
+
+def test_autotune_keeps_results(prob, orc):
+    # the tuner only changes how pass 3 splits the slices over blocks: the iterates still
+    # follow the oracle, graph == eager, and d_x is left alone
+    x0 = dev(prob.x)
+    keep = x0.clone()
+    zc = prob.ctx.autotune(x0, prob.d_atg, tm.Params(**PRIOR))
+    torch.cuda.synchronize()
+    assert torch.equal(x0, keep)
+    assert len(zc) == 1 and 1 <= zc[0] <= prob.S
+    pr = orc.Prior(**PRIOR)
+    a = torch.zeros(prob.x.size, dtype=torch.float32, device="cuda")
+    b = torch.zeros_like(a)
+    prob.ctx.reconstruct(a, prob.d_atg, tm.Params(**PRIOR, max_iter=20, use_graph=True))
+    prob.ctx.reconstruct(b, prob.d_atg, tm.Params(**PRIOR, max_iter=20, use_graph=False))
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    L = orc.lipschitz(prob.K, prob.N, pr)
+    ref = orc.nesterov(np.zeros(prob.x.shape), prob.atg, float(np.sum(prob.g ** 2)), prob.K, pr, L, 20)
+    assert rel(host(a, prob.x.shape), ref) < 1e-4
 
 
 def test_uneven_groups_equal_separate_contexts(orc):
