@@ -437,9 +437,10 @@ def main():
     ctx.fbp(sino, x)
     pt = ctx.pass_times(x, atg, tm.Params(**PRIOR), iters)
     it_ms = sum(pt)
-    names = ["pass1_rows_fwd", "pass2_columns", "pass3_rows_grad_update", "finalize"]
-    top = max(range(3), key=lambda k: pt[k])
-    bpv = [8.0 + 8.0 * (N + 1) / N, 16.0 * (N + 1) / N, 8.0 * (N + 1) / N + 4 + 8 + 4][top]
+    names = ["pass1_rows_fwd", "pass2_columns", "pass3a_rows_inv", "pass3b_prior_update", "finalize"]
+    top = max(range(4), key=lambda k: pt[k])
+    # algorithmic HBM bytes per voxel-update of each pass (FP32 spectrum)
+    bpv = [8.0 + 8.0 * (N + 1) / N, 16.0 * (N + 1) / N, 8.0 * (N + 1) / N + 4.0, 4.0 + 4 + 8 + 4][top]
     alg_bytes = bpv * S * N * N
     achieved = alg_bytes / (pt[top] / iters * 1e-3) / 1e9
     peak, peak_kind = measured_peaks()

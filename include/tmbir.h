@@ -217,15 +217,17 @@ int tmbir_downsample_sino(tmbir_ctx* ctx, const float* d_sino, int n_slices, int
 /*
  * Measurement: run `iters` iterations of tmbir_reconstruct's loop eagerly (no graph) from d_x
  * with CUDA events recorded on the context stream around every launch, and return the summed
- * device time per kernel kind in h_ms[4] = { pass 1 (rows), pass 2 (columns), pass 3 (rows +
- * gradient + update), finalize }.  d_x receives the iterate like tmbir_reconstruct.
+ * device time per kernel kind in h_ms[5] = { pass 1 (rows), pass 2 (columns), pass 3a (inverse
+ * rows), pass 3b (prior + gradient + update), finalize }.  d_x receives the iterate like
+ * tmbir_reconstruct.
  */
 int tmbir_pass_times(tmbir_ctx* ctx, float* d_x, const float* d_atg, const tmbir_params* prm, int iters, double* h_ms);
 
 /*
- * Autotuner (no counterpart in the paper): times pass 3 of one iteration on d_x / d_atg with
- * every candidate number of slices a block marches through (1, 2, 3, 4, 6, 8, 12, 16, 24, 32
- * up to the group's slice count, and the default rule) and keeps the fastest per group;
+ * Autotuner (no counterpart in the paper): times pass 3b (prior, gradient and update) of one
+ * iteration on d_x / d_atg with every candidate number of slices a block marches through (1,
+ * 2, 3, 4, 6, 8, 12, 16, 24, 32 up to the group's slice count, and the default rule) and keeps
+ * the fastest per group;
  * h_zc (may be NULL) receives the choice per group.  Later contexts of this process with the
  * same image side and slice count start from the choice.  The transform tile shapes (rows per
  * block, threads per row) are fixed per image side at compile time.  d_x is not modified.

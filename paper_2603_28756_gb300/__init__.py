@@ -417,9 +417,9 @@ class Context:
         self._post(state)
 
     def pass_times(self, x, atg, params: Params, iters: int):
-        """Summed device ms of (pass 1, pass 2, pass 3, finalize) over `iters` eager iterations."""
+        """Summed device ms of (pass 1, pass 2, pass 3a, pass 3b, finalize) over `iters` eager iterations."""
         pr = params.c_struct()
-        out = (ctypes.c_double * 4)()
+        out = (ctypes.c_double * 5)()
         self._pre()
         _check(_lib.tmbir_pass_times(self._h, ctypes.c_void_p(_ptr(x)), ctypes.c_void_p(_ptr(atg)), ctypes.byref(pr),
                                      iters, out))

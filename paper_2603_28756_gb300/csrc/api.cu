@@ -226,6 +226,7 @@ int tmbir_set_geometry(tmbir_ctx* ctx, int n_groups, const tmbir_group* groups) 
   c.off_twN.resize(n_groups);
   c.off_twM.resize(n_groups);
   c.off_spec.resize(n_groups);
+  c.off_kz.resize(n_groups);
   c.off_ang.resize(n_groups);
   c.off_K.resize(n_groups);
   c.off_psiK.resize(n_groups);
@@ -241,6 +242,7 @@ int tmbir_set_geometry(tmbir_ctx* ctx, int n_groups, const tmbir_group* groups) 
     c.off_twN[i] = take(N * sizeof(float2));
     c.off_twM[i] = take(N * sizeof(float2));
     c.off_spec[i] = take((size_t)gs[i].n_slices * (N + 1) * N * sizeof(float2));
+    c.off_kz[i] = take((size_t)gs[i].n_slices * N * N * sizeof(float));
     c.off_ang[i] = take(gs[i].n_angles * sizeof(double));
     c.off_K[i] = take((2 * N - 1) * (2 * N - 1) * sizeof(double));
     c.off_psiK[i] = take((2 * N - 1) * sizeof(double));
@@ -320,6 +322,7 @@ int tmbir_set_workspace(tmbir_ctx* ctx, void* d_ws, size_t bytes) {
     d.twN = reinterpret_cast<float2*>(ws + c.off_twN[i]);
     d.twM = reinterpret_cast<float2*>(ws + c.off_twM[i]);
     d.spec = reinterpret_cast<float2*>(ws + c.off_spec[i]);
+    d.kz = reinterpret_cast<float*>(ws + c.off_kz[i]);
     d.angles = reinterpret_cast<double*>(ws + c.off_ang[i]);
     d.K = reinterpret_cast<double*>(ws + c.off_K[i]);
     d.psiK = reinterpret_cast<double*>(ws + c.off_psiK[i]);
@@ -463,7 +466,7 @@ static int enqueue_trip(Ctx& c, float* d_x, const float* d_atg, const PriorC& pc
                         cudaGraphConditionalHandle cond, int use_cond) {
   int nb = 0;
   if (int e = enqueue_passes(c, d_x, d_atg, pc, bf16, &nb)) return e;
-  const int trip_launches = 3 * (int)c.gdev.size() + 1;
+  const int trip_launches = 4 * (int)c.gdev.size() + 1;
   return launch_finalize(c.state, c.partials, nb, c.log, c.stream, cond, use_cond, trip_launches);
 }
 
@@ -768,9 +771,9 @@ int tmbir_pass_times(tmbir_ctx* ctx, float* d_x, const float* d_atg, const tmbir
   a.xb[1] = c.xbuf[0];
   a.xb[2] = c.xbuf[1];
   a.st = c.state;
-  cudaEvent_t ev[5];
+  cudaEvent_t ev[6];
   for (auto& e : ev) TMBIR_CUDA(cudaEventCreate(&e));
-  double acc[4] = {0, 0, 0, 0};
+  double acc[5] = {0, 0, 0, 0, 0};
   int rc = TMBIR_OK;
   for (int k = 0; k < iters && rc == TMBIR_OK; ++k) {
     int off = 0;
@@ -781,26 +784,26 @@ int tmbir_pass_times(tmbir_ctx* ctx, float* d_x, const float* d_atg, const tmbir
       cudaEventRecord(ev[1], s);
       if ((rc = launch_pass2(g, c.state, s, bf16))) break;
       cudaEventRecord(ev[2], s);
-      if ((rc = launch_pass3(g, a, Pass3Mode::Iterate, pc, c.partials, off, s, bf16))) break;
+      if ((rc = launch_pass3(g, a, Pass3Mode::Iterate, pc, c.partials, off, s, bf16, 1))) break;
       cudaEventRecord(ev[3], s);
-      cudaEventSynchronize(ev[3]);
-      float ms;
-      cudaEventElapsedTime(&ms, ev[0], ev[1]);
-      acc[0] += ms;
-      cudaEventElapsedTime(&ms, ev[1], ev[2]);
-      acc[1] += ms;
-      cudaEventElapsedTime(&ms, ev[2], ev[3]);
-      acc[2] += ms;
+      if ((rc = launch_pass3(g, a, Pass3Mode::Iterate, pc, c.partials, off, s, bf16, 2))) break;
+      cudaEventRecord(ev[4], s);
+      cudaEventSynchronize(ev[4]);
+      for (int j = 0; j < 4; ++j) {
+        float ms;
+        cudaEventElapsedTime(&ms, ev[j], ev[j + 1]);
+        acc[j] += ms;
+      }
       off += blocks_pass3(g);
     }
     if (rc) break;
-    cudaEventRecord(ev[3], s);
-    rc = launch_finalize(c.state, c.partials, off, c.log, s);
     cudaEventRecord(ev[4], s);
-    cudaEventSynchronize(ev[4]);
+    rc = launch_finalize(c.state, c.partials, off, c.log, s);
+    cudaEventRecord(ev[5], s);
+    cudaEventSynchronize(ev[5]);
     float ms;
-    cudaEventElapsedTime(&ms, ev[3], ev[4]);
-    acc[3] += ms;
+    cudaEventElapsedTime(&ms, ev[4], ev[5]);
+    acc[4] += ms;
   }
   for (auto& e : ev) cudaEventDestroy(e);
   if (rc) return rc;
@@ -810,7 +813,7 @@ int tmbir_pass_times(tmbir_ctx* ctx, float* d_x, const float* d_atg, const tmbir
   TMBIR_CHECK_LAUNCH();
   c.state_ready = true;
   TMBIR_CUDA(cudaStreamSynchronize(s));
-  for (int j = 0; j < 4; ++j) h_ms[j] = acc[j];
+  for (int j = 0; j < 5; ++j) h_ms[j] = acc[j];
   return TMBIR_OK;
 }
 
@@ -860,7 +863,9 @@ int tmbir_autotune(tmbir_ctx* ctx, const float* d_x, const float* d_atg, const t
   int rc = TMBIR_OK;
   for (int i = 0; i < ng && rc == TMBIR_OK; ++i) {
     GroupDev& g = c.gdev[i];
-    if ((rc = launch_pass1(g, a, s)) || (rc = launch_pass2(g, c.state, s))) break;
+    if ((rc = launch_pass1(g, a, s)) || (rc = launch_pass2(g, c.state, s)) ||
+        (rc = launch_pass3(g, a, Pass3Mode::Iterate, pc, c.partials, 0, s, false, 1)))
+      break;
     std::vector<int> cands;
     for (int z : {1, 2, 3, 4, 6, 8, 12, 16, 24, 32})
       if (z <= g.S) cands.push_back(z);
@@ -876,7 +881,7 @@ int tmbir_autotune(tmbir_ctx* ctx, const float* d_x, const float* d_atg, const t
       float ms = 0.f;
       for (int rep = 0; rep < 4 && rc == TMBIR_OK; ++rep) {
         if (rep == 1) cudaEventRecord(e0, s);
-        rc = launch_pass3(g, a, Pass3Mode::Iterate, pc, c.partials, 0, s);
+        rc = launch_pass3(g, a, Pass3Mode::Iterate, pc, c.partials, 0, s, false, 2);
       }
       if (rc) break;
       cudaEventRecord(e1, s);

@@ -79,6 +79,7 @@ struct GroupDev {
   int* csr_ptr;        // [(2N)^2 + 1]
   int* csr_idx;        // [nnz] strength index a * n_det + (k mod n_det)
   double* csr_w;       // [nnz] kernel weight
+  float* kz;           // [S][N][N] K (*) y between passes 3a and 3b
   int zc;              // slices each pass-3 block marches through (0: the default rule)
 };
 
@@ -111,7 +112,7 @@ struct Ctx {
   bool operator_built = false;
   int last_iters = 0;
   // layout offsets computed at set_geometry
-  std::vector<size_t> off_chat, off_twN, off_twM, off_spec, off_ang, off_K, off_psiK, off_psiA, off_lam, off_gtg,
+  std::vector<size_t> off_chat, off_twN, off_twM, off_spec, off_kz, off_ang, off_K, off_psiK, off_psiA, off_lam, off_gtg,
       off_csr_ptr, off_csr_idx, off_csr_w;
   size_t off_state = 0, off_partials = 0, off_log = 0, off_xbuf0 = 0, off_xbuf1 = 0, off_scratch = 0, off_dscal = 0;
   // CUDA graph cache for reconstruct
@@ -169,8 +170,10 @@ struct StepArgs {
 // variant runs only while the run's storage phase (IterState::bf16) matches it.
 int launch_pass1(const GroupDev& g, const StepArgs& a, cudaStream_t s, bool bf16 = false);
 int launch_pass2(const GroupDev& g, const IterState* st, cudaStream_t s, bool bf16 = false);
+// Pass 3 is two launches: 3a (inverse row transforms into K (*) y) and 3b (prior, gradient,
+// update, partial sums); part selects 3a (1), 3b (2) or both (3).
 int launch_pass3(const GroupDev& g, const StepArgs& a, Pass3Mode mode, const PriorC& pc, double* partials,
-                 int block_offset, cudaStream_t s, bool bf16 = false);
+                 int block_offset, cudaStream_t s, bool bf16 = false, int part = 3);
 int blocks_pass3(const GroupDev& g);
 // Slices each pass-3 block marches through: enough blocks for about four waves of two
 // blocks per SM on 152 SMs, longer marches when the volume has slices to spare.

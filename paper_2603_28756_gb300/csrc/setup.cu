@@ -309,10 +309,10 @@ __global__ void k_scan_add(int* __restrict__ a, int n, const int* __restrict__ s
     if (t > 0) a[i] += sums[t - 1];
   }
 }
-// grid[b][cell] = sum_j wt[j] strengths[b][idx[j]], B slices per launch
+// grid[b][cell] = sum_j wt[j] strengths[idx[j]][b], B slices per launch (sample-major strengths)
 template <int B, class C>
 __global__ void k_csr_gather(const int* __restrict__ ptr, const int* __restrict__ idx, const double* __restrict__ wt,
-                             int ncells, const C* __restrict__ strengths, size_t sstride, C* __restrict__ grid, int nb) {
+                             int ncells, const C* __restrict__ strengths, C* __restrict__ grid, int nb) {
   using S = real_t<C>;
   for (int cell = blockIdx.x * blockDim.x + threadIdx.x; cell < ncells; cell += gridDim.x * blockDim.x) {
     C acc[B];
@@ -320,15 +320,14 @@ __global__ void k_csr_gather(const int* __restrict__ ptr, const int* __restrict_
     for (int b = 0; b < B; ++b) acc[b] = mkc((S)0, (S)0);
     const int e = ptr[cell + 1];
     for (int j = ptr[cell]; j < e; ++j) {
-      const int k = idx[j];
+      const C* sv = strengths + (size_t)idx[j] * B;
       const S w = (S)wt[j];
 #pragma unroll
-      for (int b = 0; b < B; ++b)
-        if (b < nb) {
-          const C v = strengths[b * sstride + k];
-          acc[b].x = fmar(w, v.x, acc[b].x);
-          acc[b].y = fmar(w, v.y, acc[b].y);
-        }
+      for (int b = 0; b < B; ++b) {
+        const C v = sv[b];
+        acc[b].x = fmar(w, v.x, acc[b].x);
+        acc[b].y = fmar(w, v.y, acc[b].y);
+      }
     }
 #pragma unroll
     for (int b = 0; b < B; ++b)
@@ -426,15 +425,20 @@ __global__ void k_prepare_rows(const float* __restrict__ sino, int nd, size_t ro
   }
 }
 
-// G(a,k) = (-1)^k * sum_m g(a,m) exp(+2 pi i k m / nd) / nd: sign flip from s_m = m - nd/2, and the 1/nd of R*
-template <class C>
-__global__ void k_strength_fix(C* rows, int nd, size_t total) {
+// G(a,k) = (-1)^k * sum_m g(a,m) exp(+2 pi i k m / nd) / nd: sign flip from s_m = m - nd/2, and the 1/nd of R*.
+// Written sample-major, out[(a nd + k) B + b], so the gather reads the B slices of a sample
+// from one contiguous run.
+template <int B, class C>
+__global__ void k_strength_fix(const C* __restrict__ rows, int nd, size_t nrows, int nb, C* __restrict__ out) {
   using S = real_t<C>;
+  const size_t total = nrows * B;
   for (size_t id = blockIdx.x * (size_t)blockDim.x + threadIdx.x; id < total; id += (size_t)gridDim.x * blockDim.x) {
-    const int k = (int)(id % nd);
+    const int b = (int)(id % B);
+    const size_t r = id / B;
+    const int k = (int)(r % nd);
     const S sg = (k & 1) ? (S)(-1.0 / nd) : (S)(1.0 / nd);
-    const C v = rows[id];
-    rows[id] = mkc(v.x * sg, v.y * sg);
+    const C v = b < nb ? rows[(size_t)b * nrows + r] : mkc((S)0, (S)0);
+    out[id] = mkc(v.x * sg, v.y * sg);
   }
 }
 
@@ -541,7 +545,8 @@ size_t setup_scratch_bytes(const tmbir_group& g) {
   const size_t k_elems = nf_k + 2 * nf_k * nf_k;
   const size_t rows = (size_t)g.n_angles * g.n_det;
   const size_t B = std::min(g.n_slices, kBackprojBatch);
-  const size_t a_elems = nf_a + B * rows + B * nf_a * nf_a + B * N * nf_a;
+  // twiddles, strengths, grids, pruned transposes, sample-major strengths (always kBackprojBatch wide)
+  const size_t a_elems = nf_a + B * rows + B * nf_a * nf_a + B * N * nf_a + (size_t)kBackprojBatch * rows;
   const size_t csr_build = (nf_a * nf_a + 2 * ((nf_a * nf_a + 2048) / 2048 + 1)) * sizeof(int);
   return std::max(std::max(k_elems, a_elems) * sizeof(double2), csr_build) + 256;
 }
@@ -630,6 +635,7 @@ static int backproject_t(Ctx& c, int gi, const float* d_sino, float* d_out, bool
   C* strengths = tw + nf;
   C* grid = strengths + (size_t)B * rows;
   C* tmp = grid + (size_t)B * ncells;
+  C* strengths_t = tmp + (size_t)B * N * nf;  // [rows][kBackprojBatch]
   for (int b0 = 0; b0 < g.S; b0 += B) {
     const int nb = std::min(B, g.S - b0);
     const float* sino_b = d_sino + g.sino_off + (size_t)b0 * rows;
@@ -640,10 +646,10 @@ static int backproject_t(Ctx& c, int gi, const float* d_sino, float* d_out, bool
     k_twiddle<C><<<(nd + 255) / 256, 256, 0, s>>>(tw, nd);
     TMBIR_CHECK_LAUNCH();
     if (int e = fft_rows(strengths, nd, nb * na, +1, tw, s)) return e;
-    k_strength_fix<C><<<1024, 256, 0, s>>>(strengths, nd, (size_t)nb * rows);
+    k_strength_fix<kBackprojBatch, C><<<1024, 256, 0, s>>>(strengths, nd, rows, nb, strengths_t);
     TMBIR_CHECK_LAUNCH();
     k_csr_gather<kBackprojBatch, C><<<(ncells + 255) / 256, 256, 0, s>>>(g.csr_ptr, g.csr_idx, g.csr_w, ncells,
-                                                                          strengths, rows, grid, nb);
+                                                                          strengths_t, grid, nb);
     TMBIR_CHECK_LAUNCH();
     k_twiddle<C><<<(nf + 255) / 256, 256, 0, s>>>(tw, nf);
     TMBIR_CHECK_LAUNCH();

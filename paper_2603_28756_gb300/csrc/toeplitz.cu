@@ -23,7 +23,7 @@ void fft_shape(int N, int* T, int* P) {
   int pass1_##N(const GroupDev& g, const StepArgs& a, bool bf16, cudaStream_t s);                           \
   int pass2_##N(const GroupDev& g, const IterState* st, bool bf16, cudaStream_t s);                         \
   int pass3_##N(const GroupDev& g, const StepArgs& a, Pass3Mode m, const PriorC& pc, double* partials, int off, \
-                bool bf16, cudaStream_t s);
+                bool bf16, int part, cudaStream_t s);
 TMBIR_DECL_N(64)
 TMBIR_DECL_N(128)
 TMBIR_DECL_N(256)
@@ -124,8 +124,8 @@ int launch_pass2(const GroupDev& g, const IterState* st, cudaStream_t s, bool bf
   TMBIR_DISPATCH_N(g.N, pass2_, g, st, bf16, s);
 }
 int launch_pass3(const GroupDev& g, const StepArgs& a, Pass3Mode m, const PriorC& pc, double* partials, int off,
-                 cudaStream_t s, bool bf16) {
-  TMBIR_DISPATCH_N(g.N, pass3_, g, a, m, pc, partials, off, bf16, s);
+                 cudaStream_t s, bool bf16, int part) {
+  TMBIR_DISPATCH_N(g.N, pass3_, g, a, m, pc, partials, off, bf16, part, s);
 }
 int blocks_pass3(const GroupDev& g) {
   int T, P;

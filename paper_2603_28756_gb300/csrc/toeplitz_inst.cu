@@ -17,7 +17,7 @@ int TMBIR_CAT(pass2_, TMBIR_N)(const GroupDev& g, const IterState* st, bool bf16
   return pass2_n<TMBIR_N>(g, st, bf16, s);
 }
 int TMBIR_CAT(pass3_, TMBIR_N)(const GroupDev& g, const StepArgs& a, Pass3Mode m, const PriorC& pc, double* partials,
-                                int off, bool bf16, cudaStream_t s) {
-  return pass3_n<TMBIR_N>(g, a, m, pc, partials, off, bf16, s);
+                                int off, bool bf16, int part, cudaStream_t s) {
+  return pass3_n<TMBIR_N>(g, a, m, pc, partials, off, bf16, part, s);
 }
 }  // namespace tmbir

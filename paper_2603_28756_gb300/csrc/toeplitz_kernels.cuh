@@ -303,28 +303,67 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) k_pass2(GroupDev g, const Ite
   }
 }
 
-// ---------------------------------------------------------------- pass 3: rows, inverse + gradient
+// ---------------------------------------------------------------- pass 3a: rows, inverse
+// Inverse packed real row transform of every row (one row group per warp, RB rows per block,
+// the layout of pass 1), crop to the first N columns: K (*) y written row-major as FP32.
+template <int N, bool BF>
+__global__ void __launch_bounds__(Geo<N>::THREADS) k_pass3a(GroupDev g, const IterState* st, float* kz) {
+  using Gm = Geo<N>;
+  using F = typename Gm::F;
+  constexpr int T = Gm::T, P = Gm::P, G = Gm::G, RB = Gm::RB, LD = Gm::LD;
+  extern __shared__ float2 sm[];
+  if (st && skip_iter<BF>(st)) return;
+  const int s = blockIdx.x / Gm::NB, rb = blockIdx.x % Gm::NB;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, grp = lane / T, t = lane % T;
+  const int rl = warp * G + grp;
+  const int r0 = rb * RB;
+  float2* tb = sm;
+  {
+    using IO = SpecIO<BF>;
+    const typename IO::T* sp = reinterpret_cast<const typename IO::T*>(g.spec) + (size_t)s * (N + 1) * N + r0;
+    for (int e = threadIdx.x; e < (N + 1) * RB; e += Gm::THREADS) {
+      const int vv = e / RB, rr = e - vv * RB;
+      tb[rr * LD + vv] = IO::ld(sp, (size_t)vv * N + rr);
+    }
+  }
+  __syncthreads();
+  // the length-2N real inverse as a length-N complex inverse of Z[v] = E[v] + i O[v]
+  float2 q[P];
+  SFor<0, P>::run([&](auto i_) {
+    constexpr int i = decltype(i_)::value;
+    const int vp = t + T * i;
+    const float2 zv = tb[rl * LD + vp];
+    const float2 zr = tb[rl * LD + N - vp];
+    const float2 e = make_float2(zv.x + zr.x, zv.y - zr.y);
+    const float2 d = make_float2(zv.x - zr.x, zv.y + zr.y);
+    const float2 o = cmulc(d, __ldg(&g.twM[vp]));
+    q[i] = make_float2(e.x - o.y, e.y + o.x);
+  });
+  __syncthreads();
+  F::template run<1>(q, sm + (warp * G + grp) * F::SMEM, g.twN, t);
+  // the first N/2 packed outputs are the N kept columns
+  float2* out = reinterpret_cast<float2*>(kz + ((size_t)s * N + r0 + rl) * N);
+  SFor<0, P / 2>::run([&](auto i_) {
+    constexpr int i = decltype(i_)::value;
+    out[t + T * i] = q[i];
+  });
+}
+
+// ---------------------------------------------------------------- pass 3b: gradient and update
 // A block owns RB consecutive rows of one group and marches through a chunk of its slices,
 // keeping y for slices z-1, z, z+1 (rows -1 .. RB) in a three-slot ring so every slice of y is
-// read from memory once per chunk.  Per slice: the inverse row transforms give K (*) y for
-// the block's rows; then each thread walks its voxels (consecutive threads on consecutive
-// columns) and sums rho' over the 26 neighbours.  The voxel loop is a plain runtime loop so
-// the unrolled neighbourhood stays small enough for the instruction cache.  Each unordered
-// neighbour pair enters Phi once, from the voxel it is a forward offset of.
-// The transforms run on the first Gm::W warps (one row group each); the voxel phase runs on
-// twice as many warps, so two resident blocks keep 16 warps per SM to hide the latency of the
-// special-function chains.
+// read from memory once per chunk.  Per slice each thread walks its voxels and sums rho' over
+// the 26 neighbours.  The voxel loop is a plain runtime loop so the unrolled neighbourhood
+// stays small enough for the instruction cache.  Each unordered neighbour pair enters Phi
+// once, from the voxel it is a forward offset of.  With only the ring in shared memory and no
+// transform registers, three blocks of eight warps fit an SM (one at N = 2048).
 template <int N>
 struct Geo3 {
   using Gm = Geo<N>;
   static constexpr int RB = Gm::RB, W = 2 * Gm::W, THREADS = 32 * W;
-  // resident blocks per SM the launch bounds ask for: two (16 warps), one for N = 2048 whose
-  // 64-point register transforms and 147 KB ring fill an SM
-  static constexpr int MINB = N >= 2048 ? 1 : 2;
   static constexpr int ROWS = RB + 2;  // ring rows (one halo row each side)
-  static constexpr size_t SM_RING = (size_t)3 * ROWS * N * sizeof(float);
-  static constexpr size_t SM_A = Gm::cmax(Gm::SM1, (size_t)RB * N * sizeof(float));
-  static constexpr size_t SM = SM_A + SM_RING;
+  static constexpr size_t SM = (size_t)3 * ROWS * N * sizeof(float);
+  static constexpr int MINB = SM * 3 <= 220 * 1024 ? 3 : 1;
 };
 
 // y = x + beta (x - x_prev) for block rows -1 .. RB of one slice into a ring slot (zero outside)
@@ -347,13 +386,15 @@ __device__ __forceinline__ void load_ring(float* slot, const float* x, const flo
   }
 }
 
-template <int N, int MODE, bool Q2, bool BF>
+// kz: K (*) y of the group from pass 3a ([slice][row][col]); phase: in Iterate mode, the storage
+// phase this launch belongs to (0 FP32, 1 BF16), checked like the other passes.
+template <int N, int MODE, bool Q2>
 __global__ void __launch_bounds__(Geo3<N>::THREADS, Geo3<N>::MINB)
-    k_pass3(GroupDev g, StepArgs a, PriorC pc, double* partials, int block_offset, int zc) {
+    k_pass3(GroupDev g, StepArgs a, PriorC pc, const float* __restrict__ kz, int phase, double* partials,
+            int block_offset, int zc) {
   using Gm = Geo<N>;
   using G3 = Geo3<N>;
-  using F = typename Gm::F;
-  constexpr int T = Gm::T, P = Gm::P, G = Gm::G, RB = Gm::RB, LD = Gm::LD, ROWS = G3::ROWS;
+  constexpr int RB = Gm::RB, ROWS = G3::ROWS;
   constexpr bool PRIOR = MODE != (int)Pass3Mode::Apply;
   constexpr bool PHI = MODE == (int)Pass3Mode::Step || MODE == (int)Pass3Mode::Iterate ||
                        MODE == (int)Pass3Mode::Objective;
@@ -364,7 +405,7 @@ __global__ void __launch_bounds__(Geo3<N>::THREADS, Geo3<N>::MINB)
   float* out;
   float beta, invL;
   if constexpr (MODE == (int)Pass3Mode::Iterate) {
-    if (skip_iter<BF>(a.st)) return;
+    if (a.st->done || a.st->bf16 != phase) return;
     const int cur = a.st->cur;
     x = cur == 0 ? a.xb[0] : (cur == 1 ? a.xb[1] : a.xb[2]);
     xp = cur == 0 ? a.xb[2] : (cur == 1 ? a.xb[0] : a.xb[1]);
@@ -380,12 +421,8 @@ __global__ void __launch_bounds__(Geo3<N>::THREADS, Geo3<N>::MINB)
   }
   const int rb = blockIdx.x % Gm::NB, chunk = blockIdx.x / Gm::NB;
   const int z0 = chunk * zc, z1 = min(g.S, z0 + zc);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, grp = lane / T, t = lane % T;
-  const int rl = warp * G + grp;
   const int r0 = rb * RB;
-  float2* tb = sm;
-  float* kzs = reinterpret_cast<float*>(sm);  // K(*)y of the block rows, [RB][N], after the transforms
-  float* ring = reinterpret_cast<float*>(reinterpret_cast<char*>(sm) + G3::SM_A);
+  float* ring = reinterpret_cast<float*>(sm);
   const size_t N2 = (size_t)N * N;
   // neighbour weights with 1/sigma^2 folded in: nbr2 sums sigma^2 rho' and sigma^2 rho
   const float2 wf = f2(pc.wf * pc.inv_sig2), we = f2(pc.we * pc.inv_sig2), wc = f2(pc.wc * pc.inv_sig2);
@@ -405,44 +442,13 @@ __global__ void __launch_bounds__(Geo3<N>::THREADS, Geo3<N>::MINB)
 
   for (int z = z0; z < z1; ++z) {
     const size_t slice_base = g.img_off + (size_t)z * N2;
-    // ---- K (*) y for rows r0 .. r0+RB-1 of slice z
-    __syncthreads();
-    {
-      using IO = SpecIO<BF>;
-      const typename IO::T* sp = reinterpret_cast<const typename IO::T*>(g.spec) + (size_t)z * (N + 1) * N + r0;
-      for (int e = threadIdx.x; e < (N + 1) * RB; e += G3::THREADS) {
-        const int vv = e / RB, rr = e - vv * RB;
-        tb[rr * LD + vv] = IO::ld(sp, (size_t)vv * N + rr);
-      }
-    }
+    // the ring slot of slice z+1 is free once every thread has finished slice z-1
     if constexpr (PRIOR) {
+      __syncthreads();
       if (z + 1 < g.S) load_ring<N>(ring + ((z + 1) % 3) * ROWS * N, x, xp, beta, slice_base + N2, r0);
+      __syncthreads();
     }
-    __syncthreads();
-    const bool fft_warp = warp < Gm::W;
-    float2 q[P];
-    if (fft_warp) {
-      SFor<0, P>::run([&](auto i_) {
-        constexpr int i = decltype(i_)::value;
-        const int vp = t + T * i;
-        const float2 zv = tb[rl * LD + vp];
-        const float2 zr = tb[rl * LD + N - vp];
-        const float2 e = make_float2(zv.x + zr.x, zv.y - zr.y);
-        const float2 d = make_float2(zv.x - zr.x, zv.y + zr.y);
-        const float2 o = cmulc(d, __ldg(&g.twM[vp]));
-        q[i] = make_float2(e.x - o.y, e.y + o.x);
-      });
-    }
-    __syncthreads();
-    if (fft_warp) F::template run<1>(q, sm + (warp * G + grp) * F::SMEM, g.twN, t);
-    __syncthreads();
-    if (fft_warp) {
-      SFor<0, P / 2>::run([&](auto i_) {
-        constexpr int i = decltype(i_)::value;
-        reinterpret_cast<float2*>(kzs + rl * N)[t + T * i] = q[i];
-      });
-    }
-    __syncthreads();
+    const float* kzr = kz + (size_t)z * N2 + (size_t)r0 * N;
 
     // ---- per voxel: prior, gradient, update, partial sums.  A thread takes the voxels in
     // columns c and c + N/2 of one block row as the two lanes of packed FP32 pairs (a warp
@@ -457,11 +463,10 @@ __global__ void __launch_bounds__(Geo3<N>::THREADS, Geo3<N>::MINB)
       const int row = i / H, c = i - row * H;
       const int grow = r0 + row;
       const size_t ia = slice_base + (size_t)grow * N + c, ib = ia + H;
-      const float2 zd = make_float2(kzs[row * N + c], kzs[row * N + c + H]);
+      const float2 zd = make_float2(__ldg(kzr + row * N + c), __ldg(kzr + row * N + c + H));
       if constexpr (!PRIOR) {
+        // Apply: pass 3a wrote K (*) x to the output itself; only the partial sums remain
         const float2 xv = make_float2(__ldg(x + ia), __ldg(x + ib));
-        out[ia] = zd.x;
-        out[ib] = zd.y;
         acc[0] = f2fma(xv, zd, acc[0]);
         acc[5] = f2fma(zd, zd, acc[5]);
       } else {
@@ -525,13 +530,13 @@ static int set_smem_limits() {
   TMBIR_CUDA(cudaFuncSetAttribute(k_pass1<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Gm::SM1));
   TMBIR_CUDA(cudaFuncSetAttribute(k_pass2<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Gm::SM2));
   TMBIR_CUDA(cudaFuncSetAttribute(k_pass2<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Gm::SM2));
-#define TMBIR_P3ATTR(M, Q, B)                                                                           \
-  TMBIR_CUDA(cudaFuncSetAttribute(k_pass3<N, M, Q, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+  TMBIR_CUDA(cudaFuncSetAttribute(k_pass3a<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Gm::SM1));
+  TMBIR_CUDA(cudaFuncSetAttribute(k_pass3a<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Gm::SM1));
+#define TMBIR_P3ATTR(M, Q)                                                                           \
+  TMBIR_CUDA(cudaFuncSetAttribute(k_pass3<N, M, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                   (int)Geo3<N>::SM));
-  TMBIR_P3ATTR(0, true, false) TMBIR_P3ATTR(1, true, false) TMBIR_P3ATTR(2, true, false)
-  TMBIR_P3ATTR(3, true, false) TMBIR_P3ATTR(4, true, false) TMBIR_P3ATTR(1, false, false)
-  TMBIR_P3ATTR(2, false, false) TMBIR_P3ATTR(3, false, false) TMBIR_P3ATTR(4, false, false)
-  TMBIR_P3ATTR(3, true, true) TMBIR_P3ATTR(3, false, true)
+  TMBIR_P3ATTR(0, true) TMBIR_P3ATTR(1, true) TMBIR_P3ATTR(2, true) TMBIR_P3ATTR(3, true) TMBIR_P3ATTR(4, true)
+  TMBIR_P3ATTR(1, false) TMBIR_P3ATTR(2, false) TMBIR_P3ATTR(3, false) TMBIR_P3ATTR(4, false)
 #undef TMBIR_P3ATTR
   done = true;
   return TMBIR_OK;
@@ -560,33 +565,44 @@ static int pass2_n(const GroupDev& g, const IterState* st, bool bf16, cudaStream
   TMBIR_CHECK_LAUNCH();
   return TMBIR_OK;
 }
-template <int N, int MODE, bool BF>
-static int pass3_nm(const GroupDev& g, const StepArgs& a, const PriorC& pc, double* partials, int off,
-                    cudaStream_t s) {
+template <int N, int MODE>
+static int pass3_nm(const GroupDev& g, const StepArgs& a, const PriorC& pc, const float* kz, int phase,
+                    double* partials, int off, cudaStream_t s) {
   using Gm = Geo<N>;
-  if (int e = set_smem_limits<N>()) return e;
   const int zc = pass3_zc(g, Gm::NB);
   const int blocks = Gm::NB * ((g.S + zc - 1) / zc);
   if (pc.q_is_2 || MODE == 0)
-    k_pass3<N, MODE, true, BF><<<blocks, Geo3<N>::THREADS, Geo3<N>::SM, s>>>(g, a, pc, partials, off, zc);
+    k_pass3<N, MODE, true><<<blocks, Geo3<N>::THREADS, Geo3<N>::SM, s>>>(g, a, pc, kz, phase, partials, off, zc);
   else
-    k_pass3<N, MODE, false, BF><<<blocks, Geo3<N>::THREADS, Geo3<N>::SM, s>>>(g, a, pc, partials, off, zc);
+    k_pass3<N, MODE, false><<<blocks, Geo3<N>::THREADS, Geo3<N>::SM, s>>>(g, a, pc, kz, phase, partials, off, zc);
   TMBIR_CHECK_LAUNCH();
   return TMBIR_OK;
 }
+// part: 1 pass 3a only, 2 pass 3b only, 3 both
 template <int N>
 static int pass3_n(const GroupDev& g, const StepArgs& a, Pass3Mode m, const PriorC& pc, double* partials, int off,
-                   bool bf16, cudaStream_t s) {
-  if (bf16) {
-    if (m != Pass3Mode::Iterate) return set_error(TMBIR_ERR_ARG, "BF16 spectra are an iteration option only");
-    return pass3_nm<N, 3, true>(g, a, pc, partials, off, s);
+                   bool bf16, int part, cudaStream_t s) {
+  using Gm = Geo<N>;
+  if (int e = set_smem_limits<N>()) return e;
+  if (bf16 && m != Pass3Mode::Iterate) return set_error(TMBIR_ERR_ARG, "BF16 spectra are an iteration option only");
+  // Apply writes K (*) x straight into the output; every other mode into the group's buffer
+  float* kz = m == Pass3Mode::Apply ? a.out + g.img_off : g.kz;
+  const IterState* st = m == Pass3Mode::Iterate ? a.st : nullptr;
+  if (part & 1) {
+    if (bf16)
+      k_pass3a<N, true><<<g.S * Gm::NB, Gm::THREADS, Gm::SM1, s>>>(g, st, kz);
+    else
+      k_pass3a<N, false><<<g.S * Gm::NB, Gm::THREADS, Gm::SM1, s>>>(g, st, kz);
+    TMBIR_CHECK_LAUNCH();
   }
+  if (!(part & 2)) return TMBIR_OK;
+  const int phase = bf16 ? 1 : 0;
   switch (m) {
-    case Pass3Mode::Apply: return pass3_nm<N, 0, false>(g, a, pc, partials, off, s);
-    case Pass3Mode::Gradient: return pass3_nm<N, 1, false>(g, a, pc, partials, off, s);
-    case Pass3Mode::Step: return pass3_nm<N, 2, false>(g, a, pc, partials, off, s);
-    case Pass3Mode::Iterate: return pass3_nm<N, 3, false>(g, a, pc, partials, off, s);
-    default: return pass3_nm<N, 4, false>(g, a, pc, partials, off, s);
+    case Pass3Mode::Apply: return pass3_nm<N, 0>(g, a, pc, kz, phase, partials, off, s);
+    case Pass3Mode::Gradient: return pass3_nm<N, 1>(g, a, pc, kz, phase, partials, off, s);
+    case Pass3Mode::Step: return pass3_nm<N, 2>(g, a, pc, kz, phase, partials, off, s);
+    case Pass3Mode::Iterate: return pass3_nm<N, 3>(g, a, pc, kz, phase, partials, off, s);
+    default: return pass3_nm<N, 4>(g, a, pc, kz, phase, partials, off, s);
   }
 }
 
