@@ -226,8 +226,11 @@ def time_to_gap(tm, ctx, stream, sino, atg, x, barrier, world, wl):
 
     def one_level(use_graph, bf16):
         def run():
-            ctx.build_operator(sino, atg)
-            ctx.fbp(sino, x)
+            if use_graph:
+                ctx.build_operator_fbp(sino, atg, x)
+            else:  # the plain form: one call after the other
+                ctx.build_operator(sino, atg)
+                ctx.fbp(sino, x)
             return ctx.reconstruct(x, atg, tm.Params(**stop, use_graph=use_graph, bf16=bf16,
                                                      refine_gap=REFINE_GAP if bf16 else 0.0))
         return run
@@ -287,13 +290,23 @@ def time_to_gap(tm, ctx, stream, sino, atg, x, barrier, world, wl):
         out["warm_start_training"] = {"error": str(e)}
 
     if 1 in nets:
+        f0 = ctx._empty(S * N * N)
+
         def learned(bf16):
             def run():
-                ctx.build_operator(sino, atg)
-                f0 = ctx.fbp(sino)
+                ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+                ev[0].record(stream)
+                ctx.build_operator_fbp(sino, atg, f0)
+                ev[1].record(stream)
+                ev[2].record(stream)
                 x0, used = nets[1].warm_start(ctx, f0, atg, tm.Params(**PRIOR), out=x)
+                ev[3].record(stream)
                 st = ctx.reconstruct(x, atg, tm.Params(**stop, bf16=bf16, refine_gap=REFINE_GAP if bf16 else 0.0))
+                ev[4].record(stream)
+                torch.cuda.synchronize()
                 st.used_cnn = used
+                st.breakdown_ms = {k: ev[i].elapsed_time(ev[i + 1]) for i, k in
+                                   enumerate(["build_operator_fbp", "-", "warm_start", "iterations"]) if k != "-"}
                 return st
             return run
         forms["learned"] = (learned(False), "CNN-refined FBP start (kept only if its objective is lower), FP32, one "
@@ -330,6 +343,8 @@ def time_to_gap(tm, ctx, stream, sino, atg, x, barrier, world, wl):
         out["forms"][name] = {"ms": ms, "finest_iterations": st.iterations, "gap_reached": st.gap, "form": desc}
         if hasattr(st, "used_cnn"):
             out["forms"][name]["used_cnn"] = st.used_cnn
+        if hasattr(st, "breakdown_ms"):
+            out["forms"][name]["breakdown_ms"] = st.breakdown_ms
     return out
 
 
@@ -399,8 +414,7 @@ def main():
     torch.cuda.synchronize()
 
     def step():
-        ctx.build_operator(sino, atg)
-        ctx.fbp(sino, x)
+        ctx.build_operator_fbp(sino, atg, x)
         ctx.reconstruct(x, atg, prm, want_stats=False)
 
     def barrier():
@@ -466,8 +480,7 @@ def main():
     with torch.cuda.stream(stream):
         for _ in range(args.steps):
             d_sino.copy_(h_sino, non_blocking=True)
-            ctx.build_operator(d_sino, atg)
-            ctx.fbp(d_sino, x)
+            ctx.build_operator_fbp(d_sino, atg, x)
             ctx.reconstruct(x, atg, prm, want_stats=False)
             h_x.copy_(x, non_blocking=True)
     f1.record(stream)
@@ -497,7 +510,7 @@ def main():
             "data": "synthetic",
             "config": {
                 "workload": args.workload, "slices": S, "N": N, "angles": na, "span": span, "iterations": iters,
-                "step": "build_operator + fbp + reconstruct(graph)", "l2": "working set > L2 (no explicit flush)",
+                "step": "build_operator_fbp (R*g and FBP overlapped) + reconstruct(graph)", "l2": "working set > L2 (no explicit flush)",
                 "parallelism": f"replicas{world}", "pass3_slices_per_block": tuned[0],
             },
             "setup_ms": setup_ms,

@@ -162,6 +162,14 @@ int tmbir_build_operator(tmbir_ctx* ctx, const float* d_sino, float* d_atg);
 int tmbir_fbp(tmbir_ctx* ctx, const float* d_sino, float* d_x0);
 
 /*
+ * tmbir_build_operator and tmbir_fbp in one call, the two overlapped: R*g (FP64) runs on the
+ * context stream while the FBP start (FP32) runs on a second stream the context owns, joined
+ * back into the context stream before any later work.  Same results as the two calls;
+ * d_atg and d_x0 must differ.  Needs a non-NULL context stream.
+ */
+int tmbir_build_operator_fbp(tmbir_ctx* ctx, const float* d_sino, float* d_atg, float* d_x0);
+
+/*
  * Fast gradient method with restart (Sec. 2, Eq. 6 with the '+' sign on the prior term)
  * from the image in d_x, which receives the last iterate.  Each iteration:
  *   y = x_k + beta_k (x_k - x_{k-1});  G = K (*) y - R*g + lambda grad Phi(y)   (Eqs. 9, 11)

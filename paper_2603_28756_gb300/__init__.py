@@ -83,7 +83,7 @@ SYMBOLS = [
     "tmbir_normal_apply_static", "tmbir_cnn_param_count", "tmbir_cnn_workspace_size", "tmbir_cnn_create",
     "tmbir_cnn_destroy", "tmbir_cnn_init", "tmbir_cnn_set_weights", "tmbir_cnn_get_weights", "tmbir_cnn_apply",
     "tmbir_cnn_train_step", "tmbir_cnn_net_forward", "tmbir_cnn_net_backward", "tmbir_warm_start",
-    "tmbir_state_size", "tmbir_state_export", "tmbir_state_import", "tmbir_autotune",
+    "tmbir_state_size", "tmbir_state_export", "tmbir_state_import", "tmbir_autotune", "tmbir_build_operator_fbp",
 ]
 
 _lib = None
@@ -138,6 +138,7 @@ def load(path: str | None = None):
         "tmbir_state_export": [vp, vp],
         "tmbir_state_import": [vp, vp],
         "tmbir_autotune": [vp, vp, vp, ctypes.POINTER(_Params), ctypes.POINTER(i)],
+        "tmbir_build_operator_fbp": [vp, vp, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -286,6 +287,16 @@ class Context:
         _check(_lib.tmbir_build_operator(self._h, ctypes.c_void_p(_ptr(sino)), ctypes.c_void_p(_ptr(atg))))
         self._post(sino, atg)
         return atg
+
+    def build_operator_fbp(self, sino, atg=None, x0=None):
+        """build_operator and fbp overlapped on two streams; returns (atg, x0)."""
+        atg = self._empty(self.image_numel()) if atg is None else atg
+        x0 = self._empty(self.image_numel()) if x0 is None else x0
+        self._pre()
+        _check(_lib.tmbir_build_operator_fbp(self._h, ctypes.c_void_p(_ptr(sino)), ctypes.c_void_p(_ptr(atg)),
+                                             ctypes.c_void_p(_ptr(x0))))
+        self._post(sino, atg, x0)
+        return atg, x0
 
     def fbp(self, sino, out=None):
         out = self._empty(self.image_numel()) if out is None else out

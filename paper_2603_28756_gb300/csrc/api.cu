@@ -158,6 +158,9 @@ int tmbir_create(tmbir_ctx** out, void* stream) {
 int tmbir_destroy(tmbir_ctx* ctx) {
   if (!ctx) return TMBIR_OK;
   if (ctx->c.graph_exec) cudaGraphExecDestroy(ctx->c.graph_exec);
+  if (ctx->c.ev_fork) cudaEventDestroy(ctx->c.ev_fork);
+  if (ctx->c.ev_join) cudaEventDestroy(ctx->c.ev_join);
+  if (ctx->c.aux) cudaStreamDestroy(ctx->c.aux);
   delete ctx;
   return TMBIR_OK;
 }
@@ -209,7 +212,7 @@ int tmbir_set_geometry(tmbir_ctx* ctx, int n_groups, const tmbir_group* groups) 
   c.off_state = take(sizeof(IterState));
   c.off_dscal = take((16 + 2 * (size_t)n_groups) * sizeof(double));
   int max_blocks = 0, slices = 0;
-  size_t voxels = 0, sino = 0, scratch = 0;
+  size_t voxels = 0, sino = 0, scratch = 0, fbp_scratch = 0;
   for (int i = 0; i < n_groups; ++i) {
     GroupDev tmp{};
     tmp.N = gs[i].N;
@@ -218,6 +221,7 @@ int tmbir_set_geometry(tmbir_ctx* ctx, int n_groups, const tmbir_group* groups) 
     voxels += (size_t)gs[i].n_slices * gs[i].N * gs[i].N;
     sino += (size_t)gs[i].n_slices * gs[i].n_angles * gs[i].n_det;
     scratch = std::max(scratch, setup_scratch_bytes(gs[i]));
+    fbp_scratch = std::max(fbp_scratch, fbp_scratch_bytes(gs[i]));
   }
   c.max_blocks = std::max(max_blocks, 1);
   c.off_partials = take((size_t)c.max_blocks * kParts * sizeof(double));
@@ -258,6 +262,7 @@ int tmbir_set_geometry(tmbir_ctx* ctx, int n_groups, const tmbir_group* groups) 
   c.off_xbuf0 = take(voxels * sizeof(float));
   c.off_xbuf1 = take(voxels * sizeof(float));
   c.off_scratch = take(scratch);
+  c.off_fbp_scratch = take(fbp_scratch);
   c.scratch_bytes = scratch;
   c.ws_need = align_up(off, 256);
   c.total_voxels = voxels;
@@ -307,6 +312,7 @@ int tmbir_set_workspace(tmbir_ctx* ctx, void* d_ws, size_t bytes) {
   c.xbuf[0] = reinterpret_cast<float*>(ws + c.off_xbuf0);
   c.xbuf[1] = reinterpret_cast<float*>(ws + c.off_xbuf1);
   c.scratch = ws + c.off_scratch;
+  c.fbp_scratch = ws + c.off_fbp_scratch;
   TMBIR_CUDA(cudaMemsetAsync(c.state, 0, sizeof(IterState), c.stream));
   c.state_ready = false;
   for (size_t i = 0; i < c.groups.size(); ++i) {
@@ -405,6 +411,51 @@ int tmbir_build_operator(tmbir_ctx* ctx, const float* d_sino, float* d_atg) {
     if (int e = backproject(c, (int)i, d_sino, d_atg, false, true)) return e;
     if (int e = group_gtg(c, (int)i, d_sino)) return e;
   }
+  c.operator_built = true;
+  return TMBIR_OK;
+}
+
+// build_operator and fbp in one call: R*g (FP64) on the context stream while the FBP start
+// (FP32, its own scratch) runs on a second stream, joined before the call returns its work.
+int tmbir_build_operator_fbp(tmbir_ctx* ctx, const float* d_sino, float* d_atg, float* d_x0) {
+  TMBIR_TRACE("tmbir_build_operator_fbp");
+  if (int e = require_ready(ctx, false)) return e;
+  REQUIRE(d_sino && d_atg && d_x0 && aligned16(d_sino) && aligned16(d_atg) && aligned16(d_x0), TMBIR_ERR_ARG,
+          "build_operator_fbp: buffers must be non-NULL and 16-byte aligned");
+  REQUIRE(d_atg != d_x0, TMBIR_ERR_ARG, "build_operator_fbp: R*g and the start must be different buffers");
+  Ctx& c = ctx->c;
+  REQUIRE(c.stream != nullptr, TMBIR_ERR_ARG, "build_operator_fbp: needs a context stream (not the legacy stream)");
+  if (!c.aux) {
+    TMBIR_CUDA(cudaStreamCreateWithFlags(&c.aux, cudaStreamNonBlocking));
+    TMBIR_CUDA(cudaEventCreateWithFlags(&c.ev_fork, cudaEventDisableTiming));
+    TMBIR_CUDA(cudaEventCreateWithFlags(&c.ev_join, cudaEventDisableTiming));
+  }
+  for (size_t i = 0; i < c.groups.size(); ++i) {
+    // geometry-only parts first: both branches read the spreading matrix
+    if (!c.spread_ready[i]) {
+      if (int e = build_spread_matrix(c, (int)i)) return e;
+      c.spread_ready[i] = true;
+    }
+    if (!c.geom_ready[i]) {
+      if (int e = build_kernel_spectrum(c, (int)i)) return e;
+      if (int e = power_iteration(c, (int)i, 100)) return e;
+      c.geom_ready[i] = true;
+    }
+  }
+  TMBIR_CUDA(cudaEventRecord(c.ev_fork, c.stream));
+  TMBIR_CUDA(cudaStreamWaitEvent(c.aux, c.ev_fork, 0));
+  int rc = TMBIR_OK;
+  for (size_t i = 0; i < c.groups.size() && rc == TMBIR_OK; ++i)
+    rc = backproject(c, (int)i, d_sino, d_x0, true, false, c.fbp_scratch, c.aux);
+  for (size_t i = 0; i < c.groups.size() && rc == TMBIR_OK; ++i) {
+    if ((rc = backproject(c, (int)i, d_sino, d_atg, false, true))) break;
+    rc = group_gtg(c, (int)i, d_sino);
+  }
+  // join whatever was enqueued, also after an error
+  cudaError_t e1 = cudaEventRecord(c.ev_join, c.aux);
+  cudaError_t e2 = cudaStreamWaitEvent(c.stream, c.ev_join, 0);
+  if (rc) return rc;
+  if (e1 != cudaSuccess || e2 != cudaSuccess) return set_error(TMBIR_ERR_CUDA, "build_operator_fbp: stream join failed");
   c.operator_built = true;
   return TMBIR_OK;
 }

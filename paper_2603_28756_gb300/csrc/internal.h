@@ -115,6 +115,10 @@ struct Ctx {
   std::vector<size_t> off_chat, off_twN, off_twM, off_spec, off_kz, off_ang, off_K, off_psiK, off_psiA, off_lam, off_gtg,
       off_csr_ptr, off_csr_idx, off_csr_w;
   size_t off_state = 0, off_partials = 0, off_log = 0, off_xbuf0 = 0, off_xbuf1 = 0, off_scratch = 0, off_dscal = 0;
+  size_t off_fbp_scratch = 0;
+  char* fbp_scratch = nullptr;  // FP32 back-projection scratch, separate so FBP can overlap R*g
+  cudaStream_t aux = nullptr;   // second stream for the overlapped FBP (created on first use)
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   // CUDA graph cache for reconstruct
   cudaGraphExec_t graph_exec = nullptr;
   const float* graph_atg = nullptr;
@@ -201,7 +205,10 @@ void fft_shape(int N, int* T, int* P);
 // setup.cu ------------------------------------------------------------------
 int setup_tables(Ctx& c);  // enqueue uploads of twiddles / psi tables into the workspace
 int build_kernel_spectrum(Ctx& c, int gi);
-int backproject(Ctx& c, int gi, const float* d_sino, float* d_out, bool ramp, bool fp64);
+// scratch / s: null for the context's setup scratch and stream
+int backproject(Ctx& c, int gi, const float* d_sino, float* d_out, bool ramp, bool fp64, char* scratch = nullptr,
+                cudaStream_t s = nullptr);
+size_t fbp_scratch_bytes(const tmbir_group& g);  // FP32 back-projection scratch of one group
 int build_spread_matrix(Ctx& c, int gi);
 size_t spread_nnz(const tmbir_group& g);
 int power_iteration(Ctx& c, int gi, int steps);

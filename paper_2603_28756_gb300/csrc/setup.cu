@@ -550,6 +550,13 @@ size_t setup_scratch_bytes(const tmbir_group& g) {
   const size_t csr_build = (nf_a * nf_a + 2 * ((nf_a * nf_a + 2048) / 2048 + 1)) * sizeof(int);
   return std::max(std::max(k_elems, a_elems) * sizeof(double2), csr_build) + 256;
 }
+size_t fbp_scratch_bytes(const tmbir_group& g) {
+  const size_t N = g.N, nf_a = 2 * N;
+  const size_t rows = (size_t)g.n_angles * g.n_det;
+  const size_t B = std::min(g.n_slices, kBackprojBatch);
+  const size_t a_elems = nf_a + B * rows + B * nf_a * nf_a + B * N * nf_a + (size_t)kBackprojBatch * rows;
+  return a_elems * sizeof(float2) + 256;
+}
 size_t spread_nnz(const tmbir_group& g) { return (size_t)g.n_angles * (g.n_det - 1) * kSpreadW * kSpreadW; }
 
 // device twiddle tables for the setup FFTs (n up to 4N), carved from the front of the scratch
@@ -625,13 +632,13 @@ int build_spread_matrix(Ctx& c, int gi) {
 }
 
 template <class C>
-static int backproject_t(Ctx& c, int gi, const float* d_sino, float* d_out, bool ramp, float scale) {
+static int backproject_t(Ctx& c, int gi, const float* d_sino, float* d_out, bool ramp, float scale, char* scratch,
+                         cudaStream_t s) {
   GroupDev& g = c.gdev[gi];
-  cudaStream_t s = c.stream;
   const int N = g.N, nf = 2 * N, nd = g.nd, na = g.na, ncells = nf * nf;
   const size_t rows = (size_t)na * nd;
   const int B = std::min(g.S, kBackprojBatch);
-  C* tw = reinterpret_cast<C*>(c.scratch);
+  C* tw = reinterpret_cast<C*>(scratch);
   C* strengths = tw + nf;
   C* grid = strengths + (size_t)B * rows;
   C* tmp = grid + (size_t)B * ncells;
@@ -667,11 +674,14 @@ static int backproject_t(Ctx& c, int gi, const float* d_sino, float* d_out, bool
   return TMBIR_OK;
 }
 
-int backproject(Ctx& c, int gi, const float* d_sino, float* d_out, bool ramp, bool fp64) {
+int backproject(Ctx& c, int gi, const float* d_sino, float* d_out, bool ramp, bool fp64, char* scratch,
+                cudaStream_t s) {
   const GroupDev& g = c.gdev[gi];
   const float scale = ramp ? (float)(g.span / g.na) : 1.0f;
-  if (fp64) return backproject_t<double2>(c, gi, d_sino, d_out, ramp, scale);
-  return backproject_t<float2>(c, gi, d_sino, d_out, ramp, scale);
+  if (!scratch) scratch = c.scratch;
+  if (!s) s = c.stream;
+  if (fp64) return backproject_t<double2>(c, gi, d_sino, d_out, ramp, scale, scratch, s);
+  return backproject_t<float2>(c, gi, d_sino, d_out, ramp, scale, scratch, s);
 }
 
 int group_gtg(Ctx& c, int gi, const float* d_sino) {

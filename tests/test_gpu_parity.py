@@ -348,6 +348,14 @@ def test_identical_groups_give_identical_results():
         assert torch.equal(G[:n], G[k * n:(k + 1) * n]), (k, "gradient")
 
 
+def test_overlapped_setup_equals_separate_calls(prob):
+    atg, x0 = prob.ctx.build_operator_fbp(prob.d_sino)
+    atg2 = prob.ctx.build_operator(prob.d_sino)
+    x02 = prob.ctx.fbp(prob.d_sino)
+    torch.cuda.synchronize()
+    assert torch.equal(atg, atg2) and torch.equal(x0, x02)
+
+
 def test_lanczos_upsampling(orc):
     rng = np.random.default_rng(9)
     for S, Nc in [(2, 32), (1, 100)]:
