@@ -266,7 +266,10 @@ int tmbir_launch_count(const tmbir_ctx* ctx, long long* h_count);
  * Learned warm start (not in the paper; the refined start of the task configuration): a
  * four-layer 3x3 convolutional network, channels 1 -> 32 -> 32 -> 32 -> 1, zero padding, a bias
  * per output channel, ReLU after the first three layers.  FP32 master weights, BF16 activations,
- * FP32 accumulation; the 32 -> 32 layers run as implicit GEMMs on the tensor cores.
+ * FP32 accumulation; the 32 -> 32 layers (forward and data gradient) run as implicit GEMMs on
+ * the 5th-generation tensor cores (tcgen05.mma, accumulators in TMEM).  Every wait on the
+ * tensor core is bounded: a convolution that gives up sets a flag that the next synchronising
+ * call (net_backward, train_step with h_loss, warm_start) reports as TMBIR_ERR_TIMEOUT.
  * Parameter vector (tmbir_cnn_param_count() = 19105 floats), layer by layer: weights
  * [cout][cin][3][3] then biases [cout].  Images are float32 [batch][H][W], all H x W.
  * Applied to a start x it gives x + s * net(x / s), s = RMS of x per image; trained with the

@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "tc05.cuh"
 
 namespace tmbir {
 
@@ -29,9 +30,14 @@ constexpr int kOff1 = kOffB0 + kB0, kOffB1 = kOff1 + kW1;
 constexpr int kOff2 = kOffB1 + kB1, kOffB2 = kOff2 + kW1;
 constexpr int kOff3 = kOffB2 + kB1, kOffB3 = kOff3 + kW3;
 constexpr int kParams = kOffB3 + kB3;  // 19105
-constexpr int TH = 8, TW = 32;         // output tile of the tensor-core convolution
-constexpr int PS = 40;                 // padded channel stride of a pixel in shared memory (bf16)
-constexpr int KS = 9 * kC + 8;         // padded row of the GEMM weight matrix (bf16)
+constexpr int kTM = 128;               // pixels of one tensor-core tile (MMA M): a run of one image row
+constexpr int kTX = kTM + 2;           // staged pixels of a row: x0 - 1 .. x0 + kTM
+constexpr int kChunkB = kTX * 16;      // bytes of one staged (row, 8-channel chunk) array
+constexpr int kStageA = 3 * 4 * kChunkB;          // three rows x four chunks
+constexpr int kStageAPad = (kStageA + 127) / 128 * 128;
+constexpr int kWElems = 9 * 4 * kC * 8;           // packed 32 -> 32 weights [tap][chunk][n][8]
+constexpr int kConvSmem = kStageAPad + kWElems * 2;
+constexpr uint32_t kMmaPolls = 1u << 22;          // bound of every wait on an MMA completion
 constexpr int kWgradBlocks = 304;      // blocks of the weight-gradient reductions
 
 struct CnnNet {
@@ -41,10 +47,11 @@ struct CnnNet {
   float* grad;          // [kParams]
   float* adam_m;        // [kParams]
   float* adam_v;        // [kParams]
-  __nv_bfloat16* wg1;   // [32][KS] layer 1 as GEMM B: [co][tap*32 + ci]
+  __nv_bfloat16* wg1;   // layer 1 as the MMA's B operand: [tap][k chunk][co][8], k = ci
   __nv_bfloat16* wg2;   // layer 2
-  __nv_bfloat16* wt1;   // [32][KS] flipped transpose of layer 1 for the data gradient: [ci][tap'*32 + co]
+  __nv_bfloat16* wt1;   // flipped transpose of layer 1 for the data gradient: [tap][k chunk][ci][8], k = co
   __nv_bfloat16* wt2;
+  int* err;             // set when a bounded wait on the tensor core gives up
   __nv_bfloat16* a0;    // activations NHWC [B][H][W][32]
   __nv_bfloat16* a1;
   __nv_bfloat16* a2;
@@ -60,136 +67,139 @@ struct CnnNet {
 };
 
 // ---------------------------------------------------------------- weight layouts
+// Weights of the two 32 -> 32 layers in the layout of the MMA's B operand (no swizzle,
+// K-major): element (tap, k chunk j, row n, e) = W[n][k = 8 j + e][tap] for the forward pass and
+// the flipped transpose W[co = 8 j + e][ci = n][8 - tap] for the data gradient.
 __global__ void k_cnn_pack(const float* __restrict__ master, __nv_bfloat16* wg1, __nv_bfloat16* wg2,
                            __nv_bfloat16* wt1, __nv_bfloat16* wt2) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kC * KS; i += gridDim.x * blockDim.x) {
-    const int r = i / KS, k = i % KS;
-    float v1 = 0.f, v2 = 0.f, t1 = 0.f, t2 = 0.f;
-    if (k < 9 * kC) {
-      const int tap = k / kC, c = k % kC;
-      // forward: row = co, k = tap*32 + ci
-      v1 = master[kOff1 + (r * kC + c) * 9 + tap];
-      v2 = master[kOff2 + (r * kC + c) * 9 + tap];
-      // data gradient: row = ci, k = tap'*32 + co with tap' = 8 - tap (flip)
-      t1 = master[kOff1 + (c * kC + r) * 9 + (8 - tap)];
-      t2 = master[kOff2 + (c * kC + r) * 9 + (8 - tap)];
-    }
-    wg1[i] = __float2bfloat16_rn(v1);
-    wg2[i] = __float2bfloat16_rn(v2);
-    wt1[i] = __float2bfloat16_rn(t1);
-    wt2[i] = __float2bfloat16_rn(t2);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kWElems; i += gridDim.x * blockDim.x) {
+    const int e = i % 8, n = (i / 8) % kC, j = (i / (8 * kC)) % 4, tap = i / (32 * kC);
+    const int k = 8 * j + e;
+    wg1[i] = __float2bfloat16_rn(master[kOff1 + (n * kC + k) * 9 + tap]);
+    wg2[i] = __float2bfloat16_rn(master[kOff2 + (n * kC + k) * 9 + tap]);
+    wt1[i] = __float2bfloat16_rn(master[kOff1 + (k * kC + n) * 9 + (8 - tap)]);
+    wt2[i] = __float2bfloat16_rn(master[kOff2 + (k * kC + n) * 9 + (8 - tap)]);
   }
 }
 
 // ---------------------------------------------------------------- tensor-core 32 -> 32 convolution
-__device__ __forceinline__ void ldsm_x4(unsigned& r0, unsigned& r1, unsigned& r2, unsigned& r3, const void* p) {
-  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
-               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-               : "r"(a));
-}
-__device__ __forceinline__ void mma_bf16(float (&d)[4], unsigned a0, unsigned a1, unsigned a2, unsigned a3, unsigned b0,
-                                         unsigned b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
-
-// out[p][n] = sum_{tap, c} w[n][tap*32 + c] in[p + tap][c]  (+ bias, ReLU), 8 x 32 pixel tiles.
+// out[p][n] = sum_{tap, c} w[tap][n][c] in[p + tap][c] (+ bias, ReLU), as an implicit GEMM on the
+// 5th-generation tensor cores: a tile is 128 consecutive pixels of one image row (MMA M = 128),
+// N = 32 output channels, and each of the nine taps is one K = 32 step (two K = 16 MMAs).
+// The three input rows y-1..y+1 (pixels x0-1..x0+128, zero outside the image) are staged once
+// per tile as 8-channel chunks, [row][chunk][pixel][8], which is the no-swizzle K-major operand
+// layout; tap (dy, dx) is the same arrays started dx pixels (16 bytes) later.  The accumulator
+// lives in 32 TMEM columns; each warp moves its 32 pixels out with tcgen05.ld.
 // MASK (data gradient): the result is multiplied by (mask[p][n] > 0).
 template <bool BIAS_RELU, bool MASK>
 __global__ void __launch_bounds__(128) k_conv32(const __nv_bfloat16* __restrict__ in, int B, int H, int W,
-                                                const __nv_bfloat16* __restrict__ wg, const float* __restrict__ bias,
-                                                const __nv_bfloat16* __restrict__ mask, __nv_bfloat16* __restrict__ out) {
-  __shared__ __align__(16) __nv_bfloat16 sin[(TH + 2) * (TW + 2) * PS];
-  __shared__ __align__(16) __nv_bfloat16 sw[kC * KS];
-  const int tiles_x = (W + TW - 1) / TW, tiles_y = (H + TH - 1) / TH;
-  const int tpi = tiles_x * tiles_y;
+                                                const __nv_bfloat16* __restrict__ wpk, const float* __restrict__ bias,
+                                                const __nv_bfloat16* __restrict__ mask, __nv_bfloat16* __restrict__ out,
+                                                int* err) {
+  namespace tc = tc05;
+  extern __shared__ __align__(128) unsigned char smraw[];
+  unsigned char* sa = smraw;
+  unsigned char* sw = smraw + kStageAPad;
+  __shared__ uint64_t bar;
+  __shared__ uint32_t tmem_base;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int i = threadIdx.x; i < kC * KS / 8; i += 128) reinterpret_cast<int4*>(sw)[i] = reinterpret_cast<const int4*>(wg)[i];
-  for (int tile = blockIdx.x; tile < B * tpi; tile += gridDim.x) {
-    const int b = tile / tpi, ty = (tile % tpi) / tiles_x, tx = tile % tiles_x;
-    const int y0 = ty * TH, x0 = tx * TW;
-    __syncthreads();
-    // input tile with a one-pixel halo, 4 channels (8 bytes) per step
-    for (int e = threadIdx.x; e < (TH + 2) * (TW + 2) * (kC / 4); e += 128) {
-      const int c4 = e % (kC / 4), pix = e / (kC / 4);
-      const int py = pix / (TW + 2), px = pix % (TW + 2);
-      const int gy = y0 - 1 + py, gx = x0 - 1 + px;
-      uint2 v = make_uint2(0u, 0u);
-      if (gy >= 0 && gy < H && gx >= 0 && gx < W)
-        v = *reinterpret_cast<const uint2*>(in + (((size_t)b * H + gy) * W + gx) * kC + c4 * 4);
-      *reinterpret_cast<uint2*>(sin + pix * PS + c4 * 4) = v;
-    }
-    __syncthreads();
-    // warp: tile rows 2*warp, 2*warp+1 -> 4 m16 tiles (16 consecutive pixels of one row)
-    float acc[4][4][4];
-#pragma unroll
-    for (int m = 0; m < 4; ++m)
-#pragma unroll
-      for (int n = 0; n < 4; ++n)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[m][n][j] = 0.f;
-#pragma unroll 1
-    for (int tap = 0; tap < 9; ++tap) {
-      const int dy = tap / 3, dx = tap % 3;
-#pragma unroll
-      for (int kh = 0; kh < 2; ++kh) {
-        unsigned bfr[4][2];
-#pragma unroll
-        for (int np = 0; np < 2; ++np) {
-          // two n8 tiles: rows co = np*16 + (lane % 8) + 8 * (lane / 16), k offset 8 * ((lane / 8) % 2)
-          const int co = np * 16 + (lane & 7) + ((lane >> 4) << 3);
-          const int kk = tap * kC + kh * 16 + (((lane >> 3) & 1) << 3);
-          unsigned r0, r1, r2, r3;
-          ldsm_x4(r0, r1, r2, r3, sw + co * KS + kk);
-          bfr[np * 2 + 0][0] = r0;
-          bfr[np * 2 + 0][1] = r1;
-          bfr[np * 2 + 1][0] = r2;
-          bfr[np * 2 + 1][1] = r3;
-        }
-#pragma unroll
-        for (int m = 0; m < 4; ++m) {
-          const int row = 2 * warp + (m >> 1), col0 = (m & 1) * 16;
-          const int px = col0 + (lane & 15);
-          const int pix = (row + dy) * (TW + 2) + px + dx;
-          unsigned a0, a1, a2, a3;
-          ldsm_x4(a0, a1, a2, a3, sin + pix * PS + kh * 16 + ((lane >> 4) << 3));
-#pragma unroll
-          for (int n = 0; n < 4; ++n) mma_bf16(acc[m][n], a0, a1, a2, a3, bfr[n][0], bfr[n][1]);
-        }
-      }
-    }
-    // epilogue: fragment (m, n): rows lane/4 and lane/4 + 8, channels n*8 + 2*(lane%4) + {0,1}
-#pragma unroll
-    for (int m = 0; m < 4; ++m) {
-      const int row = 2 * warp + (m >> 1), col0 = (m & 1) * 16;
-      const int gy = y0 + row;
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int gx = x0 + col0 + (lane >> 2) + 8 * h;
-        if (gy >= H || gx >= W) continue;
-        const size_t pbase = (((size_t)b * H + gy) * W + gx) * kC;
-#pragma unroll
-        for (int n = 0; n < 4; ++n) {
-          const int ch = n * 8 + 2 * (lane & 3);
-          float v0 = acc[m][n][2 * h], v1 = acc[m][n][2 * h + 1];
-          if constexpr (BIAS_RELU) {
-            v0 = fmaxf(v0 + bias[ch], 0.f);
-            v1 = fmaxf(v1 + bias[ch + 1], 0.f);
-          }
-          if constexpr (MASK) {
-            const __nv_bfloat162 mk = *reinterpret_cast<const __nv_bfloat162*>(mask + pbase + ch);
-            if (!(__bfloat162float(mk.x) > 0.f)) v0 = 0.f;
-            if (!(__bfloat162float(mk.y) > 0.f)) v1 = 0.f;
-          }
-          *reinterpret_cast<__nv_bfloat162*>(out + pbase + ch) = __floats2bfloat162_rn(v0, v1);
-        }
-      }
-    }
+  constexpr uint32_t IDESC = tc::idesc_bf16_f32<kTM, kC>();
+  const unsigned char* wsrc = reinterpret_cast<const unsigned char*>(wpk);
+  for (int i = threadIdx.x; i < kWElems * 2 / 16; i += blockDim.x) tc::cp_async16(sw + 16 * i, wsrc + 16 * i, true);
+  if (warp == 0) tc::tmem_alloc<32>(&tmem_base);
+  if (threadIdx.x == 0) {
+    tc::mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = tmem_base;
+  const uint32_t a_base = tc::smem_addr(sa), w_base = tc::smem_addr(sw);
+  const int tiles_x = (W + kTM - 1) / kTM;
+  const int ntiles = B * H * tiles_x;
+  uint32_t parity = 0;
+  bool failed = false;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int tx = tile % tiles_x, row = tile / tiles_x;
+    const int y = row % H, b = row / H;
+    const int x0 = tx * kTM;
+    for (int e = threadIdx.x; e < 3 * 4 * kTX; e += blockDim.x) {
+      const int px = e % kTX, j = (e / kTX) % 4, dy = e / (4 * kTX);
+      const int gy = y + dy - 1, gx = x0 - 1 + px;
+      const bool v = gy >= 0 && gy < H && gx >= 0 && gx < W;
+      const __nv_bfloat16* src = v ? in + (((size_t)b * H + gy) * W + gx) * kC + 8 * j : in;
+      tc::cp_async16(sa + (dy * 4 + j) * kChunkB + px * 16, src, v);
+    }
+    tc::cp_async_wait_all();
+    tc::fence_async_shared();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      tc::fence_after_sync();
+#pragma unroll
+      for (int tap = 0; tap < 9; ++tap) {
+        const int dy = tap / 3, dx = tap % 3;
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+          const uint64_t ad = tc::smem_desc(a_base + (dy * 4 + 2 * s) * kChunkB + dx * 16, kChunkB, 128);
+          const uint64_t bd = tc::smem_desc(w_base + (tap * 4 + 2 * s) * (kC * 16), kC * 16, 128);
+          tc::mma_bf16(tmem, ad, bd, IDESC, (tap | s) ? 1u : 0u);
+        }
+      }
+      tc::mma_commit(&bar);
+    }
+    const bool ok = tc::mbar_wait(&bar, parity, kMmaPolls);
+    parity ^= 1u;
+    if (__syncthreads_or(!ok)) {
+      failed = true;
+      break;
+    }
+    tc::fence_after_sync();
+    float v[32];
+    tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16), v);
+    const int gx = x0 + warp * 32 + lane;
+    if (gx < W) {
+      const size_t pbase = (((size_t)b * H + y) * W + gx) * kC;
+      if constexpr (BIAS_RELU) {
+#pragma unroll
+        for (int c = 0; c < kC; ++c) v[c] = fmaxf(v[c] + __ldg(bias + c), 0.f);
+      }
+      if constexpr (MASK) {
+        const uint4* mk = reinterpret_cast<const uint4*>(mask + pbase);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const uint4 m = mk[q];
+          const __nv_bfloat162* mb = reinterpret_cast<const __nv_bfloat162*>(&m);
+#pragma unroll
+          for (int h = 0; h < 4; ++h) {
+            const float2 f = __bfloat1622float2(mb[h]);
+            if (!(f.x > 0.f)) v[8 * q + 2 * h] = 0.f;
+            if (!(f.y > 0.f)) v[8 * q + 2 * h + 1] = 0.f;
+          }
+        }
+      }
+      uint4* dst = reinterpret_cast<uint4*>(out + pbase);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        uint4 o;
+        __nv_bfloat162* ob = reinterpret_cast<__nv_bfloat162*>(&o);
+#pragma unroll
+        for (int h = 0; h < 4; ++h) ob[h] = __floats2bfloat162_rn(v[8 * q + 2 * h], v[8 * q + 2 * h + 1]);
+        dst[q] = o;
+      }
+    }
+    // TMEM and the staged rows are reused by the next tile
+    tc::fence_before_sync();
+    __syncthreads();
+  }
+  if (failed) {
+    // give the outstanding MMAs a second bounded chance to finish before freeing their TMEM
+    tc::mbar_wait(&bar, parity ^ 1u, kMmaPolls);
+    if (threadIdx.x == 0) atomicExch(err, 1);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc<32>(tmem);
 }
 
 // ---------------------------------------------------------------- first and last layers (CUDA cores)
@@ -505,24 +515,37 @@ static size_t cnn_bytes(int B, int H, int W, size_t* offs) {
   offs[1] = take(kParams * 4);                         // grad
   offs[2] = take(kParams * 4);                         // m
   offs[3] = take(kParams * 4);                         // v
-  for (int i = 0; i < 4; ++i) offs[4 + i] = take((size_t)kC * KS * 2);  // wg1 wg2 wt1 wt2
+  for (int i = 0; i < 4; ++i) offs[4 + i] = take((size_t)kWElems * 2);  // wg1 wg2 wt1 wt2
   for (int i = 0; i < 5; ++i) offs[8 + i] = take(P * kC * 2);           // a0 a1 a2 g1 g2
   for (int i = 0; i < 3; ++i) offs[13 + i] = take(P * 4);               // xin out gout
   offs[16] = take((size_t)B * 4);                                        // sig
   offs[17] = take((size_t)kWgradBlocks * kW1 * 4);                       // wpart
   offs[18] = take(4096 * 8);                                             // dpart
+  offs[19] = take(256);                                                  // err
   return (off + 255) / 256 * 256;
 }
 
 static int conv32(CnnNet& n, const __nv_bfloat16* in, int B, const __nv_bfloat16* w, const float* bias,
                   const __nv_bfloat16* mask, __nv_bfloat16* out, bool relu) {
-  const int tiles = B * ((n.H + TH - 1) / TH) * ((n.W + TW - 1) / TW);
-  const int blocks = std::min(tiles, 152 * 8);
+  const int tiles = B * n.H * ((n.W + kTM - 1) / kTM);
+  const int blocks = std::min(tiles, 152 * 4);
   if (relu)
-    k_conv32<true, false><<<blocks, 128, 0, n.stream>>>(in, B, n.H, n.W, w, bias, nullptr, out);
+    k_conv32<true, false><<<blocks, 128, kConvSmem, n.stream>>>(in, B, n.H, n.W, w, bias, nullptr, out, n.err);
   else
-    k_conv32<false, true><<<blocks, 128, 0, n.stream>>>(in, B, n.H, n.W, w, bias, mask, out);
+    k_conv32<false, true><<<blocks, 128, kConvSmem, n.stream>>>(in, B, n.H, n.W, w, bias, mask, out, n.err);
   TMBIR_CHECK_LAUNCH();
+  return TMBIR_OK;
+}
+// TMBIR_ERR_TIMEOUT (and the flag cleared) when a convolution gave up waiting on the tensor core;
+// reads the flag after the stream has drained up to here
+static int check_tc(CnnNet& n) {
+  int flag = 0;
+  TMBIR_CUDA(cudaMemcpyAsync(&flag, n.err, sizeof(int), cudaMemcpyDeviceToHost, n.stream));
+  TMBIR_CUDA(cudaStreamSynchronize(n.stream));
+  if (flag) {
+    TMBIR_CUDA(cudaMemsetAsync(n.err, 0, sizeof(int), n.stream));
+    return set_error(TMBIR_ERR_TIMEOUT, "cnn: a tensor-core convolution timed out waiting for its MMAs");
+  }
   return TMBIR_OK;
 }
 
@@ -584,7 +607,7 @@ static int net_backward(CnnNet& n, int B, float* gin) {
 }
 
 static int pack(CnnNet& n) {
-  k_cnn_pack<<<(kC * KS + 255) / 256, 256, 0, n.stream>>>(n.master, n.wg1, n.wg2, n.wt1, n.wt2);
+  k_cnn_pack<<<(kWElems + 255) / 256, 256, 0, n.stream>>>(n.master, n.wg1, n.wg2, n.wt1, n.wt2);
   TMBIR_CHECK_LAUNCH();
   return TMBIR_OK;
 }
@@ -605,7 +628,7 @@ using namespace tmbir;
 
 struct tmbir_cnn {
   CnnNet n;
-  size_t offs[19];
+  size_t offs[20];
 };
 
 #define CNN_REQUIRE(cond, code, msg) \
@@ -622,7 +645,7 @@ int tmbir_cnn_param_count(void) { return kParams; }
 int tmbir_cnn_workspace_size(int max_batch, int H, int W, size_t* bytes) {
   CNN_REQUIRE(bytes && max_batch >= 1 && H >= 1 && W >= 1 && (size_t)max_batch * H * W < ((size_t)1 << 31),
               TMBIR_ERR_ARG, "cnn_workspace_size: bad sizes");
-  size_t offs[19];
+  size_t offs[20];
   *bytes = cnn_bytes(max_batch, H, W, offs);
   return TMBIR_OK;
 }
@@ -660,6 +683,11 @@ int tmbir_cnn_create(tmbir_cnn** out, void* stream, int max_batch, int H, int W,
   n.sig = reinterpret_cast<float*>(ws + c->offs[16]);
   n.wpart = reinterpret_cast<float*>(ws + c->offs[17]);
   n.dpart = reinterpret_cast<double*>(ws + c->offs[18]);
+  n.err = reinterpret_cast<int*>(ws + c->offs[19]);
+  if (cudaMemsetAsync(n.err, 0, sizeof(int), n.stream) != cudaSuccess) {
+    delete c;
+    return set_error(TMBIR_ERR_CUDA, "cnn_create: cudaMemsetAsync failed");
+  }
   n.step = 0;
   *out = c;
   return TMBIR_OK;
@@ -731,8 +759,7 @@ int tmbir_cnn_net_backward(tmbir_cnn* net, const float* d_in, const float* d_gou
   TMBIR_CUDA(cudaMemsetAsync(n.grad, 0, kParams * sizeof(float), n.stream));
   if (int e = net_backward(n, batch, d_gin)) return e;
   TMBIR_CUDA(cudaMemcpyAsync(h_gparams, n.grad, kParams * sizeof(float), cudaMemcpyDeviceToHost, n.stream));
-  TMBIR_CUDA(cudaStreamSynchronize(n.stream));
-  return TMBIR_OK;
+  return check_tc(n);
 }
 
 int tmbir_cnn_apply(tmbir_cnn* net, const float* d_x, int batch, float* d_y) {
@@ -773,7 +800,7 @@ int tmbir_cnn_train_step(tmbir_cnn* net, const float* d_x, const float* d_target
   if (int e = pack(n)) return e;
   if (h_loss) {
     TMBIR_CUDA(cudaMemcpyAsync(h_loss, n.dpart + lb, sizeof(double), cudaMemcpyDeviceToHost, n.stream));
-    TMBIR_CUDA(cudaStreamSynchronize(n.stream));
+    return check_tc(n);
   }
   return TMBIR_OK;
 }
@@ -824,7 +851,7 @@ int tmbir_warm_start(tmbir_ctx* ctx, tmbir_cnn* net, const float* d_fbp, const f
   const int use = F_cnn < F_fbp ? 1 : 0;
   if (!use) TMBIR_CUDA(cudaMemcpyAsync(d_x0, d_fbp, S * HW * sizeof(float), cudaMemcpyDeviceToDevice, c.stream));
   if (h_used_cnn) *h_used_cnn = use;
-  return TMBIR_OK;
+  return check_tc(n);
 }
 
 }  // extern "C"
