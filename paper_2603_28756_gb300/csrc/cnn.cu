@@ -233,30 +233,55 @@ __global__ void k_conv_first(const float* __restrict__ x, int B, int H, int W, c
   }
 }
 
-// out[p] = b3 + sum_{tap, ci} w3[ci][tap] a2[p + tap][ci]
-__global__ void k_conv_last(const __nv_bfloat16* __restrict__ a2, int B, int H, int W, const float* __restrict__ master,
-                            float* __restrict__ out) {
-  __shared__ float w[kW3 + kB3];
-  for (int i = threadIdx.x; i < kW3 + kB3; i += blockDim.x) w[i] = master[kOff3 + i];
-  __syncthreads();
-  const size_t total = (size_t)B * H * W;
-  for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < total; p += (size_t)gridDim.x * blockDim.x) {
-    const int xx = (int)(p % W), yy = (int)((p / W) % H);
-    const size_t b = p / ((size_t)H * W);
-    float s = w[kW3];
-#pragma unroll 1
-    for (int t = 0; t < 9; ++t) {
-      const int gy = yy + t / 3 - 1, gx = xx + t % 3 - 1;
-      if (gy < 0 || gy >= H || gx < 0 || gx >= W) continue;
-      const __nv_bfloat162* a = reinterpret_cast<const __nv_bfloat162*>(a2 + ((b * H + gy) * W + gx) * kC);
+// out[p] = b3 + sum_{tap, ci} w3[ci][tap] a2[p + tap][ci], as out[p] = b3 + sum_tap T[p + tap][tap]
+// with T[q][tap] = sum_ci w3[ci][tap] a2[q][ci]: a block computes T once per pixel of its 8 x 32
+// tile plus a one-pixel halo (each activation vector read once) and sums the nine shifted
+// entries from shared memory.
+constexpr int kLH = 8, kLW = 32;
+__global__ void __launch_bounds__(256) k_conv_last(const __nv_bfloat16* __restrict__ a2, int B, int H, int W,
+                                                   const float* __restrict__ master, float* __restrict__ out) {
+  __shared__ float w[kC][12];  // w3[ci][tap], rows padded to 12 for aligned vector reads
+  __shared__ float T[(kLH + 2) * (kLW + 2)][9];
+  for (int i = threadIdx.x; i < kC * 9; i += blockDim.x) w[i / 9][i % 9] = master[kOff3 + i];
+  const float b3 = master[kOff3 + kW3];
+  const int tiles_x = (W + kLW - 1) / kLW, tiles_y = (H + kLH - 1) / kLH;
+  const int tpi = tiles_x * tiles_y;
+  for (int tile = blockIdx.x; tile < B * tpi; tile += gridDim.x) {
+    const int b = tile / tpi, ty = (tile % tpi) / tiles_x, tx = tile % tiles_x;
+    const int y0 = ty * kLH, x0 = tx * kLW;
+    __syncthreads();  // weights loaded; T of the previous tile consumed
+    for (int q = threadIdx.x; q < (kLH + 2) * (kLW + 2); q += blockDim.x) {
+      const int gy = y0 - 1 + q / (kLW + 2), gx = x0 - 1 + q % (kLW + 2);
+      float t[9];
 #pragma unroll
-      for (int c = 0; c < kC; c += 2) {
-        const float2 v = __bfloat1622float2(a[c / 2]);
-        s = fmaf(w[c * 9 + t], v.x, s);
-        s = fmaf(w[(c + 1) * 9 + t], v.y, s);
+      for (int k = 0; k < 9; ++k) t[k] = 0.f;
+      if (gy >= 0 && gy < H && gx >= 0 && gx < W) {
+        const uint4* src = reinterpret_cast<const uint4*>(a2 + (((size_t)b * H + gy) * W + gx) * kC);
+#pragma unroll
+        for (int v4 = 0; v4 < 4; ++v4) {
+          const uint4 u = src[v4];
+          const __nv_bfloat162* h2 = reinterpret_cast<const __nv_bfloat162*>(&u);
+#pragma unroll
+          for (int h = 0; h < 4; ++h) {
+            const float2 a = __bfloat1622float2(h2[h]);
+            const int ci = 8 * v4 + 2 * h;
+#pragma unroll
+            for (int k = 0; k < 9; ++k) t[k] = fmaf(w[ci + 1][k], a.y, fmaf(w[ci][k], a.x, t[k]));
+          }
+        }
       }
+#pragma unroll
+      for (int k = 0; k < 9; ++k) T[q][k] = t[k];
     }
-    out[p] = s;
+    __syncthreads();
+    const int ly = threadIdx.x / kLW, lx = threadIdx.x % kLW;
+    const int gy = y0 + ly, gx = x0 + lx;
+    if (gy < H && gx < W) {
+      float s = b3;
+#pragma unroll
+      for (int k = 0; k < 9; ++k) s += T[(ly + k / 3) * (kLW + 2) + lx + k % 3][k];
+      out[((size_t)b * H + gy) * W + gx] = s;
+    }
   }
 }
 
@@ -433,22 +458,29 @@ __global__ void k_reduce_parts(const float* __restrict__ part, int nblocks, int 
 }
 
 // ---------------------------------------------------------------- normalisation, loss, optimiser
-// per image: sig = sqrt(mean x^2) (1 if zero); xin = x / sig
-__global__ void k_norm_stats(const float* __restrict__ x, int HW, float* __restrict__ sig) {
+// per image: sig = sqrt(mean x^2) (1 if zero); xin = x / sig.  kNormBlocks blocks per image
+// each reduce a strided share in FP64, then one block per image adds the shares in order.
+constexpr int kNormBlocks = 64;
+__global__ void k_norm_partial(const float* __restrict__ x, int HW, double* __restrict__ part) {
   __shared__ double sh[256];
-  const float* xb = x + (size_t)blockIdx.x * HW;
+  const int b = blockIdx.y;
+  const float* xb = x + (size_t)b * HW;
   double s = 0.0;
-  for (int i = threadIdx.x; i < HW; i += blockDim.x) s += (double)xb[i] * xb[i];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < HW; i += kNormBlocks * blockDim.x) s += (double)xb[i] * xb[i];
   sh[threadIdx.x] = s;
   __syncthreads();
   for (int o = 128; o > 0; o >>= 1) {
     if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
     __syncthreads();
   }
-  if (threadIdx.x == 0) {
-    const double r = sqrt(sh[0] / HW);
-    sig[blockIdx.x] = r > 0 ? (float)r : 1.f;
-  }
+  if (threadIdx.x == 0) part[(size_t)b * kNormBlocks + blockIdx.x] = sh[0];
+}
+__global__ void k_norm_stats(const double* __restrict__ part, int HW, float* __restrict__ sig) {
+  if (threadIdx.x != 0) return;
+  double s = 0.0;
+  for (int k = 0; k < kNormBlocks; ++k) s += part[(size_t)blockIdx.x * kNormBlocks + k];
+  const double r = sqrt(s / HW);
+  sig[blockIdx.x] = r > 0 ? (float)r : 1.f;
 }
 __global__ void k_scale_in(const float* __restrict__ x, int HW, size_t total, const float* __restrict__ sig,
                            float* __restrict__ xin) {
@@ -520,7 +552,7 @@ static size_t cnn_bytes(int B, int H, int W, size_t* offs) {
   for (int i = 0; i < 3; ++i) offs[13 + i] = take(P * 4);               // xin out gout
   offs[16] = take((size_t)B * 4);                                        // sig
   offs[17] = take((size_t)kWgradBlocks * kW1 * 4);                       // wpart
-  offs[18] = take(4096 * 8);                                             // dpart
+  offs[18] = take(std::max<size_t>(4096, (size_t)B * kNormBlocks) * 8);  // dpart (loss / norm partials)
   offs[19] = take(256);                                                  // err
   return (off + 255) / 256 * 256;
 }
@@ -615,7 +647,9 @@ static int pack(CnnNet& n) {
 static int normalise(CnnNet& n, const float* x, int B) {
   const int HW = n.H * n.W;
   const size_t P = (size_t)B * HW;
-  k_norm_stats<<<B, 256, 0, n.stream>>>(x, HW, n.sig);
+  k_norm_partial<<<dim3(kNormBlocks, B), 256, 0, n.stream>>>(x, HW, n.dpart);
+  TMBIR_CHECK_LAUNCH();
+  k_norm_stats<<<B, 32, 0, n.stream>>>(n.dpart, HW, n.sig);
   TMBIR_CHECK_LAUNCH();
   k_scale_in<<<(int)std::min<size_t>((P + 255) / 256, 152 * 16), 256, 0, n.stream>>>(x, HW, P, n.sig, n.xin);
   TMBIR_CHECK_LAUNCH();

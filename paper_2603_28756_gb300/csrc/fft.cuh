@@ -85,6 +85,11 @@ __device__ __forceinline__ double fmar(double a, double b, double c) { return fm
 
 template <class C> __device__ __forceinline__ C cadd(C a, C b) { return mkc(a.x + b.x, a.y + b.y); }
 template <class C> __device__ __forceinline__ C csub(C a, C b) { return mkc(a.x - b.x, a.y - b.y); }
+// FP32: one packed instruction for both parts (sm_100 and later), rounded like the scalar form
+template <> __device__ __forceinline__ float2 cadd<float2>(float2 a, float2 b) { return __fadd2_rn(a, b); }
+template <> __device__ __forceinline__ float2 csub<float2>(float2 a, float2 b) {
+  return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
+}
 template <class C> __device__ __forceinline__ C cmul(C a, C b) {
   return mkc(fmar(a.x, b.x, -a.y * b.y), fmar(a.x, b.y, a.y * b.x));
 }
