@@ -33,10 +33,11 @@ constexpr int kParams = kOffB3 + kB3;  // 19105
 constexpr int kTM = 128;               // pixels of one tensor-core tile (MMA M): a run of one image row
 constexpr int kTX = kTM + 2;           // staged pixels of a row: x0 - 1 .. x0 + kTM
 constexpr int kChunkB = kTX * 16;      // bytes of one staged (row, 8-channel chunk) array
-constexpr int kStageA = 3 * 4 * kChunkB;          // three rows x four chunks
+constexpr int kRows = 4;                          // output rows of one tile (independent accumulators)
+constexpr int kStageA = (kRows + 2) * 4 * kChunkB;  // staged rows x four chunks
 constexpr int kStageAPad = (kStageA + 127) / 128 * 128;
 constexpr int kWElems = 9 * 4 * kC * 8;           // packed 32 -> 32 weights [tap][chunk][n][8]
-constexpr int kConvSmem = kStageAPad + kWElems * 2;
+constexpr int kConvSmem = kStageAPad + kWElems * 2;  // staged rows + weights
 constexpr uint32_t kMmaPolls = 1u << 22;          // bound of every wait on an MMA completion
 constexpr int kWgradBlocks = 304;      // blocks of the weight-gradient reductions
 
@@ -84,12 +85,14 @@ __global__ void k_cnn_pack(const float* __restrict__ master, __nv_bfloat16* wg1,
 
 // ---------------------------------------------------------------- tensor-core 32 -> 32 convolution
 // out[p][n] = sum_{tap, c} w[tap][n][c] in[p + tap][c] (+ bias, ReLU), as an implicit GEMM on the
-// 5th-generation tensor cores: a tile is 128 consecutive pixels of one image row (MMA M = 128),
-// N = 32 output channels, and each of the nine taps is one K = 32 step (two K = 16 MMAs).
-// The three input rows y-1..y+1 (pixels x0-1..x0+128, zero outside the image) are staged once
-// per tile as 8-channel chunks, [row][chunk][pixel][8], which is the no-swizzle K-major operand
-// layout; tap (dy, dx) is the same arrays started dx pixels (16 bytes) later.  The accumulator
-// lives in 32 TMEM columns; each warp moves its 32 pixels out with tcgen05.ld.
+// 5th-generation tensor cores.  A tile is kRows image rows x 128 pixels; each of its rows is an
+// MMA with M = 128 pixels and N = 32 output channels, and each of the nine taps is one K = 32
+// step (two K = 16 MMAs).  The kRows accumulators (32 TMEM columns each) are independent, and
+// the MMAs are issued tap-major across them so consecutive MMAs do not wait on one another.
+// The input rows y0-1 .. y0+kRows (pixels x0-1..x0+128, zero outside the image) are staged
+// once per tile as 8-channel chunks, [row][chunk][pixel][8], which is the no-swizzle K-major
+// operand layout; tap (dy, dx) of output row r is staged row r + dy started dx pixels (16
+// bytes) later.  Each warp moves its 32 pixels of every row out with tcgen05.ld.
 // MASK (data gradient): the result is multiplied by (mask[p][n] > 0).
 template <bool BIAS_RELU, bool MASK>
 __global__ void __launch_bounds__(128) k_conv32(const __nv_bfloat16* __restrict__ in, int B, int H, int W,
@@ -106,7 +109,7 @@ __global__ void __launch_bounds__(128) k_conv32(const __nv_bfloat16* __restrict_
   constexpr uint32_t IDESC = tc::idesc_bf16_f32<kTM, kC>();
   const unsigned char* wsrc = reinterpret_cast<const unsigned char*>(wpk);
   for (int i = threadIdx.x; i < kWElems * 2 / 16; i += blockDim.x) tc::cp_async16(sw + 16 * i, wsrc + 16 * i, true);
-  if (warp == 0) tc::tmem_alloc<32>(&tmem_base);
+  if (warp == 0) tc::tmem_alloc<kRows * kC>(&tmem_base);
   if (threadIdx.x == 0) {
     tc::mbar_init(&bar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -116,34 +119,49 @@ __global__ void __launch_bounds__(128) k_conv32(const __nv_bfloat16* __restrict_
   tc::fence_after_sync();
   const uint32_t tmem = tmem_base;
   const uint32_t a_base = tc::smem_addr(sa), w_base = tc::smem_addr(sw);
-  const int tiles_x = (W + kTM - 1) / kTM;
-  const int ntiles = B * H * tiles_x;
+  const uint64_t a_desc = tc::smem_desc(a_base, kChunkB, 128), w_desc = tc::smem_desc(w_base, kC * 16, 128);
+  float bias_r[kC];
+#pragma unroll
+  for (int c = 0; c < kC; ++c) bias_r[c] = BIAS_RELU ? __ldg(bias + c) : 0.f;
+  const int tiles_x = (W + kTM - 1) / kTM, tiles_y = (H + kRows - 1) / kRows;
+  const int ntiles = B * tiles_y * tiles_x;
   uint32_t parity = 0;
   bool failed = false;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int tx = tile % tiles_x, row = tile / tiles_x;
-    const int y = row % H, b = row / H;
-    const int x0 = tx * kTM;
-    for (int e = threadIdx.x; e < 3 * 4 * kTX; e += blockDim.x) {
-      const int px = e % kTX, j = (e / kTX) % 4, dy = e / (4 * kTX);
-      const int gy = y + dy - 1, gx = x0 - 1 + px;
-      const bool v = gy >= 0 && gy < H && gx >= 0 && gx < W;
-      const __nv_bfloat16* src = v ? in + (((size_t)b * H + gy) * W + gx) * kC + 8 * j : in;
-      tc::cp_async16(sa + (dy * 4 + j) * kChunkB + px * 16, src, v);
+    const int tx = tile % tiles_x, ty = (tile / tiles_x) % tiles_y, b = tile / (tiles_x * tiles_y);
+    const int y0 = ty * kRows, x0 = tx * kTM;
+    // thread t copies staged pixel t (threads 0, 1 also pixels 128, 129) of every staged row
+    for (int px = threadIdx.x; px < kTX; px += blockDim.x) {
+      const int gx = x0 - 1 + px;
+      const bool vx = gx >= 0 && gx < W;
+#pragma unroll
+      for (int sr = 0; sr < kRows + 2; ++sr) {
+        const int gy = y0 + sr - 1;
+        const bool v = vx && gy >= 0 && gy < H;
+        const __nv_bfloat16* src = v ? in + (((size_t)b * H + gy) * W + gx) * kC : in;
+        unsigned char* dst = sa + sr * 4 * kChunkB + px * 16;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) tc::cp_async16(dst + j * kChunkB, v ? src + 8 * j : in, v);
+      }
     }
-    tc::cp_async_wait_all();
+    tc::cp_async_wait_all();  // this tile's rows (and, the first time, the weights)
     tc::fence_async_shared();
     __syncthreads();
     if (threadIdx.x == 0) {
       tc::fence_after_sync();
+      // every operand start is a fixed byte offset from the staging / weight bases, added to the
+      // descriptors' start-address field (bytes >> 4; the offsets stay inside the 14-bit field)
 #pragma unroll
       for (int tap = 0; tap < 9; ++tap) {
         const int dy = tap / 3, dx = tap % 3;
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
-          const uint64_t ad = tc::smem_desc(a_base + (dy * 4 + 2 * s) * kChunkB + dx * 16, kChunkB, 128);
-          const uint64_t bd = tc::smem_desc(w_base + (tap * 4 + 2 * s) * (kC * 16), kC * 16, 128);
-          tc::mma_bf16(tmem, ad, bd, IDESC, (tap | s) ? 1u : 0u);
+          const uint64_t bd = w_desc + (uint64_t)(((tap * 4 + 2 * s) * (kC * 16)) >> 4);
+#pragma unroll
+          for (int r = 0; r < kRows; ++r) {
+            const uint64_t ad = a_desc + (uint64_t)((((r + dy) * 4 + 2 * s) * kChunkB + dx * 16) >> 4);
+            tc::mma_bf16(tmem + r * kC, ad, bd, IDESC, (tap | s) ? 1u : 0u);
+          }
         }
       }
       tc::mma_commit(&bar);
@@ -155,14 +173,17 @@ __global__ void __launch_bounds__(128) k_conv32(const __nv_bfloat16* __restrict_
       break;
     }
     tc::fence_after_sync();
-    float v[32];
-    tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16), v);
     const int gx = x0 + warp * 32 + lane;
-    if (gx < W) {
-      const size_t pbase = (((size_t)b * H + y) * W + gx) * kC;
+#pragma unroll 1
+    for (int r = 0; r < kRows; ++r) {
+      float v[32];
+      tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + r * kC, v);
+      const int gy = y0 + r;
+      if (gx >= W || gy >= H) continue;
+      const size_t pbase = (((size_t)b * H + gy) * W + gx) * kC;
       if constexpr (BIAS_RELU) {
 #pragma unroll
-        for (int c = 0; c < kC; ++c) v[c] = fmaxf(v[c] + __ldg(bias + c), 0.f);
+        for (int c = 0; c < kC; ++c) v[c] = fmaxf(v[c] + bias_r[c], 0.f);
       }
       if constexpr (MASK) {
         const uint4* mk = reinterpret_cast<const uint4*>(mask + pbase);
@@ -199,36 +220,56 @@ __global__ void __launch_bounds__(128) k_conv32(const __nv_bfloat16* __restrict_
   }
   tc::fence_before_sync();
   __syncthreads();
-  if (warp == 0) tc::tmem_dealloc<32>(tmem);
+  if (warp == 0) tc::tmem_dealloc<kRows * kC>(tmem);
 }
 
 // ---------------------------------------------------------------- first and last layers (CUDA cores)
-// a0[p][co] = relu(b0[co] + sum_tap w0[co][tap] x[p + tap])
-__global__ void k_conv_first(const float* __restrict__ x, int B, int H, int W, const float* __restrict__ master,
-                             __nv_bfloat16* __restrict__ a0) {
-  __shared__ float w[kW0 + kB0];
-  for (int i = threadIdx.x; i < kW0 + kB0; i += blockDim.x) w[i] = master[kOff0 + i];
-  __syncthreads();
-  const size_t total = (size_t)B * H * W;
-  for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < total; p += (size_t)gridDim.x * blockDim.x) {
-    const int xx = (int)(p % W), yy = (int)((p / W) % H);
-    const size_t b = p / ((size_t)H * W);
-    float nb[9];
+// a0[p][co] = relu(b0[co] + sum_tap w0[co][tap] x[p + tap]).  A block stages an 8 x 32 tile of
+// x with a one-pixel halo; thread t owns output channels 4 (t % 8) .. +3 (weights in
+// registers) for the pixels t / 8 + 32 k, so the eight threads of a pixel write its 64 bytes.
+constexpr int kFH = 8, kFW = 32;
+__global__ void __launch_bounds__(256) k_conv_first(const float* __restrict__ x, int B, int H, int W,
+                                                    const float* __restrict__ master, __nv_bfloat16* __restrict__ a0) {
+  __shared__ float xt[kFH + 2][kFW + 2];
+  const int cg = threadIdx.x & 7, ps = threadIdx.x >> 3;
+  float wr[4][9], br[4];
 #pragma unroll
-    for (int t = 0; t < 9; ++t) {
-      const int gy = yy + t / 3 - 1, gx = xx + t % 3 - 1;
-      nb[t] = (gy >= 0 && gy < H && gx >= 0 && gx < W) ? x[(b * H + gy) * W + gx] : 0.f;
+  for (int c = 0; c < 4; ++c) {
+#pragma unroll
+    for (int t = 0; t < 9; ++t) wr[c][t] = master[kOff0 + (4 * cg + c) * 9 + t];
+    br[c] = master[kOff0 + kW0 + 4 * cg + c];
+  }
+  const int tiles_x = (W + kFW - 1) / kFW, tiles_y = (H + kFH - 1) / kFH;
+  const int tpi = tiles_x * tiles_y;
+  for (int tile = blockIdx.x; tile < B * tpi; tile += gridDim.x) {
+    const int b = tile / tpi, ty = (tile % tpi) / tiles_x, tx = tile % tiles_x;
+    const int y0 = ty * kFH, x0 = tx * kFW;
+    __syncthreads();
+    for (int q = threadIdx.x; q < (kFH + 2) * (kFW + 2); q += blockDim.x) {
+      const int gy = y0 - 1 + q / (kFW + 2), gx = x0 - 1 + q % (kFW + 2);
+      xt[q / (kFW + 2)][q % (kFW + 2)] =
+          (gy >= 0 && gy < H && gx >= 0 && gx < W) ? x[((size_t)b * H + gy) * W + gx] : 0.f;
     }
-    __nv_bfloat162* o = reinterpret_cast<__nv_bfloat162*>(a0 + p * kC);
-#pragma unroll 4
-    for (int co = 0; co < kC; co += 2) {
-      float s0 = w[kW0 + co], s1 = w[kW0 + co + 1];
+    __syncthreads();
+#pragma unroll 2
+    for (int ly = 0; ly < kFH; ++ly) {
+      const int gy = y0 + ly, gx = x0 + ps;
+      if (gy >= H || gx >= W) continue;
+      float nb[9];
 #pragma unroll
-      for (int t = 0; t < 9; ++t) {
-        s0 = fmaf(w[co * 9 + t], nb[t], s0);
-        s1 = fmaf(w[(co + 1) * 9 + t], nb[t], s1);
+      for (int t = 0; t < 9; ++t) nb[t] = xt[ly + t / 3][ps + t % 3];
+      float v[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        float acc = br[c];
+#pragma unroll
+        for (int t = 0; t < 9; ++t) acc = fmaf(wr[c][t], nb[t], acc);
+        v[c] = fmaxf(acc, 0.f);
       }
-      o[co / 2] = __floats2bfloat162_rn(fmaxf(s0, 0.f), fmaxf(s1, 0.f));
+      uint2 o;
+      reinterpret_cast<__nv_bfloat162*>(&o)[0] = __floats2bfloat162_rn(v[0], v[1]);
+      reinterpret_cast<__nv_bfloat162*>(&o)[1] = __floats2bfloat162_rn(v[2], v[3]);
+      *reinterpret_cast<uint2*>(a0 + (((size_t)b * H + gy) * W + gx) * kC + 4 * cg) = o;
     }
   }
 }
@@ -238,9 +279,9 @@ __global__ void k_conv_first(const float* __restrict__ x, int B, int H, int W, c
 // tile plus a one-pixel halo (each activation vector read once) and sums the nine shifted
 // entries from shared memory.
 constexpr int kLH = 8, kLW = 32;
-__global__ void __launch_bounds__(256) k_conv_last(const __nv_bfloat16* __restrict__ a2, int B, int H, int W,
-                                                   const float* __restrict__ master, float* __restrict__ out) {
-  __shared__ float w[kC][12];  // w3[ci][tap], rows padded to 12 for aligned vector reads
+__global__ void __launch_bounds__(256, 2) k_conv_last(const __nv_bfloat16* __restrict__ a2, int B, int H, int W,
+                                                      const float* __restrict__ master, float* __restrict__ out) {
+  __shared__ __align__(16) float w[kC][12];  // w3[ci][tap], rows padded to 12 for 16-byte vector reads
   __shared__ float T[(kLH + 2) * (kLW + 2)][9];
   for (int i = threadIdx.x; i < kC * 9; i += blockDim.x) w[i / 9][i % 9] = master[kOff3 + i];
   const float b3 = master[kOff3 + kW3];
@@ -257,16 +298,25 @@ __global__ void __launch_bounds__(256) k_conv_last(const __nv_bfloat16* __restri
       for (int k = 0; k < 9; ++k) t[k] = 0.f;
       if (gy >= 0 && gy < H && gx >= 0 && gx < W) {
         const uint4* src = reinterpret_cast<const uint4*>(a2 + (((size_t)b * H + gy) * W + gx) * kC);
-#pragma unroll
+#pragma unroll 1
         for (int v4 = 0; v4 < 4; ++v4) {
           const uint4 u = src[v4];
           const __nv_bfloat162* h2 = reinterpret_cast<const __nv_bfloat162*>(&u);
 #pragma unroll
-          for (int h = 0; h < 4; ++h) {
-            const float2 a = __bfloat1622float2(h2[h]);
-            const int ci = 8 * v4 + 2 * h;
-#pragma unroll
-            for (int k = 0; k < 9; ++k) t[k] = fmaf(w[ci + 1][k], a.y, fmaf(w[ci][k], a.x, t[k]));
+          for (int h = 0; h < 8; ++h) {
+            const float a = h & 1 ? __high2float(h2[h / 2]) : __low2float(h2[h / 2]);
+            const float* wr = w[8 * v4 + h];
+            const float4 w0 = *reinterpret_cast<const float4*>(wr);
+            const float4 w1 = *reinterpret_cast<const float4*>(wr + 4);
+            t[0] = fmaf(w0.x, a, t[0]);
+            t[1] = fmaf(w0.y, a, t[1]);
+            t[2] = fmaf(w0.z, a, t[2]);
+            t[3] = fmaf(w0.w, a, t[3]);
+            t[4] = fmaf(w1.x, a, t[4]);
+            t[5] = fmaf(w1.y, a, t[5]);
+            t[6] = fmaf(w1.z, a, t[6]);
+            t[7] = fmaf(w1.w, a, t[7]);
+            t[8] = fmaf(wr[8], a, t[8]);
           }
         }
       }
@@ -559,8 +609,14 @@ static size_t cnn_bytes(int B, int H, int W, size_t* offs) {
 
 static int conv32(CnnNet& n, const __nv_bfloat16* in, int B, const __nv_bfloat16* w, const float* bias,
                   const __nv_bfloat16* mask, __nv_bfloat16* out, bool relu) {
-  const int tiles = B * n.H * ((n.W + kTM - 1) / kTM);
-  const int blocks = std::min(tiles, 152 * 4);
+  static bool attr = false;
+  if (!attr) {
+    TMBIR_CUDA(cudaFuncSetAttribute(k_conv32<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kConvSmem));
+    TMBIR_CUDA(cudaFuncSetAttribute(k_conv32<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kConvSmem));
+    attr = true;
+  }
+  const int tiles = B * ((n.H + kRows - 1) / kRows) * ((n.W + kTM - 1) / kTM);
+  const int blocks = std::min(tiles, 152 * 3);
   if (relu)
     k_conv32<true, false><<<blocks, 128, kConvSmem, n.stream>>>(in, B, n.H, n.W, w, bias, nullptr, out, n.err);
   else
