@@ -351,14 +351,15 @@ __global__ void k_transpose_prune(const C* __restrict__ in, C* __restrict__ out,
   }
 }
 // out[b][r][c] = scale * Re tmp[b][c][(r - N/2) mod nf] / (psi[c] psi[r])
+// slice 2p from the real part, slice 2p + 1 (when there is one) from the imaginary part of pair p
 template <class C>
 __global__ void k_deconv_pruned(const C* __restrict__ B, int nf, int N, int nb, const double* __restrict__ psi,
                                 float scale, float* __restrict__ out) {
   const size_t total = (size_t)nb * N * N;
   for (size_t id = blockIdx.x * (size_t)blockDim.x + threadIdx.x; id < total; id += (size_t)gridDim.x * blockDim.x) {
     const int c = (int)(id % N), r = (int)((id / N) % N), b = (int)(id / ((size_t)N * N));
-    const C v = B[(size_t)b * N * nf + (size_t)c * nf + (r - N / 2 + nf) % nf];
-    out[id] = (float)(scale * ((double)v.x / (psi[c] * psi[r])));
+    const C v = B[(size_t)(b / 2) * N * nf + (size_t)c * nf + (r - N / 2 + nf) % nf];
+    out[id] = (float)(scale * ((double)((b & 1) ? v.y : v.x) / (psi[c] * psi[r])));
   }
 }
 
@@ -426,19 +427,23 @@ __global__ void k_prepare_rows(const float* __restrict__ sino, int nd, size_t ro
 }
 
 // G(a,k) = (-1)^k * sum_m g(a,m) exp(+2 pi i k m / nd) / nd: sign flip from s_m = m - nd/2, and the 1/nd of R*.
-// Written sample-major, out[(a nd + k) B + b], so the gather reads the B slices of a sample
+// Two slices share one transform: G_pair = G_{2p} + i G_{2p+1}.  Each slice's strengths are
+// Hermitian in k (real sinogram, samples symmetric in k), so its gridded transform is real and
+// the pair's result carries slice 2p in the real and slice 2p+1 in the imaginary part.
+// Written sample-major, out[(a nd + k) PB + p], so the gather reads the PB pairs of a sample
 // from one contiguous run.
-template <int B, class C>
-__global__ void k_strength_fix(const C* __restrict__ rows, int nd, size_t nrows, int nb, C* __restrict__ out) {
+template <int PB, class C>
+__global__ void k_strength_pack(const C* __restrict__ rows, int nd, size_t nrows, int nb, C* __restrict__ out) {
   using S = real_t<C>;
-  const size_t total = nrows * B;
+  const size_t total = nrows * PB;
   for (size_t id = blockIdx.x * (size_t)blockDim.x + threadIdx.x; id < total; id += (size_t)gridDim.x * blockDim.x) {
-    const int b = (int)(id % B);
-    const size_t r = id / B;
+    const int pr = (int)(id % PB);
+    const size_t r = id / PB;
     const int k = (int)(r % nd);
     const S sg = (k & 1) ? (S)(-1.0 / nd) : (S)(1.0 / nd);
-    const C v = b < nb ? rows[(size_t)b * nrows + r] : mkc((S)0, (S)0);
-    out[id] = mkc(v.x * sg, v.y * sg);
+    const C a = 2 * pr < nb ? rows[(size_t)(2 * pr) * nrows + r] : mkc((S)0, (S)0);
+    const C b = 2 * pr + 1 < nb ? rows[(size_t)(2 * pr + 1) * nrows + r] : mkc((S)0, (S)0);
+    out[id] = mkc((a.x - b.y) * sg, (a.y + b.x) * sg);
   }
 }
 
@@ -653,21 +658,23 @@ static int backproject_t(Ctx& c, int gi, const float* d_sino, float* d_out, bool
     k_twiddle<C><<<(nd + 255) / 256, 256, 0, s>>>(tw, nd);
     TMBIR_CHECK_LAUNCH();
     if (int e = fft_rows(strengths, nd, nb * na, +1, tw, s)) return e;
-    k_strength_fix<kBackprojBatch, C><<<1024, 256, 0, s>>>(strengths, nd, rows, nb, strengths_t);
+    constexpr int PB = kBackprojBatch / 2;  // slice pairs per batch
+    const int np = (nb + 1) / 2;
+    k_strength_pack<PB, C><<<1024, 256, 0, s>>>(strengths, nd, rows, nb, strengths_t);
     TMBIR_CHECK_LAUNCH();
-    k_csr_gather<kBackprojBatch, C><<<(ncells + 255) / 256, 256, 0, s>>>(g.csr_ptr, g.csr_idx, g.csr_w, ncells,
-                                                                          strengths_t, grid, nb);
+    k_csr_gather<PB, C><<<(ncells + 255) / 256, 256, 0, s>>>(g.csr_ptr, g.csr_idx, g.csr_w, ncells, strengths_t,
+                                                              grid, np);
     TMBIR_CHECK_LAUNCH();
     k_twiddle<C><<<(nf + 255) / 256, 256, 0, s>>>(tw, nf);
     TMBIR_CHECK_LAUNCH();
-    // 2D transform with the output pruned to the N x N image modes
-    if (int e = fft_rows(grid, nf, nb * nf, -1, tw, s)) return e;
+    // 2D transform of the pair grids with the output pruned to the N x N image modes
+    if (int e = fft_rows(grid, nf, np * nf, -1, tw, s)) return e;
     {
-      dim3 gr((N + 31) / 32, (nf + 31) / 32, nb), bl(32, 8);
+      dim3 gr((N + 31) / 32, (nf + 31) / 32, np), bl(32, 8);
       k_transpose_prune<C><<<gr, bl, 0, s>>>(grid, tmp, nf, N);
       TMBIR_CHECK_LAUNCH();
     }
-    if (int e = fft_rows(tmp, nf, nb * N, -1, tw, s)) return e;
+    if (int e = fft_rows(tmp, nf, np * N, -1, tw, s)) return e;
     k_deconv_pruned<C><<<1024, 256, 0, s>>>(tmp, nf, N, nb, g.psiA, scale, d_out + g.img_off + (size_t)b0 * N * N);
     TMBIR_CHECK_LAUNCH();
   }

@@ -2,7 +2,8 @@
 
 * The workload bench.py times: 64 slices of 1024^2, 256 angles over [0, pi), 20 ellipsoids.
 * The finest level of the hierarchical geometry: 2048^2 slices seen under 128 angles over
-  [0, 2 pi/3) (missing wedge).
+  [0, 2 pi/3) (missing wedge), two slices compared in full and the full 512-slice volume on
+  sampled outputs.
 
 The oracle evaluates sampled outputs one by one (R*g, K (*) x, the prior gradient and the FBP
 start at a pixel); the kernel K and, at 2048^2 with two slices, whole results are compared in
@@ -132,3 +133,53 @@ def test_n2048_limited_angle(orc):
     ctx.reconstruct(xs, d_b, tm.Params(**PRIOR, L=L, max_iter=3))
     ref = orc.nesterov(np.zeros(x.shape), b, 0.0, Kref, pr, L, 3, Chat=Chat)
     assert rel(host(xs, x.shape), ref) < 1e-4
+
+
+def seeded_slices(seed, S, N, scale):
+    """Slice z of a seeded uniform volume, generated slice by slice (the full volume is only
+    ever held on the device)."""
+    return lambda z: np.random.default_rng(seed * 100003 + z).uniform(0.0, scale, (N, N)).astype(np.float32)
+
+
+def test_hierarchical_finest_level_full_size(orc):
+    # 512 slices of 2048^2, 128 angles over [0, 2 pi/3): R*g, K (*) x, the gradient and one
+    # fast-gradient step at sampled voxels
+    S, N, na, span = 512, 2048, 128, 2 * math.pi / 3
+    p = synth.volume(S=S, N=N, n_angles=na, n_ellipsoids=20, span=span, seed=1003)
+    ctx = tm.Context([tm.Group(N=N, angles=list(p.theta), n_slices=S, span=span)])
+    d_atg = ctx.build_operator(dev(p.sino))
+    g = p.sino
+    rng = np.random.default_rng(11)
+    pts = samples(rng, S, N, 10)
+    amax = float(torch.max(torch.abs(d_atg)).item())
+    atg = d_atg.view(S, N, N)
+    for z, r, c in pts:
+        ref = orc.adjoint_point(g[z].astype(np.float64), N, p.theta, r, c)
+        assert abs(float(atg[z, r, c].item()) - ref) <= 1e-6 * amax
+    del atg
+    gen_x, gen_b = seeded_slices(21, S, N, 0.5), seeded_slices(22, S, N, 4.0e4)
+    x = torch.empty(S * N * N, dtype=torch.float32, device="cuda")
+    b = torch.empty_like(x)
+    for z in range(S):
+        x[z * N * N:(z + 1) * N * N] = torch.from_numpy(gen_x(z).ravel()).cuda()
+        b[z * N * N:(z + 1) * N * N] = torch.from_numpy(gen_b(z).ravel()).cuda()
+    zk = ctx.normal_apply(x).view(S, N, N)
+    G = ctx.gradient(x, b, tm.Params(**PRIOR)).view(S, N, N)
+    L = 1.0e5
+    x1 = x.clone()
+    ctx.reconstruct(x1, b, tm.Params(**PRIOR, L=L, max_iter=1))
+    x1 = x1.view(S, N, N)
+    torch.cuda.synchronize()
+    zscale = float(torch.sqrt(torch.mean(zk.double() ** 2)).item())
+    gscale = float(torch.sqrt(torch.mean(G.double() ** 2)).item())
+    Kref = orc.kernel(N, p.theta, N)
+    pr = orc.Prior(**PRIOR)
+    for zz, r, c in pts:
+        # the slice and its neighbours, regenerated on the host
+        lo, hi = max(zz - 1, 0), min(zz + 2, S)
+        xs = np.stack([gen_x(k) for k in range(lo, hi)]).astype(np.float64)
+        zr = orc.normal_point(xs[zz - lo], Kref, r, c)
+        assert abs(float(zk[zz, r, c].item()) - zr) <= 1e-5 * zscale
+        gr = zr - float(gen_b(zz)[r, c]) + orc.prior_point(xs, pr, zz - lo, r, c)
+        assert abs(float(G[zz, r, c].item()) - gr) <= 1e-5 * gscale
+        assert abs(float(x1[zz, r, c].item()) - (xs[zz - lo, r, c] - gr / L)) <= 1e-5 * gscale / L + 1e-7
