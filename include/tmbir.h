@@ -53,7 +53,7 @@ typedef struct tmbir_ctx tmbir_ctx;
  * One geometry group: n_slices slices of N x N pixels seen under the same n_angles
  * parallel-beam angles by n_det detector bins (Sec. 2, Eq. 1).  Slices of a group are
  * coupled by the 3D prior; different groups are independent.
- *   N        image side; 64 <= N <= 2048 and a power of two.
+ *   N        image side: a power of two in [64, 2048], or 1536 or 2560 (mixed-radix FFTs).
  *   n_det    detector bins; must equal N (pixel pitch = bin pitch).
  *   angles   host array of n_angles radians; copied by tmbir_set_geometry.
  *   span     angular range covered by the angles (pi for a full half turn); the FBP

@@ -174,7 +174,7 @@ int tmbir_set_geometry(tmbir_ctx* ctx, int n_groups, const tmbir_group* groups) 
   std::vector<std::vector<double>> angs(n_groups);
   for (int i = 0; i < n_groups; ++i) {
     const tmbir_group& g = gs[i];
-    REQUIRE(supported_N(g.N), TMBIR_ERR_SHAPE, "set_geometry: N must be a power of two in [64, 2048]");
+    REQUIRE(supported_N(g.N), TMBIR_ERR_SHAPE, "set_geometry: N must be a power of two in [64, 2048], or 1536 or 2560");
     REQUIRE(g.n_det == g.N, TMBIR_ERR_SHAPE, "set_geometry: n_det must equal N");
     REQUIRE(g.n_angles >= 1 && g.n_angles <= 1 << 16, TMBIR_ERR_ARG, "set_geometry: n_angles out of range");
     REQUIRE(g.angles != nullptr, TMBIR_ERR_ARG, "set_geometry: angles is NULL");
@@ -338,13 +338,14 @@ int tmbir_set_workspace(tmbir_ctx* ctx, void* d_ws, size_t bytes) {
     d.csr_w = reinterpret_cast<double*>(ws + c.off_csr_w[i]);
     d.lam_max = reinterpret_cast<double*>(ws + c.off_lam[i]);
     d.gtg = reinterpret_cast<double*>(ws + c.off_gtg[i]);
-    // twiddle tables: twN[k][t] = exp(-2 pi i t k / N) in the group-FFT layout, twM[n] = exp(-2 pi i n / 2N)
+    // twiddle tables: twN[k][t] = exp(-2 pi i t k / N) in the group-FFT layout (the plain
+    // table exp(-2 pi i j / N) for the block-FFT sides), twM[n] = exp(-2 pi i n / 2N)
     int T, P;
     fft_shape(g.N, &T, &P);
     std::vector<float2> twN((size_t)T * P), twM(g.N);
     for (int k = 0; k < P; ++k)
       for (int t = 0; t < T; ++t) {
-        const long long q = (long long)t * k % g.N;
+        const long long q = block_fft_N(g.N) ? (long long)k * T + t : (long long)t * k % g.N;
         const double a = -2.0 * M_PI * (double)q / g.N;
         twN[(size_t)k * T + t] = make_float2((float)std::cos(a), (float)std::sin(a));
       }

@@ -266,7 +266,7 @@ struct GroupFFT {
   }
 };
 
-// group shape for a transform of length n (a power of two from 64 to 2048)
+// group shape for a transform of length n (a power of two from 64 to 2048, or 1536, 2560)
 template <int n>
 struct FFTShape;
 template <> struct FFTShape<64> { using type = GroupFFT<8, 8>; };
@@ -275,5 +275,13 @@ template <> struct FFTShape<256> { using type = GroupFFT<16, 16>; };
 template <> struct FFTShape<512> { using type = GroupFFT<16, 32>; };
 template <> struct FFTShape<1024> { using type = GroupFFT<32, 32>; };
 template <> struct FFTShape<2048> { using type = GroupFFT<32, 64>; };
+// Sides with a factor 3 or 5 use the block FFT (block_fft.cuh); the shape only fixes the rows
+// per block of the row passes and of the stencil (32 threads per row).
+template <int T_, int P_>
+struct RowShape {
+  static constexpr int T = T_, P = P_, SMEM = T * (P + 1);
+};
+template <> struct FFTShape<1536> { using type = RowShape<32, 48>; };
+template <> struct FFTShape<2560> { using type = RowShape<32, 80>; };
 
 }  // namespace tmbir

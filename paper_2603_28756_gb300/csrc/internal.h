@@ -200,6 +200,7 @@ int launch_finalize(IterState* st, const double* partials, int nblocks, double* 
                     cudaGraphConditionalHandle cond = 0, int use_cond = 0, int trip_launches = 0);
 int launch_sum_partials(const double* partials, int nblocks, double* out, cudaStream_t s);
 bool supported_N(int N);
+bool block_fft_N(int N);  // sides with a factor 3 or 5 (block-FFT passes, plain twiddle table)
 void fft_shape(int N, int* T, int* P);
 
 // setup.cu ------------------------------------------------------------------

@@ -20,20 +20,20 @@
 namespace tmbir {
 
 // ---------------------------------------------------------------- batched 1D FFT along rows
-// Stockham autosort in shared memory: one block per row, radix 8/4/2 stages, natural order
+// Stockham autosort in shared memory: one block per row, radix 8/4/2/3/5 stages, natural order
 // in and out.  tw[j] = exp(-2 pi i j / n).
 template <int R, int DIR, class C>
 __device__ __forceinline__ void stockham_stage(const C* X, C* Y, int n, int Ls, const C* __restrict__ tw) {
   const int nb = n / R;
   const int tstep = n / (Ls * R);
   for (int j = threadIdx.x; j < nb; j += blockDim.x) {
-    const int k = j & (Ls - 1);
+    const int k = j % Ls;  // Ls is a product of mixed radices
     C a[R];
 #pragma unroll
     for (int m = 0; m < R; ++m) {
       C v = X[j + m * nb];
       if (m > 0 && k > 0) {
-        const C w = tw[(size_t)k * m * tstep & (n - 1)];
+        const C w = tw[(size_t)k * m * tstep];  // k m tstep < n
         v = DIR < 0 ? cmul(v, w) : cmulc(v, w);
       }
       a[m] = v;
@@ -45,29 +45,26 @@ __device__ __forceinline__ void stockham_stage(const C* X, C* Y, int n, int Ls, 
   }
 }
 
+// plan: the radices, one per 4-bit digit from the lowest (built by fft_plan)
 template <int DIR, class C>
-__global__ void __launch_bounds__(256) k_fft_rows(C* data, int n, int log2n, size_t stride, const C* __restrict__ tw) {
+__global__ void __launch_bounds__(256) k_fft_rows(C* data, int n, unsigned plan, size_t stride, const C* __restrict__ tw) {
   extern __shared__ unsigned char smraw[];
   C* X = reinterpret_cast<C*>(smraw);
   C* Y = X + n;
   C* row = data + (size_t)blockIdx.x * stride;
   for (int j = threadIdx.x; j < n; j += blockDim.x) X[j] = row[j];
   __syncthreads();
-  int Ls = 1, rem = log2n;
-  while (rem > 0) {
-    if (rem >= 3) {
-      stockham_stage<8, DIR>(X, Y, n, Ls, tw);
-      Ls *= 8;
-      rem -= 3;
-    } else if (rem == 2) {
-      stockham_stage<4, DIR>(X, Y, n, Ls, tw);
-      Ls *= 4;
-      rem -= 2;
-    } else {
-      stockham_stage<2, DIR>(X, Y, n, Ls, tw);
-      Ls *= 2;
-      rem -= 1;
+  int Ls = 1;
+  for (; plan != 0; plan >>= 4) {
+    const int R = (int)(plan & 15u);
+    switch (R) {
+      case 8: stockham_stage<8, DIR>(X, Y, n, Ls, tw); break;
+      case 4: stockham_stage<4, DIR>(X, Y, n, Ls, tw); break;
+      case 2: stockham_stage<2, DIR>(X, Y, n, Ls, tw); break;
+      case 3: stockham_stage<3, DIR>(X, Y, n, Ls, tw); break;
+      default: stockham_stage<5, DIR>(X, Y, n, Ls, tw); break;
     }
+    Ls *= R;
     __syncthreads();
     C* tmp = X;
     X = Y;
@@ -123,6 +120,22 @@ static int ilog2(int n) {
   while ((1 << l) < n) ++l;
   return l;
 }
+// radices of n = 2^a 3^b 5^c as 4-bit digits (fives and threes first, then eights, fours,
+// twos); 0 when n has another factor or needs more than eight stages
+static unsigned fft_plan(int n) {
+  unsigned plan = 0;
+  int shift = 0;
+  auto push = [&](int r) {
+    plan |= (unsigned)r << shift;
+    shift += 4;
+  };
+  while (n % 5 == 0) { push(5); n /= 5; }
+  while (n % 3 == 0) { push(3); n /= 3; }
+  while (n % 8 == 0) { push(8); n /= 8; }
+  if (n % 4 == 0) { push(4); n /= 4; }
+  if (n % 2 == 0) { push(2); n /= 2; }
+  return (n == 1 && shift <= 32) ? plan : 0u;
+}
 
 template <class C>
 static int fft_rows(C* data, int n, int rows, int dir, const C* tw, cudaStream_t s) {
@@ -138,7 +151,7 @@ static int fft_rows(C* data, int n, int rows, int dir, const C* tw, cudaStream_t
     attr_set = true;
   }
   if (smem > 200 * 1024) {
-    if (smem / 2 > 200 * 1024) return set_error(TMBIR_ERR_SHAPE, "setup FFT length too large");
+    if (smem / 2 > 200 * 1024 || (n & (n - 1)) != 0) return set_error(TMBIR_ERR_SHAPE, "setup FFT length too large");
     if (dir < 0)
       k_fft_rows_inplace<-1, C><<<rows, 1024, smem / 2, s>>>(data, n, ilog2(n), (size_t)n, tw);
     else
@@ -146,10 +159,12 @@ static int fft_rows(C* data, int n, int rows, int dir, const C* tw, cudaStream_t
     TMBIR_CHECK_LAUNCH();
     return TMBIR_OK;
   }
+  const unsigned plan = fft_plan(n);
+  if (!plan) return set_error(TMBIR_ERR_SHAPE, "setup FFT length must be 2^a 3^b 5^c");
   if (dir < 0)
-    k_fft_rows<-1, C><<<rows, 256, smem, s>>>(data, n, ilog2(n), (size_t)n, tw);
+    k_fft_rows<-1, C><<<rows, 256, smem, s>>>(data, n, plan, (size_t)n, tw);
   else
-    k_fft_rows<1, C><<<rows, 256, smem, s>>>(data, n, ilog2(n), (size_t)n, tw);
+    k_fft_rows<1, C><<<rows, 256, smem, s>>>(data, n, plan, (size_t)n, tw);
   TMBIR_CHECK_LAUNCH();
   return TMBIR_OK;
 }
@@ -543,11 +558,19 @@ void nufft_psi_table(int nmodes, int nfine, int w, double beta, std::vector<doub
 }
 
 // Scratch carve-up (complex elements, FP64 worst case):
-//   kernel spectrum:  tw[4N] | grid[(4N)^2] | tmp[(4N)^2]   (the 2N circulant FFT reuses grid)
+//   kernel spectrum:  tw[4N] | grid[(4N)^2] | tmp[(4N)^2]   (the 2N circulant FFT reuses grid);
+//                     summed directly: tw[4N] | grid[(2N)^2] | tmp[(2N)^2] | cos/sin[n_angles]
 //   back-projection:  tw[2N] | strengths[n_angles * n_det] | grid[(2N)^2] | tmp[(2N)^2]
+// K by direct summation when the rows of the 4N NUFFT grid do not fit shared memory and are
+// not a power of two (no in-place fallback): the 2560 side
+static bool kernel_direct(int N) {
+  const size_t nf = 4 * (size_t)N;
+  return 2 * nf * sizeof(double2) > 200 * 1024 && (nf & (nf - 1)) != 0;
+}
+
 size_t setup_scratch_bytes(const tmbir_group& g) {
-  const size_t N = g.N, nf_k = 4 * N, nf_a = 2 * N;
-  const size_t k_elems = nf_k + 2 * nf_k * nf_k;
+  const size_t N = g.N, nf_k = 4 * N, nf_a = 2 * N, M = 2 * N;
+  const size_t k_elems = kernel_direct(g.N) ? nf_k + 2 * M * M + (size_t)g.n_angles : nf_k + 2 * nf_k * nf_k;
   const size_t rows = (size_t)g.n_angles * g.n_det;
   const size_t B = std::min(g.n_slices, kBackprojBatch);
   // twiddles, strengths, grids, pruned transposes, sample-major strengths (always kBackprojBatch wide)
@@ -575,10 +598,46 @@ __global__ void k_twiddle(C* tw, int n) {
   }
 }
 
+// K(d) = (1/n_det) sum_a D(e_a . d) summed directly, D(t) = sin(pi (n_det - 1) e / n_det) /
+// sin(pi e / n_det) with e = t reduced to the nearest period of n_det, and n_det - 1 where the
+// denominator vanishes; cs holds (cos, sin) of every angle
+__global__ void k_angle_table(const double* __restrict__ angles, int na, double2* cs) {
+  for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < na; a += gridDim.x * blockDim.x) {
+    double sv, cv;
+    sincos(angles[a], &sv, &cv);
+    cs[a] = make_double2(cv, sv);
+  }
+}
+__global__ void k_kernel_direct(const double2* __restrict__ cs, int na, int nd, int N, double* __restrict__ K) {
+  const int W = 2 * N - 1;
+  for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < W * W; id += gridDim.x * blockDim.x) {
+    const double dx = (double)(id % W - (N - 1)), dy = (double)(id / W - (N - 1));
+    double sum = 0.0;
+    for (int a = 0; a < na; ++a) {
+      const double2 e2 = cs[a];
+      const double t = dx * e2.x + dy * e2.y;
+      const double e = t - (double)nd * rint(t / (double)nd);
+      const double den = sinpi(e / (double)nd);
+      sum += den == 0.0 ? (double)(nd - 1) : sinpi((double)(nd - 1) * e / (double)nd) / den;
+    }
+    K[id] = sum / (double)nd;
+  }
+}
+
+static int circulant_spectrum(Ctx& c, int gi);
+
 int build_kernel_spectrum(Ctx& c, int gi) {
   GroupDev& g = c.gdev[gi];
   cudaStream_t s = c.stream;
   const int N = g.N, nf = 4 * N, M = 2 * N;
+  if (kernel_direct(N)) {
+    double2* cs = reinterpret_cast<double2*>(c.scratch) + nf + 2 * (size_t)M * M;
+    k_angle_table<<<(g.na + 255) / 256, 256, 0, s>>>(g.angles, g.na, cs);
+    TMBIR_CHECK_LAUNCH();
+    k_kernel_direct<<<152 * 16, 256, 0, s>>>(cs, g.na, g.nd, N, g.K);
+    TMBIR_CHECK_LAUNCH();
+    return circulant_spectrum(c, gi);
+  }
   double2* tw = reinterpret_cast<double2*>(c.scratch);
   double2* grid = tw + nf;
   double2* tmp = grid + (size_t)nf * nf;
@@ -597,7 +656,16 @@ int build_kernel_spectrum(Ctx& c, int gi) {
   if (int e = fft2_transposed(grid, tmp, nf, 1, +1, tw, s)) return e;
   k_deconv_K<<<1024, 256, 0, s>>>(tmp, nf, N, g.psiK, g.K);
   TMBIR_CHECK_LAUNCH();
-  // real spectrum of the 2N x 2N circulant embedding
+  return circulant_spectrum(c, gi);
+}
+
+// real spectrum of the 2N x 2N circulant embedding of K, in the layout of pass 2
+static int circulant_spectrum(Ctx& c, int gi) {
+  GroupDev& g = c.gdev[gi];
+  cudaStream_t s = c.stream;
+  const int N = g.N, M = 2 * N;
+  double2* tw = reinterpret_cast<double2*>(c.scratch);
+  double2* grid = tw + 4 * (size_t)N;  // past the largest twiddle table
   k_twiddle<double2><<<(M + 255) / 256, 256, 0, s>>>(tw, M);
   TMBIR_CHECK_LAUNCH();
   double2* cg = grid;

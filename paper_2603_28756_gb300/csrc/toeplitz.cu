@@ -6,7 +6,10 @@
 
 namespace tmbir {
 
-bool supported_N(int N) { return N == 64 || N == 128 || N == 256 || N == 512 || N == 1024 || N == 2048; }
+bool supported_N(int N) {
+  return N == 64 || N == 128 || N == 256 || N == 512 || N == 1024 || N == 2048 || N == 1536 || N == 2560;
+}
+bool block_fft_N(int N) { return N == 1536 || N == 2560; }
 
 void fft_shape(int N, int* T, int* P) {
   switch (N) {
@@ -15,7 +18,8 @@ void fft_shape(int N, int* T, int* P) {
     case 256: *T = 16; *P = 16; break;
     case 512: *T = 16; *P = 32; break;
     case 1024: *T = 32; *P = 32; break;
-    default: *T = 32; *P = 64; break;
+    case 2048: *T = 32; *P = 64; break;
+    default: *T = 32; *P = N / 32; break;  // 1536, 2560: rows of the block-FFT passes
   }
 }
 
@@ -30,6 +34,8 @@ TMBIR_DECL_N(256)
 TMBIR_DECL_N(512)
 TMBIR_DECL_N(1024)
 TMBIR_DECL_N(2048)
+TMBIR_DECL_N(1536)
+TMBIR_DECL_N(2560)
 #undef TMBIR_DECL_N
 
 // ---------------------------------------------------------------- reductions and state update
@@ -114,6 +120,8 @@ __global__ void __launch_bounds__(512) k_finalize(IterState* st, const double* p
     case 512: return FN##512(__VA_ARGS__);                          \
     case 1024: return FN##1024(__VA_ARGS__);                        \
     case 2048: return FN##2048(__VA_ARGS__);                        \
+    case 1536: return FN##1536(__VA_ARGS__);                        \
+    case 2560: return FN##2560(__VA_ARGS__);                        \
     default: return set_error(TMBIR_ERR_SHAPE, "unsupported N");    \
   }
 

@@ -22,6 +22,7 @@
 #pragma once
 #include <cuda_bf16.h>
 
+#include "block_fft.cuh"
 #include "fft.cuh"
 #include "internal.h"
 
@@ -349,6 +350,141 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) k_pass3a(GroupDev g, const It
   });
 }
 
+// ---------------------------------------------------------------- passes 1, 2, 3a for 1536 and 2560
+// The same three passes with block-wide FFTs (block_fft.cuh) instead of group FFTs: a block of
+// 256 threads transforms one row or column at a time.  Layouts, scaling and the packed-real
+// split are those of the group-FFT passes.
+template <int N>
+struct BGeo {
+  static constexpr int THREADS = 256;
+  static constexpr int RB = Geo<N>::RB;             // rows per block, as the stencil expects
+  static constexpr int NB = N / RB;
+  static constexpr int LD = N + 4;
+  static constexpr size_t SM_ROWS = (size_t)(2 * N + RB * LD) * sizeof(float2);  // X, Y, RB staged rows
+  static constexpr size_t SM_COL = (size_t)4 * N * sizeof(float2);              // X, Y, column, sum
+};
+
+template <int N, bool BF>
+__global__ void __launch_bounds__(256) k_pass1_b(GroupDev g, StepArgs a) {
+  using BG = BGeo<N>;
+  extern __shared__ float2 sm[];
+  const float *x, *xp;
+  float beta;
+  if (a.st) {
+    if (skip_iter<BF>(a.st)) return;
+    const int cur = a.st->cur;
+    x = a.xb[cur];
+    xp = a.xb[(cur + 2) % 3];
+    beta = (float)a.st->beta;
+  } else {
+    x = a.x;
+    xp = a.xprev;
+    beta = a.beta;
+  }
+  const int s = blockIdx.x / BG::NB, rb = blockIdx.x % BG::NB;
+  float2* X = sm;
+  float2* Y = sm + N;
+  float2* tb = sm + 2 * N;
+  for (int rr = 0; rr < BG::RB; ++rr) {
+    __syncthreads();  // the previous row's transform has been read
+    const size_t base = g.img_off + ((size_t)s * N + rb * BG::RB + rr) * N;
+    // packed real row z[n] = y[2n] + i y[2n+1] for n < N/2, zero padding above
+    for (int n = threadIdx.x; n < N; n += BG::THREADS) {
+      float2 v = make_float2(0.f, 0.f);
+      if (n < N / 2) {
+        const float2 xv = __ldg(reinterpret_cast<const float2*>(x + base) + n);
+        const float2 pv = __ldg(reinterpret_cast<const float2*>(xp + base) + n);
+        v = make_float2(fmaf(beta, xv.x - pv.x, xv.x), fmaf(beta, xv.y - pv.y, xv.y));
+      }
+      X[n] = v;
+    }
+    const float2* Z = block_fft<N, -1>(X, Y, g.twN);
+    // Y[v] = E[v] + w^v O[v] from Z[v] and Z[N - v]; the Nyquist term Y[N] = Re Z0 - Im Z0
+    for (int v = threadIdx.x; v < N; v += BG::THREADS) {
+      const float2 z = Z[v], zs = Z[(N - v) % N];
+      const float2 e = make_float2(0.5f * (z.x + zs.x), 0.5f * (z.y - zs.y));
+      const float2 o = make_float2(0.5f * (z.y + zs.y), -0.5f * (z.x - zs.x));
+      tb[rr * BG::LD + v] = cadd(e, cmul(__ldg(&g.twM[v]), o));
+    }
+    if (threadIdx.x == 0) tb[rr * BG::LD + N] = make_float2(Z[0].x - Z[0].y, 0.f);
+  }
+  __syncthreads();
+  using IO = SpecIO<BF>;
+  typename IO::T* out = reinterpret_cast<typename IO::T*>(g.spec) + (size_t)s * (N + 1) * N + rb * BG::RB;
+  for (int e = threadIdx.x; e < (N + 1) * BG::RB; e += BG::THREADS) {
+    const int vv = e / BG::RB, rr = e - vv * BG::RB;
+    IO::st(out, (size_t)vv * N + rr, tb[rr * BG::LD + vv]);
+  }
+}
+
+template <int N, bool BF>
+__global__ void __launch_bounds__(256) k_pass2_b(GroupDev g, const IterState* st) {
+  using BG = BGeo<N>;
+  extern __shared__ float2 sm[];
+  if (st && skip_iter<BF>(st)) return;
+  const int vcol = blockIdx.x / g.S, s = blockIdx.x % g.S;  // slices fastest: kernel column reuse
+  using IO = SpecIO<BF>;
+  typename IO::T* p = reinterpret_cast<typename IO::T*>(g.spec) + ((size_t)s * (N + 1) + vcol) * N;
+  float2* X = sm;
+  float2* Y = sm + N;
+  float2* col = sm + 2 * N;
+  float2* sum = sm + 3 * N;
+  for (int r = threadIdx.x; r < N; r += BG::THREADS) col[r] = IO::ld(p, r);
+  for (int h = 0; h < 2; ++h) {
+    __syncthreads();
+    // even half: the column; odd half: the column times exp(-2 pi i r / 2N)
+    for (int r = threadIdx.x; r < N; r += BG::THREADS) X[r] = h ? cmul(col[r], __ldg(&g.twM[r])) : col[r];
+    float2* F = block_fft<N, -1>(X, Y, g.twN);
+    const float* cc = g.chat + ((size_t)vcol * 2 + h) * N;
+    for (int k = threadIdx.x; k < N; k += BG::THREADS) {
+      const float c = __ldg(&cc[k]);
+      F[k] = make_float2(F[k].x * c, F[k].y * c);
+    }
+    float2* G = block_fft<N, 1>(F, F == X ? Y : X, g.twN);
+    for (int r = threadIdx.x; r < N; r += BG::THREADS) {
+      const float2 v = h ? cmulc(G[r], __ldg(&g.twM[r])) : G[r];
+      sum[r] = h ? cadd(sum[r], v) : v;
+    }
+  }
+  __syncthreads();
+  for (int r = threadIdx.x; r < N; r += BG::THREADS) IO::st(p, r, sum[r]);
+}
+
+template <int N, bool BF>
+__global__ void __launch_bounds__(256) k_pass3a_b(GroupDev g, const IterState* st, float* kz) {
+  using BG = BGeo<N>;
+  extern __shared__ float2 sm[];
+  if (st && skip_iter<BF>(st)) return;
+  const int s = blockIdx.x / BG::NB, rb = blockIdx.x % BG::NB;
+  const int r0 = rb * BG::RB;
+  float2* X = sm;
+  float2* Y = sm + N;
+  float2* tb = sm + 2 * N;
+  {
+    using IO = SpecIO<BF>;
+    const typename IO::T* sp = reinterpret_cast<const typename IO::T*>(g.spec) + (size_t)s * (N + 1) * N + r0;
+    for (int e = threadIdx.x; e < (N + 1) * BG::RB; e += BG::THREADS) {
+      const int vv = e / BG::RB, rr = e - vv * BG::RB;
+      tb[rr * BG::LD + vv] = IO::ld(sp, (size_t)vv * N + rr);
+    }
+  }
+  for (int rr = 0; rr < BG::RB; ++rr) {
+    __syncthreads();
+    // the length-2N real inverse as a length-N complex inverse of Z[v] = E[v] + i O[v]
+    for (int vp = threadIdx.x; vp < N; vp += BG::THREADS) {
+      const float2 zv = tb[rr * BG::LD + vp];
+      const float2 zr = tb[rr * BG::LD + N - vp];
+      const float2 e = make_float2(zv.x + zr.x, zv.y - zr.y);
+      const float2 d = make_float2(zv.x - zr.x, zv.y + zr.y);
+      const float2 o = cmulc(d, __ldg(&g.twM[vp]));
+      X[vp] = make_float2(e.x - o.y, e.y + o.x);
+    }
+    const float2* Z = block_fft<N, 1>(X, Y, g.twN);
+    float2* out = reinterpret_cast<float2*>(kz + ((size_t)s * N + r0 + rr) * N);
+    for (int n = threadIdx.x; n < N / 2; n += BG::THREADS) out[n] = Z[n];
+  }
+}
+
 // ---------------------------------------------------------------- pass 3b: gradient and update
 // A block owns RB consecutive rows of one group and marches through a chunk of its slices,
 // keeping y for slices z-1, z, z+1 (rows -1 .. RB) in a three-slot ring so every slice of y is
@@ -526,12 +662,22 @@ static int set_smem_limits() {
   using Gm = Geo<N>;
   static bool done = false;
   if (done) return TMBIR_OK;
-  TMBIR_CUDA(cudaFuncSetAttribute(k_pass1<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Gm::SM1));
-  TMBIR_CUDA(cudaFuncSetAttribute(k_pass1<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Gm::SM1));
-  TMBIR_CUDA(cudaFuncSetAttribute(k_pass2<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Gm::SM2));
-  TMBIR_CUDA(cudaFuncSetAttribute(k_pass2<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Gm::SM2));
-  TMBIR_CUDA(cudaFuncSetAttribute(k_pass3a<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Gm::SM1));
-  TMBIR_CUDA(cudaFuncSetAttribute(k_pass3a<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Gm::SM1));
+  if constexpr (is_block_fft_size<N>()) {
+    using BG = BGeo<N>;
+    TMBIR_CUDA(cudaFuncSetAttribute(k_pass1_b<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BG::SM_ROWS));
+    TMBIR_CUDA(cudaFuncSetAttribute(k_pass1_b<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BG::SM_ROWS));
+    TMBIR_CUDA(cudaFuncSetAttribute(k_pass2_b<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BG::SM_COL));
+    TMBIR_CUDA(cudaFuncSetAttribute(k_pass2_b<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BG::SM_COL));
+    TMBIR_CUDA(cudaFuncSetAttribute(k_pass3a_b<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BG::SM_ROWS));
+    TMBIR_CUDA(cudaFuncSetAttribute(k_pass3a_b<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BG::SM_ROWS));
+  } else {
+    TMBIR_CUDA(cudaFuncSetAttribute(k_pass1<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Gm::SM1));
+    TMBIR_CUDA(cudaFuncSetAttribute(k_pass1<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Gm::SM1));
+    TMBIR_CUDA(cudaFuncSetAttribute(k_pass2<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Gm::SM2));
+    TMBIR_CUDA(cudaFuncSetAttribute(k_pass2<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Gm::SM2));
+    TMBIR_CUDA(cudaFuncSetAttribute(k_pass3a<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Gm::SM1));
+    TMBIR_CUDA(cudaFuncSetAttribute(k_pass3a<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Gm::SM1));
+  }
 #define TMBIR_P3ATTR(M, Q)                                                                           \
   TMBIR_CUDA(cudaFuncSetAttribute(k_pass3<N, M, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                   (int)Geo3<N>::SM));
@@ -546,10 +692,18 @@ template <int N>
 static int pass1_n(const GroupDev& g, const StepArgs& a, bool bf16, cudaStream_t s) {
   using Gm = Geo<N>;
   if (int e = set_smem_limits<N>()) return e;
-  if (bf16)
-    k_pass1<N, true><<<g.S * Gm::NB, Gm::THREADS, Gm::SM1, s>>>(g, a);
-  else
-    k_pass1<N, false><<<g.S * Gm::NB, Gm::THREADS, Gm::SM1, s>>>(g, a);
+  if constexpr (is_block_fft_size<N>()) {
+    using BG = BGeo<N>;
+    if (bf16)
+      k_pass1_b<N, true><<<g.S * BG::NB, BG::THREADS, BG::SM_ROWS, s>>>(g, a);
+    else
+      k_pass1_b<N, false><<<g.S * BG::NB, BG::THREADS, BG::SM_ROWS, s>>>(g, a);
+  } else {
+    if (bf16)
+      k_pass1<N, true><<<g.S * Gm::NB, Gm::THREADS, Gm::SM1, s>>>(g, a);
+    else
+      k_pass1<N, false><<<g.S * Gm::NB, Gm::THREADS, Gm::SM1, s>>>(g, a);
+  }
   TMBIR_CHECK_LAUNCH();
   return TMBIR_OK;
 }
@@ -557,11 +711,20 @@ template <int N>
 static int pass2_n(const GroupDev& g, const IterState* st, bool bf16, cudaStream_t s) {
   using Gm = Geo<N>;
   if (int e = set_smem_limits<N>()) return e;
-  const int blocks = (g.S * (N + 1) + Gm::CPB - 1) / Gm::CPB;
-  if (bf16)
-    k_pass2<N, true><<<blocks, Gm::THREADS, Gm::SM2, s>>>(g, st);
-  else
-    k_pass2<N, false><<<blocks, Gm::THREADS, Gm::SM2, s>>>(g, st);
+  if constexpr (is_block_fft_size<N>()) {
+    using BG = BGeo<N>;
+    const int blocks = g.S * (N + 1);
+    if (bf16)
+      k_pass2_b<N, true><<<blocks, BG::THREADS, BG::SM_COL, s>>>(g, st);
+    else
+      k_pass2_b<N, false><<<blocks, BG::THREADS, BG::SM_COL, s>>>(g, st);
+  } else {
+    const int blocks = (g.S * (N + 1) + Gm::CPB - 1) / Gm::CPB;
+    if (bf16)
+      k_pass2<N, true><<<blocks, Gm::THREADS, Gm::SM2, s>>>(g, st);
+    else
+      k_pass2<N, false><<<blocks, Gm::THREADS, Gm::SM2, s>>>(g, st);
+  }
   TMBIR_CHECK_LAUNCH();
   return TMBIR_OK;
 }
@@ -589,10 +752,18 @@ static int pass3_n(const GroupDev& g, const StepArgs& a, Pass3Mode m, const Prio
   float* kz = m == Pass3Mode::Apply ? a.out + g.img_off : g.kz;
   const IterState* st = m == Pass3Mode::Iterate ? a.st : nullptr;
   if (part & 1) {
-    if (bf16)
-      k_pass3a<N, true><<<g.S * Gm::NB, Gm::THREADS, Gm::SM1, s>>>(g, st, kz);
-    else
-      k_pass3a<N, false><<<g.S * Gm::NB, Gm::THREADS, Gm::SM1, s>>>(g, st, kz);
+    if constexpr (is_block_fft_size<N>()) {
+      using BG = BGeo<N>;
+      if (bf16)
+        k_pass3a_b<N, true><<<g.S * BG::NB, BG::THREADS, BG::SM_ROWS, s>>>(g, st, kz);
+      else
+        k_pass3a_b<N, false><<<g.S * BG::NB, BG::THREADS, BG::SM_ROWS, s>>>(g, st, kz);
+    } else {
+      if (bf16)
+        k_pass3a<N, true><<<g.S * Gm::NB, Gm::THREADS, Gm::SM1, s>>>(g, st, kz);
+      else
+        k_pass3a<N, false><<<g.S * Gm::NB, Gm::THREADS, Gm::SM1, s>>>(g, st, kz);
+    }
     TMBIR_CHECK_LAUNCH();
   }
   if (!(part & 2)) return TMBIR_OK;

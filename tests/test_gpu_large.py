@@ -183,3 +183,41 @@ def test_hierarchical_finest_level_full_size(orc):
         gr = zr - float(gen_b(zz)[r, c]) + orc.prior_point(xs, pr, zz - lo, r, c)
         assert abs(float(G[zz, r, c].item()) - gr) <= 1e-5 * gscale
         assert abs(float(x1[zz, r, c].item()) - (xs[zz - lo, r, c] - gr / L)) <= 1e-5 * gscale / L + 1e-7
+
+
+@pytest.mark.parametrize("N,na", [(1536, 96), (2560, 64)])
+def test_mixed_radix_sides(orc, N, na):
+    # image sides whose 2N transforms take radix 3 (1536 = 2^9 * 3) or radix 5 (2560 = 2^9 * 5):
+    # K in full, R*g and the FBP start at sampled pixels, then whole-slice products, the
+    # gradient and three fast-gradient iterations against the oracle
+    S, span = 2, math.pi
+    p = synth.volume(S=S, N=N, n_angles=na, n_ellipsoids=6, seed=1004)
+    ctx = tm.Context([tm.Group(N=N, angles=list(p.theta), n_slices=S)])
+    d_sino = dev(p.sino)
+    d_atg, d_x0 = ctx.build_operator_fbp(d_sino)
+    Kref = orc.kernel(N, p.theta, N)
+    K = host(ctx.kernel(0), Kref.shape)
+    assert np.max(np.abs(K - Kref)) <= 1e-10 * np.max(np.abs(Kref))
+    atg = host(d_atg, (S, N, N))
+    x0 = host(d_x0, (S, N, N))
+    g = p.sino.astype(np.float64)
+    rng = np.random.default_rng(13)
+    pts = samples(rng, S, N, 8)
+    for z, r, col in pts:
+        assert abs(atg[z, r, col] - orc.adjoint_point(g[z], N, p.theta, r, col)) <= 1e-6 * np.max(np.abs(atg))
+    h = orc.ramp_filter(g)
+    for z, r, col in pts:
+        ref = (span / na) * orc.adjoint_point(h[z], N, p.theta, r, col)
+        assert abs(x0[z, r, col] - ref) <= 2e-4 * np.max(np.abs(x0))
+    pr = orc.Prior(**PRIOR)
+    x = synth.random_image(rng, (S, N, N), 0.5).astype(np.float64)
+    b = synth.random_image(rng, (S, N, N), 4.0e4).astype(np.float64)  # seeded stand-in for R*g
+    d_b = dev(b)
+    Chat = orc.circulant_spectrum(Kref)
+    assert rel(host(ctx.normal_apply(dev(x)), x.shape), orc.toeplitz(x, Kref, Chat)) < 1e-5
+    assert rel(host(ctx.gradient(dev(x), d_b, tm.Params(**PRIOR)), x.shape), orc.gradient(x, b, Kref, pr, Chat)) < 1e-5
+    L = 1.0e5
+    xs = torch.zeros(x.size, dtype=torch.float32, device="cuda")
+    ctx.reconstruct(xs, d_b, tm.Params(**PRIOR, L=L, max_iter=3))
+    ref = orc.nesterov(np.zeros(x.shape), b, 0.0, Kref, pr, L, 3, Chat=Chat)
+    assert rel(host(xs, x.shape), ref) < 1e-4
