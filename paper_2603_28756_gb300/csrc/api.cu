@@ -919,12 +919,10 @@ int tmbir_autotune(tmbir_ctx* ctx, const float* d_x, const float* d_atg, const t
         (rc = launch_pass3(g, a, Pass3Mode::Iterate, pc, c.partials, 0, s, false, 1)))
       break;
     std::vector<int> cands;
-    for (int z : {1, 2, 3, 4, 6, 8, 12, 16, 24, 32})
+    for (int z : {1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64})
       if (z <= g.S) cands.push_back(z);
     g.zc = 0;
-    int T, P;
-    fft_shape(g.N, &T, &P);
-    const int dflt = pass3_slices_per_block(g.S, g.N / (4 * (32 / T)));
+    const int dflt = pass3_slices_per_block(g.S, pass3_row_blocks(g.N));
     if (std::find(cands.begin(), cands.end(), dflt) == cands.end()) cands.push_back(dflt);
     float best = 1e30f;
     int best_z = dflt;

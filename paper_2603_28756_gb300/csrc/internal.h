@@ -179,6 +179,9 @@ int launch_pass2(const GroupDev& g, const IterState* st, cudaStream_t s, bool bf
 int launch_pass3(const GroupDev& g, const StepArgs& a, Pass3Mode mode, const PriorC& pc, double* partials,
                  int block_offset, cudaStream_t s, bool bf16 = false, int part = 3);
 int blocks_pass3(const GroupDev& g);
+// Pass-3b blocks per slice chunk: bands of 4 rows times column blocks of up to 512 columns
+// (eight warps of 64 columns).
+constexpr int pass3_row_blocks(int N) { return (N / 4) * (N / (64 * (N / 64 < 8 ? N / 64 : 8))); }
 // Slices each pass-3 block marches through: enough blocks for about four waves of two
 // blocks per SM on 152 SMs, longer marches when the volume has slices to spare.
 inline int pass3_slices_per_block(int S, int row_blocks) {

@@ -136,17 +136,11 @@ int launch_pass3(const GroupDev& g, const StepArgs& a, Pass3Mode m, const PriorC
   TMBIR_DISPATCH_N(g.N, pass3_, g, a, m, pc, partials, off, bf16, part, s);
 }
 int blocks_pass3(const GroupDev& g) {
-  int T, P;
-  fft_shape(g.N, &T, &P);
-  const int nb = g.N / (4 * (32 / T));
+  const int nb = pass3_row_blocks(g.N);
   const int zc = pass3_zc(g, nb);
   return nb * ((g.S + zc - 1) / zc);
 }
-int max_blocks_pass3(const GroupDev& g) {
-  int T, P;
-  fft_shape(g.N, &T, &P);
-  return g.N / (4 * (32 / T)) * g.S;
-}
+int max_blocks_pass3(const GroupDev& g) { return pass3_row_blocks(g.N) * g.S; }
 
 int launch_finalize(IterState* st, const double* partials, int nblocks, double* log, cudaStream_t s,
                     cudaGraphConditionalHandle cond, int use_cond, int trip_launches) {

@@ -25,6 +25,7 @@
 #include "block_fft.cuh"
 #include "fft.cuh"
 #include "internal.h"
+#include "tc05.cuh"
 
 namespace tmbir {
 
@@ -64,11 +65,9 @@ struct Geo {
   static constexpr int CPB = UNITS / 2; // columns per block in pass 2
   static constexpr size_t SM_FFT = (size_t)W * G * F::SMEM * sizeof(float2);
   static constexpr size_t SM_TB = (size_t)RB * LD * sizeof(float2);
-  static constexpr size_t SM_Y = (size_t)3 * (RB + 2) * N * sizeof(float);
   static constexpr size_t cmax(size_t a, size_t b) { return a > b ? a : b; }
   static constexpr size_t SM1 = cmax(SM_FFT, SM_TB);
   static constexpr size_t SM2 = SM_FFT;
-  static constexpr size_t SM3 = cmax(SM1, SM_Y);
 };
 
 // ---------------------------------------------------------------- special-function unit helpers
@@ -486,57 +485,382 @@ __global__ void __launch_bounds__(256) k_pass3a_b(GroupDev g, const IterState* s
 }
 
 // ---------------------------------------------------------------- pass 3b: gradient and update
-// A block owns RB consecutive rows of one group and marches through a chunk of its slices,
-// keeping y for slices z-1, z, z+1 (rows -1 .. RB) in a three-slot ring so every slice of y is
-// read from memory once per chunk.  Per slice each thread walks its voxels and sums rho' over
-// the 26 neighbours.  The voxel loop is a plain runtime loop so the unrolled neighbourhood
-// stays small enough for the instruction cache.  Each unordered neighbour pair enters Phi
-// once, from the voxel it is a forward offset of.  With only the ring in shared memory and no
-// transform registers, three blocks of eight warps fit an SM (one at N = 2048).
+// The prior gradient of Eq. 5 at voxel v is sum_o w_o rho'(y_v - y_{v+o}) over the 26
+// neighbours; rho' is odd, so the pair (v, v+o) adds +f to v and -f to v+o.  Every unordered
+// pair is evaluated once, from its lexicographically smaller end (13 forward offsets), and
+// the value is handed to the other end instead of being recomputed there.
+//
+// A block owns R = 4 rows (a band) by BC columns of one group and marches through a chunk of
+// its slices.  Warp w owns 64 columns; lane l owns the voxel pair a = 2l, b = 2l + 1 of every
+// row of the band as the two lanes of packed FP32 pairs, so the pair (a, b) stays in the
+// thread, the pairs with columns a - 1 and b + 1 go to the neighbouring lanes by shuffle, and
+// the pairs that cross a warp's outer columns are evaluated once more by the receiving warp
+// (nine per row, spread over the lanes before the row walk).  Rows are walked top to bottom
+// with the halo rows -1 and R as sources of pairs into the band; slice z is the source of
+// the pairs into slice z + 1, whose contributions wait in shared memory (one entry per
+// thread) for the next step.  A chunk starting at z0 > 0 first evaluates the pairs between
+// slices z0 - 1 and z0 (the only pairs evaluated twice, once per chunk).  Shared memory holds
+// y for slices z and z + 1 (rows -1 .. R, columns c0 - 4 .. c0 + BC + 3), each beside a copy
+// shifted by one column so that the neighbour pairs (a - 1, a) and (b, b + 1) are aligned 8-byte
+// loads like (a, b); x and x_prev of slice z + 2, arriving by asynchronous copies while slice
+// z is worked on; the carried contributions; and K (*) y, R*g and x_k at each thread's voxels,
+// copied asynchronously one slice ahead.  Neighbours outside the volume read the voxel itself
+// (d = 0 adds nothing).
 template <int N>
-struct Geo3 {
-  using Gm = Geo<N>;
-  static constexpr int RB = Gm::RB, W = 2 * Gm::W, THREADS = 32 * W;
-  static constexpr int ROWS = RB + 2;  // ring rows (one halo row each side)
-  static constexpr size_t SM = (size_t)3 * ROWS * N * sizeof(float);
-  static constexpr int MINB = SM * 3 <= 220 * 1024 ? 3 : 1;
+struct GeoP {
+  static_assert(N % 64 == 0, "a warp owns 64 columns");
+  static constexpr int R = 4;                             // rows of a band
+  static constexpr int WPB = N / 64 < 8 ? N / 64 : 8;     // warps per block
+  static constexpr int THREADS = 32 * WPB;
+  static constexpr int BC = 64 * WPB;                     // columns of a block
+  static constexpr int CB = N / BC;                       // column blocks per band
+  static constexpr int NB = N / R;                        // bands per slice
+  static constexpr int LDR = BC + 8;                      // ring row stride (floats)
+  static constexpr int RING = (R + 2) * LDR;              // y of one slice (the shifted copy follows)
+  static constexpr int NEDGE = 9 * R;                     // cross-warp pairs per warp and step
+  static constexpr int FIN = 3 * R * THREADS;            // K (*) y, R*g, x_k of the band (float2)
+  // ring (2 slices of y and shifted y) | staging (x, x_prev of one slice) | carry | cross-warp
+  // pair values | the next slice's K (*) y, R*g and x_k at each thread's voxels
+  static constexpr size_t SM = (size_t)(6 * RING + R * BC + WPB * NEDGE) * sizeof(float) + (size_t)FIN * 8;
+  static_assert(N % BC == 0, "column blocks");
 };
 
-// y = x + beta (x - x_prev) for block rows -1 .. RB of one slice into a ring slot (zero outside)
+// y = x + beta (x - x_prev) of one slice, rows r0 - 1 .. r0 + R, columns c0 - 4 .. c0 + BC + 3,
+// into a ring slot (zero outside the image)
 template <int N>
-__device__ __forceinline__ void load_ring(float* slot, const float* x, const float* xp, float beta, size_t off_slice,
-                                          int r0) {
-  using G3 = Geo3<N>;
-  for (int e = threadIdx.x; e < G3::ROWS * (N / 4); e += G3::THREADS) {
-    const int c4 = e % (N / 4), rowi = e / (N / 4);
-    const int rr = r0 - 1 + rowi;
+__device__ __forceinline__ void load_ring_p(float* slot, const float* x, const float* xp, float beta,
+                                            size_t off_slice, int r0, int c0) {
+  using GP = GeoP<N>;
+  constexpr int Q = GP::LDR / 4;
+  for (int e = threadIdx.x; e < (GP::R + 2) * Q; e += GP::THREADS) {
+    const int q = e % Q, rowi = e / Q;
+    const int rr = r0 - 1 + rowi, cc = c0 - 4 + 4 * q;
     float4 yv = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (rr >= 0 && rr < N) {
-      const size_t off = off_slice + (size_t)rr * N;
-      const float4 xv = __ldg(reinterpret_cast<const float4*>(x + off) + c4);
-      const float4 pv = __ldg(reinterpret_cast<const float4*>(xp + off) + c4);
+    if (rr >= 0 && rr < N && cc >= 0 && cc < N) {
+      const size_t off = off_slice + (size_t)rr * N + cc;
+      const float4 xv = __ldg(reinterpret_cast<const float4*>(x + off));
+      const float4 pv = __ldg(reinterpret_cast<const float4*>(xp + off));
       yv = make_float4(fmaf(beta, xv.x - pv.x, xv.x), fmaf(beta, xv.y - pv.y, xv.y), fmaf(beta, xv.z - pv.z, xv.z),
                        fmaf(beta, xv.w - pv.w, xv.w));
     }
-    reinterpret_cast<float4*>(slot + rowi * N)[c4] = yv;
+    reinterpret_cast<float4*>(slot + rowi * GP::LDR)[q] = yv;
   }
+}
+
+// x and x_prev of one slice (the ring's rows and columns) into the staging area by
+// asynchronous 16-byte copies, zero-filled outside the image
+template <int N>
+__device__ __forceinline__ void stage_issue(float* stg, const float* x, const float* xp, size_t off_slice, int r0,
+                                            int c0) {
+  using GP = GeoP<N>;
+  constexpr int Q = GP::LDR / 4;
+  for (int e = threadIdx.x; e < (GP::R + 2) * Q; e += GP::THREADS) {
+    const int q = e % Q, rowi = e / Q;
+    const int rr = r0 - 1 + rowi, cc = c0 - 4 + 4 * q;
+    const bool ok = rr >= 0 && rr < N && cc >= 0 && cc < N;
+    const size_t off = ok ? off_slice + (size_t)rr * N + cc : off_slice;
+    tc05::cp_async16(stg + 4 * e, x + off, ok);
+    tc05::cp_async16(stg + GP::RING + 4 * e, xp + off, ok);
+  }
+}
+// y = x + beta (x - x_prev) from the staging area into a ring slot, and the copy shifted by
+// one column (shifted[i] = y[i + 1]) after it
+template <int N>
+__device__ __forceinline__ void stage_to_ring(float* slot, const float* stg, float beta) {
+  using GP = GeoP<N>;
+  for (int e = threadIdx.x; e < GP::RING / 4; e += GP::THREADS) {
+    const float4 xv = reinterpret_cast<const float4*>(stg)[e];
+    const float4 pv = reinterpret_cast<const float4*>(stg + GP::RING)[e];
+    const float4 y =
+        make_float4(fmaf(beta, xv.x - pv.x, xv.x), fmaf(beta, xv.y - pv.y, xv.y), fmaf(beta, xv.z - pv.z, xv.z),
+                    fmaf(beta, xv.w - pv.w, xv.w));
+    float nx = 0.f;
+    if (4 * e + 4 < GP::RING) {
+      const float x4 = stg[4 * e + 4], p4 = stg[GP::RING + 4 * e + 4];
+      nx = fmaf(beta, x4 - p4, x4);
+    }
+    reinterpret_cast<float4*>(slot)[e] = y;
+    reinterpret_cast<float4*>(slot + GP::RING)[e] = make_float4(y.y, y.z, y.w, nx);
+  }
+}
+// the shifted copy of a ring slot whose y part is in place
+template <int N>
+__device__ __forceinline__ void ring_shift(float* slot) {
+  using GP = GeoP<N>;
+  for (int e = threadIdx.x; e < GP::RING / 4; e += GP::THREADS) {
+    const float4 v = reinterpret_cast<const float4*>(slot)[e];
+    const float nx = 4 * e + 4 < GP::RING ? slot[4 * e + 4] : 0.f;
+    reinterpret_cast<float4*>(slot + GP::RING)[e] = make_float4(v.y, v.z, v.w, nx);
+  }
+}
+
+// The lane's neighbour pair at column offset DX in a ring row (y part; the shifted copy sits
+// RING floats further): DX = -1: (y[a - 1], y[a]), 0: (y[a], y[b]), +1: (y[b], y[b + 1]).
+// A neighbour outside the image reads the voxel itself: with ROWE for a missing row (row_ok
+// false), with COLE for a missing column a - 1 or b + 1.
+template <int N, int DX, bool ROWE, bool COLE>
+__device__ __forceinline__ float2 nb_pair(const float* row, int ia, float2 y, bool row_ok, bool okL, bool okR) {
+  constexpr int RING = GeoP<N>::RING;
+  float2 n;
+  if constexpr (DX < 0)
+    n = *reinterpret_cast<const float2*>(row + RING + ia - 2);
+  else if constexpr (DX == 0)
+    n = *reinterpret_cast<const float2*>(row + ia);
+  else
+    n = *reinterpret_cast<const float2*>(row + RING + ia);
+  if constexpr (COLE) {
+    if constexpr (DX < 0) n.x = okL ? n.x : y.x;
+    if constexpr (DX > 0) n.y = okR ? n.y : y.y;
+  }
+  if constexpr (ROWE) n = row_ok ? n : y;
+  return n;
+}
+
+// Weighted pair value f = w sigma^2 rho'(y - nb) / sigma^2 of two pairs at once (the weight
+// arrives as wq = w (q - p) / sigma^2, wp = w p / sigma^2), with the identity of nbr2:
+// sigma^2 rho'(d) = d |d/sigma|^(q-2) r (p + (q - p) r), r = 1 / (1 + |d/(c sigma)|^(q-p)).
+// With PH, ph += sigma^2 rho(d) = d^2 |d/sigma|^(q-2) r (unweighted).
+template <bool Q2, bool PH>
+__device__ __forceinline__ float2 pairv(float2 y, float2 nb, const PriorK& k, float2 wq, float2 wp, float2& ph) {
+  const float2 d = f2fma(nb, f2(-1.f), y);
+  const float2 sq = f2fma(d, d, f2(1e-30f));
+  const float2 la = make_float2(lg2a(sq.x), lg2a(sq.y));
+  const float2 s = f2fma(k.half_qp, la, k.qp_l2);
+  const float2 e = f2add(make_float2(ex2a(s.x), ex2a(s.y)), f2(1.f));
+  const float2 r = make_float2(rcpa(e.x), rcpa(e.y));
+  float2 dr = f2mul(d, r);
+  if constexpr (!Q2) {
+    const float2 s2 = f2fma(k.half_q2, la, k.q2_l2);
+    dr = f2mul(dr, make_float2(ex2a(s2.x), ex2a(s2.y)));
+  }
+  if constexpr (PH) ph = f2fma(d, dr, ph);
+  return f2mul(dr, f2fma(wq, r, wp));
+}
+
+// hi + lo += v with the rounding error of the addition kept in lo (Knuth's TwoSum): the
+// per-slice partial sums stay in FP32, whose pipe is wide, instead of FP64, whose is not
+__device__ __forceinline__ void two_sum_add(float& hi, float& lo, float v) {
+  const float s = hi + v;
+  const float bp = s - hi;
+  lo += (hi - (s - bp)) + (v - bp);
+  hi = s;
+}
+
+// Block reduction of compensated FP32 sums (hi + lo per thread) to partials[block]: TwoSum
+// across each warp, FP64 across the warps, in a fixed order.
+template <int W>
+__device__ __forceinline__ void block_partials_f(float (&hi)[kParts], float (&lo)[kParts], double* red,
+                                                 double* out) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int j = 0; j < kParts; ++j) {
+    float h = hi[j], l = lo[j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float h2 = __shfl_down_sync(0xffffffffu, h, o), l2 = __shfl_down_sync(0xffffffffu, l, o);
+      l += l2;
+      two_sum_add(h, l, h2);
+    }
+    if (lane == 0) red[warp * kParts + j] = (double)h + (double)l;
+  }
+  __syncthreads();
+  if (threadIdx.x < kParts) {
+    double sum = 0.0;
+    for (int w = 0; w < W; ++w) sum += red[w * kParts + threadIdx.x];
+    out[threadIdx.x] = sum;
+  }
+}
+
+// class weights of the pair values: wq = w (q - p) / sigma^2, wp = w p / sigma^2 for the face,
+// edge and corner neighbours
+struct PairW {
+  float2 wq[3], wp[3];
+};
+
+// the three pairs (+1, DY, -1 / 0 / +1) from source voxels (a, b) into ring row T of the next
+// slice: +f to the source, -f to the target (own lanes) or sent to the lane that owns it
+template <int N, bool Q2, bool PH, bool ROWE, bool COLE, int DY>
+__device__ __forceinline__ void cross3(float2 y, const float* T, int ia, bool rok, bool okL, bool okR,
+                                       const PriorK& k, const PairW& pw, float2& gsrc, float2& C, float& sR,
+                                       float& sL, float2 (&phr)[3]) {
+  constexpr int CS = DY == 0 ? 1 : 2;  // class of the dx = -1, +1 pairs
+  constexpr int C0 = DY == 0 ? 0 : 1;  // class of the dx = 0 pair
+  float2 f = pairv<Q2, PH>(y, nb_pair<N, -1, ROWE, COLE>(T, ia, y, rok, okL, okR), k, pw.wq[CS], pw.wp[CS], phr[CS]);
+  gsrc = f2add(gsrc, f);
+  sL += f.x;
+  C.x -= f.y;
+  f = pairv<Q2, PH>(y, nb_pair<N, 0, ROWE, COLE>(T, ia, y, rok, okL, okR), k, pw.wq[C0], pw.wp[C0], phr[C0]);
+  gsrc = f2add(gsrc, f);
+  C = f2fma(f, f2(-1.f), C);
+  f = pairv<Q2, PH>(y, nb_pair<N, 1, ROWE, COLE>(T, ia, y, rok, okL, okR), k, pw.wq[CS], pw.wp[CS], phr[CS]);
+  gsrc = f2add(gsrc, f);
+  C.y -= f.x;
+  sR += f.y;
+}
+
+// One slice step of a band: every pair whose source voxel lies in slice zs (ring slot S0) and
+// whose other end lies in zs or zs + 1 (slot S1, when have1).  The carried contributions of
+// slice zs (cr, this thread's entries, row stride BC / 2) start the gradient rows and are
+// replaced by those of slice zs + 1.  PRE: only the pairs into slice zs + 1 (a chunk start);
+// otherwise each owned row t is handed to fin(t, gradient sum, y) once complete, with ph the
+// unweighted sigma^2 rho sums by class of the pairs the band owns.  ROWE: the band is the
+// image's first or last; COLE: the warp holds its first or last 64 columns.  Elsewhere every
+// neighbour lies inside the image and the boundary tests drop out.
+template <int N, bool Q2, bool PHI, bool PRE, bool ROWE, bool COLE, class Fin>
+__device__ __forceinline__ void band_step(const float* S0, const float* S1, bool have1, int r0, int c0w, int ia,
+                                          bool okL_, bool okR_, float2* cr, float* edge, const PriorK& k,
+                                          const PairW& pw, float2 (&ph)[3], Fin&& fin) {
+  using GP = GeoP<N>;
+  constexpr int R = GP::R, LDR = GP::LDR, HALF = GP::NEDGE / 2, CRS = GP::BC / 2;
+  constexpr bool PH = PHI && !PRE;
+  const int lane = threadIdx.x & 31;
+  const int cw = ia - 4 - 2 * lane;  // ring column of the warp's first column, minus 4
+  const bool top = !ROWE || r0 > 0, bot = !ROWE || r0 + R < N;
+  const bool okL = !COLE || okL_, okR = !COLE || okR_;
+
+  // ---- pairs across the warp's outer columns, evaluated by the receiving warp.  Item
+  // kd * R + t is one pair into column c0w (kd < 5) or c0w + 63 (kd >= 5) of row t:
+  //   kd 0: (0, 0, +1) from row t       kd 5: (0, +1, -1) from row t - 1
+  //   kd 1: (0, +1, +1) from row t - 1  kd 6..8: (+1, -1 / 0 / +1, -1) from rows t + 1, t, t - 1
+  //   kd 2..4: (+1, -1 / 0 / +1, +1) from rows t + 1, t, t - 1
+  // (kd 2..4 and 6..8 land in slice zs + 1).  Two items per lane; slot = -f for the target.
+  if (lane < HALF) {
+    float ys[2], yt[2], wq[2], wp[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int i = lane + h * HALF;
+      const int kd = i / R, t = i - kd * R;
+      const bool left = kd < 5;
+      const int sr = (kd == 0 || kd == 3 || kd == 7) ? 0 : ((kd == 2 || kd == 6) ? 1 : -1);
+      const bool cross = kd >= 2 && kd != 5;
+      const int cls = kd == 0 ? 0 : ((kd & 1) ? 1 : 2);
+      const int tr = t + sr;
+      const bool ok = (!ROWE || (r0 + tr >= 0 && r0 + tr < N)) && (!COLE || (left ? c0w > 0 : c0w + 64 < N)) &&
+                      (cross ? have1 : !PRE);
+      const float tv = (cross ? S1 : S0)[(t + 1) * LDR + cw + (left ? 4 : 67)];
+      const float sv = S0[(tr + 1) * LDR + cw + (left ? 3 : 68)];
+      ys[h] = ok ? sv : tv;
+      yt[h] = tv;
+      wq[h] = cls == 0 ? pw.wq[0].x : (cls == 1 ? pw.wq[1].x : pw.wq[2].x);
+      wp[h] = cls == 0 ? pw.wp[0].x : (cls == 1 ? pw.wp[1].x : pw.wp[2].x);
+    }
+    float2 unused;
+    const float2 f = pairv<Q2, false>(make_float2(ys[0], ys[1]), make_float2(yt[0], yt[1]), k,
+                                      make_float2(wq[0], wq[1]), make_float2(wp[0], wp[1]), unused);
+    edge[lane] = -f.x;
+    edge[lane + HALF] = -f.y;
+  }
+  __syncwarp();
+
+  // ---- the row walk: source rows -1 .. R of slice zs (ring row t + 1 holds image row r0 + t),
+  // unrolled at compile time so that the row tests and the window slides cost nothing
+  const float2 zero = f2(0.f);
+  float2 gc = zero, gn = PRE ? zero : cr[0];                                // gradient rows t, t + 1
+  float2 cm = zero, cc = zero, cp = zero;                                   // carry rows t - 1, t, t + 1
+  float sRc = 0.f, sRn = 0.f, sLc = 0.f, sLn = 0.f;                         // sends into rows t, t + 1
+  float sR1m = 0.f, sR1c = 0.f, sR1p = 0.f, sL1m = 0.f, sL1c = 0.f, sL1p = 0.f;
+  SFor<-1, R + 1>::run([&](auto t_) {
+    constexpr int t = decltype(t_)::value;
+    constexpr bool own = t >= 0 && t < R;
+    const float* rowt = S0 + (t + 1) * LDR;  // slice zs, row t
+    const float2 y = *reinterpret_cast<const float2*>(rowt + ia);
+    float2 phr[3] = {zero, zero, zero};
+    if constexpr (!PRE && own) {  // (0, 0, +1), face
+      const float2 f = pairv<Q2, PH>(y, nb_pair<N, 1, ROWE, COLE>(rowt, ia, y, true, okL, okR), k, pw.wq[0], pw.wp[0],
+                                     phr[0]);
+      gc = f2add(gc, f);
+      gc.y -= f.x;
+      sRc += f.y;
+    }
+    if constexpr (!PRE && t < R) {
+      if (own || top) {  // (0, +1, -1 / 0 / +1) into row t + 1
+        const bool rok = !ROWE || r0 + t + 1 < N;
+        const float* rown = rowt + LDR;
+        float2 f = pairv<Q2, PH>(y, nb_pair<N, -1, ROWE, COLE>(rown, ia, y, rok, okL, okR), k, pw.wq[1], pw.wp[1], phr[1]);
+        gc = f2add(gc, f);
+        sLn += f.x;
+        gn.x -= f.y;
+        f = pairv<Q2, PH>(y, nb_pair<N, 0, ROWE, COLE>(rown, ia, y, rok, okL, okR), k, pw.wq[0], pw.wp[0], phr[0]);
+        gc = f2add(gc, f);
+        gn = f2fma(f, f2(-1.f), gn);
+        f = pairv<Q2, PH>(y, nb_pair<N, 1, ROWE, COLE>(rown, ia, y, rok, okL, okR), k, pw.wq[1], pw.wp[1], phr[1]);
+        gc = f2add(gc, f);
+        gn.y -= f.x;
+        sRn += f.y;
+      }
+    }
+    if (have1) {  // (+1, dy, dx) into rows t - 1, t, t + 1 of slice zs + 1
+      if constexpr (t >= 0) {
+        if (own || bot)
+          cross3<N, Q2, PH, ROWE, COLE, -1>(y, S1 + t * LDR, ia, !ROWE || r0 + t - 1 >= 0, okL, okR, k, pw, gc, cm, sR1m,
+                                      sL1m, phr);
+      }
+      if constexpr (own)
+        cross3<N, Q2, PH, ROWE, COLE, 0>(y, S1 + (t + 1) * LDR, ia, true, okL, okR, k, pw, gc, cc, sR1c, sL1c, phr);
+      if constexpr (t < R) {
+        if (own || top)
+          cross3<N, Q2, PH, ROWE, COLE, 1>(y, S1 + (t + 2) * LDR, ia, !ROWE || r0 + t + 1 < N, okL, okR, k, pw, gc, cp,
+                                     sR1p, sL1p, phr);
+      }
+    }
+    if constexpr (PH && own) {
+#pragma unroll
+      for (int j = 0; j < 3; ++j) ph[j] = f2add(ph[j], phr[j]);
+    }
+    // gradient row t (in-plane sources t - 1, t) and carry row t - 1 (sources t - 2 .. t) are
+    // complete: take the neighbouring lanes' shares
+    if constexpr (!PRE && own) {
+      const float rx = __shfl_up_sync(0xffffffffu, sRc, 1), lx = __shfl_down_sync(0xffffffffu, sLc, 1);
+      gc.x -= lane > 0 ? rx : 0.f;
+      gc.y -= lane < 31 ? lx : 0.f;
+      if (lane == 0) gc.x += edge[t] + edge[R + t];
+      if (lane == 31) gc.y += edge[5 * R + t];
+      fin(t, gc, y);
+    }
+    if constexpr (t >= 1) {
+      const float rx1 = __shfl_up_sync(0xffffffffu, sR1m, 1), lx1 = __shfl_down_sync(0xffffffffu, sL1m, 1);
+      cm.x -= lane > 0 ? rx1 : 0.f;
+      cm.y -= lane < 31 ? lx1 : 0.f;
+      if (lane == 0) cm.x += edge[2 * R + t - 1] + edge[3 * R + t - 1] + edge[4 * R + t - 1];
+      if (lane == 31) cm.y += edge[6 * R + t - 1] + edge[7 * R + t - 1] + edge[8 * R + t - 1];
+      cr[(t - 1) * CRS] = cm;
+    }
+    // slide the windows down one row
+    gc = gn;
+    if constexpr (!PRE && t + 2 < R)
+      gn = cr[(t + 2) * CRS];
+    else
+      gn = zero;
+    sRc = sRn;
+    sRn = 0.f;
+    sLc = sLn;
+    sLn = 0.f;
+    cm = cc;
+    cc = cp;
+    cp = zero;
+    sR1m = sR1c;
+    sR1c = sR1p;
+    sR1p = 0.f;
+    sL1m = sL1c;
+    sL1c = sL1p;
+    sL1p = 0.f;
+  });
 }
 
 // kz: K (*) y of the group from pass 3a ([slice][row][col]); phase: in Iterate mode, the storage
 // phase this launch belongs to (0 FP32, 1 BF16), checked like the other passes.
 template <int N, int MODE, bool Q2>
-__global__ void __launch_bounds__(Geo3<N>::THREADS, Geo3<N>::MINB)
+__global__ void __launch_bounds__(GeoP<N>::THREADS, 2)
     k_pass3(GroupDev g, StepArgs a, PriorC pc, const float* __restrict__ kz, int phase, double* partials,
             int block_offset, int zc) {
-  using Gm = Geo<N>;
-  using G3 = Geo3<N>;
-  constexpr int RB = Gm::RB, ROWS = G3::ROWS;
+  using GP = GeoP<N>;
+  constexpr int R = GP::R;
   constexpr bool PRIOR = MODE != (int)Pass3Mode::Apply;
   constexpr bool PHI = MODE == (int)Pass3Mode::Step || MODE == (int)Pass3Mode::Iterate ||
                        MODE == (int)Pass3Mode::Objective;
   constexpr bool UPDATE = MODE == (int)Pass3Mode::Step || MODE == (int)Pass3Mode::Iterate;
   extern __shared__ float2 sm[];
-  __shared__ double red[G3::W * kParts];
+  __shared__ double red[GP::WPB * kParts];
   const float *x, *xp;
   float* out;
   float beta, invL;
@@ -555,105 +879,142 @@ __global__ void __launch_bounds__(Geo3<N>::THREADS, Geo3<N>::MINB)
     beta = a.beta;
     invL = a.invL;
   }
-  const int rb = blockIdx.x % Gm::NB, chunk = blockIdx.x / Gm::NB;
+  const int band = blockIdx.x % GP::NB;
+  const int cb = (blockIdx.x / GP::NB) % GP::CB;
+  const int chunk = blockIdx.x / (GP::NB * GP::CB);
   const int z0 = chunk * zc, z1 = min(g.S, z0 + zc);
-  const int r0 = rb * RB;
-  float* ring = reinterpret_cast<float*>(sm);
+  const int r0 = band * R, c0 = cb * GP::BC;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int c0w = c0 + 64 * warp;
+  const int acol = c0w + 2 * lane;  // this lane's voxels: columns acol, acol + 1
+  const int ia = 64 * warp + 2 * lane + 4;
   const size_t N2 = (size_t)N * N;
-  // neighbour weights with 1/sigma^2 folded in: nbr2 sums sigma^2 rho' and sigma^2 rho
-  const float2 wf = f2(pc.wf * pc.inv_sig2), we = f2(pc.we * pc.inv_sig2), wc = f2(pc.wc * pc.inv_sig2);
-  const float2 lam = f2(pc.lam);
-  const PriorK pk = prior_k(pc);
-  constexpr int H = N / 2;
-  static_assert(H % 32 == 0, "a warp must cover one row segment");
 
-  double dacc[kParts];
+  float hi[kParts], lo[kParts];  // compensated FP32 sums of the block's slices
 #pragma unroll
-  for (int j = 0; j < kParts; ++j) dacc[j] = 0.0;
+  for (int j = 0; j < kParts; ++j) hi[j] = lo[j] = 0.f;
 
-  if constexpr (PRIOR) {
-    load_ring<N>(ring + (z0 % 3) * ROWS * N, x, xp, beta, g.img_off + (size_t)z0 * N2, r0);
-    if (z0 > 0) load_ring<N>(ring + ((z0 + 2) % 3) * ROWS * N, x, xp, beta, g.img_off + (size_t)(z0 - 1) * N2, r0);
-  }
-
-  for (int z = z0; z < z1; ++z) {
-    const size_t slice_base = g.img_off + (size_t)z * N2;
-    // the ring slot of slice z+1 is free once every thread has finished slice z-1
-    if constexpr (PRIOR) {
-      __syncthreads();
-      if (z + 1 < g.S) load_ring<N>(ring + ((z + 1) % 3) * ROWS * N, x, xp, beta, slice_base + N2, r0);
-      __syncthreads();
+  if constexpr (!PRIOR) {
+    // Apply: pass 3a wrote K (*) x to the output itself; only the partial sums remain
+    for (int z = z0; z < z1; ++z) {
+      float2 acc0 = f2(0.f), acc5 = f2(0.f);
+#pragma unroll
+      for (int t = 0; t < R; ++t) {
+        const size_t o = (size_t)z * N2 + (size_t)(r0 + t) * N + acol;
+        const float2 zd = __ldg(reinterpret_cast<const float2*>(kz + o));
+        const float2 xv = __ldg(reinterpret_cast<const float2*>(x + g.img_off + o));
+        acc0 = f2fma(xv, zd, acc0);
+        acc5 = f2fma(zd, zd, acc5);
+      }
+      two_sum_add(hi[0], lo[0], acc0.x + acc0.y);
+      two_sum_add(hi[5], lo[5], acc5.x + acc5.y);
     }
-    const float* kzr = kz + (size_t)z * N2 + (size_t)r0 * N;
-
-    // ---- per voxel: prior, gradient, update, partial sums.  A thread takes the voxels in
-    // columns c and c + N/2 of one block row as the two lanes of packed FP32 pairs (a warp
-    // covers 32 consecutive c of one row, so the row and slice tests are warp-uniform).
-    const float* sz[3] = {ring + ((z + 2) % 3) * ROWS * N, ring + (z % 3) * ROWS * N, ring + ((z + 1) % 3) * ROWS * N};
-    const bool zval0 = z > 0, zval2 = z + 1 < g.S;
-    float2 acc[kParts];
+  } else {
+    const PriorK pk = prior_k(pc);
+    PairW pw;
+    const float wcls[3] = {pc.wf * pc.inv_sig2, pc.we * pc.inv_sig2, pc.wc * pc.inv_sig2};
 #pragma unroll
-    for (int j = 0; j < kParts; ++j) acc[j] = f2(0.f);
-#pragma unroll 1
-    for (int i = threadIdx.x; i < RB * H; i += G3::THREADS) {
-      const int row = i / H, c = i - row * H;
-      const int grow = r0 + row;
-      const size_t ia = slice_base + (size_t)grow * N + c, ib = ia + H;
-      const float2 zd = make_float2(__ldg(kzr + row * N + c), __ldg(kzr + row * N + c + H));
-      if constexpr (!PRIOR) {
-        // Apply: pass 3a wrote K (*) x to the output itself; only the partial sums remain
-        const float2 xv = make_float2(__ldg(x + ia), __ldg(x + ib));
-        acc[0] = f2fma(xv, zd, acc[0]);
-        acc[5] = f2fma(zd, zd, acc[5]);
-      } else {
-        const float2 at = make_float2(__ldg(a.atg + ia), __ldg(a.atg + ib));
-        float2 xv = f2(0.f);
-        if constexpr (UPDATE) xv = make_float2(__ldg(x + ia), __ldg(x + ib));
-        const float* ry = sz[1] + (row + 1) * N;
-        const float2 yv = make_float2(ry[c], ry[c + H]);
-        // missing neighbours (free boundary) read the voxel itself: d = 0 adds nothing
-        const bool hasL = c > 0, hasR = c + 1 < H;  // column 0 (lane x), column N - 1 (lane y)
-        const int cl = hasL ? c - 1 : c, cr = hasR ? c + H + 1 : c + H;
-        float2 gp[3], ph[3];  // by neighbour class: face, edge, corner
+    for (int j = 0; j < 3; ++j) {
+      pw.wq[j] = f2(wcls[j] * pc.qp);
+      pw.wp[j] = f2(wcls[j] * pc.p);
+    }
+    const float2 lam = f2(pc.lam);
+    const bool okL = acol > 0, okR = acol + 2 < N;
+    float* ring = reinterpret_cast<float*>(sm);
+    constexpr int SLOT = 2 * GP::RING;  // y and its shifted copy
+    float* stg = ring + 2 * SLOT;
+    float2* cr = reinterpret_cast<float2*>(stg + 2 * GP::RING) + 32 * warp + lane;
+    float* edge = stg + 2 * GP::RING + R * GP::BC + warp * GP::NEDGE;
+    float2* fin_in = reinterpret_cast<float2*>(stg + 2 * GP::RING + R * GP::BC + GP::WPB * GP::NEDGE) + threadIdx.x;
+    // K (*) y, R*g and x_k of row t of slice zz at this thread's voxels, into fin_in
+    auto fetch = [&](int zz, int t) {
+      const size_t o = (size_t)zz * N2 + (size_t)(r0 + t) * N + acol;
+      float2* d = fin_in + 3 * t * GP::THREADS;
+      tc05::cp_async8(d, kz + o);
+      tc05::cp_async8(d + GP::THREADS, a.atg + g.img_off + o);
+      if constexpr (UPDATE) tc05::cp_async8(d + 2 * GP::THREADS, x + g.img_off + o);
+    };
+    float2 ph[3] = {f2(0.f), f2(0.f), f2(0.f)};
+    load_ring_p<N>(ring + (z0 & 1) * SLOT, x, xp, beta, g.img_off + (size_t)z0 * N2, r0, c0);
+    if (z0 > 0) {
+      load_ring_p<N>(ring + ((z0 - 1) & 1) * SLOT, x, xp, beta, g.img_off + (size_t)(z0 - 1) * N2, r0, c0);
+    } else {
 #pragma unroll
-        for (int j = 0; j < 3; ++j) gp[j] = ph[j] = f2(0.f);
+      for (int t = 0; t < R; ++t) cr[t * (GP::BC / 2)] = f2(0.f);
+    }
+    __syncthreads();
+    ring_shift<N>(ring + (z0 & 1) * SLOT);
+    if (z0 > 0) ring_shift<N>(ring + ((z0 - 1) & 1) * SLOT);
+    if (z0 + 1 < g.S) stage_issue<N>(stg, x, xp, g.img_off + (size_t)(z0 + 1) * N2, r0, c0);
 #pragma unroll
-        for (int dz = 0; dz < 3; ++dz) {
-          if ((dz == 0 && !zval0) || (dz == 2 && !zval2)) continue;
+    for (int t = 0; t < R; ++t) fetch(z0, t);
+    __syncthreads();
+    // boundary tests only where the warp's neighbourhoods leave the image
+    const bool rowe = !(r0 > 0 && r0 + R < N), cole = !(c0w > 0 && c0w + 64 < N);
+    if (z0 > 0) {
+      auto fin0 = [](int, float2, float2) {};
+      const float* s0 = ring + ((z0 - 1) & 1) * SLOT;
+      const float* s1 = ring + (z0 & 1) * SLOT;
+      if (rowe)
+        band_step<N, Q2, PHI, true, true, true>(s0, s1, true, r0, c0w, ia, okL, okR, cr, edge, pk, pw, ph, fin0);
+      else if (cole)
+        band_step<N, Q2, PHI, true, false, true>(s0, s1, true, r0, c0w, ia, okL, okR, cr, edge, pk, pw, ph, fin0);
+      else
+        band_step<N, Q2, PHI, true, false, false>(s0, s1, true, r0, c0w, ia, okL, okR, cr, edge, pk, pw, ph, fin0);
+    }
+    for (int z = z0; z < z1; ++z) {
+      // every thread has finished slice z - 1, so its ring slot takes slice z + 1 from the
+      // staging area; then the staging area takes slice z + 2 while slice z is worked on
+      tc05::cp_async_wait_all();
+      __syncthreads();
+      if (z + 1 < g.S) stage_to_ring<N>(ring + ((z + 1) & 1) * SLOT, stg, beta);
+      __syncthreads();
+      if (z + 1 < z1 && z + 2 < g.S) stage_issue<N>(stg, x, xp, g.img_off + (size_t)(z + 2) * N2, r0, c0);
+      float2 acc[kParts];
 #pragma unroll
-          for (int dy = 0; dy < 3; ++dy) {
-            if ((dy == 0 && grow == 0) || (dy == 2 && grow + 1 == N)) continue;
-            const float* rp = sz[dz] + (row + dy) * N;
-            const int cls = (dz != 1) + (dy != 1);  // class of the dx = -1, +1 neighbours
-            const bool fwd = dz > 1 || (dz == 1 && dy > 1);
-            const float2 nbL = make_float2(hasL ? rp[cl] : yv.x, rp[c + H - 1]);
-            const float2 nbR = make_float2(rp[c + 1], hasR ? rp[cr] : yv.y);
-            if (cls > 0) nbr2<Q2>(yv, make_float2(rp[c], rp[c + H]), pk, gp[cls - 1], ph[cls - 1], PHI && fwd);
-            nbr2<Q2>(yv, nbL, pk, gp[cls], ph[cls], PHI && fwd);
-            nbr2<Q2>(yv, nbR, pk, gp[cls], ph[cls], PHI && (fwd || cls == 0));
-          }
-        }
-        const float2 gpv = f2fma(wc, gp[2], f2fma(we, gp[1], f2mul(wf, gp[0])));
-        const float2 Gv = f2fma(lam, gpv, f2fma(at, f2(-1.f), zd));
+      for (int j = 0; j < kParts; ++j) acc[j] = f2(0.f);
+      const size_t img = g.img_off + (size_t)z * N2 + acol;
+      const bool more = z + 1 < z1;
+      auto fin = [&](int t, float2 gsum, float2 yv) {
+        const size_t ro = (size_t)(r0 + t) * N;
+        const float2* v = fin_in + 3 * t * GP::THREADS;
+        const float2 zd = v[0], at = v[GP::THREADS];
+        const float2 Gv = f2fma(lam, gsum, f2fma(at, f2(-1.f), zd));
         acc[0] = f2fma(yv, zd, acc[0]);
         acc[1] = f2fma(yv, at, acc[1]);
-        if constexpr (PHI) acc[2] = f2add(acc[2], f2fma(wc, ph[2], f2fma(we, ph[1], f2mul(wf, ph[0]))));
         acc[4] = f2fma(Gv, Gv, acc[4]);
         if constexpr (MODE == (int)Pass3Mode::Gradient) {
-          out[ia] = Gv.x;
-          out[ib] = Gv.y;
+          *reinterpret_cast<float2*>(out + img + ro) = Gv;
         } else if constexpr (UPDATE) {
+          const float2 xv = v[2 * GP::THREADS];
           const float2 xn = f2fma(f2(-invL), Gv, yv);
-          out[ia] = xn.x;
-          out[ib] = xn.y;
+          *reinterpret_cast<float2*>(out + img + ro) = xn;
           acc[3] = f2fma(Gv, f2fma(xv, f2(-1.f), xn), acc[3]);
         }
-      }
-    }
+        if (more) fetch(z + 1, t);  // this row's slots are free again
+      };
+      const float* s0 = ring + (z & 1) * SLOT;
+      const float* s1 = ring + ((z + 1) & 1) * SLOT;
+      if (rowe)
+        band_step<N, Q2, PHI, false, true, true>(s0, s1, z + 1 < g.S, r0, c0w, ia, okL, okR, cr, edge, pk, pw, ph, fin);
+      else if (cole)
+        band_step<N, Q2, PHI, false, false, true>(s0, s1, z + 1 < g.S, r0, c0w, ia, okL, okR, cr, edge, pk, pw, ph,
+                                                  fin);
+      else
+        band_step<N, Q2, PHI, false, false, false>(s0, s1, z + 1 < g.S, r0, c0w, ia, okL, okR, cr, edge, pk, pw, ph,
+                                                   fin);
+      if constexpr (PHI) {
 #pragma unroll
-    for (int j = 0; j < kParts; ++j) dacc[j] += (double)acc[j].x + (double)acc[j].y;
+        for (int j = 0; j < 3; ++j) {
+          acc[2] = f2fma(f2(wcls[j]), ph[j], acc[2]);
+          ph[j] = f2(0.f);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < kParts; ++j) two_sum_add(hi[j], lo[j], acc[j].x + acc[j].y);
+    }
   }
-  block_partials<G3::W>(dacc, red, partials + (size_t)(block_offset + blockIdx.x) * kParts);
+  block_partials_f<GP::WPB>(hi, lo, red, partials + (size_t)(block_offset + blockIdx.x) * kParts);
 }
 
 // ---------------------------------------------------------------- host launchers
@@ -680,9 +1041,9 @@ static int set_smem_limits() {
   }
 #define TMBIR_P3ATTR(M, Q)                                                                           \
   TMBIR_CUDA(cudaFuncSetAttribute(k_pass3<N, M, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                  (int)Geo3<N>::SM));
+                                  (int)GeoP<N>::SM));
   TMBIR_P3ATTR(0, true) TMBIR_P3ATTR(1, true) TMBIR_P3ATTR(2, true) TMBIR_P3ATTR(3, true) TMBIR_P3ATTR(4, true)
-  TMBIR_P3ATTR(1, false) TMBIR_P3ATTR(2, false) TMBIR_P3ATTR(3, false) TMBIR_P3ATTR(4, false)
+  TMBIR_P3ATTR(0, false) TMBIR_P3ATTR(1, false) TMBIR_P3ATTR(2, false) TMBIR_P3ATTR(3, false) TMBIR_P3ATTR(4, false)
 #undef TMBIR_P3ATTR
   done = true;
   return TMBIR_OK;
@@ -731,13 +1092,14 @@ static int pass2_n(const GroupDev& g, const IterState* st, bool bf16, cudaStream
 template <int N, int MODE>
 static int pass3_nm(const GroupDev& g, const StepArgs& a, const PriorC& pc, const float* kz, int phase,
                     double* partials, int off, cudaStream_t s) {
-  using Gm = Geo<N>;
-  const int zc = pass3_zc(g, Gm::NB);
-  const int blocks = Gm::NB * ((g.S + zc - 1) / zc);
+  using GP = GeoP<N>;
+  static_assert(GP::NB * GP::CB == pass3_row_blocks(N), "pass-3b block count");
+  const int zc = pass3_zc(g, GP::NB * GP::CB);
+  const int blocks = GP::NB * GP::CB * ((g.S + zc - 1) / zc);
   if (pc.q_is_2 || MODE == 0)
-    k_pass3<N, MODE, true><<<blocks, Geo3<N>::THREADS, Geo3<N>::SM, s>>>(g, a, pc, kz, phase, partials, off, zc);
+    k_pass3<N, MODE, true><<<blocks, GP::THREADS, GP::SM, s>>>(g, a, pc, kz, phase, partials, off, zc);
   else
-    k_pass3<N, MODE, false><<<blocks, Geo3<N>::THREADS, Geo3<N>::SM, s>>>(g, a, pc, kz, phase, partials, off, zc);
+    k_pass3<N, MODE, false><<<blocks, GP::THREADS, GP::SM, s>>>(g, a, pc, kz, phase, partials, off, zc);
   TMBIR_CHECK_LAUNCH();
   return TMBIR_OK;
 }
