@@ -107,6 +107,14 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
+def measured_sm_max_mhz():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["sm_max_mhz"])
+    except Exception:
+        return 2070.0
+
+
 def kernel_traffic(kernel, workload):
     """DRAM bytes per launch from the committed ncu summary, if it matches the current kernel source."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
@@ -407,7 +415,8 @@ def main():
         atg = torch.empty(S * N * N, dtype=torch.float32, device="cuda")
         x = torch.empty_like(atg)
     prm = tm.Params(**PRIOR, max_iter=iters, use_graph=not args.no_graph)
-    # pick pass 3's slices per block by timing (outside the timed region)
+    # pick pass 3b's slices per block and the spectrum chunk of passes 1-3a by timing (outside
+    # the timed region)
     ctx.build_operator(sino, atg)
     ctx.fbp(sino, x)
     tuned = ctx.autotune(x, atg, prm)
@@ -458,6 +467,24 @@ def main():
     alg_bytes = bpv * S * N * N
     achieved = alg_bytes / (pt[top] / iters * 1e-3) / 1e9
     peak, peak_kind = measured_peaks()
+    roof = {"kernel": names[top], "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "peak_source": peak_kind, "algorithmic_bytes_per_voxel": bpv,
+            "traffic": kernel_traffic(names[top], args.workload)}
+    if names[top] == "pass3b_prior_update":
+        # Pass 3b is bound by the special-function pipe, not HBM: each of the 13 neighbour pairs
+        # of a voxel costs log2, exp2 and a reciprocal (a fourth exp2 when q != 2), against
+        # SMs x 32 special-function results per clock x the maximum SM clock
+        sfu_per_voxel = 13 * (3 if PRIOR["q"] == 2.0 else 4)
+        n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+        sm_mhz = measured_sm_max_mhz()
+        sfu_peak = n_sm * 32 * sm_mhz * 1e6 / 1e9
+        sfu_achieved = sfu_per_voxel * S * N * N / (pt[top] / iters * 1e-3) / 1e9
+        roof.update({"bound": "alu", "achieved": sfu_achieved, "peak": sfu_peak, "unit": "Gop/s",
+                     "frac": sfu_achieved / sfu_peak,
+                     "peak_source": f"derived: {n_sm} SMs x 32 special-function ops/clk x {sm_mhz:.0f} MHz",
+                     "algorithmic_ops_per_voxel": sfu_per_voxel,
+                     "hbm": {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                             "peak_source": peak_kind}})
 
     # setup breakdown: R*g (FP64 NUFFT) + 1/2 g.g, and the FBP start, per call
     barrier()
@@ -512,17 +539,14 @@ def main():
                 "workload": args.workload, "slices": S, "N": N, "angles": na, "span": span, "iterations": iters,
                 "step": "build_operator_fbp (R*g and FBP overlapped) + reconstruct(graph)", "l2": "working set > L2 (no explicit flush)",
                 "parallelism": f"replicas{world}", "pass3_slices_per_block": tuned[0],
+                "spectrum_chunk_slices": ctx.spec_chunks[0],
             },
             "setup_ms": setup_ms,
             "iteration_phase": {
                 "voxel_updates_per_s": vox / (it_ms * 1e-3), "ms_per_iteration": it_ms / iters,
                 "ms_per_pass": dict(zip(names, [v / iters for v in pt])),
             },
-            "roofline": {
-                "kernel": names[top], "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "peak_source": peak_kind, "algorithmic_bytes_per_voxel": bpv,
-                "traffic": kernel_traffic(names[top], args.workload),
-            },
+            "roofline": roof,
             "e2e": {"value": world * vox * args.steps / (e2e_ms * 1e-3), "unit": "voxel-updates/s",
                     "h2d_bytes_per_step": sino.numel() * 4, "d2h_bytes_per_step": x.numel() * 4},
             "gpu_launches": launches,

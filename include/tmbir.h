@@ -232,15 +232,19 @@ int tmbir_downsample_sino(tmbir_ctx* ctx, const float* d_sino, int n_slices, int
 int tmbir_pass_times(tmbir_ctx* ctx, float* d_x, const float* d_atg, const tmbir_params* prm, int iters, double* h_ms);
 
 /*
- * Autotuner (no counterpart in the paper): times pass 3b (prior, gradient and update) of one
- * iteration on d_x / d_atg with every candidate number of slices a block marches through (1,
- * 2, 3, 4, 6, 8, 12, 16, 24, 32 up to the group's slice count, and the default rule) and keeps
- * the fastest per group;
- * h_zc (may be NULL) receives the choice per group.  Later contexts of this process with the
- * same image side and slice count start from the choice.  The transform tile shapes (rows per
- * block, threads per row) are fixed per image side at compile time.  d_x is not modified.
+ * Autotuner (no counterpart in the paper), per group on d_x / d_atg:
+ *  - the slices per spectrum chunk: passes 1, 2 and 3a can run chunk by chunk (a chunk's half
+ *    spectra may then stay in L2 between them); chunks of 4, 8 and 16 slices and the whole
+ *    group (the default) are timed over the whole group;
+ *  - the slices a pass-3b block marches through (1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64 up to
+ *    the slice count, and the default rule), timing pass 3b of one iteration.
+ * The fastest of each is kept; h_zc and h_sc (either may be NULL) receive the choices per
+ * group.  Later contexts of this process with the same image side and slice count start from
+ * the choices.  The transform tile shapes are fixed per image side at compile time.  d_x is
+ * not modified.
  */
-int tmbir_autotune(tmbir_ctx* ctx, const float* d_x, const float* d_atg, const tmbir_params* prm, int* h_zc);
+int tmbir_autotune(tmbir_ctx* ctx, const float* d_x, const float* d_atg, const tmbir_params* prm, int* h_zc,
+                   int* h_sc);
 
 /*
  * Checkpoint of a run (no counterpart in the paper): the fast-gradient state after
@@ -311,9 +315,11 @@ int tmbir_warm_start(tmbir_ctx* ctx, tmbir_cnn* net, const float* d_fbp, const f
  * has no counterpart; this entry point is for callers that cannot allocate device memory at the
  * time of the call (for example code running under a host application that owns the whole
  * device-memory budget, or a latency-critical loop where allocation is not allowed).
- *   - The array holds 8 Mi complex values (64 MiB) of spectra, summed over all groups as
- *     n_slices * (N+1) * N, and the partial sums of 65536 blocks.  Larger geometries are
- *     rejected with TMBIR_ERR_SHAPE; nothing is allocated on any path.
+ *   - The array holds 8 Mi complex values (64 MiB) of spectra, (N+1) * N per slice, and the
+ *     partial sums of 65536 blocks.  The groups run one after another in chunks of as many
+ *     slices as fit (at most the context's spectrum chunk); a geometry whose pass 3b needs
+ *     more than 65536 blocks is rejected with TMBIR_ERR_SHAPE; nothing is allocated on any
+ *     path.
  *   - Every device that loads the library holds the array until the process exits.
  *   - The first call on a device, with that device current, looks up the array's device
  *     address (cudaGetSymbolAddress) and caches it; make that first call before any stream

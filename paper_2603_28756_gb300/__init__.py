@@ -137,7 +137,7 @@ def load(path: str | None = None):
         "tmbir_state_size": [vp, ctypes.POINTER(sz)],
         "tmbir_state_export": [vp, vp],
         "tmbir_state_import": [vp, vp],
-        "tmbir_autotune": [vp, vp, vp, ctypes.POINTER(_Params), ctypes.POINTER(i)],
+        "tmbir_autotune": [vp, vp, vp, ctypes.POINTER(_Params), ctypes.POINTER(i), ctypes.POINTER(i)],
         "tmbir_build_operator_fbp": [vp, vp, vp, vp],
     }
     for name, args in sig.items():
@@ -400,12 +400,16 @@ class Context:
         return out
 
     def autotune(self, x, atg, params: Params):
-        """Pick the pass-3 slices per block for every group by timing them; returns the choices."""
+        """Pick, by timing, the pass-3b slices per block and the slices per spectrum chunk of every
+        group; returns the pass-3b choices (the chunk choices land in self.spec_chunks)."""
         zc = (ctypes.c_int * len(self.groups))()
+        sc = (ctypes.c_int * len(self.groups))()
         pr = params.c_struct()
         self._pre()
-        _check(_lib.tmbir_autotune(self._h, ctypes.c_void_p(_ptr(x)), ctypes.c_void_p(_ptr(atg)), ctypes.byref(pr), zc))
+        _check(_lib.tmbir_autotune(self._h, ctypes.c_void_p(_ptr(x)), ctypes.c_void_p(_ptr(atg)), ctypes.byref(pr), zc,
+                                   sc))
         self._post(x, atg)
+        self.spec_chunks = list(sc)
         return list(zc)
 
     def state_export(self, out=None):

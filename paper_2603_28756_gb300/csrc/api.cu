@@ -47,11 +47,18 @@ static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 // the contexts of this process (0: not tuned).
 static std::mutex g_tune_mu;
 static std::map<std::pair<int, int>, int> g_tuned_zc;
+// slices per spectrum chunk chosen by tmbir_autotune, keyed the same way
+static std::map<std::pair<int, int>, int> g_tuned_sc;
 
 static int tuned_zc(int N, int S) {
   std::lock_guard<std::mutex> lk(g_tune_mu);
   auto it = g_tuned_zc.find({N, S});
   return it == g_tuned_zc.end() ? 0 : it->second;
+}
+static int tuned_sc(int N, int S) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tuned_sc.find({N, S});
+  return it == g_tuned_sc.end() ? 0 : it->second;
 }
 
 // ---------------------------------------------------------------- small device kernels
@@ -324,6 +331,7 @@ int tmbir_set_workspace(tmbir_ctx* ctx, void* d_ws, size_t bytes) {
     d.S = g.n_slices;
     d.span = (float)g.span;
     d.zc = tuned_zc(d.N, d.S);
+    d.sc = tuned_sc(d.N, d.S);
     d.chat = reinterpret_cast<float*>(ws + c.off_chat[i]);
     d.twN = reinterpret_cast<float2*>(ws + c.off_twN[i]);
     d.twM = reinterpret_cast<float2*>(ws + c.off_twM[i]);
@@ -489,9 +497,8 @@ static int enqueue_passes(Ctx& c, float* d_x, const float* d_atg, const PriorC& 
   int off = 0;
   for (size_t i = 0; i < c.gdev.size(); ++i) {
     const GroupDev& g = c.gdev[i];
-    if (int e = launch_pass1(g, a, c.stream, bf16)) return e;
-    if (int e = launch_pass2(g, c.state, c.stream, bf16)) return e;
-    if (int e = launch_pass3(g, a, Pass3Mode::Iterate, pc, c.partials, off, c.stream, bf16)) return e;
+    if (int e = launch_convolution(g, a, Pass3Mode::Iterate, pc, c.stream, bf16)) return e;
+    if (int e = launch_pass3(g, a, Pass3Mode::Iterate, pc, c.partials, off, c.stream, bf16, 2)) return e;
     off += blocks_pass3(g);
   }
   *nblocks = off;
@@ -518,7 +525,8 @@ static int enqueue_trip(Ctx& c, float* d_x, const float* d_atg, const PriorC& pc
                         cudaGraphConditionalHandle cond, int use_cond) {
   int nb = 0;
   if (int e = enqueue_passes(c, d_x, d_atg, pc, bf16, &nb)) return e;
-  const int trip_launches = 4 * (int)c.gdev.size() + 1;
+  int trip_launches = 1;
+  for (const GroupDev& g : c.gdev) trip_launches += conv_launches(g) + 1;
   return launch_finalize(c.state, c.partials, nb, c.log, c.stream, cond, use_cond, trip_launches);
 }
 
@@ -666,9 +674,8 @@ static int run_explicit(Ctx& c, const StepArgs& a, Pass3Mode m, const PriorC& pc
   int off = 0;
   for (size_t i = 0; i < c.gdev.size(); ++i) {
     const GroupDev& g = c.gdev[i];
-    if (int e = launch_pass1(g, a, c.stream)) return e;
-    if (int e = launch_pass2(g, nullptr, c.stream)) return e;
-    if (int e = launch_pass3(g, a, m, pc, c.partials, off, c.stream)) return e;
+    if (int e = launch_convolution(g, a, m, pc, c.stream)) return e;
+    if (int e = launch_pass3(g, a, m, pc, c.partials, off, c.stream, false, 2)) return e;
     off += blocks_pass3(g);
   }
   if (h_parts) {
@@ -823,39 +830,48 @@ int tmbir_pass_times(tmbir_ctx* ctx, float* d_x, const float* d_atg, const tmbir
   a.xb[1] = c.xbuf[0];
   a.xb[2] = c.xbuf[1];
   a.st = c.state;
-  cudaEvent_t ev[6];
+  // events between consecutive launches: passes 1, 2, 3a of every spectrum chunk, then 3b
+  int max_chunks = 1;
+  for (const GroupDev& g : c.gdev) max_chunks = std::max(max_chunks, (g.S + spec_chunk(g) - 1) / spec_chunk(g));
+  std::vector<cudaEvent_t> ev(3 * max_chunks + 2);
   for (auto& e : ev) TMBIR_CUDA(cudaEventCreate(&e));
+  auto span_ms = [&](int a0, int a1) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ev[a0], ev[a1]);
+    return (double)ms;
+  };
   double acc[5] = {0, 0, 0, 0, 0};
   int rc = TMBIR_OK;
   for (int k = 0; k < iters && rc == TMBIR_OK; ++k) {
     int off = 0;
     for (int i = 0; i < ng && rc == TMBIR_OK; ++i) {
       const GroupDev& g = c.gdev[i];
+      const int sc = spec_chunk(g), nch = (g.S + sc - 1) / sc;
       cudaEventRecord(ev[0], s);
-      if ((rc = launch_pass1(g, a, s, bf16))) break;
-      cudaEventRecord(ev[1], s);
-      if ((rc = launch_pass2(g, c.state, s, bf16))) break;
-      cudaEventRecord(ev[2], s);
-      if ((rc = launch_pass3(g, a, Pass3Mode::Iterate, pc, c.partials, off, s, bf16, 1))) break;
-      cudaEventRecord(ev[3], s);
-      if ((rc = launch_pass3(g, a, Pass3Mode::Iterate, pc, c.partials, off, s, bf16, 2))) break;
-      cudaEventRecord(ev[4], s);
-      cudaEventSynchronize(ev[4]);
-      for (int j = 0; j < 4; ++j) {
-        float ms;
-        cudaEventElapsedTime(&ms, ev[j], ev[j + 1]);
-        acc[j] += ms;
+      for (int ch = 0; ch < nch && rc == TMBIR_OK; ++ch) {
+        const GroupDev v = chunk_view(g, ch * sc, std::min(sc, g.S - ch * sc));
+        if ((rc = launch_pass1(v, a, s, bf16))) break;
+        cudaEventRecord(ev[3 * ch + 1], s);
+        if ((rc = launch_pass2(v, c.state, s, bf16))) break;
+        cudaEventRecord(ev[3 * ch + 2], s);
+        if ((rc = launch_pass3(v, a, Pass3Mode::Iterate, pc, nullptr, 0, s, bf16, 1))) break;
+        cudaEventRecord(ev[3 * ch + 3], s);
       }
+      if (rc) break;
+      if ((rc = launch_pass3(g, a, Pass3Mode::Iterate, pc, c.partials, off, s, bf16, 2))) break;
+      cudaEventRecord(ev[3 * nch + 1], s);
+      cudaEventSynchronize(ev[3 * nch + 1]);
+      for (int ch = 0; ch < nch; ++ch)
+        for (int j = 0; j < 3; ++j) acc[j] += span_ms(3 * ch + j, 3 * ch + j + 1);
+      acc[3] += span_ms(3 * nch, 3 * nch + 1);
       off += blocks_pass3(g);
     }
     if (rc) break;
-    cudaEventRecord(ev[4], s);
+    cudaEventRecord(ev[0], s);
     rc = launch_finalize(c.state, c.partials, off, c.log, s);
-    cudaEventRecord(ev[5], s);
-    cudaEventSynchronize(ev[5]);
-    float ms;
-    cudaEventElapsedTime(&ms, ev[4], ev[5]);
-    acc[4] += ms;
+    cudaEventRecord(ev[1], s);
+    cudaEventSynchronize(ev[1]);
+    acc[4] += span_ms(0, 1);
   }
   for (auto& e : ev) cudaEventDestroy(e);
   if (rc) return rc;
@@ -884,7 +900,8 @@ int tmbir_launch_count(const tmbir_ctx* ctx, long long* h_count) {
 
 // ---------------------------------------------------------------- autotuning
 
-int tmbir_autotune(tmbir_ctx* ctx, const float* d_x, const float* d_atg, const tmbir_params* prm, int* h_zc) {
+int tmbir_autotune(tmbir_ctx* ctx, const float* d_x, const float* d_atg, const tmbir_params* prm, int* h_zc,
+                   int* h_sc) {
   TMBIR_TRACE("tmbir_autotune");
   if (int e = require_ready(ctx, true)) return e;
   if (int e = check_params(prm)) return e;
@@ -915,9 +932,40 @@ int tmbir_autotune(tmbir_ctx* ctx, const float* d_x, const float* d_atg, const t
   int rc = TMBIR_OK;
   for (int i = 0; i < ng && rc == TMBIR_OK; ++i) {
     GroupDev& g = c.gdev[i];
-    if ((rc = launch_pass1(g, a, s)) || (rc = launch_pass2(g, c.state, s)) ||
-        (rc = launch_pass3(g, a, Pass3Mode::Iterate, pc, c.partials, 0, s, false, 1)))
-      break;
+    // slices per spectrum chunk: passes 1, 2, 3a of the whole group with every candidate
+    {
+      std::vector<int> sc_c;
+      for (int z : {4, 8, 16})
+        if (z < g.S) sc_c.push_back(z);
+      const int sc_d = g.S;  // one chunk
+      sc_c.push_back(sc_d);
+      float best = 1e30f;
+      int best_sc = sc_d;
+      for (int z : sc_c) {
+        g.sc = z;
+        float ms = 0.f;
+        for (int rep = 0; rep < 3 && rc == TMBIR_OK; ++rep) {
+          if (rep == 1) cudaEventRecord(e0, s);
+          rc = launch_convolution(g, a, Pass3Mode::Iterate, pc, s);
+        }
+        if (rc) break;
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+          rc = set_error(TMBIR_ERR_CUDA, "autotune: event timing failed");
+          break;
+        }
+        if (ms < best) {
+          best = ms;
+          best_sc = z;
+        }
+      }
+      if (rc) break;
+      g.sc = best_sc;
+      if (h_sc) h_sc[i] = best_sc;
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      g_tuned_sc[{g.N, g.S}] = best_sc;
+    }
+    if ((rc = launch_convolution(g, a, Pass3Mode::Iterate, pc, s))) break;
     std::vector<int> cands;
     for (int z : {1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64})
       if (z <= g.S) cands.push_back(z);

@@ -81,7 +81,14 @@ struct GroupDev {
   double* csr_w;       // [nnz] kernel weight
   float* kz;           // [S][N][N] K (*) y between passes 3a and 3b
   int zc;              // slices each pass-3 block marches through (0: the default rule)
+  int sc;              // slices per spectrum chunk of passes 1, 2, 3a (0: the default rule)
 };
+
+// Passes 1, 2 and 3a may run in chunks of slices (a chunk's half spectra can then stay in L2
+// between the three passes).  Measured on GB300 at 64 x 1024^2 the whole group in one chunk is
+// fastest (the shorter launches lose more to launch gaps and partial last waves than L2 reuse
+// saves), so that is the default; tmbir_autotune tries chunks of 4, 8 and 16 slices too.
+inline int spec_chunk(const GroupDev& g) { return g.sc > 0 && g.sc < g.S ? g.sc : g.S; }
 
 constexpr int kSpreadW = 10;       // kernel width of the R*g / FBP spreading (error ~1e-9)
 constexpr int kBackprojBatch = 8;  // slices per back-projection batch
@@ -179,6 +186,13 @@ int launch_pass2(const GroupDev& g, const IterState* st, cudaStream_t s, bool bf
 int launch_pass3(const GroupDev& g, const StepArgs& a, Pass3Mode mode, const PriorC& pc, double* partials,
                  int block_offset, cudaStream_t s, bool bf16 = false, int part = 3);
 int blocks_pass3(const GroupDev& g);
+// slices [c0, c0 + n) of a group as a group of their own (same spectrum buffer)
+GroupDev chunk_view(const GroupDev& g, int c0, int n);
+// passes 1, 2, 3a of a whole group, chunk by chunk (K (*) y into g.kz, or into the output in
+// Apply mode); conv_launches: the kernels that enqueues
+int launch_convolution(const GroupDev& g, const StepArgs& a, Pass3Mode mode, const PriorC& pc, cudaStream_t s,
+                       bool bf16 = false);
+int conv_launches(const GroupDev& g);
 // Pass-3b blocks per slice chunk: bands of 4 rows times column blocks of up to 512 columns
 // (eight warps of 64 columns).
 constexpr int pass3_row_blocks(int N) { return (N / 4) * (N / (64 * (N / 64 < 8 ? N / 64 : 8))); }

@@ -791,9 +791,8 @@ int power_iteration(Ctx& c, int gi, int steps) {
     a.beta = 0.f;
     a.out = w;
     a.st = nullptr;
-    if (int e = launch_pass1(g, a, s)) return e;
-    if (int e = launch_pass2(g, nullptr, s)) return e;
-    if (int e = launch_pass3(g, a, Pass3Mode::Apply, pc, c.partials, 0, s)) return e;
+    if (int e = launch_convolution(g, a, Pass3Mode::Apply, pc, s)) return e;
+    if (int e = launch_pass3(g, a, Pass3Mode::Apply, pc, c.partials, 0, s, false, 2)) return e;
     if (int e = launch_sum_partials(c.partials, blocks_pass3(g), c.dscal, s)) return e;
     k_normalize<<<256, 256, 0, s>>>(w, v, n, c.dscal, g.lam_max);
     TMBIR_CHECK_LAUNCH();

@@ -14,6 +14,7 @@
 namespace tmbir {
 
 // 8 Mi complex floats (64 MiB) of half spectra: for example 7 slices of 1024^2, or 31 of 512^2
+// at once; the passes run in chunks of slices that fit
 constexpr size_t kStaticSpecElems = (size_t)8 << 20;
 // partial sums of up to 65536 reducing blocks
 constexpr size_t kStaticPartElems = (size_t)65536 * kParts;
@@ -63,17 +64,16 @@ extern "C" int tmbir_normal_apply_static(tmbir_ctx* ctx, const float* d_x, float
   if (!c.operator_built) return set_error(TMBIR_ERR_STATE, "normal_apply_static: operator not built");
   if (!d_x || !d_z || ((uintptr_t)d_x & 15u) || ((uintptr_t)d_z & 15u) || d_x == d_z)
     return set_error(TMBIR_ERR_ARG, "normal_apply_static: bad buffers");
-  // every group's spectra side by side in the static array; refuse what does not fit
-  size_t need = 0;
+  // the groups one after another, each in spectrum chunks that fit the static array
   int blocks = 0;
   for (const GroupDev& g : c.gdev) {
-    need += (size_t)g.S * (g.N + 1) * g.N;
+    const size_t per = (size_t)(g.N + 1) * g.N;
+    if (per > kStaticSpecElems)
+      return set_error(TMBIR_ERR_SHAPE, "normal_apply_static: one slice needs " + std::to_string(per) +
+                                            " complex scratch values, the static array holds " +
+                                            std::to_string(kStaticSpecElems));
     blocks += blocks_pass3(g);
   }
-  if (need > kStaticSpecElems)
-    return set_error(TMBIR_ERR_SHAPE, "normal_apply_static: the geometry needs " + std::to_string(need) +
-                                          " complex scratch values, the static array holds " +
-                                          std::to_string(kStaticSpecElems));
   if ((size_t)blocks * kParts > kStaticPartElems)
     return set_error(TMBIR_ERR_SHAPE, "normal_apply_static: too many reducing blocks for the static array");
   float2* spec = nullptr;
@@ -85,15 +85,13 @@ extern "C" int tmbir_normal_apply_static(tmbir_ctx* ctx, const float* d_x, float
   a.beta = 0.f;
   a.out = d_z;
   PriorC pc{};
-  size_t off = 0;
   int boff = 0;
   for (const GroupDev& g0 : c.gdev) {
     GroupDev g = g0;
-    g.spec = spec + off;
-    if (int e = launch_pass1(g, a, c.stream)) return e;
-    if (int e = launch_pass2(g, nullptr, c.stream)) return e;
-    if (int e = launch_pass3(g, a, Pass3Mode::Apply, pc, parts, boff, c.stream)) return e;
-    off += (size_t)g.S * (g.N + 1) * g.N;
+    g.spec = spec;
+    g.sc = std::min(spec_chunk(g0), (int)(kStaticSpecElems / ((size_t)(g.N + 1) * g.N)));
+    if (int e = launch_convolution(g, a, Pass3Mode::Apply, pc, c.stream)) return e;
+    if (int e = launch_pass3(g, a, Pass3Mode::Apply, pc, parts, boff, c.stream, false, 2)) return e;
     boff += blocks_pass3(g);
   }
   return TMBIR_OK;

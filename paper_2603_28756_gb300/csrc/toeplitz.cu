@@ -135,6 +135,31 @@ int launch_pass3(const GroupDev& g, const StepArgs& a, Pass3Mode m, const PriorC
                  cudaStream_t s, bool bf16, int part) {
   TMBIR_DISPATCH_N(g.N, pass3_, g, a, m, pc, partials, off, bf16, part, s);
 }
+GroupDev chunk_view(const GroupDev& g, int c0, int n) {
+  GroupDev v = g;
+  const size_t off = (size_t)c0 * g.N * g.N;
+  v.S = n;
+  v.slice0 = g.slice0 + c0;
+  v.img_off = g.img_off + off;
+  if (g.kz) v.kz = g.kz + off;
+  return v;
+}
+int launch_convolution(const GroupDev& g, const StepArgs& a, Pass3Mode m, const PriorC& pc, cudaStream_t s,
+                       bool bf16) {
+  const int sc = spec_chunk(g);
+  for (int c0 = 0; c0 < g.S; c0 += sc) {
+    const GroupDev v = chunk_view(g, c0, g.S - c0 < sc ? g.S - c0 : sc);
+    if (int e = launch_pass1(v, a, s, bf16)) return e;
+    if (int e = launch_pass2(v, a.st, s, bf16)) return e;
+    if (int e = launch_pass3(v, a, m, pc, nullptr, 0, s, bf16, 1)) return e;
+  }
+  return TMBIR_OK;
+}
+int conv_launches(const GroupDev& g) {
+  const int sc = spec_chunk(g);
+  return 3 * ((g.S + sc - 1) / sc);
+}
+
 int blocks_pass3(const GroupDev& g) {
   const int nb = pass3_row_blocks(g.N);
   const int zc = pass3_zc(g, nb);
