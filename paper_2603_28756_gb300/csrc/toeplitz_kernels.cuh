@@ -321,9 +321,19 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) k_pass3a(GroupDev g, const It
   {
     using IO = SpecIO<BF>;
     const typename IO::T* sp = reinterpret_cast<const typename IO::T*>(g.spec) + (size_t)s * (N + 1) * N + r0;
-    for (int e = threadIdx.x; e < (N + 1) * RB; e += Gm::THREADS) {
-      const int vv = e / RB, rr = e - vv * RB;
-      tb[rr * LD + vv] = IO::ld(sp, (size_t)vv * N + rr);
+    if constexpr (!BF) {
+      // RB-row segments of the column-major spectrum, gathered by asynchronous 8-byte copies so
+      // that every thread has all of its loads in flight at once
+      for (int e = threadIdx.x; e < (N + 1) * RB; e += Gm::THREADS) {
+        const int vv = e / RB, rr = e - vv * RB;
+        tc05::cp_async8(&tb[rr * LD + vv], sp + (size_t)vv * N + rr);
+      }
+      tc05::cp_async_wait_all();
+    } else {
+      for (int e = threadIdx.x; e < (N + 1) * RB; e += Gm::THREADS) {
+        const int vv = e / RB, rr = e - vv * RB;
+        tb[rr * LD + vv] = IO::ld(sp, (size_t)vv * N + rr);
+      }
     }
   }
   __syncthreads();
