@@ -52,11 +52,11 @@ __device__ __forceinline__ bool skip_iter(const IterState* st) {
 }
 
 // ---------------------------------------------------------------- launch geometry
-template <int N>
+template <int N, int Wp = 4>
 struct Geo {
   using F = typename FFTShape<N>::type;
   static constexpr int T = F::T, P = F::P, G = 32 / T;
-  static constexpr int W = 4;           // warps per block
+  static constexpr int W = Wp;          // warps per block
   static constexpr int THREADS = 32 * W;
   static constexpr int RB = W * G;      // rows per block in passes 1 and 3
   static constexpr int NB = N / RB;     // row blocks per slice
@@ -69,6 +69,30 @@ struct Geo {
   static constexpr size_t SM1 = cmax(SM_FFT, SM_TB);
   static constexpr size_t SM2 = SM_FFT;
 };
+
+// Launch shapes of pass 3a and pass 2 at N = 1024, chosen by measurement on GB300 (64 slices,
+// 256 angles; ms per launch):
+//   pass 3a: eight warps per block gather 8-row (64-byte) segments of the column-major
+//            spectrum instead of 4-row (32-byte) ones; with at most 128 registers (two blocks
+//            per SM) 0.211 ms against 0.262 with four warps (0.252 with eight warps at the
+//            compiler's register choice, 0.278 at three blocks per SM).  Eight warps do not
+//            help pass 1 (0.234 against 0.230), which keeps four.
+//   pass 2:  at most 170 registers (three blocks per SM), 0.401 ms against 0.407 (128
+//            registers: 0.588, spills).
+// The other image sides keep four warps and the compiler's register choice.
+#if defined(TMBIR_N) && TMBIR_N == 1024
+#define TMBIR_P3A_BOUNDS(T) __launch_bounds__(T, 2)
+#define TMBIR_P2_BOUNDS(T) __launch_bounds__(T, 3)
+#else
+#define TMBIR_P3A_BOUNDS(T) __launch_bounds__(T)
+#define TMBIR_P2_BOUNDS(T) __launch_bounds__(T)
+#endif
+template <int N>
+constexpr int pass3a_warps() {
+  return N == 1024 ? 8 : 4;
+}
+template <int N>
+using Geo3a = Geo<N, pass3a_warps<N>()>;
 
 // ---------------------------------------------------------------- special-function unit helpers
 __device__ __forceinline__ float ex2a(float x) {
@@ -183,8 +207,9 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) k_pass1(GroupDev g, StepArgs 
   if (a.st) {
     if (skip_iter<BF>(a.st)) return;
     int cur = a.st->cur;
-    x = a.xb[cur];
-    xp = a.xb[(cur + 2) % 3];
+    // selects rather than an indexed parameter array, which would be copied to local memory
+    x = cur == 0 ? a.xb[0] : (cur == 1 ? a.xb[1] : a.xb[2]);
+    xp = cur == 0 ? a.xb[2] : (cur == 1 ? a.xb[0] : a.xb[1]);
     beta = (float)a.st->beta;
   } else {
     x = a.x;
@@ -247,7 +272,7 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) k_pass1(GroupDev g, StepArgs 
 
 // ---------------------------------------------------------------- pass 2: columns
 template <int N, bool BF>
-__global__ void __launch_bounds__(Geo<N>::THREADS) k_pass2(GroupDev g, const IterState* st) {
+__global__ void TMBIR_P2_BOUNDS(Geo<N>::THREADS) k_pass2(GroupDev g, const IterState* st) {
   using Gm = Geo<N>;
   using F = typename Gm::F;
   constexpr int T = Gm::T, P = Gm::P, G = Gm::G;
@@ -307,8 +332,8 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) k_pass2(GroupDev g, const Ite
 // Inverse packed real row transform of every row (one row group per warp, RB rows per block,
 // the layout of pass 1), crop to the first N columns: K (*) y written row-major as FP32.
 template <int N, bool BF>
-__global__ void __launch_bounds__(Geo<N>::THREADS) k_pass3a(GroupDev g, const IterState* st, float* kz) {
-  using Gm = Geo<N>;
+__global__ void TMBIR_P3A_BOUNDS(Geo3a<N>::THREADS) k_pass3a(GroupDev g, const IterState* st, float* kz) {
+  using Gm = Geo3a<N>;
   using F = typename Gm::F;
   constexpr int T = Gm::T, P = Gm::P, G = Gm::G, RB = Gm::RB, LD = Gm::LD;
   extern __shared__ float2 sm[];
@@ -382,8 +407,9 @@ __global__ void __launch_bounds__(256) k_pass1_b(GroupDev g, StepArgs a) {
   if (a.st) {
     if (skip_iter<BF>(a.st)) return;
     const int cur = a.st->cur;
-    x = a.xb[cur];
-    xp = a.xb[(cur + 2) % 3];
+    // selects rather than an indexed parameter array, which would be copied to local memory
+    x = cur == 0 ? a.xb[0] : (cur == 1 ? a.xb[1] : a.xb[2]);
+    xp = cur == 0 ? a.xb[2] : (cur == 1 ? a.xb[0] : a.xb[1]);
     beta = (float)a.st->beta;
   } else {
     x = a.x;
@@ -1031,6 +1057,7 @@ __global__ void __launch_bounds__(GeoP<N>::THREADS, 2)
 template <int N>
 static int set_smem_limits() {
   using Gm = Geo<N>;
+  using Gr = Geo3a<N>;
   static bool done = false;
   if (done) return TMBIR_OK;
   if constexpr (is_block_fft_size<N>()) {
@@ -1046,8 +1073,8 @@ static int set_smem_limits() {
     TMBIR_CUDA(cudaFuncSetAttribute(k_pass1<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Gm::SM1));
     TMBIR_CUDA(cudaFuncSetAttribute(k_pass2<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Gm::SM2));
     TMBIR_CUDA(cudaFuncSetAttribute(k_pass2<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Gm::SM2));
-    TMBIR_CUDA(cudaFuncSetAttribute(k_pass3a<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Gm::SM1));
-    TMBIR_CUDA(cudaFuncSetAttribute(k_pass3a<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Gm::SM1));
+    TMBIR_CUDA(cudaFuncSetAttribute(k_pass3a<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Gr::SM1));
+    TMBIR_CUDA(cudaFuncSetAttribute(k_pass3a<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Gr::SM1));
   }
 #define TMBIR_P3ATTR(M, Q)                                                                           \
   TMBIR_CUDA(cudaFuncSetAttribute(k_pass3<N, M, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
@@ -1117,7 +1144,7 @@ static int pass3_nm(const GroupDev& g, const StepArgs& a, const PriorC& pc, cons
 template <int N>
 static int pass3_n(const GroupDev& g, const StepArgs& a, Pass3Mode m, const PriorC& pc, double* partials, int off,
                    bool bf16, int part, cudaStream_t s) {
-  using Gm = Geo<N>;
+  using Gm = Geo3a<N>;
   if (int e = set_smem_limits<N>()) return e;
   if (bf16 && m != Pass3Mode::Iterate) return set_error(TMBIR_ERR_ARG, "BF16 spectra are an iteration option only");
   // Apply writes K (*) x straight into the output; every other mode into the group's buffer
