@@ -48,11 +48,33 @@ def dist_env():
     return rank, world, local
 
 
+def rank_seed(rank):
+    """Phantom seed of a rank: every rank reconstructs its own independent batch (weak scaling,
+    no collective on the data path)."""
+    return 1002 + 17 * rank
+
+
+def max_over_ranks(ms, world, device):
+    """The slowest rank's time: each rank passes its own and every rank gets the maximum."""
+    if world <= 1:
+        return ms
+    import torch
+
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, steps, world, ms):
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return world * units_per_rank * steps / (ms * 1e-3)
+
+
 def make_problem(name, rank):
     import synth
 
     S, N, na, span, iters, ne = WORKLOADS[name]
-    p = synth.volume(S=S, N=N, n_angles=na, n_ellipsoids=ne, span=span, seed=1002 + 17 * rank)
+    p = synth.volume(S=S, N=N, n_angles=na, n_ellipsoids=ne, span=span, seed=rank_seed(rank))
     return p, iters
 
 
@@ -343,11 +365,7 @@ def time_to_gap(tm, ctx, stream, sino, atg, x, barrier, world, wl):
             st = run()
             e1.record(stream)
             barrier()
-        ms = e0.elapsed_time(e1)
-        if world > 1:
-            t = torch.tensor([ms], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(e0.elapsed_time(e1), world, "cuda")
         out["forms"][name] = {"ms": ms, "finest_iterations": st.iterations, "gap_reached": st.gap, "form": desc}
         if hasattr(st, "used_cnn"):
             out["forms"][name]["used_cnn"] = st.used_cnn
@@ -445,13 +463,9 @@ def main():
     barrier()
     clk = clocks.stop()
     launches = ctx.launch_count() - n0
-    ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1), world, "cuda")
     vox = S * N * N * iters
-    value = world * vox * args.steps / (ms * 1e-3)
+    value = job_rate(vox, args.steps, world, ms)
 
     # one reconstruction's stats (outside the timed region): convergence sanity
     st = ctx.reconstruct(x, atg, prm)
@@ -512,11 +526,7 @@ def main():
             h_x.copy_(x, non_blocking=True)
     f1.record(stream)
     barrier()
-    e2e_ms = f0.elapsed_time(f1)
-    if world > 1:
-        t = torch.tensor([e2e_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(f0.elapsed_time(f1), world, "cuda")
 
     gap_info = None if args.no_gap else time_to_gap(tm, ctx, stream, sino, atg, x, barrier, world,
                                                     (S, N, prob.theta, span))
@@ -547,7 +557,7 @@ def main():
                 "ms_per_pass": dict(zip(names, [v / iters for v in pt])),
             },
             "roofline": roof,
-            "e2e": {"value": world * vox * args.steps / (e2e_ms * 1e-3), "unit": "voxel-updates/s",
+            "e2e": {"value": job_rate(vox, args.steps, world, e2e_ms), "unit": "voxel-updates/s",
                     "h2d_bytes_per_step": sino.numel() * 4, "d2h_bytes_per_step": x.numel() * 4},
             "gpu_launches": launches,
             "time_to_gap": gap_info,
