@@ -21,7 +21,9 @@ def main():
     seeds = [None] * world
     dist.all_gather_object(seeds, bench.rank_seed(rank))
     rate = bench.job_rate(1000, 2, world, slowest)
-    print(json.dumps({"rank": rank, "world": world, "max_ms": slowest, "seeds": seeds, "rate": rate}), flush=True)
+    # one file per rank: the ranks' standard outputs share a pipe and can interleave
+    with open(os.path.join(sys.argv[1], f"rank{rank}.json"), "w") as f:
+        json.dump({"rank": rank, "world": world, "max_ms": slowest, "seeds": seeds, "rate": rate}, f)
     dist.barrier()
     dist.destroy_process_group()
 

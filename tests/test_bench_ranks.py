@@ -25,10 +25,10 @@ def _torchrun(args, timeout):
     return subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True, timeout=timeout)
 
 
-def test_two_ranks_time_the_slowest_and_count_every_rank():
-    r = _torchrun([os.path.join(ROOT, "tests", "ranks_worker.py")], 300)
+def test_two_ranks_time_the_slowest_and_count_every_rank(tmp_path):
+    r = _torchrun([os.path.join(ROOT, "tests", "ranks_worker.py"), str(tmp_path)], 300)
     assert r.returncode == 0, r.stderr[-2000:]
-    lines = [json.loads(l) for l in r.stdout.splitlines() if l.startswith("{")]
+    lines = [json.loads((tmp_path / f"rank{k}.json").read_text()) for k in range(2)]
     assert sorted(d["rank"] for d in lines) == [0, 1]
     for d in lines:
         assert d["world"] == 2
