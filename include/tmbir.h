@@ -267,7 +267,7 @@ int tmbir_state_import(tmbir_ctx* ctx, const void* d_state);
 int tmbir_launch_count(const tmbir_ctx* ctx, long long* h_count);
 
 /*
- * Learned warm start (not in the paper; the refined start of the task configuration): a
+ * Learned warm start (not in the paper; an addition that refines the FBP start): a
  * four-layer 3x3 convolutional network, channels 1 -> 32 -> 32 -> 32 -> 1, zero padding, a bias
  * per output channel, ReLU after the first three layers.  FP32 master weights, BF16 activations,
  * FP32 accumulation; the 32 -> 32 layers (forward and data gradient) run as implicit GEMMs on

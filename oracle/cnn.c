@@ -3,9 +3,8 @@
  *
  * TEST INFRASTRUCTURE ONLY (see radon.c).
  *
- * The paper has no learned component; the refiner is specified only by the task
- * configuration: four 3x3 convolutions with 32 channels refining the filtered
- * back-projection.  Reading used here: channels 1 -> 32 -> 32 -> 32 -> 1, zero padding
+ * The paper has no learned component; this refiner of the filtered back-projection
+ * start is an addition: four 3x3 convolutions with 32 channels.  Reading used here: channels 1 -> 32 -> 32 -> 32 -> 1, zero padding
  * of one pixel, a bias per output channel, ReLU after the first three layers, none
  * after the last.  The network maps a normalised FBP image to a correction (the caller
  * forms x' = x + s * net(x / s)).
