@@ -407,6 +407,12 @@ def test_argument_errors():
     with pytest.raises(tm.TmbirError) as e:
         tm.Context([tm.Group(N=64, angles=[0.0], n_det=128)])
     assert e.value.code == -2
+    # empty and degenerate geometries are refused, not run
+    for bad in ([], [tm.Group(N=64, angles=[])], [tm.Group(N=64, angles=[0.0, 1.0], n_slices=0)],
+                [tm.Group(N=64, angles=[0.0, float("nan")])], [tm.Group(N=64, angles=[0.0], span=0.0)]):
+        with pytest.raises(tm.TmbirError) as e:
+            tm.Context(bad)
+        assert e.value.code == -1
     ctx = tm.Context([tm.Group(N=64, angles=[0.0, 1.0])])
     x = torch.zeros(64 * 64 + 1, device="cuda")
     with pytest.raises(tm.TmbirError) as e:
