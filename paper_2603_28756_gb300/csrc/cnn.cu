@@ -1,11 +1,11 @@
 // Learned warm start: a four-layer 3x3 convolutional refiner (1 -> 32 -> 32 -> 32 -> 1, ReLU
 // after the first three layers, zero padding) applied to the normalised FBP start, with its
-// own training kernels.  The paper has no learned component; the network shape comes from the
-// task configuration.
+// own training kernels.  The paper has no learned component; this refiner is an addition.
 //
 // Precision: FP32 master weights, BF16 activations and weight copies, FP32 accumulation.
-// The two 32 -> 32 layers are implicit GEMMs on the tensor cores (mma.sync m16n8k16, BF16 in,
-// FP32 out): M = pixels of an 8 x 32 tile, N = 32 output channels, K = 9 taps x 32 channels.
+// The two 32 -> 32 layers are implicit GEMMs on the 5th-generation tensor cores (tcgen05.mma,
+// BF16 operands in shared memory, FP32 accumulators in TMEM): M = 128 pixels of an image row,
+// N = 32 output channels, K = 9 taps x 32 channels.
 // Their data gradient is the same kernel run on the flipped, transposed weights.  The first
 // and last layers (32 MACs per tap) and all weight gradients run on the CUDA cores; weight
 // gradients are reduced over a fixed set of blocks in a fixed order (deterministic).
