@@ -140,6 +140,27 @@ def test_reconstruct_follows_oracle_trajectory(prob, orc):
             assert bool(rs) == rso
 
 
+def test_single_slice_plain_method_follows_oracle(orc):
+    """The plain single-slice form: one 128^2 slice, 90 angles over [0, pi), Poisson noise at 1e4
+    photons per ray, FBP start, 50 iterations; a single slice keeps its 8 in-plane neighbours of
+    the 26-neighbourhood.  Final iterate within 1e-3 of the FP64 oracle's."""
+    N, iters = 128, 50
+    p = synth.single_slice(N=N, n_angles=90, n_ellipses=10, seed=1001, with_truth=False)
+    ctx = tm.Context([tm.Group(N=N, angles=list(p.theta), n_slices=1)])
+    sino = dev(p.sino)
+    atg = ctx.build_operator(sino)
+    x = ctx.fbp(sino)
+    st = ctx.reconstruct(x, atg, tm.Params(**PRIOR, max_iter=iters))
+    assert st.iterations == iters and st.status == 0
+    pr = orc.Prior(**PRIOR)
+    g = p.sino.astype(np.float64)[0]
+    K = orc.kernel(N, p.theta, N)
+    L = orc.lipschitz(K, N, pr)
+    ref = orc.nesterov(orc.fbp(g, N, p.theta, math.pi), orc.adjoint(g, N, p.theta), float(np.sum(g * g)), K, pr, L,
+                       iters)
+    assert rel(host(x, (N, N)), ref) < 1e-3
+
+
 def test_graph_replay_is_bitwise_eager(prob):
     prm = dict(PRIOR, max_iter=7)
     a = torch.zeros(prob.x.size, dtype=torch.float32, device="cuda")
