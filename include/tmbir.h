@@ -331,6 +331,18 @@ int tmbir_warm_start(tmbir_ctx* ctx, tmbir_cnn* net, const float* d_fbp, const f
  */
 int tmbir_normal_apply_static(tmbir_ctx* ctx, const float* d_x, float* d_z);
 
+/*
+ * Bounded-wait check (failure detection; no counterpart in the paper).  Every wait of the library
+ * on a device barrier polls at most a fixed number of times; a wait that gives up records that in
+ * a status word and its kernel returns, so the call reports TMBIR_ERR_TIMEOUT instead of hanging
+ * the GPU, and the context stays usable.  This call runs that mechanism on its own: one block
+ * waits, for at most `polls` polls (1 .. 2^24), on a shared-memory barrier that one of its threads
+ * arrives on first (arrive != 0: returns TMBIR_OK) or that nothing arrives on (arrive == 0:
+ * returns TMBIR_ERR_TIMEOUT).  The status word is a library-wide device variable: checks that
+ * overlap on the GPU race on it.  Synchronises the context stream.
+ */
+int tmbir_wait_check(tmbir_ctx* ctx, unsigned polls, int arrive);
+
 /* Wait for the context stream; reports a pending CUDA error. */
 int tmbir_sync(tmbir_ctx* ctx);
 

@@ -84,6 +84,7 @@ SYMBOLS = [
     "tmbir_cnn_destroy", "tmbir_cnn_init", "tmbir_cnn_set_weights", "tmbir_cnn_get_weights", "tmbir_cnn_apply",
     "tmbir_cnn_train_step", "tmbir_cnn_net_forward", "tmbir_cnn_net_backward", "tmbir_warm_start",
     "tmbir_state_size", "tmbir_state_export", "tmbir_state_import", "tmbir_autotune", "tmbir_build_operator_fbp",
+    "tmbir_wait_check",
 ]
 
 _lib = None
@@ -122,6 +123,7 @@ def load(path: str | None = None):
         "tmbir_pass_times": [vp, vp, vp, ctypes.POINTER(_Params), i, dp],
         "tmbir_launch_count": [vp, ctypes.POINTER(ctypes.c_longlong)],
         "tmbir_normal_apply_static": [vp, vp, vp],
+        "tmbir_wait_check": [vp, ctypes.c_uint, i],
         "tmbir_cnn_param_count": [],
         "tmbir_cnn_workspace_size": [i, i, i, ctypes.POINTER(sz)],
         "tmbir_cnn_create": [ctypes.POINTER(vp), vp, i, i, i, vp, sz],
@@ -337,6 +339,12 @@ class Context:
         _check(_lib.tmbir_normal_apply_static(self._h, ctypes.c_void_p(_ptr(x)), ctypes.c_void_p(_ptr(out))))
         self._post(x, out)
         return out
+
+    def wait_check(self, polls: int, arrive: bool):
+        """Run the library's bounded device wait on its own: returns when the wait completes
+        (arrive), raises TmbirError(TMBIR_ERR_TIMEOUT) when it gives up (nothing arrives)."""
+        self._pre()
+        _check(_lib.tmbir_wait_check(self._h, int(polls), 1 if arrive else 0))
 
     def gradient(self, x, atg, params: Params, out=None):
         out = self._empty(x.numel()) if out is None else out

@@ -457,3 +457,20 @@ def test_nonfinite_input_is_reported():
     with pytest.raises(tm.TmbirError) as e:
         ctx.reconstruct(x, atg, tm.Params(max_iter=5))
     assert e.value.code == -6
+
+
+def test_bounded_wait_gives_up_and_the_context_stays_usable():
+    """A device wait that nothing satisfies gives up after its poll bound: the call reports
+    TMBIR_ERR_TIMEOUT, no GPU fault or hang, and the context keeps working."""
+    p = synth.volume(S=1, N=64, n_angles=20, n_ellipsoids=3, seed=77)
+    ctx = tm.Context([tm.Group(N=64, angles=list(p.theta))])
+    ctx.build_operator(dev(p.sino))
+    x = dev(synth.random_image(np.random.default_rng(3), (64, 64), 0.5))
+    before = host(ctx.normal_apply(x), (64, 64))
+    ctx.wait_check(1 << 20, arrive=True)
+    with pytest.raises(tm.TmbirError) as e:
+        ctx.wait_check(1000, arrive=False)
+    assert e.value.code == -5
+    ctx.wait_check(1 << 20, arrive=True)
+    after = host(ctx.normal_apply(x), (64, 64))
+    assert np.array_equal(before, after)
