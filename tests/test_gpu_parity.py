@@ -161,6 +161,17 @@ def test_single_slice_plain_method_follows_oracle(orc):
     assert rel(host(x, (N, N)), ref) < 1e-3
 
 
+def test_batched_normal_operator_equals_slices_alone(prob):
+    """The data term is slice-separable (Sec. 2): R*R applied to a batch equals R*R applied to
+    each slice in a context of its own."""
+    z = host(prob.ctx.normal_apply(dev(prob.x)), prob.x.shape)
+    ctx1 = tm.Context([tm.Group(N=prob.N, angles=list(prob.theta), n_slices=1, span=prob.span)])
+    ctx1.build_operator(dev(prob.sino[:1]))
+    for s in range(prob.S):
+        z1 = host(ctx1.normal_apply(dev(prob.x[s])), (prob.N, prob.N))
+        assert rel(z1, z[s]) < 1e-6
+
+
 def test_graph_replay_is_bitwise_eager(prob):
     prm = dict(PRIOR, max_iter=7)
     a = torch.zeros(prob.x.size, dtype=torch.float32, device="cuda")
