@@ -3,7 +3,7 @@
 // gradient over the 26-neighbourhood (Eq. 5, Sec. 2.4) and the fast-gradient update with
 // restart (Sec. 2, Eq. 6).
 //
-// Three passes per iteration, each one launch over every slice of a group:
+// Four launches per iteration, each over every slice of a group:
 //   pass 1  rows:    y = x_k + beta (x_k - x_{k-1}); real FFT of length 2N of each row (the
 //                    upper N entries are the zero padding), written column-major
 //                    spec[v][r], v = 0..N (half spectrum), r = 0..N-1 (nonzero rows only).
@@ -11,9 +11,10 @@
 //                    real kernel spectrum, inverse FFT, keep the first N rows (the crop).
 //                    The length-2N transforms are split into their even and odd halves, two
 //                    length-N transforms each, so the zero padding and the crop cost nothing.
-//   pass 3  rows:    inverse real FFT of each row, keep the first N columns -> K (*) y; then
-//                    per voxel G = K(*)y - R*g + lambda grad Phi(y), x_{k+1} = y - G/L, and the
-//                    FP64 partial sums the optimiser needs.
+//   pass 3a rows:    inverse real FFT of each row, keep the first N columns -> K (*) y.
+//   pass 3b stencil: per voxel G = K(*)y - R*g + lambda grad Phi(y) (each neighbour pair of the
+//                    26-neighbourhood evaluated once), x_{k+1} = y - G/L, and the partial sums
+//                    the optimiser needs (compensated FP32 per thread, FP64 per block).
 // A finalize kernel (one block) reduces the partials in a fixed order and advances the
 // device-resident momentum state, so a whole run needs no host round trip.
 //
@@ -109,16 +110,6 @@ __device__ __forceinline__ float rcpa(float x) {
   float y;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
-}
-
-// 1/x for x >= 1 on the FMA pipe: integer seed then three Newton steps r <- r (2 - x r).
-// Seed: the bit pattern of 1/x is about (253 + c) 2^23 - bits(x); c = 0.9 balances the seed
-// error to within 5.2 % over every binade, and three quadratic steps bring it below 1e-7.
-__device__ __forceinline__ float rcp_newton(float x) {
-  float r = __int_as_float(0x7EF33333 - __float_as_int(x));
-#pragma unroll
-  for (int it = 0; it < 3; ++it) r = fmaf(r, fmaf(-x, r, 1.0f), r);
-  return r;
 }
 
 // Packed FP32 pairs: one instruction computes both lanes of a float2 (sm_100 and later).
