@@ -106,6 +106,24 @@ def test_bench_workload_gradient_and_step(bench_case, orc):
         assert abs(x1[zz, r, col] - (x[zz, r, col] - gr / L)) <= 1e-5 * gscale / L + 1e-7
 
 
+def test_bench_workload_bf16_spectra(bench_case):
+    """BF16 storage of the padded spectra at the bench size (eight-warp pass 3a, BF16 gathers):
+    one step's K (*) y within 3e-3 relative L2 of the FP32 path's over the whole volume (BF16
+    changes only the stored spectra, so the two steps differ by (K (*) y)_bf16 - (K (*) y)_fp32
+    over L)."""
+    c = bench_case
+    S, N = c["S"], c["N"]
+    x = synth.random_image(np.random.default_rng(9), (S, N, N), 0.5)
+    L = 3.0e5
+    steps = []
+    for bf16 in (False, True):
+        xs = dev(x)
+        c["ctx"].reconstruct(xs, c["atg"], tm.Params(**PRIOR, L=L, max_iter=1, bf16=bf16))
+        steps.append(host(xs, (S, N, N)))
+    z = host(c["ctx"].normal_apply(dev(x)), (S, N, N))
+    assert np.linalg.norm(L * (steps[1] - steps[0])) <= 3e-3 * np.linalg.norm(z)
+
+
 def test_n2048_limited_angle(orc):
     # two slices at the finest level of the hierarchical geometry, compared in full
     S, N, na, span = 2, 2048, 128, 2 * math.pi / 3
