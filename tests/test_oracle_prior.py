@@ -106,3 +106,38 @@ def test_invariances(orc):
     # mirror symmetry of the neighbourhood
     gm, phim = orc.prior(x[::-1, ::-1, ::-1].copy(), pr)
     assert np.allclose(gm, g[::-1, ::-1, ::-1], atol=1e-12) and abs(phim - phi) < 1e-10 * phi
+
+
+def test_potential_with_q_below_two(orc):
+    # q != 2 (the general qGGMRF): the closed forms and derivatives hold for any 1 <= p <= q
+    for p, q in ((1.1, 1.8), (1.0, 1.5), (1.5, 1.9)):
+        pr = P(orc, p=p, q=q)
+        cs = pr.c * pr.sigma
+        assert abs(orc.rho(cs, pr) - pr.c ** q / 2) < 1e-15  # u = 1 at |D| = c sigma
+        for d in (-0.4, -3e-3, 5e-4, 0.02, 1.3):
+            h = 1e-6 * abs(d)
+            fd = (orc.rho(d + h, pr) - orc.rho(d - h, pr)) / (2 * h)
+            assert abs(orc.drho(d, pr) - fd) <= 1e-6 * abs(fd)
+            assert orc.drho(-d, pr) == -orc.drho(d, pr)
+        # far tail: rho ~ c^(q-p) |D/sigma|^p
+        d = 1e8 * cs
+        assert abs(orc.rho(d, pr) / (pr.c ** (q - p) * (d / pr.sigma) ** p) - 1) < 1e-3
+    # p = q < 2: the generalised Gaussian |D/sigma|^q / 2
+    g = P(orc, p=1.6, q=1.6)
+    for d in (-0.3, 0.05, 1.7):
+        assert abs(orc.rho(d, g) - 0.5 * abs(d / g.sigma) ** 1.6) < 1e-12
+
+
+def test_gradient_with_q_below_two_matches_finite_differences(orc):
+    rng = np.random.default_rng(13)
+    pr = P(orc, p=1.1, q=1.8)
+    x = rng.normal(0, 0.05, (3, 5, 6))
+    g, _ = orc.prior(x, pr)
+    h = 1e-7
+    for idx in [(0, 0, 0), (1, 2, 3), (2, 4, 5), (1, 0, 2)]:
+        xp = x.copy()
+        xp[idx] += h
+        xm = x.copy()
+        xm[idx] -= h
+        fd = (orc.prior(xp, pr)[1] - orc.prior(xm, pr)[1]) / (2 * h)
+        assert abs(g[idx] - fd) <= 1e-6 * max(abs(fd), 1e-6)
