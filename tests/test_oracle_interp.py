@@ -100,3 +100,26 @@ def test_downsample_sino(orc):
     assert np.array_equal(d, g[:, :, ::4] / 4)
     # the centre bin nd/2 maps to the coarse centre bin
     assert d[0, 0, 2] == g[0, 0, 8] / 4
+
+
+def test_levels_are_consistent_on_a_smooth_phantom(orc):
+    # Sec. 2.3: a coarse level sees the subsampled data of the same object.  A Gaussian blob on
+    # the fine grid (pitch 1) is, on the centre-aligned coarse grid (pitch 2), the blob with half
+    # its centre and width; its coarse projections must equal the subsampled fine projections
+    # (divided by 2: line integrals in coarse-pixel units), and the x2 Lanczos upsampling of
+    # the coarse image must give back the fine one (nodes exactly, between nodes closely).
+    Nf, Nc = 64, 32
+    x0, y0, w = 3.1, -2.4, 5.0
+    th = synth.angles(17)
+    fine = synth.gaussian_blob(Nf, x0, y0, w)
+    coarse = synth.gaussian_blob(Nc, x0 / 2, y0 / 2, w / 2)
+    g_c = orc.downsample_sino(orc.forward(fine, th, Nf), 2)
+    got = orc.forward(coarse, th, Nc)
+    assert np.linalg.norm(got - g_c) / np.linalg.norm(g_c) < 1e-7  # the blobs are cut at the grid edge (~1e-9)
+    # a missing 1/2, or bins taken off-centre, is far off
+    assert np.linalg.norm(got - 2 * g_c) / np.linalg.norm(g_c) > 0.5
+    assert np.linalg.norm(got - np.roll(g_c, 1, axis=1)) / np.linalg.norm(g_c) > 0.05
+    up = orc.lanczos_up(coarse)
+    assert np.array_equal(up[::2, ::2], coarse)
+    assert np.max(np.abs(up[::2, ::2] - fine[::2, ::2])) < 1e-14
+    assert np.max(np.abs(up - fine)) < 1e-2 * fine.max()
