@@ -554,7 +554,8 @@ class CNN:
         import numpy as np
 
         a = np.ascontiguousarray(params, dtype=np.float32)
-        assert a.size == self.n_params
+        if a.size != self.n_params:
+            raise ValueError(f"expected {self.n_params} parameters, got {a.size}")
         _check(_lib.tmbir_cnn_set_weights(self._h, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
 
     def get_weights(self):
