@@ -151,3 +151,28 @@ def test_restart_modes(orc):
     # until the first restart of a mode
     first = min(k for k, (_, _, r) in enumerate(logs["gradient"]) if r)
     assert all(abs(a[0] - b[0]) <= 1e-12 * abs(b[0]) for a, b in zip(logs["gradient"][:first + 1], logs["none"][:first + 1]))
+
+
+def test_accelerated_rate_without_restart(orc):
+    # the fast gradient method's guarantee (Nesterov; Beck and Teboulle's bound): without restart
+    # F(x_k) - F* <= 2 L |x_0 - x*|^2 / (k + 1)^2 on the quadratic case, whose minimiser x* is a
+    # dense linear solve; a broken momentum sequence loses this rate
+    S, N, nd, na = 1, 6, 8, 5
+    pr = orc.Prior(p=2.0, q=2.0, sigma=0.5, lam=0.3)
+    rng = np.random.default_rng(26)
+    th = synth.angles(na)
+    g = rng.uniform(0, 1, (S, na, nd))
+    A = np.stack([nudft_forward(e.reshape(N, N), th, nd).ravel() for e in np.eye(N * N)], axis=1)
+    H = A.T @ A + pr.lam / pr.sigma ** 2 * gaussian_mrf_laplacian(orc, S, N)
+    x_star = np.linalg.solve(H, A.T @ g[0].ravel()).reshape(S, N, N)
+    K = orc.kernel(N, th, nd)
+    atg = orc.adjoint(g, N, th)
+    gtg = float(np.sum(g * g))
+    L = orc.lipschitz(K, N, pr)
+    F_star = orc.objective(x_star, atg, gtg, K, pr)
+    x0 = np.zeros((S, N, N))
+    r0 = float(np.sum((x0 - x_star) ** 2))
+    for k in (1, 2, 3, 5, 8, 13, 21, 34, 55):
+        xk = orc.nesterov(x0, atg, gtg, K, pr, L, k, restart="none")
+        gap = orc.objective(xk, atg, gtg, K, pr) - F_star
+        assert -1e-9 * abs(F_star) <= gap <= 2 * L * r0 / (k + 1) ** 2, k
