@@ -122,7 +122,12 @@ typedef struct {
   double grad_norm; /* ||grad F(y_k)||_2 of the last iteration */
 } tmbir_stats;
 
-/* Create a context bound to a CUDA stream (cudaStream_t passed as void*; NULL = legacy default stream). */
+/*
+ * Create a context bound to a CUDA stream (cudaStream_t passed as void*; NULL = legacy default
+ * stream).  On the device current at the call it also commits the fixed scratch arrays of
+ * tmbir_normal_apply_static (67 MiB, held until the process exits) and caches their addresses;
+ * fails with TMBIR_ERR_CUDA if that device cannot hold them.
+ */
 int tmbir_create(tmbir_ctx** out, void* stream);
 int tmbir_destroy(tmbir_ctx* ctx);
 /* Message of the last failing call on this thread ("" if none).  Owned by the library. */
@@ -320,10 +325,15 @@ int tmbir_warm_start(tmbir_ctx* ctx, tmbir_cnn* net, const float* d_fbp, const f
  *     slices as fit (at most the context's spectrum chunk); a geometry whose pass 3b needs
  *     more than 65536 blocks is rejected with TMBIR_ERR_SHAPE; nothing is allocated on any
  *     path.
- *   - Every device that loads the library holds the array until the process exits.
- *   - The first call on a device, with that device current, looks up the array's device
- *     address (cudaGetSymbolAddress) and caches it; make that first call before any stream
- *     capture.
+ *   - Every device that loads the library holds the array until the process exits.  The
+ *     memory is committed when tmbir_create runs with that device current (it looks up the
+ *     array's device address with cudaGetSymbolAddress, which loads the module holding it, and
+ *     caches the address), not at this call, so a caller that owns the rest of the memory
+ *     budget learns of a shortage at context creation.  On a device where no context was
+ *     created, the first call of this entry point does that lookup itself; make that first call
+ *     before any stream capture.
+ *   - A device reset (cudaDeviceReset) invalidates the cached address along with every context
+ *     and workspace on that device: create a new context after a reset, which refreshes it.
  *   - All calls share the one array and it keeps the last call's contents: calls whose work
  *     overlaps on the GPU (different streams or contexts, concurrently) race on it.
  *   - The operator must be built (tmbir_build_operator); its kernel spectrum still lives in the

@@ -146,6 +146,14 @@ static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
     if (!(cond)) return set_error(code, msg); \
   } while (0)
 
+int tmbir::require_ready(const tmbir_ctx* ctx, bool need_operator) {
+  if (!ctx) return set_error(TMBIR_ERR_ARG, "ctx is NULL");
+  if (ctx->c.groups.empty()) return set_error(TMBIR_ERR_STATE, "no geometry set");
+  if (!ctx->c.ws) return set_error(TMBIR_ERR_WORKSPACE, "no workspace bound");
+  if (need_operator && !ctx->c.operator_built) return set_error(TMBIR_ERR_STATE, "operator not built");
+  return TMBIR_OK;
+}
+
 extern "C" {
 
 const char* tmbir_last_error(void) { return g_last_error.c_str(); }
@@ -155,6 +163,9 @@ int tmbir_create(tmbir_ctx** out, void* stream) {
   int dev_count = 0;
   cudaError_t e = cudaGetDeviceCount(&dev_count);
   if (e != cudaSuccess || dev_count == 0) return set_error(TMBIR_ERR_CUDA, "tmbir_create: no CUDA device");
+  // commit the fixed scratch arrays of tmbir_normal_apply_static on this device now, not at
+  // that entry point's first call (and refresh their cached addresses, e.g. after a reset)
+  if (int rc = static_scratch_resolve()) return rc;
   tmbir_ctx* ctx = new tmbir_ctx();
   ctx->c.stream = (cudaStream_t)stream;
   *out = ctx;
@@ -376,14 +387,6 @@ int tmbir_set_workspace(tmbir_ctx* ctx, void* d_ws, size_t bytes) {
   c.operator_built = false;
   c.geom_ready.assign(c.groups.size(), false);
   c.spread_ready.assign(c.groups.size(), false);
-  return TMBIR_OK;
-}
-
-static int require_ready(const tmbir_ctx* ctx, bool need_operator) {
-  if (!ctx) return set_error(TMBIR_ERR_ARG, "ctx is NULL");
-  if (ctx->c.groups.empty()) return set_error(TMBIR_ERR_STATE, "no geometry set");
-  if (!ctx->c.ws) return set_error(TMBIR_ERR_WORKSPACE, "no workspace bound");
-  if (need_operator && !ctx->c.operator_built) return set_error(TMBIR_ERR_STATE, "operator not built");
   return TMBIR_OK;
 }
 

@@ -240,6 +240,16 @@ int launch_downsample_sino(const float* in, int S, int na, int nd, int f, float*
 
 PriorC make_prior(const tmbir_params& p);
 
+// argument checks shared by the entry points: a context with a geometry and a bound
+// workspace (and, with need_operator, a built operator); sets the error message otherwise
+int require_ready(const tmbir_ctx* ctx, bool need_operator);
+
+// static_scratch.cu: looks up the device addresses of the fixed scratch arrays of
+// tmbir_normal_apply_static on the current device and caches them.  Looking them up loads
+// the module that holds the arrays, which commits their device memory, so tmbir_create calls
+// this once for the device current at creation.
+int static_scratch_resolve();
+
 }  // namespace tmbir
 
 // the opaque handle of the C ABI

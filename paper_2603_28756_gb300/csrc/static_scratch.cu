@@ -4,8 +4,11 @@
 //
 // The array is a file-scope __device__ variable: every device that loads the library holds it
 // until the process exits.  Host code only sees a host-side stand-in for its name, so the
-// device address is looked up once per device with cudaGetSymbolAddress (on the first call
-// made while that device is current) and cached.
+// device address is looked up with cudaGetSymbolAddress while the device is current.  The
+// lookup loads this file's module, which commits the arrays' device memory; tmbir_create does
+// it for the device current at creation (and refreshes the cached address each time, so a
+// context created after a device reset sees the new address), and the entry point itself does
+// it for a device that has no context yet.
 #include <cstdint>
 #include <mutex>
 
@@ -27,26 +30,41 @@ constexpr int kMaxDevices = 64;
 std::mutex g_static_mu;
 float2* g_spec_addr[kMaxDevices] = {};
 double* g_part_addr[kMaxDevices] = {};
+
+int current_device(int* dev) {
+  TMBIR_CUDA(cudaGetDevice(dev));
+  if (*dev < 0 || *dev >= kMaxDevices) return set_error(TMBIR_ERR_CUDA, "static scratch: device index out of range");
+  return TMBIR_OK;
+}
+
+// looks the two arrays up on the current device (the caller holds g_static_mu)
+int lookup_locked(int dev) {
+  void* p = nullptr;
+  void* q = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_static_spec);
+  if (e == cudaSuccess) e = cudaGetSymbolAddress(&q, g_static_parts);
+  if (e != cudaSuccess)
+    return set_error(TMBIR_ERR_CUDA, std::string("static scratch: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+  g_spec_addr[dev] = static_cast<float2*>(p);
+  g_part_addr[dev] = static_cast<double*>(q);
+  return TMBIR_OK;
+}
 }  // namespace
 
-// device addresses of the two arrays on the current device (set up on first use)
+int static_scratch_resolve() {
+  int dev = 0;
+  if (int e = current_device(&dev)) return e;
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  return lookup_locked(dev);
+}
+
+// device addresses of the two arrays on the current device (looked up on first use)
 static int static_scratch(float2** spec, double** parts) {
   int dev = 0;
-  TMBIR_CUDA(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= kMaxDevices) return set_error(TMBIR_ERR_CUDA, "normal_apply_static: device index out of range");
+  if (int e = current_device(&dev)) return e;
   std::lock_guard<std::mutex> lock(g_static_mu);
-  if (!g_spec_addr[dev]) {
-    void* p = nullptr;
-    void* q = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_static_spec);
-    if (e != cudaSuccess)
-      return set_error(TMBIR_ERR_CUDA, std::string("normal_apply_static: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-    e = cudaGetSymbolAddress(&q, g_static_parts);
-    if (e != cudaSuccess)
-      return set_error(TMBIR_ERR_CUDA, std::string("normal_apply_static: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-    g_spec_addr[dev] = static_cast<float2*>(p);
-    g_part_addr[dev] = static_cast<double*>(q);
-  }
+  if (!g_spec_addr[dev])
+    if (int e = lookup_locked(dev)) return e;
   *spec = g_spec_addr[dev];
   *parts = g_part_addr[dev];
   return TMBIR_OK;
@@ -57,11 +75,9 @@ static int static_scratch(float2** spec, double** parts) {
 using namespace tmbir;
 
 extern "C" int tmbir_normal_apply_static(tmbir_ctx* ctx, const float* d_x, float* d_z) {
-  if (!ctx) return set_error(TMBIR_ERR_ARG, "normal_apply_static: ctx is NULL");
+  TMBIR_TRACE("tmbir_normal_apply_static");
+  if (int e = require_ready(ctx, true)) return e;
   Ctx& c = ctx->c;
-  if (c.groups.empty()) return set_error(TMBIR_ERR_STATE, "normal_apply_static: no geometry set");
-  if (!c.ws) return set_error(TMBIR_ERR_WORKSPACE, "normal_apply_static: no workspace bound");
-  if (!c.operator_built) return set_error(TMBIR_ERR_STATE, "normal_apply_static: operator not built");
   if (!d_x || !d_z || ((uintptr_t)d_x & 15u) || ((uintptr_t)d_z & 15u) || d_x == d_z)
     return set_error(TMBIR_ERR_ARG, "normal_apply_static: bad buffers");
   // the groups one after another, each in spectrum chunks that fit the static array

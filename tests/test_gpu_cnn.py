@@ -40,13 +40,17 @@ def random_params(orc, seed):
     return p.astype(np.float32).astype(np.float64)
 
 
-@pytest.mark.parametrize("H,W", [(20, 36), (33, 64)])
-def test_forward_matches_oracle(orc, H, W):
+# Image widths against the 128-pixel rows of one tensor-core tile: 36 and 64 are one partial tile;
+# 300 is two full tiles and a partial one (unmasked tiles and the halo handed from tile to tile);
+# 2560 is twenty full tiles, the row width of the largest slices.  Heights 6, 12, 20 and 33 end
+# the four-row tile groups full and partial.
+@pytest.mark.parametrize("B,H,W", [(2, 20, 36), (2, 33, 64), (2, 12, 300), (1, 6, 2560)])
+def test_forward_matches_oracle(orc, B, H, W):
     p = random_params(orc, 1)
-    net = tm.CNN(H, W, max_batch=2)
+    net = tm.CNN(H, W, max_batch=B)
     net.set_weights(p)
-    x = np.random.default_rng(2).standard_normal((2, H, W)).astype(np.float32)
-    out = net.net_forward(dev(x), 2)
+    x = np.random.default_rng(2).standard_normal((B, H, W)).astype(np.float32)
+    out = net.net_forward(dev(x), B)
     torch.cuda.synchronize()
     ref = orc.cnn_forward(x.astype(np.float64), p)
     assert rel(out.cpu().numpy().reshape(ref.shape), ref) < 2e-2
@@ -94,30 +98,32 @@ def check_backward(orc, p, x, gout, tol):
     assert rel(gin.cpu().numpy().reshape(rgin.shape), rgin) < tol
 
 
-def test_backward_matches_oracle(orc):
+@pytest.mark.parametrize("B,H,W", [(2, 18, 40), (2, 12, 300), (1, 6, 2560)])
+def test_backward_matches_oracle(orc, B, H, W):
     # Every ReLU decision is the same on both sides (margin far above the BF16 error of a
     # pre-activation), so the gradients differ only by BF16 rounding of activations, gradients
     # and weight copies: 2^-9 per operand, a few 1e-3 after three layers and up to about 1e-2
     # in the bias sums, whose terms cancel (BF16 rounding modelled on the CPU: at most 9e-3).
-    H, W = 18, 40
+    # Widths as in the forward test: one partial tile, two full tiles and a partial one, and
+    # twenty full tiles.
     rng = np.random.default_rng(4)
     p = robust_params(orc, 3)
-    x = rng.uniform(-0.5, 0.5, (2, H, W)).astype(np.float32)
-    gout = rng.standard_normal((2, H, W)).astype(np.float32)
+    x = rng.uniform(-0.5, 0.5, (B, H, W)).astype(np.float32)
+    gout = rng.standard_normal((B, H, W)).astype(np.float32)
     assert min_preactivation(orc, x, p) > 0.1
     check_backward(orc, p, x, gout, 2e-2)
 
 
-def test_backward_random_network(orc):
+@pytest.mark.parametrize("B,H,W", [(2, 18, 40), (2, 12, 300)])
+def test_backward_random_network(orc, B, H, W):
     # A random He-initialised network has pre-activations near zero, where BF16 rounding
     # flips the ReLU decision of a small fraction f of units; each flip moves a gradient term
     # by its full size, so the relative L2 error grows like sqrt(f) rather than like the unit
     # roundoff (BF16 rounding modelled on the CPU: 4e-2 to 8e-2 across the parameter blocks).
-    H, W = 18, 40
     p = random_params(orc, 3)
     rng = np.random.default_rng(4)
-    x = rng.standard_normal((2, H, W)).astype(np.float32)
-    gout = rng.standard_normal((2, H, W)).astype(np.float32)
+    x = rng.standard_normal((B, H, W)).astype(np.float32)
+    gout = rng.standard_normal((B, H, W)).astype(np.float32)
     check_backward(orc, p, x, gout, 0.15)
 
 

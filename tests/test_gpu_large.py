@@ -124,13 +124,22 @@ def test_bench_workload_bf16_spectra(bench_case):
     assert np.linalg.norm(L * (steps[1] - steps[0])) <= 3e-3 * np.linalg.norm(z)
 
 
-def test_n2048_limited_angle(orc):
-    # two slices at the finest level of the hierarchical geometry, compared in full
+@pytest.fixture(scope="module")
+def n2048(orc):
+    """Two slices at the finest level of the hierarchical geometry: 2048^2, 128 angles over
+    [0, 2 pi/3) (missing wedge); the oracle's kernel K and its spectrum on the 4096^2 grid."""
     S, N, na, span = 2, 2048, 128, 2 * math.pi / 3
-    p = synth.volume(S=S, N=N, n_angles=na, n_ellipsoids=6, span=span, seed=1003)
+    p = synth.volume(S=S, N=N, n_angles=na, n_ellipsoids=6, span=span, seed=1003, with_truth=True)
     ctx = tm.Context([tm.Group(N=N, angles=list(p.theta), n_slices=S, span=span)])
     d_atg = ctx.build_operator(dev(p.sino))
     Kref = orc.kernel(N, p.theta, N)
+    return dict(S=S, N=N, na=na, span=span, p=p, ctx=ctx, d_atg=d_atg, K=Kref,
+                Chat=orc.circulant_spectrum(Kref, 2 * N))
+
+
+def test_n2048_limited_angle(orc, n2048):
+    # two slices at the finest level of the hierarchical geometry, compared in full
+    S, N, p, ctx, d_atg, Kref = (n2048[k] for k in ("S", "N", "p", "ctx", "d_atg", "K"))
     K = host(ctx.kernel(0), Kref.shape)
     assert np.max(np.abs(K - Kref)) <= 1e-10 * np.max(np.abs(Kref))
     atg = host(d_atg, (S, N, N))
@@ -142,7 +151,7 @@ def test_n2048_limited_angle(orc):
     x = synth.random_image(rng, (S, N, N), 0.5).astype(np.float64)
     b = synth.random_image(rng, (S, N, N), 4.0e4).astype(np.float64)  # seeded stand-in for R*g
     d_b = dev(b)
-    Chat = orc.circulant_spectrum(Kref)
+    Chat = n2048["Chat"]
     assert rel(host(ctx.normal_apply(dev(x)), x.shape), orc.toeplitz(x, Kref, Chat)) < 1e-5
     assert rel(host(ctx.gradient(dev(x), d_b, tm.Params(**PRIOR)), x.shape), orc.gradient(x, b, Kref, pr, Chat)) < 1e-5
     # three fast-gradient iterations from zero with an explicit step constant
@@ -151,6 +160,29 @@ def test_n2048_limited_angle(orc):
     ctx.reconstruct(xs, d_b, tm.Params(**PRIOR, L=L, max_iter=3))
     ref = orc.nesterov(np.zeros(x.shape), b, 0.0, Kref, pr, L, 3, Chat=Chat)
     assert rel(host(xs, x.shape), ref) < 1e-4
+
+
+N2048_BF16_ITERS, N2048_TOTAL_ITERS = 4, 24
+
+
+def test_n2048_bf16_refinement_follows_oracle(orc, n2048):
+    """BF16 spectra for the first iterations, then FP32 refinement iterations (a resumed run,
+    which continues the momentum state exactly), at 2 x 2048^2 with the limited-angle geometry:
+    the final iterate within 1e-3 relative L2 of the FP64 oracle's after the same count.  R*g is
+    the oracle's R*R applied to the phantom (the R*g of noiseless data); the step constant is
+    the oracle's bound max |C^| (the circulant spectrum bounds the Toeplitz operator's norm) plus
+    the prior's curvature bound."""
+    S, N, p, ctx, K, Chat = (n2048[k] for k in ("S", "N", "p", "ctx", "K", "Chat"))
+    pr = orc.Prior(**PRIOR)
+    b = orc.toeplitz(p.truth, K, Chat)
+    L = float(np.max(np.abs(Chat))) + pr.lam * 2.0 * orc.max_rho2(pr)
+    ref = orc.nesterov(np.zeros((S, N, N)), b, 0.0, K, pr, L, N2048_TOTAL_ITERS, Chat=Chat)
+    d_b = dev(b)
+    x = torch.zeros(S * N * N, dtype=torch.float32, device="cuda")
+    ctx.reconstruct(x, d_b, tm.Params(**PRIOR, L=L, max_iter=N2048_BF16_ITERS, bf16=True))
+    st = ctx.reconstruct(x, d_b, tm.Params(**PRIOR, L=L, max_iter=N2048_TOTAL_ITERS - N2048_BF16_ITERS, resume=True))
+    assert st.iterations == N2048_TOTAL_ITERS and st.status == 0
+    assert rel(host(x, (S, N, N)), ref) < 1e-3
 
 
 def seeded_slices(seed, S, N, scale):

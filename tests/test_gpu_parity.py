@@ -285,6 +285,29 @@ def test_bf16_refinement_matches_fp32(prob):
     assert rel(host(a, prob.x.shape), host(c, prob.x.shape).astype(np.float64)) < 1e-2
 
 
+REFINE_ITERS = 150
+
+
+def test_bf16_refinement_follows_oracle(prob, orc):
+    """The chosen precision form: BF16 spectra until the relative gap reaches 1e-1, then FP32
+    refinement iterations (the device-side switch of refine_gap, inside the graph loop) to a
+    fixed count.  The final iterate is within 1e-3 relative L2 of the FP64 oracle's after the
+    same count.  F_ref (which places the switch) and the step constant L are the oracle's."""
+    pr = orc.Prior(**PRIOR)
+    gtg = float(np.sum(prob.g ** 2))
+    Chat = orc.circulant_spectrum(prob.K)
+    L = orc.lipschitz(prob.K, prob.N, pr, Chat=Chat)
+    x0 = np.zeros(prob.x.shape)
+    F_ref = orc.objective(orc.nesterov(x0, prob.atg, gtg, prob.K, pr, L, 400, Chat=Chat), prob.atg, gtg, prob.K, pr,
+                          Chat)
+    ref = orc.nesterov(x0, prob.atg, gtg, prob.K, pr, L, REFINE_ITERS, Chat=Chat)
+    x = torch.zeros(prob.x.size, dtype=torch.float32, device="cuda")
+    st = prob.ctx.reconstruct(x, prob.d_atg, tm.Params(**PRIOR, L=L, max_iter=REFINE_ITERS, F_ref=F_ref, bf16=True,
+                                                       refine_gap=1e-1))
+    assert st.iterations == REFINE_ITERS and st.status == 0
+    assert rel(host(x, prob.x.shape), ref) < 1e-3
+
+
 @pytest.mark.parametrize("use_graph", [True, False])
 def test_checkpoint_resume_is_bitwise(prob, use_graph):
     # 30 iterations in one run == 18 iterations, export, unrelated work, import, 12 more
