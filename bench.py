@@ -1,16 +1,21 @@
-"""Benchmark: gradient voxel-updates/s of the Toeplitz MBIR path on GB300.
+"""Benchmark: gradient voxel-updates/s and time to a 1e-3 relative objective gap of the
+Toeplitz MBIR path on GB300, through the C ABI.
 
-One step = one full reconstruction of a synthetic batch through the C ABI, with the
-sinogram already resident on the device:
-  build_operator (kernel K, its 2N x 2N spectrum, R*g, 1/2 g.g, lambda_max)  -- setup, FP64
-  fbp (ramp-filtered back-projection start)
-  reconstruct (100 fast-gradient iterations replayed from one CUDA graph).
-value = slices * N^2 * iterations / step time, summed over ranks (each rank reconstructs its
-own independent batch: weak scaling, no collective on the data path).
+Default workload (the largest single-GPU configuration): 512 slices of 2048^2, 128 angles
+over [0, 2 pi/3) (missing wedge), 20 ellipsoids, Gaussian noise of 1 %.  One step is the
+chosen form of the method, from the resident sinogram to the 1e-3 gap:
+  levels 512^2 -> 1024^2 -> 2048^2 (Sec. 2.3): subsampled sinograms, setup per level
+  (kernel spectrum, R*g, 1/2 g.g; Sec. 2.1), FBP start at the coarsest level (Sec. 2.2)
+  refined by the learned network where that lowers the objective, Lanczos-3 x2 between
+  levels, BF16 spectra with FP32 refinement, iterations in device-driven graph loops that
+  stop at the gap.
+value = the voxel-updates of all levels (slices x N_l^2 x iterations_l) / step time, summed
+over ranks (each rank reconstructs its own independent batch: weak scaling, no collective on
+the data path).  The iteration phase is also timed on its own, pass by pass, for the roofline.
 
-The default workload is 64 slices of 1024^2, 256 angles over [0, pi), 100 iterations.
-`--impl reference` times the FP64 CPU oracle on the host cores instead, on a bounded
-sample of the same workload (iteration phase only).
+`--workload batched-64x1024sq-256ang-100it` is the earlier fixed-work step: setup plus 100
+iterations of one level.  `--impl reference` times the FP64 CPU oracle on the host cores on
+a bounded sample of the same workload.
 """
 from __future__ import annotations
 
@@ -28,17 +33,42 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+# kind "hier": one step = the chosen form to the gap; kind "fixed": setup + `iters` iterations
 WORKLOADS = {
-    # name: (slices, N, angles, span, iterations, ellipsoids)
-    "batched-64x1024sq-256ang-100it": (64, 1024, 256, math.pi, 100, 20),
-    "single-1x128sq-90ang-50it": (1, 128, 90, math.pi, 50, 10),
-    "small-8x256sq-128ang-50it": (8, 256, 128, math.pi, 50, 10),
-    # profiling case: same image side and angles as the default, 16 slices (> L2, a few GB on device)
-    "profile-16x1024sq-256ang-20it": (16, 1024, 256, math.pi, 20, 20),
+    "hier-512x2048sq-128ang-limited": dict(S=512, N=2048, na=128, span=2 * math.pi / 3, ne=20, kind="hier"),
+    "batched-64x1024sq-256ang-100it": dict(S=64, N=1024, na=256, span=math.pi, ne=20, kind="fixed", iters=100),
+    # the chosen form at the batched workload's size
+    "hier-64x1024sq-256ang": dict(S=64, N=1024, na=256, span=math.pi, ne=20, kind="hier"),
+    "single-1x128sq-90ang-50it": dict(S=1, N=128, na=90, span=math.pi, ne=10, kind="fixed", iters=50),
+    # profiling cases: the image sides and angles of the workloads, a few GB on the device
+    "profile-16x1024sq-256ang-20it": dict(S=16, N=1024, na=256, span=math.pi, ne=20, kind="fixed", iters=20),
+    "profile-8x2048sq-128ang-limited-20it": dict(S=8, N=2048, na=128, span=2 * math.pi / 3, ne=20, kind="fixed",
+                                                 iters=20),
 }
-DEFAULT = "batched-64x1024sq-256ang-100it"
+DEFAULT = "hier-512x2048sq-128ang-limited"
 PRIOR = dict(p=1.2, q=2.0, c=0.01, sigma=0.1, lam=1.0)
 METRIC = "gradient voxel-updates/s"
+
+GAP = 1e-3
+LEVELS = 3
+COARSE_ITERS = (40, 15)  # iterations at N/4 and N/2 before the finest level of the hierarchy
+FINEST_CAP = 400  # iteration cap of the finest level (the gap stops it first)
+REF_ITERS = 600  # finest-level FP32 iterations after the hierarchy that give F_ref
+PLAIN_CAP = 800  # iteration cap of the one-level forms
+REFINE_GAP = 1e-2  # BF16 spectra until this gap, FP32 after
+CNN_EPOCHS = 12
+CNN_BATCH = 8
+CNN_TARGET_ITERS = 300  # iterations that make a training target from an FBP start
+CNN_TRAIN_SLICES = 128  # slices of the separate training volume
+PASS_ITERS = 5  # eager iterations timed pass by pass
+
+
+_t_start = time.perf_counter()
+
+
+def progress(msg):
+    """A timestamped progress line on stderr (the JSON line alone goes to stdout)."""
+    print(f"[bench {time.perf_counter() - _t_start:7.1f}s] {msg}", file=sys.stderr, flush=True)
 
 
 def dist_env():
@@ -48,10 +78,10 @@ def dist_env():
     return rank, world, local
 
 
-def rank_seed(rank):
+def rank_seed(rank, base=1002):
     """Phantom seed of a rank: every rank reconstructs its own independent batch (weak scaling,
     no collective on the data path)."""
-    return 1002 + 17 * rank
+    return base + 17 * rank
 
 
 def max_over_ranks(ms, world, device):
@@ -73,9 +103,10 @@ def job_rate(units_per_rank, steps, world, ms):
 def make_problem(name, rank):
     import synth
 
-    S, N, na, span, iters, ne = WORKLOADS[name]
-    p = synth.volume(S=S, N=N, n_angles=na, n_ellipsoids=ne, span=span, seed=rank_seed(rank))
-    return p, iters
+    w = WORKLOADS[name]
+    base = 1003 if w["span"] < math.pi else 1002
+    return synth.volume(S=w["S"], N=w["N"], n_angles=w["na"], n_ellipsoids=w["ne"], span=w["span"],
+                        seed=rank_seed(rank, base))
 
 
 class Clocks:
@@ -129,14 +160,6 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-def measured_sm_max_mhz():
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            return float(json.load(f)["sm_max_mhz"])
-    except Exception:
-        return 2070.0
-
-
 def kernel_traffic(kernel, workload):
     """DRAM bytes per launch from the committed ncu summary, if it matches the current kernel source."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
@@ -153,61 +176,88 @@ def kernel_traffic(kernel, workload):
     return None
 
 
-def cpu_baseline(name, samples_slices=2, samples_iters=2):
-    """FP64 oracle on the host cores: iteration phase of the same workload on a bounded sample."""
+# ------------------------------------------------------------------------------ CPU baseline
+
+_oracle_kernels = {}  # workload -> (K, its spectrum, seconds to build them)
+
+
+def oracle_sample(name, slices, iters):
+    """Seconds the FP64 oracle takes for `iters` fast-gradient iterations of `slices` slices at the
+    workload's image side and angles (K (*) y by FFT convolution, the qGGMRF prior, the update;
+    seeded images of that size).  The kernel K and its spectrum are built once per workload and
+    not timed."""
     import numpy as np
 
     import oracle
     import synth
 
-    S, N, na, span, iters, _ = WORKLOADS[name]
-    th = synth.angles(na, span)
+    w = WORKLOADS[name]
+    N = w["N"]
     rng = np.random.default_rng(5)
-    s = min(samples_slices, S)
-    x0 = rng.uniform(0, 0.5, (s, N, N))
-    atg = rng.uniform(0, 1.0, (s, N, N))
+    x0 = rng.uniform(0, 0.5, (slices, N, N))
+    atg = rng.uniform(0, 1.0, (slices, N, N))
     pr = oracle.Prior(**PRIOR)
-    t0 = time.perf_counter()
-    K = oracle.kernel(N, th, N)
-    t_setup = time.perf_counter() - t0
-    Chat = oracle.circulant_spectrum(K)
+    if name not in _oracle_kernels:
+        t0 = time.perf_counter()
+        K = oracle.kernel(N, synth.angles(w["na"], w["span"]), N)
+        _oracle_kernels[name] = (K, oracle.circulant_spectrum(K), time.perf_counter() - t0)
+    K, Chat, t_setup = _oracle_kernels[name]
     L = 1.01 * 50.0 + pr.lam * 4.0 / pr.sigma ** 2
     t0 = time.perf_counter()
-    oracle.nesterov(x0, atg, 1.0, K, pr, L, samples_iters, Chat=Chat)
-    dt = time.perf_counter() - t0
+    oracle.nesterov(x0, atg, 1.0, K, pr, L, iters, Chat=Chat)
+    return time.perf_counter() - t0, t_setup
+
+
+def cpu_baseline(name, slices=1, iters=2, single_thread=True):
+    """FP64 oracle on the host cores on a bounded sample of the workload's iteration phase:
+    all cores, and (in a child process with one OpenMP thread) a single core."""
+    w = WORKLOADS[name]
+    N = w["N"]
+    dt, t_setup = oracle_sample(name, slices, iters)
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return {
-        "value": s * N * N * samples_iters / dt,
+    out = {
+        "value": slices * N * N * iters / dt,
         "unit": "voxel-updates/s",
         "cores": cores,
         "kind": "oracle",
-        "sample": f"{s} of {S} slices x {samples_iters} of {iters} iterations at {N}^2, {na} angles; "
-                  f"iteration phase only (kernel K setup {t_setup:.1f} s excluded); numpy FFT single-threaded, "
-                  f"prior in C with OpenMP",
+        "sample": f"{slices} of {w['S']} slices x {iters} iterations at {N}^2, {w['na']} angles; iteration phase "
+                  f"only (kernel K and spectrum {t_setup:.1f} s excluded); numpy FFT single-threaded, prior in C with "
+                  f"OpenMP",
     }
+    if single_thread:
+        # a child process whose OpenMP runtime starts with one thread; it takes the kernel K
+        # from a file instead of building it again on one core
+        import numpy as np
+
+        env = dict(os.environ, OMP_NUM_THREADS="1")
+        with tempfile.TemporaryDirectory() as td:
+            kf = os.path.join(td, "K.npy")
+            np.save(kf, _oracle_kernels[name][0])
+            code = (f"import sys; sys.path.insert(0, {ROOT!r}); import numpy as np, oracle, bench; "
+                    f"K = np.load({kf!r}); bench._oracle_kernels[{name!r}] = (K, oracle.circulant_spectrum(K), 0.0); "
+                    f"print(bench.oracle_sample({name!r}, {slices}, {iters})[0])")
+            try:
+                r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+                out["single_thread"] = {"value": slices * N * N * iters / float(r.stdout.strip().splitlines()[-1]),
+                                        "cores": 1}
+            except Exception as e:  # reported, not hidden
+                out["single_thread"] = {"error": str(e)[:200]}
+    return out
 
 
-GAP = 1e-3
-REF_ITERS = 1000
+# ------------------------------------------------------------------------------ learned start
 
-
-COARSE_ITERS = (40, 15)  # iterations at N/4 and N/2 before the finest level of the hierarchy
-REFINE_GAP = 1e-2  # BF16 spectra until this gap, FP32 after
-CNN_EPOCHS = 30
-CNN_BATCH = 8
-CNN_TARGET_ITERS = 300  # iterations that make a training target from an FBP start
-
-
-def train_warm_start(tm, N, na, span, S, factor, stream):
+def train_warm_start(tm, w, factor, stream):
     """The learned warm start for images of N / factor: trained on (FBP, reconstruction) pairs
     the method itself produces from a separate seeded volume (same geometry, other phantoms)."""
-    import synth
-
-    p = synth.volume(S=S, N=N, n_angles=na, n_ellipsoids=20, span=span, seed=7001)
-    Nl = N // factor
-    ctx = tm.Context([tm.Group(N=Nl, angles=list(p.theta), n_slices=S, span=span)], stream=stream)
     import torch
 
+    import synth
+
+    S, N, na, span = min(w["S"], CNN_TRAIN_SLICES), w["N"], w["na"], w["span"]
+    p = synth.volume(S=S, N=N, n_angles=na, n_ellipsoids=w["ne"], span=span, seed=7001)
+    Nl = N // factor
+    ctx = tm.Context([tm.Group(N=Nl, angles=list(p.theta), n_slices=S, span=span)], stream=stream)
     sino = torch.from_numpy(p.sino.ravel()).cuda()
     if factor > 1:
         sino = ctx.downsample_sino(sino, S, na, N, factor)
@@ -218,320 +268,444 @@ def train_warm_start(tm, N, na, span, S, factor, stream):
     net = tm.CNN(Nl, Nl, max_batch=CNN_BATCH, stream=stream, seed=11)
     plane = Nl * Nl
     losses = []
+    t0 = time.perf_counter()
     for _ in range(CNN_EPOCHS):
         for b in range(0, S - CNN_BATCH + 1, CNN_BATCH):
             losses.append(net.train_step(fbp[b * plane:(b + CNN_BATCH) * plane],
                                          target[b * plane:(b + CNN_BATCH) * plane], CNN_BATCH, lr=1e-3))
     steps = max(1, S // CNN_BATCH)
-    return net, {"image": Nl, "pairs": S, "epochs": CNN_EPOCHS, "loss_first_epoch": sum(losses[:steps]) / steps,
-                 "loss_last_epoch": sum(losses[-steps:]) / steps}
+    info = {"image": Nl, "pairs": S, "epochs": CNN_EPOCHS, "train_s": time.perf_counter() - t0,
+            "loss_first_epoch": sum(losses[:steps]) / steps, "loss_last_epoch": sum(losses[-steps:]) / steps}
+    del ctx
+    return net, info
 
 
-def time_to_gap(tm, ctx, stream, sino, atg, x, barrier, world, wl):
-    """Device time from a resident sinogram to relative objective gap <= 1e-3.
+# ------------------------------------------------------------------------------ the chosen form
 
-    gap(y_k) = (F(y_k) - F_ref) / (F(0) - F_ref) with F(0) = 1/2 g.g and F_ref the objective
-    after REF_ITERS fast-gradient iterations from the FBP start (FP32).  Each form is timed
-    from the resident sinogram (setup included) until the device stops the finest level's
-    iterations at the gap.
-    """
+class Hier:
+    """Level contexts (N/4, N/2, N) on one stream and the per-level buffers of the chosen form."""
+
+    def __init__(self, tm, w, theta, stream):
+        self.tm, self.w, self.theta, self.stream = tm, w, list(theta), stream
+        S, N, span = w["S"], w["N"], w["span"]
+        self.ctxs = [tm.Context([tm.Group(N=N >> (LEVELS - 1 - k), angles=self.theta, n_slices=S, span=span)],
+                                stream=stream) for k in range(LEVELS)]
+        self.net = None
+
+    def run(self, sino, prms, start_cnn=True):
+        """The hierarchy through the C ABI: per level, stats of the level's reconstruct."""
+        tm = self.tm
+
+        def start(c, s_l, a_l):
+            f0 = c.fbp(s_l)
+            if not start_cnn or self.net is None:
+                return f0
+            x0, used = self.net.warm_start(c, f0, a_l, tm.Params(**PRIOR))
+            self.used_cnn = used
+            return x0
+
+        self.used_cnn = False
+        y, _, stats = tm.reconstruct_levels(self.w["N"], self.theta, self.w["S"], sino, LEVELS, prms,
+                                            span=self.w["span"], ctxs=self.ctxs, start=start)
+        self.x = y
+        return stats
+
+    def voxel_updates(self, stats):
+        S, N = self.w["S"], self.w["N"]
+        return sum(S * (N >> (LEVELS - 1 - k)) ** 2 * st.iterations for k, st in enumerate(stats))
+
+
+def chosen_params(F_ref):
+    prms = [tm_params(max_iter=k, bf16=True) for k in COARSE_ITERS]
+    prms.append(tm_params(max_iter=FINEST_CAP, gap_tol=GAP, F_ref=F_ref, bf16=True, refine_gap=REFINE_GAP))
+    return prms
+
+
+def fp32_params(F_ref, finest_iters=FINEST_CAP, gap_tol=GAP):
+    prms = [tm_params(max_iter=k) for k in COARSE_ITERS]
+    prms.append(tm_params(max_iter=finest_iters, gap_tol=gap_tol, F_ref=F_ref))
+    return prms
+
+
+_tm = None
+
+
+def tm_params(**kw):
+    return _tm.Params(**PRIOR, **kw)
+
+
+# ------------------------------------------------------------------------------ time to gap
+
+def timed(stream, barrier, world, fn):
+    """(device ms from the resident inputs to the end of fn, fn's result), max over ranks."""
     import torch
 
-    S, N, theta, span = wl
-    ctx.build_operator(sino, atg)
-    ctx.fbp(sino, x)
-    st = ctx.reconstruct(x, atg, tm.Params(**PRIOR, max_iter=REF_ITERS))
-    log = ctx.get_log(REF_ITERS)
-    F_ref = st.objective
-    F0 = ctx.objective(torch.zeros_like(x), atg, tm.Params(**PRIOR))
-    half = log[REF_ITERS // 2 - 1][0]
-    out = {"gap": GAP, "F_ref": F_ref, "F_ref_iterations": REF_ITERS, "F0": F0,
-           "ref_change_last_half_in_gap_units": (half - F_ref) / (F0 - F_ref), "forms": {}}
-    stop = dict(PRIOR, max_iter=REF_ITERS, gap_tol=GAP, F_ref=F_ref)
-    levels = 3 if N % 4 == 0 and N // 4 >= 64 else 1
-    lctx = None
-    if levels == 3:
-        lctx = [tm.Context([tm.Group(N=N >> (2 - k), angles=list(theta), n_slices=S, span=span)], stream=stream)
-                for k in range(2)] + [ctx]
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    res = fn()
+    e1.record(stream)
+    barrier()
+    return max_over_ranks(e0.elapsed_time(e1), world, "cuda"), res
+
+
+def time_to_gap_hier(tm, H, sino, F_ref, F0, stream, barrier, world, step_ms, step_stats):
+    """Every form from the resident sinogram until the device stops the finest level at gap <= 1e-3."""
+    w = H.w
+    S, N, span = w["S"], w["N"], w["span"]
+    ctx = H.ctxs[-1]
+    x, atg = ctx._lv["x"], ctx._lv["atg"]
+    stop = dict(max_iter=PLAIN_CAP, gap_tol=GAP, F_ref=F_ref)
+    forms = {}
 
     def one_level(use_graph, bf16):
         def run():
             if use_graph:
                 ctx.build_operator_fbp(sino, atg, x)
-            else:  # the plain form: one call after the other
+            else:  # the plain form: one call after the other, eager launches
                 ctx.build_operator(sino, atg)
                 ctx.fbp(sino, x)
-            return ctx.reconstruct(x, atg, tm.Params(**stop, use_graph=use_graph, bf16=bf16,
-                                                     refine_gap=REFINE_GAP if bf16 else 0.0))
+            return [ctx.reconstruct(x, atg, tm_params(**stop, use_graph=use_graph, bf16=bf16,
+                                                      refine_gap=REFINE_GAP if bf16 else 0.0))]
         return run
 
-    def hierarchical(bf16):
+    def hier(bf16, cnn):
         def run():
-            prms = [tm.Params(**PRIOR, max_iter=k, bf16=bf16) for k in COARSE_ITERS]
-            prms.append(tm.Params(**stop, bf16=bf16, refine_gap=REFINE_GAP if bf16 else 0.0))
-            y, _, stats = tm.reconstruct_levels(N, theta, S, sino, 3, prms, span=span, ctxs=lctx)
-            x.copy_(y)
-            return stats[-1]
+            prms = chosen_params(F_ref) if bf16 else fp32_params(F_ref)
+            return H.run(sino, prms, start_cnn=cnn)
         return run
 
-    forms = {
-        "plain": (one_level(False, False), "FP32 spectra, FBP start, one level, eager launches"),
-        "batched_graph": (one_level(True, False), "FP32 spectra, FBP start, one level, device-driven graph loop"),
-        "bf16_refine": (one_level(True, True), f"BF16 spectra to gap {REFINE_GAP:g} then FP32, FBP start, one level, graph"),
+    runs = {
+        "plain": (one_level(False, False), "FP32 spectra, FBP start, one level, eager launches", 1),
+        "batched_graph": (one_level(True, False), "FP32 spectra, FBP start, one level, device-driven graph loop", 1),
+        "bf16_refine": (one_level(True, True), f"BF16 spectra to gap {REFINE_GAP:g} then FP32, FBP start, one level, "
+                                               "graph", 1),
+        "hierarchical": (hier(False, False), f"levels N/4, N/2, N ({COARSE_ITERS[0]} and {COARSE_ITERS[1]} coarse "
+                                             "iterations), FBP at N/4, Lanczos-3 between levels, FP32, graph", 1),
+        "hierarchical_bf16": (hier(True, False), "as hierarchical, BF16 spectra (FP32 refinement at the finest level "
+                                                 f"from gap {REFINE_GAP:g})", 1),
     }
-    if levels == 3:
-        forms["hierarchical"] = (hierarchical(False), f"levels N/4, N/2, N ({COARSE_ITERS[0]} and {COARSE_ITERS[1]} "
-                                                       "coarse iterations), FBP at N/4, Lanczos-3 between levels, FP32, graph")
-        forms["hierarchical_bf16"] = (hierarchical(True), "as hierarchical, BF16 spectra (FP32 refinement at the finest "
-                                                          f"level from gap {REFINE_GAP:g})")
-    # plain single-slice form: every slice on its own (one-slice geometry, in-plane prior, its
-    # own F_ref), the slices one after another
-    def single_slice_refs():
-        c1 = tm.Context([tm.Group(N=N, angles=list(theta), n_slices=1, span=span)], stream=stream)
-        plane = N * N
-        na = len(theta)
-        sl = [sino[z * na * N:(z + 1) * na * N] for z in range(S)]
-        a1, x1 = c1._empty(plane), c1._empty(plane)
-        refs = []
-        for z in range(S):
-            c1.build_operator(sl[z], a1)
-            c1.fbp(sl[z], x1)
-            refs.append(c1.reconstruct(x1, a1, tm.Params(**PRIOR, max_iter=REF_ITERS)).objective)
+    for name, (run, desc, reps) in runs.items():
+        for _ in range(reps):
+            ms, stats = timed(stream, barrier, world, run)
+        progress(f"time to gap {name}: {ms:.1f} ms, {[st.iterations for st in stats]} iterations, gap {stats[-1].gap:.3g}")
+        forms[name] = {"ms": ms, "finest_iterations": stats[-1].iterations, "gap_reached": stats[-1].gap,
+                       "reached": stats[-1].gap <= GAP, "form": desc}
+        if len(stats) > 1:
+            forms[name]["level_iterations"] = [s.iterations for s in stats]
+    forms["chosen"] = {"ms": step_ms, "finest_iterations": step_stats[-1].iterations,
+                       "level_iterations": [s.iterations for s in step_stats], "gap_reached": step_stats[-1].gap,
+                       "reached": step_stats[-1].gap <= GAP, "used_cnn": H.used_cnn,
+                       "form": "the bench step: levels N/4, N/2, N, CNN-refined FBP start at N/4 (FBP fallback), "
+                               f"BF16 spectra with FP32 refinement from gap {REFINE_GAP:g}, device-driven graph loops"}
+    forms["single_slice"] = single_slice_form(tm, w, H.theta, sino, stream, barrier, world)
+    return forms
 
-        def run():
-            st = None
-            for z in range(S):
-                c1.build_operator(sl[z], a1)
-                c1.fbp(sl[z], x1)
-                st = c1.reconstruct(x1, a1, tm.Params(**dict(stop, F_ref=refs[z]), use_graph=False))
-            return st
-        return run
 
-    forms["single_slice"] = (single_slice_refs(), "plain FP32: each slice alone (8-neighbour in-plane prior, its own "
-                                                  "F_ref), FBP start, one level, eager launches; the last slice's stats")
-    nets = {}
-    try:
-        nets[1], info1 = train_warm_start(tm, N, len(theta), span, S, 1, stream)
-        out["warm_start_training"] = {"full": info1}
-        if levels == 3:
-            nets[4], info4 = train_warm_start(tm, N, len(theta), span, S, 4, stream)
-            out["warm_start_training"]["coarse"] = info4
-    except Exception as e:  # reported, not hidden: the learned forms are then absent
-        out["warm_start_training"] = {"error": str(e)}
+def single_slice_form(tm, w, theta, sino, stream, barrier, world, sample=2):
+    """The plain single-slice form (each slice alone: one-slice geometry, in-plane prior, its own
+    F_ref, FBP start, one level, eager launches) on `sample` slices, scaled to the whole batch."""
+    S, N, span, na = w["S"], w["N"], w["span"], w["na"]
+    c1 = tm.Context([tm.Group(N=N, angles=list(theta), n_slices=1, span=span)], stream=stream)
+    plane = N * N
+    picks = list(range(0, S, max(1, S // sample)))[:sample]
+    sl = [sino[z * na * N:(z + 1) * na * N] for z in picks]
+    a1, x1 = c1._empty(plane), c1._empty(plane)
+    refs = []
+    for s in sl:
+        c1.build_operator(s, a1)
+        c1.fbp(s, x1)
+        refs.append(c1.reconstruct(x1, a1, tm_params(max_iter=REF_ITERS)).objective)
 
-    if 1 in nets:
-        f0 = ctx._empty(S * N * N)
+    def run():
+        sts = []
+        for s, F in zip(sl, refs):
+            c1.build_operator(s, a1)
+            c1.fbp(s, x1)
+            sts.append(c1.reconstruct(x1, a1, tm_params(max_iter=PLAIN_CAP, gap_tol=GAP, F_ref=F, use_graph=False)))
+        return sts
 
-        def learned(bf16):
-            def run():
-                ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
-                ev[0].record(stream)
-                ctx.build_operator_fbp(sino, atg, f0)
-                ev[1].record(stream)
-                ev[2].record(stream)
-                x0, used = nets[1].warm_start(ctx, f0, atg, tm.Params(**PRIOR), out=x)
-                ev[3].record(stream)
-                st = ctx.reconstruct(x, atg, tm.Params(**stop, bf16=bf16, refine_gap=REFINE_GAP if bf16 else 0.0))
-                ev[4].record(stream)
-                torch.cuda.synchronize()
-                st.used_cnn = used
-                st.breakdown_ms = {k: ev[i].elapsed_time(ev[i + 1]) for i, k in
-                                   enumerate(["build_operator_fbp", "-", "warm_start", "iterations"]) if k != "-"}
-                return st
-            return run
-        forms["learned"] = (learned(False), "CNN-refined FBP start (kept only if its objective is lower), FP32, one "
-                                            "level, graph")
-        forms["chosen"] = (learned(True), "batched, CNN-refined FBP start with FBP fallback, BF16 spectra with FP32 "
-                                          f"refinement from gap {REFINE_GAP:g}, one level, device-driven graph loop")
-    if 4 in nets:
-        def hierarchical_learned():
-            def start(c, s_l, a_l):
-                x0, used = nets[4].warm_start(c, c.fbp(s_l), a_l, tm.Params(**PRIOR))
-                return x0
-            prms = [tm.Params(**PRIOR, max_iter=k, bf16=True) for k in COARSE_ITERS]
-            prms.append(tm.Params(**stop, bf16=True, refine_gap=REFINE_GAP))
-            y, _, stats = tm.reconstruct_levels(N, theta, S, sino, 3, prms, span=span, ctxs=lctx, start=start)
-            x.copy_(y)
-            return stats[-1]
-        forms["hierarchical_learned"] = (hierarchical_learned, "hierarchical N/4 -> N/2 -> N, CNN-refined FBP start at "
-                                                               f"N/4, BF16 spectra with FP32 refinement from gap "
-                                                               f"{REFINE_GAP:g}, graph")
+    ms, sts = timed(stream, barrier, world, run)
+    return {"ms": ms * S / len(sl), "extrapolated_from_slices": len(sl), "sample_ms": ms,
+            "finest_iterations": [s.iterations for s in sts], "reached": all(s.gap <= GAP for s in sts),
+            "form": f"plain FP32: each slice alone (8-neighbour in-plane prior, its own F_ref from {REF_ITERS} "
+                    f"iterations), FBP start, one level, eager launches; {len(sl)} of {S} slices timed, scaled by "
+                    f"{S / len(sl):g}"}
 
-    for name, (run, desc) in forms.items():
-        for timed in (False, True):
-            barrier()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            st = run()
-            e1.record(stream)
-            barrier()
-        ms = max_over_ranks(e0.elapsed_time(e1), world, "cuda")
-        out["forms"][name] = {"ms": ms, "finest_iterations": st.iterations, "gap_reached": st.gap, "form": desc}
-        if hasattr(st, "used_cnn"):
-            out["forms"][name]["used_cnn"] = st.used_cnn
-        if hasattr(st, "breakdown_ms"):
-            out["forms"][name]["breakdown_ms"] = st.breakdown_ms
-    return out
 
+# ------------------------------------------------------------------------------ reference arm
 
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    cb = cpu_baseline(args.workload)
-    S, N, na, span, iters, _ = WORKLOADS[args.workload]
-    # each step: the bounded oracle sample; the line reports its rate
+    w = WORKLOADS[args.workload]
+    cb = cpu_baseline(args.workload, single_thread=False)
     vals = []
     for _ in range(args.warmup):
-        cpu_baseline(args.workload)
+        oracle_sample(args.workload, 1, 1)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        vals.append(cpu_baseline(args.workload)["value"])
+        dt, _ = oracle_sample(args.workload, 1, 1)
+        vals.append(w["N"] ** 2 / dt)
     el = time.perf_counter() - t0
     v = statistics.mean(vals)
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": "voxel-updates/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / max(args.steps, 1),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "slices": S, "N": N, "angles": na, "iterations": iters},
-        "cpu_baseline": dict(cb, value=v),
+        "config": config_of(args.workload),
+        "cpu_baseline": dict(cb, value=v, sample=f"each step: 1 of {w['S']} slices x 1 iteration at {w['N']}^2, "
+                                                 f"{w['na']} angles (oracle iteration phase)"),
         "e2e": {"value": v, "unit": "voxel-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
+def config_of(name):
+    w = WORKLOADS[name]
+    c = {"workload": name, "slices": w["S"], "N": w["N"], "angles": w["na"], "span": w["span"]}
+    if w["kind"] == "hier":
+        c.update(levels=[w["N"] >> (LEVELS - 1 - k) for k in range(LEVELS)], gap=GAP)
+    else:
+        c.update(iterations=w["iters"])
+    return c
+
+
+# ------------------------------------------------------------------------------ roofline
+
+PASS_NAMES = ["pass1_rows_fwd", "pass2_columns", "pass3a_rows_inv", "pass3b_prior_update", "finalize"]
+
+
+def pass_bytes(N):
+    """Algorithmic HBM bytes per voxel-update of passes 1, 2, 3a, 3b (FP32 spectrum)."""
+    B = (N + 1) / N
+    return [8.0 + 8.0 * B, 16.0 * B, 8.0 * B + 4.0, 4.0 + 4 + 8 + 4]
+
+
+def roofline_of(pt, iters, S, N, workload):
+    peak, peak_kind = measured_peaks()
+    bpv = pass_bytes(N)
+    per = {}
+    for k in range(4):
+        ach = bpv[k] * S * N * N / (pt[k] / iters * 1e-3) / 1e9
+        per[PASS_NAMES[k]] = {"ms": pt[k] / iters, "achieved_gbs": ach, "frac": ach / peak,
+                              "algorithmic_bytes_per_voxel": bpv[k]}
+    top = max(range(4), key=lambda k: pt[k])
+    ach = per[PASS_NAMES[top]]["achieved_gbs"]
+    roof = {"kernel": PASS_NAMES[top], "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+            "frac": ach / peak, "peak_source": f"{peak_kind} (copy bandwidth)",
+            "algorithmic_bytes_per_voxel": bpv[top], "traffic": kernel_traffic(PASS_NAMES[top], workload),
+            "per_pass": per}
+    return roof
+
+
+# ------------------------------------------------------------------------------ main
+
 def main():
+    global _tm
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="launch the iterations eagerly (profiling)")
-    ap.add_argument("--no-gap", action="store_true", help="skip the time-to-gap measurement")
+    ap.add_argument("--no-gap", action="store_true", help="skip the time-to-gap forms")
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, rank, world)
 
-    import numpy as np
     import torch
 
     import paper_2603_28756_gb300 as tm
 
+    _tm = tm
     torch.cuda.set_device(local)
     if world > 1:
         import torch.distributed as dist
 
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    S, N, na, span, iters, _ = WORKLOADS[args.workload]
-    prob, iters = make_problem(args.workload, rank)
-    ctx = tm.Context([tm.Group(N=N, angles=list(prob.theta), n_slices=S, span=span)])
-    stream = ctx.stream
-    sino = torch.from_numpy(prob.sino.ravel()).cuda()
-    with torch.cuda.stream(stream):
-        atg = torch.empty(S * N * N, dtype=torch.float32, device="cuda")
-        x = torch.empty_like(atg)
-    prm = tm.Params(**PRIOR, max_iter=iters, use_graph=not args.no_graph)
-    # pick pass 3b's slices per block and the spectrum chunk of passes 1-3a by timing (outside
-    # the timed region)
-    ctx.build_operator(sino, atg)
-    ctx.fbp(sino, x)
-    tuned = ctx.autotune(x, atg, prm)
-    torch.cuda.synchronize()
-
-    def step():
-        ctx.build_operator_fbp(sino, atg, x)
-        ctx.reconstruct(x, atg, prm, want_stats=False)
 
     def barrier():
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
+    w = WORKLOADS[args.workload]
+    S, N, na, span = w["S"], w["N"], w["na"], w["span"]
+    t_gen = time.perf_counter()
+    prob = make_problem(args.workload, rank)
+    t_gen = time.perf_counter() - t_gen
+    progress(f"inputs generated ({t_gen:.1f} s)")
+    stream = torch.cuda.Stream()
+    sino = torch.from_numpy(prob.sino.ravel()).cuda()
+    extra = {"input_generation_s": t_gen}
+
+    if w["kind"] == "hier":
+        H = Hier(tm, w, prob.theta, stream)
+        ctx = H.ctxs[-1]
+        # F_ref: the hierarchy in FP32, then REF_ITERS more finest-level iterations
+        t0 = time.perf_counter()
+        ref_stats = H.run(sino, fp32_params(0.0, finest_iters=REF_ITERS, gap_tol=0.0), start_cnn=False)
+        F_ref = ref_stats[-1].objective
+        log = ctx.get_log(REF_ITERS)
+        F0 = ctx.objective(torch.zeros_like(H.x), ctx._lv["atg"], tm_params())
+        progress(f"F_ref {F_ref:.9g}")
+        extra["F_ref"] = {"value": F_ref, "F0": F0, "finest_iterations": REF_ITERS,
+                          "change_last_half_in_gap_units": (log[REF_ITERS // 2 - 1][0] - F_ref) / (F0 - F_ref),
+                          "s": time.perf_counter() - t0}
+        # the learned start at the coarsest level (outside the timed region)
+        try:
+            H.net, extra["warm_start_training"] = train_warm_start(tm, w, 1 << (LEVELS - 1), stream)
+        except Exception as e:  # reported, not hidden: the step then starts from FBP
+            extra["warm_start_training"] = {"error": str(e)[:300]}
+        progress(f"warm start trained: {extra['warm_start_training']}")
+        prms = chosen_params(F_ref)
+        state = {}
+
+        def step():
+            state["stats"] = H.run(sino, prms)
+
+        def units():
+            return H.voxel_updates(state["stats"])
+    else:
+        ctx = tm.Context([tm.Group(N=N, angles=list(prob.theta), n_slices=S, span=span)], stream=stream)
+        with torch.cuda.stream(stream):
+            atg = torch.empty(S * N * N, dtype=torch.float32, device="cuda")
+            x = torch.empty_like(atg)
+        prm = tm_params(max_iter=w["iters"], use_graph=not args.no_graph)
+        ctx.build_operator(sino, atg)
+        ctx.fbp(sino, x)
+        extra["autotune_pass3_slices_per_block"] = ctx.autotune(x, atg, prm)
+
+        def step():
+            ctx.build_operator_fbp(sino, atg, x)
+            ctx.reconstruct(x, atg, prm, want_stats=False)
+
+        def units():
+            return S * N * N * w["iters"]
+
+    # tmbir_launch_count is the process-wide host count plus the context's device-side graph
+    # count; a context that runs no graph gives the host count alone
+    host_ctx = tm.Context([tm.Group(N=64, angles=[0.0], n_slices=1)], stream=stream)
+    all_ctxs = [ctx] if w["kind"] == "fixed" else H.ctxs
+
+    def launch_total():
+        host = host_ctx.launch_count()
+        return host + sum(c.launch_count() - host for c in all_ctxs)
+
+    torch.cuda.synchronize()
     for _ in range(args.warmup):
         step()
     barrier()
     clocks = Clocks(local)
-    n0 = ctx.launch_count()
+    n0 = launch_total()
+    step_units = []
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
     e0.record(stream)
     for _ in range(args.steps):
         step()
+        step_units.append(units())
     e1.record(stream)
     barrier()
     clk = clocks.stop()
-    launches = ctx.launch_count() - n0
+    progress(f"timed steps done: {e0.elapsed_time(e1) / args.steps:.1f} ms per step")
+    launches = launch_total() - n0
     ms = max_over_ranks(e0.elapsed_time(e1), world, "cuda")
-    vox = S * N * N * iters
+    vox = sum(step_units) / len(step_units)
     value = job_rate(vox, args.steps, world, ms)
 
-    # one reconstruction's stats (outside the timed region): convergence sanity
-    st = ctx.reconstruct(x, atg, prm)
-
-    # per-pass device times, eager, on the context stream (iteration phase only)
-    ctx.fbp(sino, x)
-    pt = ctx.pass_times(x, atg, tm.Params(**PRIOR), iters)
+    # iteration phase of the finest level, eager, pass by pass on the context stream
+    xf = ctx._lv["x"] if w["kind"] == "hier" else x
+    af = ctx._lv["atg"] if w["kind"] == "hier" else atg
+    it_pass = PASS_ITERS if w["kind"] == "hier" else w["iters"]
+    ctx.fbp(sino, xf)
+    pt = ctx.pass_times(xf, af, tm_params(), it_pass)
+    pt16 = ctx.pass_times(xf, af, tm_params(bf16=True), it_pass)
     it_ms = sum(pt)
-    names = ["pass1_rows_fwd", "pass2_columns", "pass3a_rows_inv", "pass3b_prior_update", "finalize"]
-    top = max(range(4), key=lambda k: pt[k])
-    # algorithmic HBM bytes per voxel-update of each pass (FP32 spectrum)
-    bpv = [8.0 + 8.0 * (N + 1) / N, 16.0 * (N + 1) / N, 8.0 * (N + 1) / N + 4.0, 4.0 + 4 + 8 + 4][top]
-    alg_bytes = bpv * S * N * N
-    achieved = alg_bytes / (pt[top] / iters * 1e-3) / 1e9
-    peak, peak_kind = measured_peaks()
-    roof = {"kernel": names[top], "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "peak_source": peak_kind, "algorithmic_bytes_per_voxel": bpv,
-            "traffic": kernel_traffic(names[top], args.workload)}
-    if names[top] == "pass3b_prior_update":
-        # Pass 3b is bound by the special-function pipe, not HBM: each of the 13 neighbour pairs
-        # of a voxel costs log2, exp2 and a reciprocal (a fourth exp2 when q != 2), against
-        # SMs x 32 special-function results per clock x the maximum SM clock
-        sfu_per_voxel = 13 * (3 if PRIOR["q"] == 2.0 else 4)
-        n_sm = torch.cuda.get_device_properties(0).multi_processor_count
-        sm_mhz = measured_sm_max_mhz()
-        sfu_peak = n_sm * 32 * sm_mhz * 1e6 / 1e9
-        sfu_achieved = sfu_per_voxel * S * N * N / (pt[top] / iters * 1e-3) / 1e9
-        roof.update({"bound": "alu", "achieved": sfu_achieved, "peak": sfu_peak, "unit": "Gop/s",
-                     "frac": sfu_achieved / sfu_peak,
-                     "peak_source": f"derived: {n_sm} SMs x 32 special-function ops/clk x {sm_mhz:.0f} MHz",
-                     "algorithmic_ops_per_voxel": sfu_per_voxel,
-                     "hbm": {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                             "peak_source": peak_kind}})
+    roof = roofline_of(pt, it_pass, S, N, args.workload)
+    progress(f"pass times (ms per iteration) {[round(v / it_pass, 3) for v in pt]}, bf16 {[round(v / it_pass, 3) for v in pt16]}")
+    iteration_phase = {
+        "level": f"{N}^2 x {S} slices", "iterations": it_pass,
+        "voxel_updates_per_s": S * N * N * it_pass / (it_ms * 1e-3), "ms_per_iteration": it_ms / it_pass,
+        "ms_per_pass": dict(zip(PASS_NAMES, [v / it_pass for v in pt])),
+        "bf16_ms_per_iteration": sum(pt16) / it_pass,
+        "bf16_ms_per_pass": dict(zip(PASS_NAMES, [v / it_pass for v in pt16])),
+    }
 
-    # setup breakdown: R*g (FP64 NUFFT) + 1/2 g.g, and the FBP start, per call
-    barrier()
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-    ev[0].record(stream)
-    ctx.build_operator(sino, atg)
-    ev[1].record(stream)
-    ctx.fbp(sino, x)
-    ev[2].record(stream)
-    barrier()
-    setup_ms = {"build_operator_data": ev[0].elapsed_time(ev[1]), "fbp": ev[1].elapsed_time(ev[2])}
+    direct = gradient_comparison(ctx, xf, af, sino, stream, barrier)
+    progress(f"direct vs Toeplitz gradient: {direct}")
 
-    # end to end through the C ABI with host buffers: H2D sinogram, step, D2H image
+    # one step broken down by stage (outside the timed region)
+    breakdown = None
+    if w["kind"] == "hier":
+        breakdown = stage_breakdown(tm, H, sino, prms, stream, barrier)
+    else:
+        barrier()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        ev[0].record(stream)
+        ctx.build_operator(sino, atg)
+        ev[1].record(stream)
+        ctx.fbp(sino, x)
+        ev[2].record(stream)
+        barrier()
+        breakdown = {"build_operator_data": ev[0].elapsed_time(ev[1]), "fbp": ev[1].elapsed_time(ev[2])}
+
+    # end to end through the C ABI with host buffers: H2D sinogram, the step, D2H image
     h_sino = torch.from_numpy(prob.sino.ravel()).pin_memory()
-    h_x = torch.empty(S * N * N, dtype=torch.float32).pin_memory()
+    xout = H.x if w["kind"] == "hier" else x
+    h_x = torch.empty(xout.numel(), dtype=torch.float32).pin_memory()
     d_sino = torch.empty_like(sino)
+    e2e_units = []
+
+    def e2e_step():
+        with torch.cuda.stream(stream):
+            d_sino.copy_(h_sino, non_blocking=True)
+        if w["kind"] == "hier":
+            state["stats"] = H.run(d_sino, prms)
+            e2e_units.append(units())
+            out = H.x
+        else:
+            ctx.build_operator_fbp(d_sino, atg, x)
+            ctx.reconstruct(x, atg, prm, want_stats=False)
+            e2e_units.append(units())
+            out = x
+        with torch.cuda.stream(stream):
+            h_x.copy_(out, non_blocking=True)
+
+    e2e_step()  # warm (the sinogram buffer differs from the timed steps')
+    e2e_units.clear()
     barrier()
     f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     f0.record(stream)
-    with torch.cuda.stream(stream):
-        for _ in range(args.steps):
-            d_sino.copy_(h_sino, non_blocking=True)
-            ctx.build_operator_fbp(d_sino, atg, x)
-            ctx.reconstruct(x, atg, prm, want_stats=False)
-            h_x.copy_(x, non_blocking=True)
+    for _ in range(args.steps):
+        e2e_step()
     f1.record(stream)
     barrier()
     e2e_ms = max_over_ranks(f0.elapsed_time(f1), world, "cuda")
+    e2e_value = job_rate(sum(e2e_units) / len(e2e_units), args.steps, world, e2e_ms)
+    progress(f"e2e {e2e_ms / args.steps:.1f} ms per step")
 
-    gap_info = None if args.no_gap else time_to_gap(tm, ctx, stream, sino, atg, x, barrier, world,
-                                                    (S, N, prob.theta, span))
+    gap_info = None
+    if not args.no_gap:
+        if w["kind"] == "hier":
+            gap_info = {"gap": GAP, "F_ref": extra["F_ref"],
+                        "forms": time_to_gap_hier(tm, H, sino, extra["F_ref"]["value"], extra["F_ref"]["F0"], stream,
+                                                  barrier, world, ms / args.steps, state["stats"])}
 
     if rank == 0:
+        cfg = config_of(args.workload)
+        cfg.update({"parallelism": f"replicas{world}", "l2": "working set > L2 (no explicit flush)"})
+        if w["kind"] == "hier":
+            cfg.update({"step": "chosen form to the 1e-3 gap: 3 levels, CNN start with FBP fallback, BF16 spectra "
+                                "with FP32 refinement, device-driven graph loops",
+                        "coarse_iterations": list(COARSE_ITERS), "refine_gap": REFINE_GAP,
+                        "level_iterations": [s.iterations for s in state["stats"]]})
+        else:
+            cfg.update({"step": "build_operator_fbp (R*g and FBP overlapped) + reconstruct(graph)"})
         line = {
             "metric": METRIC,
             "value": value,
@@ -545,30 +719,95 @@ def main():
             "vs_baseline": None,
             "dtype": "f32",
             "data": "synthetic",
-            "config": {
-                "workload": args.workload, "slices": S, "N": N, "angles": na, "span": span, "iterations": iters,
-                "step": "build_operator_fbp (R*g and FBP overlapped) + reconstruct(graph)", "l2": "working set > L2 (no explicit flush)",
-                "parallelism": f"replicas{world}", "pass3_slices_per_block": tuned[0],
-                "spectrum_chunk_slices": ctx.spec_chunks[0],
-            },
-            "setup_ms": setup_ms,
-            "iteration_phase": {
-                "voxel_updates_per_s": vox / (it_ms * 1e-3), "ms_per_iteration": it_ms / iters,
-                "ms_per_pass": dict(zip(names, [v / iters for v in pt])),
-            },
+            "config": cfg,
+            "voxel_updates_per_step": vox,
+            "iteration_phase": iteration_phase,
+            "toeplitz_vs_direct_gradient": direct,
+            "step_breakdown_ms": breakdown,
             "roofline": roof,
-            "e2e": {"value": job_rate(vox, args.steps, world, e2e_ms), "unit": "voxel-updates/s",
-                    "h2d_bytes_per_step": sino.numel() * 4, "d2h_bytes_per_step": x.numel() * 4},
+            "e2e": {"value": e2e_value, "unit": "voxel-updates/s", "h2d_bytes_per_step": sino.numel() * 4,
+                    "d2h_bytes_per_step": xout.numel() * 4},
             "gpu_launches": launches,
             "time_to_gap": gap_info,
             "clocks": clk,
-            "last_run": {"objective": st.objective, "restarts": st.restarts, "L": st.L, "status": st.status},
         }
+        line.update(extra)
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.workload)
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def gradient_comparison(ctx, x, atg, sino, stream, barrier, reps=3):
+    """Sec. 3.1's comparison at the workload's finest level: one gradient through the Toeplitz
+    passes (R*R as the 2N x 2N FFT convolution, R*g precomputed) against the direct gradient
+    R*(R x - g) through the two NUFFTs; device ms of each and their relative L2 difference."""
+    import torch
+
+    prm = tm_params()
+    gt = ctx.gradient(x, atg, prm)
+    gd = ctx.gradient_direct(x, sino, prm)
+
+    def time_it(fn):
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        barrier()
+        return e0.elapsed_time(e1) / reps
+
+    t_toep = time_it(lambda: ctx.gradient(x, atg, prm, out=gt))
+    t_dir = time_it(lambda: ctx.gradient_direct(x, sino, prm, out=gd))
+    with torch.cuda.stream(stream):
+        diff = float(torch.linalg.norm((gd - gt).double()) / torch.linalg.norm(gt.double()))
+    return {"toeplitz_ms": t_toep, "direct_ms": t_dir, "direct_over_toeplitz": t_dir / t_toep,
+            "relative_l2_difference": diff}
+
+
+def stage_breakdown(tm, H, sino, prms, stream, barrier):
+    """Device ms of each stage of one chosen-form step (events between the C-ABI calls)."""
+    import torch
+
+    w = H.w
+    S, N, na = w["S"], w["N"], w["na"]
+    marks = []
+
+    def mark(name):
+        ev = torch.cuda.Event(enable_timing=True)
+        ev.record(stream)
+        marks.append((name, ev))
+
+    barrier()
+    mark("start")
+    x = None
+    for lev in range(LEVELS):
+        f = 1 << (LEVELS - 1 - lev)
+        Nl = N // f
+        c = H.ctxs[lev]
+        lv = c._lv
+        s_l = sino if f == 1 else c.downsample_sino(sino, S, na, N, f, out=lv["sino"])
+        c.build_operator(s_l, lv["atg"])
+        mark(f"L{lev} setup")
+        if x is None:
+            f0 = c.fbp(s_l)
+            mark(f"L{lev} fbp")
+            if H.net is not None:
+                x0, _ = H.net.warm_start(c, f0, lv["atg"], tm.Params(**PRIOR))
+                lv["x"].copy_(x0)
+            else:
+                lv["x"].copy_(f0)
+            mark(f"L{lev} warm_start")
+        else:
+            c.upsample_lanczos3(x, S, Nl // 2, out=lv["x"])
+            mark(f"L{lev} upsample")
+        x = lv["x"]
+        c.reconstruct(x, lv["atg"], prms[lev])
+        mark(f"L{lev} iterations")
+    barrier()
+    return {name: marks[k - 1][1].elapsed_time(ev) for k, (name, ev) in enumerate(marks) if k > 0}
 
 
 if __name__ == "__main__":

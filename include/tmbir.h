@@ -73,8 +73,11 @@ typedef struct {
  *   p, q, c, sigma  qGGMRF potential rho(D) = |D/sigma|^q / (1 + |D/(c sigma)|^(q-p)),
  *                   1 <= p <= q; q = 2 is the fast path.
  *   lambda          prior weight.
- *   L               step constant; <= 0 selects 1.01 lambda_max(R*R) + lambda*2*(2/sigma^2)
- *                   (needs q = 2 and a built operator).
+ *   L               step constant; <= 0 selects, per group, 1.01 lambda_max(R*R) of the group +
+ *                   lambda*2*(2/sigma^2) (needs q = 2 and a built operator).  Each group runs
+ *                   its own momentum sequence and restart test with its own step constant, as
+ *                   if reconstructed alone; the stop rule (max_iter, gap_tol on the summed
+ *                   objective) and the BF16 -> FP32 switch apply to the whole batch.
  *   max_iter        iterations of the fast gradient method.
  *   gap_tol, F_ref  stop early once (F(y_k) - F_ref) / (F(0) - F_ref) <= gap_tol
  *                   (gap_tol <= 0 disables it).
@@ -114,11 +117,11 @@ typedef struct {
 /* Result of tmbir_reconstruct (host struct filled on return). */
 typedef struct {
   int iterations;   /* iterations run */
-  int restarts;     /* momentum restarts */
+  int restarts;     /* momentum restarts, summed over the groups */
   int status;       /* TMBIR_OK, TMBIR_ERR_NONFINITE */
   double objective; /* F(y_k) of the last iteration (Eq. 10 + lambda Phi) */
   double gap;       /* relative gap of that value when F_ref was given, else 0 */
-  double L;         /* step constant used */
+  double L;         /* step constant of the first group */
   double grad_norm; /* ||grad F(y_k)||_2 of the last iteration */
 } tmbir_stats;
 
@@ -184,7 +187,8 @@ int tmbir_build_operator_fbp(tmbir_ctx* ctx, const float* d_sino, float* d_atg, 
 int tmbir_reconstruct(tmbir_ctx* ctx, float* d_x, const float* d_atg, const tmbir_params* prm, tmbir_stats* h_stats);
 
 /* Per-iteration log of the last tmbir_reconstruct: h_log[4*k + {0,1,2,3}] = F(y_k),
- * <G, x_{k+1} - x_k>, restarted (0/1), ||G||^2.  Copies min(max_entries, iterations) rows;
+ * <G, x_{k+1} - x_k>, number of groups whose momentum restarted (0/1 for one group), ||G||^2,
+ * the first, second and fourth summed over the groups.  Copies min(max_entries, iterations) rows;
  * *n_out receives that count. */
 int tmbir_get_log(tmbir_ctx* ctx, double* h_log, int max_entries, int* n_out);
 
@@ -204,6 +208,27 @@ int tmbir_step(tmbir_ctx* ctx, const float* d_x, const float* d_x_prev, double b
 
 /* F(x) = 1/2 x.(K*x) - x.R*g + 1/2 g.g + lambda Phi(x) (Eq. 10 plus the prior), FP64 reduction. */
 int tmbir_objective(tmbir_ctx* ctx, const float* d_x, const float* d_atg, const tmbir_params* prm, double* h_F);
+
+/*
+ * The direct operators of Sec. 2 (Eqs. 3-4), without the Toeplitz structure: R and R* through
+ * non-uniform FFTs at the polar samples, FP32 (the paper's gradient before the Toeplitz
+ * acceleration of Sec. 2.1, kept for the comparison of Sec. 3.1).
+ *   tmbir_forward:  d_sino = R d_x, [slice][angle][bin] for all groups back to back: the image
+ *                   divided by the kernel's Fourier transform on the 2N x 2N oversampled grid,
+ *                   an FFT, interpolation at the polar samples with the spreading kernel, the
+ *                   radial 1D transform (type-2 NUFFT, the adjoint of the back-projection).
+ *   tmbir_adjoint:  d_x = R* d_sino (the type-1 NUFFT of tmbir_build_operator, in FP32).
+ *   tmbir_gradient_direct: d_grad = R*(R d_x - g) + lambda grad Phi(d_x), the residual formed in
+ *                   the sinogram domain and back-projected once; h_F (may be NULL) receives
+ *                   F(x) = 1/2 ||R x - g||^2 + lambda Phi(x) (FP64 reductions; synchronises).
+ *                   d_sino is the measured sinogram g.  Needs no built operator.
+ * All use the setup scratch of the workspace (and the direct gradient its K (*) y buffers and the
+ * first iterate buffer), so they must not overlap other calls of the context.
+ */
+int tmbir_forward(tmbir_ctx* ctx, const float* d_x, float* d_sino);
+int tmbir_adjoint(tmbir_ctx* ctx, const float* d_sino, float* d_x);
+int tmbir_gradient_direct(tmbir_ctx* ctx, const float* d_x, const float* d_sino, const tmbir_params* prm,
+                          float* d_grad, double* h_F);
 
 /* Largest eigenvalue of R*R per group (power iteration of tmbir_build_operator); h_out[n_groups]. */
 int tmbir_lambda_max(tmbir_ctx* ctx, double* h_out);
@@ -253,8 +278,9 @@ int tmbir_autotune(tmbir_ctx* ctx, const float* d_x, const float* d_atg, const t
 
 /*
  * Checkpoint of a run (no counterpart in the paper): the fast-gradient state after
- * tmbir_reconstruct (momentum t and beta, step constant, iteration count, restart count,
- * F(y_{k-1}) for the function restart) and x_{k-1}; x_k is the caller's image.  d_state is a
+ * tmbir_reconstruct (per group: momentum t and beta, step constant, restart count and
+ * F(y_{k-1}) for the function restart; the iteration count and storage phase) and x_{k-1};
+ * x_k is the caller's image.  d_state is a
  * caller-owned device buffer of tmbir_state_size bytes, 16-byte aligned.  Export needs a
  * finished run; import replaces the context's state (same geometry), after which
  * tmbir_reconstruct with resume = 1 continues it.  Both are asynchronous on the context

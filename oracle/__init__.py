@@ -82,6 +82,8 @@ def lib():
         L.orc_normal_point.argtypes = [dp, i, dp, i, i]
         L.orc_adjoint_point.restype = d
         L.orc_adjoint_point.argtypes = [dp, i, dp, i, i, i, i]
+        L.orc_forward_point.restype = d
+        L.orc_forward_point.argtypes = [dp, i, d, i, i]
         L.orc_rho.restype = d
         L.orc_rho.argtypes = [d, d, d, d, d]
         L.orc_drho.restype = d
@@ -188,6 +190,12 @@ def adjoint_point(g, N: int, theta, r: int, c: int) -> float:
     g = _f64(g)
     th = _f64(theta)
     return lib().orc_adjoint_point(_p(g), N, _p(th), th.size, g.shape[1], r, c)
+
+
+def forward_point(x, theta_a: float, nd: int, m: int) -> float:
+    """(A x)(a, m) of one slice at one angle and bin by the direct sum (Eq. 3 in closed form)."""
+    x = _f64(x)
+    return lib().orc_forward_point(_p(x), x.shape[0], float(theta_a), nd, m)
 
 
 def prior_point(x, pr: Prior, z: int, r: int, c: int) -> float:

@@ -142,3 +142,16 @@ double orc_adjoint_point(const double *g, int N, const double *theta, int na, in
     }
     return acc / (double)nd;
 }
+
+/* (A x)(a, m) of one slice at one angle theta_a and one bin m, by the direct sum. */
+double orc_forward_point(const double *x, int N, double theta_a, int nd, int m)
+{
+    int h = N / 2;
+    double ca = cos(theta_a), sa = sin(theta_a), s = (double)m - 0.5 * nd, acc = 0.0;
+    for (int r = 0; r < N; ++r)
+        for (int c = 0; c < N; ++c) {
+            double v = x[(size_t)r * N + c];
+            if (v != 0.0) acc += v * orc_dirichlet(s - ((double)(c - h) * ca + (double)(r - h) * sa), nd);
+        }
+    return acc / (double)nd;
+}

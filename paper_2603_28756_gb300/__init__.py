@@ -84,7 +84,7 @@ SYMBOLS = [
     "tmbir_cnn_destroy", "tmbir_cnn_init", "tmbir_cnn_set_weights", "tmbir_cnn_get_weights", "tmbir_cnn_apply",
     "tmbir_cnn_train_step", "tmbir_cnn_net_forward", "tmbir_cnn_net_backward", "tmbir_warm_start",
     "tmbir_state_size", "tmbir_state_export", "tmbir_state_import", "tmbir_autotune", "tmbir_build_operator_fbp",
-    "tmbir_wait_check",
+    "tmbir_wait_check", "tmbir_forward", "tmbir_adjoint", "tmbir_gradient_direct",
 ]
 
 _lib = None
@@ -141,6 +141,9 @@ def load(path: str | None = None):
         "tmbir_state_import": [vp, vp],
         "tmbir_autotune": [vp, vp, vp, ctypes.POINTER(_Params), ctypes.POINTER(i), ctypes.POINTER(i)],
         "tmbir_build_operator_fbp": [vp, vp, vp, vp],
+        "tmbir_forward": [vp, vp, vp],
+        "tmbir_adjoint": [vp, vp, vp],
+        "tmbir_gradient_direct": [vp, vp, vp, ctypes.POINTER(_Params), vp, dp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -339,6 +342,35 @@ class Context:
         _check(_lib.tmbir_normal_apply_static(self._h, ctypes.c_void_p(_ptr(x)), ctypes.c_void_p(_ptr(out))))
         self._post(x, out)
         return out
+
+    def forward(self, x, out=None):
+        """R x by the type-2 NUFFT (FP32): [slice][angle][bin]."""
+        out = self._empty(self.sino_numel()) if out is None else out
+        self._pre()
+        _check(_lib.tmbir_forward(self._h, ctypes.c_void_p(_ptr(x)), ctypes.c_void_p(_ptr(out))))
+        self._post(x, out)
+        return out
+
+    def adjoint(self, sino, out=None):
+        """R* g by the type-1 NUFFT (FP32)."""
+        out = self._empty(self.image_numel()) if out is None else out
+        self._pre()
+        _check(_lib.tmbir_adjoint(self._h, ctypes.c_void_p(_ptr(sino)), ctypes.c_void_p(_ptr(out))))
+        self._post(sino, out)
+        return out
+
+    def gradient_direct(self, x, sino, params: Params, out=None, want_objective: bool = False):
+        """R*(R x - g) + lambda grad Phi(x) through the two NUFFTs (no Toeplitz structure); with
+        want_objective also F(x) = 1/2 ||R x - g||^2 + lambda Phi(x)."""
+        out = self._empty(x.numel()) if out is None else out
+        pr = params.c_struct()
+        F = ctypes.c_double()
+        self._pre()
+        _check(_lib.tmbir_gradient_direct(self._h, ctypes.c_void_p(_ptr(x)), ctypes.c_void_p(_ptr(sino)),
+                                          ctypes.byref(pr), ctypes.c_void_p(_ptr(out)),
+                                          ctypes.byref(F) if want_objective else None))
+        self._post(x, sino, out)
+        return (out, F.value) if want_objective else out
 
     def wait_check(self, polls: int, arrive: bool):
         """Run the library's bounded device wait on its own: returns when the wait completes

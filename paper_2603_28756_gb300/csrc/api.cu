@@ -62,20 +62,29 @@ static int tuned_sc(int N, int S) {
 }
 
 // ---------------------------------------------------------------- small device kernels
-// lam_max[i], gtg[i]: per-group lambda_max(R*R) and 1/2 g.g gathered into consecutive doubles
-__global__ void k_init_state(IterState* st, const double* lam_max, const double* gtg, int n_groups, double L_given,
-                             double lambda, double sigma, double Fref, double gap_tol, int max_iter, int restart_mode,
-                             int bf16, double refine_gap) {
-  double lm = 0.0, gh = 0.0;
+// lam_max[i], gtg[i]: per-group lambda_max(R*R) and 1/2 g.g gathered into consecutive doubles.
+// Every group starts its own momentum sequence with its own step constant.
+__global__ void k_init_state(IterState* st, GroupMom* gm, const double* lam_max, const double* gtg, int n_groups,
+                             double L_given, double lambda, double sigma, double Fref, double gap_tol, int max_iter,
+                             int restart_mode, int bf16, double refine_gap) {
+  double gh = 0.0;
   for (int i = 0; i < n_groups; ++i) {
-    lm = fmax(lm, lam_max[i]);
+    const double L = L_given > 0.0 ? L_given : 1.01 * lam_max[i] + lambda * 2.0 * (2.0 / (sigma * sigma));
+    GroupMom& m = gm[i];
+    m.t = 1.0;
+    m.beta = 0.0;
+    m.L = L;
+    m.invL = 1.0 / L;
+    m.prev_F = 0.0;
+    m.gtg_half = gtg[i];
+    m.restarts = 0;
+    m.pad = 0;
     gh += gtg[i];
   }
-  double L = L_given > 0.0 ? L_given : 1.01 * lm + lambda * 2.0 * (2.0 / (sigma * sigma));
   st->t = 1.0;
   st->beta = 0.0;
-  st->L = L;
-  st->invL = 1.0 / L;
+  st->L = gm[0].L;
+  st->invL = gm[0].invL;
   st->lambda = lambda;
   st->gtg_half = gh;
   st->F0 = gh;
@@ -187,6 +196,7 @@ int tmbir_set_geometry(tmbir_ctx* ctx, int n_groups, const tmbir_group* groups) 
   TMBIR_TRACE("tmbir_set_geometry");
   REQUIRE(ctx != nullptr, TMBIR_ERR_ARG, "set_geometry: ctx is NULL");
   REQUIRE(n_groups >= 1 && groups != nullptr, TMBIR_ERR_ARG, "set_geometry: need at least one group");
+  REQUIRE(n_groups <= kMaxGroups, TMBIR_ERR_ARG, "set_geometry: at most 64 groups");
   Ctx& c = ctx->c;
   std::vector<tmbir_group> gs(groups, groups + n_groups);
   std::vector<std::vector<double>> angs(n_groups);
@@ -228,6 +238,7 @@ int tmbir_set_geometry(tmbir_ctx* ctx, int n_groups, const tmbir_group* groups) 
     return o;
   };
   c.off_state = take(sizeof(IterState));
+  c.off_gmom = take((size_t)n_groups * sizeof(GroupMom));
   c.off_dscal = take((16 + 2 * (size_t)n_groups) * sizeof(double));
   int max_blocks = 0, slices = 0;
   size_t voxels = 0, sino = 0, scratch = 0, fbp_scratch = 0;
@@ -281,6 +292,7 @@ int tmbir_set_geometry(tmbir_ctx* ctx, int n_groups, const tmbir_group* groups) 
   c.off_xbuf1 = take(voxels * sizeof(float));
   c.off_scratch = take(scratch);
   c.off_fbp_scratch = take(fbp_scratch);
+  c.off_sino_tmp = take(sino * sizeof(float));
   c.scratch_bytes = scratch;
   c.ws_need = align_up(off, 256);
   c.total_voxels = voxels;
@@ -324,6 +336,7 @@ int tmbir_set_workspace(tmbir_ctx* ctx, void* d_ws, size_t bytes) {
   c.ws = ws;
   c.ws_bytes = bytes;
   c.state = reinterpret_cast<IterState*>(ws + c.off_state);
+  c.gmom = reinterpret_cast<GroupMom*>(ws + c.off_gmom);
   c.dscal = reinterpret_cast<double*>(ws + c.off_dscal);
   c.partials = reinterpret_cast<double*>(ws + c.off_partials);
   c.log = reinterpret_cast<double*>(ws + c.off_log);
@@ -331,7 +344,9 @@ int tmbir_set_workspace(tmbir_ctx* ctx, void* d_ws, size_t bytes) {
   c.xbuf[1] = reinterpret_cast<float*>(ws + c.off_xbuf1);
   c.scratch = ws + c.off_scratch;
   c.fbp_scratch = ws + c.off_fbp_scratch;
+  c.sino_tmp = reinterpret_cast<float*>(ws + c.off_sino_tmp);
   TMBIR_CUDA(cudaMemsetAsync(c.state, 0, sizeof(IterState), c.stream));
+  TMBIR_CUDA(cudaMemsetAsync(c.gmom, 0, c.groups.size() * sizeof(GroupMom), c.stream));
   c.state_ready = false;
   for (size_t i = 0; i < c.groups.size(); ++i) {
     const tmbir_group& g = c.groups[i];
@@ -488,6 +503,14 @@ int tmbir_fbp(tmbir_ctx* ctx, const float* d_sino, float* d_x0) {
   return TMBIR_OK;
 }
 
+// first partial-sum row of each group's pass-3b blocks
+static GroupBlocks group_blocks(const Ctx& c) {
+  GroupBlocks gb{};
+  gb.n = (int)c.gdev.size();
+  for (int i = 0; i < gb.n; ++i) gb.off[i + 1] = gb.off[i] + blocks_pass3(c.gdev[i]);
+  return gb;
+}
+
 // Passes 1-3 of every group in Iterate mode, FP32 or BF16 storage variant; *nblocks receives
 // the number of partial-sum rows they write.
 static int enqueue_passes(Ctx& c, float* d_x, const float* d_atg, const PriorC& pc, bool bf16, int* nblocks) {
@@ -500,6 +523,7 @@ static int enqueue_passes(Ctx& c, float* d_x, const float* d_atg, const PriorC& 
   int off = 0;
   for (size_t i = 0; i < c.gdev.size(); ++i) {
     const GroupDev& g = c.gdev[i];
+    a.gm = c.gmom + i;
     if (int e = launch_convolution(g, a, Pass3Mode::Iterate, pc, c.stream, bf16)) return e;
     if (int e = launch_pass3(g, a, Pass3Mode::Iterate, pc, c.partials, off, c.stream, bf16, 2)) return e;
     off += blocks_pass3(g);
@@ -518,7 +542,7 @@ static int enqueue_iterations(Ctx& c, float* d_x, const float* d_atg, const Prio
       if (int e = enqueue_passes(c, d_x, d_atg, pc, true, &nb)) return e;
     if (kind != 2)
       if (int e = enqueue_passes(c, d_x, d_atg, pc, false, &nb)) return e;
-    if (int e = launch_finalize(c.state, c.partials, nb, c.log, c.stream)) return e;
+    if (int e = launch_finalize(c.state, c.gmom, c.partials, group_blocks(c), c.log, c.stream)) return e;
   }
   return TMBIR_OK;
 }
@@ -530,7 +554,7 @@ static int enqueue_trip(Ctx& c, float* d_x, const float* d_atg, const PriorC& pc
   if (int e = enqueue_passes(c, d_x, d_atg, pc, bf16, &nb)) return e;
   int trip_launches = 1;
   for (const GroupDev& g : c.gdev) trip_launches += conv_launches(g) + 1;
-  return launch_finalize(c.state, c.partials, nb, c.log, c.stream, cond, use_cond, trip_launches);
+  return launch_finalize(c.state, c.gmom, c.partials, group_blocks(c), c.log, c.stream, cond, use_cond, trip_launches);
 }
 
 // Appends a WHILE node after `dep` (may be null) whose body is one trip; *node receives it.
@@ -603,8 +627,8 @@ int tmbir_reconstruct(tmbir_ctx* ctx, float* d_x, const float* d_atg, const tmbi
                                    prm->refine_gap);
     TMBIR_CHECK_LAUNCH();
   } else {
-    k_init_state<<<1, 1, 0, s>>>(c.state, c.dscal + 16, c.dscal + 16 + ng, ng, prm->L, prm->lambda, prm->sigma,
-                                 prm->F_ref, prm->gap_tol, prm->max_iter, prm->restart, bf16 ? 1 : 0,
+    k_init_state<<<1, 1, 0, s>>>(c.state, c.gmom, c.dscal + 16, c.dscal + 16 + ng, ng, prm->L, prm->lambda,
+                                 prm->sigma, prm->F_ref, prm->gap_tol, prm->max_iter, prm->restart, bf16 ? 1 : 0,
                                  prm->refine_gap);
     TMBIR_CHECK_LAUNCH();
     // x_{-1} = x_0 so that the first (beta = 0) extrapolation reads finite values
@@ -766,6 +790,83 @@ int tmbir_objective(tmbir_ctx* ctx, const float* d_x, const float* d_atg, const 
   return TMBIR_OK;
 }
 
+// ---------------------------------------------------------------- direct (non-Toeplitz) operators
+static int ensure_spread(Ctx& c) {
+  for (size_t i = 0; i < c.groups.size(); ++i)
+    if (!c.spread_ready[i]) {
+      if (int e = build_spread_matrix(c, (int)i)) return e;
+      c.spread_ready[i] = true;
+    }
+  return TMBIR_OK;
+}
+
+int tmbir_forward(tmbir_ctx* ctx, const float* d_x, float* d_sino) {
+  TMBIR_TRACE("tmbir_forward");
+  if (int e = require_ready(ctx, false)) return e;
+  REQUIRE(d_x && d_sino && aligned16(d_x) && aligned16(d_sino), TMBIR_ERR_ARG, "forward: bad buffers");
+  Ctx& c = ctx->c;
+  for (size_t i = 0; i < c.groups.size(); ++i)
+    if (int e = forward_project(c, (int)i, d_x, d_sino)) return e;
+  return TMBIR_OK;
+}
+
+int tmbir_adjoint(tmbir_ctx* ctx, const float* d_sino, float* d_x) {
+  TMBIR_TRACE("tmbir_adjoint");
+  if (int e = require_ready(ctx, false)) return e;
+  REQUIRE(d_x && d_sino && aligned16(d_x) && aligned16(d_sino), TMBIR_ERR_ARG, "adjoint: bad buffers");
+  Ctx& c = ctx->c;
+  if (int e = ensure_spread(c)) return e;
+  for (size_t i = 0; i < c.groups.size(); ++i)
+    if (int e = backproject(c, (int)i, d_sino, d_x, false, false)) return e;
+  return TMBIR_OK;
+}
+
+int tmbir_gradient_direct(tmbir_ctx* ctx, const float* d_x, const float* d_sino, const tmbir_params* prm,
+                          float* d_grad, double* h_F) {
+  TMBIR_TRACE("tmbir_gradient_direct");
+  if (int e = require_ready(ctx, false)) return e;
+  if (int e = check_params(prm)) return e;
+  REQUIRE(d_x && d_sino && d_grad && aligned16(d_x) && aligned16(d_sino) && aligned16(d_grad), TMBIR_ERR_ARG,
+          "gradient_direct: bad buffers");
+  REQUIRE(d_x != d_grad, TMBIR_ERR_ARG, "gradient_direct: in-place not supported");
+  Ctx& c = ctx->c;
+  cudaStream_t s = c.stream;
+  if (int e = ensure_spread(c)) return e;
+  const int ng = (int)c.groups.size();
+  // the residual r = R x - g in the sinogram domain, 1/2 r.r per group, R* r into each group's
+  // K (*) y buffer; the data term enters pass 3b as that buffer against a zero R*g
+  for (int i = 0; i < ng; ++i) {
+    const GroupDev& g = c.gdev[i];
+    if (int e = forward_project(c, i, d_x, c.sino_tmp)) return e;
+    if (int e = residual(c, i, c.sino_tmp, d_sino)) return e;
+    if (int e = half_sumsq(c, c.sino_tmp + g.sino_off, (size_t)g.S * g.na * g.nd, c.dscal + 16 + i)) return e;
+    if (int e = backproject(c, i, c.sino_tmp, g.kz, false, false, nullptr, nullptr, true)) return e;
+  }
+  TMBIR_CUDA(cudaMemsetAsync(c.xbuf[0], 0, c.total_voxels * sizeof(float), s));
+  StepArgs a{};
+  a.x = d_x;
+  a.xprev = d_x;
+  a.beta = 0.f;
+  a.atg = c.xbuf[0];
+  a.out = d_grad;
+  const PriorC pc = make_prior(*prm);
+  int off = 0;
+  for (int i = 0; i < ng; ++i) {
+    if (int e = launch_pass3(c.gdev[i], a, Pass3Mode::Gradient, pc, c.partials, off, s, false, 2)) return e;
+    off += blocks_pass3(c.gdev[i]);
+  }
+  if (h_F) {
+    if (int e = launch_sum_partials(c.partials, off, c.dscal, s)) return e;
+    std::vector<double> h(16 + ng);
+    TMBIR_CUDA(cudaMemcpyAsync(h.data(), c.dscal, h.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+    TMBIR_CUDA(cudaStreamSynchronize(s));
+    double F = prm->lambda * h[2];
+    for (int i = 0; i < ng; ++i) F += h[16 + i];
+    *h_F = F;
+  }
+  return TMBIR_OK;
+}
+
 int tmbir_lambda_max(tmbir_ctx* ctx, double* h_out) {
   TMBIR_TRACE("tmbir_lambda_max");
   if (int e = require_ready(ctx, true)) return e;
@@ -823,7 +924,7 @@ int tmbir_pass_times(tmbir_ctx* ctx, float* d_x, const float* d_atg, const tmbir
   }
   // the storage chosen by prm->spectra for every iteration (no refinement switch)
   const bool bf16 = prm->spectra == TMBIR_SPECTRA_BF16;
-  k_init_state<<<1, 1, 0, s>>>(c.state, c.dscal + 16, c.dscal + 16 + ng, ng, prm->L, prm->lambda, prm->sigma,
+  k_init_state<<<1, 1, 0, s>>>(c.state, c.gmom, c.dscal + 16, c.dscal + 16 + ng, ng, prm->L, prm->lambda, prm->sigma,
                                prm->F_ref, 0.0, iters, prm->restart, bf16 ? 1 : 0, 0.0);
   TMBIR_CHECK_LAUNCH();
   TMBIR_CUDA(cudaMemcpyAsync(c.xbuf[1], d_x, c.total_voxels * sizeof(float), cudaMemcpyDeviceToDevice, s));
@@ -849,6 +950,7 @@ int tmbir_pass_times(tmbir_ctx* ctx, float* d_x, const float* d_atg, const tmbir
     int off = 0;
     for (int i = 0; i < ng && rc == TMBIR_OK; ++i) {
       const GroupDev& g = c.gdev[i];
+      a.gm = c.gmom + i;
       const int sc = spec_chunk(g), nch = (g.S + sc - 1) / sc;
       cudaEventRecord(ev[0], s);
       for (int ch = 0; ch < nch && rc == TMBIR_OK; ++ch) {
@@ -871,7 +973,7 @@ int tmbir_pass_times(tmbir_ctx* ctx, float* d_x, const float* d_atg, const tmbir
     }
     if (rc) break;
     cudaEventRecord(ev[0], s);
-    rc = launch_finalize(c.state, c.partials, off, c.log, s);
+    rc = launch_finalize(c.state, c.gmom, c.partials, group_blocks(c), c.log, s);
     cudaEventRecord(ev[1], s);
     cudaEventSynchronize(ev[1]);
     acc[4] += span_ms(0, 1);
@@ -919,8 +1021,8 @@ int tmbir_autotune(tmbir_ctx* ctx, const float* d_x, const float* d_atg, const t
   }
   // a state whose iterations never stop, and x_{-1} = x_0: pass 3 (Iterate) writes only the
   // rotation slot of x_{k+1} and the partial sums, never d_x
-  k_init_state<<<1, 1, 0, s>>>(c.state, c.dscal + 16, c.dscal + 16 + ng, ng, prm->L, prm->lambda, prm->sigma, 0.0, 0.0,
-                               kLogCap, TMBIR_RESTART_GRADIENT, 0, 0.0);
+  k_init_state<<<1, 1, 0, s>>>(c.state, c.gmom, c.dscal + 16, c.dscal + 16 + ng, ng, prm->L, prm->lambda, prm->sigma,
+                               0.0, 0.0, kLogCap, TMBIR_RESTART_GRADIENT, 0, 0.0);
   TMBIR_CHECK_LAUNCH();
   TMBIR_CUDA(cudaMemcpyAsync(c.xbuf[1], d_x, c.total_voxels * sizeof(float), cudaMemcpyDeviceToDevice, s));
   StepArgs a{};
@@ -935,6 +1037,7 @@ int tmbir_autotune(tmbir_ctx* ctx, const float* d_x, const float* d_atg, const t
   int rc = TMBIR_OK;
   for (int i = 0; i < ng && rc == TMBIR_OK; ++i) {
     GroupDev& g = c.gdev[i];
+    a.gm = c.gmom + i;
     // slices per spectrum chunk: passes 1, 2, 3a of the whole group with every candidate
     {
       std::vector<int> sc_c;
@@ -1014,7 +1117,7 @@ int tmbir_autotune(tmbir_ctx* ctx, const float* d_x, const float* d_atg, const t
 int tmbir_state_size(const tmbir_ctx* ctx, size_t* bytes) {
   if (int e = require_ready(ctx, false)) return e;
   REQUIRE(bytes != nullptr, TMBIR_ERR_ARG, "state_size: NULL argument");
-  *bytes = kStateHeader + ctx->c.total_voxels * sizeof(float);
+  *bytes = state_header_bytes((int)ctx->c.groups.size()) + ctx->c.total_voxels * sizeof(float);
   return TMBIR_OK;
 }
 
@@ -1025,9 +1128,11 @@ int tmbir_state_export(tmbir_ctx* ctx, void* d_state) {
   Ctx& c = ctx->c;
   REQUIRE(c.state_ready, TMBIR_ERR_STATE, "state_export: no run to export");
   char* p = static_cast<char*>(d_state);
+  const size_t ng = c.groups.size();
   TMBIR_CUDA(cudaMemcpyAsync(p, c.state, sizeof(IterState), cudaMemcpyDeviceToDevice, c.stream));
-  TMBIR_CUDA(cudaMemcpyAsync(p + kStateHeader, c.xbuf[1], c.total_voxels * sizeof(float), cudaMemcpyDeviceToDevice,
-                             c.stream));
+  TMBIR_CUDA(cudaMemcpyAsync(p + kStateHeader, c.gmom, ng * sizeof(GroupMom), cudaMemcpyDeviceToDevice, c.stream));
+  TMBIR_CUDA(cudaMemcpyAsync(p + state_header_bytes((int)ng), c.xbuf[1], c.total_voxels * sizeof(float),
+                             cudaMemcpyDeviceToDevice, c.stream));
   return TMBIR_OK;
 }
 
@@ -1041,10 +1146,12 @@ int tmbir_state_import(tmbir_ctx* ctx, const void* d_state) {
   long long launches = 0;
   TMBIR_CUDA(cudaMemcpyAsync(&launches, &c.state->graph_launches, sizeof(long long), cudaMemcpyDeviceToHost, c.stream));
   TMBIR_CUDA(cudaStreamSynchronize(c.stream));
+  const size_t ng = c.groups.size();
   TMBIR_CUDA(cudaMemcpyAsync(c.state, p, sizeof(IterState), cudaMemcpyDeviceToDevice, c.stream));
   TMBIR_CUDA(cudaMemcpyAsync(&c.state->graph_launches, &launches, sizeof(long long), cudaMemcpyHostToDevice, c.stream));
-  TMBIR_CUDA(cudaMemcpyAsync(c.xbuf[1], p + kStateHeader, c.total_voxels * sizeof(float), cudaMemcpyDeviceToDevice,
-                             c.stream));
+  TMBIR_CUDA(cudaMemcpyAsync(c.gmom, p + kStateHeader, ng * sizeof(GroupMom), cudaMemcpyDeviceToDevice, c.stream));
+  TMBIR_CUDA(cudaMemcpyAsync(c.xbuf[1], p + state_header_bytes((int)ng), c.total_voxels * sizeof(float),
+                             cudaMemcpyDeviceToDevice, c.stream));
   TMBIR_CUDA(cudaStreamSynchronize(c.stream));
   c.state_ready = true;
   return TMBIR_OK;

@@ -224,7 +224,9 @@ __device__ __forceinline__ void reg_dft(C (&a)[P]) {
 
 // ---------------------------------------------------------------- group FFT of length n = T * P
 // Thread layout in and out: thread t of the group holds x[t + T*i], i < P.
-// tw: table [P][T] of exp(-2*pi*i*t*k1/n) (conjugated on the fly for the inverse).
+// tw: table of exp(-2*pi*i*t*k1/n) at tw[k1 * TWS * T + t] (conjugated on the fly for the
+// inverse); TWS = 1 is the table [P][T] of this length, TWS = 2 reads every other row of the
+// table of a transform twice as long (exp(-2 pi i t (2 k1) / 2n) = exp(-2 pi i t k1 / n)).
 // sm: T*(P+1) complex values of shared memory owned by this group.
 template <int T_, int P_>
 struct GroupFFT {
@@ -235,12 +237,12 @@ struct GroupFFT {
   static_assert(P % T == 0, "P must be a multiple of T");
   static_assert(T <= 32 && (32 % T) == 0, "group must divide a warp");
 
-  template <int DIR, class C>
+  template <int DIR, class C, int TWS = 1>
   __device__ __forceinline__ static void run(C (&v)[P], C* sm, const C* __restrict__ tw, int t) {
     reg_dft<P, DIR, C>(v);
     SFor<1, P>::run([&](auto k_) {
       constexpr int k1 = decltype(k_)::value;
-      C w = __ldg(&tw[k1 * T + t]);
+      C w = __ldg(&tw[k1 * TWS * T + t]);
       v[k1] = DIR < 0 ? cmul(v[k1], w) : cmulc(v[k1], w);
     });
     __syncwarp();

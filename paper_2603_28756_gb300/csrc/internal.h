@@ -12,11 +12,13 @@
 
 namespace tmbir {
 
-// Device-resident optimiser state, advanced by the finalize kernel once per iteration.
+// Device-resident optimiser state, advanced by the finalize kernel once per iteration.  The
+// momentum, step constant and restart test are per geometry group (GroupMom): groups are
+// independent problems; the stop rule, the storage phase and the buffer rotation are shared.
 struct IterState {
-  double t;         // momentum sequence t_k
-  double beta;      // beta_k used by the current iteration
-  double L, invL;   // step constant
+  double t;         // unused (per group: GroupMom)
+  double beta;      // unused (per group: GroupMom)
+  double L, invL;   // step constant of the first group (reported in the stats)
   double lambda;    // prior weight
   double gtg_half;  // 1/2 g.g summed over all groups
   double F0, Fref, gap_tol;
@@ -35,12 +37,34 @@ struct IterState {
   long long graph_launches;  // kernels run by device-driven graph trips, cumulative (zeroed at workspace binding)
 };
 
+// Fast-gradient state of one geometry group (Sec. 2, Eq. 6 with restart): its own step
+// constant, momentum sequence and restart test, as if the group were reconstructed alone.
+struct GroupMom {
+  double t;         // momentum sequence t_k
+  double beta;      // beta_k used by the current iteration
+  double L, invL;   // step constant
+  double prev_F;    // F_g(y_{k-1}), for the function-value restart
+  double gtg_half;  // 1/2 g.g of the group
+  int restarts;
+  int pad;
+};
+constexpr int kMaxGroups = 64;
+// First partial-sum row of each group's pass-3b blocks (off[n] = total), passed by value.
+struct GroupBlocks {
+  int n;
+  int off[kMaxGroups + 1];
+};
+
 // Number of FP64 partial sums each reducing block writes.
 constexpr int kParts = 6;  // y.z, y.atg, Phi(y), <G, x_new - x>, G.G, z.z
 constexpr int kLogCap = 1 << 16;
 // checkpoint layout: the iteration state in the first kStateHeader bytes, then x_{k-1}
 constexpr size_t kStateHeader = 256;
 static_assert(sizeof(IterState) <= kStateHeader, "checkpoint header too small");
+// checkpoint bytes before x_{k-1}: the iteration state, then the groups' momentum states
+inline size_t state_header_bytes(int n_groups) {
+  return kStateHeader + ((size_t)n_groups * sizeof(GroupMom) + 255) / 256 * 256;
+}
 
 // qGGMRF constants in the form the kernels use.
 struct PriorC {
@@ -109,6 +133,7 @@ struct Ctx {
   char* ws = nullptr;
   size_t ws_bytes = 0, ws_need = 0;
   IterState* state = nullptr;
+  GroupMom* gmom = nullptr;    // [n_groups]
   double* partials = nullptr;  // [max_blocks][kParts]
   int max_blocks = 0;
   double* log = nullptr;       // [kLogCap][4]
@@ -121,9 +146,11 @@ struct Ctx {
   // layout offsets computed at set_geometry
   std::vector<size_t> off_chat, off_twN, off_twM, off_spec, off_kz, off_ang, off_K, off_psiK, off_psiA, off_lam, off_gtg,
       off_csr_ptr, off_csr_idx, off_csr_w;
-  size_t off_state = 0, off_partials = 0, off_log = 0, off_xbuf0 = 0, off_xbuf1 = 0, off_scratch = 0, off_dscal = 0;
+  size_t off_state = 0, off_gmom = 0, off_partials = 0, off_log = 0, off_xbuf0 = 0, off_xbuf1 = 0, off_scratch = 0, off_dscal = 0;
   size_t off_fbp_scratch = 0;
   char* fbp_scratch = nullptr;  // FP32 back-projection scratch, separate so FBP can overlap R*g
+  float* sino_tmp = nullptr;    // a sinogram of the whole batch: R x and the residual of the direct gradient
+  size_t off_sino_tmp = 0;
   cudaStream_t aux = nullptr;   // second stream for the overlapped FBP (created on first use)
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   // CUDA graph cache for reconstruct
@@ -172,9 +199,10 @@ struct StepArgs {
   const float* atg;     // R*g (Gradient, Step, Iterate, Objective)
   float* out;           // z (Apply), G (Gradient), x_next (Step)
   float invL;           // explicit step (Step mode)
-  // Iterate mode: rotation buffers and device state
+  // Iterate mode: rotation buffers, device state and the group's momentum state
   float* xb[3];
   const IterState* st;
+  const GroupMom* gm;
 };
 
 // bf16: the BF16-storage variant of the pass (Iterate mode only for pass 3); in Iterate mode a
@@ -213,8 +241,8 @@ int max_blocks_pass3(const GroupDev& g);
 // cond: the WHILE handle of a device-driven graph loop, set to 0 once the run is done
 // (use_cond 1) or also once the run leaves its BF16 phase (use_cond 2); trip_launches:
 // kernels of one loop trip, added to IterState::graph_launches.
-int launch_finalize(IterState* st, const double* partials, int nblocks, double* log, cudaStream_t s,
-                    cudaGraphConditionalHandle cond = 0, int use_cond = 0, int trip_launches = 0);
+int launch_finalize(IterState* st, GroupMom* gm, const double* partials, const GroupBlocks& gb, double* log,
+                    cudaStream_t s, cudaGraphConditionalHandle cond = 0, int use_cond = 0, int trip_launches = 0);
 int launch_sum_partials(const double* partials, int nblocks, double* out, cudaStream_t s);
 bool supported_N(int N);
 bool block_fft_N(int N);  // sides with a factor 3 or 5 (block-FFT passes, plain twiddle table)
@@ -224,10 +252,19 @@ void fft_shape(int N, int* T, int* P);
 int setup_tables(Ctx& c);  // enqueue uploads of twiddles / psi tables into the workspace
 int build_kernel_spectrum(Ctx& c, int gi);
 // scratch / s: null for the context's setup scratch and stream
+// local_out: d_out is the group's own [slice][row][col] buffer (no stacked-image offset)
 int backproject(Ctx& c, int gi, const float* d_sino, float* d_out, bool ramp, bool fp64, char* scratch = nullptr,
-                cudaStream_t s = nullptr);
+                cudaStream_t s = nullptr, bool local_out = false);
+// *d_out = 1/2 sum p[i]^2 (FP64, fixed order; uses the setup scratch)
+int half_sumsq(Ctx& c, const float* p, size_t n, double* d_out, cudaStream_t s = nullptr);
 size_t fbp_scratch_bytes(const tmbir_group& g);  // FP32 back-projection scratch of one group
 int build_spread_matrix(Ctx& c, int gi);
+// R x of one group by the type-2 NUFFT (FP32, Eqs. 3-4) into d_sino (the group's rows of the
+// stacked sinogram); uses the setup scratch
+int forward_project(Ctx& c, int gi, const float* d_x, float* d_sino, cudaStream_t s = nullptr);
+size_t forward_scratch_bytes(const tmbir_group& g);
+// d_rx -= d_g over one group's sinogram rows
+int residual(Ctx& c, int gi, float* d_rx, const float* d_g, cudaStream_t s = nullptr);
 size_t spread_nnz(const tmbir_group& g);
 int power_iteration(Ctx& c, int gi, int steps);
 int group_gtg(Ctx& c, int gi, const float* d_sino);

@@ -576,7 +576,7 @@ size_t setup_scratch_bytes(const tmbir_group& g) {
   // twiddles, strengths, grids, pruned transposes, sample-major strengths (always kBackprojBatch wide)
   const size_t a_elems = nf_a + B * rows + B * nf_a * nf_a + B * N * nf_a + (size_t)kBackprojBatch * rows;
   const size_t csr_build = (nf_a * nf_a + 2 * ((nf_a * nf_a + 2048) / 2048 + 1)) * sizeof(int);
-  return std::max(std::max(k_elems, a_elems) * sizeof(double2), csr_build) + 256;
+  return std::max(std::max(std::max(k_elems, a_elems) * sizeof(double2), csr_build) + 256, forward_scratch_bytes(g));
 }
 size_t fbp_scratch_bytes(const tmbir_group& g) {
   const size_t N = g.N, nf_a = 2 * N;
@@ -706,7 +706,7 @@ int build_spread_matrix(Ctx& c, int gi) {
 
 template <class C>
 static int backproject_t(Ctx& c, int gi, const float* d_sino, float* d_out, bool ramp, float scale, char* scratch,
-                         cudaStream_t s) {
+                         cudaStream_t s, bool local_out) {
   GroupDev& g = c.gdev[gi];
   const int N = g.N, nf = 2 * N, nd = g.nd, na = g.na, ncells = nf * nf;
   const size_t rows = (size_t)na * nd;
@@ -743,20 +743,179 @@ static int backproject_t(Ctx& c, int gi, const float* d_sino, float* d_out, bool
       TMBIR_CHECK_LAUNCH();
     }
     if (int e = fft_rows(tmp, nf, np * N, -1, tw, s)) return e;
-    k_deconv_pruned<C><<<1024, 256, 0, s>>>(tmp, nf, N, nb, g.psiA, scale, d_out + g.img_off + (size_t)b0 * N * N);
+    k_deconv_pruned<C><<<1024, 256, 0, s>>>(tmp, nf, N, nb, g.psiA, scale,
+                                            d_out + (local_out ? 0 : g.img_off) + (size_t)b0 * N * N);
     TMBIR_CHECK_LAUNCH();
   }
   return TMBIR_OK;
 }
 
 int backproject(Ctx& c, int gi, const float* d_sino, float* d_out, bool ramp, bool fp64, char* scratch,
-                cudaStream_t s) {
+                cudaStream_t s, bool local_out) {
   const GroupDev& g = c.gdev[gi];
   const float scale = ramp ? (float)(g.span / g.na) : 1.0f;
   if (!scratch) scratch = c.scratch;
   if (!s) s = c.stream;
-  if (fp64) return backproject_t<double2>(c, gi, d_sino, d_out, ramp, scale, scratch, s);
-  return backproject_t<float2>(c, gi, d_sino, d_out, ramp, scale, scratch, s);
+  if (fp64) return backproject_t<double2>(c, gi, d_sino, d_out, ramp, scale, scratch, s, local_out);
+  return backproject_t<float2>(c, gi, d_sino, d_out, ramp, scale, scratch, s, local_out);
+}
+
+int half_sumsq(Ctx& c, const float* p, size_t n, double* d_out, cudaStream_t s) {
+  if (!s) s = c.stream;
+  double* part = reinterpret_cast<double*>(c.scratch);
+  k_sumsq_blocks<<<1024, 256, 0, s>>>(p, n, part);
+  TMBIR_CHECK_LAUNCH();
+  k_sum_half<<<1, 256, 0, s>>>(part, 1024, d_out);
+  TMBIR_CHECK_LAUNCH();
+  return TMBIR_OK;
+}
+
+// ---------------------------------------------------------------- forward projection (type-2 NUFFT)
+// R x(a, m) = (1/n_det) sum_k exp(-2 pi i k s_m / n_det) xhat(xi_{a,k}),
+// xhat(xi) = sum_x x(x) exp(+2 pi i xi . x)  (Eqs. 3-4, the adjoint of the back-projection):
+// divide the image by the kernel's Fourier transform, place it on the 2N x 2N periodic grid,
+// FFT with the + sign, interpolate at the polar samples with the spreading kernel (width
+// kSpreadW), then the radial 1D transform.  FP32; two slices share one complex grid (the
+// result of a real image pair is R x_{2p} + i R x_{2p+1}).
+
+// grid[p][row'][col'] = (x_{2p} + i x_{2p+1})[r][c] / (psi[c] psi[r]) at row' = (r - N/2) mod nf,
+// col' = (c - N/2) mod nf, zero elsewhere
+__global__ void k_pad_deconv_pairs(const float* __restrict__ x, int N, int nf, int nb, const double* __restrict__ psi,
+                                   float2* __restrict__ grid) {
+  const int np = (nb + 1) / 2;
+  const size_t cells = (size_t)nf * nf, total = (size_t)np * cells, plane = (size_t)N * N;
+  for (size_t id = blockIdx.x * (size_t)blockDim.x + threadIdx.x; id < total; id += (size_t)gridDim.x * blockDim.x) {
+    const int p = (int)(id / cells);
+    const int cell = (int)(id % cells), rp = cell / nf, cp = cell % nf;
+    const int r = (rp + N / 2) % nf, c = (cp + N / 2) % nf;
+    float2 v = make_float2(0.f, 0.f);
+    if (r < N && c < N) {
+      const float inv = (float)(1.0 / (psi[c] * psi[r]));
+      const size_t o = (size_t)r * N + c;
+      v.x = x[(size_t)(2 * p) * plane + o] * inv;
+      if (2 * p + 1 < nb) v.y = x[(size_t)(2 * p + 1) * plane + o] * inv;
+    }
+    grid[id] = v;
+  }
+}
+
+__device__ __forceinline__ float es_kernel_f(float z, float beta) {  // z in [-1, 1]
+  const float t = 1.f - z * z;
+  return t > 0.f ? expf(beta * (sqrtf(t) - 1.f)) : 0.f;
+}
+
+// rows[p][a][k mod n_det] = (-1)^k / n_det * sum_l psi(u - l) F_p[l] for |k| <= n_det/2 - 1 (0 at
+// the Nyquist index), F transposed ([lx][ly]); one thread per sample, all pairs of the batch
+template <int W, int PB>
+__global__ void k_interp_pairs(const float2* __restrict__ F, const double* __restrict__ angles, int na, int nd, int nf,
+                               float beta, int np, float2* __restrict__ rows) {
+  const size_t total = (size_t)na * nd, cells = (size_t)nf * nf;
+  for (size_t id = blockIdx.x * (size_t)blockDim.x + threadIdx.x; id < total; id += (size_t)gridDim.x * blockDim.x) {
+    const int kk = (int)(id % nd), a = (int)(id / nd);
+    float2 acc[PB];
+#pragma unroll
+    for (int p = 0; p < PB; ++p) acc[p] = make_float2(0.f, 0.f);
+    if (kk != nd / 2) {
+      const int k = kk < nd / 2 ? kk : kk - nd;
+      double sa, ca;
+      sincos(angles[a], &sa, &ca);
+      const double ux = (double)k * ca * nf / nd, uy = (double)k * sa * nf / nd;
+      const int lx0 = (int)ceil(ux - 0.5 * W), ly0 = (int)ceil(uy - 0.5 * W);
+      float wx[W], wy[W];
+#pragma unroll
+      for (int j = 0; j < W; ++j) {
+        wx[j] = es_kernel_f((float)((2.0 * (lx0 + j - ux)) / W), beta);
+        wy[j] = es_kernel_f((float)((2.0 * (ly0 + j - uy)) / W), beta);
+      }
+#pragma unroll 1
+      for (int jx = 0; jx < W; ++jx) {
+        const int lx = (lx0 + jx + nf) % nf;
+#pragma unroll
+        for (int p = 0; p < PB; ++p) {
+          if (p < np) {
+            const float2* col = F + (size_t)p * cells + (size_t)lx * nf;
+            float2 s = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int jy = 0; jy < W; ++jy) {
+              const float2 v = col[(ly0 + jy + nf) % nf];
+              s.x = fmaf(wy[jy], v.x, s.x);
+              s.y = fmaf(wy[jy], v.y, s.y);
+            }
+            acc[p].x = fmaf(wx[jx], s.x, acc[p].x);
+            acc[p].y = fmaf(wx[jx], s.y, acc[p].y);
+          }
+        }
+      }
+      const float sg = (k & 1) ? -1.f / nd : 1.f / nd;
+#pragma unroll
+      for (int p = 0; p < PB; ++p) acc[p] = make_float2(acc[p].x * sg, acc[p].y * sg);
+    }
+#pragma unroll
+    for (int p = 0; p < PB; ++p)
+      if (p < np) rows[(size_t)p * total + id] = acc[p];
+  }
+}
+
+// sino[b][a][m] = Re (b even) or Im (b odd) of rows[b / 2][a][m]
+__global__ void k_unpack_pairs(const float2* __restrict__ rows, size_t per_pair, int nb, float* __restrict__ sino) {
+  const size_t total = (size_t)nb * per_pair;
+  for (size_t id = blockIdx.x * (size_t)blockDim.x + threadIdx.x; id < total; id += (size_t)gridDim.x * blockDim.x) {
+    const int b = (int)(id / per_pair);
+    const float2 v = rows[(size_t)(b / 2) * per_pair + id % per_pair];
+    sino[id] = (b & 1) ? v.y : v.x;
+  }
+}
+
+size_t forward_scratch_bytes(const tmbir_group& g) {
+  const size_t nf = 2 * (size_t)g.N, np = (std::min(g.n_slices, kBackprojBatch) + 1) / 2;
+  return (nf + g.n_det + 2 * np * nf * nf + np * (size_t)g.n_angles * g.n_det) * sizeof(float2) + 256;
+}
+
+int forward_project(Ctx& c, int gi, const float* d_x, float* d_sino, cudaStream_t s) {
+  GroupDev& g = c.gdev[gi];
+  if (!s) s = c.stream;
+  const int N = g.N, nf = 2 * N, nd = g.nd, na = g.na;
+  const size_t cells = (size_t)nf * nf, rows = (size_t)na * nd;
+  const int B = std::min(g.S, kBackprojBatch);
+  constexpr int PB = kBackprojBatch / 2;
+  if (forward_scratch_bytes(c.groups[gi]) > c.scratch_bytes)
+    return set_error(TMBIR_ERR_WORKSPACE, "forward projection: setup scratch too small");
+  float2* tw_f = reinterpret_cast<float2*>(c.scratch);
+  float2* tw_d = tw_f + nf;
+  float2* grid = tw_d + nd;
+  float2* tmp = grid + (size_t)PB * cells;
+  float2* prow = tmp + (size_t)PB * cells;
+  k_twiddle<float2><<<(nf + 255) / 256, 256, 0, s>>>(tw_f, nf);
+  TMBIR_CHECK_LAUNCH();
+  k_twiddle<float2><<<(nd + 255) / 256, 256, 0, s>>>(tw_d, nd);
+  TMBIR_CHECK_LAUNCH();
+  for (int b0 = 0; b0 < g.S; b0 += B) {
+    const int nb = std::min(B, g.S - b0), np = (nb + 1) / 2;
+    k_pad_deconv_pairs<<<1024, 256, 0, s>>>(d_x + g.img_off + (size_t)b0 * N * N, N, nf, nb, g.psiA, grid);
+    TMBIR_CHECK_LAUNCH();
+    if (int e = fft2_transposed(grid, tmp, nf, np, +1, tw_f, s)) return e;
+    k_interp_pairs<kSpreadW, PB><<<(int)std::min<size_t>((rows + 255) / 256, 152 * 16), 256, 0, s>>>(
+        tmp, g.angles, na, nd, nf, (float)c.spread_beta, np, prow);
+    TMBIR_CHECK_LAUNCH();
+    if (int e = fft_rows(prow, nd, np * na, -1, tw_d, s)) return e;
+    k_unpack_pairs<<<1024, 256, 0, s>>>(prow, rows, nb, d_sino + g.sino_off + (size_t)b0 * rows);
+    TMBIR_CHECK_LAUNCH();
+  }
+  return TMBIR_OK;
+}
+
+// d_sino -= d_g over one group (the residual R x - g)
+__global__ void k_sub_inplace(float* __restrict__ a, const float* __restrict__ b, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    a[i] -= b[i];
+}
+int residual(Ctx& c, int gi, float* d_rx, const float* d_g, cudaStream_t s) {
+  const GroupDev& g = c.gdev[gi];
+  if (!s) s = c.stream;
+  const size_t n = (size_t)g.S * g.na * g.nd;
+  k_sub_inplace<<<1024, 256, 0, s>>>(d_rx + g.sino_off, d_g + g.sino_off, n);
+  TMBIR_CHECK_LAUNCH();
+  return TMBIR_OK;
 }
 
 int group_gtg(Ctx& c, int gi, const float* d_sino) {

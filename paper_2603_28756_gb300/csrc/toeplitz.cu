@@ -59,36 +59,55 @@ __global__ void __launch_bounds__(512) k_sum_partials(const double* partials, in
   reduce_blocks(partials, nblocks, out);
 }
 
-// Reduces the partial sums of one iteration and advances the momentum state (Eq. 6 with the
-// restart test).  Inside a device-driven graph loop it also sets the loop's condition: 0 once
+// Reduces the partial sums of one iteration and advances the optimiser state (Eq. 6 with the
+// restart test): per group its momentum sequence and restart decision (the group's blocks are
+// the rows gb.off[g] .. gb.off[g + 1] of the partials, reduced in the same order as in a context
+// of that group alone), over all groups the objective, the stop rule, the storage phase and the
+// buffer rotation.  Inside a device-driven graph loop it also sets the loop's condition: 0 once
 // the run is done (every path sets it, so the loop always ends by max_iter).
-__global__ void __launch_bounds__(512) k_finalize(IterState* st, const double* partials, int nblocks, double* log,
-                                                  cudaGraphConditionalHandle cond, int use_cond, int trip_launches) {
+__global__ void __launch_bounds__(512) k_finalize(IterState* st, GroupMom* gm, const double* partials, GroupBlocks gb,
+                                                  double* log, cudaGraphConditionalHandle cond, int use_cond,
+                                                  int trip_launches) {
   __shared__ double S[kParts];
+  __shared__ double tot[4];  // F, <G, x_new - x>, G.G, restarts
   if (st->done) {
     if (use_cond && threadIdx.x == 0) cudaGraphSetConditional(cond, 0);
     return;
   }
-  reduce_blocks(partials, nblocks, S);
-  if (threadIdx.x != 0) return;
-  const double yz = S[0], yatg = S[1], phi = S[2], gdx = S[3], gg = S[4];
-  const double F = 0.5 * yz - yatg + st->gtg_half + st->lambda * phi;
-  // gradient restart: <grad F(y_k), x_{k+1} - x_k> > 0; function restart: F(y_k) > F(y_{k-1})
-  const bool restart = (st->restart_mode == TMBIR_RESTART_GRADIENT && gdx > 0.0) ||
-                       (st->restart_mode == TMBIR_RESTART_FUNCTION && st->k > 0 && F > st->prev_F);
-  st->prev_F = F;
+  if (threadIdx.x == 0) tot[0] = tot[1] = tot[2] = tot[3] = 0.0;
   const int k = st->k;
+  for (int g = 0; g < gb.n; ++g) {
+    reduce_blocks(partials + (size_t)gb.off[g] * kParts, gb.off[g + 1] - gb.off[g], S);
+    if (threadIdx.x == 0) {
+      GroupMom& m = gm[g];
+      const double yz = S[0], yatg = S[1], phi = S[2], gdx = S[3], gg = S[4];
+      const double F = 0.5 * yz - yatg + m.gtg_half + st->lambda * phi;
+      // gradient restart: <grad F(y_k), x_{k+1} - x_k> > 0; function restart: F(y_k) > F(y_{k-1})
+      const bool restart = (st->restart_mode == TMBIR_RESTART_GRADIENT && gdx > 0.0) ||
+                           (st->restart_mode == TMBIR_RESTART_FUNCTION && k > 0 && F > m.prev_F);
+      m.prev_F = F;
+      const double tn = restart ? 1.0 : 0.5 * (1.0 + sqrt(1.0 + 4.0 * m.t * m.t));
+      const double tnn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * tn * tn));
+      m.beta = (tn - 1.0) / tnn;
+      m.t = tn;
+      m.restarts += restart ? 1 : 0;
+      tot[0] += F;
+      tot[1] += gdx;
+      tot[2] += gg;
+      tot[3] += restart ? 1.0 : 0.0;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x != 0) return;
+  const double F = tot[0], gdx = tot[1], gg = tot[2];
   if (k < st->log_cap) {
     log[4 * k + 0] = F;
     log[4 * k + 1] = gdx;
-    log[4 * k + 2] = restart ? 1.0 : 0.0;
+    log[4 * k + 2] = tot[3];  // groups that restarted (0 or 1 for one group)
     log[4 * k + 3] = gg;
   }
-  const double tn = restart ? 1.0 : 0.5 * (1.0 + sqrt(1.0 + 4.0 * st->t * st->t));
-  const double tnn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * tn * tn));
-  st->beta = (tn - 1.0) / tnn;
-  st->t = tn;
-  st->restarts += restart ? 1 : 0;
+  st->restarts += (int)tot[3];
+  st->prev_F = F;
   st->k = k + 1;
   st->cur = (st->cur + 1) % 3;
   st->last_F = F;
@@ -167,9 +186,9 @@ int blocks_pass3(const GroupDev& g) {
 }
 int max_blocks_pass3(const GroupDev& g) { return pass3_row_blocks(g.N) * g.S; }
 
-int launch_finalize(IterState* st, const double* partials, int nblocks, double* log, cudaStream_t s,
-                    cudaGraphConditionalHandle cond, int use_cond, int trip_launches) {
-  k_finalize<<<1, 512, 0, s>>>(st, partials, nblocks, log, cond, use_cond, trip_launches);
+int launch_finalize(IterState* st, GroupMom* gm, const double* partials, const GroupBlocks& gb, double* log,
+                    cudaStream_t s, cudaGraphConditionalHandle cond, int use_cond, int trip_launches) {
+  k_finalize<<<1, 512, 0, s>>>(st, gm, partials, gb, log, cond, use_cond, trip_launches);
   TMBIR_CHECK_LAUNCH();
   return TMBIR_OK;
 }

@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) k_pass1(GroupDev g, StepArgs 
     // selects rather than an indexed parameter array, which would be copied to local memory
     x = cur == 0 ? a.xb[0] : (cur == 1 ? a.xb[1] : a.xb[2]);
     xp = cur == 0 ? a.xb[2] : (cur == 1 ? a.xb[0] : a.xb[1]);
-    beta = (float)a.st->beta;
+    beta = (float)a.gm->beta;
   } else {
     x = a.x;
     xp = a.xprev;
@@ -262,6 +262,19 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) k_pass1(GroupDev g, StepArgs 
 }
 
 // ---------------------------------------------------------------- pass 2: columns
+// Column order of pass 2: chunks of kColChunk slices, and within a chunk the slices fastest, so
+// that consecutive blocks share a column of the kernel spectrum (L2 reuse) while the blocks in
+// flight stay within a few hundred MB of the spectrum instead of spreading over every slice of
+// a large volume (TLB reach).  Column index -> (kernel column vcol, slice s).
+constexpr int kColChunk = 16;
+__device__ __forceinline__ void column_of(int col, int S, int ncol, int& vcol, int& s) {
+  const int chunk = col / (kColChunk * ncol);
+  const int within = col - chunk * kColChunk * ncol;
+  const int rem = min(kColChunk, S - chunk * kColChunk);
+  vcol = within / rem;
+  s = chunk * kColChunk + (within - vcol * rem);
+}
+
 template <int N, bool BF>
 __global__ void TMBIR_P2_BOUNDS(Geo<N>::THREADS) k_pass2(GroupDev g, const IterState* st) {
   using Gm = Geo<N>;
@@ -274,7 +287,8 @@ __global__ void TMBIR_P2_BOUNDS(Geo<N>::THREADS) k_pass2(GroupDev g, const IterS
   const int col = blockIdx.x * Gm::CPB + (unit >> 1);
   const int ncols = g.S * (N + 1);
   const bool active = col < ncols;
-  const int vcol = active ? col / g.S : 0, s = active ? col % g.S : 0;  // slices fastest: kernel column reuse
+  int vcol = 0, s = 0;
+  if (active) column_of(col, g.S, N + 1, vcol, s);
   using IO = SpecIO<BF>;
   typename IO::T* p = reinterpret_cast<typename IO::T*>(g.spec) + ((size_t)s * (N + 1) + vcol) * N;
   float2 v[P];
@@ -401,7 +415,7 @@ __global__ void __launch_bounds__(256) k_pass1_b(GroupDev g, StepArgs a) {
     // selects rather than an indexed parameter array, which would be copied to local memory
     x = cur == 0 ? a.xb[0] : (cur == 1 ? a.xb[1] : a.xb[2]);
     xp = cur == 0 ? a.xb[2] : (cur == 1 ? a.xb[0] : a.xb[1]);
-    beta = (float)a.st->beta;
+    beta = (float)a.gm->beta;
   } else {
     x = a.x;
     xp = a.xprev;
@@ -448,7 +462,8 @@ __global__ void __launch_bounds__(256) k_pass2_b(GroupDev g, const IterState* st
   using BG = BGeo<N>;
   extern __shared__ float2 sm[];
   if (st && skip_iter<BF>(st)) return;
-  const int vcol = blockIdx.x / g.S, s = blockIdx.x % g.S;  // slices fastest: kernel column reuse
+  int vcol, s;
+  column_of(blockIdx.x, g.S, N + 1, vcol, s);
   using IO = SpecIO<BF>;
   typename IO::T* p = reinterpret_cast<typename IO::T*>(g.spec) + ((size_t)s * (N + 1) + vcol) * N;
   float2* X = sm;
@@ -509,6 +524,216 @@ __global__ void __launch_bounds__(256) k_pass3a_b(GroupDev g, const IterState* s
     float2* out = reinterpret_cast<float2*>(kz + ((size_t)s * N + r0 + rr) * N);
     for (int n = threadIdx.x; n < N / 2; n += BG::THREADS) out[n] = Z[n];
   }
+}
+
+// ---------------------------------------------------------------- passes 1, 2, 3a for N = 2048
+// At N = 2048 a thread of the register group FFT would hold 64 complex values (254 registers,
+// spills in pass 2).  The zero padding lets each transform split into transforms of half the
+// length, so these passes run the 1024-point group FFT of N = 1024 (32 threads x 32 values),
+// one warp per part, with the same layouts and scaling as the group-FFT passes
+// (w = exp(-2 pi i / 2048), W = exp(-2 pi i / 4096)):
+//   pass 1: the packed row z has 1024 nonzero values of 2048, so
+//           Z[2k + j] = DFT_1024(z[m] w^(jm))[k], j = 0, 1 (two warps per row);
+//   pass 2: the column c has 2048 nonzero values of 4096, so
+//           X[4k + j] = DFT_1024(W^(jm) (c[m] + (-i)^j c[m + 1024]))[k], j = 0..3 (four warps
+//           per column); after the kernel multiply the kept rows n = m + 1024 q are
+//           sum_j W^(-jm) i^(jq) u_j[m], u_j the inverse 1024-point transforms;
+//   pass 3a: only the first 1024 packed outputs are kept, z[n] = sum_j w^(-jn) u_j[n], u_j the
+//           inverse 1024-point transforms of Z[2k + j], j = 0, 1 (two warps per row).
+// Each has the flops of the unsplit transforms (the split is the first radix-2 or radix-4
+// stage, pruned by the padding and the crop).
+struct Q2048 {
+  static constexpr int N = 2048, H = 1024;
+  using F = GroupFFT<32, 32>;
+  static constexpr int LDZ = N + 4;  // row stride (complex) of staged rows
+  static constexpr int RB1 = 4;      // rows per block of pass 1 (eight warps)
+  static constexpr int RB3 = 8;      // rows per block of pass 3a (sixteen warps: 64-byte gathers)
+  template <int RB>
+  static constexpr size_t sm_rows() {  // staged rows and the warps' exchange buffers, aliased
+    return (size_t)(RB * LDZ > 2 * RB * F::SMEM ? RB * LDZ : 2 * RB * F::SMEM) * sizeof(float2);
+  }
+  static constexpr size_t SM2 = (size_t)(N + 4 * F::SMEM) * sizeof(float2);  // column + 4 exchange buffers
+};
+
+// W^n = exp(-2 pi i n / 4096) for 0 <= n < 4096 from the table of n < 2048 (W^(n + 2048) = -W^n)
+__device__ __forceinline__ float2 tw4096(const float2* __restrict__ twM, int n) {
+  const float2 w = __ldg(&twM[n & 2047]);
+  return n < 2048 ? w : make_float2(-w.x, -w.y);
+}
+
+template <bool BF>
+__global__ void __launch_bounds__(32 * 2 * Q2048::RB1) k_pass1_q(GroupDev g, StepArgs a) {
+  using Q = Q2048;
+  constexpr int N = Q::N, T = 32, P = 32, RB = Q::RB1, LDZ = Q::LDZ, THREADS = 64 * RB, NB = N / RB;
+  extern __shared__ float2 sm[];
+  const float *x, *xp;
+  float beta;
+  if (a.st) {
+    if (skip_iter<BF>(a.st)) return;
+    const int cur = a.st->cur;
+    x = cur == 0 ? a.xb[0] : (cur == 1 ? a.xb[1] : a.xb[2]);
+    xp = cur == 0 ? a.xb[2] : (cur == 1 ? a.xb[0] : a.xb[1]);
+    beta = (float)a.gm->beta;
+  } else {
+    x = a.x;
+    xp = a.xprev;
+    beta = a.beta;
+  }
+  const int s = blockIdx.x / NB, rb = blockIdx.x % NB;
+  const int warp = threadIdx.x >> 5, t = threadIdx.x & 31, rl = warp >> 1, j = warp & 1;
+  const size_t base = g.img_off + ((size_t)s * N + rb * RB + rl) * N;
+  // packed row z[m] = y[2m] + i y[2m+1], m < 1024 (the padding above is zero), times w^(jm)
+  float2 v[P];
+  SFor<0, P>::run([&](auto i_) {
+    constexpr int i = decltype(i_)::value;
+    const int m = t + T * i;
+    const float2 xv = __ldg(reinterpret_cast<const float2*>(x + base) + m);
+    const float2 pv = __ldg(reinterpret_cast<const float2*>(xp + base) + m);
+    float2 z = make_float2(fmaf(beta, xv.x - pv.x, xv.x), fmaf(beta, xv.y - pv.y, xv.y));
+    if (j) z = cmul(z, __ldg(&g.twM[2 * m]));  // w^m = W^(2m)
+    v[i] = z;
+  });
+  Q::F::template run<-1, float2, 2>(v, sm + warp * Q::F::SMEM, g.twN, t);
+  __syncthreads();  // every exchange buffer is free: the staged rows alias them
+  float2* zrow = sm + rl * LDZ;
+  SFor<0, P>::run([&](auto i_) {
+    constexpr int i = decltype(i_)::value;
+    zrow[2 * (t + T * i) + j] = v[i];
+  });
+  __syncthreads();
+  // split Y[v] = E[v] + W^v O[v] from Z[v] and Z[N - v]; Y[N] = Re Z[0] - Im Z[0]; written
+  // column-major (RB-row segments)
+  using IO = SpecIO<BF>;
+  typename IO::T* out = reinterpret_cast<typename IO::T*>(g.spec) + (size_t)s * (N + 1) * N + rb * RB;
+  for (int e = threadIdx.x; e < (N + 1) * RB; e += THREADS) {
+    const int vv = e / RB, rr = e - vv * RB;
+    const float2* zr = sm + rr * LDZ;
+    float2 y;
+    if (vv < N) {
+      const float2 z = zr[vv], zs = zr[(N - vv) & (N - 1)];
+      const float2 ev = make_float2(0.5f * (z.x + zs.x), 0.5f * (z.y - zs.y));
+      const float2 od = make_float2(0.5f * (z.y + zs.y), -0.5f * (z.x - zs.x));
+      y = cadd(ev, cmul(__ldg(&g.twM[vv]), od));
+    } else {
+      y = make_float2(zr[0].x - zr[0].y, 0.f);
+    }
+    IO::st(out, (size_t)vv * N + rr, y);
+  }
+}
+
+template <bool BF>
+__global__ void __launch_bounds__(128, 3) k_pass2_q(GroupDev g, const IterState* st) {
+  using Q = Q2048;
+  constexpr int N = Q::N, H = Q::H, T = 32, P = 32;
+  extern __shared__ float2 sm[];
+  if (st && skip_iter<BF>(st)) return;
+  const int j = threadIdx.x >> 5, t = threadIdx.x & 31;
+  int vcol, s;
+  column_of(blockIdx.x, g.S, N + 1, vcol, s);
+  using IO = SpecIO<BF>;
+  typename IO::T* p = reinterpret_cast<typename IO::T*>(g.spec) + ((size_t)s * (N + 1) + vcol) * N;
+  float2* col = sm;
+  for (int r = threadIdx.x; r < N; r += 128) col[r] = IO::ld(p, r);
+  __syncthreads();
+  float2 v[P];
+  SFor<0, P>::run([&](auto i_) {
+    constexpr int i = decltype(i_)::value;
+    const int m = t + T * i;
+    const float2 a0 = col[m], b = col[m + H];
+    float2 c;
+    if (j == 0)
+      c = cadd(a0, b);
+    else if (j == 1)
+      c = make_float2(a0.x + b.y, a0.y - b.x);  // a + (-i) b
+    else if (j == 2)
+      c = csub(a0, b);
+    else
+      c = make_float2(a0.x - b.y, a0.y + b.x);  // a + i b
+    if (j) c = cmul(c, tw4096(g.twM, j * m));
+    v[i] = c;
+  });
+  float2* xs = sm + N + j * Q::F::SMEM;
+  Q::F::template run<-1, float2, 2>(v, xs, g.twN, t);
+  // v[i] = X[4k + j], k = t + 32 i: row 4k + j of the 2N grid is row 2k + (j >> 1) of the
+  // (j & 1) half of the kernel spectrum
+  const float* cc = g.chat + ((size_t)vcol * 2 + (j & 1)) * N + (j >> 1);
+  SFor<0, P>::run([&](auto i_) {
+    constexpr int i = decltype(i_)::value;
+    const float c = __ldg(&cc[2 * (t + T * i)]);
+    v[i] = make_float2(v[i].x * c, v[i].y * c);
+  });
+  Q::F::template run<1, float2, 2>(v, xs, g.twN, t);
+  __syncwarp();  // the transform's last exchange reads are done: the buffer takes W^(-jm) u_j
+  SFor<0, P>::run([&](auto i_) {
+    constexpr int i = decltype(i_)::value;
+    const int m = t + T * i;
+    xs[m] = j ? cmulc(v[i], tw4096(g.twM, j * m)) : v[i];
+  });
+  __syncthreads();
+  // kept rows: z[m] = v_0 + v_1 + v_2 + v_3, z[m + 1024] = (v_0 - v_2) + i (v_1 - v_3)
+  const float2* b0 = sm + N;
+  for (int m = threadIdx.x; m < H; m += 128) {
+    const float2 a0 = b0[m], a1 = b0[Q::F::SMEM + m], a2 = b0[2 * Q::F::SMEM + m], a3 = b0[3 * Q::F::SMEM + m];
+    const float2 s02 = cadd(a0, a2), d02 = csub(a0, a2), s13 = cadd(a1, a3), d13 = csub(a1, a3);
+    IO::st(p, m, cadd(s02, s13));
+    IO::st(p, m + H, make_float2(d02.x - d13.y, d02.y + d13.x));
+  }
+}
+
+template <bool BF>
+__global__ void __launch_bounds__(64 * Q2048::RB3, 1) k_pass3a_q(GroupDev g, const IterState* st, float* kz) {
+  using Q = Q2048;
+  constexpr int N = Q::N, T = 32, P = 32, RB = Q::RB3, LDZ = Q::LDZ, THREADS = 64 * RB, NB = N / RB;
+  extern __shared__ float2 sm[];
+  if (st && skip_iter<BF>(st)) return;
+  const int s = blockIdx.x / NB, rb = blockIdx.x % NB;
+  const int warp = threadIdx.x >> 5, t = threadIdx.x & 31, rl = warp >> 1, j = warp & 1;
+  const int r0 = rb * RB;
+  {
+    using IO = SpecIO<BF>;
+    const typename IO::T* sp = reinterpret_cast<const typename IO::T*>(g.spec) + (size_t)s * (N + 1) * N + r0;
+    if constexpr (!BF) {
+      // RB-row segments of the column-major spectrum, all copies in flight at once
+      for (int e = threadIdx.x; e < (N + 1) * RB; e += THREADS) {
+        const int vv = e / RB, rr = e - vv * RB;
+        tc05::cp_async8(&sm[rr * LDZ + vv], sp + (size_t)vv * N + rr);
+      }
+      tc05::cp_async_wait_all();
+    } else {
+      for (int e = threadIdx.x; e < (N + 1) * RB; e += THREADS) {
+        const int vv = e / RB, rr = e - vv * RB;
+        sm[rr * LDZ + vv] = IO::ld(sp, (size_t)vv * N + rr);
+      }
+    }
+  }
+  __syncthreads();
+  // the length-2N real inverse as the length-N complex inverse of Z[v] = E[v] + i O[v], at the
+  // v = 2k + j of this warp
+  float2 q[P];
+  const float2* row = sm + rl * LDZ;
+  SFor<0, P>::run([&](auto i_) {
+    constexpr int i = decltype(i_)::value;
+    const int vp = 2 * (t + T * i) + j;
+    const float2 zv = row[vp], zr = row[N - vp];
+    const float2 e = make_float2(zv.x + zr.x, zv.y - zr.y);
+    const float2 d = make_float2(zv.x - zr.x, zv.y + zr.y);
+    const float2 o = cmulc(d, __ldg(&g.twM[vp]));
+    q[i] = make_float2(e.x - o.y, e.y + o.x);
+  });
+  __syncthreads();  // the staged rows are read: the exchange buffers alias them
+  float2* xs = sm + warp * Q::F::SMEM;
+  Q::F::template run<1, float2, 2>(q, xs, g.twN, t);
+  __syncwarp();
+  SFor<0, P>::run([&](auto i_) {
+    constexpr int i = decltype(i_)::value;
+    const int n = t + T * i;
+    xs[n] = j ? cmulc(q[i], __ldg(&g.twM[2 * n])) : q[i];  // w^(-jn) u_j[n]
+  });
+  __syncthreads();
+  // z[n] = sum_j w^(-jn) u_j[n]: each warp of the row sums one half of it
+  const float2* o0 = sm + (2 * rl) * Q::F::SMEM;
+  float2* out = reinterpret_cast<float2*>(kz + ((size_t)s * N + r0 + rl) * N);
+  for (int n = j * (Q::H / 2) + t; n < (j + 1) * (Q::H / 2); n += 32) out[n] = cadd(o0[n], o0[Q::F::SMEM + n]);
 }
 
 // ---------------------------------------------------------------- pass 3b: gradient and update
@@ -897,8 +1122,8 @@ __global__ void __launch_bounds__(GeoP<N>::THREADS, 2)
     x = cur == 0 ? a.xb[0] : (cur == 1 ? a.xb[1] : a.xb[2]);
     xp = cur == 0 ? a.xb[2] : (cur == 1 ? a.xb[0] : a.xb[1]);
     out = cur == 0 ? a.xb[1] : (cur == 1 ? a.xb[2] : a.xb[0]);
-    beta = (float)a.st->beta;
-    invL = (float)a.st->invL;
+    beta = (float)a.gm->beta;
+    invL = (float)a.gm->invL;
   } else {
     x = a.x;
     xp = a.xprev;
@@ -1051,7 +1276,16 @@ static int set_smem_limits() {
   using Gr = Geo3a<N>;
   static bool done = false;
   if (done) return TMBIR_OK;
-  if constexpr (is_block_fft_size<N>()) {
+  if constexpr (N == 2048) {
+    using Q = Q2048;
+    const int s1 = (int)Q::sm_rows<Q::RB1>(), s3 = (int)Q::sm_rows<Q::RB3>();
+    TMBIR_CUDA(cudaFuncSetAttribute(k_pass1_q<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, s1));
+    TMBIR_CUDA(cudaFuncSetAttribute(k_pass1_q<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, s1));
+    TMBIR_CUDA(cudaFuncSetAttribute(k_pass2_q<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Q::SM2));
+    TMBIR_CUDA(cudaFuncSetAttribute(k_pass2_q<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Q::SM2));
+    TMBIR_CUDA(cudaFuncSetAttribute(k_pass3a_q<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, s3));
+    TMBIR_CUDA(cudaFuncSetAttribute(k_pass3a_q<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, s3));
+  } else if constexpr (is_block_fft_size<N>()) {
     using BG = BGeo<N>;
     TMBIR_CUDA(cudaFuncSetAttribute(k_pass1_b<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BG::SM_ROWS));
     TMBIR_CUDA(cudaFuncSetAttribute(k_pass1_b<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BG::SM_ROWS));
@@ -1081,7 +1315,14 @@ template <int N>
 static int pass1_n(const GroupDev& g, const StepArgs& a, bool bf16, cudaStream_t s) {
   using Gm = Geo<N>;
   if (int e = set_smem_limits<N>()) return e;
-  if constexpr (is_block_fft_size<N>()) {
+  if constexpr (N == 2048) {
+    using Q = Q2048;
+    const int blocks = g.S * (N / Q::RB1);
+    if (bf16)
+      k_pass1_q<true><<<blocks, 64 * Q::RB1, Q::sm_rows<Q::RB1>(), s>>>(g, a);
+    else
+      k_pass1_q<false><<<blocks, 64 * Q::RB1, Q::sm_rows<Q::RB1>(), s>>>(g, a);
+  } else if constexpr (is_block_fft_size<N>()) {
     using BG = BGeo<N>;
     if (bf16)
       k_pass1_b<N, true><<<g.S * BG::NB, BG::THREADS, BG::SM_ROWS, s>>>(g, a);
@@ -1100,7 +1341,13 @@ template <int N>
 static int pass2_n(const GroupDev& g, const IterState* st, bool bf16, cudaStream_t s) {
   using Gm = Geo<N>;
   if (int e = set_smem_limits<N>()) return e;
-  if constexpr (is_block_fft_size<N>()) {
+  if constexpr (N == 2048) {
+    const int blocks = g.S * (N + 1);
+    if (bf16)
+      k_pass2_q<true><<<blocks, 128, Q2048::SM2, s>>>(g, st);
+    else
+      k_pass2_q<false><<<blocks, 128, Q2048::SM2, s>>>(g, st);
+  } else if constexpr (is_block_fft_size<N>()) {
     using BG = BGeo<N>;
     const int blocks = g.S * (N + 1);
     if (bf16)
@@ -1142,7 +1389,14 @@ static int pass3_n(const GroupDev& g, const StepArgs& a, Pass3Mode m, const Prio
   float* kz = m == Pass3Mode::Apply ? a.out + g.img_off : g.kz;
   const IterState* st = m == Pass3Mode::Iterate ? a.st : nullptr;
   if (part & 1) {
-    if constexpr (is_block_fft_size<N>()) {
+    if constexpr (N == 2048) {
+      using Q = Q2048;
+      const int blocks = g.S * (N / Q::RB3);
+      if (bf16)
+        k_pass3a_q<true><<<blocks, 64 * Q::RB3, Q::sm_rows<Q::RB3>(), s>>>(g, st, kz);
+      else
+        k_pass3a_q<false><<<blocks, 64 * Q::RB3, Q::sm_rows<Q::RB3>(), s>>>(g, st, kz);
+    } else if constexpr (is_block_fft_size<N>()) {
       using BG = BGeo<N>;
       if (bf16)
         k_pass3a_b<N, true><<<g.S * BG::NB, BG::THREADS, BG::SM_ROWS, s>>>(g, st, kz);

@@ -162,7 +162,7 @@ def test_n2048_limited_angle(orc, n2048):
     assert rel(host(xs, x.shape), ref) < 1e-4
 
 
-N2048_BF16_ITERS, N2048_TOTAL_ITERS = 4, 24
+N2048_BF16_ITERS, N2048_TOTAL_ITERS = 4, 12
 
 
 def test_n2048_bf16_refinement_follows_oracle(orc, n2048):

@@ -388,6 +388,46 @@ def test_uneven_groups_equal_separate_contexts(orc):
         off += n
 
 
+def test_uneven_groups_reconstruct_like_separate_contexts(orc):
+    """Groups are independent problems (Sec. 2: the data term is slice-separable and the prior
+    couples only the slices of a group): each keeps its own step constant, momentum and restart
+    test, so 25 iterations of an uneven batch give, group by group, bitwise the iterates of a
+    context holding that group alone (graph and eager launches), and follow the FP64 oracle's
+    fast gradient method on that group."""
+    specs = [(64, 2, 30), (128, 1, 50), (64, 1, 20)]
+    iters = 25
+    groups, sinos, thetas = [], [], []
+    for k, (N, S, na) in enumerate(specs):
+        p = synth.volume(S=S, N=N, n_angles=na, n_ellipsoids=4, seed=40 + k)
+        groups.append(tm.Group(N=N, angles=list(p.theta), n_slices=S))
+        sinos.append(p.sino.ravel())
+        thetas.append(p.theta)
+    big = tm.Context(groups)
+    atg = big.build_operator(dev(np.concatenate(sinos)))
+    xg = torch.zeros(atg.numel(), dtype=torch.float32, device="cuda")
+    xe = torch.zeros_like(xg)
+    sg = big.reconstruct(xg, atg, tm.Params(**PRIOR, max_iter=iters, use_graph=True))
+    big.reconstruct(xe, atg, tm.Params(**PRIOR, max_iter=iters, use_graph=False))
+    torch.cuda.synchronize()
+    assert sg.iterations == iters and torch.equal(xg, xe)
+    pr = orc.Prior(**PRIOR)
+    off = 0
+    for k, (N, S, na) in enumerate(specs):
+        n = S * N * N
+        ctx = tm.Context([groups[k]])
+        a1 = ctx.build_operator(dev(sinos[k]))
+        x1 = torch.zeros(n, dtype=torch.float32, device="cuda")
+        ctx.reconstruct(x1, a1, tm.Params(**PRIOR, max_iter=iters))
+        torch.cuda.synchronize()
+        assert torch.equal(xg[off:off + n], x1), k
+        g = sinos[k].reshape(S, na, N).astype(np.float64)
+        K = orc.kernel(N, thetas[k], N)
+        ref = orc.nesterov(np.zeros((S, N, N)), orc.adjoint(g, N, thetas[k]), float(np.sum(g * g)), K, pr,
+                           orc.lipschitz(K, N, pr), iters)
+        assert rel(host(xg[off:off + n], (S, N, N)), ref) < 1e-4, k
+        off += n
+
+
 def test_identical_groups_give_identical_results():
     p = synth.volume(S=2, N=64, n_angles=24, n_ellipsoids=4, seed=50)
     grp = tm.Group(N=64, angles=list(p.theta), n_slices=2)

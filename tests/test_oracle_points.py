@@ -1,5 +1,5 @@
 """The single-voxel oracle functions the full-size GPU parity tests sample (normal_point,
-adjoint_point, prior_point, and the FBP start at a pixel) equal the corresponding entries of the
+adjoint_point, forward_point, prior_point, and the FBP start at a pixel) equal the corresponding entries of the
 whole-array oracle functions, at corners, edges and interior voxels."""
 import math
 
@@ -52,3 +52,12 @@ def test_fbp_at_a_pixel_equals_the_fbp_image(orc):
     for r, c in [(0, 0), (15, 15), (7, 8), (2, 13)]:
         v = (math.pi / th.size) * orc.adjoint_point(filtered, N, th, r, c)
         assert abs(v - full[r, c]) <= 1e-12 * np.abs(full).max()
+
+
+def test_forward_point_equals_the_forward_projection(orc):
+    N = 12
+    th = synth.angles(9, 2 * math.pi / 3)
+    x = np.random.default_rng(25).standard_normal((N, N))
+    full = orc.forward(x, th, N)
+    for a, m in [(0, 0), (8, 11), (4, 6), (2, 0), (6, 9)]:
+        assert abs(orc.forward_point(x, th[a], N, m) - full[a, m]) <= 1e-12 * np.abs(full).max()
