@@ -502,7 +502,7 @@ class Context:
 
 
 def reconstruct_levels(N: int, angles, n_slices: int, sino, levels: int, params, span: float = math.pi,
-                       stream=None, device="cuda", start=None, ctxs=None):
+                       stream=None, device="cuda", start=None, ctxs=None, overlap_setup: bool = False):
     """Hierarchical reconstruction (Sec. 2.3) through the C ABI.
 
     Level l = 0 .. levels-1 reconstructs n_slices slices of N / 2^(levels-1-l) pixels.  A
@@ -510,9 +510,13 @@ def reconstruct_levels(N: int, angles, n_slices: int, sino, levels: int, params,
     divided by f (tmbir_downsample_sino, f = 2^(levels-1-l)); the coarsest level starts from
     its FBP image (or from `start`, a callable (ctx, sino_l, atg_l) -> image), every finer
     level from the Lanczos-3 x2 upsampling of the level below (tmbir_upsample_lanczos3).
-    `params` is one Params per level.  All levels share one stream; `ctxs` (the list a
-    previous call returned) reuses the level contexts and their workspaces.  Returns the
-    finest image, the level contexts and the per-level Stats.
+    `params` is one Params per level.  `ctxs` (the list a previous call returned) reuses the
+    level contexts and their workspaces.  With overlap_setup, every level's setup (its
+    subsampled sinogram, kernel spectrum and R*g, which depend on the data only) is enqueued
+    first on that level's own context stream, so the setups of the finer levels run while the
+    coarser levels iterate; the contexts must then have distinct streams (created here when
+    `ctxs` is None).  Without it all levels share one stream and run one after another.
+    Returns the finest image, the level contexts and the per-level Stats.
     """
     import torch
 
@@ -521,13 +525,17 @@ def reconstruct_levels(N: int, angles, n_slices: int, sino, levels: int, params,
     if N % (1 << (levels - 1)):
         raise ValueError("N must be divisible by 2^(levels-1)")
     if ctxs is None:
-        stream = stream if stream is not None else torch.cuda.Stream(device=torch.device(device))
+        dev = torch.device(device)
+        shared = stream if stream is not None else torch.cuda.Stream(device=dev)
         ctxs = [Context([Group(N=N >> (levels - 1 - lev), angles=list(angles), n_slices=n_slices, span=span)],
-                        stream=stream, device=device) for lev in range(levels)]
+                        stream=torch.cuda.Stream(device=dev) if overlap_setup else shared, device=device)
+                for lev in range(levels)]
+    if overlap_setup and len({c.stream.cuda_stream for c in ctxs}) != levels:
+        raise ValueError("overlap_setup needs one stream per level context")
     na = len(angles)
-    stats = []
-    x = None
-    for lev in range(levels):
+    caller = torch.cuda.current_stream(ctxs[0].device)
+
+    def setup(lev):
         f = 1 << (levels - 1 - lev)
         Nl = N // f
         ctx = ctxs[lev]
@@ -537,17 +545,35 @@ def reconstruct_levels(N: int, angles, n_slices: int, sino, levels: int, params,
             ctx._lv = {"x": ctx._empty(n_slices * Nl * Nl), "atg": ctx._empty(n_slices * Nl * Nl),
                        "sino": ctx._empty(n_slices * na * Nl) if f > 1 else None}
         lv = ctx._lv
-        sino_l = sino if f == 1 else ctx.downsample_sino(sino, n_slices, na, N, f, out=lv["sino"])
-        atg = ctx.build_operator(sino_l, lv["atg"])
-        if x is None:
-            if start is not None:
-                lv["x"].copy_(start(ctx, sino_l, atg))
+        lv["sino_l"] = sino if f == 1 else ctx.downsample_sino(sino, n_slices, na, N, f, out=lv["sino"])
+        ctx.build_operator(lv["sino_l"], lv["atg"])
+
+    if overlap_setup:
+        for lev in range(levels):
+            ctxs[lev].stream.wait_stream(caller)  # the sinogram is ready on the caller's stream
+            with torch.cuda.stream(ctxs[lev].stream):
+                setup(lev)
+    stats = []
+    x = None
+    for lev in range(levels):
+        ctx = ctxs[lev]
+        with torch.cuda.stream(ctx.stream if overlap_setup else caller):
+            if not overlap_setup:
+                setup(lev)
+            lv = ctx._lv
+            if x is None:
+                if start is not None:
+                    lv["x"].copy_(start(ctx, lv["sino_l"], lv["atg"]))
+                else:
+                    ctx.fbp(lv["sino_l"], lv["x"])
             else:
-                ctx.fbp(sino_l, lv["x"])
-        else:
-            ctx.upsample_lanczos3(x, n_slices, Nl // 2, out=lv["x"])
-        x = lv["x"]
-        stats.append(ctx.reconstruct(x, atg, params[lev]))
+                if overlap_setup:
+                    ctx.stream.wait_stream(ctxs[lev - 1].stream)  # the coarser level's result
+                ctx.upsample_lanczos3(x, n_slices, (N >> (levels - 1 - lev)) // 2, out=lv["x"])
+            x = lv["x"]
+            stats.append(ctx.reconstruct(x, lv["atg"], params[lev]))
+    if overlap_setup:
+        caller.wait_stream(ctxs[-1].stream)
     return x, ctxs, stats
 
 

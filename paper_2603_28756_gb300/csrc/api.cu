@@ -856,6 +856,13 @@ int tmbir_gradient_direct(tmbir_ctx* ctx, const float* d_x, const float* d_sino,
     off += blocks_pass3(c.gdev[i]);
   }
   if (h_F) {
+    // Phi(x) for the objective: the Gradient-mode stencil does not accumulate it, the Objective
+    // mode does (its other partial sums are not used here)
+    off = 0;
+    for (int i = 0; i < ng; ++i) {
+      if (int e = launch_pass3(c.gdev[i], a, Pass3Mode::Objective, pc, c.partials, off, s, false, 2)) return e;
+      off += blocks_pass3(c.gdev[i]);
+    }
     if (int e = launch_sum_partials(c.partials, off, c.dscal, s)) return e;
     std::vector<double> h(16 + ng);
     TMBIR_CUDA(cudaMemcpyAsync(h.data(), c.dscal, h.size() * sizeof(double), cudaMemcpyDeviceToHost, s));

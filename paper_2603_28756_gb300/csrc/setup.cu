@@ -45,6 +45,25 @@ __device__ __forceinline__ void stockham_stage(const C* X, C* Y, int n, int Ls, 
   }
 }
 
+// X[perm(j)] = row[j] for j < n, in batches of eight loads per thread issued before their stores
+// (a long row fills a block alone, so nothing else on the SM hides the load latency)
+template <class C, class Perm>
+__device__ __forceinline__ void load_row(const C* __restrict__ row, C* X, int n, Perm perm) {
+  for (int j0 = threadIdx.x; j0 < n; j0 += 8 * blockDim.x) {
+    C v[8];
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+      const int j = j0 + b * blockDim.x;
+      if (j < n) v[b] = row[j];
+    }
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+      const int j = j0 + b * blockDim.x;
+      if (j < n) X[perm(j)] = v[b];
+    }
+  }
+}
+
 // plan: the radices, one per 4-bit digit from the lowest (built by fft_plan)
 template <int DIR, class C>
 __global__ void __launch_bounds__(256) k_fft_rows(C* data, int n, unsigned plan, size_t stride, const C* __restrict__ tw) {
@@ -52,7 +71,7 @@ __global__ void __launch_bounds__(256) k_fft_rows(C* data, int n, unsigned plan,
   C* X = reinterpret_cast<C*>(smraw);
   C* Y = X + n;
   C* row = data + (size_t)blockIdx.x * stride;
-  for (int j = threadIdx.x; j < n; j += blockDim.x) X[j] = row[j];
+  load_row(row, X, n, [](int j) { return j; });
   __syncthreads();
   int Ls = 1;
   for (; plan != 0; plan >>= 4) {
@@ -81,7 +100,7 @@ __global__ void __launch_bounds__(1024) k_fft_rows_inplace(C* data, int n, int l
   extern __shared__ unsigned char smraw[];
   C* X = reinterpret_cast<C*>(smraw);
   C* row = data + (size_t)blockIdx.x * stride;
-  for (int j = threadIdx.x; j < n; j += blockDim.x) X[__brev((unsigned)j) >> (32 - log2n)] = row[j];
+  load_row(row, X, n, [log2n](int j) { return (int)(__brev((unsigned)j) >> (32 - log2n)); });
   __syncthreads();
   for (int half = 1, tstep = n / 2; half < n; half <<= 1, tstep >>= 1) {
     for (int b = threadIdx.x; b < n / 2; b += blockDim.x) {

@@ -52,6 +52,26 @@ __device__ __forceinline__ bool skip_iter(const IterState* st) {
   return st->done || (st->bf16 != 0) != BF;
 }
 
+// Copies count elements, e = threadIdx.x + k * NT, from ld(e) to st(e, v) in batches of B whose
+// loads are all issued before their stores, so that a thread keeps B global loads in flight
+// instead of waiting out each load's latency before the next.
+template <int NT, int B, class Ld, class St>
+__device__ __forceinline__ void batched_copy(int count, Ld&& ld, St&& st) {
+  for (int e0 = threadIdx.x; e0 < count; e0 += B * NT) {
+    float2 v[B];
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      const int e = e0 + b * NT;
+      v[b] = e < count ? ld(e) : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      const int e = e0 + b * NT;
+      if (e < count) st(e, v[b]);
+    }
+  }
+}
+
 // ---------------------------------------------------------------- launch geometry
 template <int N, int Wp = 4>
 struct Geo {
@@ -360,10 +380,9 @@ __global__ void TMBIR_P3A_BOUNDS(Geo3a<N>::THREADS) k_pass3a(GroupDev g, const I
       }
       tc05::cp_async_wait_all();
     } else {
-      for (int e = threadIdx.x; e < (N + 1) * RB; e += Gm::THREADS) {
-        const int vv = e / RB, rr = e - vv * RB;
-        tb[rr * LD + vv] = IO::ld(sp, (size_t)vv * N + rr);
-      }
+      batched_copy<Gm::THREADS, 8>(
+          (N + 1) * RB, [&](int e) { return IO::ld(sp, (size_t)(e / RB) * N + e % RB); },
+          [&](int e, float2 v) { tb[(e % RB) * LD + e / RB] = v; });
     }
   }
   __syncthreads();
@@ -429,15 +448,15 @@ __global__ void __launch_bounds__(256) k_pass1_b(GroupDev g, StepArgs a) {
     __syncthreads();  // the previous row's transform has been read
     const size_t base = g.img_off + ((size_t)s * N + rb * BG::RB + rr) * N;
     // packed real row z[n] = y[2n] + i y[2n+1] for n < N/2, zero padding above
-    for (int n = threadIdx.x; n < N; n += BG::THREADS) {
-      float2 v = make_float2(0.f, 0.f);
-      if (n < N / 2) {
-        const float2 xv = __ldg(reinterpret_cast<const float2*>(x + base) + n);
-        const float2 pv = __ldg(reinterpret_cast<const float2*>(xp + base) + n);
-        v = make_float2(fmaf(beta, xv.x - pv.x, xv.x), fmaf(beta, xv.y - pv.y, xv.y));
-      }
-      X[n] = v;
-    }
+    batched_copy<BG::THREADS, 4>(
+        N / 2,
+        [&](int n) {
+          const float2 xv = __ldg(reinterpret_cast<const float2*>(x + base) + n);
+          const float2 pv = __ldg(reinterpret_cast<const float2*>(xp + base) + n);
+          return make_float2(fmaf(beta, xv.x - pv.x, xv.x), fmaf(beta, xv.y - pv.y, xv.y));
+        },
+        [&](int n, float2 v) { X[n] = v; });
+    for (int n = N / 2 + threadIdx.x; n < N; n += BG::THREADS) X[n] = make_float2(0.f, 0.f);
     const float2* Z = block_fft<N, -1>(X, Y, g.twN);
     // Y[v] = E[v] + w^v O[v] from Z[v] and Z[N - v]; the Nyquist term Y[N] = Re Z0 - Im Z0
     for (int v = threadIdx.x; v < N; v += BG::THREADS) {
@@ -470,7 +489,7 @@ __global__ void __launch_bounds__(256) k_pass2_b(GroupDev g, const IterState* st
   float2* Y = sm + N;
   float2* col = sm + 2 * N;
   float2* sum = sm + 3 * N;
-  for (int r = threadIdx.x; r < N; r += BG::THREADS) col[r] = IO::ld(p, r);
+  batched_copy<BG::THREADS, 8>(N, [&](int r) { return IO::ld(p, r); }, [&](int r, float2 v) { col[r] = v; });
   for (int h = 0; h < 2; ++h) {
     __syncthreads();
     // even half: the column; odd half: the column times exp(-2 pi i r / 2N)
@@ -504,10 +523,9 @@ __global__ void __launch_bounds__(256) k_pass3a_b(GroupDev g, const IterState* s
   {
     using IO = SpecIO<BF>;
     const typename IO::T* sp = reinterpret_cast<const typename IO::T*>(g.spec) + (size_t)s * (N + 1) * N + r0;
-    for (int e = threadIdx.x; e < (N + 1) * BG::RB; e += BG::THREADS) {
-      const int vv = e / BG::RB, rr = e - vv * BG::RB;
-      tb[rr * BG::LD + vv] = IO::ld(sp, (size_t)vv * N + rr);
-    }
+    batched_copy<BG::THREADS, 8>(
+        (N + 1) * BG::RB, [&](int e) { return IO::ld(sp, (size_t)(e / BG::RB) * N + e % BG::RB); },
+        [&](int e, float2 v) { tb[(e % BG::RB) * BG::LD + e / BG::RB] = v; });
   }
   for (int rr = 0; rr < BG::RB; ++rr) {
     __syncthreads();
@@ -633,7 +651,16 @@ __global__ void __launch_bounds__(128, 3) k_pass2_q(GroupDev g, const IterState*
   using IO = SpecIO<BF>;
   typename IO::T* p = reinterpret_cast<typename IO::T*>(g.spec) + ((size_t)s * (N + 1) + vcol) * N;
   float2* col = sm;
-  for (int r = threadIdx.x; r < N; r += 128) col[r] = IO::ld(p, r);
+  if constexpr (!BF) {
+    // all of the column's copies in flight at once
+    SFor<0, N / 128>::run([&](auto i_) {
+      constexpr int i = decltype(i_)::value;
+      tc05::cp_async8(&col[threadIdx.x + 128 * i], p + threadIdx.x + 128 * i);
+    });
+    tc05::cp_async_wait_all();
+  } else {
+    batched_copy<128, 16>(N, [&](int r) { return IO::ld(p, r); }, [&](int r, float2 v) { col[r] = v; });
+  }
   __syncthreads();
   float2 v[P];
   SFor<0, P>::run([&](auto i_) {
@@ -700,10 +727,9 @@ __global__ void __launch_bounds__(64 * Q2048::RB3, 1) k_pass3a_q(GroupDev g, con
       }
       tc05::cp_async_wait_all();
     } else {
-      for (int e = threadIdx.x; e < (N + 1) * RB; e += THREADS) {
-        const int vv = e / RB, rr = e - vv * RB;
-        sm[rr * LDZ + vv] = IO::ld(sp, (size_t)vv * N + rr);
-      }
+      batched_copy<THREADS, 8>(
+          (N + 1) * RB, [&](int e) { return IO::ld(sp, (size_t)(e / RB) * N + e % RB); },
+          [&](int e, float2 v) { sm[(e % RB) * LDZ + e / RB] = v; });
     }
   }
   __syncthreads();
