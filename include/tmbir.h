@@ -100,6 +100,9 @@ typedef struct {
  *                   the context holds (the previous tmbir_reconstruct, or a checkpoint loaded
  *                   by tmbir_state_import) for max_iter more iterations; d_x must hold that
  *                   run's x_k.  The result is bitwise the one an uninterrupted run gives.
+ *   nonneg          1: project every iterate onto x >= 0 (x_{k+1} = max(y - G/L, 0)), the
+ *                   fast gradient method on Eq. 5 restricted to non-negative images (a variant:
+ *                   Eq. 5 itself has no constraint); 0: unconstrained.
  */
 typedef struct {
   double p, q, c, sigma, lambda;
@@ -112,6 +115,7 @@ typedef struct {
   int spectra;
   double refine_gap;
   int resume;
+  int nonneg;
 } tmbir_params;
 
 /* Result of tmbir_reconstruct (host struct filled on return). */

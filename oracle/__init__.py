@@ -320,7 +320,8 @@ def lipschitz(K, N: int, pr: Prior, steps: int = 100, Chat=None) -> float:
 # ----------------------------------------------------------------------------- optimisers
 
 
-def nesterov(x0, atg, gtg: float, K, pr: Prior, L: float, iters: int, Chat=None, log=None, restart="gradient"):
+def nesterov(x0, atg, gtg: float, K, pr: Prior, L: float, iters: int, Chat=None, log=None, restart="gradient",
+             nonneg=False):
     """Fast gradient method with adaptive restart (Sec. 2, which cites the restarted scheme
     without stating the test).
 
@@ -333,7 +334,9 @@ def nesterov(x0, atg, gtg: float, K, pr: Prior, L: float, iters: int, Chat=None,
         "gradient": <G, x_new - x> > 0
         "function": F(y_k) > F(y_{k-1})
         "none":     never
-    ``log`` (a list) receives (F(y_k), <G,x_new-x>, restarted) per step.
+    ``log`` (a list) receives (F(y_k), <G,x_new-x>, restarted) per step.  With ``nonneg`` every
+    x_new is projected onto x >= 0 (max(., 0)) before the restart test: the projected fast
+    gradient method on Eq. 5 restricted to non-negative images, a variant the paper does not use.
     """
     if restart not in ("gradient", "function", "none"):
         raise ValueError(restart)
@@ -351,6 +354,8 @@ def nesterov(x0, atg, gtg: float, K, pr: Prior, L: float, iters: int, Chat=None,
         gp, phi = prior(y, pr)
         G = z - atg + gp
         x_new = y - G / L
+        if nonneg:
+            x_new = np.maximum(x_new, 0.0)
         dot = float(np.sum(G * (x_new - x)))
         F = 0.5 * float(np.sum(y * z)) - float(np.sum(y * atg)) + 0.5 * gtg + phi
         if restart == "gradient":

@@ -60,6 +60,7 @@ class _Params(ctypes.Structure):
         ("spectra", ctypes.c_int),
         ("refine_gap", ctypes.c_double),
         ("resume", ctypes.c_int),
+        ("nonneg", ctypes.c_int),
     ]
 
 
@@ -189,11 +190,12 @@ class Params:
     bf16: bool = False  # BF16 storage of the intermediate spectrum
     refine_gap: float = 0.0  # with bf16: switch to FP32 spectra once the gap is <= refine_gap
     resume: bool = False  # continue the context's run (or an imported checkpoint)
+    nonneg: bool = False  # project every iterate onto x >= 0
 
     def c_struct(self) -> _Params:
         return _Params(self.p, self.q, self.c, self.sigma, self.lam, self.L, self.max_iter, self.gap_tol, self.F_ref,
                        self.restart, 1 if self.use_graph else 0, 1 if self.bf16 else 0, self.refine_gap,
-                       1 if self.resume else 0)
+                       1 if self.resume else 0, 1 if self.nonneg else 0)
 
 
 @dataclass

@@ -35,6 +35,7 @@ PriorC make_prior(const tmbir_params& p) {
   c.we = (float)(1.0 / std::sqrt(2.0) / total);
   c.wc = (float)(1.0 / std::sqrt(3.0) / total);
   c.q_is_2 = p.q == 2.0 ? 1 : 0;
+  c.nonneg = p.nonneg ? 1 : 0;
   c.l2_inv_csig = (float)std::log2(1.0 / (p.c * p.sigma));
   c.qp_l2_inv_csig = (float)((p.q - p.p) * std::log2(1.0 / (p.c * p.sigma)));
   c.l2_inv_sig = (float)std::log2(1.0 / p.sigma);

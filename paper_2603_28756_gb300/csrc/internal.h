@@ -78,6 +78,7 @@ struct PriorC {
   float qp_l2_inv_csig;  // (q - p) log2(1 / (c sigma))
   float l2_inv_sig;      // log2(1 / sigma)
   int q_is_2;
+  int nonneg;            // project each iterate onto x >= 0
 };
 
 // One geometry group as the kernels see it (device pointers into the workspace).

@@ -1265,7 +1265,8 @@ __global__ void __launch_bounds__(GeoP<N>::THREADS, 2)
           *reinterpret_cast<float2*>(out + img + ro) = Gv;
         } else if constexpr (UPDATE) {
           const float2 xv = v[2 * GP::THREADS];
-          const float2 xn = f2fma(f2(-invL), Gv, yv);
+          float2 xn = f2fma(f2(-invL), Gv, yv);
+          if (pc.nonneg) xn = make_float2(fmaxf(xn.x, 0.f), fmaxf(xn.y, 0.f));
           *reinterpret_cast<float2*>(out + img + ro) = xn;
           acc[3] = f2fma(Gv, f2fma(xv, f2(-1.f), xn), acc[3]);
         }

@@ -172,6 +172,23 @@ def test_batched_normal_operator_equals_slices_alone(prob):
         assert rel(z1, z[s]) < 1e-6
 
 
+def test_nonneg_projection_follows_oracle(prob, orc):
+    # the projected variant: every iterate max(y - G/L, 0); 30 iterations from a start with
+    # negative entries follow the oracle's projected method and stay non-negative
+    pr = orc.Prior(**PRIOR)
+    iters = 30
+    x0 = prob.x - 0.25
+    L = orc.lipschitz(prob.K, prob.N, pr)
+    x = dev(x0)
+    st = prob.ctx.reconstruct(x, prob.d_atg, tm.Params(**PRIOR, L=L, max_iter=iters, nonneg=True))
+    assert st.iterations == iters and st.status == 0
+    got = host(x, prob.x.shape)
+    ref = orc.nesterov(x0.astype(np.float32).astype(np.float64), prob.atg, float(np.sum(prob.g ** 2)), prob.K, pr, L,
+                       iters, nonneg=True)
+    assert got.min() >= 0.0 and np.mean(ref == 0.0) > 0.01
+    assert rel(got, ref) < 1e-4
+
+
 def test_graph_replay_is_bitwise_eager(prob):
     prm = dict(PRIOR, max_iter=7)
     a = torch.zeros(prob.x.size, dtype=torch.float32, device="cuda")

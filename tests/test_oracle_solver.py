@@ -94,6 +94,34 @@ def test_quadratic_case_reaches_linear_solve(orc):
     assert np.linalg.norm(xg - x_star) > np.linalg.norm(orc.nesterov(np.zeros((S, N, N)), atg, float(np.sum(g * g)), K, pr, L, 200) - x_star)
 
 
+def test_projected_method_reaches_the_bounded_least_squares_solution(orc):
+    # the quadratic case again, with data whose unconstrained minimiser has negative entries:
+    # the projected fast gradient method (x_{k+1} = max(y - G/L, 0)) reaches the minimiser over
+    # x >= 0, computed independently by non-negative least squares on a Cholesky factor of the
+    # dense system (|| R x - d ||^2 = x.H x - 2 rhs.x + const with H = R^T R, R^T d = rhs)
+    from scipy.linalg import cholesky, solve_triangular
+    from scipy.optimize import nnls
+
+    S, N, nd, na = 2, 6, 8, 5
+    pr = orc.Prior(p=2.0, q=2.0, sigma=0.5, lam=0.3)
+    rng = np.random.default_rng(25)
+    th = synth.angles(na)
+    g = rng.uniform(-1, 1, (S, na, nd))
+    A = np.stack([nudft_forward(e.reshape(N, N), th, nd).ravel() for e in np.eye(N * N)], axis=1)
+    H = np.kron(np.eye(S), A.T @ A) + pr.lam / pr.sigma ** 2 * gaussian_mrf_laplacian(orc, S, N)
+    rhs = np.concatenate([A.T @ g[s].ravel() for s in range(S)])
+    assert np.min(np.linalg.solve(H, rhs)) < -1e-2  # the bound is active
+    R = cholesky(H)  # upper: H = R^T R
+    x_star, _ = nnls(R, solve_triangular(R, rhs, trans="T"), maxiter=10000)
+    x_star = x_star.reshape(S, N, N)
+    K = orc.kernel(N, th, nd)
+    atg = orc.adjoint(g, N, th)
+    L = orc.lipschitz(K, N, pr)
+    x = orc.nesterov(np.zeros((S, N, N)), atg, float(np.sum(g * g)), K, pr, L, 5000, nonneg=True)
+    assert np.min(x) >= 0.0
+    assert np.linalg.norm(x - x_star) < 1e-6 * np.linalg.norm(x_star)
+
+
 def test_descent_is_monotone_and_nesterov_reaches_same_minimum(orc):
     pr = orc.Prior()
     th, g, K, atg, gtg = small_problem(orc, N=10, S=2)
