@@ -383,6 +383,15 @@ int tmbir_normal_apply_static(tmbir_ctx* ctx, const float* d_x, float* d_z);
  */
 int tmbir_wait_check(tmbir_ctx* ctx, unsigned polls, int arrive);
 
+/*
+ * Measurement (no counterpart in the paper): the special-function throughput of the device the
+ * context runs on.  Threads run independent chains of log2, exp2 and reciprocal, the three
+ * special-function operations per neighbour pair of the prior stencil, `iters` (1 .. 2^20) times
+ * eight chains per thread on eight blocks of 256 threads per SM; h_ops_per_s receives those
+ * operations per second over the timed launch (CUDA events on the context stream).  Synchronises.
+ */
+int tmbir_sfu_rate(tmbir_ctx* ctx, int iters, double* h_ops_per_s);
+
 /* Wait for the context stream; reports a pending CUDA error. */
 int tmbir_sync(tmbir_ctx* ctx);
 

@@ -85,7 +85,7 @@ SYMBOLS = [
     "tmbir_cnn_destroy", "tmbir_cnn_init", "tmbir_cnn_set_weights", "tmbir_cnn_get_weights", "tmbir_cnn_apply",
     "tmbir_cnn_train_step", "tmbir_cnn_net_forward", "tmbir_cnn_net_backward", "tmbir_warm_start",
     "tmbir_state_size", "tmbir_state_export", "tmbir_state_import", "tmbir_autotune", "tmbir_build_operator_fbp",
-    "tmbir_wait_check", "tmbir_forward", "tmbir_adjoint", "tmbir_gradient_direct",
+    "tmbir_wait_check", "tmbir_forward", "tmbir_adjoint", "tmbir_gradient_direct", "tmbir_sfu_rate",
 ]
 
 _lib = None
@@ -145,6 +145,7 @@ def load(path: str | None = None):
         "tmbir_forward": [vp, vp, vp],
         "tmbir_adjoint": [vp, vp, vp],
         "tmbir_gradient_direct": [vp, vp, vp, ctypes.POINTER(_Params), vp, dp],
+        "tmbir_sfu_rate": [vp, i, dp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -373,6 +374,13 @@ class Context:
                                           ctypes.byref(F) if want_objective else None))
         self._post(x, sino, out)
         return (out, F.value) if want_objective else out
+
+    def sfu_rate(self, iters: int = 4096) -> float:
+        """Measured special-function operations per second (log2, exp2, reciprocal chains)."""
+        out = ctypes.c_double()
+        self._pre()
+        _check(_lib.tmbir_sfu_rate(self._h, int(iters), ctypes.byref(out)))
+        return out.value
 
     def wait_check(self, polls: int, arrive: bool):
         """Run the library's bounded device wait on its own: returns when the wait completes

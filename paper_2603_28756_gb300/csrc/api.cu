@@ -224,7 +224,7 @@ int tmbir_set_geometry(tmbir_ctx* ctx, int n_groups, const tmbir_group* groups) 
   c.ws_bytes = 0;
   c.operator_built = false;
   c.nufft_beta64 = 2.30 * 12;
-  c.spread_beta = 2.30 * kSpreadW;
+  c.spread_beta = kSpreadBetaPerWidth * kSpreadW;
   c.psiK_h.assign(n_groups, {});
   c.psiA_h.assign(n_groups, {});
   c.geom_ready.assign(n_groups, false);
@@ -281,13 +281,13 @@ int tmbir_set_geometry(tmbir_ctx* ctx, int n_groups, const tmbir_group* groups) 
     c.off_K[i] = take((2 * N - 1) * (2 * N - 1) * sizeof(double));
     c.off_psiK[i] = take((2 * N - 1) * sizeof(double));
     c.off_psiA[i] = take(N * sizeof(double));
-    c.off_csr_ptr[i] = take((4 * N * N + 1) * sizeof(int));
+    c.off_csr_ptr[i] = take(((size_t)spread_grid((int)N) * spread_grid((int)N) + 1) * sizeof(int));
     c.off_csr_idx[i] = take(spread_nnz(gs[i]) * sizeof(int));
     c.off_csr_w[i] = take(spread_nnz(gs[i]) * sizeof(double));
     c.off_lam[i] = take(sizeof(double));
     c.off_gtg[i] = take(sizeof(double));
     nufft_psi_table(2 * N - 1, 4 * N, 12, c.nufft_beta64, c.psiK_h[i]);
-    nufft_psi_table(N, 2 * N, kSpreadW, c.spread_beta, c.psiA_h[i]);
+    nufft_psi_table(N, spread_grid((int)N), kSpreadW, c.spread_beta, c.psiA_h[i]);
   }
   c.off_xbuf0 = take(voxels * sizeof(float));
   c.off_xbuf1 = take(voxels * sizeof(float));

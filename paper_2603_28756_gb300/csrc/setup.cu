@@ -4,11 +4,11 @@
 // Polar samples xi_{a,k} = (k / n_det) (cos theta_a, sin theta_a), |k| <= n_det/2 - 1.
 //   K(d)    = (1/n_det) sum_{a,k} exp(+2 pi i xi . d),               d in [-(N-1), N-1]^2
 //   R*g(x)  = (1/n_det) sum_{a,k} G(a,k) exp(-2 pi i xi . x),       G(a,k) = sum_m g(a,m) exp(2 pi i k s_m / n_det)
-// The type-1 transform spreads the samples onto a 2x oversampled periodic grid with the
+// The type-1 transform spreads the samples onto an oversampled periodic grid with the
 // "exponential of semicircle" kernel psi(u) = exp(beta (sqrt(1 - (2u/w)^2) - 1)) (Barnett,
 // Magland & af Klinteberg 2019), takes a 2D FFT and divides each output mode by the
-// kernel's Fourier transform.  K (width 12) and R*g (width 10) run in FP64, the FBP start in
-// FP32.  K is spread with fixed-point integer atomics and R*g / FBP through a sorted sparse
+// kernel's Fourier transform.  K (4N grid, width 12) and R*g (5N/4 grid, width 14) run in
+// FP64, the FBP start (same grid as R*g) in FP32.  K is spread with fixed-point integer atomics and R*g / FBP through a sorted sparse
 // matrix, so every result is bit-reproducible.
 #include <algorithm>
 #include <cmath>
@@ -588,7 +588,7 @@ static bool kernel_direct(int N) {
 }
 
 size_t setup_scratch_bytes(const tmbir_group& g) {
-  const size_t N = g.N, nf_k = 4 * N, nf_a = 2 * N, M = 2 * N;
+  const size_t N = g.N, nf_k = 4 * N, nf_a = spread_grid(g.N), M = 2 * N;
   const size_t k_elems = kernel_direct(g.N) ? nf_k + 2 * M * M + (size_t)g.n_angles : nf_k + 2 * nf_k * nf_k;
   const size_t rows = (size_t)g.n_angles * g.n_det;
   const size_t B = std::min(g.n_slices, kBackprojBatch);
@@ -598,7 +598,7 @@ size_t setup_scratch_bytes(const tmbir_group& g) {
   return std::max(std::max(std::max(k_elems, a_elems) * sizeof(double2), csr_build) + 256, forward_scratch_bytes(g));
 }
 size_t fbp_scratch_bytes(const tmbir_group& g) {
-  const size_t N = g.N, nf_a = 2 * N;
+  const size_t N = g.N, nf_a = spread_grid(g.N);
   const size_t rows = (size_t)g.n_angles * g.n_det;
   const size_t B = std::min(g.n_slices, kBackprojBatch);
   const size_t a_elems = nf_a + B * rows + B * nf_a * nf_a + B * N * nf_a + (size_t)kBackprojBatch * rows;
@@ -700,7 +700,7 @@ static int circulant_spectrum(Ctx& c, int gi) {
 int build_spread_matrix(Ctx& c, int gi) {
   GroupDev& g = c.gdev[gi];
   cudaStream_t s = c.stream;
-  const int nf = 2 * g.N, ncells = nf * nf;
+  const int nf = spread_grid(g.N), ncells = nf * nf;
   const size_t total = (size_t)g.na * (g.nd - 1);
   const int blocks = (int)std::min<size_t>((total + 255) / 256, 152 * 16);
   int* cursor = reinterpret_cast<int*>(c.scratch);
@@ -727,7 +727,7 @@ template <class C>
 static int backproject_t(Ctx& c, int gi, const float* d_sino, float* d_out, bool ramp, float scale, char* scratch,
                          cudaStream_t s, bool local_out) {
   GroupDev& g = c.gdev[gi];
-  const int N = g.N, nf = 2 * N, nd = g.nd, na = g.na, ncells = nf * nf;
+  const int N = g.N, nf = spread_grid(N), nd = g.nd, na = g.na, ncells = nf * nf;
   const size_t rows = (size_t)na * nd;
   const int B = std::min(g.S, kBackprojBatch);
   C* tw = reinterpret_cast<C*>(scratch);
@@ -886,14 +886,14 @@ __global__ void k_unpack_pairs(const float2* __restrict__ rows, size_t per_pair,
 }
 
 size_t forward_scratch_bytes(const tmbir_group& g) {
-  const size_t nf = 2 * (size_t)g.N, np = (std::min(g.n_slices, kBackprojBatch) + 1) / 2;
+  const size_t nf = spread_grid(g.N), np = (std::min(g.n_slices, kBackprojBatch) + 1) / 2;
   return (nf + g.n_det + 2 * np * nf * nf + np * (size_t)g.n_angles * g.n_det) * sizeof(float2) + 256;
 }
 
 int forward_project(Ctx& c, int gi, const float* d_x, float* d_sino, cudaStream_t s) {
   GroupDev& g = c.gdev[gi];
   if (!s) s = c.stream;
-  const int N = g.N, nf = 2 * N, nd = g.nd, na = g.na;
+  const int N = g.N, nf = spread_grid(N), nd = g.nd, na = g.na;
   const size_t cells = (size_t)nf * nf, rows = (size_t)na * nd;
   const int B = std::min(g.S, kBackprojBatch);
   constexpr int PB = kBackprojBatch / 2;

@@ -663,22 +663,34 @@ __global__ void __launch_bounds__(128, 3) k_pass2_q(GroupDev g, const IterState*
   }
   __syncthreads();
   float2 v[P];
-  SFor<0, P>::run([&](auto i_) {
-    constexpr int i = decltype(i_)::value;
-    const int m = t + T * i;
-    const float2 a0 = col[m], b = col[m + H];
-    float2 c;
-    if (j == 0)
-      c = cadd(a0, b);
-    else if (j == 1)
-      c = make_float2(a0.x + b.y, a0.y - b.x);  // a + (-i) b
-    else if (j == 2)
-      c = csub(a0, b);
-    else
-      c = make_float2(a0.x - b.y, a0.y + b.x);  // a + i b
-    if (j) c = cmul(c, tw4096(g.twM, j * m));
-    v[i] = c;
-  });
+  // y_j[m] = W^(jm) (c[m] + (-i)^j c[m + 1024]) with m = t + 32 i; W^(jm) = W^(jt) W^(32 j i), the
+  // first factor one table read per thread, the second a compile-time constant per element
+  auto prologue = [&](auto J_) {
+    constexpr int J = decltype(J_)::value;
+    const float2 base = tw4096(g.twM, J * t);
+    SFor<0, P>::run([&](auto i_) {
+      constexpr int i = decltype(i_)::value;
+      const int m = t + T * i;
+      const float2 a0 = col[m], b = col[m + H];
+      float2 c;
+      if constexpr (J == 0)
+        c = cadd(a0, b);
+      else if constexpr (J == 1)
+        c = make_float2(a0.x + b.y, a0.y - b.x);  // a + (-i) b
+      else if constexpr (J == 2)
+        c = csub(a0, b);
+      else
+        c = make_float2(a0.x - b.y, a0.y + b.x);  // a + i b
+      if constexpr (J != 0) c = cmul(c, twmul<32 * J * i, 4096, -1>(base));
+      v[i] = c;
+    });
+  };
+  switch (j) {
+    case 0: prologue(std::integral_constant<int, 0>{}); break;
+    case 1: prologue(std::integral_constant<int, 1>{}); break;
+    case 2: prologue(std::integral_constant<int, 2>{}); break;
+    default: prologue(std::integral_constant<int, 3>{}); break;
+  }
   float2* xs = sm + N + j * Q::F::SMEM;
   Q::F::template run<-1, float2, 2>(v, xs, g.twN, t);
   // v[i] = X[4k + j], k = t + 32 i: row 4k + j of the 2N grid is row 2k + (j >> 1) of the
@@ -691,11 +703,23 @@ __global__ void __launch_bounds__(128, 3) k_pass2_q(GroupDev g, const IterState*
   });
   Q::F::template run<1, float2, 2>(v, xs, g.twN, t);
   __syncwarp();  // the transform's last exchange reads are done: the buffer takes W^(-jm) u_j
-  SFor<0, P>::run([&](auto i_) {
-    constexpr int i = decltype(i_)::value;
-    const int m = t + T * i;
-    xs[m] = j ? cmulc(v[i], tw4096(g.twM, j * m)) : v[i];
-  });
+  auto epilogue = [&](auto J_) {
+    constexpr int J = decltype(J_)::value;
+    const float2 base = tw4096(g.twM, J * t);
+    SFor<0, P>::run([&](auto i_) {
+      constexpr int i = decltype(i_)::value;
+      if constexpr (J == 0)
+        xs[t + T * i] = v[i];
+      else
+        xs[t + T * i] = cmulc(v[i], twmul<32 * J * i, 4096, -1>(base));
+    });
+  };
+  switch (j) {
+    case 0: epilogue(std::integral_constant<int, 0>{}); break;
+    case 1: epilogue(std::integral_constant<int, 1>{}); break;
+    case 2: epilogue(std::integral_constant<int, 2>{}); break;
+    default: epilogue(std::integral_constant<int, 3>{}); break;
+  }
   __syncthreads();
   // kept rows: z[m] = v_0 + v_1 + v_2 + v_3, z[m + 1024] = (v_0 - v_2) + i (v_1 - v_3)
   const float2* b0 = sm + N;
