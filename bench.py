@@ -638,6 +638,11 @@ def run_ours(args, tm, w, prob, stream, rank, world, local, barrier, extra):
         extra["F_ref"] = {"value": F_ref, "F0": F0, "finest_iterations": REF_ITERS,
                           "change_last_half_in_gap_units": (log[REF_ITERS // 2 - 1][0] - F_ref) / (F0 - F_ref),
                           "s": time.perf_counter() - t0}
+        # launch shapes of every level by timing (pass-3b slices per block, spectrum chunk, rows
+        # per block of the row passes where a side has variants)
+        extra["autotune"] = [{"N": c.groups[0].N, "pass3_slices_per_block": c.autotune(c._lv["x"], c._lv["atg"],
+                                                                                       tm_params()),
+                              "spectrum_chunk": c.spec_chunks} for c in H.ctxs]
         # the learned start at the coarsest level (outside the timed region)
         try:
             H.net, extra["warm_start_training"] = train_warm_start(tm, w, 1 << (LEVELS - 1), stream)

@@ -271,11 +271,14 @@ int tmbir_pass_times(tmbir_ctx* ctx, float* d_x, const float* d_atg, const tmbir
  *    spectra may then stay in L2 between them); chunks of 4, 8 and 16 slices and the whole
  *    group (the default) are timed over the whole group;
  *  - the slices a pass-3b block marches through (1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64 up to
- *    the slice count, and the default rule), timing pass 3b of one iteration.
+ *    the slice count, and the default rule), timing pass 3b of one iteration;
+ *  - for sides with transform variants (N = 2048), the rows per block of the row passes 1 and
+ *    3a (4 or 8; eight rows move 64-byte segments of the column-major spectrum, four rows leave
+ *    room for more blocks per SM), timing each pass.
  * The fastest of each is kept; h_zc and h_sc (either may be NULL) receive the choices per
  * group.  Later contexts of this process with the same image side and slice count start from
- * the choices.  The transform tile shapes are fixed per image side at compile time.  d_x is
- * not modified.
+ * the choices.  The other transform tile shapes are fixed per image side at compile time.  d_x
+ * is not modified.
  */
 int tmbir_autotune(tmbir_ctx* ctx, const float* d_x, const float* d_atg, const tmbir_params* prm, int* h_zc,
                    int* h_sc);

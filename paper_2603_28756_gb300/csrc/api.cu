@@ -50,6 +50,8 @@ static std::mutex g_tune_mu;
 static std::map<std::pair<int, int>, int> g_tuned_zc;
 // slices per spectrum chunk chosen by tmbir_autotune, keyed the same way
 static std::map<std::pair<int, int>, int> g_tuned_sc;
+// rows per block of passes 1 and 3a (sides with variants), keyed the same way
+static std::map<std::pair<int, int>, std::pair<int, int>> g_tuned_rb;
 
 static int tuned_zc(int N, int S) {
   std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -60,6 +62,11 @@ static int tuned_sc(int N, int S) {
   std::lock_guard<std::mutex> lk(g_tune_mu);
   auto it = g_tuned_sc.find({N, S});
   return it == g_tuned_sc.end() ? 0 : it->second;
+}
+static std::pair<int, int> tuned_rb(int N, int S) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tuned_rb.find({N, S});
+  return it == g_tuned_rb.end() ? std::make_pair(0, 0) : it->second;
 }
 
 // ---------------------------------------------------------------- small device kernels
@@ -224,9 +231,8 @@ int tmbir_set_geometry(tmbir_ctx* ctx, int n_groups, const tmbir_group* groups) 
   c.ws_bytes = 0;
   c.operator_built = false;
   c.nufft_beta64 = 2.30 * 12;
-  c.spread_beta = kSpreadBetaPerWidth * kSpreadW;
   c.psiK_h.assign(n_groups, {});
-  c.psiA_h.assign(n_groups, {});
+  for (int k = 0; k < 2; ++k) c.psiS_h[k].assign(n_groups, {});
   c.geom_ready.assign(n_groups, false);
   c.spread_ready.assign(n_groups, false);
 
@@ -264,10 +270,12 @@ int tmbir_set_geometry(tmbir_ctx* ctx, int n_groups, const tmbir_group* groups) 
   c.off_ang.resize(n_groups);
   c.off_K.resize(n_groups);
   c.off_psiK.resize(n_groups);
-  c.off_psiA.resize(n_groups);
-  c.off_csr_ptr.resize(n_groups);
-  c.off_csr_idx.resize(n_groups);
-  c.off_csr_w.resize(n_groups);
+  for (int k = 0; k < 2; ++k) {
+    c.off_sp_psi[k].resize(n_groups);
+    c.off_sp_ptr[k].resize(n_groups);
+    c.off_sp_idx[k].resize(n_groups);
+    c.off_sp_wt[k].resize(n_groups);
+  }
   c.off_lam.resize(n_groups);
   c.off_gtg.resize(n_groups);
   for (int i = 0; i < n_groups; ++i) {
@@ -280,14 +288,18 @@ int tmbir_set_geometry(tmbir_ctx* ctx, int n_groups, const tmbir_group* groups) 
     c.off_ang[i] = take(gs[i].n_angles * sizeof(double));
     c.off_K[i] = take((2 * N - 1) * (2 * N - 1) * sizeof(double));
     c.off_psiK[i] = take((2 * N - 1) * sizeof(double));
-    c.off_psiA[i] = take(N * sizeof(double));
-    c.off_csr_ptr[i] = take(((size_t)spread_grid((int)N) * spread_grid((int)N) + 1) * sizeof(int));
-    c.off_csr_idx[i] = take(spread_nnz(gs[i]) * sizeof(int));
-    c.off_csr_w[i] = take(spread_nnz(gs[i]) * sizeof(double));
+    for (int k = 0; k < 2; ++k) {
+      const size_t nf = spread_grid(k, (int)N);
+      c.off_sp_psi[k][i] = take(N * sizeof(double));
+      c.off_sp_ptr[k][i] = take((nf * nf + 1) * sizeof(int));
+      c.off_sp_idx[k][i] = take(spread_nnz(gs[i], k) * sizeof(int));
+      c.off_sp_wt[k][i] = take(spread_nnz(gs[i], k) * sizeof(double));
+    }
     c.off_lam[i] = take(sizeof(double));
     c.off_gtg[i] = take(sizeof(double));
     nufft_psi_table(2 * N - 1, 4 * N, 12, c.nufft_beta64, c.psiK_h[i]);
-    nufft_psi_table(N, spread_grid((int)N), kSpreadW, c.spread_beta, c.psiA_h[i]);
+    for (int k = 0; k < 2; ++k)
+      nufft_psi_table(N, spread_grid(k, (int)N), kSpreadWidth[k], spread_beta(k), c.psiS_h[k][i]);
   }
   c.off_xbuf0 = take(voxels * sizeof(float));
   c.off_xbuf1 = take(voxels * sizeof(float));
@@ -359,6 +371,8 @@ int tmbir_set_workspace(tmbir_ctx* ctx, void* d_ws, size_t bytes) {
     d.span = (float)g.span;
     d.zc = tuned_zc(d.N, d.S);
     d.sc = tuned_sc(d.N, d.S);
+    d.rb1 = tuned_rb(d.N, d.S).first;
+    d.rb3 = tuned_rb(d.N, d.S).second;
     d.chat = reinterpret_cast<float*>(ws + c.off_chat[i]);
     d.twN = reinterpret_cast<float2*>(ws + c.off_twN[i]);
     d.twM = reinterpret_cast<float2*>(ws + c.off_twM[i]);
@@ -367,10 +381,13 @@ int tmbir_set_workspace(tmbir_ctx* ctx, void* d_ws, size_t bytes) {
     d.angles = reinterpret_cast<double*>(ws + c.off_ang[i]);
     d.K = reinterpret_cast<double*>(ws + c.off_K[i]);
     d.psiK = reinterpret_cast<double*>(ws + c.off_psiK[i]);
-    d.psiA = reinterpret_cast<double*>(ws + c.off_psiA[i]);
-    d.csr_ptr = reinterpret_cast<int*>(ws + c.off_csr_ptr[i]);
-    d.csr_idx = reinterpret_cast<int*>(ws + c.off_csr_idx[i]);
-    d.csr_w = reinterpret_cast<double*>(ws + c.off_csr_w[i]);
+    for (int k = 0; k < 2; ++k) {
+      d.sp[k].nf = spread_grid(k, g.N);
+      d.sp[k].psi = reinterpret_cast<double*>(ws + c.off_sp_psi[k][i]);
+      d.sp[k].ptr = reinterpret_cast<int*>(ws + c.off_sp_ptr[k][i]);
+      d.sp[k].idx = reinterpret_cast<int*>(ws + c.off_sp_idx[k][i]);
+      d.sp[k].wt = reinterpret_cast<double*>(ws + c.off_sp_wt[k][i]);
+    }
     d.lam_max = reinterpret_cast<double*>(ws + c.off_lam[i]);
     d.gtg = reinterpret_cast<double*>(ws + c.off_gtg[i]);
     // twiddle tables: twN[k][t] = exp(-2 pi i t k / N) in the group-FFT layout (the plain
@@ -394,8 +411,9 @@ int tmbir_set_workspace(tmbir_ctx* ctx, void* d_ws, size_t bytes) {
                                c.stream));
     TMBIR_CUDA(cudaMemcpyAsync(d.psiK, c.psiK_h[i].data(), c.psiK_h[i].size() * sizeof(double), cudaMemcpyHostToDevice,
                                c.stream));
-    TMBIR_CUDA(cudaMemcpyAsync(d.psiA, c.psiA_h[i].data(), c.psiA_h[i].size() * sizeof(double), cudaMemcpyHostToDevice,
-                               c.stream));
+    for (int k = 0; k < 2; ++k)
+      TMBIR_CUDA(cudaMemcpyAsync(d.sp[k].psi, c.psiS_h[k][i].data(), c.psiS_h[k][i].size() * sizeof(double),
+                                 cudaMemcpyHostToDevice, c.stream));
 
   }
   // pageable host sources: make sure the copies have consumed them before the vectors go away
@@ -1078,6 +1096,35 @@ int tmbir_autotune(tmbir_ctx* ctx, const float* d_x, const float* d_atg, const t
       if (h_sc) h_sc[i] = best_sc;
       std::lock_guard<std::mutex> lk(g_tune_mu);
       g_tuned_sc[{g.N, g.S}] = best_sc;
+    }
+    // rows per block of passes 1 and 3a, where the side has variants (4 or 8 rows)
+    if (g.N == 2048) {
+      auto time_ms = [&](auto&& launch, float* out) {
+        for (int rep = 0; rep < 3 && rc == TMBIR_OK; ++rep) {
+          if (rep == 1) cudaEventRecord(e0, s);
+          rc = launch();
+        }
+        if (rc) return;
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(out, e0, e1) != cudaSuccess)
+          rc = set_error(TMBIR_ERR_CUDA, "autotune: event timing failed");
+      };
+      float best1 = 1e30f, best3 = 1e30f;
+      int rb1 = 4, rb3 = 8;
+      for (int rb : {4, 8}) {
+        float t1 = 0.f, t3 = 0.f;
+        g.rb1 = g.rb3 = rb;
+        time_ms([&] { return launch_pass1(g, a, s, false); }, &t1);
+        time_ms([&] { return launch_pass3(g, a, Pass3Mode::Iterate, pc, nullptr, 0, s, false, 1); }, &t3);
+        if (rc) break;
+        if (t1 < best1) best1 = t1, rb1 = rb;
+        if (t3 < best3) best3 = t3, rb3 = rb;
+      }
+      if (rc) break;
+      g.rb1 = rb1;
+      g.rb3 = rb3;
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      g_tuned_rb[{g.N, g.S}] = {rb1, rb3};
     }
     if ((rc = launch_convolution(g, a, Pass3Mode::Iterate, pc, s))) break;
     std::vector<int> cands;

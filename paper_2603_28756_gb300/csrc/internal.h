@@ -97,16 +97,21 @@ struct GroupDev {
   double* angles;      // [na]
   double* K;           // [(2N-1)^2] point-spread kernel
   double* psiK;        // [2N-1] deconvolution factors for K (fine grid 4N)
-  double* psiA;        // [N] deconvolution factors of the back-projection spreading (grid spread_grid(N))
+
   double* lam_max;     // device scalar
   double* gtg;         // device scalar (1/2 g.g of the group)
-  // sparse spreading onto the spread_grid(N)^2 grid (geometry only)
-  int* csr_ptr;        // [spread_grid(N)^2 + 1]
-  int* csr_idx;        // [nnz] strength index a * n_det + (k mod n_det)
-  double* csr_w;       // [nnz] kernel weight
+  // sparse spreading operators (geometry only): sp[0] for the FP32 paths, sp[1] for R*g in FP64
+  struct Spread {
+    int nf;            // periodic grid side
+    double* psi;       // [N] deconvolution factors (the kernel's Fourier transform at the image modes)
+    int* ptr;          // [nf^2 + 1] rows of grid cells
+    int* idx;          // [nnz] strength index a * n_det + (k mod n_det)
+    double* wt;        // [nnz] kernel weight
+  } sp[2];
   float* kz;           // [S][N][N] K (*) y between passes 3a and 3b
   int zc;              // slices each pass-3 block marches through (0: the default rule)
   int sc;              // slices per spectrum chunk of passes 1, 2, 3a (0: the default rule)
+  int rb1, rb3;        // rows per block of passes 1 and 3a where a side has variants (0: default)
 };
 
 // Passes 1, 2 and 3a may run in chunks of slices (a chunk's half spectra can then stay in L2
@@ -115,14 +120,18 @@ struct GroupDev {
 // saves), so that is the default; tmbir_autotune tries chunks of 4, 8 and 16 slices too.
 inline int spec_chunk(const GroupDev& g) { return g.sc > 0 && g.sc < g.S ? g.sc : g.S; }
 
-// Spreading of R*g, the FBP start and the forward projection: a 5N/4 x 5N/4 periodic grid
-// (oversampling 1.25; 2^a 3^b 5^c for every supported side) and an exponential-of-semicircle
-// kernel of width 14 with beta = 0.97 pi (1 - 1/(2 * 1.25)) * 14, relative error about 1e-8
-// (R*g is stored in FP32).  The smaller grid than the usual factor 2 cuts the FP64 grid FFTs,
-// which dominate the setup, to 0.37x for 1.96x the (cheaper) sparse gather.
-constexpr int kSpreadW = 14;
-inline int spread_grid(int N) { return N * 5 / 4; }
-constexpr double kSpreadBetaPerWidth = 0.97 * 3.14159265358979323846 * (1.0 - 1.0 / 2.5);
+// The two spreading configurations of the back-projection (exponential-of-semicircle kernel,
+// relative error of R* about 1e-9 / 1e-8):
+//   0, the FP32 paths (FBP start, forward and adjoint projections): a 2N x 2N grid, width 10,
+//      beta 2.30 per unit width;
+//   1, R*g in FP64: a 5N/4 x 5N/4 grid (2^a 3^b 5^c for every supported side), width 14,
+//      beta = 0.97 pi (1 - 1/(2 * 1.25)) per unit width.  The smaller grid cuts the FP64 grid
+//      FFTs, which dominate the setup, to 0.37x for 1.96x the sparse gather; dividing by the
+//      kernel's Fourier transform amplifies rounding towards the image corners (up to ~5e5 at
+//      1.25, 13 at 2), harmless in FP64 but not in FP32, hence two configurations.
+constexpr int kSpreadWidth[2] = {10, 14};
+inline int spread_grid(int k, int N) { return k ? N * 5 / 4 : 2 * N; }
+inline double spread_beta(int k) { return k ? 0.97 * 3.14159265358979323846 * (1.0 - 1.0 / 2.5) * 14 : 2.30 * 10; }
 constexpr int kBackprojBatch = 8;  // slices per back-projection batch
 
 struct Ctx {
@@ -131,8 +140,8 @@ struct Ctx {
   std::vector<std::vector<double>> angles;
   std::vector<GroupDev> gdev;
   // host copies of the NUFFT deconvolution tables (uploaded at set_workspace)
-  std::vector<std::vector<double>> psiK_h, psiA_h;
-  double nufft_beta64 = 0, spread_beta = 0;
+  std::vector<std::vector<double>> psiK_h, psiS_h[2];
+  double nufft_beta64 = 0;
   std::vector<bool> geom_ready;    // K, its spectrum and lambda_max built
   std::vector<bool> spread_ready;  // sparse spreading matrix built
   size_t total_voxels = 0, total_sino = 0;
@@ -152,8 +161,8 @@ struct Ctx {
   bool operator_built = false;
   int last_iters = 0;
   // layout offsets computed at set_geometry
-  std::vector<size_t> off_chat, off_twN, off_twM, off_spec, off_kz, off_ang, off_K, off_psiK, off_psiA, off_lam, off_gtg,
-      off_csr_ptr, off_csr_idx, off_csr_w;
+  std::vector<size_t> off_chat, off_twN, off_twM, off_spec, off_kz, off_ang, off_K, off_psiK, off_lam, off_gtg;
+  std::vector<size_t> off_sp_psi[2], off_sp_ptr[2], off_sp_idx[2], off_sp_wt[2];
   size_t off_state = 0, off_gmom = 0, off_partials = 0, off_log = 0, off_xbuf0 = 0, off_xbuf1 = 0, off_scratch = 0, off_dscal = 0;
   size_t off_fbp_scratch = 0;
   char* fbp_scratch = nullptr;  // FP32 back-projection scratch, separate so FBP can overlap R*g
@@ -273,7 +282,7 @@ int forward_project(Ctx& c, int gi, const float* d_x, float* d_sino, cudaStream_
 size_t forward_scratch_bytes(const tmbir_group& g);
 // d_rx -= d_g over one group's sinogram rows
 int residual(Ctx& c, int gi, float* d_rx, const float* d_g, cudaStream_t s = nullptr);
-size_t spread_nnz(const tmbir_group& g);
+size_t spread_nnz(const tmbir_group& g, int k);
 int power_iteration(Ctx& c, int gi, int steps);
 int group_gtg(Ctx& c, int gi, const float* d_sino);
 void nufft_psi_table(int nmodes, int nfine, int w, double beta, std::vector<double>& out);

@@ -8,7 +8,7 @@
 // "exponential of semicircle" kernel psi(u) = exp(beta (sqrt(1 - (2u/w)^2) - 1)) (Barnett,
 // Magland & af Klinteberg 2019), takes a 2D FFT and divides each output mode by the
 // kernel's Fourier transform.  K (4N grid, width 12) and R*g (5N/4 grid, width 14) run in
-// FP64, the FBP start (same grid as R*g) in FP32.  K is spread with fixed-point integer atomics and R*g / FBP through a sorted sparse
+// FP64, the FBP start (2N grid, width 10) in FP32.  K is spread with fixed-point integer atomics and R*g / FBP through a sorted sparse
 // matrix, so every result is bit-reproducible.
 #include <algorithm>
 #include <cmath>
@@ -587,24 +587,26 @@ static bool kernel_direct(int N) {
   return 2 * nf * sizeof(double2) > 200 * 1024 && (nf & (nf - 1)) != 0;
 }
 
+// complex elements of one back-projection batch on the grid of spreading configuration k:
+// twiddles, strengths, grids, pruned transposes, sample-major strengths (kBackprojBatch wide)
+static size_t backproject_elems(const tmbir_group& g, int k) {
+  const size_t N = g.N, nf = spread_grid(k, g.N);
+  const size_t rows = (size_t)g.n_angles * g.n_det;
+  const size_t B = std::min(g.n_slices, kBackprojBatch);
+  return nf + B * rows + B * nf * nf + B * N * nf + (size_t)kBackprojBatch * rows;
+}
 size_t setup_scratch_bytes(const tmbir_group& g) {
-  const size_t N = g.N, nf_k = 4 * N, nf_a = spread_grid(g.N), M = 2 * N;
+  const size_t N = g.N, nf_k = 4 * N, M = 2 * N, nf0 = spread_grid(0, g.N);
   const size_t k_elems = kernel_direct(g.N) ? nf_k + 2 * M * M + (size_t)g.n_angles : nf_k + 2 * nf_k * nf_k;
-  const size_t rows = (size_t)g.n_angles * g.n_det;
-  const size_t B = std::min(g.n_slices, kBackprojBatch);
-  // twiddles, strengths, grids, pruned transposes, sample-major strengths (always kBackprojBatch wide)
-  const size_t a_elems = nf_a + B * rows + B * nf_a * nf_a + B * N * nf_a + (size_t)kBackprojBatch * rows;
-  const size_t csr_build = (nf_a * nf_a + 2 * ((nf_a * nf_a + 2048) / 2048 + 1)) * sizeof(int);
-  return std::max(std::max(std::max(k_elems, a_elems) * sizeof(double2), csr_build) + 256, forward_scratch_bytes(g));
+  // R*g in FP64 on grid 1; the FP32 back-projection of the direct operators on grid 0
+  const size_t a_bytes = std::max(backproject_elems(g, 1) * sizeof(double2), backproject_elems(g, 0) * sizeof(float2));
+  const size_t csr_build = (nf0 * nf0 + 2 * ((nf0 * nf0 + 2048) / 2048 + 1)) * sizeof(int);
+  return std::max(std::max(std::max(k_elems * sizeof(double2), a_bytes), csr_build) + 256, forward_scratch_bytes(g));
 }
-size_t fbp_scratch_bytes(const tmbir_group& g) {
-  const size_t N = g.N, nf_a = spread_grid(g.N);
-  const size_t rows = (size_t)g.n_angles * g.n_det;
-  const size_t B = std::min(g.n_slices, kBackprojBatch);
-  const size_t a_elems = nf_a + B * rows + B * nf_a * nf_a + B * N * nf_a + (size_t)kBackprojBatch * rows;
-  return a_elems * sizeof(float2) + 256;
+size_t fbp_scratch_bytes(const tmbir_group& g) { return backproject_elems(g, 0) * sizeof(float2) + 256; }
+size_t spread_nnz(const tmbir_group& g, int k) {
+  return (size_t)g.n_angles * (g.n_det - 1) * kSpreadWidth[k] * kSpreadWidth[k];
 }
-size_t spread_nnz(const tmbir_group& g) { return (size_t)g.n_angles * (g.n_det - 1) * kSpreadW * kSpreadW; }
 
 // device twiddle tables for the setup FFTs (n up to 4N), carved from the front of the scratch
 template <class C>
@@ -700,26 +702,29 @@ static int circulant_spectrum(Ctx& c, int gi) {
 int build_spread_matrix(Ctx& c, int gi) {
   GroupDev& g = c.gdev[gi];
   cudaStream_t s = c.stream;
-  const int nf = spread_grid(g.N), ncells = nf * nf;
   const size_t total = (size_t)g.na * (g.nd - 1);
   const int blocks = (int)std::min<size_t>((total + 255) / 256, 152 * 16);
-  int* cursor = reinterpret_cast<int*>(c.scratch);
-  int* sums = cursor + ncells;
-  TMBIR_CUDA(cudaMemsetAsync(g.csr_ptr, 0, sizeof(int) * (ncells + 1), s));
-  k_csr_count<<<blocks, 256, 0, s>>>(g.angles, g.na, g.nd, nf, kSpreadW, g.csr_ptr);
-  TMBIR_CHECK_LAUNCH();
-  const int ntiles = (ncells + 1 + 2047) / 2048;
-  k_scan_tiles<<<ntiles, 256, 0, s>>>(g.csr_ptr, ncells + 1, sums);
-  TMBIR_CHECK_LAUNCH();
-  k_scan_sums<<<1, 32, 0, s>>>(sums, ntiles);
-  TMBIR_CHECK_LAUNCH();
-  k_scan_add<<<1024, 256, 0, s>>>(g.csr_ptr, ncells + 1, sums);
-  TMBIR_CHECK_LAUNCH();
-  TMBIR_CUDA(cudaMemcpyAsync(cursor, g.csr_ptr, sizeof(int) * ncells, cudaMemcpyDeviceToDevice, s));
-  k_csr_fill<<<blocks, 256, 0, s>>>(g.angles, g.na, g.nd, nf, kSpreadW, c.spread_beta, cursor, g.csr_idx, g.csr_w);
-  TMBIR_CHECK_LAUNCH();
-  k_csr_sort<<<(ncells + 255) / 256, 256, 0, s>>>(g.csr_ptr, ncells, g.csr_idx, g.csr_w);
-  TMBIR_CHECK_LAUNCH();
+  for (int k = 0; k < 2; ++k) {
+    GroupDev::Spread& sp = g.sp[k];
+    const int nf = sp.nf, ncells = nf * nf, W = kSpreadWidth[k];
+    int* cursor = reinterpret_cast<int*>(c.scratch);
+    int* sums = cursor + ncells;
+    TMBIR_CUDA(cudaMemsetAsync(sp.ptr, 0, sizeof(int) * (ncells + 1), s));
+    k_csr_count<<<blocks, 256, 0, s>>>(g.angles, g.na, g.nd, nf, W, sp.ptr);
+    TMBIR_CHECK_LAUNCH();
+    const int ntiles = (ncells + 1 + 2047) / 2048;
+    k_scan_tiles<<<ntiles, 256, 0, s>>>(sp.ptr, ncells + 1, sums);
+    TMBIR_CHECK_LAUNCH();
+    k_scan_sums<<<1, 32, 0, s>>>(sums, ntiles);
+    TMBIR_CHECK_LAUNCH();
+    k_scan_add<<<1024, 256, 0, s>>>(sp.ptr, ncells + 1, sums);
+    TMBIR_CHECK_LAUNCH();
+    TMBIR_CUDA(cudaMemcpyAsync(cursor, sp.ptr, sizeof(int) * ncells, cudaMemcpyDeviceToDevice, s));
+    k_csr_fill<<<blocks, 256, 0, s>>>(g.angles, g.na, g.nd, nf, W, spread_beta(k), cursor, sp.idx, sp.wt);
+    TMBIR_CHECK_LAUNCH();
+    k_csr_sort<<<(ncells + 255) / 256, 256, 0, s>>>(sp.ptr, ncells, sp.idx, sp.wt);
+    TMBIR_CHECK_LAUNCH();
+  }
   return TMBIR_OK;
 }
 
@@ -727,7 +732,9 @@ template <class C>
 static int backproject_t(Ctx& c, int gi, const float* d_sino, float* d_out, bool ramp, float scale, char* scratch,
                          cudaStream_t s, bool local_out) {
   GroupDev& g = c.gdev[gi];
-  const int N = g.N, nf = spread_grid(N), nd = g.nd, na = g.na, ncells = nf * nf;
+  // R*g in FP64 on the 5N/4 grid, the FP32 back-projections on the 2N grid
+  const GroupDev::Spread& sp = g.sp[sizeof(real_t<C>) == 8 ? 1 : 0];
+  const int N = g.N, nf = sp.nf, nd = g.nd, na = g.na, ncells = nf * nf;
   const size_t rows = (size_t)na * nd;
   const int B = std::min(g.S, kBackprojBatch);
   C* tw = reinterpret_cast<C*>(scratch);
@@ -749,7 +756,7 @@ static int backproject_t(Ctx& c, int gi, const float* d_sino, float* d_out, bool
     const int np = (nb + 1) / 2;
     k_strength_pack<PB, C><<<1024, 256, 0, s>>>(strengths, nd, rows, nb, strengths_t);
     TMBIR_CHECK_LAUNCH();
-    k_csr_gather<PB, C><<<(ncells + 255) / 256, 256, 0, s>>>(g.csr_ptr, g.csr_idx, g.csr_w, ncells, strengths_t,
+    k_csr_gather<PB, C><<<(ncells + 255) / 256, 256, 0, s>>>(sp.ptr, sp.idx, sp.wt, ncells, strengths_t,
                                                               grid, np);
     TMBIR_CHECK_LAUNCH();
     k_twiddle<C><<<(nf + 255) / 256, 256, 0, s>>>(tw, nf);
@@ -762,7 +769,7 @@ static int backproject_t(Ctx& c, int gi, const float* d_sino, float* d_out, bool
       TMBIR_CHECK_LAUNCH();
     }
     if (int e = fft_rows(tmp, nf, np * N, -1, tw, s)) return e;
-    k_deconv_pruned<C><<<1024, 256, 0, s>>>(tmp, nf, N, nb, g.psiA, scale,
+    k_deconv_pruned<C><<<1024, 256, 0, s>>>(tmp, nf, N, nb, sp.psi, scale,
                                             d_out + (local_out ? 0 : g.img_off) + (size_t)b0 * N * N);
     TMBIR_CHECK_LAUNCH();
   }
@@ -886,14 +893,15 @@ __global__ void k_unpack_pairs(const float2* __restrict__ rows, size_t per_pair,
 }
 
 size_t forward_scratch_bytes(const tmbir_group& g) {
-  const size_t nf = spread_grid(g.N), np = (std::min(g.n_slices, kBackprojBatch) + 1) / 2;
+  const size_t nf = spread_grid(0, g.N), np = (std::min(g.n_slices, kBackprojBatch) + 1) / 2;
   return (nf + g.n_det + 2 * np * nf * nf + np * (size_t)g.n_angles * g.n_det) * sizeof(float2) + 256;
 }
 
 int forward_project(Ctx& c, int gi, const float* d_x, float* d_sino, cudaStream_t s) {
   GroupDev& g = c.gdev[gi];
   if (!s) s = c.stream;
-  const int N = g.N, nf = spread_grid(N), nd = g.nd, na = g.na;
+  const GroupDev::Spread& sp = g.sp[0];  // FP32: the 2N grid
+  const int N = g.N, nf = sp.nf, nd = g.nd, na = g.na;
   const size_t cells = (size_t)nf * nf, rows = (size_t)na * nd;
   const int B = std::min(g.S, kBackprojBatch);
   constexpr int PB = kBackprojBatch / 2;
@@ -910,11 +918,11 @@ int forward_project(Ctx& c, int gi, const float* d_x, float* d_sino, cudaStream_
   TMBIR_CHECK_LAUNCH();
   for (int b0 = 0; b0 < g.S; b0 += B) {
     const int nb = std::min(B, g.S - b0), np = (nb + 1) / 2;
-    k_pad_deconv_pairs<<<1024, 256, 0, s>>>(d_x + g.img_off + (size_t)b0 * N * N, N, nf, nb, g.psiA, grid);
+    k_pad_deconv_pairs<<<1024, 256, 0, s>>>(d_x + g.img_off + (size_t)b0 * N * N, N, nf, nb, sp.psi, grid);
     TMBIR_CHECK_LAUNCH();
     if (int e = fft2_transposed(grid, tmp, nf, np, +1, tw_f, s)) return e;
-    k_interp_pairs<kSpreadW, PB><<<(int)std::min<size_t>((rows + 255) / 256, 152 * 16), 256, 0, s>>>(
-        tmp, g.angles, na, nd, nf, (float)c.spread_beta, np, prow);
+    k_interp_pairs<kSpreadWidth[0], PB><<<(int)std::min<size_t>((rows + 255) / 256, 152 * 16), 256, 0, s>>>(
+        tmp, g.angles, na, nd, nf, (float)spread_beta(0), np, prow);
     TMBIR_CHECK_LAUNCH();
     if (int e = fft_rows(prow, nd, np * na, -1, tw_d, s)) return e;
     k_unpack_pairs<<<1024, 256, 0, s>>>(prow, rows, nb, d_sino + g.sino_off + (size_t)b0 * rows);

@@ -564,8 +564,12 @@ struct Q2048 {
   static constexpr int N = 2048, H = 1024;
   using F = GroupFFT<32, 32>;
   static constexpr int LDZ = N + 4;  // row stride (complex) of staged rows
-  static constexpr int RB1 = 4;      // rows per block of pass 1 (eight warps)
-  static constexpr int RB3 = 8;      // rows per block of pass 3a (sixteen warps: 64-byte gathers)
+  // rows per block of passes 1 and 3a (two warps per row): 4 or 8, chosen per group by the
+  // autotuner (GroupDev::rb1, rb3); eight rows write and gather 64-byte segments of the
+  // column-major spectrum but hold one 135 KB block per SM, four rows 32-byte segments with two
+  // or three blocks per SM whose phases overlap
+  static constexpr int RB1 = 4;      // default of pass 1
+  static constexpr int RB3 = 8;      // default of pass 3a
   template <int RB>
   static constexpr size_t sm_rows() {  // staged rows and the warps' exchange buffers, aliased
     return (size_t)(RB * LDZ > 2 * RB * F::SMEM ? RB * LDZ : 2 * RB * F::SMEM) * sizeof(float2);
@@ -579,10 +583,10 @@ __device__ __forceinline__ float2 tw4096(const float2* __restrict__ twM, int n) 
   return n < 2048 ? w : make_float2(-w.x, -w.y);
 }
 
-template <bool BF>
-__global__ void __launch_bounds__(32 * 2 * Q2048::RB1) k_pass1_q(GroupDev g, StepArgs a) {
+template <bool BF, int RB>
+__global__ void __launch_bounds__(64 * RB) k_pass1_q(GroupDev g, StepArgs a) {
   using Q = Q2048;
-  constexpr int N = Q::N, T = 32, P = 32, RB = Q::RB1, LDZ = Q::LDZ, THREADS = 64 * RB, NB = N / RB;
+  constexpr int N = Q::N, T = 32, P = 32, LDZ = Q::LDZ, THREADS = 64 * RB, NB = N / RB;
   extern __shared__ float2 sm[];
   const float *x, *xp;
   float beta;
@@ -731,10 +735,10 @@ __global__ void __launch_bounds__(128, 3) k_pass2_q(GroupDev g, const IterState*
   }
 }
 
-template <bool BF>
-__global__ void __launch_bounds__(64 * Q2048::RB3, 1) k_pass3a_q(GroupDev g, const IterState* st, float* kz) {
+template <bool BF, int RB>
+__global__ void __launch_bounds__(64 * RB, 8 / RB) k_pass3a_q(GroupDev g, const IterState* st, float* kz) {
   using Q = Q2048;
-  constexpr int N = Q::N, T = 32, P = 32, RB = Q::RB3, LDZ = Q::LDZ, THREADS = 64 * RB, NB = N / RB;
+  constexpr int N = Q::N, T = 32, P = 32, LDZ = Q::LDZ, THREADS = 64 * RB, NB = N / RB;
   extern __shared__ float2 sm[];
   if (st && skip_iter<BF>(st)) return;
   const int s = blockIdx.x / NB, rb = blockIdx.x % NB;
@@ -1329,13 +1333,17 @@ static int set_smem_limits() {
   if (done) return TMBIR_OK;
   if constexpr (N == 2048) {
     using Q = Q2048;
-    const int s1 = (int)Q::sm_rows<Q::RB1>(), s3 = (int)Q::sm_rows<Q::RB3>();
-    TMBIR_CUDA(cudaFuncSetAttribute(k_pass1_q<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, s1));
-    TMBIR_CUDA(cudaFuncSetAttribute(k_pass1_q<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, s1));
+    const int s4 = (int)Q::sm_rows<4>(), s8 = (int)Q::sm_rows<8>();
+    TMBIR_CUDA(cudaFuncSetAttribute(k_pass1_q<false, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, s4));
+    TMBIR_CUDA(cudaFuncSetAttribute(k_pass1_q<true, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, s4));
+    TMBIR_CUDA(cudaFuncSetAttribute(k_pass1_q<false, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, s8));
+    TMBIR_CUDA(cudaFuncSetAttribute(k_pass1_q<true, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, s8));
     TMBIR_CUDA(cudaFuncSetAttribute(k_pass2_q<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Q::SM2));
     TMBIR_CUDA(cudaFuncSetAttribute(k_pass2_q<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Q::SM2));
-    TMBIR_CUDA(cudaFuncSetAttribute(k_pass3a_q<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, s3));
-    TMBIR_CUDA(cudaFuncSetAttribute(k_pass3a_q<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, s3));
+    TMBIR_CUDA(cudaFuncSetAttribute(k_pass3a_q<false, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, s4));
+    TMBIR_CUDA(cudaFuncSetAttribute(k_pass3a_q<true, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, s4));
+    TMBIR_CUDA(cudaFuncSetAttribute(k_pass3a_q<false, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, s8));
+    TMBIR_CUDA(cudaFuncSetAttribute(k_pass3a_q<true, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, s8));
   } else if constexpr (is_block_fft_size<N>()) {
     using BG = BGeo<N>;
     TMBIR_CUDA(cudaFuncSetAttribute(k_pass1_b<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BG::SM_ROWS));
@@ -1368,11 +1376,17 @@ static int pass1_n(const GroupDev& g, const StepArgs& a, bool bf16, cudaStream_t
   if (int e = set_smem_limits<N>()) return e;
   if constexpr (N == 2048) {
     using Q = Q2048;
-    const int blocks = g.S * (N / Q::RB1);
-    if (bf16)
-      k_pass1_q<true><<<blocks, 64 * Q::RB1, Q::sm_rows<Q::RB1>(), s>>>(g, a);
-    else
-      k_pass1_q<false><<<blocks, 64 * Q::RB1, Q::sm_rows<Q::RB1>(), s>>>(g, a);
+    if ((g.rb1 ? g.rb1 : Q::RB1) == 8) {
+      if (bf16)
+        k_pass1_q<true, 8><<<g.S * (N / 8), 512, Q::sm_rows<8>(), s>>>(g, a);
+      else
+        k_pass1_q<false, 8><<<g.S * (N / 8), 512, Q::sm_rows<8>(), s>>>(g, a);
+    } else {
+      if (bf16)
+        k_pass1_q<true, 4><<<g.S * (N / 4), 256, Q::sm_rows<4>(), s>>>(g, a);
+      else
+        k_pass1_q<false, 4><<<g.S * (N / 4), 256, Q::sm_rows<4>(), s>>>(g, a);
+    }
   } else if constexpr (is_block_fft_size<N>()) {
     using BG = BGeo<N>;
     if (bf16)
@@ -1442,11 +1456,17 @@ static int pass3_n(const GroupDev& g, const StepArgs& a, Pass3Mode m, const Prio
   if (part & 1) {
     if constexpr (N == 2048) {
       using Q = Q2048;
-      const int blocks = g.S * (N / Q::RB3);
-      if (bf16)
-        k_pass3a_q<true><<<blocks, 64 * Q::RB3, Q::sm_rows<Q::RB3>(), s>>>(g, st, kz);
-      else
-        k_pass3a_q<false><<<blocks, 64 * Q::RB3, Q::sm_rows<Q::RB3>(), s>>>(g, st, kz);
+      if ((g.rb3 ? g.rb3 : Q::RB3) == 8) {
+        if (bf16)
+          k_pass3a_q<true, 8><<<g.S * (N / 8), 512, Q::sm_rows<8>(), s>>>(g, st, kz);
+        else
+          k_pass3a_q<false, 8><<<g.S * (N / 8), 512, Q::sm_rows<8>(), s>>>(g, st, kz);
+      } else {
+        if (bf16)
+          k_pass3a_q<true, 4><<<g.S * (N / 4), 256, Q::sm_rows<4>(), s>>>(g, st, kz);
+        else
+          k_pass3a_q<false, 4><<<g.S * (N / 4), 256, Q::sm_rows<4>(), s>>>(g, st, kz);
+      }
     } else if constexpr (is_block_fft_size<N>()) {
       using BG = BGeo<N>;
       if (bf16)
