@@ -353,7 +353,28 @@ __global__ void k_csr_gather(const int* __restrict__ ptr, const int* __restrict_
 #pragma unroll
     for (int b = 0; b < B; ++b) acc[b] = mkc((S)0, (S)0);
     const int e = ptr[cell + 1];
-    for (int j = ptr[cell]; j < e; ++j) {
+    int j = ptr[cell];
+    // two entries per step with all their loads issued first (the index load and the dependent
+    // strength loads are a latency chain); the accumulation order is that of one at a time
+    for (; j + 1 < e; j += 2) {
+      const C* sv0 = strengths + (size_t)idx[j] * B;
+      const C* sv1 = strengths + (size_t)idx[j + 1] * B;
+      const S w0 = (S)wt[j], w1 = (S)wt[j + 1];
+      C v0[B], v1[B];
+#pragma unroll
+      for (int b = 0; b < B; ++b) {
+        v0[b] = sv0[b];
+        v1[b] = sv1[b];
+      }
+#pragma unroll
+      for (int b = 0; b < B; ++b) {
+        acc[b].x = fmar(w0, v0[b].x, acc[b].x);
+        acc[b].y = fmar(w0, v0[b].y, acc[b].y);
+        acc[b].x = fmar(w1, v1[b].x, acc[b].x);
+        acc[b].y = fmar(w1, v1[b].y, acc[b].y);
+      }
+    }
+    if (j < e) {
       const C* sv = strengths + (size_t)idx[j] * B;
       const S w = (S)wt[j];
 #pragma unroll
@@ -385,15 +406,28 @@ __global__ void k_transpose_prune(const C* __restrict__ in, C* __restrict__ out,
   }
 }
 // out[b][r][c] = scale * Re tmp[b][c][(r - N/2) mod nf] / (psi[c] psi[r])
-// slice 2p from the real part, slice 2p + 1 (when there is one) from the imaginary part of pair p
+// slice 2p from the real part, slice 2p + 1 (when there is one) from the imaginary part of pair p.
+// tmp is column-major ([c][r']) and out row-major, so 32 x 32 tiles pass through shared memory
+// and both sides are read and written along their contiguous index.  Grid: (N/32, N/32, pairs).
 template <class C>
-__global__ void k_deconv_pruned(const C* __restrict__ B, int nf, int N, int nb, const double* __restrict__ psi,
-                                float scale, float* __restrict__ out) {
-  const size_t total = (size_t)nb * N * N;
-  for (size_t id = blockIdx.x * (size_t)blockDim.x + threadIdx.x; id < total; id += (size_t)gridDim.x * blockDim.x) {
-    const int c = (int)(id % N), r = (int)((id / N) % N), b = (int)(id / ((size_t)N * N));
-    const C v = B[(size_t)(b / 2) * N * nf + (size_t)c * nf + (r - N / 2 + nf) % nf];
-    out[id] = (float)(scale * ((double)((b & 1) ? v.y : v.x) / (psi[c] * psi[r])));
+__global__ void __launch_bounds__(256) k_deconv_pruned(const C* __restrict__ B, int nf, int N, int nb,
+                                                       const double* __restrict__ psi, float scale,
+                                                       float* __restrict__ out) {
+  __shared__ C tile[32][33];
+  const int p = blockIdx.z, c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  const C* Bp = B + (size_t)p * N * nf;
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {  // column c0 + i, rows r0 .. r0 + 31
+    const int c = c0 + i, r = r0 + threadIdx.x;
+    if (c < N && r < N) tile[i][threadIdx.x] = Bp[(size_t)c * nf + (r - N / 2 + nf) % nf];
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {  // row r0 + i, columns c0 .. c0 + 31
+    const int r = r0 + i, c = c0 + threadIdx.x;
+    if (c >= N || r >= N) continue;
+    const C v = tile[threadIdx.x][i];
+    const double d = psi[c] * psi[r];
+    out[((size_t)(2 * p) * N + r) * N + c] = (float)(scale * ((double)v.x / d));
+    if (2 * p + 1 < nb) out[((size_t)(2 * p + 1) * N + r) * N + c] = (float)(scale * ((double)v.y / d));
   }
 }
 
@@ -769,8 +803,11 @@ static int backproject_t(Ctx& c, int gi, const float* d_sino, float* d_out, bool
       TMBIR_CHECK_LAUNCH();
     }
     if (int e = fft_rows(tmp, nf, np * N, -1, tw, s)) return e;
-    k_deconv_pruned<C><<<1024, 256, 0, s>>>(tmp, nf, N, nb, sp.psi, scale,
-                                            d_out + (local_out ? 0 : g.img_off) + (size_t)b0 * N * N);
+    {
+      dim3 gr((N + 31) / 32, (N + 31) / 32, np), bl(32, 8);
+      k_deconv_pruned<C><<<gr, bl, 0, s>>>(tmp, nf, N, nb, sp.psi, scale,
+                                           d_out + (local_out ? 0 : g.img_off) + (size_t)b0 * N * N);
+    }
     TMBIR_CHECK_LAUNCH();
   }
   return TMBIR_OK;
