@@ -97,14 +97,6 @@ template <class C> __device__ __forceinline__ C cmul(C a, C b) {
 template <class C> __device__ __forceinline__ C cmulc(C a, C b) {
   return mkc(fmar(a.x, b.x, a.y * b.y), fmar(a.y, b.x, -a.x * b.y));
 }
-// FP32: two packed instructions each, rounded exactly like the scalar forms (the same products
-// rounded, the same fused additions)
-template <> __device__ __forceinline__ float2 cmul<float2>(float2 a, float2 b) {
-  return __ffma2_rn(make_float2(a.x, a.x), b, __fmul2_rn(make_float2(a.y, a.y), make_float2(-b.y, b.x)));
-}
-template <> __device__ __forceinline__ float2 cmulc<float2>(float2 a, float2 b) {
-  return __ffma2_rn(make_float2(a.x, a.y), make_float2(b.x, b.x), __fmul2_rn(make_float2(a.y, a.x), make_float2(b.y, -b.y)));
-}
 template <class C> __device__ __forceinline__ C cconj(C a) { return mkc(a.x, -a.y); }
 template <class C> __device__ __forceinline__ C cscale(C a, real_t<C> s) { return mkc(a.x * s, a.y * s); }
 // a * (DIR * i)
@@ -135,10 +127,7 @@ __device__ __forceinline__ C twmul(C a) {
   } else {
     constexpr S c = (S)ct_trig2pi(k, N, 0);
     constexpr S s = (S)(DIR * ct_trig2pi(k, N, 1));
-    if constexpr (std::is_same<C, float2>::value)
-      return __ffma2_rn(make_float2(a.x, a.x), make_float2(c, s), __fmul2_rn(make_float2(a.y, a.y), make_float2(-s, c)));
-    else
-      return mkc(fmar(a.x, c, -a.y * s), fmar(a.x, s, a.y * c));
+    return mkc(fmar(a.x, c, -a.y * s), fmar(a.x, s, a.y * c));
   }
 }
 

@@ -87,6 +87,22 @@ def test_gradient(prob, orc):
     assert rel(G, ref) < 1e-5
 
 
+def test_general_q_gradient_and_iterations_follow_oracle(prob, orc):
+    # the stencil's general-exponent variant (q != 2: |d/sigma|^(q-2) by a fourth special-function
+    # operation per pair), at an exponent pair the oracle's potential is pinned at
+    prm = dict(PRIOR, p=1.1, q=1.8)
+    pr = orc.Prior(**prm)
+    L = 4.0 * orc.power_lambda_max(prob.K, prob.N)  # rho'' is unbounded at 0 for q < 2: a given L
+    G = host(prob.ctx.gradient(dev(prob.x), prob.d_atg, tm.Params(**prm, L=L)), prob.x.shape)
+    assert rel(G, orc.gradient(prob.x, prob.atg, prob.K, pr)) < 1e-5
+    iters = 10
+    x = dev(prob.x)
+    prob.ctx.reconstruct(x, prob.d_atg, tm.Params(**prm, L=L, max_iter=iters))
+    ref = orc.nesterov(prob.x.astype(np.float32).astype(np.float64), prob.atg, float(np.sum(prob.g ** 2)), prob.K,
+                       pr, L, iters)
+    assert rel(host(x, prob.x.shape), ref) < 1e-4
+
+
 def test_fused_step_and_partials(prob, orc):
     pr = orc.Prior(**PRIOR)
     beta, L = 0.37, 55.0
