@@ -46,6 +46,12 @@ WORKLOADS = {
     # learned warm start: trained on (FBP, converged) pairs at 1024^2 with 90..180 angles, evaluated
     # on 128 slices of 2560^2 with 150 angles (the CNN start against the FBP start, to the 1e-3 gap)
     "learned-128x2560sq-150ang": dict(S=128, N=2560, na=150, span=math.pi, ne=20, kind="learned"),
+    # a host-resident volume streamed through the GPU in slabs (Sec. 2.4), the paper's nano-CT
+    # shape (212 angles over [0, pi), 2448-bin detector rows on the 2560 grid) with 256 of its
+    # 2048 slices: setup + `iters` FP32 iterations from and to host memory, against the same
+    # iterations on the resident volume
+    "streamed-256x2560sq-212ang": dict(S=256, N=2560, na=212, span=math.pi, ne=20, kind="streamed", iters=10,
+                                       slab=16),
     # profiling cases: the image sides and angles of the workloads, a few GB on the device
     "profile-16x1024sq-256ang-20it": dict(S=16, N=1024, na=256, span=math.pi, ne=20, kind="fixed", iters=20),
     "profile-8x2048sq-128ang-limited-20it": dict(S=8, N=2048, na=128, span=2 * math.pi / 3, ne=20, kind="fixed",
@@ -509,6 +515,8 @@ def config_of(name):
     elif w["kind"] == "learned":
         c.update(gap=GAP, train={"N": LEARN_TRAIN_N, "pairs": LEARN_TRAIN_VOLUMES * LEARN_TRAIN_SLICES,
                                  "angles": [90, 180]})
+    elif w["kind"] == "streamed":
+        c.update(iterations=w["iters"], slab=w["slab"])
     else:
         c.update(iterations=w["iters"])
     return c
@@ -611,6 +619,8 @@ def main():
             run_uneven(args, tm, prob, stream, rank, world, local, barrier, {"input_generation_s": t_gen})
         elif w["kind"] == "learned":
             run_learned(args, tm, w, prob, stream, rank, world, local, barrier, {"input_generation_s": t_gen})
+        elif w["kind"] == "streamed":
+            run_streamed(args, tm, w, prob, stream, rank, world, local, barrier, {"input_generation_s": t_gen})
         else:
             run_ours(args, tm, w, prob, stream, rank, world, local, barrier, {"input_generation_s": t_gen})
     if world > 1:
@@ -1073,6 +1083,82 @@ def run_learned(args, tm, w, prob, stream, rank, world, local, barrier, extra):
                 "iterations_saved": state["st_fbp"].iterations - state["st"].iterations}},
             "clocks": clk,
             "e2e": None,
+        }
+        line.update(extra)
+        print(json.dumps(line), flush=True)
+
+
+def run_streamed(args, tm, w, prob, stream, rank, world, local, barrier, extra):
+    """A volume in host memory streamed through the GPU slab by slab: one step is the streamed
+    setup (R*g, 1/2 g.g and the FBP start) and `iters` streamed FP32 iterations, every input read
+    from and every output written to page-locked host memory.  The same iterations on the
+    resident volume give the streaming overhead, and their final iterates are compared."""
+    import torch
+
+    S, N, na, span, slab, iters = w["S"], w["N"], w["na"], w["span"], w["slab"], w["iters"]
+    ctx = tm.Context([tm.Group(N=N, angles=list(prob.theta), n_slices=slab, span=span)], stream=stream)
+    h_sino = torch.from_numpy(prob.sino.ravel()).pin_memory()
+    h_x = torch.empty(S * N * N, dtype=torch.float32, pin_memory=True)
+    prm = tm_params(max_iter=iters)
+    state = {}
+
+    def step():
+        h_atg, gtg, h_x0 = ctx.stream_build_operator(h_sino, S, fbp=True)
+        h_x.copy_(h_x0)
+        state["st"] = ctx.stream_reconstruct(h_x, h_atg, gtg, prm)
+        state["atg"], state["gtg"], state["x0"] = h_atg, gtg, h_x0
+        return S * N * N * state["st"].iterations
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    clocks = Clocks(local)
+    units = []
+    n0 = ctx.launch_count()
+    ms, _ = timed(stream, barrier, world, lambda: [units.append(step()) for _ in range(args.steps)])
+    launches = ctx.launch_count() - n0
+    clk = clocks.stop()
+    # the iteration phase alone, streamed and resident
+    h_x.copy_(state["x0"])
+    ms_it, _ = timed(stream, barrier, world, lambda: ctx.stream_reconstruct(h_x, state["atg"], state["gtg"], prm))
+    x_streamed = h_x.clone()
+    res = tm.Context([tm.Group(N=N, angles=list(prob.theta), n_slices=S, span=span)], stream=stream)
+    atg = state["atg"].cuda()
+    x = state["x0"].cuda()
+    res.reconstruct(x.clone(), atg, prm)
+    ms_res, _ = timed(stream, barrier, world, lambda: res.reconstruct(x, atg, prm))
+    diff = float((x.cpu() - x_streamed).abs().max()) / max(float(x_streamed.abs().max()), 1e-30)
+    nslab = (S + slab - 1) // slab
+    plane = N * N * 4
+    h2d_it = (2 * (S + 2 * (nslab - 1)) + S) * plane  # x_k and x_{k-1} with the halo slices, R*g
+    d2h_it = S * plane
+    progress(f"streamed step {ms / args.steps:.1f} ms; iterations streamed {ms_it / iters:.1f} ms, resident "
+             f"{ms_res / iters:.1f} ms per iteration; max |difference| / max |x| = {diff:.2e}")
+    if rank == 0:
+        cfg = config_of(args.workload)
+        cfg.update({"parallelism": f"replicas{world}", "l2": "working set > L2 (no explicit flush)",
+                    "step": "stream_build_operator (R*g, FBP) + stream_reconstruct, host volume in slabs of "
+                            f"{slab} slices", "stand_in_for": "2048 x 2448^2 nano-CT volume, 212 angles"})
+        vox = sum(units) / len(units)
+        val = job_rate(vox, args.steps, world, ms)
+        sino_b = S * na * N * 4
+        line = {
+            "metric": METRIC, "value": val, "unit": "voxel-updates/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg, "voxel_updates_per_step": vox,
+            "streaming": {
+                "slab": slab, "slabs": nslab,
+                "streamed_ms_per_iteration": ms_it / iters, "resident_ms_per_iteration": ms_res / iters,
+                "overhead": ms_it / ms_res,
+                "host_copies_per_iteration_bytes": {"h2d": h2d_it, "d2h": d2h_it},
+                "copy_GBps_per_iteration": (h2d_it + d2h_it) / (ms_it / iters) / 1e6,
+                "max_abs_difference_vs_resident_over_max_abs_x": diff,
+                "host_bytes_for_the_2048_slice_volume": 5 * 2048 * plane,
+            },
+            "clocks": clk,
+            "e2e": {"value": val, "unit": "voxel-updates/s", "h2d_bytes_per_step": sino_b + iters * h2d_it,
+                    "d2h_bytes_per_step": 2 * S * plane + iters * d2h_it},
+            "gpu_launches": launches,
         }
         line.update(extra)
         print(json.dumps(line), flush=True)

@@ -395,6 +395,58 @@ int tmbir_wait_check(tmbir_ctx* ctx, unsigned polls, int arrive);
  */
 int tmbir_sfu_rate(tmbir_ctx* ctx, int iters, double* h_ops_per_s);
 
+/*
+ * Volumes larger than the device's memory (Sec. 2.4: the volume is partitioned along the
+ * rotation axis, each partition keeps a halo of boundary slices for the 26-neighbour prior, and
+ * a node scheduler overlaps host-device copies with the kernels).  The volume, its sinogram, R*g
+ * and the iterates stay in host memory; the context's one geometry group is the slab, its
+ * n_slices the slices the GPU holds at a time.  Slabs pass through the GPU in order in three
+ * overlapping stages on three streams (copies in, kernels on the context stream, copies out)
+ * with two device buffer sets.  Host buffers should be page-locked (cudaHostAlloc or
+ * cudaHostRegister); pageable ones work but their copies do not overlap the kernels.  Both calls
+ * return after their host outputs are written (they synchronise the three streams).  The context
+ * stream must not be the legacy stream.
+ *
+ * tmbir_stream_workspace_size: bytes of the caller's device buffer d_swork (256-byte aligned)
+ *   for a volume of n_slices slices with this context's slab: two buffer sets (x_k, x_{k-1},
+ *   R*g and x_{k+1} of a slab with one halo slice each way, and a slab's sinogram), K (*) y of a
+ *   slab, and the partial sums of the whole volume's pass-3b blocks (any slices-per-block choice).
+ */
+int tmbir_stream_workspace_size(const tmbir_ctx* ctx, int n_slices, size_t* bytes);
+
+/*
+ * R*g (Eq. 11) and 1/2 g.g of a host volume, and optionally the FBP start (Eq. 12), one slab
+ * at a time through tmbir_build_operator (or tmbir_build_operator_fbp).
+ *   h_sino  [n_slices][n_angles][n_det] FP32, host.
+ *   h_atg   [n_slices][N][N] FP32, host (out).
+ *   h_x0    [n_slices][N][N] FP32, host (out), or NULL for no FBP start.
+ *   h_gtg   host double (out): 1/2 g.g of the volume, the slabs' sums added in slab order.
+ * The setup transforms pair slices 2p and 2p + 1 of each slab, so with an even slab R*g is bit
+ * for bit that of the resident volume.
+ */
+int tmbir_stream_build_operator(tmbir_ctx* ctx, int n_slices, const float* h_sino, float* h_atg, float* h_x0,
+                                void* d_swork, size_t swork_bytes, double* h_gtg);
+
+/*
+ * tmbir_reconstruct on a host volume: prm->max_iter iterations (fewer when the gap rule stops
+ * the run), the step constant from this geometry's lambda_max unless prm->L is given.
+ *   h_x       [n_slices][N][N] FP32, host: x_0 in, the final iterate out.
+ *   h_atg     R*g of the volume (tmbir_stream_build_operator); gtg_half its 1/2 g.g.
+ *   h_work    2 n_slices N^2 floats of host scratch: with h_x, the three slots x_{k-1}, x_k and
+ *             x_{k+1} rotate through.
+ * Per iteration each slab copies in x_k and x_{k-1} (with one halo slice on each side) and its
+ * R*g, runs passes 1-3b on its own slices, and copies out x_{k+1}; the finalize kernel then
+ * reduces the partial sums of all slabs in the order of the resident volume's pass-3b blocks, and
+ * the host reads the stop flag.  The slices per pass-3b block are the slab's (tuned or default)
+ * value lowered to a divisor of the slab; when the resident volume uses the same value, every
+ * iterate equals tmbir_reconstruct's bit for bit.  Options as in tmbir_reconstruct, except that
+ * use_graph is ignored and resume is refused (TMBIR_ERR_ARG); the iteration log (tmbir_get_log)
+ * is kept; the state cannot be exported afterwards.
+ */
+int tmbir_stream_reconstruct(tmbir_ctx* ctx, int n_slices, float* h_x, const float* h_atg, double gtg_half,
+                             float* h_work, void* d_swork, size_t swork_bytes, const tmbir_params* prm,
+                             tmbir_stats* h_stats);
+
 /* Wait for the context stream; reports a pending CUDA error. */
 int tmbir_sync(tmbir_ctx* ctx);
 

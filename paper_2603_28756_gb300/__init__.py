@@ -86,6 +86,7 @@ SYMBOLS = [
     "tmbir_cnn_train_step", "tmbir_cnn_net_forward", "tmbir_cnn_net_backward", "tmbir_warm_start",
     "tmbir_state_size", "tmbir_state_export", "tmbir_state_import", "tmbir_autotune", "tmbir_build_operator_fbp",
     "tmbir_wait_check", "tmbir_forward", "tmbir_adjoint", "tmbir_gradient_direct", "tmbir_sfu_rate",
+    "tmbir_stream_workspace_size", "tmbir_stream_build_operator", "tmbir_stream_reconstruct",
 ]
 
 _lib = None
@@ -146,6 +147,9 @@ def load(path: str | None = None):
         "tmbir_adjoint": [vp, vp, vp],
         "tmbir_gradient_direct": [vp, vp, vp, ctypes.POINTER(_Params), vp, dp],
         "tmbir_sfu_rate": [vp, i, dp],
+        "tmbir_stream_workspace_size": [vp, i, ctypes.POINTER(sz)],
+        "tmbir_stream_build_operator": [vp, i, vp, vp, vp, vp, sz, dp],
+        "tmbir_stream_reconstruct": [vp, i, vp, vp, d, vp, vp, sz, ctypes.POINTER(_Params), ctypes.POINTER(_Stats)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -322,6 +326,66 @@ class Context:
         self._post(x, atg)
         if not want_stats:
             return None
+        return Stats(st.iterations, st.restarts, st.status, st.objective, st.gap, st.L, st.grad_norm)
+
+    # host volumes (tmbir_stream_*): the context's one group is the slab ---------------------
+    def _stream_work(self, n_slices: int):
+        import torch
+
+        nbytes = ctypes.c_size_t()
+        _check(_lib.tmbir_stream_workspace_size(self._h, int(n_slices), ctypes.byref(nbytes)))
+        if getattr(self, "_swork_key", None) != (n_slices, nbytes.value):
+            with torch.cuda.stream(self.stream):
+                self._swork = torch.empty(nbytes.value + 256, dtype=torch.uint8, device=self.device)
+            self._swork_key = (n_slices, nbytes.value)
+        base = self._swork.data_ptr()
+        return (base + 255) // 256 * 256, nbytes.value
+
+    def stream_build_operator(self, h_sino, n_slices: int, fbp: bool = False):
+        """R*g (and the FBP start) of a host volume of n_slices slices, slab by slab.
+        h_sino: a contiguous float32 CPU tensor (page-locked for overlapped copies).
+        Returns (h_atg, gtg_half, h_x0 or None) as page-locked CPU tensors."""
+        import torch
+
+        g = self.groups[0]
+        if h_sino.is_cuda or not h_sino.is_contiguous() or h_sino.dtype != torch.float32:
+            raise TypeError("expected a contiguous float32 CPU tensor")
+        if h_sino.numel() != n_slices * len(g.angles) * (g.n_det or g.N):
+            raise ValueError("sinogram size does not match n_slices")
+        nimg = n_slices * g.N * g.N
+        h_atg = torch.empty(nimg, dtype=torch.float32, pin_memory=True)
+        h_x0 = torch.empty(nimg, dtype=torch.float32, pin_memory=True) if fbp else None
+        ws, nb = self._stream_work(n_slices)
+        gtg = ctypes.c_double()
+        self._pre()
+        _check(_lib.tmbir_stream_build_operator(self._h, int(n_slices), ctypes.c_void_p(h_sino.data_ptr()),
+                                                ctypes.c_void_p(h_atg.data_ptr()),
+                                                ctypes.c_void_p(h_x0.data_ptr() if fbp else None),
+                                                ctypes.c_void_p(ws), nb, ctypes.byref(gtg)))
+        return h_atg, gtg.value, h_x0
+
+    def stream_reconstruct(self, h_x, h_atg, gtg_half: float, params: Params):
+        """tmbir_reconstruct on a host volume: h_x (x_0 in, the final iterate out) and h_atg are
+        contiguous float32 CPU tensors of n_slices N^2 values."""
+        import torch
+
+        g = self.groups[0]
+        for t in (h_x, h_atg):
+            if t.is_cuda or not t.is_contiguous() or t.dtype != torch.float32:
+                raise TypeError("expected contiguous float32 CPU tensors")
+        if h_x.numel() != h_atg.numel() or h_x.numel() % (g.N * g.N):
+            raise ValueError("image sizes do not match")
+        n_slices = h_x.numel() // (g.N * g.N)
+        if getattr(self, "_hwork", None) is None or self._hwork.numel() != 2 * h_x.numel():
+            self._hwork = torch.empty(2 * h_x.numel(), dtype=torch.float32, pin_memory=True)
+        ws, nb = self._stream_work(n_slices)
+        st = _Stats()
+        pr = params.c_struct()
+        self._pre()
+        _check(_lib.tmbir_stream_reconstruct(self._h, int(n_slices), ctypes.c_void_p(h_x.data_ptr()),
+                                             ctypes.c_void_p(h_atg.data_ptr()), float(gtg_half),
+                                             ctypes.c_void_p(self._hwork.data_ptr()), ctypes.c_void_p(ws), nb,
+                                             ctypes.byref(pr), ctypes.byref(st)))
         return Stats(st.iterations, st.restarts, st.status, st.objective, st.gap, st.L, st.grad_norm)
 
     def get_log(self, max_entries: int = 1 << 16):

@@ -14,7 +14,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libtmbir.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-SOURCES = ["api.cu", "toeplitz.cu", "setup.cu", "levels.cu", "static_scratch.cu", "cnn.cu", "wait_check.cu", "rates.cu"]
+SOURCES = ["api.cu", "toeplitz.cu", "setup.cu", "levels.cu", "static_scratch.cu", "cnn.cu", "wait_check.cu", "rates.cu", "stream.cu"]
 # the Toeplitz passes are instantiated once per supported image side, in parallel
 SIZES = [64, 128, 256, 512, 1024, 2048, 1536, 2560]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

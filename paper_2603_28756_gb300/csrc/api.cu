@@ -135,6 +135,15 @@ __global__ void k_gather_final(const IterState* st, float* x0, float* x1, float*
 }
 __global__ void k_rotation_reset(IterState* st) { st->cur = 0; }
 
+int launch_init_state(Ctx& c, const tmbir_params& p, const double* lam_max, const double* gtg, int n_groups,
+                      cudaStream_t s) {
+  const bool bf16 = p.spectra == TMBIR_SPECTRA_BF16;
+  k_init_state<<<1, 1, 0, s>>>(c.state, c.gmom, lam_max, gtg, n_groups, p.L, p.lambda, p.sigma, p.F_ref, p.gap_tol,
+                               p.max_iter, p.restart, bf16 ? 1 : 0, p.refine_gap);
+  TMBIR_CHECK_LAUNCH();
+  return TMBIR_OK;
+}
+
 // continue a run from the current state: max_iter more iterations with new stop settings
 __global__ void k_resume_state(IterState* st, double Fref, double gap_tol, int max_iter, int restart_mode, int bf16,
                                double refine_gap) {
@@ -171,6 +180,18 @@ int tmbir::require_ready(const tmbir_ctx* ctx, bool need_operator) {
   return TMBIR_OK;
 }
 
+int tmbir::check_params(const tmbir_params* p) {
+  if (!p) return set_error(TMBIR_ERR_ARG, "params is NULL");
+  if (!(p->p >= 1.0 && p->q >= p->p && p->q <= 4.0)) return set_error(TMBIR_ERR_ARG, "need 1 <= p <= q <= 4");
+  if (!(p->c > 0.0 && p->sigma > 0.0 && p->lambda >= 0.0)) return set_error(TMBIR_ERR_ARG, "need c > 0, sigma > 0, lambda >= 0");
+  if (p->L <= 0.0 && p->q != 2.0) return set_error(TMBIR_ERR_ARG, "automatic L needs q = 2; pass L > 0");
+  if (p->restart != TMBIR_RESTART_GRADIENT && p->restart != TMBIR_RESTART_NONE && p->restart != TMBIR_RESTART_FUNCTION)
+    return set_error(TMBIR_ERR_ARG, "unknown restart mode");
+  if ((p->spectra != TMBIR_SPECTRA_FP32 && p->spectra != TMBIR_SPECTRA_BF16) || !(p->refine_gap >= 0.0))
+    return set_error(TMBIR_ERR_ARG, "spectra must be FP32 or BF16 and refine_gap >= 0");
+  return TMBIR_OK;
+}
+
 extern "C" {
 
 const char* tmbir_last_error(void) { return g_last_error.c_str(); }
@@ -196,6 +217,14 @@ int tmbir_destroy(tmbir_ctx* ctx) {
   if (ctx->c.ev_fork) cudaEventDestroy(ctx->c.ev_fork);
   if (ctx->c.ev_join) cudaEventDestroy(ctx->c.ev_join);
   if (ctx->c.aux) cudaStreamDestroy(ctx->c.aux);
+  for (int s = 0; s < 2; ++s) {
+    if (ctx->c.ev_in[s]) cudaEventDestroy(ctx->c.ev_in[s]);
+    if (ctx->c.ev_comp[s]) cudaEventDestroy(ctx->c.ev_comp[s]);
+    if (ctx->c.ev_out[s]) cudaEventDestroy(ctx->c.ev_out[s]);
+  }
+  if (ctx->c.ev_start) cudaEventDestroy(ctx->c.ev_start);
+  if (ctx->c.s_in) cudaStreamDestroy(ctx->c.s_in);
+  if (ctx->c.s_out) cudaStreamDestroy(ctx->c.s_out);
   delete ctx;
   return TMBIR_OK;
 }
@@ -424,17 +453,6 @@ int tmbir_set_workspace(tmbir_ctx* ctx, void* d_ws, size_t bytes) {
   return TMBIR_OK;
 }
 
-static int check_params(const tmbir_params* p) {
-  if (!p) return set_error(TMBIR_ERR_ARG, "params is NULL");
-  if (!(p->p >= 1.0 && p->q >= p->p && p->q <= 4.0)) return set_error(TMBIR_ERR_ARG, "need 1 <= p <= q <= 4");
-  if (!(p->c > 0.0 && p->sigma > 0.0 && p->lambda >= 0.0)) return set_error(TMBIR_ERR_ARG, "need c > 0, sigma > 0, lambda >= 0");
-  if (p->L <= 0.0 && p->q != 2.0) return set_error(TMBIR_ERR_ARG, "automatic L needs q = 2; pass L > 0");
-  if (p->restart != TMBIR_RESTART_GRADIENT && p->restart != TMBIR_RESTART_NONE && p->restart != TMBIR_RESTART_FUNCTION)
-    return set_error(TMBIR_ERR_ARG, "unknown restart mode");
-  if ((p->spectra != TMBIR_SPECTRA_FP32 && p->spectra != TMBIR_SPECTRA_BF16) || !(p->refine_gap >= 0.0))
-    return set_error(TMBIR_ERR_ARG, "spectra must be FP32 or BF16 and refine_gap >= 0");
-  return TMBIR_OK;
-}
 
 int tmbir_build_operator(tmbir_ctx* ctx, const float* d_sino, float* d_atg) {
   TMBIR_TRACE("tmbir_build_operator");

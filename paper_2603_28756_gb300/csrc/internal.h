@@ -110,6 +110,9 @@ struct GroupDev {
   } sp[2];
   float* kz;           // [S][N][N] K (*) y between passes 3a and 3b
   int zc;              // slices each pass-3 block marches through (0: the default rule)
+  // pass 3b's slice range [zlo, zlo + zn) (zn = 0: all S slices); the slices outside it are
+  // neighbours only (the halo of a slab of a larger volume)
+  int zlo, zn;
   int sc;              // slices per spectrum chunk of passes 1, 2, 3a (0: the default rule)
   int rb1, rb3;        // rows per block of passes 1 and 3a where a side has variants (0: default)
 };
@@ -170,6 +173,10 @@ struct Ctx {
   size_t off_sino_tmp = 0;
   cudaStream_t aux = nullptr;   // second stream for the overlapped FBP (created on first use)
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // host volumes: copy-in and copy-out streams beside the context stream, events per buffer set
+  cudaStream_t s_in = nullptr, s_out = nullptr;
+  cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_comp[2] = {nullptr, nullptr}, ev_out[2] = {nullptr, nullptr};
+  cudaEvent_t ev_start = nullptr;
   // CUDA graph cache for reconstruct
   cudaGraphExec_t graph_exec = nullptr;
   const float* graph_atg = nullptr;
@@ -249,9 +256,12 @@ inline int pass3_slices_per_block(int S, int row_blocks) {
   if (chunks > S) chunks = S;
   return (S + chunks - 1) / chunks;
 }
+// slices whose gradient pass 3b computes
+inline int pass3_slices(const GroupDev& g) { return g.zn > 0 ? g.zn : g.S; }
 // the group's tuned value (tmbir_autotune) or the default rule
 inline int pass3_zc(const GroupDev& g, int row_blocks) {
-  return g.zc > 0 ? (g.zc < g.S ? g.zc : g.S) : pass3_slices_per_block(g.S, row_blocks);
+  const int n = pass3_slices(g);
+  return g.zc > 0 ? (g.zc < n ? g.zc : n) : pass3_slices_per_block(n, row_blocks);
 }
 // partial-sum rows pass 3 can write for a group at most (one slice per block)
 int max_blocks_pass3(const GroupDev& g);
@@ -293,6 +303,12 @@ int launch_upsample_lanczos3(const float* in, int S, int Nc, float* out, cudaStr
 int launch_downsample_sino(const float* in, int S, int na, int nd, int f, float* out, cudaStream_t s);
 
 PriorC make_prior(const tmbir_params& p);
+// checks of the prior and optimiser settings shared by the entry points (sets the message)
+int check_params(const tmbir_params* p);
+// the iteration state of a new run: per group its step constant (from lam_max[i] unless p.L is
+// given) and momentum start, 1/2 g.g from gtg[i]; both arrays on the device
+int launch_init_state(Ctx& c, const tmbir_params& p, const double* lam_max, const double* gtg, int n_groups,
+                      cudaStream_t s);
 
 // argument checks shared by the entry points: a context with a geometry and a bound
 // workspace (and, with need_operator, a built operator); sets the error message otherwise

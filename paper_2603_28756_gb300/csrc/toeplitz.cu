@@ -182,7 +182,7 @@ int conv_launches(const GroupDev& g) {
 int blocks_pass3(const GroupDev& g) {
   const int nb = pass3_row_blocks(g.N);
   const int zc = pass3_zc(g, nb);
-  return nb * ((g.S + zc - 1) / zc);
+  return nb * ((pass3_slices(g) + zc - 1) / zc);
 }
 int max_blocks_pass3(const GroupDev& g) { return pass3_row_blocks(g.N) * g.S; }
 

@@ -1188,7 +1188,7 @@ __global__ void __launch_bounds__(GeoP<N>::THREADS, 2)
   const int band = blockIdx.x % GP::NB;
   const int cb = (blockIdx.x / GP::NB) % GP::CB;
   const int chunk = blockIdx.x / (GP::NB * GP::CB);
-  const int z0 = chunk * zc, z1 = min(g.S, z0 + zc);
+  const int z0 = g.zlo + chunk * zc, z1 = min(g.zlo + (g.zn > 0 ? g.zn : g.S), z0 + zc);
   const int r0 = band * R, c0 = cb * GP::BC;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int c0w = c0 + 64 * warp;
@@ -1435,7 +1435,7 @@ static int pass3_nm(const GroupDev& g, const StepArgs& a, const PriorC& pc, cons
   using GP = GeoP<N>;
   static_assert(GP::NB * GP::CB == pass3_row_blocks(N), "pass-3b block count");
   const int zc = pass3_zc(g, GP::NB * GP::CB);
-  const int blocks = GP::NB * GP::CB * ((g.S + zc - 1) / zc);
+  const int blocks = GP::NB * GP::CB * ((pass3_slices(g) + zc - 1) / zc);
   if (pc.q_is_2 || MODE == 0)
     k_pass3<N, MODE, true><<<blocks, GP::THREADS, GP::SM, s>>>(g, a, pc, kz, phase, partials, off, zc);
   else
