@@ -1123,7 +1123,8 @@ def run_streamed(args, tm, w, prob, stream, rank, world, local, barrier, extra):
     ms_it, _ = timed(stream, barrier, world, lambda: ctx.stream_reconstruct(h_x, state["atg"], state["gtg"], prm))
     x_streamed = h_x.clone()
     res = tm.Context([tm.Group(N=N, angles=list(prob.theta), n_slices=S, span=span)], stream=stream)
-    atg = state["atg"].cuda()
+    atg = res.build_operator(h_sino.cuda())
+    atg_same = bool(torch.equal(atg.cpu(), state["atg"]))
     x = state["x0"].cuda()
     res.reconstruct(x.clone(), atg, prm)
     ms_res, _ = timed(stream, barrier, world, lambda: res.reconstruct(x, atg, prm))
@@ -1153,6 +1154,7 @@ def run_streamed(args, tm, w, prob, stream, rank, world, local, barrier, extra):
                 "host_copies_per_iteration_bytes": {"h2d": h2d_it, "d2h": d2h_it},
                 "copy_GBps_per_iteration": (h2d_it + d2h_it) / (ms_it / iters) / 1e6,
                 "max_abs_difference_vs_resident_over_max_abs_x": diff,
+                "atg_bitwise_equal_to_resident": atg_same,
                 "host_bytes_for_the_2048_slice_volume": 5 * 2048 * plane,
             },
             "clocks": clk,
