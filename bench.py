@@ -1088,6 +1088,47 @@ def run_learned(args, tm, w, prob, stream, rank, world, local, barrier, extra):
         print(json.dumps(line), flush=True)
 
 
+def host_link(stream, nbytes=1 << 30, reps=3):
+    """Page-locked host <-> device copy rates (GB/s, best of reps, CUDA events): one direction at a
+    time on one stream, host-to-device on two streams at once, and both directions at once."""
+    import torch
+
+    h = [torch.empty(nbytes, dtype=torch.uint8, pin_memory=True) for _ in range(2)]
+    d = [torch.empty(nbytes, dtype=torch.uint8, device="cuda") for _ in range(2)]
+    s2 = torch.cuda.Stream()
+
+    def rate(fn, moved):
+        best = 0.0
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            s2.wait_stream(stream)
+            stream.wait_stream(s2)
+            e1.record(stream)
+            e1.synchronize()
+            best = max(best, moved / (e0.elapsed_time(e1) * 1e-3) / 1e9)
+        return best
+
+    def two(first, second):
+        def fn():
+            s2.wait_stream(stream)
+            first()
+            with torch.cuda.stream(s2):
+                second()
+        return fn
+
+    return {
+        "h2d": rate(lambda: d[0].copy_(h[0], non_blocking=True), nbytes),
+        "d2h": rate(lambda: h[0].copy_(d[0], non_blocking=True), nbytes),
+        "h2d_two_streams": rate(two(lambda: d[0].copy_(h[0], non_blocking=True),
+                                    lambda: d[1].copy_(h[1], non_blocking=True)), 2 * nbytes),
+        "both_directions": rate(two(lambda: d[0].copy_(h[0], non_blocking=True),
+                                    lambda: h[1].copy_(d[1], non_blocking=True)), 2 * nbytes),
+    }
+
+
 def run_streamed(args, tm, w, prob, stream, rank, world, local, barrier, extra):
     """A volume in host memory streamed through the GPU slab by slab: one step is the streamed
     setup (R*g, 1/2 g.g and the FBP start) and `iters` streamed FP32 iterations, every input read
@@ -1129,6 +1170,9 @@ def run_streamed(args, tm, w, prob, stream, rank, world, local, barrier, extra):
     res.reconstruct(x.clone(), atg, prm)
     ms_res, _ = timed(stream, barrier, world, lambda: res.reconstruct(x, atg, prm))
     diff = float((x.cpu() - x_streamed).abs().max()) / max(float(x_streamed.abs().max()), 1e-30)
+    del res, atg, x
+    link = host_link(stream)
+    progress(f"host link GB/s {link}")
     nslab = (S + slab - 1) // slab
     plane = N * N * 4
     h2d_it = (2 * (S + 2 * (nslab - 1)) + S) * plane  # x_k and x_{k-1} with the halo slices, R*g
@@ -1153,6 +1197,10 @@ def run_streamed(args, tm, w, prob, stream, rank, world, local, barrier, extra):
                 "overhead": ms_it / ms_res,
                 "host_copies_per_iteration_bytes": {"h2d": h2d_it, "d2h": d2h_it},
                 "copy_GBps_per_iteration": (h2d_it + d2h_it) / (ms_it / iters) / 1e6,
+                "host_link_GBps": link,
+                # the copies alone at the measured rates (both directions at once): the streamed
+                # iteration's floor when it is copy-bound
+                "copy_floor_ms_per_iteration": (h2d_it + d2h_it) / (link["both_directions"] * 1e9) * 1e3,
                 "max_abs_difference_vs_resident_over_max_abs_x": diff,
                 "atg_bitwise_equal_to_resident": atg_same,
                 "host_bytes_for_the_2048_slice_volume": 5 * 2048 * plane,

@@ -574,7 +574,7 @@ struct Q2048 {
   static constexpr size_t sm_rows() {  // staged rows and the warps' exchange buffers, aliased
     return (size_t)(RB * LDZ > 2 * RB * F::SMEM ? RB * LDZ : 2 * RB * F::SMEM) * sizeof(float2);
   }
-  static constexpr size_t SM2 = (size_t)(2 * N + 4 * F::SMEM) * sizeof(float2);  // 2 columns + 4 exchange buffers
+  static constexpr size_t SM2 = (size_t)(N + 4 * F::SMEM) * sizeof(float2);  // column + 4 exchange buffers
 };
 
 // W^n = exp(-2 pi i n / 4096) for 0 <= n < 4096 from the table of n < 2048 (W^(n + 2048) = -W^n)
@@ -583,14 +583,6 @@ __device__ __forceinline__ float2 tw4096(const float2* __restrict__ twM, int n) 
   return n < 2048 ? w : make_float2(-w.x, -w.y);
 }
 
-// L2 prefetch of n contiguous bytes (a multiple of 16, 16-byte aligned) by one thread
-__device__ __forceinline__ void prefetch_l2_bulk(const void* p, unsigned n) {
-  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(n) : "memory");
-}
-__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
-
-// Persistent: a block walks the row groups blockIdx.x, blockIdx.x + gridDim.x, ... and asks L2
-// for the next group's rows of x_k and x_{k-1} while it transforms the current ones.
 template <bool BF, int RB>
 __global__ void __launch_bounds__(64 * RB) k_pass1_q(GroupDev g, StepArgs a) {
   using Q = Q2048;
@@ -609,60 +601,46 @@ __global__ void __launch_bounds__(64 * RB) k_pass1_q(GroupDev g, StepArgs a) {
     xp = a.xprev;
     beta = a.beta;
   }
+  const int s = blockIdx.x / NB, rb = blockIdx.x % NB;
   const int warp = threadIdx.x >> 5, t = threadIdx.x & 31, rl = warp >> 1, j = warp & 1;
-  const int groups = g.S * NB;
-  for (int grp = blockIdx.x; grp < groups; grp += gridDim.x) {
-    const int nxt = grp + gridDim.x;
-    if (nxt < groups && threadIdx.x < 2 * RB) {
-      const size_t nb = g.img_off + ((size_t)(nxt / NB) * N + (nxt % NB) * RB + (threadIdx.x >> 1)) * N;
-      prefetch_l2_bulk((threadIdx.x & 1 ? xp : x) + nb, N * sizeof(float));
-    }
-    const int s = grp / NB, rb = grp % NB;
-    const size_t base = g.img_off + ((size_t)s * N + rb * RB + rl) * N;
-    // packed row z[m] = y[2m] + i y[2m+1], m < 1024 (the padding above is zero), times w^(jm)
-    float2 v[P];
-    SFor<0, P>::run([&](auto i_) {
-      constexpr int i = decltype(i_)::value;
-      const int m = t + T * i;
-      const float2 xv = __ldg(reinterpret_cast<const float2*>(x + base) + m);
-      const float2 pv = __ldg(reinterpret_cast<const float2*>(xp + base) + m);
-      float2 z = make_float2(fmaf(beta, xv.x - pv.x, xv.x), fmaf(beta, xv.y - pv.y, xv.y));
-      if (j) z = cmul(z, __ldg(&g.twM[2 * m]));  // w^m = W^(2m)
-      v[i] = z;
-    });
-    Q::F::template run<-1, float2, 2>(v, sm + warp * Q::F::SMEM, g.twN, t);
-    __syncthreads();  // every exchange buffer is free: the staged rows alias them
-    float2* zrow = sm + rl * LDZ;
-    SFor<0, P>::run([&](auto i_) {
-      constexpr int i = decltype(i_)::value;
-      zrow[2 * (t + T * i) + j] = v[i];
-    });
-    __syncthreads();
-    // split Y[v] = E[v] + W^v O[v] from Z[v] and Z[N - v]; Y[N] = Re Z[0] - Im Z[0]; written
-    // column-major (RB-row segments)
-    using IO = SpecIO<BF>;
-    typename IO::T* out = reinterpret_cast<typename IO::T*>(g.spec) + (size_t)s * (N + 1) * N + rb * RB;
-    for (int e = threadIdx.x; e < (N + 1) * RB; e += THREADS) {
-      const int vv = e / RB, rr = e - vv * RB;
-      const float2* zr = sm + rr * LDZ;
-      float2 y;
-      if (vv < N) {
-        const float2 z = zr[vv], zs = zr[(N - vv) & (N - 1)];
-        const float2 ev = make_float2(0.5f * (z.x + zs.x), 0.5f * (z.y - zs.y));
-        const float2 od = make_float2(0.5f * (z.y + zs.y), -0.5f * (z.x - zs.x));
-        y = cadd(ev, cmul(__ldg(&g.twM[vv]), od));
-      } else {
-        y = make_float2(zr[0].x - zr[0].y, 0.f);
-      }
-      IO::st(out, (size_t)vv * N + rr, y);
-    }
-    __syncthreads();  // the staged rows are read: the next group's exchange buffers alias them
+  const size_t base = g.img_off + ((size_t)s * N + rb * RB + rl) * N;
+  // packed row z[m] = y[2m] + i y[2m+1], m < 1024 (the padding above is zero), times w^(jm)
+  float2 v[P];
+  SFor<0, P>::run([&](auto i_) {
+    constexpr int i = decltype(i_)::value;
+    const int m = t + T * i;
+    const float2 xv = __ldg(reinterpret_cast<const float2*>(x + base) + m);
+    const float2 pv = __ldg(reinterpret_cast<const float2*>(xp + base) + m);
+    float2 z = make_float2(fmaf(beta, xv.x - pv.x, xv.x), fmaf(beta, xv.y - pv.y, xv.y));
+    if (j) z = cmul(z, __ldg(&g.twM[2 * m]));  // w^m = W^(2m)
+    v[i] = z;
+  });
+  Q::F::template run<-1, float2, 2>(v, sm + warp * Q::F::SMEM, g.twN, t);
+  __syncthreads();  // every exchange buffer is free: the staged rows alias them
+  float2* zrow = sm + rl * LDZ;
+  SFor<0, P>::run([&](auto i_) {
+    constexpr int i = decltype(i_)::value;
+    zrow[2 * (t + T * i) + j] = v[i];
+  });
+  __syncthreads();
+  // split Y[v] = E[v] + W^v O[v] with E = (Z[v] + conj Z[N - v]) / 2, O = (Z[v] - conj Z[N - v]) / 2i,
+  // two mirrored outputs at a time: E[N - v] = conj E[v], O[N - v] = conj O[v] and
+  // W^(N - v) = -conj W^v give Y[N - v] = conj(E[v] - W^v O[v]) (v = 0: Y[N] = Re Z[0] - Im Z[0]);
+  // written column-major (RB-row segments)
+  using IO = SpecIO<BF>;
+  typename IO::T* out = reinterpret_cast<typename IO::T*>(g.spec) + (size_t)s * (N + 1) * N + rb * RB;
+  for (int e = threadIdx.x; e < (N / 2 + 1) * RB; e += THREADS) {
+    const int vv = e / RB, rr = e - vv * RB;
+    const float2* zr = sm + rr * LDZ;
+    const float2 z = zr[vv], zs = zr[(N - vv) & (N - 1)];
+    const float2 ev = make_float2(0.5f * (z.x + zs.x), 0.5f * (z.y - zs.y));
+    const float2 od = make_float2(0.5f * (z.y + zs.y), -0.5f * (z.x - zs.x));
+    const float2 wo = cmul(__ldg(&g.twM[vv]), od);
+    IO::st(out, (size_t)vv * N + rr, cadd(ev, wo));
+    if (vv != N / 2) IO::st(out, (size_t)(N - vv) * N + rr, make_float2(ev.x - wo.x, wo.y - ev.y));
   }
 }
 
-// Persistent: a block walks the columns blockIdx.x, blockIdx.x + gridDim.x, ... and copies the
-// next column into its second column buffer (cp.async, one commit group per column) while it
-// transforms the current one, so the column loads of a block overlap its transforms.
 template <bool BF>
 __global__ void __launch_bounds__(128, 3) k_pass2_q(GroupDev g, const IterState* st) {
   using Q = Q2048;
@@ -670,180 +648,144 @@ __global__ void __launch_bounds__(128, 3) k_pass2_q(GroupDev g, const IterState*
   extern __shared__ float2 sm[];
   if (st && skip_iter<BF>(st)) return;
   const int j = threadIdx.x >> 5, t = threadIdx.x & 31;
+  int vcol, s;
+  column_of(blockIdx.x, g.S, N + 1, vcol, s);
   using IO = SpecIO<BF>;
-  typename IO::T* spec = reinterpret_cast<typename IO::T*>(g.spec);
-  const int total = g.S * (N + 1);
-  // two column buffers of N complex FP32 values (a BF16 column uses the first half of its buffer)
-  auto colbuf = [&](int k) { return sm + k * N; };
-  auto column = [&](int b) {
-    int vcol, s;
-    column_of(b, g.S, N + 1, vcol, s);
-    return spec + ((size_t)s * (N + 1) + vcol) * N;
-  };
-  auto issue = [&](int b, int k) {
-    const typename IO::T* p = column(b);
-    typename IO::T* dst = reinterpret_cast<typename IO::T*>(colbuf(k));
+  typename IO::T* p = reinterpret_cast<typename IO::T*>(g.spec) + ((size_t)s * (N + 1) + vcol) * N;
+  float2* col = sm;
+  if constexpr (!BF) {
+    // all of the column's copies in flight at once
     SFor<0, N / 128>::run([&](auto i_) {
       constexpr int i = decltype(i_)::value;
-      if constexpr (!BF)
-        tc05::cp_async8(&dst[threadIdx.x + 128 * i], p + threadIdx.x + 128 * i);
-      else
-        tc05::cp_async4(&dst[threadIdx.x + 128 * i], p + threadIdx.x + 128 * i);
+      tc05::cp_async8(&col[threadIdx.x + 128 * i], p + threadIdx.x + 128 * i);
     });
-    tc05::cp_async_commit();
-  };
-  float2* xs = sm + 2 * N + j * Q::F::SMEM;
-  const float* cbase = g.chat + (j & 1) * N + (j >> 1);
-  int b = blockIdx.x;
-  if (b < total) issue(b, 0);
-  for (int it = 0; b < total; ++it, b += gridDim.x) {
-    const int nb = b + gridDim.x;
-    if (nb < total) {
-      issue(nb, (it + 1) & 1);  // the buffer the previous column used, read before the last barrier
-      tc05::cp_async_wait_group<1>();
-    } else {
-      tc05::cp_async_wait_group<0>();
-    }
-    __syncthreads();
-    const typename IO::T* col = reinterpret_cast<const typename IO::T*>(colbuf(it & 1));
-    int vcol, s;
-    column_of(b, g.S, N + 1, vcol, s);
-    float2 v[P];
-    // y_j[m] = W^(jm) (c[m] + (-i)^j c[m + 1024]) with m = t + 32 i; W^(jm) = W^(jt) W^(32 j i), the
-    // first factor one table read per thread, the second a compile-time constant per element
-    auto prologue = [&](auto J_) {
-      constexpr int J = decltype(J_)::value;
-      const float2 base = tw4096(g.twM, J * t);
-      SFor<0, P>::run([&](auto i_) {
-        constexpr int i = decltype(i_)::value;
-        const int m = t + T * i;
-        const float2 a0 = IO::ld(col, m), bb = IO::ld(col, m + H);
-        float2 c;
-        if constexpr (J == 0)
-          c = cadd(a0, bb);
-        else if constexpr (J == 1)
-          c = make_float2(a0.x + bb.y, a0.y - bb.x);  // a + (-i) b
-        else if constexpr (J == 2)
-          c = csub(a0, bb);
-        else
-          c = make_float2(a0.x - bb.y, a0.y + bb.x);  // a + i b
-        if constexpr (J != 0) c = cmul(c, twmul<32 * J * i, 4096, -1>(base));
-        v[i] = c;
-      });
-    };
-    switch (j) {
-      case 0: prologue(std::integral_constant<int, 0>{}); break;
-      case 1: prologue(std::integral_constant<int, 1>{}); break;
-      case 2: prologue(std::integral_constant<int, 2>{}); break;
-      default: prologue(std::integral_constant<int, 3>{}); break;
-    }
-    Q::F::template run<-1, float2, 2>(v, xs, g.twN, t);
-    // v[i] = X[4k + j], k = t + 32 i: row 4k + j of the 2N grid is row 2k + (j >> 1) of the
-    // (j & 1) half of the kernel spectrum
-    const float* cc = cbase + (size_t)vcol * 2 * N;
+    tc05::cp_async_wait_all();
+  } else {
+    batched_copy<128, 16>(N, [&](int r) { return IO::ld(p, r); }, [&](int r, float2 v) { col[r] = v; });
+  }
+  __syncthreads();
+  float2 v[P];
+  // y_j[m] = W^(jm) (c[m] + (-i)^j c[m + 1024]) with m = t + 32 i; W^(jm) = W^(jt) W^(32 j i), the
+  // first factor one table read per thread, the second a compile-time constant per element
+  auto prologue = [&](auto J_) {
+    constexpr int J = decltype(J_)::value;
+    const float2 base = tw4096(g.twM, J * t);
     SFor<0, P>::run([&](auto i_) {
       constexpr int i = decltype(i_)::value;
-      const float c = __ldg(&cc[2 * (t + T * i)]);
-      v[i] = make_float2(v[i].x * c, v[i].y * c);
+      const int m = t + T * i;
+      const float2 a0 = col[m], b = col[m + H];
+      float2 c;
+      if constexpr (J == 0)
+        c = cadd(a0, b);
+      else if constexpr (J == 1)
+        c = make_float2(a0.x + b.y, a0.y - b.x);  // a + (-i) b
+      else if constexpr (J == 2)
+        c = csub(a0, b);
+      else
+        c = make_float2(a0.x - b.y, a0.y + b.x);  // a + i b
+      if constexpr (J != 0) c = cmul(c, twmul<32 * J * i, 4096, -1>(base));
+      v[i] = c;
     });
-    Q::F::template run<1, float2, 2>(v, xs, g.twN, t);
-    __syncwarp();  // the transform's last exchange reads are done: the buffer takes W^(-jm) u_j
-    auto epilogue = [&](auto J_) {
-      constexpr int J = decltype(J_)::value;
-      const float2 base = tw4096(g.twM, J * t);
-      SFor<0, P>::run([&](auto i_) {
-        constexpr int i = decltype(i_)::value;
-        if constexpr (J == 0)
-          xs[t + T * i] = v[i];
-        else
-          xs[t + T * i] = cmulc(v[i], twmul<32 * J * i, 4096, -1>(base));
-      });
-    };
-    switch (j) {
-      case 0: epilogue(std::integral_constant<int, 0>{}); break;
-      case 1: epilogue(std::integral_constant<int, 1>{}); break;
-      case 2: epilogue(std::integral_constant<int, 2>{}); break;
-      default: epilogue(std::integral_constant<int, 3>{}); break;
-    }
-    __syncthreads();
-    // kept rows: z[m] = v_0 + v_1 + v_2 + v_3, z[m + 1024] = (v_0 - v_2) + i (v_1 - v_3)
-    typename IO::T* p = spec + ((size_t)s * (N + 1) + vcol) * N;
-    const float2* b0 = sm + 2 * N;
-    for (int m = threadIdx.x; m < H; m += 128) {
-      const float2 a0 = b0[m], a1 = b0[Q::F::SMEM + m], a2 = b0[2 * Q::F::SMEM + m], a3 = b0[3 * Q::F::SMEM + m];
-      const float2 s02 = cadd(a0, a2), d02 = csub(a0, a2), s13 = cadd(a1, a3), d13 = csub(a1, a3);
-      IO::st(p, m, cadd(s02, s13));
-      IO::st(p, m + H, make_float2(d02.x - d13.y, d02.y + d13.x));
-    }
-    __syncthreads();  // the exchange buffers and this column buffer are free for the next column
+  };
+  switch (j) {
+    case 0: prologue(std::integral_constant<int, 0>{}); break;
+    case 1: prologue(std::integral_constant<int, 1>{}); break;
+    case 2: prologue(std::integral_constant<int, 2>{}); break;
+    default: prologue(std::integral_constant<int, 3>{}); break;
+  }
+  float2* xs = sm + N + j * Q::F::SMEM;
+  Q::F::template run<-1, float2, 2>(v, xs, g.twN, t);
+  // v[i] = X[4k + j], k = t + 32 i: row 4k + j of the 2N grid is row 2k + (j >> 1) of the
+  // (j & 1) half of the kernel spectrum
+  const float* cc = g.chat + ((size_t)vcol * 2 + (j & 1)) * N + (j >> 1);
+  SFor<0, P>::run([&](auto i_) {
+    constexpr int i = decltype(i_)::value;
+    const float c = __ldg(&cc[2 * (t + T * i)]);
+    v[i] = make_float2(v[i].x * c, v[i].y * c);
+  });
+  Q::F::template run<1, float2, 2>(v, xs, g.twN, t);
+  __syncwarp();  // the transform's last exchange reads are done: the buffer takes W^(-jm) u_j
+  auto epilogue = [&](auto J_) {
+    constexpr int J = decltype(J_)::value;
+    const float2 base = tw4096(g.twM, J * t);
+    SFor<0, P>::run([&](auto i_) {
+      constexpr int i = decltype(i_)::value;
+      if constexpr (J == 0)
+        xs[t + T * i] = v[i];
+      else
+        xs[t + T * i] = cmulc(v[i], twmul<32 * J * i, 4096, -1>(base));
+    });
+  };
+  switch (j) {
+    case 0: epilogue(std::integral_constant<int, 0>{}); break;
+    case 1: epilogue(std::integral_constant<int, 1>{}); break;
+    case 2: epilogue(std::integral_constant<int, 2>{}); break;
+    default: epilogue(std::integral_constant<int, 3>{}); break;
+  }
+  __syncthreads();
+  // kept rows: z[m] = v_0 + v_1 + v_2 + v_3, z[m + 1024] = (v_0 - v_2) + i (v_1 - v_3)
+  const float2* b0 = sm + N;
+  for (int m = threadIdx.x; m < H; m += 128) {
+    const float2 a0 = b0[m], a1 = b0[Q::F::SMEM + m], a2 = b0[2 * Q::F::SMEM + m], a3 = b0[3 * Q::F::SMEM + m];
+    const float2 s02 = cadd(a0, a2), d02 = csub(a0, a2), s13 = cadd(a1, a3), d13 = csub(a1, a3);
+    IO::st(p, m, cadd(s02, s13));
+    IO::st(p, m + H, make_float2(d02.x - d13.y, d02.y + d13.x));
   }
 }
 
-// Persistent like pass 1: the next row group's column segments are requested into L2 while the
-// current group is transformed.
 template <bool BF, int RB>
 __global__ void __launch_bounds__(64 * RB, 8 / RB) k_pass3a_q(GroupDev g, const IterState* st, float* kz) {
   using Q = Q2048;
   constexpr int N = Q::N, T = 32, P = 32, LDZ = Q::LDZ, THREADS = 64 * RB, NB = N / RB;
   extern __shared__ float2 sm[];
   if (st && skip_iter<BF>(st)) return;
+  const int s = blockIdx.x / NB, rb = blockIdx.x % NB;
   const int warp = threadIdx.x >> 5, t = threadIdx.x & 31, rl = warp >> 1, j = warp & 1;
-  using IO = SpecIO<BF>;
-  const typename IO::T* spec = reinterpret_cast<const typename IO::T*>(g.spec);
-  const int groups = g.S * NB;
-  for (int grp = blockIdx.x; grp < groups; grp += gridDim.x) {
-    const int nxt = grp + gridDim.x;
-    if (nxt < groups) {
-      const typename IO::T* sn = spec + (size_t)(nxt / NB) * (N + 1) * N + (nxt % NB) * RB;
-      for (int vv = threadIdx.x; vv <= N; vv += THREADS) prefetch_l2(sn + (size_t)vv * N);
-    }
-    const int s = grp / NB, rb = grp % NB;
-    const int r0 = rb * RB;
-    {
-      const typename IO::T* sp = spec + (size_t)s * (N + 1) * N + r0;
-      if constexpr (!BF) {
-        // RB-row segments of the column-major spectrum, all copies in flight at once
-        for (int e = threadIdx.x; e < (N + 1) * RB; e += THREADS) {
-          const int vv = e / RB, rr = e - vv * RB;
-          tc05::cp_async8(&sm[rr * LDZ + vv], sp + (size_t)vv * N + rr);
-        }
-        tc05::cp_async_wait_all();
-      } else {
-        batched_copy<THREADS, 8>(
-            (N + 1) * RB, [&](int e) { return IO::ld(sp, (size_t)(e / RB) * N + e % RB); },
-            [&](int e, float2 v) { sm[(e % RB) * LDZ + e / RB] = v; });
+  const int r0 = rb * RB;
+  {
+    using IO = SpecIO<BF>;
+    const typename IO::T* sp = reinterpret_cast<const typename IO::T*>(g.spec) + (size_t)s * (N + 1) * N + r0;
+    if constexpr (!BF) {
+      // RB-row segments of the column-major spectrum, all copies in flight at once
+      for (int e = threadIdx.x; e < (N + 1) * RB; e += THREADS) {
+        const int vv = e / RB, rr = e - vv * RB;
+        tc05::cp_async8(&sm[rr * LDZ + vv], sp + (size_t)vv * N + rr);
       }
+      tc05::cp_async_wait_all();
+    } else {
+      batched_copy<THREADS, 8>(
+          (N + 1) * RB, [&](int e) { return IO::ld(sp, (size_t)(e / RB) * N + e % RB); },
+          [&](int e, float2 v) { sm[(e % RB) * LDZ + e / RB] = v; });
     }
-    __syncthreads();
-    // the length-2N real inverse as the length-N complex inverse of Z[v] = E[v] + i O[v], at the
-    // v = 2k + j of this warp
-    float2 q[P];
-    const float2* row = sm + rl * LDZ;
-    SFor<0, P>::run([&](auto i_) {
-      constexpr int i = decltype(i_)::value;
-      const int vp = 2 * (t + T * i) + j;
-      const float2 zv = row[vp], zr = row[N - vp];
-      const float2 e = make_float2(zv.x + zr.x, zv.y - zr.y);
-      const float2 d = make_float2(zv.x - zr.x, zv.y + zr.y);
-      const float2 o = cmulc(d, __ldg(&g.twM[vp]));
-      q[i] = make_float2(e.x - o.y, e.y + o.x);
-    });
-    __syncthreads();  // the staged rows are read: the exchange buffers alias them
-    float2* xs = sm + warp * Q::F::SMEM;
-    Q::F::template run<1, float2, 2>(q, xs, g.twN, t);
-    __syncwarp();
-    SFor<0, P>::run([&](auto i_) {
-      constexpr int i = decltype(i_)::value;
-      const int n = t + T * i;
-      xs[n] = j ? cmulc(q[i], __ldg(&g.twM[2 * n])) : q[i];  // w^(-jn) u_j[n]
-    });
-    __syncthreads();
-    // z[n] = sum_j w^(-jn) u_j[n]: each warp of the row sums one half of it
-    const float2* o0 = sm + (2 * rl) * Q::F::SMEM;
-    float2* out = reinterpret_cast<float2*>(kz + ((size_t)s * N + r0 + rl) * N);
-    for (int n = j * (Q::H / 2) + t; n < (j + 1) * (Q::H / 2); n += 32) out[n] = cadd(o0[n], o0[Q::F::SMEM + n]);
-    __syncthreads();  // the exchange buffers are read: the next group stages into them
   }
+  __syncthreads();
+  // the length-2N real inverse as the length-N complex inverse of Z[v] = E[v] + i O[v], at the
+  // v = 2k + j of this warp
+  float2 q[P];
+  const float2* row = sm + rl * LDZ;
+  SFor<0, P>::run([&](auto i_) {
+    constexpr int i = decltype(i_)::value;
+    const int vp = 2 * (t + T * i) + j;
+    const float2 zv = row[vp], zr = row[N - vp];
+    const float2 e = make_float2(zv.x + zr.x, zv.y - zr.y);
+    const float2 d = make_float2(zv.x - zr.x, zv.y + zr.y);
+    const float2 o = cmulc(d, __ldg(&g.twM[vp]));
+    q[i] = make_float2(e.x - o.y, e.y + o.x);
+  });
+  __syncthreads();  // the staged rows are read: the exchange buffers alias them
+  float2* xs = sm + warp * Q::F::SMEM;
+  Q::F::template run<1, float2, 2>(q, xs, g.twN, t);
+  __syncwarp();
+  SFor<0, P>::run([&](auto i_) {
+    constexpr int i = decltype(i_)::value;
+    const int n = t + T * i;
+    xs[n] = j ? cmulc(q[i], __ldg(&g.twM[2 * n])) : q[i];  // w^(-jn) u_j[n]
+  });
+  __syncthreads();
+  // z[n] = sum_j w^(-jn) u_j[n]: each warp of the row sums one half of it
+  const float2* o0 = sm + (2 * rl) * Q::F::SMEM;
+  float2* out = reinterpret_cast<float2*>(kz + ((size_t)s * N + r0 + rl) * N);
+  for (int n = j * (Q::H / 2) + t; n < (j + 1) * (Q::H / 2); n += 32) out[n] = cadd(o0[n], o0[Q::F::SMEM + n]);
 }
 
 // ---------------------------------------------------------------- pass 3b: gradient and update
@@ -1426,24 +1368,6 @@ static int set_smem_limits() {
   return TMBIR_OK;
 }
 
-// Grid of a persistent kernel: as many blocks as fit on the device at once, at most `work`.
-template <class K>
-static int persistent_grid(K kernel, int threads, size_t smem, int work) {
-  int dev = 0, sms = 0, per = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess ||
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, smem) != cudaSuccess)
-    return -1;
-  per = per < 1 ? 1 : per;
-  return work < per * sms ? work : per * sms;
-}
-#define TMBIR_PERSISTENT(kernel, threads, smem, work, ...)                          \
-  do {                                                                              \
-    const int nblk_ = persistent_grid(kernel, threads, smem, work);                 \
-    if (nblk_ < 0) return set_error(TMBIR_ERR_CUDA, "occupancy query failed");      \
-    kernel<<<nblk_, threads, smem, s>>>(__VA_ARGS__);                               \
-  } while (0)
-
 template <int N>
 static int pass1_n(const GroupDev& g, const StepArgs& a, bool bf16, cudaStream_t s) {
   using Gm = Geo<N>;
@@ -1452,14 +1376,14 @@ static int pass1_n(const GroupDev& g, const StepArgs& a, bool bf16, cudaStream_t
     using Q = Q2048;
     if ((g.rb1 ? g.rb1 : Q::RB1) == 8) {
       if (bf16)
-        TMBIR_PERSISTENT((k_pass1_q<true, 8>), 512, Q::sm_rows<8>(), g.S * (N / 8), g, a);
+        k_pass1_q<true, 8><<<g.S * (N / 8), 512, Q::sm_rows<8>(), s>>>(g, a);
       else
-        TMBIR_PERSISTENT((k_pass1_q<false, 8>), 512, Q::sm_rows<8>(), g.S * (N / 8), g, a);
+        k_pass1_q<false, 8><<<g.S * (N / 8), 512, Q::sm_rows<8>(), s>>>(g, a);
     } else {
       if (bf16)
-        TMBIR_PERSISTENT((k_pass1_q<true, 4>), 256, Q::sm_rows<4>(), g.S * (N / 4), g, a);
+        k_pass1_q<true, 4><<<g.S * (N / 4), 256, Q::sm_rows<4>(), s>>>(g, a);
       else
-        TMBIR_PERSISTENT((k_pass1_q<false, 4>), 256, Q::sm_rows<4>(), g.S * (N / 4), g, a);
+        k_pass1_q<false, 4><<<g.S * (N / 4), 256, Q::sm_rows<4>(), s>>>(g, a);
     }
   } else if constexpr (is_block_fft_size<N>()) {
     using BG = BGeo<N>;
@@ -1481,10 +1405,11 @@ static int pass2_n(const GroupDev& g, const IterState* st, bool bf16, cudaStream
   using Gm = Geo<N>;
   if (int e = set_smem_limits<N>()) return e;
   if constexpr (N == 2048) {
+    const int blocks = g.S * (N + 1);
     if (bf16)
-      TMBIR_PERSISTENT(k_pass2_q<true>, 128, Q2048::SM2, g.S * (N + 1), g, st);
+      k_pass2_q<true><<<blocks, 128, Q2048::SM2, s>>>(g, st);
     else
-      TMBIR_PERSISTENT(k_pass2_q<false>, 128, Q2048::SM2, g.S * (N + 1), g, st);
+      k_pass2_q<false><<<blocks, 128, Q2048::SM2, s>>>(g, st);
   } else if constexpr (is_block_fft_size<N>()) {
     using BG = BGeo<N>;
     const int blocks = g.S * (N + 1);
@@ -1531,14 +1456,14 @@ static int pass3_n(const GroupDev& g, const StepArgs& a, Pass3Mode m, const Prio
       using Q = Q2048;
       if ((g.rb3 ? g.rb3 : Q::RB3) == 8) {
         if (bf16)
-          TMBIR_PERSISTENT((k_pass3a_q<true, 8>), 512, Q::sm_rows<8>(), g.S * (N / 8), g, st, kz);
+          k_pass3a_q<true, 8><<<g.S * (N / 8), 512, Q::sm_rows<8>(), s>>>(g, st, kz);
         else
-          TMBIR_PERSISTENT((k_pass3a_q<false, 8>), 512, Q::sm_rows<8>(), g.S * (N / 8), g, st, kz);
+          k_pass3a_q<false, 8><<<g.S * (N / 8), 512, Q::sm_rows<8>(), s>>>(g, st, kz);
       } else {
         if (bf16)
-          TMBIR_PERSISTENT((k_pass3a_q<true, 4>), 256, Q::sm_rows<4>(), g.S * (N / 4), g, st, kz);
+          k_pass3a_q<true, 4><<<g.S * (N / 4), 256, Q::sm_rows<4>(), s>>>(g, st, kz);
         else
-          TMBIR_PERSISTENT((k_pass3a_q<false, 4>), 256, Q::sm_rows<4>(), g.S * (N / 4), g, st, kz);
+          k_pass3a_q<false, 4><<<g.S * (N / 4), 256, Q::sm_rows<4>(), s>>>(g, st, kz);
       }
     } else if constexpr (is_block_fft_size<N>()) {
       using BG = BGeo<N>;
