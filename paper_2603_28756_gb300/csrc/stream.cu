@@ -242,6 +242,24 @@ int iter_out(Ctx& c, const Plan& p, char* ws, int j, float* xnext) {
   return TMBIR_OK;
 }
 
+// the final iterate from host slot src into the caller's buffer dst, slab by slab through the
+// device (copies in and out overlap; a host-to-host copy runs far below the link's rate)
+int copy_back(Ctx& c, const Plan& p, char* ws, const float* src, float* dst) {
+  const size_t N2 = (size_t)p.N * p.N;
+  for (int j = 0; j < p.nslab; ++j) {
+    const int s = j & 1, a = j * p.slab, n = std::min(p.slab, p.n - a);
+    TMBIR_CUDA(cudaStreamWaitEvent(c.s_in, c.ev_out[s], 0));  // set s's previous slab has left
+    TMBIR_CUDA(cudaMemcpyAsync(ws + p.off_x[s], src + (size_t)a * N2, (size_t)n * N2 * sizeof(float),
+                               cudaMemcpyHostToDevice, c.s_in));
+    TMBIR_CUDA(cudaEventRecord(c.ev_in[s], c.s_in));
+    TMBIR_CUDA(cudaStreamWaitEvent(c.s_out, c.ev_in[s], 0));
+    TMBIR_CUDA(cudaMemcpyAsync(dst + (size_t)a * N2, ws + p.off_x[s], (size_t)n * N2 * sizeof(float),
+                               cudaMemcpyDeviceToHost, c.s_out));
+    TMBIR_CUDA(cudaEventRecord(c.ev_out[s], c.s_out));
+  }
+  return TMBIR_OK;
+}
+
 }  // namespace
 }  // namespace tmbir
 
@@ -339,9 +357,9 @@ int tmbir_stream_reconstruct(tmbir_ctx* ctx, int n_slices, float* h_x, const flo
     TMBIR_CUDA(cudaStreamSynchronize(s));
   }
   if (prm->max_iter > 0 && cur != 0) {  // the final iterate back into the caller's buffer
-    TMBIR_CUDA(cudaMemcpyAsync(h_x, slot[cur], (size_t)n_slices * p.N * p.N * sizeof(float), cudaMemcpyHostToHost,
-                               c.s_out));
-    TMBIR_CUDA(cudaStreamSynchronize(c.s_out));
+    rc = fork_copies(c);
+    if (!rc) rc = copy_back(c, p, ws, slot[cur], h_x);
+    if ((rc = join_all(c, rc))) return rc;
   }
   c.last_iters = st.k;
   if (h_stats) {

@@ -697,17 +697,14 @@ __global__ void __launch_bounds__(128, 3) k_pass2_q(GroupDev g, const IterState*
   Q::F::template run<-1, float2, 2>(v, xs, g.twN, t);
   // v[i] = X[4k + j], k = t + 32 i: row 4k + j of the 2N grid is row 2k + (j >> 1) of the
   // (j & 1) half of the kernel spectrum
-  // times the kernel spectrum, conjugated: the inverse transform runs as the forward transform of
-  // the conjugate (conj(DFT(conj u)) = inverse DFT(u)), so the kernel holds one transform's code
   const float* cc = g.chat + ((size_t)vcol * 2 + (j & 1)) * N + (j >> 1);
   SFor<0, P>::run([&](auto i_) {
     constexpr int i = decltype(i_)::value;
     const float c = __ldg(&cc[2 * (t + T * i)]);
-    v[i] = make_float2(v[i].x * c, v[i].y * -c);
+    v[i] = make_float2(v[i].x * c, v[i].y * c);
   });
-  Q::F::template run<-1, float2, 2>(v, xs, g.twN, t);
-  __syncwarp();  // the transform's last exchange reads are done: the buffer takes conj(W^(-jm) u_j)
-  // v[i] = conj(u_j[m]); conj(W^(-jm) u_j) = W^(jm) v[i]
+  Q::F::template run<1, float2, 2>(v, xs, g.twN, t);
+  __syncwarp();  // the transform's last exchange reads are done: the buffer takes W^(-jm) u_j
   auto epilogue = [&](auto J_) {
     constexpr int J = decltype(J_)::value;
     const float2 base = tw4096(g.twM, J * t);
@@ -716,7 +713,7 @@ __global__ void __launch_bounds__(128, 3) k_pass2_q(GroupDev g, const IterState*
       if constexpr (J == 0)
         xs[t + T * i] = v[i];
       else
-        xs[t + T * i] = cmul(v[i], twmul<32 * J * i, 4096, -1>(base));
+        xs[t + T * i] = cmulc(v[i], twmul<32 * J * i, 4096, -1>(base));
     });
   };
   switch (j) {
@@ -726,14 +723,13 @@ __global__ void __launch_bounds__(128, 3) k_pass2_q(GroupDev g, const IterState*
     default: epilogue(std::integral_constant<int, 3>{}); break;
   }
   __syncthreads();
-  // kept rows from the conjugated parts w_j = conj(W^(-jm) u_j): z[m] = conj(w_0 + w_1 + w_2 + w_3),
-  // z[m + 1024] = conj((w_0 - w_2) - i (w_1 - w_3))
+  // kept rows: z[m] = v_0 + v_1 + v_2 + v_3, z[m + 1024] = (v_0 - v_2) + i (v_1 - v_3)
   const float2* b0 = sm + N;
   for (int m = threadIdx.x; m < H; m += 128) {
     const float2 a0 = b0[m], a1 = b0[Q::F::SMEM + m], a2 = b0[2 * Q::F::SMEM + m], a3 = b0[3 * Q::F::SMEM + m];
     const float2 s02 = cadd(a0, a2), d02 = csub(a0, a2), s13 = cadd(a1, a3), d13 = csub(a1, a3);
-    IO::st(p, m, make_float2(s02.x + s13.x, -s02.y - s13.y));
-    IO::st(p, m + H, make_float2(d02.x + d13.y, d13.x - d02.y));
+    IO::st(p, m, cadd(s02, s13));
+    IO::st(p, m + H, make_float2(d02.x - d13.y, d02.y + d13.x));
   }
 }
 
