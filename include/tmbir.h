@@ -433,7 +433,9 @@ int tmbir_stream_build_operator(tmbir_ctx* ctx, int n_slices, const float* h_sin
  *   h_x       [n_slices][N][N] FP32, host: x_0 in, the final iterate out.
  *   h_atg     R*g of the volume (tmbir_stream_build_operator); gtg_half its 1/2 g.g.
  *   h_work    2 n_slices N^2 floats of host scratch: with h_x, the three slots x_{k-1}, x_k and
- *             x_{k+1} rotate through.
+ *             x_{k+1} rotate through.  After a number of iterations that is a multiple of 3 the
+ *             final iterate is already in h_x; otherwise it is copied back into h_x through the
+ *             device, slab by slab (one more pass of copies in and out).
  * Per iteration each slab copies in x_k and x_{k-1} (with one halo slice on each side) and its
  * R*g, runs passes 1-3b on its own slices, and copies out x_{k+1}; the finalize kernel then
  * reduces the partial sums of all slabs in the order of the resident volume's pass-3b blocks, and

@@ -548,8 +548,27 @@ static GroupBlocks group_blocks(const Ctx& c) {
   return gb;
 }
 
-// Passes 1-3 of every group in Iterate mode, FP32 or BF16 storage variant; *nblocks receives
-// the number of partial-sum rows they write.
+// The launch sets of an iteration: runs of consecutive groups (at most kMergeMax) that one launch
+// per pass covers, [first, end) each; a group that cannot share launches forms a run of its own.
+static std::vector<std::pair<int, int>> launch_runs(const Ctx& c) {
+  std::vector<std::pair<int, int>> runs;
+  const int ng = (int)c.gdev.size();
+  for (int i = 0; i < ng;) {
+    int j = i + 1;
+    while (j < ng && j - i < kMergeMax && launch_set_ok(c.gdev[i], c.gdev[j])) ++j;
+    runs.emplace_back(i, j);
+    i = j;
+  }
+  return runs;
+}
+static int run_launches(const Ctx& c, const std::pair<int, int>& r) {
+  return r.second - r.first > 1 ? 4 : conv_launches(c.gdev[r.first]) + 1;
+}
+
+// Passes 1-3 of every group in Iterate mode, FP32 or BF16 storage variant: one launch per pass
+// for each run of groups that can share launches (consecutive groups of one image side, e.g.
+// the angle counts of one side in an uneven batch).  *nblocks receives the number of
+// partial-sum rows they write (each group's rows where its own launches would put them).
 static int enqueue_passes(Ctx& c, float* d_x, const float* d_atg, const PriorC& pc, bool bf16, int* nblocks) {
   StepArgs a{};
   a.atg = d_atg;
@@ -558,12 +577,18 @@ static int enqueue_passes(Ctx& c, float* d_x, const float* d_atg, const PriorC& 
   a.xb[2] = c.xbuf[1];
   a.st = c.state;
   int off = 0;
-  for (size_t i = 0; i < c.gdev.size(); ++i) {
-    const GroupDev& g = c.gdev[i];
-    a.gm = c.gmom + i;
-    if (int e = launch_convolution(g, a, Pass3Mode::Iterate, pc, c.stream, bf16)) return e;
-    if (int e = launch_pass3(g, a, Pass3Mode::Iterate, pc, c.partials, off, c.stream, bf16, 2)) return e;
-    off += blocks_pass3(g);
+  for (const auto& r : launch_runs(c)) {
+    a.gm = c.gmom + r.first;
+    if (r.second - r.first > 1) {
+      if (int e = launch_passes_set(c.gdev.data() + r.first, r.second - r.first, a, pc, c.partials, off, c.stream,
+                                    bf16))
+        return e;
+    } else {
+      const GroupDev& g = c.gdev[r.first];
+      if (int e = launch_convolution(g, a, Pass3Mode::Iterate, pc, c.stream, bf16)) return e;
+      if (int e = launch_pass3(g, a, Pass3Mode::Iterate, pc, c.partials, off, c.stream, bf16, 2)) return e;
+    }
+    for (int i = r.first; i < r.second; ++i) off += blocks_pass3(c.gdev[i]);
   }
   *nblocks = off;
   return TMBIR_OK;
@@ -590,7 +615,7 @@ static int enqueue_trip(Ctx& c, float* d_x, const float* d_atg, const PriorC& pc
   int nb = 0;
   if (int e = enqueue_passes(c, d_x, d_atg, pc, bf16, &nb)) return e;
   int trip_launches = 1;
-  for (const GroupDev& g : c.gdev) trip_launches += conv_launches(g) + 1;
+  for (const auto& r : launch_runs(c)) trip_launches += run_launches(c, r);
   return launch_finalize(c.state, c.gmom, c.partials, group_blocks(c), c.log, c.stream, cond, use_cond, trip_launches);
 }
 

@@ -117,6 +117,25 @@ struct GroupDev {
   int rb1, rb3;        // rows per block of passes 1 and 3a where a side has variants (0: default)
 };
 
+// Up to kMergeMax consecutive groups of one image side that one launch of a pass covers: block
+// b of the launch belongs to the group i with boff[i] <= b < boff[i + 1].  Kernels take it as a
+// __grid_constant__ parameter, so the per-block group lookup reads the parameter bank in place.
+constexpr int kMergeMax = 8;
+struct GroupSet {
+  int n;
+  int boff[kMergeMax + 1];
+  GroupDev g[kMergeMax];
+#ifdef __CUDACC__
+  // the group of this block, and the block's index within that group
+  __device__ __forceinline__ int pick(int& bid) const {
+    int i = 0;
+    while (i + 1 < n && (int)blockIdx.x >= boff[i + 1]) ++i;
+    bid = (int)blockIdx.x - boff[i];
+    return i;
+  }
+#endif
+};
+
 // Passes 1, 2 and 3a may run in chunks of slices (a chunk's half spectra can then stay in L2
 // between the three passes).  Measured on GB300 at 64 x 1024^2 the whole group in one chunk is
 // fastest (the shorter launches lose more to launch gaps and partial last waves than L2 reuse
@@ -237,6 +256,13 @@ int launch_pass2(const GroupDev& g, const IterState* st, cudaStream_t s, bool bf
 // update, partial sums); part selects 3a (1), 3b (2) or both (3).
 int launch_pass3(const GroupDev& g, const StepArgs& a, Pass3Mode mode, const PriorC& pc, double* partials,
                  int block_offset, cudaStream_t s, bool bf16 = false, int part = 3);
+// The passes of n consecutive groups (n <= kMergeMax) of one image side in one launch each, in
+// Iterate mode (a.gm is the first group's momentum state).  The groups must share the rows per
+// block of passes 1 and 3a and hold their spectra in one chunk (launch_set_ok); pass 3b's blocks
+// write the partial-sum rows the groups' separate launches would.
+bool launch_set_ok(const GroupDev& first, const GroupDev& g);
+int launch_passes_set(const GroupDev* gs, int n, const StepArgs& a, const PriorC& pc, double* partials,
+                      int block_offset, cudaStream_t s, bool bf16);
 int blocks_pass3(const GroupDev& g);
 // slices [c0, c0 + n) of a group as a group of their own (same spectrum buffer)
 GroupDev chunk_view(const GroupDev& g, int c0, int n);

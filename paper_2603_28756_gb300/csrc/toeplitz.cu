@@ -24,10 +24,10 @@ void fft_shape(int N, int* T, int* P) {
 }
 
 #define TMBIR_DECL_N(N)                                                                                     \
-  int pass1_##N(const GroupDev& g, const StepArgs& a, bool bf16, cudaStream_t s);                           \
-  int pass2_##N(const GroupDev& g, const IterState* st, bool bf16, cudaStream_t s);                         \
-  int pass3_##N(const GroupDev& g, const StepArgs& a, Pass3Mode m, const PriorC& pc, double* partials, int off, \
-                bool bf16, int part, cudaStream_t s);
+  int pass1_##N(const GroupDev* gs, int n, const StepArgs& a, bool bf16, cudaStream_t s);                   \
+  int pass2_##N(const GroupDev* gs, int n, const IterState* st, bool bf16, cudaStream_t s);                 \
+  int pass3_##N(const GroupDev* gs, int n, const StepArgs& a, Pass3Mode m, const PriorC& pc, double* partials, \
+                int off, bool bf16, int part, cudaStream_t s);
 TMBIR_DECL_N(64)
 TMBIR_DECL_N(128)
 TMBIR_DECL_N(256)
@@ -145,14 +145,38 @@ __global__ void __launch_bounds__(512) k_finalize(IterState* st, GroupMom* gm, c
   }
 
 int launch_pass1(const GroupDev& g, const StepArgs& a, cudaStream_t s, bool bf16) {
-  TMBIR_DISPATCH_N(g.N, pass1_, g, a, bf16, s);
+  TMBIR_DISPATCH_N(g.N, pass1_, &g, 1, a, bf16, s);
 }
 int launch_pass2(const GroupDev& g, const IterState* st, cudaStream_t s, bool bf16) {
-  TMBIR_DISPATCH_N(g.N, pass2_, g, st, bf16, s);
+  TMBIR_DISPATCH_N(g.N, pass2_, &g, 1, st, bf16, s);
 }
 int launch_pass3(const GroupDev& g, const StepArgs& a, Pass3Mode m, const PriorC& pc, double* partials, int off,
                  cudaStream_t s, bool bf16, int part) {
-  TMBIR_DISPATCH_N(g.N, pass3_, g, a, m, pc, partials, off, bf16, part, s);
+  TMBIR_DISPATCH_N(g.N, pass3_, &g, 1, a, m, pc, partials, off, bf16, part, s);
+}
+bool launch_set_ok(const GroupDev& first, const GroupDev& g) {
+  return g.N == first.N && g.rb1 == first.rb1 && g.rb3 == first.rb3 && spec_chunk(g) == g.S &&
+         spec_chunk(first) == first.S;
+}
+static int pass1_set(const GroupDev* gs, int n, const StepArgs& a, cudaStream_t s, bool bf16) {
+  TMBIR_DISPATCH_N(gs[0].N, pass1_, gs, n, a, bf16, s);
+}
+static int pass2_set(const GroupDev* gs, int n, const IterState* st, cudaStream_t s, bool bf16) {
+  TMBIR_DISPATCH_N(gs[0].N, pass2_, gs, n, st, bf16, s);
+}
+static int pass3_set(const GroupDev* gs, int n, const StepArgs& a, const PriorC& pc, double* partials, int off,
+                     cudaStream_t s, bool bf16, int part) {
+  TMBIR_DISPATCH_N(gs[0].N, pass3_, gs, n, a, Pass3Mode::Iterate, pc, partials, off, bf16, part, s);
+}
+int launch_passes_set(const GroupDev* gs, int n, const StepArgs& a, const PriorC& pc, double* partials,
+                      int block_offset, cudaStream_t s, bool bf16) {
+  if (n < 1 || n > kMergeMax) return set_error(TMBIR_ERR_ARG, "group set size");
+  for (int i = 1; i < n; ++i)
+    if (!launch_set_ok(gs[0], gs[i])) return set_error(TMBIR_ERR_ARG, "groups of one launch must share its shape");
+  if (int e = pass1_set(gs, n, a, s, bf16)) return e;
+  if (int e = pass2_set(gs, n, a.st, s, bf16)) return e;
+  if (int e = pass3_set(gs, n, a, pc, nullptr, 0, s, bf16, 1)) return e;
+  return pass3_set(gs, n, a, pc, partials, block_offset, s, bf16, 2);
 }
 GroupDev chunk_view(const GroupDev& g, int c0, int n) {
   GroupDev v = g;

@@ -208,11 +208,14 @@ __device__ __forceinline__ void block_partials(double (&acc)[kParts], double* re
 
 // ---------------------------------------------------------------- pass 1: rows, forward
 template <int N, bool BF>
-__global__ void __launch_bounds__(Geo<N>::THREADS) k_pass1(GroupDev g, StepArgs a) {
+__global__ void __launch_bounds__(Geo<N>::THREADS) k_pass1(const __grid_constant__ GroupSet gs, StepArgs a) {
   using Gm = Geo<N>;
   using F = typename Gm::F;
   constexpr int T = Gm::T, P = Gm::P, G = Gm::G, RB = Gm::RB, LD = Gm::LD;
   extern __shared__ float2 sm[];
+  int bid_;
+  const int gi_ = gs.pick(bid_);
+  const GroupDev& g = gs.g[gi_];
   const float *x, *xp;
   float beta;
   if (a.st) {
@@ -221,13 +224,13 @@ __global__ void __launch_bounds__(Geo<N>::THREADS) k_pass1(GroupDev g, StepArgs 
     // selects rather than an indexed parameter array, which would be copied to local memory
     x = cur == 0 ? a.xb[0] : (cur == 1 ? a.xb[1] : a.xb[2]);
     xp = cur == 0 ? a.xb[2] : (cur == 1 ? a.xb[0] : a.xb[1]);
-    beta = (float)a.gm->beta;
+    beta = (float)(a.gm + gi_)->beta;
   } else {
     x = a.x;
     xp = a.xprev;
     beta = a.beta;
   }
-  const int s = blockIdx.x / Gm::NB, rb = blockIdx.x % Gm::NB;
+  const int s = bid_ / Gm::NB, rb = bid_ % Gm::NB;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, grp = lane / T, t = lane % T;
   const int rl = warp * G + grp;
   const int r = rb * RB + rl;
@@ -296,15 +299,18 @@ __device__ __forceinline__ void column_of(int col, int S, int ncol, int& vcol, i
 }
 
 template <int N, bool BF>
-__global__ void TMBIR_P2_BOUNDS(Geo<N>::THREADS) k_pass2(GroupDev g, const IterState* st) {
+__global__ void TMBIR_P2_BOUNDS(Geo<N>::THREADS) k_pass2(const __grid_constant__ GroupSet gs, const IterState* st) {
   using Gm = Geo<N>;
   using F = typename Gm::F;
   constexpr int T = Gm::T, P = Gm::P, G = Gm::G;
   extern __shared__ float2 sm[];
+  int bid_;
+  const int gi_ = gs.pick(bid_);
+  const GroupDev& g = gs.g[gi_];
   if (st && skip_iter<BF>(st)) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, grp = lane / T, t = lane % T;
   const int unit = warp * G + grp, h = unit & 1;
-  const int col = blockIdx.x * Gm::CPB + (unit >> 1);
+  const int col = bid_ * Gm::CPB + (unit >> 1);
   const int ncols = g.S * (N + 1);
   const bool active = col < ncols;
   int vcol = 0, s = 0;
@@ -357,13 +363,17 @@ __global__ void TMBIR_P2_BOUNDS(Geo<N>::THREADS) k_pass2(GroupDev g, const IterS
 // Inverse packed real row transform of every row (one row group per warp, RB rows per block,
 // the layout of pass 1), crop to the first N columns: K (*) y written row-major as FP32.
 template <int N, bool BF>
-__global__ void TMBIR_P3A_BOUNDS(Geo3a<N>::THREADS) k_pass3a(GroupDev g, const IterState* st, float* kz) {
+__global__ void TMBIR_P3A_BOUNDS(Geo3a<N>::THREADS) k_pass3a(const __grid_constant__ GroupSet gs, const IterState* st, float* apply_out) {
   using Gm = Geo3a<N>;
   using F = typename Gm::F;
   constexpr int T = Gm::T, P = Gm::P, G = Gm::G, RB = Gm::RB, LD = Gm::LD;
   extern __shared__ float2 sm[];
+  int bid_;
+  const int gi_ = gs.pick(bid_);
+  const GroupDev& g = gs.g[gi_];
+  float* kz = apply_out ? apply_out + g.img_off : g.kz;
   if (st && skip_iter<BF>(st)) return;
-  const int s = blockIdx.x / Gm::NB, rb = blockIdx.x % Gm::NB;
+  const int s = bid_ / Gm::NB, rb = bid_ % Gm::NB;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, grp = lane / T, t = lane % T;
   const int rl = warp * G + grp;
   const int r0 = rb * RB;
@@ -423,9 +433,12 @@ struct BGeo {
 };
 
 template <int N, bool BF>
-__global__ void __launch_bounds__(256) k_pass1_b(GroupDev g, StepArgs a) {
+__global__ void __launch_bounds__(256) k_pass1_b(const __grid_constant__ GroupSet gs, StepArgs a) {
   using BG = BGeo<N>;
   extern __shared__ float2 sm[];
+  int bid_;
+  const int gi_ = gs.pick(bid_);
+  const GroupDev& g = gs.g[gi_];
   const float *x, *xp;
   float beta;
   if (a.st) {
@@ -434,13 +447,13 @@ __global__ void __launch_bounds__(256) k_pass1_b(GroupDev g, StepArgs a) {
     // selects rather than an indexed parameter array, which would be copied to local memory
     x = cur == 0 ? a.xb[0] : (cur == 1 ? a.xb[1] : a.xb[2]);
     xp = cur == 0 ? a.xb[2] : (cur == 1 ? a.xb[0] : a.xb[1]);
-    beta = (float)a.gm->beta;
+    beta = (float)(a.gm + gi_)->beta;
   } else {
     x = a.x;
     xp = a.xprev;
     beta = a.beta;
   }
-  const int s = blockIdx.x / BG::NB, rb = blockIdx.x % BG::NB;
+  const int s = bid_ / BG::NB, rb = bid_ % BG::NB;
   float2* X = sm;
   float2* Y = sm + N;
   float2* tb = sm + 2 * N;
@@ -477,12 +490,15 @@ __global__ void __launch_bounds__(256) k_pass1_b(GroupDev g, StepArgs a) {
 }
 
 template <int N, bool BF>
-__global__ void __launch_bounds__(256) k_pass2_b(GroupDev g, const IterState* st) {
+__global__ void __launch_bounds__(256) k_pass2_b(const __grid_constant__ GroupSet gs, const IterState* st) {
   using BG = BGeo<N>;
   extern __shared__ float2 sm[];
+  int bid_;
+  const int gi_ = gs.pick(bid_);
+  const GroupDev& g = gs.g[gi_];
   if (st && skip_iter<BF>(st)) return;
   int vcol, s;
-  column_of(blockIdx.x, g.S, N + 1, vcol, s);
+  column_of(bid_, g.S, N + 1, vcol, s);
   using IO = SpecIO<BF>;
   typename IO::T* p = reinterpret_cast<typename IO::T*>(g.spec) + ((size_t)s * (N + 1) + vcol) * N;
   float2* X = sm;
@@ -511,11 +527,15 @@ __global__ void __launch_bounds__(256) k_pass2_b(GroupDev g, const IterState* st
 }
 
 template <int N, bool BF>
-__global__ void __launch_bounds__(256) k_pass3a_b(GroupDev g, const IterState* st, float* kz) {
+__global__ void __launch_bounds__(256) k_pass3a_b(const __grid_constant__ GroupSet gs, const IterState* st, float* apply_out) {
   using BG = BGeo<N>;
   extern __shared__ float2 sm[];
+  int bid_;
+  const int gi_ = gs.pick(bid_);
+  const GroupDev& g = gs.g[gi_];
+  float* kz = apply_out ? apply_out + g.img_off : g.kz;
   if (st && skip_iter<BF>(st)) return;
-  const int s = blockIdx.x / BG::NB, rb = blockIdx.x % BG::NB;
+  const int s = bid_ / BG::NB, rb = bid_ % BG::NB;
   const int r0 = rb * BG::RB;
   float2* X = sm;
   float2* Y = sm + N;
@@ -584,10 +604,13 @@ __device__ __forceinline__ float2 tw4096(const float2* __restrict__ twM, int n) 
 }
 
 template <bool BF, int RB>
-__global__ void __launch_bounds__(64 * RB) k_pass1_q(GroupDev g, StepArgs a) {
+__global__ void __launch_bounds__(64 * RB) k_pass1_q(const __grid_constant__ GroupSet gs, StepArgs a) {
   using Q = Q2048;
   constexpr int N = Q::N, T = 32, P = 32, LDZ = Q::LDZ, THREADS = 64 * RB, NB = N / RB;
   extern __shared__ float2 sm[];
+  int bid_;
+  const int gi_ = gs.pick(bid_);
+  const GroupDev& g = gs.g[gi_];
   const float *x, *xp;
   float beta;
   if (a.st) {
@@ -595,13 +618,13 @@ __global__ void __launch_bounds__(64 * RB) k_pass1_q(GroupDev g, StepArgs a) {
     const int cur = a.st->cur;
     x = cur == 0 ? a.xb[0] : (cur == 1 ? a.xb[1] : a.xb[2]);
     xp = cur == 0 ? a.xb[2] : (cur == 1 ? a.xb[0] : a.xb[1]);
-    beta = (float)a.gm->beta;
+    beta = (float)(a.gm + gi_)->beta;
   } else {
     x = a.x;
     xp = a.xprev;
     beta = a.beta;
   }
-  const int s = blockIdx.x / NB, rb = blockIdx.x % NB;
+  const int s = bid_ / NB, rb = bid_ % NB;
   const int warp = threadIdx.x >> 5, t = threadIdx.x & 31, rl = warp >> 1, j = warp & 1;
   const size_t base = g.img_off + ((size_t)s * N + rb * RB + rl) * N;
   // packed row z[m] = y[2m] + i y[2m+1], m < 1024 (the padding above is zero), times w^(jm)
@@ -642,14 +665,17 @@ __global__ void __launch_bounds__(64 * RB) k_pass1_q(GroupDev g, StepArgs a) {
 }
 
 template <bool BF>
-__global__ void __launch_bounds__(128, 3) k_pass2_q(GroupDev g, const IterState* st) {
+__global__ void __launch_bounds__(128, 3) k_pass2_q(const __grid_constant__ GroupSet gs, const IterState* st) {
   using Q = Q2048;
   constexpr int N = Q::N, H = Q::H, T = 32, P = 32;
   extern __shared__ float2 sm[];
+  int bid_;
+  const int gi_ = gs.pick(bid_);
+  const GroupDev& g = gs.g[gi_];
   if (st && skip_iter<BF>(st)) return;
   const int j = threadIdx.x >> 5, t = threadIdx.x & 31;
   int vcol, s;
-  column_of(blockIdx.x, g.S, N + 1, vcol, s);
+  column_of(bid_, g.S, N + 1, vcol, s);
   using IO = SpecIO<BF>;
   typename IO::T* p = reinterpret_cast<typename IO::T*>(g.spec) + ((size_t)s * (N + 1) + vcol) * N;
   float2* col = sm;
@@ -734,12 +760,16 @@ __global__ void __launch_bounds__(128, 3) k_pass2_q(GroupDev g, const IterState*
 }
 
 template <bool BF, int RB>
-__global__ void __launch_bounds__(64 * RB, 8 / RB) k_pass3a_q(GroupDev g, const IterState* st, float* kz) {
+__global__ void __launch_bounds__(64 * RB, 8 / RB) k_pass3a_q(const __grid_constant__ GroupSet gs, const IterState* st, float* apply_out) {
   using Q = Q2048;
   constexpr int N = Q::N, T = 32, P = 32, LDZ = Q::LDZ, THREADS = 64 * RB, NB = N / RB;
   extern __shared__ float2 sm[];
+  int bid_;
+  const int gi_ = gs.pick(bid_);
+  const GroupDev& g = gs.g[gi_];
+  float* kz = apply_out ? apply_out + g.img_off : g.kz;
   if (st && skip_iter<BF>(st)) return;
-  const int s = blockIdx.x / NB, rb = blockIdx.x % NB;
+  const int s = bid_ / NB, rb = bid_ % NB;
   const int warp = threadIdx.x >> 5, t = threadIdx.x & 31, rl = warp >> 1, j = warp & 1;
   const int r0 = rb * RB;
   {
@@ -1155,8 +1185,8 @@ __device__ __forceinline__ void band_step(const float* S0, const float* S1, bool
 // phase this launch belongs to (0 FP32, 1 BF16), checked like the other passes.
 template <int N, int MODE, bool Q2>
 __global__ void __launch_bounds__(GeoP<N>::THREADS, 2)
-    k_pass3(GroupDev g, StepArgs a, PriorC pc, const float* __restrict__ kz, int phase, double* partials,
-            int block_offset, int zc) {
+    k_pass3(const __grid_constant__ GroupSet gs, StepArgs a, PriorC pc, const float* apply_out, int phase,
+            double* partials, int block_offset) {
   using GP = GeoP<N>;
   constexpr int R = GP::R;
   constexpr bool PRIOR = MODE != (int)Pass3Mode::Apply;
@@ -1165,6 +1195,11 @@ __global__ void __launch_bounds__(GeoP<N>::THREADS, 2)
   constexpr bool UPDATE = MODE == (int)Pass3Mode::Step || MODE == (int)Pass3Mode::Iterate;
   extern __shared__ float2 sm[];
   __shared__ double red[GP::WPB * kParts];
+  int bid_;
+  const int gi_ = gs.pick(bid_);
+  const GroupDev& g = gs.g[gi_];
+  const float* __restrict__ kz = apply_out ? apply_out + g.img_off : g.kz;
+  const int zc = g.zc;  // resolved by the launcher
   const float *x, *xp;
   float* out;
   float beta, invL;
@@ -1174,8 +1209,8 @@ __global__ void __launch_bounds__(GeoP<N>::THREADS, 2)
     x = cur == 0 ? a.xb[0] : (cur == 1 ? a.xb[1] : a.xb[2]);
     xp = cur == 0 ? a.xb[2] : (cur == 1 ? a.xb[0] : a.xb[1]);
     out = cur == 0 ? a.xb[1] : (cur == 1 ? a.xb[2] : a.xb[0]);
-    beta = (float)a.gm->beta;
-    invL = (float)a.gm->invL;
+    beta = (float)(a.gm + gi_)->beta;
+    invL = (float)(a.gm + gi_)->invL;
   } else {
     x = a.x;
     xp = a.xprev;
@@ -1183,10 +1218,17 @@ __global__ void __launch_bounds__(GeoP<N>::THREADS, 2)
     beta = a.beta;
     invL = a.invL;
   }
-  const int band = blockIdx.x % GP::NB;
-  const int cb = (blockIdx.x / GP::NB) % GP::CB;
-  const int chunk = blockIdx.x / (GP::NB * GP::CB);
-  const int z0 = g.zlo + chunk * zc, z1 = min(g.zlo + (g.zn > 0 ? g.zn : g.S), z0 + zc);
+  // the group's slices as the origin of every image pointer
+  const size_t go = g.img_off;
+  const int S = g.S;
+  x += go;
+  xp += go;
+  out += go;
+  const float* __restrict__ atg = a.atg + go;
+  const int band = bid_ % GP::NB;
+  const int cb = (bid_ / GP::NB) % GP::CB;
+  const int chunk = bid_ / (GP::NB * GP::CB);
+  const int z0 = g.zlo + chunk * zc, z1 = min(g.zlo + (g.zn > 0 ? g.zn : S), z0 + zc);
   const int r0 = band * R, c0 = cb * GP::BC;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int c0w = c0 + 64 * warp;
@@ -1206,7 +1248,7 @@ __global__ void __launch_bounds__(GeoP<N>::THREADS, 2)
       for (int t = 0; t < R; ++t) {
         const size_t o = (size_t)z * N2 + (size_t)(r0 + t) * N + acol;
         const float2 zd = __ldg(reinterpret_cast<const float2*>(kz + o));
-        const float2 xv = __ldg(reinterpret_cast<const float2*>(x + g.img_off + o));
+        const float2 xv = __ldg(reinterpret_cast<const float2*>(x + o));
         acc0 = f2fma(xv, zd, acc0);
         acc5 = f2fma(zd, zd, acc5);
       }
@@ -1235,13 +1277,13 @@ __global__ void __launch_bounds__(GeoP<N>::THREADS, 2)
       const size_t o = (size_t)zz * N2 + (size_t)(r0 + t) * N + acol;
       float2* d = fin_in + 3 * t * GP::THREADS;
       tc05::cp_async8(d, kz + o);
-      tc05::cp_async8(d + GP::THREADS, a.atg + g.img_off + o);
-      if constexpr (UPDATE) tc05::cp_async8(d + 2 * GP::THREADS, x + g.img_off + o);
+      tc05::cp_async8(d + GP::THREADS, atg + o);
+      if constexpr (UPDATE) tc05::cp_async8(d + 2 * GP::THREADS, x + o);
     };
     float2 ph[3] = {f2(0.f), f2(0.f), f2(0.f)};
-    load_ring_p<N>(ring + (z0 & 1) * SLOT, x, xp, beta, g.img_off + (size_t)z0 * N2, r0, c0);
+    load_ring_p<N>(ring + (z0 & 1) * SLOT, x, xp, beta, (size_t)z0 * N2, r0, c0);
     if (z0 > 0) {
-      load_ring_p<N>(ring + ((z0 - 1) & 1) * SLOT, x, xp, beta, g.img_off + (size_t)(z0 - 1) * N2, r0, c0);
+      load_ring_p<N>(ring + ((z0 - 1) & 1) * SLOT, x, xp, beta, (size_t)(z0 - 1) * N2, r0, c0);
     } else {
 #pragma unroll
       for (int t = 0; t < R; ++t) cr[t * (GP::BC / 2)] = f2(0.f);
@@ -1249,7 +1291,7 @@ __global__ void __launch_bounds__(GeoP<N>::THREADS, 2)
     __syncthreads();
     ring_shift<N>(ring + (z0 & 1) * SLOT);
     if (z0 > 0) ring_shift<N>(ring + ((z0 - 1) & 1) * SLOT);
-    if (z0 + 1 < g.S) stage_issue<N>(stg, x, xp, g.img_off + (size_t)(z0 + 1) * N2, r0, c0);
+    if (z0 + 1 < S) stage_issue<N>(stg, x, xp, (size_t)(z0 + 1) * N2, r0, c0);
 #pragma unroll
     for (int t = 0; t < R; ++t) fetch(z0, t);
     __syncthreads();
@@ -1271,13 +1313,13 @@ __global__ void __launch_bounds__(GeoP<N>::THREADS, 2)
       // staging area; then the staging area takes slice z + 2 while slice z is worked on
       tc05::cp_async_wait_all();
       __syncthreads();
-      if (z + 1 < g.S) stage_to_ring<N>(ring + ((z + 1) & 1) * SLOT, stg, beta);
+      if (z + 1 < S) stage_to_ring<N>(ring + ((z + 1) & 1) * SLOT, stg, beta);
       __syncthreads();
-      if (z + 1 < z1 && z + 2 < g.S) stage_issue<N>(stg, x, xp, g.img_off + (size_t)(z + 2) * N2, r0, c0);
+      if (z + 1 < z1 && z + 2 < S) stage_issue<N>(stg, x, xp, (size_t)(z + 2) * N2, r0, c0);
       float2 acc[kParts];
 #pragma unroll
       for (int j = 0; j < kParts; ++j) acc[j] = f2(0.f);
-      const size_t img = g.img_off + (size_t)z * N2 + acol;
+      const size_t img = (size_t)z * N2 + acol;
       const bool more = z + 1 < z1;
       auto fin = [&](int t, float2 gsum, float2 yv) {
         const size_t ro = (size_t)(r0 + t) * N;
@@ -1301,12 +1343,12 @@ __global__ void __launch_bounds__(GeoP<N>::THREADS, 2)
       const float* s0 = ring + (z & 1) * SLOT;
       const float* s1 = ring + ((z + 1) & 1) * SLOT;
       if (rowe)
-        band_step<N, Q2, PHI, false, true, true>(s0, s1, z + 1 < g.S, r0, c0w, ia, okL, okR, cr, edge, pk, pw, ph, fin);
+        band_step<N, Q2, PHI, false, true, true>(s0, s1, z + 1 < S, r0, c0w, ia, okL, okR, cr, edge, pk, pw, ph, fin);
       else if (cole)
-        band_step<N, Q2, PHI, false, false, true>(s0, s1, z + 1 < g.S, r0, c0w, ia, okL, okR, cr, edge, pk, pw, ph,
+        band_step<N, Q2, PHI, false, false, true>(s0, s1, z + 1 < S, r0, c0w, ia, okL, okR, cr, edge, pk, pw, ph,
                                                   fin);
       else
-        band_step<N, Q2, PHI, false, false, false>(s0, s1, z + 1 < g.S, r0, c0w, ia, okL, okR, cr, edge, pk, pw, ph,
+        band_step<N, Q2, PHI, false, false, false>(s0, s1, z + 1 < S, r0, c0w, ia, okL, okR, cr, edge, pk, pw, ph,
                                                    fin);
       if constexpr (PHI) {
 #pragma unroll
@@ -1368,125 +1410,154 @@ static int set_smem_limits() {
   return TMBIR_OK;
 }
 
+// A group set of n groups, with each group's share of the launch's blocks.
+template <class BlocksOf>
+static GroupSet make_set(const GroupDev* gs, int n, BlocksOf&& blocks_of) {
+  static_assert(sizeof(GroupSet) <= 4000, "group set exceeds the kernel parameter space");
+  GroupSet set{};
+  set.n = n;
+  for (int i = 0; i < n; ++i) {
+    set.g[i] = gs[i];
+    set.boff[i + 1] = set.boff[i] + blocks_of(gs[i]);
+  }
+  return set;
+}
+
 template <int N>
-static int pass1_n(const GroupDev& g, const StepArgs& a, bool bf16, cudaStream_t s) {
+static int pass1_n(const GroupDev* gs, int n, const StepArgs& a, bool bf16, cudaStream_t s) {
   using Gm = Geo<N>;
   if (int e = set_smem_limits<N>()) return e;
   if constexpr (N == 2048) {
     using Q = Q2048;
-    if ((g.rb1 ? g.rb1 : Q::RB1) == 8) {
+    if ((gs[0].rb1 ? gs[0].rb1 : Q::RB1) == 8) {
+      const GroupSet set = make_set(gs, n, [](const GroupDev& g) { return g.S * (N / 8); });
       if (bf16)
-        k_pass1_q<true, 8><<<g.S * (N / 8), 512, Q::sm_rows<8>(), s>>>(g, a);
+        k_pass1_q<true, 8><<<set.boff[n], 512, Q::sm_rows<8>(), s>>>(set, a);
       else
-        k_pass1_q<false, 8><<<g.S * (N / 8), 512, Q::sm_rows<8>(), s>>>(g, a);
+        k_pass1_q<false, 8><<<set.boff[n], 512, Q::sm_rows<8>(), s>>>(set, a);
     } else {
+      const GroupSet set = make_set(gs, n, [](const GroupDev& g) { return g.S * (N / 4); });
       if (bf16)
-        k_pass1_q<true, 4><<<g.S * (N / 4), 256, Q::sm_rows<4>(), s>>>(g, a);
+        k_pass1_q<true, 4><<<set.boff[n], 256, Q::sm_rows<4>(), s>>>(set, a);
       else
-        k_pass1_q<false, 4><<<g.S * (N / 4), 256, Q::sm_rows<4>(), s>>>(g, a);
+        k_pass1_q<false, 4><<<set.boff[n], 256, Q::sm_rows<4>(), s>>>(set, a);
     }
   } else if constexpr (is_block_fft_size<N>()) {
     using BG = BGeo<N>;
+    const GroupSet set = make_set(gs, n, [](const GroupDev& g) { return g.S * BG::NB; });
     if (bf16)
-      k_pass1_b<N, true><<<g.S * BG::NB, BG::THREADS, BG::SM_ROWS, s>>>(g, a);
+      k_pass1_b<N, true><<<set.boff[n], BG::THREADS, BG::SM_ROWS, s>>>(set, a);
     else
-      k_pass1_b<N, false><<<g.S * BG::NB, BG::THREADS, BG::SM_ROWS, s>>>(g, a);
+      k_pass1_b<N, false><<<set.boff[n], BG::THREADS, BG::SM_ROWS, s>>>(set, a);
   } else {
+    const GroupSet set = make_set(gs, n, [](const GroupDev& g) { return g.S * Gm::NB; });
     if (bf16)
-      k_pass1<N, true><<<g.S * Gm::NB, Gm::THREADS, Gm::SM1, s>>>(g, a);
+      k_pass1<N, true><<<set.boff[n], Gm::THREADS, Gm::SM1, s>>>(set, a);
     else
-      k_pass1<N, false><<<g.S * Gm::NB, Gm::THREADS, Gm::SM1, s>>>(g, a);
+      k_pass1<N, false><<<set.boff[n], Gm::THREADS, Gm::SM1, s>>>(set, a);
   }
   TMBIR_CHECK_LAUNCH();
   return TMBIR_OK;
 }
 template <int N>
-static int pass2_n(const GroupDev& g, const IterState* st, bool bf16, cudaStream_t s) {
+static int pass2_n(const GroupDev* gs, int n, const IterState* st, bool bf16, cudaStream_t s) {
   using Gm = Geo<N>;
   if (int e = set_smem_limits<N>()) return e;
   if constexpr (N == 2048) {
-    const int blocks = g.S * (N + 1);
+    const GroupSet set = make_set(gs, n, [](const GroupDev& g) { return g.S * (N + 1); });
     if (bf16)
-      k_pass2_q<true><<<blocks, 128, Q2048::SM2, s>>>(g, st);
+      k_pass2_q<true><<<set.boff[n], 128, Q2048::SM2, s>>>(set, st);
     else
-      k_pass2_q<false><<<blocks, 128, Q2048::SM2, s>>>(g, st);
+      k_pass2_q<false><<<set.boff[n], 128, Q2048::SM2, s>>>(set, st);
   } else if constexpr (is_block_fft_size<N>()) {
     using BG = BGeo<N>;
-    const int blocks = g.S * (N + 1);
+    const GroupSet set = make_set(gs, n, [](const GroupDev& g) { return g.S * (N + 1); });
     if (bf16)
-      k_pass2_b<N, true><<<blocks, BG::THREADS, BG::SM_COL, s>>>(g, st);
+      k_pass2_b<N, true><<<set.boff[n], BG::THREADS, BG::SM_COL, s>>>(set, st);
     else
-      k_pass2_b<N, false><<<blocks, BG::THREADS, BG::SM_COL, s>>>(g, st);
+      k_pass2_b<N, false><<<set.boff[n], BG::THREADS, BG::SM_COL, s>>>(set, st);
   } else {
-    const int blocks = (g.S * (N + 1) + Gm::CPB - 1) / Gm::CPB;
+    const GroupSet set =
+        make_set(gs, n, [](const GroupDev& g) { return (g.S * (N + 1) + Gm::CPB - 1) / Gm::CPB; });
     if (bf16)
-      k_pass2<N, true><<<blocks, Gm::THREADS, Gm::SM2, s>>>(g, st);
+      k_pass2<N, true><<<set.boff[n], Gm::THREADS, Gm::SM2, s>>>(set, st);
     else
-      k_pass2<N, false><<<blocks, Gm::THREADS, Gm::SM2, s>>>(g, st);
+      k_pass2<N, false><<<set.boff[n], Gm::THREADS, Gm::SM2, s>>>(set, st);
   }
   TMBIR_CHECK_LAUNCH();
   return TMBIR_OK;
 }
 template <int N, int MODE>
-static int pass3_nm(const GroupDev& g, const StepArgs& a, const PriorC& pc, const float* kz, int phase,
-                    double* partials, int off, cudaStream_t s) {
+static int pass3_nm(const GroupDev* gs, int n, const StepArgs& a, const PriorC& pc, const float* apply_out,
+                    int phase, double* partials, int off, cudaStream_t s) {
   using GP = GeoP<N>;
   static_assert(GP::NB * GP::CB == pass3_row_blocks(N), "pass-3b block count");
-  const int zc = pass3_zc(g, GP::NB * GP::CB);
-  const int blocks = GP::NB * GP::CB * ((pass3_slices(g) + zc - 1) / zc);
+  // each group's slices per block resolved (tuned value or the default rule)
+  GroupDev rz[kMergeMax];
+  for (int i = 0; i < n; ++i) {
+    rz[i] = gs[i];
+    rz[i].zc = pass3_zc(gs[i], GP::NB * GP::CB);
+  }
+  const GroupSet set =
+      make_set(rz, n, [](const GroupDev& g) { return GP::NB * GP::CB * ((pass3_slices(g) + g.zc - 1) / g.zc); });
   if (pc.q_is_2 || MODE == 0)
-    k_pass3<N, MODE, true><<<blocks, GP::THREADS, GP::SM, s>>>(g, a, pc, kz, phase, partials, off, zc);
+    k_pass3<N, MODE, true><<<set.boff[n], GP::THREADS, GP::SM, s>>>(set, a, pc, apply_out, phase, partials, off);
   else
-    k_pass3<N, MODE, false><<<blocks, GP::THREADS, GP::SM, s>>>(g, a, pc, kz, phase, partials, off, zc);
+    k_pass3<N, MODE, false><<<set.boff[n], GP::THREADS, GP::SM, s>>>(set, a, pc, apply_out, phase, partials, off);
   TMBIR_CHECK_LAUNCH();
   return TMBIR_OK;
 }
 // part: 1 pass 3a only, 2 pass 3b only, 3 both
 template <int N>
-static int pass3_n(const GroupDev& g, const StepArgs& a, Pass3Mode m, const PriorC& pc, double* partials, int off,
-                   bool bf16, int part, cudaStream_t s) {
+static int pass3_n(const GroupDev* gs, int n, const StepArgs& a, Pass3Mode m, const PriorC& pc, double* partials,
+                   int off, bool bf16, int part, cudaStream_t s) {
   using Gm = Geo3a<N>;
   if (int e = set_smem_limits<N>()) return e;
+  if (n < 1 || n > kMergeMax) return set_error(TMBIR_ERR_ARG, "group set size");
   if (bf16 && m != Pass3Mode::Iterate) return set_error(TMBIR_ERR_ARG, "BF16 spectra are an iteration option only");
   // Apply writes K (*) x straight into the output; every other mode into the group's buffer
-  float* kz = m == Pass3Mode::Apply ? a.out + g.img_off : g.kz;
+  float* apply_out = m == Pass3Mode::Apply ? a.out : nullptr;
   const IterState* st = m == Pass3Mode::Iterate ? a.st : nullptr;
   if (part & 1) {
     if constexpr (N == 2048) {
       using Q = Q2048;
-      if ((g.rb3 ? g.rb3 : Q::RB3) == 8) {
+      if ((gs[0].rb3 ? gs[0].rb3 : Q::RB3) == 8) {
+        const GroupSet set = make_set(gs, n, [](const GroupDev& g) { return g.S * (N / 8); });
         if (bf16)
-          k_pass3a_q<true, 8><<<g.S * (N / 8), 512, Q::sm_rows<8>(), s>>>(g, st, kz);
+          k_pass3a_q<true, 8><<<set.boff[n], 512, Q::sm_rows<8>(), s>>>(set, st, apply_out);
         else
-          k_pass3a_q<false, 8><<<g.S * (N / 8), 512, Q::sm_rows<8>(), s>>>(g, st, kz);
+          k_pass3a_q<false, 8><<<set.boff[n], 512, Q::sm_rows<8>(), s>>>(set, st, apply_out);
       } else {
+        const GroupSet set = make_set(gs, n, [](const GroupDev& g) { return g.S * (N / 4); });
         if (bf16)
-          k_pass3a_q<true, 4><<<g.S * (N / 4), 256, Q::sm_rows<4>(), s>>>(g, st, kz);
+          k_pass3a_q<true, 4><<<set.boff[n], 256, Q::sm_rows<4>(), s>>>(set, st, apply_out);
         else
-          k_pass3a_q<false, 4><<<g.S * (N / 4), 256, Q::sm_rows<4>(), s>>>(g, st, kz);
+          k_pass3a_q<false, 4><<<set.boff[n], 256, Q::sm_rows<4>(), s>>>(set, st, apply_out);
       }
     } else if constexpr (is_block_fft_size<N>()) {
       using BG = BGeo<N>;
+      const GroupSet set = make_set(gs, n, [](const GroupDev& g) { return g.S * BG::NB; });
       if (bf16)
-        k_pass3a_b<N, true><<<g.S * BG::NB, BG::THREADS, BG::SM_ROWS, s>>>(g, st, kz);
+        k_pass3a_b<N, true><<<set.boff[n], BG::THREADS, BG::SM_ROWS, s>>>(set, st, apply_out);
       else
-        k_pass3a_b<N, false><<<g.S * BG::NB, BG::THREADS, BG::SM_ROWS, s>>>(g, st, kz);
+        k_pass3a_b<N, false><<<set.boff[n], BG::THREADS, BG::SM_ROWS, s>>>(set, st, apply_out);
     } else {
+      const GroupSet set = make_set(gs, n, [](const GroupDev& g) { return g.S * Gm::NB; });
       if (bf16)
-        k_pass3a<N, true><<<g.S * Gm::NB, Gm::THREADS, Gm::SM1, s>>>(g, st, kz);
+        k_pass3a<N, true><<<set.boff[n], Gm::THREADS, Gm::SM1, s>>>(set, st, apply_out);
       else
-        k_pass3a<N, false><<<g.S * Gm::NB, Gm::THREADS, Gm::SM1, s>>>(g, st, kz);
+        k_pass3a<N, false><<<set.boff[n], Gm::THREADS, Gm::SM1, s>>>(set, st, apply_out);
     }
     TMBIR_CHECK_LAUNCH();
   }
   if (!(part & 2)) return TMBIR_OK;
   const int phase = bf16 ? 1 : 0;
   switch (m) {
-    case Pass3Mode::Apply: return pass3_nm<N, 0>(g, a, pc, kz, phase, partials, off, s);
-    case Pass3Mode::Gradient: return pass3_nm<N, 1>(g, a, pc, kz, phase, partials, off, s);
-    case Pass3Mode::Step: return pass3_nm<N, 2>(g, a, pc, kz, phase, partials, off, s);
-    case Pass3Mode::Iterate: return pass3_nm<N, 3>(g, a, pc, kz, phase, partials, off, s);
-    default: return pass3_nm<N, 4>(g, a, pc, kz, phase, partials, off, s);
+    case Pass3Mode::Apply: return pass3_nm<N, 0>(gs, n, a, pc, apply_out, phase, partials, off, s);
+    case Pass3Mode::Gradient: return pass3_nm<N, 1>(gs, n, a, pc, apply_out, phase, partials, off, s);
+    case Pass3Mode::Step: return pass3_nm<N, 2>(gs, n, a, pc, apply_out, phase, partials, off, s);
+    case Pass3Mode::Iterate: return pass3_nm<N, 3>(gs, n, a, pc, apply_out, phase, partials, off, s);
+    default: return pass3_nm<N, 4>(gs, n, a, pc, apply_out, phase, partials, off, s);
   }
 }
 

@@ -461,6 +461,47 @@ def test_uneven_groups_reconstruct_like_separate_contexts(orc):
         off += n
 
 
+def test_groups_of_one_side_share_launches(orc):
+    """Consecutive groups of one image side (different angle counts and slice counts) run each
+    pass as one launch over all their blocks: 25 iterations give, group by group, bitwise the
+    iterates of a context holding that group alone, and an iteration launches one kernel per
+    pass per run of such groups (runs: three groups of 64^2, two of 128^2, one of 64^2)."""
+    specs = [(64, 2, 30), (64, 1, 20), (64, 3, 45), (128, 1, 50), (128, 2, 37), (64, 1, 24)]
+    iters = 25
+    groups, sinos = [], []
+    for k, (N, S, na) in enumerate(specs):
+        p = synth.volume(S=S, N=N, n_angles=na, n_ellipsoids=4, seed=60 + k)
+        groups.append(tm.Group(N=N, angles=list(p.theta), n_slices=S))
+        sinos.append(p.sino.ravel())
+    big = tm.Context(groups)
+    atg = big.build_operator(dev(np.concatenate(sinos)))
+    xg = torch.zeros(atg.numel(), dtype=torch.float32, device="cuda")
+    xe = torch.zeros_like(xg)
+    big.reconstruct(xg, atg, tm.Params(**PRIOR, max_iter=iters, use_graph=True))
+    n0 = big.launch_count()
+    big.reconstruct(xe, atg, tm.Params(**PRIOR, max_iter=iters, use_graph=False))
+    n1 = big.launch_count()
+    big.reconstruct(xe.zero_(), atg, tm.Params(**PRIOR, max_iter=iters + 5, use_graph=False))
+    n2 = big.launch_count()
+    torch.cuda.synchronize()
+    assert (n2 - n1) - (n1 - n0) == 5 * (4 + 4 + 4 + 1)  # three runs of four passes, and the finalize
+    xe.zero_()
+    big.reconstruct(xe, atg, tm.Params(**PRIOR, max_iter=iters, use_graph=False))
+    torch.cuda.synchronize()
+    assert torch.equal(xg, xe)
+    off = 0
+    for k, (N, S, na) in enumerate(specs):
+        n = S * N * N
+        ctx = tm.Context([groups[k]])
+        a1 = ctx.build_operator(dev(sinos[k]))
+        assert torch.equal(atg[off:off + n], a1), (k, "R*g")
+        x1 = torch.zeros(n, dtype=torch.float32, device="cuda")
+        ctx.reconstruct(x1, a1, tm.Params(**PRIOR, max_iter=iters))
+        torch.cuda.synchronize()
+        assert torch.equal(xg[off:off + n], x1), k
+        off += n
+
+
 def test_identical_groups_give_identical_results():
     p = synth.volume(S=2, N=64, n_angles=24, n_ellipsoids=4, seed=50)
     grp = tm.Group(N=64, angles=list(p.theta), n_slices=2)
