@@ -662,6 +662,9 @@ def run_ours(args, tm, w, prob, stream, rank, world, local, barrier, extra):
         coarse, extra["coarse_iteration_tuning"] = tune_coarse(H, sino, F_ref, stream, barrier, world)
         progress(f"coarse iterations {coarse}: {extra['coarse_iteration_tuning']}")
         prms = chosen_params(F_ref, coarse)
+        if args.no_graph:  # profiling: every iteration's kernels launched one by one
+            for prm in prms:
+                prm.use_graph = False
         state = {}
 
         def step():

@@ -126,8 +126,14 @@ struct GroupSet {
   int boff[kMergeMax + 1];
   GroupDev g[kMergeMax];
 #ifdef __CUDACC__
-  // the group of this block, and the block's index within that group
+  // the group of this block, and the block's index within that group (MULTI false: a set of one
+  // group, whose fields the kernel then reads at fixed parameter offsets)
+  template <bool MULTI = true>
   __device__ __forceinline__ int pick(int& bid) const {
+    if constexpr (!MULTI) {
+      bid = (int)blockIdx.x;
+      return 0;
+    }
     int i = 0;
     while (i + 1 < n && (int)blockIdx.x >= boff[i + 1]) ++i;
     bid = (int)blockIdx.x - boff[i];

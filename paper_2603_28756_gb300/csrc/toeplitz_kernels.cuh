@@ -1183,7 +1183,7 @@ __device__ __forceinline__ void band_step(const float* S0, const float* S1, bool
 
 // kz: K (*) y of the group from pass 3a ([slice][row][col]); phase: in Iterate mode, the storage
 // phase this launch belongs to (0 FP32, 1 BF16), checked like the other passes.
-template <int N, int MODE, bool Q2>
+template <int N, int MODE, bool Q2, bool MULTI>
 __global__ void __launch_bounds__(GeoP<N>::THREADS, 2)
     k_pass3(const __grid_constant__ GroupSet gs, StepArgs a, PriorC pc, const float* apply_out, int phase,
             double* partials, int block_offset) {
@@ -1196,8 +1196,8 @@ __global__ void __launch_bounds__(GeoP<N>::THREADS, 2)
   extern __shared__ float2 sm[];
   __shared__ double red[GP::WPB * kParts];
   int bid_;
-  const int gi_ = gs.pick(bid_);
-  const GroupDev& g = gs.g[gi_];
+  const int gi_ = gs.template pick<MULTI>(bid_);
+  const GroupDev& g = gs.g[MULTI ? gi_ : 0];
   const float* __restrict__ kz = apply_out ? apply_out + g.img_off : g.kz;
   const int zc = g.zc;  // resolved by the launcher
   const float *x, *xp;
@@ -1401,11 +1401,15 @@ static int set_smem_limits() {
     TMBIR_CUDA(cudaFuncSetAttribute(k_pass3a<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Gr::SM1));
   }
 #define TMBIR_P3ATTR(M, Q)                                                                           \
-  TMBIR_CUDA(cudaFuncSetAttribute(k_pass3<N, M, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+  TMBIR_CUDA(cudaFuncSetAttribute(k_pass3<N, M, Q, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                   (int)GeoP<N>::SM));
   TMBIR_P3ATTR(0, true) TMBIR_P3ATTR(1, true) TMBIR_P3ATTR(2, true) TMBIR_P3ATTR(3, true) TMBIR_P3ATTR(4, true)
   TMBIR_P3ATTR(0, false) TMBIR_P3ATTR(1, false) TMBIR_P3ATTR(2, false) TMBIR_P3ATTR(3, false) TMBIR_P3ATTR(4, false)
 #undef TMBIR_P3ATTR
+  TMBIR_CUDA(cudaFuncSetAttribute(k_pass3<N, 3, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)GeoP<N>::SM));
+  TMBIR_CUDA(cudaFuncSetAttribute(k_pass3<N, 3, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)GeoP<N>::SM));
   done = true;
   return TMBIR_OK;
 }
@@ -1500,10 +1504,24 @@ static int pass3_nm(const GroupDev* gs, int n, const StepArgs& a, const PriorC& 
   }
   const GroupSet set =
       make_set(rz, n, [](const GroupDev& g) { return GP::NB * GP::CB * ((pass3_slices(g) + g.zc - 1) / g.zc); });
+  // a set of several groups only in Iterate mode (the other modes run one group per launch)
+  if constexpr (MODE == 3) {
+    if (n > 1) {
+      if (pc.q_is_2)
+        k_pass3<N, 3, true, true><<<set.boff[n], GP::THREADS, GP::SM, s>>>(set, a, pc, apply_out, phase, partials, off);
+      else
+        k_pass3<N, 3, false, true><<<set.boff[n], GP::THREADS, GP::SM, s>>>(set, a, pc, apply_out, phase, partials,
+                                                                           off);
+      TMBIR_CHECK_LAUNCH();
+      return TMBIR_OK;
+    }
+  }
+  if (n != 1) return set_error(TMBIR_ERR_ARG, "pass 3b takes several groups in Iterate mode only");
   if (pc.q_is_2 || MODE == 0)
-    k_pass3<N, MODE, true><<<set.boff[n], GP::THREADS, GP::SM, s>>>(set, a, pc, apply_out, phase, partials, off);
+    k_pass3<N, MODE, true, false><<<set.boff[n], GP::THREADS, GP::SM, s>>>(set, a, pc, apply_out, phase, partials, off);
   else
-    k_pass3<N, MODE, false><<<set.boff[n], GP::THREADS, GP::SM, s>>>(set, a, pc, apply_out, phase, partials, off);
+    k_pass3<N, MODE, false, false><<<set.boff[n], GP::THREADS, GP::SM, s>>>(set, a, pc, apply_out, phase, partials,
+                                                                            off);
   TMBIR_CHECK_LAUNCH();
   return TMBIR_OK;
 }
