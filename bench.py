@@ -1166,6 +1166,12 @@ def run_streamed(args, tm, w, prob, stream, rank, world, local, barrier, extra):
     h_x.copy_(state["x0"])
     ms_it, _ = timed(stream, barrier, world, lambda: ctx.stream_reconstruct(h_x, state["atg"], state["gtg"], prm))
     x_streamed = h_x.clone()
+    # the same with R*g kept in device memory (only the iterates stream)
+    d_atg = state["atg"].cuda()
+    h_x.copy_(state["x0"])
+    ms_it_dev, _ = timed(stream, barrier, world, lambda: ctx.stream_reconstruct(h_x, d_atg, state["gtg"], prm))
+    same_dev = bool(torch.equal(h_x, x_streamed))
+    del d_atg
     res = tm.Context([tm.Group(N=N, angles=list(prob.theta), n_slices=S, span=span)], stream=stream)
     atg = res.build_operator(h_sino.cuda())
     atg_same = bool(torch.equal(atg.cpu(), state["atg"]))
@@ -1180,7 +1186,8 @@ def run_streamed(args, tm, w, prob, stream, rank, world, local, barrier, extra):
     plane = N * N * 4
     h2d_it = (2 * (S + 2 * (nslab - 1)) + S) * plane  # x_k and x_{k-1} with the halo slices, R*g
     d2h_it = S * plane
-    progress(f"streamed step {ms / args.steps:.1f} ms; iterations streamed {ms_it / iters:.1f} ms, resident "
+    progress(f"streamed step {ms / args.steps:.1f} ms; iterations streamed {ms_it / iters:.1f} ms (R*g on the "
+             f"device {ms_it_dev / iters:.1f} ms), resident "
              f"{ms_res / iters:.1f} ms per iteration; max |difference| / max |x| = {diff:.2e}")
     if rank == 0:
         cfg = config_of(args.workload)
@@ -1197,6 +1204,8 @@ def run_streamed(args, tm, w, prob, stream, rank, world, local, barrier, extra):
             "streaming": {
                 "slab": slab, "slabs": nslab,
                 "streamed_ms_per_iteration": ms_it / iters, "resident_ms_per_iteration": ms_res / iters,
+                "streamed_atg_on_device_ms_per_iteration": ms_it_dev / iters,
+                "atg_on_device_iterates_equal": same_dev,
                 "overhead": ms_it / ms_res,
                 "host_copies_per_iteration_bytes": {"h2d": h2d_it, "d2h": d2h_it},
                 "copy_GBps_per_iteration": (h2d_it + d2h_it) / (ms_it / iters) / 1e6,

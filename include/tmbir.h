@@ -431,13 +431,14 @@ int tmbir_stream_build_operator(tmbir_ctx* ctx, int n_slices, const float* h_sin
  * tmbir_reconstruct on a host volume: prm->max_iter iterations (fewer when the gap rule stops
  * the run), the step constant from this geometry's lambda_max unless prm->L is given.
  *   h_x       [n_slices][N][N] FP32, host: x_0 in, the final iterate out.
- *   h_atg     R*g of the volume (tmbir_stream_build_operator); gtg_half its 1/2 g.g.
+ *   atg       R*g of the volume (tmbir_stream_build_operator) in host memory, or in device memory
+ *             (16-byte aligned; read in place, so only the iterates stream); gtg_half its 1/2 g.g.
  *   h_work    2 n_slices N^2 floats of host scratch: with h_x, the three slots x_{k-1}, x_k and
  *             x_{k+1} rotate through.  After a number of iterations that is a multiple of 3 the
  *             final iterate is already in h_x; otherwise it is copied back into h_x through the
  *             device, slab by slab (one more pass of copies in and out).
  * Per iteration each slab copies in x_k and x_{k-1} (with one halo slice on each side) and its
- * R*g, runs passes 1-3b on its own slices, and copies out x_{k+1}; the finalize kernel then
+ * R*g (when on the host), runs passes 1-3b on its own slices, and copies out x_{k+1}; the finalize kernel then
  * reduces the partial sums of all slabs in the order of the resident volume's pass-3b blocks, and
  * the host reads the stop flag.  The slices per pass-3b block are the slab's (tuned or default)
  * value lowered to a divisor of the slab; when the resident volume uses the same value, every
@@ -445,7 +446,7 @@ int tmbir_stream_build_operator(tmbir_ctx* ctx, int n_slices, const float* h_sin
  * use_graph is ignored and resume is refused (TMBIR_ERR_ARG); the iteration log (tmbir_get_log)
  * is kept; the state cannot be exported afterwards.
  */
-int tmbir_stream_reconstruct(tmbir_ctx* ctx, int n_slices, float* h_x, const float* h_atg, double gtg_half,
+int tmbir_stream_reconstruct(tmbir_ctx* ctx, int n_slices, float* h_x, const float* atg, double gtg_half,
                              float* h_work, void* d_swork, size_t swork_bytes, const tmbir_params* prm,
                              tmbir_stats* h_stats);
 

@@ -364,15 +364,18 @@ class Context:
                                                 ctypes.c_void_p(ws), nb, ctypes.byref(gtg)))
         return h_atg, gtg.value, h_x0
 
-    def stream_reconstruct(self, h_x, h_atg, gtg_half: float, params: Params):
-        """tmbir_reconstruct on a host volume: h_x (x_0 in, the final iterate out) and h_atg are
-        contiguous float32 CPU tensors of n_slices N^2 values."""
+    def stream_reconstruct(self, h_x, atg, gtg_half: float, params: Params):
+        """tmbir_reconstruct on a host volume: h_x (x_0 in, the final iterate out) is a contiguous
+        float32 CPU tensor of n_slices N^2 values; atg (R*g) the same on the CPU, or a CUDA tensor
+        (read in place: only the iterates stream)."""
         import torch
 
         g = self.groups[0]
-        for t in (h_x, h_atg):
-            if t.is_cuda or not t.is_contiguous() or t.dtype != torch.float32:
-                raise TypeError("expected contiguous float32 CPU tensors")
+        if h_x.is_cuda or not h_x.is_contiguous() or h_x.dtype != torch.float32:
+            raise TypeError("expected a contiguous float32 CPU tensor for the image")
+        if not atg.is_contiguous() or atg.dtype != torch.float32:
+            raise TypeError("expected a contiguous float32 tensor for R*g")
+        h_atg = atg
         if h_x.numel() != h_atg.numel() or h_x.numel() % (g.N * g.N):
             raise ValueError("image sizes do not match")
         n_slices = h_x.numel() // (g.N * g.N)

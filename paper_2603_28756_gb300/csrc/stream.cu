@@ -154,6 +154,8 @@ int build_slab(tmbir_ctx* ctx, const Plan& p, char* ws, int j, int s, float* h_a
   return TMBIR_OK;
 }
 
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
 int sino_in(Ctx& c, const Plan& p, char* ws, int j, const float* h_sino) {
   const tmbir_group& g = c.groups[0];
   const int s = j & 1, a = j * p.slab, n = std::min(p.slab, p.n - a);
@@ -179,8 +181,10 @@ SlabGeo slab_geo(const Plan& p, int j) {
   return q;
 }
 
-// copies in of slab j: x_k and x_{k-1} with the halo, and R*g of the slab's own slices
-int iter_in(Ctx& c, const Plan& p, char* ws, int j, const float* xk, const float* xkm1, const float* h_atg) {
+// copies in of slab j: x_k and x_{k-1} with the halo, and R*g of the slab's own slices (unless R*g
+// is in device memory)
+int iter_in(Ctx& c, const Plan& p, char* ws, int j, const float* xk, const float* xkm1, const float* h_atg,
+            bool atg_dev) {
   const int s = j & 1;
   const SlabGeo q = slab_geo(p, j);
   const size_t N2 = (size_t)p.N * p.N;
@@ -188,15 +192,17 @@ int iter_in(Ctx& c, const Plan& p, char* ws, int j, const float* xk, const float
   TMBIR_CUDA(cudaStreamWaitEvent(c.s_in, c.ev_comp[s], 0));  // slab j - 2's kernels are done with set s
   TMBIR_CUDA(cudaMemcpyAsync(ws + p.off_x[s], xk + first, cnt * sizeof(float), cudaMemcpyHostToDevice, c.s_in));
   TMBIR_CUDA(cudaMemcpyAsync(ws + p.off_xp[s], xkm1 + first, cnt * sizeof(float), cudaMemcpyHostToDevice, c.s_in));
-  TMBIR_CUDA(cudaMemcpyAsync(reinterpret_cast<float*>(ws + p.off_atg[s]) + (size_t)q.lo * N2, h_atg + (size_t)q.a * N2,
-                             (size_t)q.n * N2 * sizeof(float), cudaMemcpyHostToDevice, c.s_in));
+  if (!atg_dev)
+    TMBIR_CUDA(cudaMemcpyAsync(reinterpret_cast<float*>(ws + p.off_atg[s]) + (size_t)q.lo * N2,
+                               h_atg + (size_t)q.a * N2, (size_t)q.n * N2 * sizeof(float), cudaMemcpyHostToDevice,
+                               c.s_in));
   TMBIR_CUDA(cudaEventRecord(c.ev_in[s], c.s_in));
   return TMBIR_OK;
 }
 
 // the kernels of slab j in Iterate mode, both storage variants of `kind` (each checks the run's
 // phase on the device, as in tmbir_reconstruct)
-int iter_compute(Ctx& c, const Plan& p, char* ws, int j, int cur, const PriorC& pc, int kind) {
+int iter_compute(Ctx& c, const Plan& p, char* ws, int j, int cur, const PriorC& pc, int kind, const float* d_atg) {
   const int s = j & 1;
   const SlabGeo q = slab_geo(p, j);
   TMBIR_CUDA(cudaStreamWaitEvent(c.stream, c.ev_in[s], 0));
@@ -210,7 +216,8 @@ int iter_compute(Ctx& c, const Plan& p, char* ws, int j, int cur, const PriorC& 
   v.img_off = 0;
   v.kz = reinterpret_cast<float*>(ws + p.off_kz);
   StepArgs a{};
-  a.atg = reinterpret_cast<const float*>(ws + p.off_atg[s]);
+  // R*g at the slab's buffer index z: the set's copy, or the device volume from slice a - lo
+  a.atg = d_atg ? d_atg + (size_t)(q.a - q.lo) * p.N * p.N : reinterpret_cast<const float*>(ws + p.off_atg[s]);
   a.xb[cur] = reinterpret_cast<float*>(ws + p.off_x[s]);
   a.xb[(cur + 2) % 3] = reinterpret_cast<float*>(ws + p.off_xp[s]);
   a.xb[(cur + 1) % 3] = reinterpret_cast<float*>(ws + p.off_out[s]);
@@ -304,7 +311,7 @@ int tmbir_stream_build_operator(tmbir_ctx* ctx, int n_slices, const float* h_sin
   return TMBIR_OK;
 }
 
-int tmbir_stream_reconstruct(tmbir_ctx* ctx, int n_slices, float* h_x, const float* h_atg, double gtg_half,
+int tmbir_stream_reconstruct(tmbir_ctx* ctx, int n_slices, float* h_x, const float* atg, double gtg_half,
                              float* h_work, void* d_swork, size_t swork_bytes, const tmbir_params* prm,
                              tmbir_stats* h_stats) {
   TMBIR_TRACE("tmbir_stream_reconstruct");
@@ -312,13 +319,18 @@ int tmbir_stream_reconstruct(tmbir_ctx* ctx, int n_slices, float* h_x, const flo
   if (int e = check_params(prm)) return e;
   SREQ(!prm->resume, TMBIR_ERR_ARG, "stream_reconstruct: resume is not supported for host volumes");
   SREQ(prm->max_iter >= 0 && prm->max_iter <= kLogCap, TMBIR_ERR_ARG, "stream_reconstruct: max_iter out of range");
-  SREQ(h_x && h_atg && h_work, TMBIR_ERR_ARG, "stream_reconstruct: NULL host buffer");
+  SREQ(h_x && atg && h_work, TMBIR_ERR_ARG, "stream_reconstruct: NULL buffer");
   SREQ(std::isfinite(gtg_half) && gtg_half >= 0.0, TMBIR_ERR_ARG, "stream_reconstruct: gtg_half must be >= 0");
   Ctx& c = ctx->c;
   const int zc = run_zc(c);
   Plan p;
   if (int e = check_common(ctx, n_slices, d_swork, swork_bytes, &p, zc)) return e;
   char* ws = static_cast<char*>(d_swork);
+  // R*g in device memory stays there; only the iterates stream
+  cudaPointerAttributes pa{};
+  TMBIR_CUDA(cudaPointerGetAttributes(&pa, atg));
+  const bool atg_dev = pa.type == cudaMemoryTypeDevice;
+  SREQ(!atg_dev || aligned16(atg), TMBIR_ERR_ARG, "stream_reconstruct: device R*g must be 16-byte aligned");
   const PriorC pc = make_prior(*prm);
   const bool bf16 = prm->spectra == TMBIR_SPECTRA_BF16;
   const int kind = !bf16 ? 1 : (prm->refine_gap > 0.0 ? 3 : 2);
@@ -337,10 +349,10 @@ int tmbir_stream_reconstruct(tmbir_ctx* ctx, int n_slices, float* h_x, const flo
     const float* xkm1 = k == 0 ? slot[cur] : slot[(cur + 2) % 3];  // x_{-1} = x_0
     float* xnext = slot[(cur + 1) % 3];
     rc = fork_copies(c);
-    if (!rc) rc = iter_in(c, p, ws, 0, xk, xkm1, h_atg);
+    if (!rc) rc = iter_in(c, p, ws, 0, xk, xkm1, atg, atg_dev);
     for (int j = 0; j < p.nslab && !rc; ++j) {
-      if (j + 1 < p.nslab) rc = iter_in(c, p, ws, j + 1, xk, xkm1, h_atg);
-      if (!rc) rc = iter_compute(c, p, ws, j, cur, pc, kind);
+      if (j + 1 < p.nslab) rc = iter_in(c, p, ws, j + 1, xk, xkm1, atg, atg_dev);
+      if (!rc) rc = iter_compute(c, p, ws, j, cur, pc, kind, atg_dev ? atg : nullptr);
       if (!rc) rc = iter_out(c, p, ws, j, xnext);
     }
     if (!rc) rc = launch_finalize(c.state, c.gmom, reinterpret_cast<double*>(ws + p.off_part), gb, c.log, s);

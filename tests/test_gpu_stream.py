@@ -65,10 +65,11 @@ def test_streamed_setup_equals_resident(vol):
     assert abs(vol.gtg - gtg) <= 1e-12 * gtg
 
 
-@pytest.mark.parametrize("mode", ["fp32", "bf16_refined"])
+@pytest.mark.parametrize("mode", ["fp32", "bf16_refined", "fp32_device_atg"])
 def test_streamed_iterates_equal_resident(vol, mode):
     """Every iterate, the stats and the log of a streamed run equal the resident run's (the
-    resident and the slab contexts both take one slice per pass-3b block at these sizes)."""
+    resident and the slab contexts both take one slice per pass-3b block at these sizes); R*g
+    may stay in device memory while the iterates stream."""
     kw = dict(PRIOR, max_iter=12)
     if mode == "bf16_refined":
         # refinement needs a reference objective: a longer FP32 run of the resident volume
@@ -79,7 +80,8 @@ def test_streamed_iterates_equal_resident(vol, mode):
     st = vol.res.reconstruct(x, vol.d_atg, tm.Params(**kw))
     log = vol.res.get_log()
     hx = vol.h_x0.clone()
-    sst = vol.slabctx.stream_reconstruct(hx, vol.h_atg, vol.gtg, tm.Params(**kw))
+    atg = vol.d_atg if mode == "fp32_device_atg" else vol.h_atg
+    sst = vol.slabctx.stream_reconstruct(hx, atg, vol.gtg, tm.Params(**kw))
     slog = vol.slabctx.get_log()
     torch.cuda.synchronize()
     assert torch.equal(hx, x.cpu())
