@@ -320,8 +320,9 @@ class Hier:
                                 stream=torch.cuda.Stream()) for k in range(LEVELS)]
         self.net = None
 
-    def run(self, sino, prms, start_cnn=True):
-        """The hierarchy through the C ABI: per level, stats of the level's reconstruct."""
+    def run(self, sino, prms, start_cnn=True, coarse_fp32=False):
+        """The hierarchy through the C ABI: per level, stats of the level's reconstruct
+        (coarse_fp32: the coarse levels build R*g in FP32)."""
         tm = self.tm
 
         def start(c, s_l, a_l):
@@ -334,7 +335,8 @@ class Hier:
 
         self.used_cnn = False
         y, _, stats = tm.reconstruct_levels(self.w["N"], self.theta, self.w["S"], sino, LEVELS, prms,
-                                            span=self.w["span"], ctxs=self.ctxs, start=start, overlap_setup=True)
+                                            span=self.w["span"], ctxs=self.ctxs, start=start, overlap_setup=True,
+                                            coarse_setup_fp32=coarse_fp32)
         self.x = y
         return stats
 
@@ -350,8 +352,8 @@ def tune_coarse(H, sino, F_ref, stream, barrier, world):
     trials = {}
     for cand in COARSE_CANDIDATES:
         prms = chosen_params(F_ref, cand)
-        H.run(sino, prms)
-        ms, stats = timed(stream, barrier, world, lambda: H.run(sino, prms))
+        H.run(sino, prms, coarse_fp32=True)
+        ms, stats = timed(stream, barrier, world, lambda: H.run(sino, prms, coarse_fp32=True))
         trials[str(list(cand))] = {"ms": ms, "level_iterations": [st.iterations for st in stats],
                                    "reached": stats[-1].gap <= GAP}
     ok = [c for c in COARSE_CANDIDATES if trials[str(list(c))]["reached"]] or COARSE_CANDIDATES
@@ -440,7 +442,8 @@ def time_to_gap_hier(tm, H, sino, F_ref, F0, stream, barrier, world, step_ms, st
     forms["chosen"] = {"ms": step_ms, "finest_iterations": step_stats[-1].iterations,
                        "level_iterations": [s.iterations for s in step_stats], "gap_reached": step_stats[-1].gap,
                        "reached": step_stats[-1].gap <= GAP, "used_cnn": H.used_cnn,
-                       "form": "the bench step: levels N/4, N/2, N, CNN-refined FBP start at N/4 (FBP fallback), "
+                       "form": "the bench step: levels N/4, N/2, N (R*g in FP32 at the coarse levels, FP64 at N), "
+                               "CNN-refined FBP start at N/4 (FBP fallback), "
                                f"BF16 spectra with FP32 refinement from gap {REFINE_GAP:g}, device-driven graph loops"}
     forms["single_slice"] = single_slice_form(tm, w, H.theta, sino, stream, barrier, world)
     return forms
@@ -668,7 +671,7 @@ def run_ours(args, tm, w, prob, stream, rank, world, local, barrier, extra):
         state = {}
 
         def step():
-            state["stats"] = H.run(sino, prms)
+            state["stats"] = H.run(sino, prms, coarse_fp32=True)
 
         def units():
             return H.voxel_updates(state["stats"])
@@ -770,7 +773,7 @@ def run_ours(args, tm, w, prob, stream, rank, world, local, barrier, extra):
         with torch.cuda.stream(stream):
             d_sino.copy_(h_sino, non_blocking=True)
         if w["kind"] == "hier":
-            state["stats"] = H.run(d_sino, prms)
+            state["stats"] = H.run(d_sino, prms, coarse_fp32=True)
             e2e_units.append(units())
             out = H.x
         else:
@@ -806,8 +809,8 @@ def run_ours(args, tm, w, prob, stream, rank, world, local, barrier, extra):
         cfg = config_of(args.workload)
         cfg.update({"parallelism": f"replicas{world}", "l2": "working set > L2 (no explicit flush)"})
         if w["kind"] == "hier":
-            cfg.update({"step": "chosen form to the 1e-3 gap: 3 levels, CNN start with FBP fallback, BF16 spectra "
-                                "with FP32 refinement, device-driven graph loops",
+            cfg.update({"step": "chosen form to the 1e-3 gap: 3 levels (coarse R*g in FP32), CNN start with FBP "
+                                "fallback, BF16 spectra with FP32 refinement, device-driven graph loops",
                         "coarse_iterations": [s.iterations for s in state["stats"][:-1]],
                         "refine_gap": REFINE_GAP,
                         "level_iterations": [s.iterations for s in state["stats"]]})
@@ -1278,7 +1281,7 @@ def stage_breakdown(tm, H, sino, prms, stream, barrier):
         c = H.ctxs[lev]
         lv = c._lv
         s_l = sino if f == 1 else c.downsample_sino(sino, S, na, N, f, out=lv["sino"])
-        c.build_operator(s_l, lv["atg"])
+        c.build_operator(s_l, lv["atg"], fp64=lev == LEVELS - 1)  # as the chosen form
         mark(f"L{lev} setup")
         if x is None:
             f0 = c.fbp(s_l)

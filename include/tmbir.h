@@ -167,6 +167,16 @@ int tmbir_set_workspace(tmbir_ctx* ctx, void* d_workspace, size_t bytes);
 int tmbir_build_operator(tmbir_ctx* ctx, const float* d_sino, float* d_atg);
 
 /*
+ * tmbir_build_operator with R*g computed in FP32: the back-projection of the FBP start without
+ * its ramp filter (2N spreading grid, width-10 kernel, FP32 arithmetic: the error of an FP32
+ * transform, against 1e-10 for the FP64 one before the FP32 store), at a fraction of the FP64
+ * transform's cost on a GPU whose FP64 rate is far below its FP32 rate.  K, its spectrum, lambda_max and 1/2 g.g are
+ * built as in tmbir_build_operator.  Meant for the coarse levels of the hierarchy (Sec. 2.3),
+ * whose result only starts the next level; the finest level keeps the FP64 R*g.
+ */
+int tmbir_build_operator_fp32(tmbir_ctx* ctx, const float* d_sino, float* d_atg);
+
+/*
  * Filtered back-projection start of Sec. 2.2 (Eqs. 12-14): every projection row is
  * convolved with the unit-pitch Ram-Lak kernel (zero padded, no wrap-around), back-projected
  * with R* and weighted by span / n_angles.  d_x0 receives [slice][row][col].

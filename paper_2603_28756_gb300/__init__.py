@@ -87,6 +87,7 @@ SYMBOLS = [
     "tmbir_state_size", "tmbir_state_export", "tmbir_state_import", "tmbir_autotune", "tmbir_build_operator_fbp",
     "tmbir_wait_check", "tmbir_forward", "tmbir_adjoint", "tmbir_gradient_direct", "tmbir_sfu_rate",
     "tmbir_stream_workspace_size", "tmbir_stream_build_operator", "tmbir_stream_reconstruct",
+    "tmbir_build_operator_fp32",
 ]
 
 _lib = None
@@ -110,6 +111,7 @@ def load(path: str | None = None):
         "tmbir_workspace_size": [vp, ctypes.POINTER(sz)],
         "tmbir_set_workspace": [vp, vp, sz],
         "tmbir_build_operator": [vp, vp, vp],
+        "tmbir_build_operator_fp32": [vp, vp, vp],
         "tmbir_fbp": [vp, vp, vp],
         "tmbir_reconstruct": [vp, vp, vp, ctypes.POINTER(_Params), ctypes.POINTER(_Stats)],
         "tmbir_get_log": [vp, dp, i, ctypes.POINTER(i)],
@@ -293,10 +295,12 @@ class Context:
                     t.record_stream(self.stream)
 
     # calls --------------------------------------------------------------------
-    def build_operator(self, sino, atg=None):
+    def build_operator(self, sino, atg=None, fp64: bool = True):
+        """K, its spectrum, lambda_max, 1/2 g.g and R*g (FP64, or FP32 with fp64=False)."""
         atg = self._empty(self.image_numel()) if atg is None else atg
         self._pre()
-        _check(_lib.tmbir_build_operator(self._h, ctypes.c_void_p(_ptr(sino)), ctypes.c_void_p(_ptr(atg))))
+        fn = _lib.tmbir_build_operator if fp64 else _lib.tmbir_build_operator_fp32
+        _check(fn(self._h, ctypes.c_void_p(_ptr(sino)), ctypes.c_void_p(_ptr(atg))))
         self._post(sino, atg)
         return atg
 
@@ -579,7 +583,8 @@ class Context:
 
 
 def reconstruct_levels(N: int, angles, n_slices: int, sino, levels: int, params, span: float = math.pi,
-                       stream=None, device="cuda", start=None, ctxs=None, overlap_setup: bool = False):
+                       stream=None, device="cuda", start=None, ctxs=None, overlap_setup: bool = False,
+                       coarse_setup_fp32: bool = False):
     """Hierarchical reconstruction (Sec. 2.3) through the C ABI.
 
     Level l = 0 .. levels-1 reconstructs n_slices slices of N / 2^(levels-1-l) pixels.  A
@@ -592,7 +597,9 @@ def reconstruct_levels(N: int, angles, n_slices: int, sino, levels: int, params,
     subsampled sinogram, kernel spectrum and R*g, which depend on the data only) is enqueued
     first on that level's own context stream, so the setups of the finer levels run while the
     coarser levels iterate; the contexts must then have distinct streams (created here when
-    `ctxs` is None).  Without it all levels share one stream and run one after another.
+    `ctxs` is None).  Without it all levels share one stream and run one after another.  With
+    coarse_setup_fp32 the levels below the finest build their R*g in FP32
+    (tmbir_build_operator_fp32); the finest level's is FP64 either way.
     Returns the finest image, the level contexts and the per-level Stats.
     """
     import torch
@@ -623,7 +630,7 @@ def reconstruct_levels(N: int, angles, n_slices: int, sino, levels: int, params,
                        "sino": ctx._empty(n_slices * na * Nl) if f > 1 else None}
         lv = ctx._lv
         lv["sino_l"] = sino if f == 1 else ctx.downsample_sino(sino, n_slices, na, N, f, out=lv["sino"])
-        ctx.build_operator(lv["sino_l"], lv["atg"])
+        ctx.build_operator(lv["sino_l"], lv["atg"], fp64=not (coarse_setup_fp32 and lev < levels - 1))
 
     if overlap_setup:
         for lev in range(levels):

@@ -479,6 +479,30 @@ int tmbir_build_operator(tmbir_ctx* ctx, const float* d_sino, float* d_atg) {
   return TMBIR_OK;
 }
 
+int tmbir_build_operator_fp32(tmbir_ctx* ctx, const float* d_sino, float* d_atg) {
+  TMBIR_TRACE("tmbir_build_operator_fp32");
+  if (int e = require_ready(ctx, false)) return e;
+  REQUIRE(d_sino && d_atg && aligned16(d_sino) && aligned16(d_atg), TMBIR_ERR_ARG,
+          "build_operator_fp32: sinogram and output must be non-NULL and 16-byte aligned");
+  Ctx& c = ctx->c;
+  for (size_t i = 0; i < c.groups.size(); ++i) {
+    if (!c.spread_ready[i]) {
+      if (int e = build_spread_matrix(c, (int)i)) return e;
+      c.spread_ready[i] = true;
+    }
+    if (!c.geom_ready[i]) {
+      if (int e = build_kernel_spectrum(c, (int)i)) return e;
+      if (int e = power_iteration(c, (int)i, 100)) return e;
+      c.geom_ready[i] = true;
+    }
+    // R*g by the FP32 back-projection (the FBP start's transform, without the ramp filter)
+    if (int e = backproject(c, (int)i, d_sino, d_atg, false, false)) return e;
+    if (int e = group_gtg(c, (int)i, d_sino)) return e;
+  }
+  c.operator_built = true;
+  return TMBIR_OK;
+}
+
 // build_operator and fbp in one call: R*g (FP64) on the context stream while the FBP start
 // (FP32, its own scratch) runs on a second stream, joined before the call returns its work.
 int tmbir_build_operator_fbp(tmbir_ctx* ctx, const float* d_sino, float* d_atg, float* d_x0) {

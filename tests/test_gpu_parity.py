@@ -545,15 +545,18 @@ def test_downsample_sino_bitwise(orc):
         assert np.array_equal(d, orc.downsample_sino(g.astype(np.float64), f))
 
 
-def test_hierarchical_levels_follow_oracle(orc):
+@pytest.mark.parametrize("coarse_fp32", [False, True], ids=["fp64_setup", "fp32_coarse_setup"])
+def test_hierarchical_levels_follow_oracle(orc, coarse_fp32):
     # three levels 64 -> 128 -> 256 (Sec. 2.3): coarse sinograms by bin subsampling, FBP at the
-    # coarsest level, Lanczos-3 x2 upsampling between levels; the oracle runs the same chain
+    # coarsest level, Lanczos-3 x2 upsampling between levels; the oracle runs the same chain (with
+    # the FP64 R*g at every level, also when the coarse levels build theirs in FP32)
     N, S, na, levels = 256, 3, 60, 3
     iters = [25, 15, 8]
     p = synth.volume(S=S, N=N, n_angles=na, n_ellipsoids=6, seed=61)
     pr = orc.Prior(**PRIOR)
     x, ctxs, stats = tm.reconstruct_levels(N, p.theta, S, dev(p.sino), levels,
-                                           [tm.Params(**PRIOR, max_iter=k) for k in iters])
+                                           [tm.Params(**PRIOR, max_iter=k) for k in iters],
+                                           coarse_setup_fp32=coarse_fp32)
     assert [s.iterations for s in stats] == iters
     g = p.sino.astype(np.float64)
     xo = None
@@ -622,3 +625,16 @@ def test_bounded_wait_gives_up_and_the_context_stays_usable():
     ctx.wait_check(1 << 20, arrive=True)
     after = host(ctx.normal_apply(x), (64, 64))
     assert np.array_equal(before, after)
+
+
+def test_fp32_setup_for_coarse_levels(prob, orc):
+    """tmbir_build_operator_fp32: R*g from the FP32 back-projection (within FP32 transform
+    error of the oracle's sums), the same kernel, lambda_max and 1/2 g.g as the FP64 build."""
+    ctx = tm.Context([tm.Group(N=prob.N, angles=list(prob.theta), n_slices=prob.S, span=prob.span)])
+    atg32 = ctx.build_operator(prob.d_sino, fp64=False)
+    assert rel(host(atg32, prob.atg.shape), prob.atg) < 1e-5
+    assert torch.equal(ctx.kernel(0), prob.ctx.kernel(0))
+    assert ctx.lambda_max()[0] == prob.ctx.lambda_max()[0]
+    F64 = prob.ctx.objective(dev(prob.x), prob.d_atg, tm.Params(**PRIOR))
+    F32 = ctx.objective(dev(prob.x), atg32, tm.Params(**PRIOR))
+    assert abs(F32 - F64) <= 1e-5 * abs(F64)
