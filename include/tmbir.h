@@ -158,6 +158,19 @@ int tmbir_workspace_size(const tmbir_ctx* ctx, size_t* bytes);
 int tmbir_set_workspace(tmbir_ctx* ctx, void* d_workspace, size_t bytes);
 
 /*
+ * Per-angle weights of the data term (a variant of Eq. 5: F = 1/2 sum_a w_a ||R_a f - g_a||^2 +
+ * lambda Phi(f), e.g. to down-weight noisy or partial views).  Weights that depend on the angle
+ * alone keep R* W R shift-invariant, so the Toeplitz form holds with the kernel
+ * K_w(d) = (1/n_det) sum_{a,k} w_a exp(2 pi i xi_{a,k} . d), and R*g becomes R* W g.
+ *   group  index of the geometry group (0 .. n_groups - 1).
+ *   h_w    host array of the group's n_angles weights in [0, 1] (copied), or NULL for all 1.
+ * The weights enter K, lambda_max, R*g and 1/2 g.g at the next tmbir_build_operator* call (the
+ * previous operator is dropped) and the direct gradient (R* W (R x - g)); the FBP start and
+ * tmbir_adjoint stay unweighted.  Call after tmbir_set_geometry; a later set_geometry clears them.
+ */
+int tmbir_set_angle_weights(tmbir_ctx* ctx, int group, const double* h_w);
+
+/*
  * Setup of Sec. 2.1 ("computed once prior to the iterative reconstruction"): per group the
  * point-spread kernel K = NUFFT1(ones) on [-(N-1), N-1]^2 and the real spectrum of its 2N x 2N
  * circulant embedding (kept in the workspace); R*g for every slice into d_atg

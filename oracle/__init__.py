@@ -166,6 +166,38 @@ def kernel(N: int, theta, nd: int) -> np.ndarray:
     return K
 
 
+def kernel_weighted(N: int, theta, nd: int, w) -> np.ndarray:
+    """K_w = sum_a w_a K_a: the kernel of R* W R for per-angle data-term weights w_a, written as the
+    weighted sum of the kernels of each angle alone (each K_a the Dirichlet sum of Sec. 2.1)."""
+    th = _f64(theta)
+    w = _f64(w)
+    K = np.zeros((2 * N - 1, 2 * N - 1))
+    for a in range(th.size):
+        if w[a] != 0.0:
+            K += w[a] * kernel(N, th[a:a + 1], nd)
+    return K
+
+
+def adjoint_weighted(g, N: int, theta, w) -> np.ndarray:
+    """R* W g: every projection g_a scaled by its weight w_a, then the adjoint."""
+    g = _f64(g)
+    return adjoint(g * _f64(w).reshape((1,) * (g.ndim - 2) + (-1, 1)), N, theta)
+
+
+def gtg_weighted(g, w) -> float:
+    """g . W g = sum_a w_a ||g_a||^2 (the objective takes its half)."""
+    g = _f64(g)
+    return float(np.sum(_f64(w).reshape((1,) * (g.ndim - 2) + (-1, 1)) * g * g))
+
+
+def objective_direct_weighted(x, g, theta, pr: Prior, w) -> float:
+    """1/2 sum_a w_a ||A_a x - g_a||^2 + lambda Phi(x), A by brute force."""
+    x = _f64(x)
+    g = _f64(g)
+    r = forward(x, theta, g.shape[-1]) - g
+    return 0.5 * float(np.sum(_f64(w).reshape((1,) * (g.ndim - 2) + (-1, 1)) * r * r)) + prior(x, pr)[1]
+
+
 def normal_direct(x, K) -> np.ndarray:
     """sum_i K(x_j - x_i) x_i by the direct sum, for a slice or a stack."""
     x = _f64(x)

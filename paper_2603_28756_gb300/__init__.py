@@ -87,7 +87,7 @@ SYMBOLS = [
     "tmbir_state_size", "tmbir_state_export", "tmbir_state_import", "tmbir_autotune", "tmbir_build_operator_fbp",
     "tmbir_wait_check", "tmbir_forward", "tmbir_adjoint", "tmbir_gradient_direct", "tmbir_sfu_rate",
     "tmbir_stream_workspace_size", "tmbir_stream_build_operator", "tmbir_stream_reconstruct",
-    "tmbir_build_operator_fp32",
+    "tmbir_build_operator_fp32", "tmbir_set_angle_weights",
 ]
 
 _lib = None
@@ -112,6 +112,7 @@ def load(path: str | None = None):
         "tmbir_set_workspace": [vp, vp, sz],
         "tmbir_build_operator": [vp, vp, vp],
         "tmbir_build_operator_fp32": [vp, vp, vp],
+        "tmbir_set_angle_weights": [vp, i, dp],
         "tmbir_fbp": [vp, vp, vp],
         "tmbir_reconstruct": [vp, vp, vp, ctypes.POINTER(_Params), ctypes.POINTER(_Stats)],
         "tmbir_get_log": [vp, dp, i, ctypes.POINTER(i)],
@@ -295,6 +296,17 @@ class Context:
                     t.record_stream(self.stream)
 
     # calls --------------------------------------------------------------------
+    def set_angle_weights(self, group: int, weights=None):
+        """Per-angle data-term weights in [0, 1] for one group (None: all 1); the next
+        build_operator rebuilds K, lambda_max, R*g and 1/2 g.g with them."""
+        if weights is None:
+            _check(_lib.tmbir_set_angle_weights(self._h, int(group), None))
+            return
+        w = (ctypes.c_double * len(weights))(*[float(v) for v in weights])
+        if len(weights) != len(self.groups[group].angles):
+            raise ValueError("one weight per angle")
+        _check(_lib.tmbir_set_angle_weights(self._h, int(group), w))
+
     def build_operator(self, sino, atg=None, fp64: bool = True):
         """K, its spectrum, lambda_max, 1/2 g.g and R*g (FP64, or FP32 with fp64=False)."""
         atg = self._empty(self.image_numel()) if atg is None else atg

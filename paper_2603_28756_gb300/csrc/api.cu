@@ -264,6 +264,7 @@ int tmbir_set_geometry(tmbir_ctx* ctx, int n_groups, const tmbir_group* groups) 
   for (int k = 0; k < 2; ++k) c.psiS_h[k].assign(n_groups, {});
   c.geom_ready.assign(n_groups, false);
   c.spread_ready.assign(n_groups, false);
+  c.weights.assign(n_groups, {});
 
   // workspace layout
   size_t off = 0;
@@ -307,6 +308,7 @@ int tmbir_set_geometry(tmbir_ctx* ctx, int n_groups, const tmbir_group* groups) 
   }
   c.off_lam.resize(n_groups);
   c.off_gtg.resize(n_groups);
+  c.off_wts.resize(n_groups);
   for (int i = 0; i < n_groups; ++i) {
     const size_t N = gs[i].N;
     c.off_chat[i] = take((N + 1) * 2 * N * sizeof(float));
@@ -326,6 +328,7 @@ int tmbir_set_geometry(tmbir_ctx* ctx, int n_groups, const tmbir_group* groups) 
     }
     c.off_lam[i] = take(sizeof(double));
     c.off_gtg[i] = take(sizeof(double));
+    c.off_wts[i] = take(gs[i].n_angles * sizeof(double));
     nufft_psi_table(2 * N - 1, 4 * N, 12, c.nufft_beta64, c.psiK_h[i]);
     for (int k = 0; k < 2; ++k)
       nufft_psi_table(N, spread_grid(k, (int)N), kSpreadWidth[k], spread_beta(k), c.psiS_h[k][i]);
@@ -419,6 +422,13 @@ int tmbir_set_workspace(tmbir_ctx* ctx, void* d_ws, size_t bytes) {
     }
     d.lam_max = reinterpret_cast<double*>(ws + c.off_lam[i]);
     d.gtg = reinterpret_cast<double*>(ws + c.off_gtg[i]);
+    d.wts = nullptr;
+    if (!c.weights[i].empty()) {
+      double* w = reinterpret_cast<double*>(ws + c.off_wts[i]);
+      TMBIR_CUDA(cudaMemcpyAsync(w, c.weights[i].data(), c.weights[i].size() * sizeof(double), cudaMemcpyHostToDevice,
+                                 c.stream));
+      d.wts = w;
+    }
     // twiddle tables: twN[k][t] = exp(-2 pi i t k / N) in the group-FFT layout (the plain
     // table exp(-2 pi i j / N) for the block-FFT sides), twM[n] = exp(-2 pi i n / 2N)
     int T, P;
@@ -454,6 +464,39 @@ int tmbir_set_workspace(tmbir_ctx* ctx, void* d_ws, size_t bytes) {
 }
 
 
+int tmbir_set_angle_weights(tmbir_ctx* ctx, int group, const double* h_w) {
+  TMBIR_TRACE("tmbir_set_angle_weights");
+  REQUIRE(ctx != nullptr, TMBIR_ERR_ARG, "set_angle_weights: ctx is NULL");
+  Ctx& c = ctx->c;
+  REQUIRE(!c.groups.empty(), TMBIR_ERR_STATE, "set_angle_weights: no geometry");
+  REQUIRE(group >= 0 && group < (int)c.groups.size(), TMBIR_ERR_ARG, "set_angle_weights: no such group");
+  const int na = c.groups[group].n_angles;
+  std::vector<double> w;
+  if (h_w) {
+    w.assign(h_w, h_w + na);
+    for (double v : w)
+      REQUIRE(std::isfinite(v) && v >= 0.0 && v <= 1.0, TMBIR_ERR_ARG, "set_angle_weights: weights must lie in [0, 1]");
+  }
+  c.weights[group] = w;
+  GroupDev& d = c.gdev[group];
+  d.wts = nullptr;
+  if (c.ws && !w.empty()) {
+    double* dw = reinterpret_cast<double*>(c.ws + c.off_wts[group]);
+    TMBIR_CUDA(cudaMemcpyAsync(dw, c.weights[group].data(), na * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+    TMBIR_CUDA(cudaStreamSynchronize(c.stream));
+    d.wts = dw;
+  }
+  // K, lambda_max, R*g and 1/2 g.g depend on the weights: rebuilt by the next build call
+  c.geom_ready[group] = false;
+  c.operator_built = false;
+  c.state_ready = false;
+  if (c.graph_exec) {
+    cudaGraphExecDestroy(c.graph_exec);
+    c.graph_exec = nullptr;
+  }
+  return TMBIR_OK;
+}
+
 int tmbir_build_operator(tmbir_ctx* ctx, const float* d_sino, float* d_atg) {
   TMBIR_TRACE("tmbir_build_operator");
   if (int e = require_ready(ctx, false)) return e;
@@ -472,7 +515,7 @@ int tmbir_build_operator(tmbir_ctx* ctx, const float* d_sino, float* d_atg) {
       c.geom_ready[i] = true;
     }
     // data parts: every call
-    if (int e = backproject(c, (int)i, d_sino, d_atg, false, true)) return e;
+    if (int e = backproject(c, (int)i, d_sino, d_atg, false, true, nullptr, nullptr, false, true)) return e;
     if (int e = group_gtg(c, (int)i, d_sino)) return e;
   }
   c.operator_built = true;
@@ -496,7 +539,7 @@ int tmbir_build_operator_fp32(tmbir_ctx* ctx, const float* d_sino, float* d_atg)
       c.geom_ready[i] = true;
     }
     // R*g by the FP32 back-projection (the FBP start's transform, without the ramp filter)
-    if (int e = backproject(c, (int)i, d_sino, d_atg, false, false)) return e;
+    if (int e = backproject(c, (int)i, d_sino, d_atg, false, false, nullptr, nullptr, false, true)) return e;
     if (int e = group_gtg(c, (int)i, d_sino)) return e;
   }
   c.operator_built = true;
@@ -536,7 +579,7 @@ int tmbir_build_operator_fbp(tmbir_ctx* ctx, const float* d_sino, float* d_atg, 
   for (size_t i = 0; i < c.groups.size() && rc == TMBIR_OK; ++i)
     rc = backproject(c, (int)i, d_sino, d_x0, true, false, c.fbp_scratch, c.aux);
   for (size_t i = 0; i < c.groups.size() && rc == TMBIR_OK; ++i) {
-    if ((rc = backproject(c, (int)i, d_sino, d_atg, false, true))) break;
+    if ((rc = backproject(c, (int)i, d_sino, d_atg, false, true, nullptr, nullptr, false, true))) break;
     rc = group_gtg(c, (int)i, d_sino);
   }
   // join whatever was enqueued, also after an error
@@ -925,8 +968,10 @@ int tmbir_gradient_direct(tmbir_ctx* ctx, const float* d_x, const float* d_sino,
     const GroupDev& g = c.gdev[i];
     if (int e = forward_project(c, i, d_x, c.sino_tmp)) return e;
     if (int e = residual(c, i, c.sino_tmp, d_sino)) return e;
-    if (int e = half_sumsq(c, c.sino_tmp + g.sino_off, (size_t)g.S * g.na * g.nd, c.dscal + 16 + i)) return e;
-    if (int e = backproject(c, i, c.sino_tmp, g.kz, false, false, nullptr, nullptr, true)) return e;
+    if (int e = half_sumsq(c, c.sino_tmp + g.sino_off, (size_t)g.S * g.na * g.nd, c.dscal + 16 + i, nullptr, g.wts,
+                           g.na, g.nd))
+      return e;
+    if (int e = backproject(c, i, c.sino_tmp, g.kz, false, false, nullptr, nullptr, true, true)) return e;
   }
   TMBIR_CUDA(cudaMemsetAsync(c.xbuf[0], 0, c.total_voxels * sizeof(float), s));
   StepArgs a{};

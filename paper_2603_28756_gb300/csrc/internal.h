@@ -98,6 +98,7 @@ struct GroupDev {
   double* K;           // [(2N-1)^2] point-spread kernel
   double* psiK;        // [2N-1] deconvolution factors for K (fine grid 4N)
 
+  const double* wts;   // [na] per-angle weights of the data term (nullptr: all 1)
   double* lam_max;     // device scalar
   double* gtg;         // device scalar (1/2 g.g of the group)
   // sparse spreading operators (geometry only): sp[0] for the FP32 paths, sp[1] for R*g in FP64
@@ -170,6 +171,7 @@ struct Ctx {
   // host copies of the NUFFT deconvolution tables (uploaded at set_workspace)
   std::vector<std::vector<double>> psiK_h, psiS_h[2];
   double nufft_beta64 = 0;
+  std::vector<std::vector<double>> weights;  // per-angle data-term weights per group (empty: all 1)
   std::vector<bool> geom_ready;    // K, its spectrum and lambda_max built
   std::vector<bool> spread_ready;  // sparse spreading matrix built
   size_t total_voxels = 0, total_sino = 0;
@@ -189,7 +191,7 @@ struct Ctx {
   bool operator_built = false;
   int last_iters = 0;
   // layout offsets computed at set_geometry
-  std::vector<size_t> off_chat, off_twN, off_twM, off_spec, off_kz, off_ang, off_K, off_psiK, off_lam, off_gtg;
+  std::vector<size_t> off_chat, off_twN, off_twM, off_spec, off_kz, off_ang, off_K, off_psiK, off_lam, off_gtg, off_wts;
   std::vector<size_t> off_sp_psi[2], off_sp_ptr[2], off_sp_idx[2], off_sp_wt[2];
   size_t off_state = 0, off_gmom = 0, off_partials = 0, off_log = 0, off_xbuf0 = 0, off_xbuf1 = 0, off_scratch = 0, off_dscal = 0;
   size_t off_fbp_scratch = 0;
@@ -312,10 +314,13 @@ int setup_tables(Ctx& c);  // enqueue uploads of twiddles / psi tables into the 
 int build_kernel_spectrum(Ctx& c, int gi);
 // scratch / s: null for the context's setup scratch and stream
 // local_out: d_out is the group's own [slice][row][col] buffer (no stacked-image offset)
+// weighted: the sinogram rows scaled by the group's per-angle weights (R* W g) when it has them
 int backproject(Ctx& c, int gi, const float* d_sino, float* d_out, bool ramp, bool fp64, char* scratch = nullptr,
-                cudaStream_t s = nullptr, bool local_out = false);
-// *d_out = 1/2 sum p[i]^2 (FP64, fixed order; uses the setup scratch)
-int half_sumsq(Ctx& c, const float* p, size_t n, double* d_out, cudaStream_t s = nullptr);
+                cudaStream_t s = nullptr, bool local_out = false, bool weighted = false);
+// *d_out = 1/2 sum p[i]^2 (FP64, fixed order; uses the setup scratch); with wts, element i of the
+// [slice][angle][bin] rows (na angles, nd bins) counts wts[angle] times
+int half_sumsq(Ctx& c, const float* p, size_t n, double* d_out, cudaStream_t s = nullptr, const double* wts = nullptr,
+               int na = 0, int nd = 0);
 size_t fbp_scratch_bytes(const tmbir_group& g);  // FP32 back-projection scratch of one group
 int build_spread_matrix(Ctx& c, int gi);
 // R x of one group by the type-2 NUFFT (FP32, Eqs. 3-4) into d_sino (the group's rows of the

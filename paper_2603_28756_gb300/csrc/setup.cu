@@ -216,7 +216,7 @@ __device__ __forceinline__ double es_kernel(double z, double beta) {  // z in [-
 constexpr double kFixScale = 4503599627370496.0;  // 2^52
 template <int W>
 __global__ void k_spread_fixed(const double* __restrict__ angles, int na, int nd, int nf,
-                               unsigned long long* __restrict__ grid, double beta) {
+                               unsigned long long* __restrict__ grid, double beta, const double* __restrict__ wts) {
   const int npa = nd - 1;
   const size_t total = (size_t)na * npa;
   for (size_t id = blockIdx.x * (size_t)blockDim.x + threadIdx.x; id < total; id += (size_t)gridDim.x * blockDim.x) {
@@ -232,7 +232,7 @@ __global__ void k_spread_fixed(const double* __restrict__ angles, int na, int nd
       kx[j] = es_kernel((2.0 * (lx0 + j - ux)) / W, beta);
       ky[j] = es_kernel((2.0 * (ly0 + j - uy)) / W, beta);
     }
-    const double c = kFixScale / nd;
+    const double c = kFixScale / nd * (wts ? wts[a] : 1.0);  // weights in [0, 1] keep the bound
 #pragma unroll 1
     for (int jy = 0; jy < W; ++jy) {
       const int ly = (ly0 + jy + nf) % nf;
@@ -500,15 +500,18 @@ __global__ void k_prepare_rows(const float* __restrict__ sino, int nd, size_t ro
 // the pair's result carries slice 2p in the real and slice 2p+1 in the imaginary part.
 // Written sample-major, out[(a nd + k) PB + p], so the gather reads the PB pairs of a sample
 // from one contiguous run.
+// wts: per-angle weights of the data term (R* W g; nullptr: none), angle = r / nd.
 template <int PB, class C>
-__global__ void k_strength_pack(const C* __restrict__ rows, int nd, size_t nrows, int nb, C* __restrict__ out) {
+__global__ void k_strength_pack(const C* __restrict__ rows, int nd, size_t nrows, int nb, C* __restrict__ out,
+                                const double* __restrict__ wts) {
   using S = real_t<C>;
   const size_t total = nrows * PB;
   for (size_t id = blockIdx.x * (size_t)blockDim.x + threadIdx.x; id < total; id += (size_t)gridDim.x * blockDim.x) {
     const int pr = (int)(id % PB);
     const size_t r = id / PB;
     const int k = (int)(r % nd);
-    const S sg = (k & 1) ? (S)(-1.0 / nd) : (S)(1.0 / nd);
+    const double w = wts ? wts[r / nd] / nd : 1.0 / nd;
+    const S sg = (k & 1) ? (S)(-w) : (S)w;
     const C a = 2 * pr < nb ? rows[(size_t)(2 * pr) * nrows + r] : mkc((S)0, (S)0);
     const C b = 2 * pr + 1 < nb ? rows[(size_t)(2 * pr + 1) * nrows + r] : mkc((S)0, (S)0);
     out[id] = mkc((a.x - b.y) * sg, (a.y + b.x) * sg);
@@ -517,12 +520,13 @@ __global__ void k_strength_pack(const C* __restrict__ rows, int nd, size_t nrows
 
 // 1/2 sum x^2: each block reduces a strided share in FP64 (fixed order), then one block sums
 // the block partials in order.
-__global__ void k_sumsq_blocks(const float* __restrict__ x, size_t n, double* part) {
+__global__ void k_sumsq_blocks(const float* __restrict__ x, size_t n, double* part, const double* __restrict__ wts,
+                               int na, int nd) {
   __shared__ double sh[256];
   double s = 0.0;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     const double v = x[i];
-    s += v * v;
+    s += wts ? wts[(i / nd) % na] * (v * v) : v * v;
   }
   sh[threadIdx.x] = s;
   __syncthreads();
@@ -653,9 +657,9 @@ __global__ void k_twiddle(C* tw, int n) {
   }
 }
 
-// K(d) = (1/n_det) sum_a D(e_a . d) summed directly, D(t) = sin(pi (n_det - 1) e / n_det) /
+// K(d) = (1/n_det) sum_a w_a D(e_a . d) summed directly, D(t) = sin(pi (n_det - 1) e / n_det) /
 // sin(pi e / n_det) with e = t reduced to the nearest period of n_det, and n_det - 1 where the
-// denominator vanishes; cs holds (cos, sin) of every angle
+// denominator vanishes; cs holds (cos, sin) of every angle, wts the weights w_a (nullptr: 1)
 __global__ void k_angle_table(const double* __restrict__ angles, int na, double2* cs) {
   for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < na; a += gridDim.x * blockDim.x) {
     double sv, cv;
@@ -663,7 +667,8 @@ __global__ void k_angle_table(const double* __restrict__ angles, int na, double2
     cs[a] = make_double2(cv, sv);
   }
 }
-__global__ void k_kernel_direct(const double2* __restrict__ cs, int na, int nd, int N, double* __restrict__ K) {
+__global__ void k_kernel_direct(const double2* __restrict__ cs, int na, int nd, int N, double* __restrict__ K,
+                                const double* __restrict__ wts) {
   const int W = 2 * N - 1;
   for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < W * W; id += gridDim.x * blockDim.x) {
     const double dx = (double)(id % W - (N - 1)), dy = (double)(id / W - (N - 1));
@@ -673,7 +678,8 @@ __global__ void k_kernel_direct(const double2* __restrict__ cs, int na, int nd, 
       const double t = dx * e2.x + dy * e2.y;
       const double e = t - (double)nd * rint(t / (double)nd);
       const double den = sinpi(e / (double)nd);
-      sum += den == 0.0 ? (double)(nd - 1) : sinpi((double)(nd - 1) * e / (double)nd) / den;
+      const double D = den == 0.0 ? (double)(nd - 1) : sinpi((double)(nd - 1) * e / (double)nd) / den;
+      sum += wts ? wts[a] * D : D;
     }
     K[id] = sum / (double)nd;
   }
@@ -689,7 +695,7 @@ int build_kernel_spectrum(Ctx& c, int gi) {
     double2* cs = reinterpret_cast<double2*>(c.scratch) + nf + 2 * (size_t)M * M;
     k_angle_table<<<(g.na + 255) / 256, 256, 0, s>>>(g.angles, g.na, cs);
     TMBIR_CHECK_LAUNCH();
-    k_kernel_direct<<<152 * 16, 256, 0, s>>>(cs, g.na, g.nd, N, g.K);
+    k_kernel_direct<<<152 * 16, 256, 0, s>>>(cs, g.na, g.nd, N, g.K, g.wts);
     TMBIR_CHECK_LAUNCH();
     return circulant_spectrum(c, gi);
   }
@@ -703,7 +709,7 @@ int build_kernel_spectrum(Ctx& c, int gi) {
   {
     const size_t total = (size_t)g.na * (g.nd - 1);
     const int blocks = (int)std::min<size_t>((total + 255) / 256, 152 * 16);
-    k_spread_fixed<12><<<blocks, 256, 0, s>>>(g.angles, g.na, g.nd, nf, fixed_grid, c.nufft_beta64);
+    k_spread_fixed<12><<<blocks, 256, 0, s>>>(g.angles, g.na, g.nd, nf, fixed_grid, c.nufft_beta64, g.wts);
     TMBIR_CHECK_LAUNCH();
   }
   k_fixed_to_complex<<<1024, 256, 0, s>>>(fixed_grid, grid, (size_t)nf * nf);
@@ -764,7 +770,7 @@ int build_spread_matrix(Ctx& c, int gi) {
 
 template <class C>
 static int backproject_t(Ctx& c, int gi, const float* d_sino, float* d_out, bool ramp, float scale, char* scratch,
-                         cudaStream_t s, bool local_out) {
+                         cudaStream_t s, bool local_out, const double* wts) {
   GroupDev& g = c.gdev[gi];
   // R*g in FP64 on the 5N/4 grid, the FP32 back-projections on the 2N grid
   const GroupDev::Spread& sp = g.sp[sizeof(real_t<C>) == 8 ? 1 : 0];
@@ -788,7 +794,7 @@ static int backproject_t(Ctx& c, int gi, const float* d_sino, float* d_out, bool
     if (int e = fft_rows(strengths, nd, nb * na, +1, tw, s)) return e;
     constexpr int PB = kBackprojBatch / 2;  // slice pairs per batch
     const int np = (nb + 1) / 2;
-    k_strength_pack<PB, C><<<1024, 256, 0, s>>>(strengths, nd, rows, nb, strengths_t);
+    k_strength_pack<PB, C><<<1024, 256, 0, s>>>(strengths, nd, rows, nb, strengths_t, wts);
     TMBIR_CHECK_LAUNCH();
     k_csr_gather<PB, C><<<(ncells + 255) / 256, 256, 0, s>>>(sp.ptr, sp.idx, sp.wt, ncells, strengths_t,
                                                               grid, np);
@@ -814,19 +820,20 @@ static int backproject_t(Ctx& c, int gi, const float* d_sino, float* d_out, bool
 }
 
 int backproject(Ctx& c, int gi, const float* d_sino, float* d_out, bool ramp, bool fp64, char* scratch,
-                cudaStream_t s, bool local_out) {
+                cudaStream_t s, bool local_out, bool weighted) {
   const GroupDev& g = c.gdev[gi];
   const float scale = ramp ? (float)(g.span / g.na) : 1.0f;
+  const double* wts = weighted ? g.wts : nullptr;
   if (!scratch) scratch = c.scratch;
   if (!s) s = c.stream;
-  if (fp64) return backproject_t<double2>(c, gi, d_sino, d_out, ramp, scale, scratch, s, local_out);
-  return backproject_t<float2>(c, gi, d_sino, d_out, ramp, scale, scratch, s, local_out);
+  if (fp64) return backproject_t<double2>(c, gi, d_sino, d_out, ramp, scale, scratch, s, local_out, wts);
+  return backproject_t<float2>(c, gi, d_sino, d_out, ramp, scale, scratch, s, local_out, wts);
 }
 
-int half_sumsq(Ctx& c, const float* p, size_t n, double* d_out, cudaStream_t s) {
+int half_sumsq(Ctx& c, const float* p, size_t n, double* d_out, cudaStream_t s, const double* wts, int na, int nd) {
   if (!s) s = c.stream;
   double* part = reinterpret_cast<double*>(c.scratch);
-  k_sumsq_blocks<<<1024, 256, 0, s>>>(p, n, part);
+  k_sumsq_blocks<<<1024, 256, 0, s>>>(p, n, part, wts, na, nd);
   TMBIR_CHECK_LAUNCH();
   k_sum_half<<<1, 256, 0, s>>>(part, 1024, d_out);
   TMBIR_CHECK_LAUNCH();
@@ -986,7 +993,7 @@ int group_gtg(Ctx& c, int gi, const float* d_sino) {
   const GroupDev& g = c.gdev[gi];
   const float* p = d_sino + g.sino_off;
   double* part = reinterpret_cast<double*>(c.scratch);
-  k_sumsq_blocks<<<1024, 256, 0, c.stream>>>(p, (size_t)g.S * g.na * g.nd, part);
+  k_sumsq_blocks<<<1024, 256, 0, c.stream>>>(p, (size_t)g.S * g.na * g.nd, part, g.wts, g.na, g.nd);
   TMBIR_CHECK_LAUNCH();
   k_sum_half<<<1, 256, 0, c.stream>>>(part, 1024, g.gtg);
   TMBIR_CHECK_LAUNCH();
