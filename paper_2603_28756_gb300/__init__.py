@@ -303,7 +303,7 @@ class Context:
             _check(_lib.tmbir_set_angle_weights(self._h, int(group), None))
             return
         w = (ctypes.c_double * len(weights))(*[float(v) for v in weights])
-        if len(weights) != len(self.groups[group].angles):
+        if 0 <= group < len(self.groups) and len(weights) != len(self.groups[group].angles):
             raise ValueError("one weight per angle")
         _check(_lib.tmbir_set_angle_weights(self._h, int(group), w))
 
