@@ -14,6 +14,8 @@
 #include <type_traits>
 #include <utility>
 
+#include "dfloat.cuh"
+
 namespace tmbir {
 
 // ---------------------------------------------------------------- compile-time loops
@@ -82,6 +84,10 @@ __device__ __forceinline__ float2 mkc(float x, float y) { return make_float2(x, 
 __device__ __forceinline__ double2 mkc(double x, double y) { return make_double2(x, y); }
 __device__ __forceinline__ float fmar(float a, float b, float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ double fmar(double a, double b, double c) { return fma(a, b, c); }
+// double-word FP32 (the setup transforms of R*g): the same generic code, on the FP32 pipe
+template <> struct Real<dfc> { using type = df; };
+__device__ __forceinline__ dfc mkc(df x, df y) { return dfc{x, y}; }
+__device__ __forceinline__ df fmar(df a, df b, df c) { return a * b + c; }
 
 template <class C> __device__ __forceinline__ C cadd(C a, C b) { return mkc(a.x + b.x, a.y + b.y); }
 template <class C> __device__ __forceinline__ C csub(C a, C b) { return mkc(a.x - b.x, a.y - b.y); }

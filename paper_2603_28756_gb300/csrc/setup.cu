@@ -343,6 +343,25 @@ __global__ void k_scan_add(int* __restrict__ a, int n, const int* __restrict__ s
     if (t > 0) a[i] += sums[t - 1];
   }
 }
+// a weight of the sparse spreading matrix as the arithmetic's real type: FP64 and FP32 read the
+// double; the double-word matrix holds each weight as an (hi, lo) pair of floats in its 8 bytes
+template <class S>
+__device__ __forceinline__ S load_wt(const double* wt, int j) {
+  return (S)wt[j];
+}
+template <>
+__device__ __forceinline__ df load_wt<df>(const double* wt, int j) {
+  const float2 w = __ldg(reinterpret_cast<const float2*>(wt) + j);
+  return df(w.x, w.y);
+}
+// in place: every double weight of a spreading matrix becomes its double-word (hi, lo)
+__global__ void k_wt_to_df(double* wt, size_t n) {
+  for (size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x; j < n; j += (size_t)gridDim.x * blockDim.x) {
+    const df w(wt[j]);
+    reinterpret_cast<float2*>(wt)[j] = make_float2(w.hi, w.lo);
+  }
+}
+
 // grid[b][cell] = sum_j wt[j] strengths[idx[j]][b], B slices per launch (sample-major strengths)
 template <int B, class C>
 __global__ void k_csr_gather(const int* __restrict__ ptr, const int* __restrict__ idx, const double* __restrict__ wt,
@@ -359,7 +378,7 @@ __global__ void k_csr_gather(const int* __restrict__ ptr, const int* __restrict_
     for (; j + 1 < e; j += 2) {
       const C* sv0 = strengths + (size_t)idx[j] * B;
       const C* sv1 = strengths + (size_t)idx[j + 1] * B;
-      const S w0 = (S)wt[j], w1 = (S)wt[j + 1];
+      const S w0 = load_wt<S>(wt, j), w1 = load_wt<S>(wt, j + 1);
       C v0[B], v1[B];
 #pragma unroll
       for (int b = 0; b < B; ++b) {
@@ -376,7 +395,7 @@ __global__ void k_csr_gather(const int* __restrict__ ptr, const int* __restrict_
     }
     if (j < e) {
       const C* sv = strengths + (size_t)idx[j] * B;
-      const S w = (S)wt[j];
+      const S w = load_wt<S>(wt, j);
 #pragma unroll
       for (int b = 0; b < B; ++b) {
         const C v = sv[b];
@@ -764,6 +783,10 @@ int build_spread_matrix(Ctx& c, int gi) {
     TMBIR_CHECK_LAUNCH();
     k_csr_sort<<<(ncells + 255) / 256, 256, 0, s>>>(sp.ptr, ncells, sp.idx, sp.wt);
     TMBIR_CHECK_LAUNCH();
+    if (k == 1) {  // R*g runs in double-word FP32: its weights as (hi, lo) pairs
+      k_wt_to_df<<<1024, 256, 0, s>>>(sp.wt, spread_nnz(c.groups[gi], 1));
+      TMBIR_CHECK_LAUNCH();
+    }
   }
   return TMBIR_OK;
 }
@@ -772,7 +795,7 @@ template <class C>
 static int backproject_t(Ctx& c, int gi, const float* d_sino, float* d_out, bool ramp, float scale, char* scratch,
                          cudaStream_t s, bool local_out, const double* wts) {
   GroupDev& g = c.gdev[gi];
-  // R*g in FP64 on the 5N/4 grid, the FP32 back-projections on the 2N grid
+  // R*g in double-word FP32 on the 5N/4 grid, the FP32 back-projections on the 2N grid
   const GroupDev::Spread& sp = g.sp[sizeof(real_t<C>) == 8 ? 1 : 0];
   const int N = g.N, nf = sp.nf, nd = g.nd, na = g.na, ncells = nf * nf;
   const size_t rows = (size_t)na * nd;
@@ -826,7 +849,7 @@ int backproject(Ctx& c, int gi, const float* d_sino, float* d_out, bool ramp, bo
   const double* wts = weighted ? g.wts : nullptr;
   if (!scratch) scratch = c.scratch;
   if (!s) s = c.stream;
-  if (fp64) return backproject_t<double2>(c, gi, d_sino, d_out, ramp, scale, scratch, s, local_out, wts);
+  if (fp64) return backproject_t<dfc>(c, gi, d_sino, d_out, ramp, scale, scratch, s, local_out, wts);
   return backproject_t<float2>(c, gi, d_sino, d_out, ramp, scale, scratch, s, local_out, wts);
 }
 
