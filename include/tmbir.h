@@ -175,17 +175,21 @@ int tmbir_set_angle_weights(tmbir_ctx* ctx, int group, const double* h_w);
  * point-spread kernel K = NUFFT1(ones) on [-(N-1), N-1]^2 and the real spectrum of its 2N x 2N
  * circulant embedding (kept in the workspace); R*g for every slice into d_atg
  * [slice][row][col]; 1/2 g.g per group; lambda_max(R*R) by 100 power steps (kept in the
- * workspace).  d_sino is [slice][angle][bin] for all groups back to back.  FP64 arithmetic.
+ * workspace).  d_sino is [slice][angle][bin] for all groups back to back.  K, its spectrum and
+ * the reductions in FP64; R*g (the type-1 NUFFT of Eq. 4 on a 1.25x grid) in double-word FP32
+ * arithmetic (hi + lo pairs of FP32, a 48-bit significand: FP64-class accuracy, about 1e-10
+ * relative before the FP32 store) on the FP32 pipe, whose rate on GB300 is far above the FP64
+ * pipe's.
  */
 int tmbir_build_operator(tmbir_ctx* ctx, const float* d_sino, float* d_atg);
 
 /*
  * tmbir_build_operator with R*g computed in FP32: the back-projection of the FBP start without
  * its ramp filter (2N spreading grid, width-10 kernel, FP32 arithmetic: the error of an FP32
- * transform, against 1e-10 for the FP64 one before the FP32 store), at a fraction of the FP64
- * transform's cost on a GPU whose FP64 rate is far below its FP32 rate.  K, its spectrum, lambda_max and 1/2 g.g are
- * built as in tmbir_build_operator.  Meant for the coarse levels of the hierarchy (Sec. 2.3),
- * whose result only starts the next level; the finest level keeps the FP64 R*g.
+ * transform, against about 1e-10 for the double-word one before the FP32 store), at a fraction
+ * of that transform's cost.  K, its spectrum, lambda_max and 1/2 g.g are built as in
+ * tmbir_build_operator.  Meant for the coarse levels of the hierarchy (Sec. 2.3), whose result
+ * only starts the next level; the finest level keeps the double-word R*g.
  */
 int tmbir_build_operator_fp32(tmbir_ctx* ctx, const float* d_sino, float* d_atg);
 
@@ -197,7 +201,7 @@ int tmbir_build_operator_fp32(tmbir_ctx* ctx, const float* d_sino, float* d_atg)
 int tmbir_fbp(tmbir_ctx* ctx, const float* d_sino, float* d_x0);
 
 /*
- * tmbir_build_operator and tmbir_fbp in one call, the two overlapped: R*g (FP64) runs on the
+ * tmbir_build_operator and tmbir_fbp in one call, the two overlapped: R*g (double-word) runs on the
  * context stream while the FBP start (FP32) runs on a second stream the context owns, joined
  * back into the context stream before any later work.  Same results as the two calls;
  * d_atg and d_x0 must differ.  Needs a non-NULL context stream.
