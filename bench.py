@@ -590,6 +590,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="launch the iterations eagerly (profiling)")
     ap.add_argument("--no-gap", action="store_true", help="skip the time-to-gap forms")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="keep the default coarse iteration counts instead of timing the candidates (profiling)")
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.impl == "reference":
@@ -662,7 +664,10 @@ def run_ours(args, tm, w, prob, stream, rank, world, local, barrier, extra):
         except Exception as e:  # reported, not hidden: the step then starts from FBP
             extra["warm_start_training"] = {"error": str(e)[:300]}
         progress(f"warm start trained: {extra['warm_start_training']}")
-        coarse, extra["coarse_iteration_tuning"] = tune_coarse(H, sino, F_ref, stream, barrier, world)
+        if args.no_tune:
+            coarse, extra["coarse_iteration_tuning"] = COARSE_ITERS, "skipped (--no-tune)"
+        else:
+            coarse, extra["coarse_iteration_tuning"] = tune_coarse(H, sino, F_ref, stream, barrier, world)
         progress(f"coarse iterations {coarse}: {extra['coarse_iteration_tuning']}")
         prms = chosen_params(F_ref, coarse)
         if args.no_graph:  # profiling: every iteration's kernels launched one by one
