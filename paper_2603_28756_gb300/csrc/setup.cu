@@ -433,20 +433,26 @@ __global__ void __launch_bounds__(256) k_deconv_pruned(const C* __restrict__ B, 
                                                        const double* __restrict__ psi, float scale,
                                                        float* __restrict__ out) {
   __shared__ C tile[32][33];
+  __shared__ double inv_r[32], inv_c[32];  // 1 / psi of the tile's rows and columns
   const int p = blockIdx.z, c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
   const C* Bp = B + (size_t)p * N * nf;
   for (int i = threadIdx.y; i < 32; i += blockDim.y) {  // column c0 + i, rows r0 .. r0 + 31
     const int c = c0 + i, r = r0 + threadIdx.x;
     if (c < N && r < N) tile[i][threadIdx.x] = Bp[(size_t)c * nf + (r - N / 2 + nf) % nf];
   }
+  if (threadIdx.y == 0) {  // one division per row and column of the tile instead of one per pixel
+    const int r = r0 + threadIdx.x, c = c0 + threadIdx.x;
+    inv_r[threadIdx.x] = r < N ? 1.0 / psi[r] : 0.0;
+    inv_c[threadIdx.x] = c < N ? 1.0 / psi[c] : 0.0;
+  }
   __syncthreads();
   for (int i = threadIdx.y; i < 32; i += blockDim.y) {  // row r0 + i, columns c0 .. c0 + 31
     const int r = r0 + i, c = c0 + threadIdx.x;
     if (c >= N || r >= N) continue;
     const C v = tile[threadIdx.x][i];
-    const double d = psi[c] * psi[r];
-    out[((size_t)(2 * p) * N + r) * N + c] = (float)(scale * ((double)v.x / d));
-    if (2 * p + 1 < nb) out[((size_t)(2 * p + 1) * N + r) * N + c] = (float)(scale * ((double)v.y / d));
+    const double f = scale * inv_c[threadIdx.x] * inv_r[i];
+    out[((size_t)(2 * p) * N + r) * N + c] = (float)((double)v.x * f);
+    if (2 * p + 1 < nb) out[((size_t)(2 * p + 1) * N + r) * N + c] = (float)((double)v.y * f);
   }
 }
 
