@@ -1,6 +1,6 @@
 // Volumes larger than the device's memory (Sec. 2.4).  The volume, its sinogram and R*g stay in
-// host memory and pass through the GPU in slabs of slices; the context's one geometry group is
-// the slab.  The paper's node scheduler (three threads joined by bounded work queues: copies in,
+// host memory (R*g may instead stay in device memory, read in place) and pass through the GPU in
+// slabs of slices; the context's one geometry group is the slab.  The paper's node scheduler (three threads joined by bounded work queues: copies in,
 // kernels, copies out) becomes three CUDA streams and two device buffer sets ordered by events,
 // so the copies of slab j + 1 in and of slab j - 1 out overlap the kernels of slab j.
 //
